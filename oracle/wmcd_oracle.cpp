@@ -1,0 +1,1140 @@
+/*
+ * CPU oracle for Wavelet Monte Carlo dynamics (Dyer & Ball, arXiv:1611.09160).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is a plain, slow, sequential FP64 statement of
+ * what the WMCD sweep computes. It is loaded only by the test-suite, by the smoke check
+ * and by the benchmark's CPU-baseline leg; the product library never links, loads or
+ * calls it, and it shares no code, header, table or constant generator with the CUDA
+ * library. The only thing both sides share is the seeded input generator (initial bead
+ * positions), which contains none of the method's arithmetic.
+ *
+ * What it follows (sections and equations of the paper):
+ *   - potentials: FENE (Eq. 1), WCA (Eq. 2), harmonic theta-solvent bond (Sec. VI.B);
+ *   - the move loop and Metropolis test (Sec. V, Eq. 20); no Jacobian (divergence-free);
+ *   - tapered wavelet, w = p x grad(phi), phi = r^2/2 - r^3/3 - 1/6 (Sec. V.A, Eqs. 21-25),
+ *     which gives the displacement  d = A_w (1 - |x|) (p x x),  x = (r - b)/lambda;
+ *   - P_b (Eq. 26), A_w = A0 lambda / sqrt(n) (Eq. 29), P_lambda ~ lambda^-4 (Eq. 32);
+ *   - time per accepted move (Eq. 34 wavelet-only, Eq. 57 wavelet + plane wave);
+ *   - lambda_a = (2/pi) M4/M3 (Eq. 42) with the moments M_m of Eq. 22;
+ *   - plane-wave moves (Sec. VI, Eqs. 47, 48, 51, 55, 56) and
+ *   - the generation procedures of Appendix D (choice of move type, lambda by inverse
+ *     transform, bead pick, uniform point in a ball by rejection, polarisation, n counted
+ *     with one image, periodic k, phase and polarisation of a plane wave, recycling of
+ *     lambda and |k| after a rejection, time advanced only on acceptance).
+ *
+ * Readings where the paper leaves a choice (a "sweep", the layered lambda schedule, the
+ * colouring and deferral rule that define the order of moves, recycling per queue, the
+ * random-number stream, the truncated periodic k set) are stated where they are used.
+ *
+ * Arithmetic contract: every quantity that changes a position is formed from IEEE
+ * +, -, *, /, sqrt and explicit fma in a fixed order (see the comments at each step);
+ * cube roots and cos/sin are evaluated by our own Newton iteration and Taylor polynomials
+ * for that reason. Compile with -ffp-contract=off.
+ */
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cstdio>
+#include <vector>
+#include <algorithm>
+
+namespace orc {
+
+static const double PI = 3.141592653589793;
+static const double TWO_PI = 6.283185307179586;
+static const double LN2 = 0.6931471805599453;
+static const double WCA_CUT = 1.122462048309373;   // 2^(1/6): WCA cutoff in units of sigma (Eq. 2)
+
+/* ------------------------------------------------------------------------------------
+ * Fourier transform of the scalar wavelet (Sec. V.A, Eq. 25) and its moments (Eq. 22).
+ * ------------------------------------------------------------------------------------ */
+
+// phi~(k) = 4 pi k^-6 (5 k sin k - (k^2 - 8) cos k - 8).  For small k the bracket cancels
+// catastrophically, so there we use the power series of the same transform, obtained by
+// expanding sin(kr)/(kr) inside  phi~(k) = 4 pi Int_0^1 phi(r) sin(kr)/(kr) r^2 dr  with
+// phi(r) = r^2/2 - r^3/3 - 1/6 (Eq. 24):
+//   phi~(k) = 4 pi Sum_j (-1)^j k^{2j}/(2j+1)! [1/(2(2j+5)) - 1/(3(2j+6)) - 1/(6(2j+3))].
+double phitilde(double k) {
+    k = std::fabs(k);
+    if (k < 2.0) {
+        double sum = 0.0, kp = 1.0, fact = 1.0;   // kp = k^{2j}, fact = (2j+1)!
+        for (int j = 0; j < 30; j++) {
+            if (j > 0) { kp *= k * k; fact *= (double)(2 * j) * (double)(2 * j + 1); }
+            double c = 1.0 / (2.0 * (2 * j + 5)) - 1.0 / (3.0 * (2 * j + 6)) - 1.0 / (6.0 * (2 * j + 3));
+            double term = kp / fact * c;
+            sum += (j % 2 == 0) ? term : -term;
+        }
+        return 4.0 * PI * sum;
+    }
+    double k2 = k * k, k6 = k2 * k2 * k2;
+    return 4.0 * PI * (5.0 * k * std::sin(k) - (k2 - 8.0) * std::cos(k) - 8.0) / k6;
+}
+
+// Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0); w.assign(n, 0.0);
+    for (int i = 0; i < n; i++) {
+        double z = std::cos(PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; j++) { double p3 = p2; p2 = p1; p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j; }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z; w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+// Cut-off of the numerical k integrals: an even multiple of pi/2, so that the leading
+// oscillatory part of the tail (~ sin 2K) vanishes; the smooth part of the tail is added
+// in closed form from the large-k expansion of phi~^2 (Eq. 25 squared):
+//   k^m phi~^2 = 16 pi^2 k^{m-12} [k^4/2 + 9/2 k^2 + 96 + (oscillating terms)].
+static const int TAIL_PANELS = 20000;              // panels of width pi/8 up to K = 2500 pi
+static double KMAX() { return TAIL_PANELS * (PI / 8.0); }
+
+static double smooth_tail(int m, double K) {
+    // Int_K^inf 16 pi^2 k^{m-12} (k^4/2 + 4.5 k^2 + 96) dk,  valid for m <= 6
+    double c = 16.0 * PI * PI, s = 0.0;
+    int p1 = m - 8, p2 = m - 10, p3 = m - 12;        // exponents
+    s += 0.5 * std::pow(K, p1 + 1) / (-(p1 + 1));
+    s += 4.5 * std::pow(K, p2 + 1) / (-(p2 + 1));
+    s += 96.0 * std::pow(K, p3 + 1) / (-(p3 + 1));
+    return c * s;
+}
+
+// M_m = Int_0^inf k^m phi~(k)^2 dk  (Eq. 22).
+double moment(int m) {
+    std::vector<double> gx, gw;
+    gauss_legendre(16, gx, gw);
+    double h = PI / 8.0, sum = 0.0;
+    for (int p = 0; p < TAIL_PANELS; p++) {
+        double a = p * h, c = a + 0.5 * h;
+        for (int i = 0; i < 16; i++) {
+            double k = c + 0.5 * h * gx[i], f = phitilde(k);
+            sum += 0.5 * h * gw[i] * std::pow(k, m) * f * f;
+        }
+    }
+    return sum + smooth_tail(m, KMAX());
+}
+
+// G(Q) = Int_Q^inf q^3 phi~(q)^2 dq, the weight of a plane-wave mode (Eqs. 49, 51).
+// Evaluated for many Q at once: integrate panel by panel from K downwards.
+void G_many(const std::vector<double>& Q, std::vector<double>& out) {
+    std::vector<double> gx, gw;
+    gauss_legendre(16, gx, gw);
+    double h = PI / 8.0;
+    auto seg = [&](double a, double b) {
+        double s = 0.0, c = 0.5 * (a + b), hh = 0.5 * (b - a);
+        for (int i = 0; i < 16; i++) { double k = c + hh * gx[i], f = phitilde(k); s += hh * gw[i] * k * k * k * f * f; }
+        return s;
+    };
+    // cumulative integral from K down to each panel edge
+    std::vector<double> from_edge(TAIL_PANELS + 1, 0.0);
+    from_edge[TAIL_PANELS] = smooth_tail(3, KMAX());
+    for (int p = TAIL_PANELS - 1; p >= 0; p--) from_edge[p] = from_edge[p + 1] + seg(p * h, (p + 1) * h);
+    out.resize(Q.size());
+    for (size_t i = 0; i < Q.size(); i++) {
+        double q = Q[i];
+        if (q >= KMAX()) { out[i] = smooth_tail(3, q); continue; }
+        int p = (int)std::floor(q / h);
+        double hi = (p + 1) * h;
+        out[i] = from_edge[p + 1] + (hi > q ? seg(q, hi) : 0.0);
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Random numbers. The paper only says "a pseudo random number generator" (App. D).
+ * Reading: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter-based, so that
+ * every draw is a pure function of (seed, simulation, sweep, layer, slot, attempt).
+ * ------------------------------------------------------------------------------------ */
+struct U4 { uint32_t v[4]; };
+
+U4 philox(U4 c, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    for (int r = 0; r < 10; r++) {
+        uint64_t p0 = (uint64_t)M0 * c.v[0], p1 = (uint64_t)M1 * c.v[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        U4 n;
+        n.v[0] = hi1 ^ c.v[1] ^ k0;
+        n.v[1] = lo1;
+        n.v[2] = hi0 ^ c.v[3] ^ k1;
+        n.v[3] = lo0;
+        c = n;
+        k0 += W0; k1 += W1;
+    }
+    return c;
+}
+
+// stream kinds (bits 24..31 of counter word 2)
+enum { K_COUNT = 1, K_SLOT = 2, K_VB = 3, K_VP = 4, K_ACC = 5, K_PWCOUNT = 6, K_PWMODE = 7, K_PWDIR = 8,
+       K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12, K_PROPOSE = 13 };
+
+struct Stream {
+    uint32_t k0, k1;
+    // counter = (index, sweep lo, kind<<24 | layer<<16 | attempt, sweep hi)
+    U4 draw(int kind, int layer, uint64_t sweep, uint32_t index, uint32_t attempt) const {
+        U4 c;
+        c.v[0] = index;
+        c.v[1] = (uint32_t)sweep;
+        c.v[2] = ((uint32_t)kind << 24) | ((uint32_t)(layer & 0xFF) << 16) | (attempt & 0xFFFFu);
+        c.v[3] = (uint32_t)(sweep >> 32);
+        return philox(c, k0, k1);
+    }
+};
+static Stream make_stream(uint64_t seed, uint64_t sim_id) {
+    Stream s;
+    s.k0 = (uint32_t)seed;
+    s.k1 = (uint32_t)(seed >> 32) ^ (uint32_t)sim_id;
+    return s;
+}
+// uniform in [0, 1) with 53 random bits
+static double u53(uint32_t hi, uint32_t lo) {
+    uint64_t m = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
+    return (double)m * (1.0 / 9007199254740992.0);
+}
+// uniform integer in [0, n): high 64 bits of (64-bit draw) * n
+static int64_t pick(uint32_t hi, uint32_t lo, int64_t n) {
+    uint64_t x = ((uint64_t)hi << 32) | lo;
+    return (int64_t)(((unsigned __int128)x * (unsigned __int128)(uint64_t)n) >> 64);
+}
+// component of a point of [-1, 1)^3
+static double sym(uint32_t w) { return (double)w * (1.0 / 2147483648.0) - 1.0; }
+
+/* ------------------------------------------------------------------------------------
+ * Own elementary functions (fixed operation order, explicit fma).
+ * ------------------------------------------------------------------------------------ */
+// lambda = w^(-1/3) by 8 Newton steps on f(y) = y^-3 - w from the lower edge `lo` of the
+// band that contains the root (the band spans at most a factor 2, Newton from below is
+// monotone): y <- y (4 - w y^3) / 3.
+static double inv_cbrt_from(double w, double lo) {
+    double y = lo;
+    for (int it = 0; it < 8; it++) {
+        double t = w * ((y * y) * y);
+        y = (y * (4.0 - t)) / 3.0;
+    }
+    return y;
+}
+// Taylor coefficients of cos and sin about 0, evaluated on [0, pi/4]
+static double cos_poly(double t) {
+    double z = t * t;
+    double c = 1.0 / 6402373705728000.0;                             // 1/18!
+    c = std::fma(c, -z, 1.0 / 20922789888000.0);                      // 1/16!
+    c = std::fma(c, -z, 1.0 / 87178291200.0);                         // 1/14!
+    c = std::fma(c, -z, 1.0 / 479001600.0);                           // 1/12!
+    c = std::fma(c, -z, 1.0 / 3628800.0);                             // 1/10!
+    c = std::fma(c, -z, 1.0 / 40320.0);                               // 1/8!
+    c = std::fma(c, -z, 1.0 / 720.0);
+    c = std::fma(c, -z, 1.0 / 24.0);
+    c = std::fma(c, -z, 0.5);
+    c = std::fma(c, -z, 1.0);
+    return c;
+}
+static double sin_poly(double t) {
+    double z = t * t;
+    double c = 1.0 / 121645100408832000.0;                           // 1/19!
+    c = std::fma(c, -z, 1.0 / 355687428096000.0);                     // 1/17!
+    c = std::fma(c, -z, 1.0 / 1307674368000.0);                       // 1/15!
+    c = std::fma(c, -z, 1.0 / 6227020800.0);                          // 1/13!
+    c = std::fma(c, -z, 1.0 / 39916800.0);                            // 1/11!
+    c = std::fma(c, -z, 1.0 / 362880.0);                              // 1/9!
+    c = std::fma(c, -z, 1.0 / 5040.0);
+    c = std::fma(c, -z, 1.0 / 120.0);
+    c = std::fma(c, -z, 1.0 / 6.0);
+    c = std::fma(c, -z, 1.0);
+    return c * t;
+}
+// cos(2 pi t) and sin(2 pi t) for t in turns: reduce to [0, 1/2] by symmetry, then to an
+// octant (all reductions are exact by Sterbenz), then one Taylor polynomial.
+static double cos2pi(double t) {
+    double x = t - std::floor(t);                 // [0, 1)
+    if (x > 0.5) x = 1.0 - x;                      // cos symmetric about 1/2
+    if (x <= 0.125) return cos_poly(TWO_PI * x);
+    if (x <= 0.375) return sin_poly(TWO_PI * (0.25 - x));
+    return -cos_poly(TWO_PI * (0.5 - x));
+}
+static double sin2pi(double t) {
+    double x = t - std::floor(t);                 // [0, 1)
+    double sgn = 1.0;
+    if (x >= 0.5) { x = x - 0.5; sgn = -1.0; }     // sin(2pi(x+1/2)) = -sin(2pi x)
+    if (x > 0.25) x = 0.5 - x;                     // symmetric about 1/4
+    double r = (x <= 0.125) ? sin_poly(TWO_PI * x) : cos_poly(TWO_PI * (0.25 - x));
+    return sgn * r;
+}
+// single-precision variants for the mixed-precision displacement (reduction in FP64)
+static float cos_poly_f(float t) {
+    float z = t * t;
+    float c = 1.0f / 3628800.0f;                   // 1/10!
+    c = std::fma(c, -z, 1.0f / 40320.0f);
+    c = std::fma(c, -z, 1.0f / 720.0f);
+    c = std::fma(c, -z, 1.0f / 24.0f);
+    c = std::fma(c, -z, 0.5f);
+    c = std::fma(c, -z, 1.0f);
+    return c;
+}
+static float sin_poly_f(float t) {
+    float z = t * t;
+    float c = 1.0f / 39916800.0f;                  // 1/11!
+    c = std::fma(c, -z, 1.0f / 362880.0f);
+    c = std::fma(c, -z, 1.0f / 5040.0f);
+    c = std::fma(c, -z, 1.0f / 120.0f);
+    c = std::fma(c, -z, 1.0f / 6.0f);
+    c = std::fma(c, -z, 1.0f);
+    return c * t;
+}
+static float cos2pi_f(double t) {
+    double x = t - std::floor(t);
+    if (x > 0.5) x = 1.0 - x;
+    if (x <= 0.125) return cos_poly_f((float)(TWO_PI * x));
+    if (x <= 0.375) return sin_poly_f((float)(TWO_PI * (0.25 - x)));
+    return -cos_poly_f((float)(TWO_PI * (0.5 - x)));
+}
+
+}  // namespace orc
+
+/* ====================================================================================
+ * Simulation state
+ * ==================================================================================== */
+extern "C" {
+// Parameters of one simulation (lengths in units of the bead radius a, energies in kT units
+// when kT = 1). Mirrors the product's parameter block field by field but is declared here
+// on its own.
+typedef struct OParams {
+    int64_t n_beads;
+    double box_L;
+    double lambda_min, lambda_max, A0, kT;
+    int32_t bond_type;            // 0 none, 1 harmonic (k/2)(r - r0)^2, 2 FENE (Eq. 1)
+    double bond_k, bond_r0, fene_R0;
+    double wca_sigma, wca_eps;    // WCA (Eq. 2); eps = 0 disables it
+    double ext_kappa;             // external well (kappa/2)|r - centre|^2, 0 disables it
+    int32_t planewave_mode;       // 0 off (wavelets only), 1 periodic plane waves
+    int32_t lcut;                 // plane-wave modes |l| <= lcut
+    int32_t precision;            // 0 FP64, 1 mixed (FP32 displacement, FP64 decision)
+    uint64_t seed, sim_id;
+    int32_t colour_K;             // colours per axis of the concurrent schedule (2..4)
+    int32_t grid_f;               // fine cells per axis
+    int32_t n_cap;                // largest support handled by a concurrent move
+    int32_t grid_layer[16];       // coarse cells per axis per layer, 0 = serial layer
+} OParams;
+
+typedef struct OStats {
+    int64_t attempts[16], accepts[16], deferred[16];
+    int64_t pw_attempts, pw_accepts;
+    int64_t bead_updates;
+    int64_t accepted_total;
+    double sim_time;
+    int64_t sweeps;
+    int64_t n_layers;
+    double dt_move, p_fourier;
+} OStats;
+}
+
+namespace orc {
+
+enum { ACCEPT = 1, REJECT = 2, DEFER = 3 };
+
+struct Layer {
+    double lo, hi;        // band [lo, hi) of lambda
+    double ilo3, ihi3;    // lo^-3, hi^-3
+    double mass;          // p_l: probability of the band under P_lambda (Eq. 32)
+    double expect;        // expected slots per sweep, N (1 - P_F) p_l
+    int G;                // coarse cells per axis, 0 = serial
+};
+
+struct Sim {
+    OParams P;
+    int64_t N;
+    double L, halfL, invf;
+    std::vector<double> pos;      // 3N, wrapped into [0, L)
+    std::vector<int32_t> img;     // 3N image counters
+    std::vector<uint8_t> bnext;   // bead i bonded to i+1
+    std::vector<Layer> layers;
+    Stream rng;
+    uint64_t sweep = 0;
+    uint64_t pw_calls = 0;
+    double rc2 = 0.0, rc = 0.0;   // WCA cutoff
+    double r_reach = 0.0;         // spatial reach of interactions used by the region rule
+    double dt_move = 0.0;         // simulated time per accepted move (units of tau)
+    double p_fourier = 0.0;
+    // carries of lambda after a rejection (Appendix D, parameter recycling)
+    std::vector<std::vector<double>> carry_q;   // per layer, per coarse cell (0 = none)
+    std::vector<double> carry_serial;           // per layer
+    int pw_carry = -1;                          // carried plane-wave mode (index), -1 none
+    int pw_carry_l[3] = {0, 0, 0};
+    // plane-wave tables
+    std::vector<int> modes;                     // 3 per mode
+    std::vector<double> mode_prob, mode_cdf;
+    double R = 1.0;
+    // statistics and per-slot trace of the last sweep
+    OStats st;
+    std::vector<std::vector<uint8_t>> tr_out;
+    std::vector<std::vector<int32_t>> tr_n;
+    std::vector<uint8_t> tr_pw_out;
+    std::vector<int32_t> tr_pw_mode;
+    // scratch
+    std::vector<uint8_t> inS;
+};
+
+static inline double wrap(double x, double L, int32_t* im) {
+    if (x >= L) { x = x - L; if (im) *im += 1; }
+    else if (x < 0.0) { x = x + L; if (im) *im -= 1; }
+    if (x >= L) x = 0.0;          // a tiny negative value rounded up to L
+    return x;
+}
+static inline double mi(double d, double L, double h) {
+    if (d > h) d = d - L;
+    else if (d < -h) d = d + L;
+    return d;
+}
+
+/* ---- energies (Eqs. 1, 2; harmonic bond of Sec. VII.B; external well for tests) ---- */
+static double U_wca(const Sim& s, double r2) {
+    if (s.P.wca_eps == 0.0 || !(r2 < s.rc2)) return 0.0;
+    double s2 = (s.P.wca_sigma * s.P.wca_sigma) / r2;
+    double s6 = (s2 * s2) * s2;
+    return 4.0 * s.P.wca_eps * (s6 * s6 - s6) + s.P.wca_eps;
+}
+static double U_bond(const Sim& s, double r2) {
+    if (s.P.bond_type == 1) {
+        double r = std::sqrt(r2), d = r - s.P.bond_r0;
+        return 0.5 * s.P.bond_k * d * d;
+    }
+    if (s.P.bond_type == 2) {
+        double R02 = s.P.fene_R0 * s.P.fene_R0, x = r2 / R02;
+        if (!(x < 1.0)) return INFINITY;
+        return -0.5 * s.P.bond_k * R02 * std::log(1.0 - x);
+    }
+    return 0.0;
+}
+static double U_ext(const Sim& s, const double* p) {
+    if (s.P.ext_kappa == 0.0) return 0.0;
+    double r2 = 0.0;
+    for (int a = 0; a < 3; a++) { double d = mi(p[a] - s.halfL, s.L, s.halfL); r2 += d * d; }
+    return 0.5 * s.P.ext_kappa * r2;
+}
+static inline double dist2(const Sim& s, const double* p, const double* q) {
+    double dx = mi(p[0] - q[0], s.L, s.halfL), dy = mi(p[1] - q[1], s.L, s.halfL), dz = mi(p[2] - q[2], s.L, s.halfL);
+    return (dx * dx + dy * dy) + dz * dz;
+}
+static inline bool bonded(const Sim& s, int64_t i, int64_t j) {
+    if (j == i + 1) return s.bnext[i];
+    if (i == j + 1) return s.bnext[j];
+    return false;
+}
+static double U_pair(const Sim& s, int64_t i, int64_t j, const double* p, const double* q) {
+    double r2 = dist2(s, p, q);
+    double u = U_wca(s, r2);
+    if (bonded(s, i, j)) u += U_bond(s, r2);
+    return u;
+}
+
+// Energy change when the beads in `S` move from `pos` to `newp` (3 per entry of S).
+// Brute force over all partners: every pair with at least one moved bead, counted once.
+static double delta_U(Sim& s, const std::vector<int64_t>& S, const std::vector<double>& newp) {
+    for (size_t k = 0; k < S.size(); k++) s.inS[S[k]] = 1;
+    // map from bead to its index in S (only for moved beads)
+    std::vector<std::pair<int64_t, size_t>> idx(S.size());
+    for (size_t k = 0; k < S.size(); k++) idx[k] = {S[k], k};
+    std::sort(idx.begin(), idx.end());
+    auto where = [&](int64_t b) {
+        auto it = std::lower_bound(idx.begin(), idx.end(), std::make_pair(b, (size_t)0));
+        return it->second;
+    };
+    double dU = 0.0;
+    for (size_t k = 0; k < S.size(); k++) {
+        int64_t m = S[k];
+        const double* om = &s.pos[3 * m];
+        const double* nm = &newp[3 * k];
+        dU += U_ext(s, nm) - U_ext(s, om);
+        for (int64_t q = 0; q < s.N; q++) {
+            if (q == m) continue;
+            const double* oq = &s.pos[3 * q];
+            if (s.inS[q]) {
+                if (q < m) continue;                 // pair of two moved beads: counted once
+                const double* nq = &newp[3 * where(q)];
+                dU += U_pair(s, m, q, nm, nq) - U_pair(s, m, q, om, oq);
+            } else {
+                dU += U_pair(s, m, q, nm, oq) - U_pair(s, m, q, om, oq);
+            }
+        }
+    }
+    for (size_t k = 0; k < S.size(); k++) s.inS[S[k]] = 0;
+    return dU;
+}
+
+// Metropolis test (Eq. 20): accept with probability min(1, exp(-dU/kT)), i.e. accept iff
+// dU <= -kT ln(1 - u) with u uniform in [0, 1); an infinite or undefined dU rejects.
+static bool metropolis(const Sim& s, double dU, double u) {
+    double thr = -s.P.kT * std::log(1.0 - u);
+    return dU <= thr;
+}
+
+/* ---- proposal parameters (Appendix D) ---- */
+// Uniform point of the closed unit ball by rejection from [-1, 1)^3 (Appendix D, choosing b).
+// Attempts are counter-indexed; after 64 failed attempts (probability 0.48^64) the centre
+// is used.
+static void ball_point(const Sim& s, int kind, int layer, uint64_t sweep, uint32_t j, double V[3], bool nonzero) {
+    for (uint32_t a = 0; a < 64; a++) {
+        U4 w = s.rng.draw(kind, layer, sweep, j, a);
+        double x = sym(w.v[0]), y = sym(w.v[1]), z = sym(w.v[2]);
+        double q = (x * x + y * y) + z * z;
+        if (q <= 1.0 && (!nonzero || q > 0.0)) { V[0] = x; V[1] = y; V[2] = z; return; }
+    }
+    V[0] = 0.0; V[1] = 0.0; V[2] = nonzero ? 1.0 : 0.0;
+}
+// Isotropic polarisation p = V / |V| (Appendix D, choosing p).
+static void polarisation(const Sim& s, int layer, uint64_t sweep, uint32_t j, double p[3]) {
+    double V[3];
+    ball_point(s, K_VP, layer, sweep, j, V, true);
+    double q = (V[0] * V[0] + V[1] * V[1]) + V[2] * V[2];
+    double r = std::sqrt(q);
+    p[0] = V[0] / r; p[1] = V[1] / r; p[2] = V[2] / r;
+}
+
+// Displacement of a bead at minimum-image offset d from the centre (Sec. V.A):
+//   delta = A_w (1 - |x|) (p x x),  x = d / lambda,
+// evaluated as  s = (A_w (1 - sqrt(d2)/lambda)) / lambda,  delta = s (p x d).
+static void wavelet_disp(const Sim& s, const double d[3], double d2, double lam, double Aw, const double p[3],
+                         double out[3]) {
+    if (s.P.precision == 0) {
+        double rho = std::sqrt(d2) / lam;
+        double sc = (Aw * (1.0 - rho)) / lam;
+        double cx = p[1] * d[2] - p[2] * d[1];
+        double cy = p[2] * d[0] - p[0] * d[2];
+        double cz = p[0] * d[1] - p[1] * d[0];
+        out[0] = sc * cx; out[1] = sc * cy; out[2] = sc * cz;
+    } else {
+        // mixed precision: the same expression in binary32 on FP64 inputs rounded once
+        float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
+        float d2f = (dx * dx + dy * dy) + dz * dz;
+        float lf = (float)lam, af = (float)Aw, px = (float)p[0], py = (float)p[1], pz = (float)p[2];
+        float rho = std::sqrt(d2f) / lf;
+        float sc = (af * (1.0f - rho)) / lf;
+        float cx = py * dz - pz * dy;
+        float cy = pz * dx - px * dz;
+        float cz = px * dy - py * dx;
+        out[0] = (double)(sc * cx); out[1] = (double)(sc * cy); out[2] = (double)(sc * cz);
+    }
+}
+
+/* ---- the concurrency region of a coarse cell (our schedule; the paper runs moves one
+ *      after another and names parallel non-overlapping moves as future work, Sec. VIII) ----
+ * A coloured layer splits the box into G^3 coarse cells, coloured by (cx mod K, cy mod K,
+ * cz mod K). The region of a cell is the cell widened by (K-1)/2 cells on every side; the
+ * regions of one colour tile the box. A move of the queue of cell C may run concurrently
+ * with the other queues of its colour only if everything it reads or writes lies in fine
+ * cells wholly inside C's region; otherwise it is deferred to the serial phase. */
+static inline int64_t floordiv(int64_t a, int64_t b) { int64_t q = a / b; if ((a % b != 0) && ((a < 0) != (b < 0))) q--; return q; }
+static inline int64_t ceildiv(int64_t a, int64_t b) { return -floordiv(-a, b); }
+
+struct Region { int64_t lo[3], hi[3]; };   // inclusive fine-cell index ranges (may exceed [0, Gf))
+
+static Region region_of(const Sim& s, int G, const int c[3]) {
+    Region R;
+    int64_t K = s.P.colour_K, Gf = s.P.grid_f;
+    for (int a = 0; a < 3; a++) {
+        R.lo[a] = ceildiv((2 * (int64_t)c[a] - (K - 1)) * Gf, 2 * (int64_t)G);
+        R.hi[a] = floordiv((2 * (int64_t)c[a] + 2 + (K - 1)) * Gf, 2 * (int64_t)G) - 1;
+    }
+    return R;
+}
+static inline bool range_inside(int64_t t0, int64_t t1, int64_t lo, int64_t hi, int64_t Gf) {
+    for (int64_t sh = -Gf; sh <= Gf; sh += Gf)
+        if (t0 + sh >= lo && t1 + sh <= hi) return true;
+    return false;
+}
+static inline int64_t fine_cell(const Sim& s, double x) {
+    int64_t c = (int64_t)std::floor(x * s.invf);
+    if (c < 0) c = 0;
+    if (c >= s.P.grid_f) c = s.P.grid_f - 1;
+    return c;
+}
+// The influence ball of a move centred at b with scale lam: everything read or written is
+// within R = lam + A0 lam / 4 + r_reach of b (|delta| <= A_w / 4 <= A0 lam / 4).
+static bool ball_inside(const Sim& s, const Region& Rg, const double b[3], double lam) {
+    double R = (lam + (0.25 * s.P.A0) * lam) + s.r_reach;
+    for (int a = 0; a < 3; a++) {
+        int64_t t0 = (int64_t)std::floor((b[a] - R) * s.invf);
+        int64_t t1 = (int64_t)std::floor((b[a] + R) * s.invf);
+        if (!range_inside(t0, t1, Rg.lo[a], Rg.hi[a], s.P.grid_f)) return false;
+    }
+    return true;
+}
+static bool point_inside(const Sim& s, const Region& Rg, const double* p) {
+    for (int a = 0; a < 3; a++) {
+        int64_t c = fine_cell(s, p[a]);
+        if (!range_inside(c, c, Rg.lo[a], Rg.hi[a], s.P.grid_f)) return false;
+    }
+    return true;
+}
+
+// One wavelet move (Sec. V and Appendix D): slot j of layer l in the current sweep, with
+// scale lam (own draw or the carried scale of a rejected move). `Rg` is the concurrency
+// region when the move runs in a coloured phase, null in the serial phase.
+// Returns ACCEPT, REJECT or DEFER; n receives the number of beads in the support.
+static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, const Region* Rg, int* n_out) {
+    const uint64_t sw = s.sweep;
+    // centre: b = r_i + lam V, V uniform in the unit ball (wrapped into the box)
+    double V[3], b[3];
+    ball_point(s, K_VB, l, sw, j, V, false);
+    for (int a = 0; a < 3; a++) b[a] = wrap(s.pos[3 * i + a] + lam * V[a], s.L, nullptr);
+    if (Rg && !ball_inside(s, *Rg, b, lam)) return DEFER;
+    // support: beads strictly inside the ball, one image each (lam <= L/2)
+    std::vector<int64_t> S;
+    std::vector<double> D;   // offsets d = mi(r - b), 4 per member (d, d2)
+    double lam2 = lam * lam;
+    for (int64_t m = 0; m < s.N; m++) {
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = mi(s.pos[3 * m + a] - b[a], s.L, s.halfL);
+        double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        if (d2 < lam2) { S.push_back(m); D.insert(D.end(), {d[0], d[1], d[2], d2}); }
+    }
+    int n = (int)S.size();
+    *n_out = n;
+    if (Rg && n > s.P.n_cap) return DEFER;
+    double p[3];
+    polarisation(s, l, sw, j, p);
+    // amplitude A_w = A0 lam / sqrt(n)  (Eq. 29) and the new positions
+    std::vector<double> newp(3 * (size_t)n);
+    std::vector<int32_t> newimg(3 * (size_t)n);
+    if (n > 0) {
+        double Aw = (s.P.A0 * lam) / std::sqrt((double)n);
+        for (int k = 0; k < n; k++) {
+            double dl[3];
+            wavelet_disp(s, &D[4 * k], D[4 * k + 3], lam, Aw, p, dl);
+            for (int a = 0; a < 3; a++) {
+                int32_t im = s.img[3 * S[k] + a];
+                newp[3 * k + a] = wrap(s.pos[3 * S[k] + a] + dl[a], s.L, &im);
+                newimg[3 * k + a] = im;
+            }
+        }
+    }
+    // bonded partners outside the support must lie in the region too
+    if (Rg) {
+        for (int k = 0; k < n; k++) {
+            int64_t m = S[k];
+            for (int e = 0; e < 2; e++) {
+                int64_t q = (e == 0) ? m - 1 : m + 1;
+                if (q < 0 || q >= s.N || !bonded(s, m, q)) continue;
+                bool in = std::find(S.begin(), S.end(), q) != S.end();
+                if (!in && !point_inside(s, *Rg, &s.pos[3 * q])) return DEFER;
+            }
+        }
+    }
+    double dU = n > 0 ? delta_U(s, S, newp) : 0.0;
+    U4 w = s.rng.draw(K_ACC, l, sw, j, 0);
+    bool acc = metropolis(s, dU, u53(w.v[0], w.v[1]));
+    if (acc) {
+        for (int k = 0; k < n; k++)
+            for (int a = 0; a < 3; a++) { s.pos[3 * S[k] + a] = newp[3 * k + a]; s.img[3 * S[k] + a] = newimg[3 * k + a]; }
+    }
+    return acc ? ACCEPT : REJECT;
+}
+
+}  // namespace orc
+
+namespace orc {
+
+/* ---- slot parameters: scale within the layer's band and the picked bead ----
+ * Eq. 32 restricted to the band [lo, hi):  lambda = (lo^-3 - u (lo^-3 - hi^-3))^(-1/3),
+ * the inverse transform of Appendix D applied to one octave; the bead is uniform. */
+static void slot_draw(const Sim& s, int l, uint64_t sweep, uint32_t j, double* lam, int64_t* bead) {
+    const Layer& L = s.layers[l];
+    U4 w = s.rng.draw(K_SLOT, l, sweep, j, 0);
+    double u = u53(w.v[0], w.v[1]);
+    double wv = L.ilo3 - u * (L.ilo3 - L.ihi3);
+    *lam = inv_cbrt_from(wv, L.lo);
+    *bead = pick(w.v[2], w.v[3], s.N);
+}
+// Number of slots: floor(x) plus one more with probability frac(x) (stratified count).
+static int64_t slot_count(const Sim& s, int kind, int l, uint64_t ctr, double x) {
+    U4 w = s.rng.draw(kind, l, ctr, 0, 0);
+    double u = u53(w.v[0], w.v[1]);
+    double f = std::floor(x);
+    return (int64_t)f + ((u < x - f) ? 1 : 0);
+}
+
+/* ---- one layer: coloured phases then the serial phase ---- */
+static void run_layer(Sim& s, int l) {
+    const Layer& Ly = s.layers[l];
+    const uint64_t sw = s.sweep;
+    int64_t M = slot_count(s, K_COUNT, l, sw, Ly.expect);
+    std::vector<double> lam(M);
+    std::vector<int64_t> bead(M);
+    for (int64_t j = 0; j < M; j++) slot_draw(s, l, sw, (uint32_t)j, &lam[j], &bead[j]);
+    s.tr_out[l].assign(M, 0);
+    s.tr_n[l].assign(M, 0);
+    std::vector<int64_t> serial;
+    auto record = [&](int64_t j, int r, int n, bool deferred) {
+        s.tr_out[l][j] = (uint8_t)((r == ACCEPT ? 1 : 2) | (deferred ? 4 : 0));
+        s.tr_n[l][j] = n;
+        s.st.attempts[l]++;
+        s.st.bead_updates += n;
+        if (r == ACCEPT) { s.st.accepts[l]++; s.st.accepted_total++; }
+    };
+    const int G = Ly.G;
+    if (G > 0) {
+        // bucket the slots by the coarse cell of their bead at the start of the layer;
+        // order: colour, then cell (ascending linear index within the colour), then slot
+        const int K = s.P.colour_K, Q = G / K;
+        const int64_t nq3 = (int64_t)Q * Q * Q;
+        const double invG = (double)G / s.L;
+        std::vector<std::pair<int64_t, int64_t>> keyed(M);
+        for (int64_t j = 0; j < M; j++) {
+            int c[3];
+            for (int a = 0; a < 3; a++) {
+                int64_t v = (int64_t)std::floor(s.pos[3 * bead[j] + a] * invG);
+                if (v < 0) v = 0;
+                if (v >= G) v = G - 1;
+                c[a] = (int)v;
+            }
+            int64_t colour = (c[0] % K) + K * ((c[1] % K) + K * (c[2] % K));
+            int64_t q = (c[0] / K) + (int64_t)Q * ((c[1] / K) + (int64_t)Q * (c[2] / K));
+            keyed[j] = {colour * nq3 + q, j};
+        }
+        std::sort(keyed.begin(), keyed.end());
+        int64_t a = 0;
+        while (a < M) {
+            int64_t key = keyed[a].first, e = a;
+            while (e < M && keyed[e].first == key) e++;
+            int64_t colour = key / nq3, q = key % nq3;
+            int c[3] = {(int)(K * (q % Q) + colour % K), (int)(K * ((q / Q) % Q) + (colour / K) % K),
+                        (int)(K * (q / ((int64_t)Q * Q)) + colour / (K * K))};
+            Region Rg = region_of(s, G, c);
+            int64_t cell = c[0] + (int64_t)G * (c[1] + (int64_t)G * c[2]);
+            double carry = s.carry_q[l][cell];
+            for (int64_t t = a; t < e; t++) {
+                int64_t j = keyed[t].second;
+                double lam_eff = carry > 0.0 ? carry : lam[j];
+                int n = 0;
+                int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, &Rg, &n);
+                if (r == DEFER) { serial.push_back(j); s.st.deferred[l]++; continue; }
+                record(j, r, n, false);
+                carry = (r == ACCEPT) ? 0.0 : lam_eff;
+            }
+            s.carry_q[l][cell] = carry;
+            a = e;
+        }
+    } else {
+        for (int64_t j = 0; j < M; j++) serial.push_back(j);
+    }
+    // serial phase: deferred slots in schedule order (or all slots of a serial layer)
+    double carry = s.carry_serial[l];
+    for (int64_t j : serial) {
+        double lam_eff = carry > 0.0 ? carry : lam[j];
+        int n = 0;
+        int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, nullptr, &n);
+        record(j, r, n, G > 0);
+        carry = (r == ACCEPT) ? 0.0 : lam_eff;
+    }
+    s.carry_serial[l] = carry;
+}
+
+/* ---- plane-wave moves (Sec. VI; Appendix D, periodic system) ---- */
+static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// Returns ACCEPT or REJECT; mode receives the packed wave vector index.
+static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr, uint32_t m, int32_t* mode_out) {
+    U4 w1 = s.rng.draw(kmode, 0, ctr, m, 0);
+    U4 w2 = s.rng.draw(kdir, 0, ctr, m, 0);
+    double u_mode = u53(w1.v[0], w1.v[1]), phi = u53(w1.v[2], w1.v[3]);   // phase in turns
+    double psi = u53(w2.v[0], w2.v[1]);                                     // polarisation angle in turns
+    int perm = (int)(((uint64_t)w2.v[2] * 6u) >> 32);
+    uint32_t signs = w2.v[3] & 7u;
+    int lv[3];
+    if (s.pw_carry >= 0) {
+        // recycle |k| after a rejection: permute the components, flip each sign with prob 1/2
+        for (int a = 0; a < 3; a++) {
+            int v = s.pw_carry_l[PERM[perm][a]];
+            lv[a] = ((signs >> a) & 1u) ? -v : v;
+        }
+    } else {
+        size_t nm = s.mode_prob.size(), idx = nm - 1;
+        for (size_t i = 0; i < nm; i++) if (u_mode < s.mode_cdf[i]) { idx = i; break; }
+        for (int a = 0; a < 3; a++) lv[a] = s.modes[3 * idx + a];
+    }
+    *mode_out = (lv[0] + 128) | ((lv[1] + 128) << 8) | ((lv[2] + 128) << 16);
+    s.st.pw_attempts++;
+    if (lv[0] == 0 && lv[1] == 0 && lv[2] == 0) {
+        // the k = 0 mode moves nothing and is accepted (Sec. VI.A)
+        s.pw_carry = -1;
+        s.st.pw_accepts++;
+        s.st.accepted_total++;
+        return ACCEPT;
+    }
+    s.st.bead_updates += s.N;
+    // amplitude A_F = (2/k) sqrt(dU_est/(mu N)) with dU_est/mu = M6 A0^2/(2pi)^3 = A0^2/5 (Eq. 48)
+    int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
+    double lm = std::sqrt((double)l2);
+    double kmag = (TWO_PI * lm) / s.L;
+    double AF = (2.0 * s.P.A0) / (kmag * std::sqrt(5.0 * (double)s.N));
+    // polarisation e, uniform in the plane perpendicular to k (Appendix D)
+    double kh[3] = {lv[0] / lm, lv[1] / lm, lv[2] / lm}, u1[3], u2[3];
+    if (lv[0] == 0 && lv[1] == 0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
+    else {
+        double nr = std::sqrt((double)(lv[0] * lv[0] + lv[1] * lv[1]));
+        u1[0] = lv[1] / nr; u1[1] = -lv[0] / nr; u1[2] = 0.0;
+    }
+    u2[0] = kh[1] * u1[2] - kh[2] * u1[1];
+    u2[1] = kh[2] * u1[0] - kh[0] * u1[2];
+    u2[2] = kh[0] * u1[1] - kh[1] * u1[0];
+    double cp = cos2pi(psi), sp = sin2pi(psi), e[3];
+    for (int a = 0; a < 3; a++) e[a] = cp * u1[a] + sp * u2[a];
+    // displacement A_F cos(k.r + Phi) e of every bead (Eq. 47)
+    std::vector<double> newp(3 * (size_t)s.N);
+    std::vector<int32_t> newimg(3 * (size_t)s.N);
+    for (int64_t i = 0; i < s.N; i++) {
+        const double* r = &s.pos[3 * i];
+        double t = ((lv[0] * r[0] + lv[1] * r[1]) + lv[2] * r[2]) / s.L + phi;
+        double dl[3];
+        if (s.P.precision == 0) {
+            double amp = AF * cos2pi(t);
+            for (int a = 0; a < 3; a++) dl[a] = amp * e[a];
+        } else {
+            float amp = (float)AF * cos2pi_f(t);
+            for (int a = 0; a < 3; a++) dl[a] = (double)(amp * (float)e[a]);
+        }
+        for (int a = 0; a < 3; a++) {
+            int32_t im = s.img[3 * i + a];
+            newp[3 * i + a] = wrap(r[a] + dl[a], s.L, &im);
+            newimg[3 * i + a] = im;
+        }
+    }
+    // energy change over all pairs and the external term
+    double dU = 0.0;
+    for (int64_t i = 0; i < s.N; i++) {
+        dU += U_ext(s, &newp[3 * i]) - U_ext(s, &s.pos[3 * i]);
+        for (int64_t j = i + 1; j < s.N; j++)
+            dU += U_pair(s, i, j, &newp[3 * i], &newp[3 * j]) - U_pair(s, i, j, &s.pos[3 * i], &s.pos[3 * j]);
+    }
+    U4 w3 = s.rng.draw(kacc, 0, ctr, m, 0);
+    bool acc = metropolis(s, dU, u53(w3.v[0], w3.v[1]));
+    if (acc) {
+        s.pos.swap(newp);
+        s.img.swap(newimg);
+        s.pw_carry = -1;
+        s.st.pw_accepts++;
+        s.st.accepted_total++;
+    } else {
+        s.pw_carry = 1;
+        for (int a = 0; a < 3; a++) s.pw_carry_l[a] = lv[a];
+    }
+    return acc ? ACCEPT : REJECT;
+}
+
+static void sweep_once(Sim& s) {
+    for (int l = 0; l < (int)s.layers.size(); l++) run_layer(s, l);
+    s.tr_pw_out.clear();
+    s.tr_pw_mode.clear();
+    if (s.P.planewave_mode == 1) {
+        int64_t MF = slot_count(s, K_PWCOUNT, 0, s.sweep, (double)s.N * s.p_fourier);
+        for (int64_t m = 0; m < MF; m++) {
+            int32_t mode = 0;
+            int r = planewave_attempt(s, K_PWMODE, K_PWDIR, K_PWACC, s.sweep, (uint32_t)m, &mode);
+            s.tr_pw_out.push_back((uint8_t)(r == ACCEPT ? 1 : 2));
+            s.tr_pw_mode.push_back(mode);
+        }
+    }
+    s.sweep++;
+    s.st.sweeps++;
+    s.st.sim_time = (double)s.st.accepted_total * s.dt_move;
+}
+
+}  // namespace orc
+
+namespace orc {
+
+static const double LAMBDA_A = 1.0 / (1.125 - LN2);   // Eq. 42 for the tapered wavelet
+
+static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* chain_len, int64_t n_chains) {
+    s.P = *p;
+    const OParams& P = s.P;
+    if (P.n_beads < 1 || !(P.box_L > 0) || !(P.lambda_min > 0) || !(P.lambda_max > P.lambda_min) ||
+        P.lambda_max > 0.5 * P.box_L || !(P.A0 > 0) || !(P.kT > 0) || P.colour_K < 2 || P.colour_K > 4 ||
+        P.grid_f < 1 || P.n_cap < 1 || P.bond_type < 0 || P.bond_type > 2)
+        return -1;
+    s.N = P.n_beads;
+    s.L = P.box_L;
+    s.halfL = 0.5 * P.box_L;
+    s.invf = (double)P.grid_f / P.box_L;
+    s.pos.assign(pos, pos + 3 * s.N);
+    for (int64_t i = 0; i < 3 * s.N; i++)
+        if (!(pos[i] >= 0.0 && pos[i] < s.L)) return -1;
+    s.img.assign(3 * s.N, 0);
+    s.bnext.assign(s.N, 0);
+    int64_t b = 0;
+    for (int64_t c = 0; c < n_chains; c++) {
+        for (int32_t k = 0; k + 1 < chain_len[c]; k++) s.bnext[b + k] = 1;
+        b += chain_len[c];
+    }
+    if (b != s.N) return -1;
+    s.inS.assign(s.N, 0);
+    s.rng = make_stream(P.seed, P.sim_id);
+    s.rc = WCA_CUT * P.wca_sigma;
+    s.rc2 = s.rc * s.rc;
+    s.r_reach = (P.wca_eps != 0.0 ? s.rc : 0.0) + 1e-6;
+    // plane-wave tables and the probability of a plane-wave move (Eqs. 51, 55, 56)
+    s.p_fourier = 0.0;
+    if (P.planewave_mode == 1) {
+        if (P.lcut < 0 || P.lcut > 120) return -1;
+        std::vector<double> Q;
+        for (int lx = -P.lcut; lx <= P.lcut; lx++)
+            for (int ly = -P.lcut; ly <= P.lcut; ly++)
+                for (int lz = -P.lcut; lz <= P.lcut; lz++)
+                    if (lx * lx + ly * ly + lz * lz <= P.lcut * P.lcut) {
+                        s.modes.insert(s.modes.end(), {lx, ly, lz});
+                        Q.push_back(TWO_PI * std::sqrt((double)(lx * lx + ly * ly + lz * lz)) / s.L * P.lambda_max);
+                    }
+        std::vector<double> Gv;
+        G_many(Q, Gv);
+        double tot = 0.0;
+        for (double g : Gv) tot += g;
+        s.mode_prob.resize(Gv.size());
+        s.mode_cdf.resize(Gv.size());
+        double acc = 0.0;
+        for (size_t i = 0; i < Gv.size(); i++) { s.mode_prob[i] = Gv[i] / tot; acc += Gv[i]; s.mode_cdf[i] = acc / tot; }
+        const double M6 = 8.0 * PI * PI * PI / 5.0;
+        double ratio = s.L / P.lambda_max;
+        s.R = (1.0 / (6.0 * PI * PI)) * (ratio * ratio * ratio) * M6 / tot;
+        double rl = P.lambda_max / P.lambda_min;
+        s.p_fourier = 1.0 / (1.0 + s.R * (rl * rl * rl - 1.0));
+    }
+    // octave layers of P_lambda (Eq. 32): [lmin 2^l, lmin 2^(l+1)), the last one ending at lmax
+    int nL = 1;
+    while (P.lambda_min * std::ldexp(1.0, nL) < P.lambda_max) nL++;
+    if (nL > 16) return -1;
+    double imin3 = 1.0 / ((P.lambda_min * P.lambda_min) * P.lambda_min);
+    double imax3 = 1.0 / ((P.lambda_max * P.lambda_max) * P.lambda_max);
+    s.layers.resize(nL);
+    for (int l = 0; l < nL; l++) {
+        Layer& Ly = s.layers[l];
+        Ly.lo = P.lambda_min * std::ldexp(1.0, l);
+        Ly.hi = (l + 1 == nL) ? P.lambda_max : P.lambda_min * std::ldexp(1.0, l + 1);
+        Ly.ilo3 = 1.0 / ((Ly.lo * Ly.lo) * Ly.lo);
+        Ly.ihi3 = 1.0 / ((Ly.hi * Ly.hi) * Ly.hi);
+        Ly.mass = (Ly.ilo3 - Ly.ihi3) / (imin3 - imax3);
+        Ly.expect = ((double)s.N * (1.0 - s.p_fourier)) * Ly.mass;
+        Ly.G = P.grid_layer[l];
+        if (Ly.G < 0 || (Ly.G > 0 && (Ly.G % P.colour_K != 0 || Ly.G < P.colour_K))) return -1;
+    }
+    s.carry_q.resize(nL);
+    for (int l = 0; l < nL; l++) s.carry_q[l].assign(s.layers[l].G > 0 ? (size_t)s.layers[l].G * s.layers[l].G * s.layers[l].G : 0, 0.0);
+    s.carry_serial.assign(nL, 0.0);
+    s.tr_out.resize(nL);
+    s.tr_n.resize(nL);
+    // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2pi)^3 = 1/105)
+    double A02 = P.A0 * P.A0, la2 = LAMBDA_A * LAMBDA_A;
+    if (P.planewave_mode == 1) s.dt_move = (6.0 * A02 * la2) / (105.0 * (double)s.N);
+    else {
+        double Nl = 3.0 / (imin3 - imax3);
+        s.dt_move = ((2.0 * A02 * la2) / (105.0 * (double)s.N)) * (Nl * imin3) * (1.0 - P.lambda_min / P.lambda_max);
+    }
+    std::memset(&s.st, 0, sizeof s.st);
+    s.st.n_layers = nL;
+    s.st.dt_move = s.dt_move;
+    s.st.p_fourier = s.p_fourier;
+    return 0;
+}
+
+static double total_energy(const Sim& s) {
+    double E = 0.0;
+    for (int64_t i = 0; i < s.N; i++) {
+        E += U_ext(s, &s.pos[3 * i]);
+        for (int64_t j = i + 1; j < s.N; j++) E += U_pair(s, i, j, &s.pos[3 * i], &s.pos[3 * j]);
+    }
+    return E;
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+void* oracle_create(const OParams* p, const double* pos, const int32_t* chain_len, int64_t n_chains, int* err) {
+    Sim* s = new Sim();
+    int rc = setup(*s, p, pos, chain_len, n_chains);
+    if (err) *err = rc;
+    if (rc != 0) { delete s; return nullptr; }
+    return s;
+}
+void oracle_destroy(void* h) { delete (Sim*)h; }
+
+int oracle_sweep(void* h, int64_t n) {
+    Sim& s = *(Sim*)h;
+    for (int64_t k = 0; k < n; k++) sweep_once(s);
+    return 0;
+}
+// n plane-wave moves outside the sweep schedule (their own counter stream)
+int oracle_planewave(void* h, int64_t n) {
+    Sim& s = *(Sim*)h;
+    if (s.P.planewave_mode != 1) return -1;
+    s.tr_pw_out.clear();
+    s.tr_pw_mode.clear();
+    for (int64_t m = 0; m < n; m++) {
+        int32_t mode = 0;
+        int r = planewave_attempt(s, K_DPWMODE, K_DPWDIR, K_DPWACC, s.pw_calls, (uint32_t)m, &mode);
+        s.tr_pw_out.push_back((uint8_t)(r == ACCEPT ? 1 : 2));
+        s.tr_pw_mode.push_back(mode);
+    }
+    s.pw_calls++;
+    s.st.sim_time = (double)s.st.accepted_total * s.dt_move;
+    return 0;
+}
+int oracle_positions(void* h, double* out, int unwrapped) {
+    Sim& s = *(Sim*)h;
+    for (int64_t i = 0; i < 3 * s.N; i++) out[i] = unwrapped ? s.pos[i] + (double)s.img[i] * s.L : s.pos[i];
+    return 0;
+}
+int oracle_stats(void* h, OStats* out) { *out = ((Sim*)h)->st; return 0; }
+
+int64_t oracle_trace_layer(void* h, int l, uint8_t* out, int32_t* n, int64_t cap) {
+    Sim& s = *(Sim*)h;
+    if (l < 0 || l >= (int)s.layers.size()) return -1;
+    int64_t M = (int64_t)s.tr_out[l].size();
+    for (int64_t j = 0; j < M && j < cap; j++) { out[j] = s.tr_out[l][j]; n[j] = s.tr_n[l][j]; }
+    return M;
+}
+int64_t oracle_trace_pw(void* h, uint8_t* out, int32_t* mode, int64_t cap) {
+    Sim& s = *(Sim*)h;
+    int64_t M = (int64_t)s.tr_pw_out.size();
+    for (int64_t j = 0; j < M && j < cap; j++) { out[j] = s.tr_pw_out[j]; mode[j] = s.tr_pw_mode[j]; }
+    return M;
+}
+
+/* ---- entry points used by the pins ---- */
+void oracle_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+    U4 c;
+    for (int a = 0; a < 4; a++) c.v[a] = ctr[a];
+    U4 r = philox(c, key[0], key[1]);
+    for (int a = 0; a < 4; a++) out[a] = r.v[a];
+}
+double oracle_phitilde(double k) { return phitilde(k); }
+double oracle_moment(int m) { return moment(m); }
+void oracle_G(const double* Q, int64_t n, double* out) {
+    std::vector<double> q(Q, Q + n), o;
+    G_many(q, o);
+    for (int64_t i = 0; i < n; i++) out[i] = o[i];
+}
+double oracle_cos2pi(double t) { return cos2pi(t); }
+double oracle_sin2pi(double t) { return sin2pi(t); }
+float oracle_cos2pi_f(double t) { return cos2pi_f(t); }
+double oracle_inv_cbrt(double w, double lo) { return inv_cbrt_from(w, lo); }
+double oracle_lambda_a(void) { return LAMBDA_A; }
+
+int oracle_layers(void* h, double* lo, double* hi, double* mass, double* expect, int cap) {
+    Sim& s = *(Sim*)h;
+    int nL = (int)s.layers.size();
+    for (int l = 0; l < nL && l < cap; l++) { lo[l] = s.layers[l].lo; hi[l] = s.layers[l].hi; mass[l] = s.layers[l].mass; expect[l] = s.layers[l].expect; }
+    return nL;
+}
+// scales and beads of slots 0..n-1 of layer l in the current sweep
+int64_t oracle_sample_slots(void* h, int l, int64_t n, double* lam, int64_t* bead) {
+    Sim& s = *(Sim*)h;
+    if (l < 0 || l >= (int)s.layers.size()) return -1;
+    for (int64_t j = 0; j < n; j++) slot_draw(s, l, s.sweep, (uint32_t)j, &lam[j], &bead[j]);
+    return n;
+}
+// n uniform points of the unit ball from the centre stream of layer 0, sweep `sw`
+int64_t oracle_sample_ball(void* h, uint64_t sw, int64_t n, double* out) {
+    Sim& s = *(Sim*)h;
+    for (int64_t j = 0; j < n; j++) ball_point(s, K_VB, 0, sw, (uint32_t)j, &out[3 * j], false);
+    return n;
+}
+int64_t oracle_sample_polarisation(void* h, uint64_t sw, int64_t n, double* out) {
+    Sim& s = *(Sim*)h;
+    for (int64_t j = 0; j < n; j++) polarisation(s, 0, sw, (uint32_t)j, &out[3 * j]);
+    return n;
+}
+// displacement of a bead at `pt` by a wavelet (b, lam, p, A_w): zero outside the support
+void oracle_wavelet_field(void* h, const double* b, double lam, const double* p, double Aw, const double* pt, double* out) {
+    Sim& s = *(Sim*)h;
+    double d[3];
+    for (int a = 0; a < 3; a++) d[a] = mi(pt[a] - b[a], s.L, s.halfL);
+    double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    if (!(d2 < lam * lam)) { out[0] = out[1] = out[2] = 0.0; return; }
+    wavelet_disp(s, d, d2, lam, Aw, p, out);
+}
+double oracle_delta_u(void* h, int64_t n, const int64_t* ids, const double* newpos) {
+    Sim& s = *(Sim*)h;
+    std::vector<int64_t> S(ids, ids + n);
+    std::vector<double> np(newpos, newpos + 3 * n);
+    return delta_U(s, S, np);
+}
+double oracle_total_energy(void* h) { return total_energy(*(Sim*)h); }
+
+int64_t oracle_pw_modes(void* h, int32_t* modes, double* prob, int64_t cap, double* R, double* PF) {
+    Sim& s = *(Sim*)h;
+    int64_t nm = (int64_t)s.mode_prob.size();
+    for (int64_t i = 0; i < nm && i < cap; i++) {
+        for (int a = 0; a < 3; a++) modes[3 * i + a] = s.modes[3 * i + a];
+        prob[i] = s.mode_prob[i];
+    }
+    *R = s.R;
+    *PF = s.p_fourier;
+    return nm;
+}
+
+// Moments of proposed wavelet displacements of beads 0 and 1 on the frozen configuration:
+// out[0..8] = <d0 (x) d1>, out[9..17] = <d0 (x) d0>, out[18..26] = <d1 (x) d1>, per proposal.
+// Proposals use the move generation of Appendix D with the layered P_lambda; nothing is
+// accepted or moved.
+int oracle_propose_moments(void* h, int64_t n_props, uint64_t offset, double* out) {
+    Sim& s = *(Sim*)h;
+    if (s.N < 2) return -1;
+    double acc[27] = {0};
+    int nL = (int)s.layers.size();
+    std::vector<double> cum(nL);
+    double c = 0.0;
+    for (int l = 0; l < nL; l++) { c += s.layers[l].mass; cum[l] = c; }
+    for (int64_t t = 0; t < n_props; t++) {
+        uint64_t sw = (1ull << 40) + offset + (uint64_t)t;
+        U4 w = s.rng.draw(K_PROPOSE, 0, sw, 0, 0);
+        double ul = u53(w.v[0], w.v[1]) * c;
+        int l = nL - 1;
+        for (int k = 0; k < nL; k++) if (ul < cum[k]) { l = k; break; }
+        double lam;
+        int64_t i;
+        slot_draw(s, l, sw, 0, &lam, &i);
+        double V[3], b[3], p[3];
+        ball_point(s, K_VB, l, sw, 0, V, false);
+        for (int a = 0; a < 3; a++) b[a] = wrap(s.pos[3 * i + a] + lam * V[a], s.L, nullptr);
+        polarisation(s, l, sw, 0, p);
+        int n = 0;
+        double dd[2][4];
+        bool in01[2] = {false, false};
+        for (int64_t m = 0; m < s.N; m++) {
+            double d[3];
+            for (int a = 0; a < 3; a++) d[a] = mi(s.pos[3 * m + a] - b[a], s.L, s.halfL);
+            double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            if (d2 < lam * lam) {
+                n++;
+                if (m < 2) { in01[m] = true; dd[m][0] = d[0]; dd[m][1] = d[1]; dd[m][2] = d[2]; dd[m][3] = d2; }
+            }
+        }
+        if (n == 0) continue;
+        double Aw = (s.P.A0 * lam) / std::sqrt((double)n), dl[2][3] = {{0, 0, 0}, {0, 0, 0}};
+        for (int m = 0; m < 2; m++) if (in01[m]) wavelet_disp(s, dd[m], dd[m][3], lam, Aw, p, dl[m]);
+        for (int a = 0; a < 3; a++)
+            for (int bb = 0; bb < 3; bb++) {
+                acc[3 * a + bb] += dl[0][a] * dl[1][bb];
+                acc[9 + 3 * a + bb] += dl[0][a] * dl[0][bb];
+                acc[18 + 3 * a + bb] += dl[1][a] * dl[1][bb];
+            }
+    }
+    for (int k = 0; k < 27; k++) out[k] = acc[k] / (double)n_props;
+    return 0;
+}
+
+// run n sweeps, recording the unwrapped position of bead 0 after each
+int oracle_sweep_record(void* h, int64_t n, double* out) {
+    Sim& s = *(Sim*)h;
+    for (int64_t k = 0; k < n; k++) {
+        sweep_once(s);
+        for (int a = 0; a < 3; a++) out[3 * k + a] = s.pos[a] + (double)s.img[a] * s.L;
+    }
+    return 0;
+}
+
+}  // extern "C"

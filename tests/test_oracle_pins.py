@@ -1,0 +1,463 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks one oracle function against something other than the oracle itself:
+printed values of the paper (tests/golden/paper_values.txt), published known-answer
+vectors (Philox), closed forms derived from the paper's definitions (moments, the
+free-bead diffusion of Eq. 33, the simulated mobility tensor of Eqs. 40-41, the
+periodic correction of Eq. 60), invariants (divergence-free wavelet field, Boltzmann
+stationarity of one bead in a well), textbook routines (libm cos/sin, scipy quadrature
+of the Fourier transform) and brute force written independently in numpy (energies).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special, stats
+
+import oracle as O
+from paper_1611_09160_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def params(**kw):
+    p = dict(n_beads=2, box_L=64.0, lambda_min=2.0, lambda_max=32.0, A0=0.5, kT=1.0, bond_type=0, bond_k=0.0,
+             bond_r0=2.0, fene_R0=3.0, wca_sigma=2.0, wca_eps=0.0, ext_kappa=0.0, planewave_mode=0, lcut=8,
+             precision=0, seed=11, sim_id=0, colour_K=2, grid_f=16, n_cap=64, grid_layer=[0] * 16)
+    p.update(kw)
+    return p
+
+
+def paper_value(name):
+    for line in open(os.path.join(GOLD, "paper_values.txt")):
+        if line.startswith(name + " "):
+            f = line.split()
+            return float(f[1]), float(f[2])
+    raise KeyError(name)
+
+
+# ---- test-side independent definitions -------------------------------------------------
+
+def phitilde_np(k):
+    """Eq. 25 (closed form); the test's own copy, valid for k >= 0.5."""
+    k = np.asarray(k, dtype=float)
+    return 4 * np.pi * (5 * k * np.sin(k) - (k ** 2 - 8) * np.cos(k) - 8) / k ** 6
+
+
+def phitilde_by_quadrature(k):
+    """Fourier transform of phi(r) = r^2/2 - r^3/3 - 1/6 on the unit ball (Eq. 24), by scipy."""
+    f = lambda r: (r * r / 2 - r ** 3 / 3 - 1 / 6) * (np.sinc(k * r / np.pi)) * r * r
+    return 4 * np.pi * integrate.quad(f, 0, 1, epsabs=1e-14, epsrel=1e-13)[0]
+
+
+# ---- random numbers --------------------------------------------------------------------
+
+def test_philox_known_answers():
+    n = 0
+    for line in open(os.path.join(GOLD, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        out = O.philox(v[0:4], v[4:6])
+        assert out.tolist() == v[6:10]
+        n += 1
+    assert n == 3
+
+
+# ---- wavelet constants (Eqs. 22, 25, 42) ------------------------------------------------
+
+def test_phitilde_series_and_closed_form():
+    # value at 0 from the definition: 4 pi Int_0^1 phi r^2 dr = 4 pi (1/10 - 1/18 - 1/18) = -2 pi / 45
+    assert O.phitilde(0.0) == pytest.approx(-2 * math.pi / 45, rel=1e-14)
+    for k in [0.01, 0.3, 0.7, 1.5, 1.99, 2.0, 3.7, 10.0, 55.5]:
+        assert O.phitilde(k) == pytest.approx(phitilde_by_quadrature(k), rel=1e-9, abs=1e-13)
+    for k in [0.6, 1.0, 1.9]:   # series branch against the closed form where it does not cancel badly
+        assert O.phitilde(k) == pytest.approx(float(phitilde_np(k)), rel=1e-9)
+
+
+def test_moments_closed_forms_and_lambda_a():
+    # derived: M4 = 8 pi^3/105, M6 = (2 pi)^3/5 (Parseval), M3 = (16 pi^2/105)(9/8 - ln 2)
+    assert O.moment(4) == pytest.approx(8 * math.pi ** 3 / 105, rel=1e-10)
+    assert O.moment(6) == pytest.approx((2 * math.pi) ** 3 / 5, rel=1e-9)
+    M3 = O.moment(3)
+    assert M3 == pytest.approx(16 * math.pi ** 2 / 105 * (9 / 8 - math.log(2)), rel=1e-10)
+    la = 2 / math.pi * O.moment(4) / M3            # Eq. 42
+    v, tol = paper_value("lambda_a")
+    assert la == pytest.approx(v, rel=tol)
+    assert O.lambda_a() == pytest.approx(la, rel=1e-10)
+    lm, _ = paper_value("lambda_min_bar")
+    a, tol = paper_value("a_bar")
+    assert lm / O.lambda_a() == pytest.approx(a, rel=tol)
+
+
+def test_G_tail_integral():
+    # G(0) = M3; G decreasing; large-Q asymptote 2 pi^2 Q^-4 (phi~^2 ~ 16 pi^2 k^-8 cos^2 k)
+    g = O.G([0.0, 1.0, 5.0, 40.0, 400.0])
+    assert g[0] == pytest.approx(16 * math.pi ** 2 / 105 * (9 / 8 - math.log(2)), rel=1e-10)
+    assert np.all(np.diff(g) < 0)
+    assert g[4] == pytest.approx(2 * math.pi ** 2 * 400.0 ** -4, rel=1e-2)   # oscillating part is O(1/Q)
+    # against scipy on a finite range plus the same asymptote
+    q = 3.0
+    f = lambda x: x ** 3 * phitilde_np(x) ** 2
+    edges = np.arange(q, 2000.0, math.pi / 2)
+    ref = sum(integrate.quad(f, a, b, epsabs=0, epsrel=1e-12)[0] for a, b in zip(edges[:-1], edges[1:]))
+    ref += 2 * math.pi ** 2 * edges[-1] ** -4
+    assert O.G([q])[0] == pytest.approx(ref, rel=1e-7)
+
+
+# ---- own elementary functions ----------------------------------------------------------
+
+def test_own_cos_sin_and_cube_root():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 120
+    t = np.concatenate([np.linspace(0, 1, 2001), np.random.default_rng(1).random(2000) * 7 - 3])
+    c = np.array([O.cos2pi(x) for x in t])
+    s = np.array([O.sin2pi(x) for x in t])
+    c_ref = np.array([float(mpmath.cos(2 * mpmath.pi * mpmath.mpf(float(x)))) for x in t])
+    s_ref = np.array([float(mpmath.sin(2 * mpmath.pi * mpmath.mpf(float(x)))) for x in t])
+    assert np.max(np.abs(c - c_ref)) < 2.3e-16
+    assert np.max(np.abs(s - s_ref)) < 2.3e-16
+    cf = np.array([O.cos2pi_f(x) for x in t[:2000]])
+    assert np.max(np.abs(cf - np.cos(2 * np.pi * t[:2000]))) < 3e-7
+    for lo, hi in [(2.0, 4.0), (64.0, 102.4), (2.0, 2.5)]:
+        for u in [0.0, 0.3, 0.999999]:
+            w = lo ** -3 - u * (lo ** -3 - hi ** -3)
+            assert O.inv_cbrt(w, lo) == pytest.approx(w ** (-1 / 3), rel=2e-15)
+
+
+# ---- the wavelet field (Eqs. 21, 23, 24; Appendix D) ------------------------------------
+
+def test_wavelet_field_properties():
+    o = O.Oracle(params(), np.array([[10.0, 10, 10], [20, 20, 20]]), np.array([1, 1], np.int32))
+    rng = np.random.default_rng(3)
+    b = np.array([30.0, 31.0, 29.5])
+    lam, Aw = 5.0, 0.7
+    for _ in range(20):
+        p = rng.normal(size=3)
+        p /= np.linalg.norm(p)
+        x = rng.normal(size=3)
+        x *= rng.random() * 0.9 / np.linalg.norm(x)
+        pt = b + lam * x
+        d = o.wavelet_field(b, lam, p, Aw, pt)
+        # transverse: delta . x = 0; magnitude A_w (1 - |x|) |p x x|
+        assert abs(d @ x) < 1e-13
+        assert np.linalg.norm(d) == pytest.approx(Aw * (1 - np.linalg.norm(x)) * np.linalg.norm(np.cross(p, x)), rel=1e-12)
+        # divergence-free (Eq. 17) by central differences
+        h = 1e-4
+        div = sum((o.wavelet_field(b, lam, p, Aw, pt + h * e)[a] - o.wavelet_field(b, lam, p, Aw, pt - h * e)[a]) / (2 * h)
+                  for a, e in enumerate(np.eye(3)))
+        assert abs(div) < 1e-8
+    # Eq. 23 for p = z:  w = r sin(theta) (1 - r) phi_hat
+    p = np.array([0.0, 0.0, 1.0])
+    x = np.array([0.3, -0.2, 0.4])
+    r = np.linalg.norm(x)
+    phi_hat = np.array([-x[1], x[0], 0.0]) / math.hypot(x[0], x[1])
+    sin_t = math.hypot(x[0], x[1]) / r
+    want = Aw * r * sin_t * (1 - r) * phi_hat
+    assert np.allclose(o.wavelet_field(b, lam, p, Aw, b + lam * x), want, rtol=1e-12, atol=1e-14)
+    # zero on and outside the support (Eq. 16)
+    assert np.all(o.wavelet_field(b, lam, p, Aw, b + np.array([lam, 0, 0])) == 0)
+    assert np.all(o.wavelet_field(b, lam, p, Aw, b + np.array([0, 1.01 * lam, 0])) == 0)
+
+
+# ---- energies: oracle dU against an independent numpy brute force ----------------------
+
+def energy_np(pos, chain_len, L, p):
+    """Total energy: WCA (Eq. 2) on all pairs, bonds on chain neighbours, external well."""
+    n = len(pos)
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= L * np.round(d / L)
+    r2 = np.sum(d * d, axis=-1)
+    iu = np.triu_indices(n, 1)
+    r2p = r2[iu]
+    E = 0.0
+    if p["wca_eps"]:
+        rc2 = (2 ** (1 / 6) * p["wca_sigma"]) ** 2
+        m = r2p < rc2
+        s6 = (p["wca_sigma"] ** 2 / r2p[m]) ** 3
+        E += np.sum(4 * p["wca_eps"] * (s6 * s6 - s6) + p["wca_eps"])
+    ends = np.cumsum(chain_len)
+    bonded = np.ones(n - 1, bool)
+    bonded[ends[:-1] - 1] = False
+    rb = np.sqrt(r2[np.arange(n - 1), np.arange(1, n)])[bonded]
+    if p["bond_type"] == 1:
+        E += np.sum(0.5 * p["bond_k"] * (rb - p["bond_r0"]) ** 2)
+    elif p["bond_type"] == 2:
+        x = (rb / p["fene_R0"]) ** 2
+        E += np.inf if np.any(x >= 1) else np.sum(-0.5 * p["bond_k"] * p["fene_R0"] ** 2 * np.log(1 - x))
+    if p["ext_kappa"]:
+        c = pos - L / 2
+        c -= L * np.round(c / L)
+        E += 0.5 * p["ext_kappa"] * np.sum(c * c)
+    return E
+
+
+@pytest.mark.parametrize("bond_type", [1, 2])
+def test_delta_u_matches_brute_force(bond_type):
+    sysm = I.make_system([12, 9, 1, 1], 0, 14.0, seed=5)   # small box: many pairs, chains across the boundary
+    p = params(n_beads=sysm.n_beads, box_L=14.0, lambda_max=7.0, bond_type=bond_type, bond_k=30.0, bond_r0=2.0,
+               fene_R0=3.2, wca_eps=1.0, ext_kappa=0.05)
+    o = O.Oracle(p, sysm.pos, sysm.chain_len)
+    E0 = energy_np(sysm.pos, sysm.chain_len, 14.0, p)
+    assert o.total_energy() == pytest.approx(E0, rel=1e-12)
+    rng = np.random.default_rng(8)
+    for trial in range(40):
+        k = rng.integers(1, 8)
+        ids = np.sort(rng.choice(sysm.n_beads, size=k, replace=False))
+        newp = sysm.pos[ids] + rng.normal(scale=0.15, size=(k, 3))
+        newp %= 14.0
+        after = sysm.pos.copy()
+        after[ids] = newp
+        want = energy_np(after, sysm.chain_len, 14.0, p) - E0
+        got = o.delta_u(ids, newp)
+        if np.isinf(want):
+            assert np.isinf(got) and got > 0
+        else:
+            assert got == pytest.approx(want, rel=1e-9, abs=1e-9)
+
+
+# ---- sampling distributions (Eqs. 26, 32; Appendix D) ----------------------------------
+
+def test_layers_partition_P_lambda():
+    o = O.Oracle(params(box_L=409.5, lambda_max=204.75), np.array([[1.0, 1, 1], [5, 5, 5]]), np.array([1, 1], np.int32))
+    lo, hi, mass, expect = o.layers()
+    assert len(lo) == 7 and lo[0] == 2.0 and hi[-1] == 204.75
+    assert np.all(hi[:-1] == lo[1:])
+    assert mass.sum() == pytest.approx(1.0, rel=1e-14)
+    Nl = 3 / (2.0 ** -3 - 204.75 ** -3)         # Eq. 32
+    for a, b, m in zip(lo, hi, mass):
+        assert m == pytest.approx(integrate.quad(lambda x: Nl * x ** -4, a, b)[0], rel=1e-10)
+
+
+def test_lambda_within_band_follows_P_lambda():
+    o = O.Oracle(params(box_L=409.5, lambda_max=204.75), np.array([[1.0, 1, 1], [5, 5, 5]]), np.array([1, 1], np.int32))
+    lo, hi, _, _ = o.layers()
+    for l in [0, 3, 6]:
+        lam, bead = o.sample_slots(l, 20000)
+        a, b = lo[l], hi[l]
+        cdf = lambda x: (a ** -3 - np.asarray(x) ** -3) / (a ** -3 - b ** -3)
+        assert stats.kstest(lam, cdf).pvalue > 1e-3
+        assert np.all((lam >= a) & (lam <= b))
+        assert set(np.unique(bead)) == {0, 1}
+
+
+def test_ball_points_and_polarisation():
+    o = O.Oracle(params(), np.array([[1.0, 1, 1], [5, 5, 5]]), np.array([1, 1], np.int32))
+    V = o.sample_ball(3, 40000)
+    r = np.linalg.norm(V, axis=1)
+    assert np.all(r <= 1.0)
+    assert stats.kstest(r, lambda x: np.clip(x, 0, 1) ** 3).pvalue > 1e-3     # uniform in the ball
+    assert np.all(np.abs(V.mean(0)) < 4 * np.sqrt(0.2 / len(V)))
+    P = o.sample_polarisation(4, 40000)
+    assert np.allclose(np.linalg.norm(P, axis=1), 1.0, atol=1e-15)
+    assert np.allclose(P.T @ P / len(P), np.eye(3) / 3, atol=0.012)              # isotropic
+    assert stats.kstest(P[:, 2], "uniform", args=(-1, 2)).pvalue > 1e-3         # Archimedes: z uniform
+
+
+# ---- dynamics pins ---------------------------------------------------------------------
+
+def _msd_per_move(o, sweeps, batches):
+    x0 = o.positions(unwrapped=True)
+    acc0 = o.stats().accepted_total
+    per = []
+    for _ in range(batches):
+        o.sweep(sweeps)
+        x1 = o.positions(unwrapped=True)
+        acc1 = o.stats().accepted_total
+        per.append(np.mean(np.sum((x1 - x0) ** 2, axis=1)) / (acc1 - acc0))
+        x0, acc0 = x1, acc1
+    per = np.array(per)
+    return per.mean(), per.std(ddof=1) / np.sqrt(len(per))
+
+
+def test_free_bead_diffusion_wavelets():
+    """Eq. 33: per move <dr^2> = (2/105) A0^2 N_lambda (1/lmin - 1/lmax) / N for any
+    configuration of non-interacting beads, and MSD = a^2 t (Eq. 34, a = lmin/lambda_a)."""
+    N, L = 24, 64.0
+    s = I.make_system([], N, L, seed=2)
+    p = params(n_beads=N, box_L=L, seed=21)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    m, se = _msd_per_move(o, 200, 30)
+    Nl = 3 / (2.0 ** -3 - 32.0 ** -3)
+    want = 2 / 105 * 0.25 * Nl * (1 / 2.0 - 1 / 32.0) / N
+    assert abs(m - want) < 4 * se + 1e-3 * want
+    st = o.stats()
+    assert st.accepted_total == sum(st.attempts)                 # nothing rejects without interactions
+    a = 2.0 / O.lambda_a()
+    assert st.dt_move * a * a == pytest.approx(want, rel=1e-12)
+
+
+def test_free_bead_diffusion_with_plane_waves():
+    """Wavelets + periodic plane waves: per move (1-P_F)<dr^2>_w + P_F sum_k P(k) A_F(k)^2/2,
+    predicted from the mode tables; and the infinite-system identity of Eq. 57."""
+    N, L = 8, 24.0
+    s = I.make_system([], N, L, seed=4)
+    p = params(n_beads=N, box_L=L, lambda_max=12.0, planewave_mode=1, lcut=8, seed=5, grid_f=8)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    modes, prob, R, PF = o.pw_modes()
+    l2 = np.sum(modes.astype(float) ** 2, axis=1)
+    nz = l2 > 0
+    drF = np.sum(prob[nz] * 4 * 0.25 / ((2 * np.pi / L) ** 2 * l2[nz] * 5 * N) / 2)
+    Nl = 3 / (2.0 ** -3 - 12.0 ** -3)
+    drw = 2 / 105 * 0.25 * Nl * (1 / 2.0 - 1 / 12.0) / N
+    want = (1 - PF) * drw + PF * drF
+    m, se = _msd_per_move(o, 400, 30)
+    assert abs(m - want) < 4 * se + 2e-3 * want
+    assert o.stats().pw_attempts > 20
+    # infinite system: (1 - P_F)<dr^2>_w + P_F <dr^2>_F = 6 A0^2 lmin^2 / (105 N)  (Eqs. 53, 54, 57)
+    PFi = (2.0 / 12.0) ** 3
+    drFi = 6 * 0.25 * 12.0 ** 2 / (105 * N)
+    assert (1 - PFi) * drw + PFi * drFi == pytest.approx(6 * 0.25 * 4 / (105 * N), rel=1e-13)
+
+
+def Ow(r, lp, A0):
+    """Eq. 40: (g_rr, g_tt) of O_w(r; lambda', infinity), by scipy quadrature."""
+    def f(q, which):
+        Q = q * r / lp
+        ph = float(phitilde_np(q)) if q >= 0.5 else O.phitilde(q)
+        si = special.sici(Q)[0]
+        b = (math.sin(Q) - Q * math.cos(Q)) / Q ** 2
+        return q ** 3 * ph ** 2 * ((2 * si - 2 * b) if which == "rr" else (si + b))
+    pts = np.arange(0, 400, math.pi)
+    out = []
+    for w in ("rr", "tt"):
+        tot = sum(integrate.quad(f, a, b, args=(w,), limit=200)[0] for a, b in zip(pts[:-1], pts[1:]))
+        out.append(A0 ** 2 / (3 * math.pi * r) * tot)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("r", [3.0, 12.0])
+def test_two_bead_correlations_follow_Ow(r):
+    """<dr_0 (x) dr_1> per proposal = 3 N_lambda/(16 pi^2 N) O_w(r; lmin, lmax)  (Eqs. 39-41;
+    the constant follows from the Fourier transform of the proposal average). Also close to
+    Rotne-Prager (Eqs. 11-12) at a = lmin/lambda_a between lmin and lmax (Sec. V.D: "very close")."""
+    A0, lmin, lmax = 0.5, 2.0, 32.0
+    pos = np.array([[100.0, 100, 100], [100 + r, 100, 100]])
+    o = O.Oracle(params(box_L=200.0, lambda_max=lmax, seed=17), pos, np.array([1, 1], np.int32))
+    est = []
+    for b in range(10):
+        c01, c00, _ = o.propose_moments(100000, offset=b * 100000)
+        est.append([c01[0, 0], c01[1, 1], np.trace(c00)])
+    est = np.array(est)
+    m, se = est.mean(0), est.std(0, ddof=1) / np.sqrt(len(est))
+    Nl = 3 / (lmin ** -3 - lmax ** -3)
+    c = 3 * Nl / (16 * math.pi ** 2 * 2)
+    want = c * (Ow(r, lmin, A0) - Ow(r, lmax, A0))
+    assert abs(m[0] - want[0]) < 4.5 * se[0]
+    assert abs(m[1] - want[1]) < 4.5 * se[1]
+    tr0 = 4 * A0 ** 2 * (8 * math.pi ** 3 / 105) / (3 * math.pi) * (1 / lmin - 1 / lmax)
+    assert abs(m[2] - c * tr0) < 4.5 * se[2]
+    # Rotne-Prager (Eqs. 11-12), normalised by the self mobility 1/(6 pi eta a): compare the
+    # measured tensor plus the part lambda > lmax (which plane waves supply, Sec. VI), i.e.
+    # the full O_w(r; lmin, infinity) of Sec. V.D, with a = lmin / lambda_a.
+    a = lmin / O.lambda_a()
+    rp_rr = 6 * math.pi * a * (2 / (8 * math.pi * r) - 2 / (12 * math.pi * r) * (a / r) ** 2)
+    rp_tt = 6 * math.pi * a * (1 / (8 * math.pi * r) + 1 / (12 * math.pi * r) * (a / r) ** 2)
+    tail = c * Ow(r, lmax, A0)
+    self_ = (m[2] + c * 4 * A0 ** 2 * (8 * math.pi ** 3 / 105) / (3 * math.pi * lmax)) / 3
+    assert (m[0] + tail[0]) / self_ == pytest.approx(rp_rr, rel=0.08)
+    assert (m[1] + tail[1]) / self_ == pytest.approx(rp_tt, rel=0.08)
+
+
+def test_boltzmann_one_bead_in_a_well():
+    """One bead in a harmonic well with wavelet moves: the proposal is symmetric and
+    position independent, so Metropolis (Eq. 20) leaves exp(-U/kT) invariant exactly."""
+    kappa, kT = 0.3, 1.0
+    p = params(n_beads=1, box_L=64.0, lambda_max=16.0, ext_kappa=kappa, kT=kT, seed=99)
+    o = O.Oracle(p, np.array([[32.0, 32.0, 32.0]]), np.array([1], np.int32))
+    o.sweep(2000)
+    x = o.sweep_record(400000) - 32.0
+    bm = x.reshape(200, -1, 3)
+    var_b = np.mean(bm ** 2, axis=1)                  # batch means of x^2
+    v, se = var_b.mean(0), var_b.std(0, ddof=1) / np.sqrt(len(var_b))
+    assert np.all(np.abs(v - kT / kappa) < 4.5 * se + 0.01 * kT / kappa)
+    # histogram of x against the Gaussian (thinned to reduce correlation)
+    xs = x[::40, 0]
+    edges = np.linspace(-3, 3, 13) * math.sqrt(kT / kappa)
+    h, _ = np.histogram(xs, bins=edges)
+    pr = np.diff(stats.norm.cdf(edges / math.sqrt(kT / kappa)))
+    pr = pr / pr.sum() * h.sum()
+    chi2 = np.sum((h - pr) ** 2 / pr)
+    assert chi2 < 40.0
+
+
+@pytest.mark.parametrize("L", [40.0, 80.0, 160.0])
+def test_periodic_mobility_finite_box(L):
+    """Eq. 60: the periodic self-mobility is the infinite one times (1 - 2.837 a/L), with
+    a = lmin/lambda_a. From the oracle's mode tables and P_F (Eqs. 48, 51, 55, 56)."""
+    A0, lmin = 0.5, 2.0
+    o = O.Oracle(params(n_beads=1, box_L=L, lambda_max=L / 2, planewave_mode=1, lcut=15, grid_f=8),
+                 np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+    modes, prob, R, PF = o.pw_modes()
+    l2 = np.sum(modes.astype(float) ** 2, axis=1)
+    nz = l2 > 0
+    drF = np.sum(prob[nz] * 4 * A0 ** 2 / ((2 * np.pi / L) ** 2 * l2[nz] * 5) / 2)
+    Nl = 3 / (lmin ** -3 - (L / 2) ** -3)
+    drw = 2 / 105 * A0 ** 2 * Nl * (1 / lmin - 2 / L)
+    ratio = ((1 - PF) * drw + PF * drF) / (6 * A0 ** 2 * lmin ** 2 / 105)
+    a = lmin / O.lambda_a()
+    assert ratio == pytest.approx(1 - 2.837 * a / L, abs=4e-5)
+
+
+def test_plane_wave_normalisation_converges():
+    """R -> 1 as the mode set grows at lambda_max = L/2 (continuum limit of Eq. 55), and the
+    k = 0 mode carries 0.1018 of the probability at |l| <= 8."""
+    Rs = []
+    for lcut in (4, 8, 16, 32):
+        o = O.Oracle(params(n_beads=1, planewave_mode=1, lcut=lcut), np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+        modes, prob, R, PF = o.pw_modes()
+        Rs.append(R)
+        n_expected = sum(1 for x in range(-lcut, lcut + 1) for y in range(-lcut, lcut + 1)
+                         for z in range(-lcut, lcut + 1) if x * x + y * y + z * z <= lcut * lcut)
+        assert len(modes) == n_expected
+        assert prob.sum() == pytest.approx(1.0, rel=1e-13)
+        if lcut == 8:
+            assert prob[np.all(modes == 0, axis=1)][0] == pytest.approx(0.1018, abs=1e-4)
+            assert PF == pytest.approx(1 / (1 + R * (16.0 ** 3 - 1)), rel=1e-14)
+    Rs = np.array(Rs)
+    assert np.all(np.diff(Rs) < 0) and np.all(Rs > 1)
+    assert (Rs[3] - 1) < 0.55 * (Rs[2] - 1)          # roughly 1/lcut convergence
+
+
+def test_metropolis_rejects_overstretched_fene_and_counts():
+    # a two-bead FENE chain close to R0: large moves overstretch and must reject
+    p = params(n_beads=2, box_L=64.0, lambda_max=32.0, bond_type=2, bond_k=30.0, fene_R0=2.05, wca_eps=1.0, seed=3,
+               A0=2.0)
+    o = O.Oracle(p, np.array([[30.0, 30, 30], [32.0, 30, 30]]), np.array([2], np.int32))
+    o.sweep(3000)
+    x = o.positions(unwrapped=True)
+    assert np.linalg.norm(x[1] - x[0]) < 2.05
+    st = o.stats()
+    assert 0 < sum(st.accepts) < sum(st.attempts)
+
+
+def test_coloured_schedule_keeps_free_diffusion_and_defers_correctly():
+    """The colouring only reorders moves: free-bead diffusion per move still follows Eq. 33.
+    With coarse cells too small for the support every concurrent attempt is deferred."""
+    from paper_1611_09160_gb300 import schedule
+    N = 400
+    s = I.free_spheres(N, 2e-3, seed=9)
+    L = s.box_L
+    sch = schedule.choose(L, 2.0, L / 2, 0.5, 2.0, 0.0)
+    assert sch["grid_layer"][0] > 0
+    p = params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31, **sch)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    m, se = _msd_per_move(o, 20, 20)
+    lo, hi, _, _ = o.layers()
+    Nl = 3 / (2.0 ** -3 - (L / 2) ** -3)
+    want = 2 / 105 * 0.25 * Nl * (1 / 2.0 - 2 / L) / N
+    assert abs(m - want) < 4 * se + 1e-3 * want
+    st = o.stats()
+    assert sum(st.attempts) == sum(st.accepts)
+    # tiny coarse cells: every concurrent attempt of layer 0 must be deferred
+    # region side 2h below the smallest influence diameter 2 * 1.125 * lambda_min = 4.5
+    G = 2 * int(math.ceil(L / 2.2 / 2))
+    assert 2 * L / G < 4.5
+    fine = dict(sch, grid_layer=[G] + [0] * 15)
+    o2 = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31, **fine), s.pos, s.chain_len)
+    o2.sweep(1)
+    st2 = o2.stats()
+    assert st2.deferred[0] == st2.attempts[0] > 0
+    out, n = o2.trace_layer(0)
+    assert np.all(out & 4)
