@@ -1,0 +1,161 @@
+/*
+ * wmcd.h — C ABI of the GB300 (sm_103a) Wavelet Monte Carlo dynamics library.
+ *
+ * Wavelet Monte Carlo dynamics (Dyer & Ball, arXiv:1611.09160) evolves N interacting
+ * Brownian beads by Metropolis-accepted, spatially correlated moves: divergence-free
+ * tapered-wavelet moves of scale lambda drawn from P_lambda ~ lambda^-4 (Secs. IV-V,
+ * Eqs. 21-34, Appendix D) and, for a periodic box, plane-wave moves that carry the
+ * longest-range correlations (Sec. VI, Eqs. 47-57). Their accumulated displacements
+ * reproduce Oseen / Rotne-Prager hydrodynamics.
+ *
+ * Conventions for every entry point:
+ *  - lengths are in units of the bead radius a, energies in the same units as kT;
+ *  - positions are double[3 * n_beads], row-major (x, y, z per bead);
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream); all
+ *    work is enqueued on it and is asynchronous unless stated otherwise;
+ *  - a pointer argument documented "host or device" is classified with
+ *    cudaPointerGetAttributes; host memory may be pageable or pinned;
+ *  - the handle owns all device state; caller buffers are only borrowed for the call;
+ *  - a handle is not thread-safe; different handles are independent;
+ *  - every function returns 0 (WMCD_OK) or a negative wmcd_status; no C++ exception or
+ *    CUDA error crosses the ABI. wmcd_strerror() turns a status into text.
+ */
+#ifndef WMCD_H
+#define WMCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum wmcd_status {
+    WMCD_OK = 0,
+    WMCD_EINVAL = -1,     /* bad argument or parameter (see wmcd_create) */
+    WMCD_ENOMEM = -2,     /* device or host allocation failed */
+    WMCD_ECUDA = -3,      /* a CUDA runtime call failed */
+    WMCD_ETIMEOUT = -4,   /* a bounded device-side wait or list walk gave up */
+    WMCD_ESTATE = -5      /* non-finite positions or a corrupted cell list were detected */
+} wmcd_status;
+
+enum { WMCD_BOND_NONE = 0, WMCD_BOND_HARMONIC = 1, WMCD_BOND_FENE = 2 };
+enum { WMCD_PLANEWAVE_OFF = 0, WMCD_PLANEWAVE_PERIODIC = 1 };
+enum { WMCD_FP64 = 0, WMCD_MIXED = 1 };
+#define WMCD_MAX_LAYERS 16
+
+/* Parameters of one simulation. */
+typedef struct wmcd_params {
+    int64_t n_beads;          /* N >= 1 */
+    double box_L;             /* side of the periodic cube */
+    double lambda_min;        /* smallest wavelet scale (sets the hydrodynamic radius, Eq. 42) */
+    double lambda_max;        /* largest scale, lambda_min < lambda_max <= L/2 (Sec. V.C) */
+    double A0;                /* move amplitude parameter A_w = A0 lambda / sqrt(n) (Eq. 29) */
+    double kT;                /* thermal energy of the Metropolis test (Eq. 20) */
+    int32_t bond_type;        /* WMCD_BOND_*: chain neighbours i, i+1 of one chain are bonded */
+    double bond_k;            /* harmonic: U = (k/2)(r - r0)^2; FENE: Eq. 1 with k and R0 */
+    double bond_r0;
+    double fene_R0;
+    double wca_sigma;         /* WCA repulsion (Eq. 2) between all pairs; eps = 0 disables */
+    double wca_eps;
+    double ext_kappa;         /* external well (kappa/2)|r - box centre|^2; 0 disables */
+    int32_t planewave_mode;   /* WMCD_PLANEWAVE_*: periodic plane-wave moves (Sec. VI) */
+    int32_t lcut;             /* plane-wave modes k = (2 pi / L) l with |l| <= lcut */
+    int32_t precision;        /* WMCD_FP64, or WMCD_MIXED: FP32 displacements and pair
+                                 energies, FP64 positions, FP64 recheck near the threshold */
+    uint64_t seed;            /* Philox key, with sim_id */
+    uint64_t sim_id;
+    /* concurrent schedule: moves of one layer run concurrently in K^3 colour phases over
+       G^3 coarse cells; a move that does not fit its cell's region is deferred to a serial
+       phase, so results do not depend on these values except through that order */
+    int32_t colour_K;         /* colours per axis, 2..4 */
+    int32_t grid_f;           /* fine (cell-list) cells per axis, L / grid_f >= WCA cutoff */
+    int32_t n_cap;            /* largest support a concurrent move handles (1..64) */
+    int32_t grid_layer[WMCD_MAX_LAYERS];  /* coarse cells per axis per layer; 0 = serial;
+                                             otherwise a multiple of colour_K, at most 256 */
+} wmcd_params;
+
+/* Counters since creation (or the last wmcd_set_state). */
+typedef struct wmcd_stats_t {
+    int64_t attempts[WMCD_MAX_LAYERS];   /* wavelet moves attempted, per layer */
+    int64_t accepts[WMCD_MAX_LAYERS];
+    int64_t deferred[WMCD_MAX_LAYERS];   /* concurrent attempts sent to the serial phase */
+    int64_t pw_attempts, pw_accepts;     /* plane-wave moves (k = 0 counts as accepted) */
+    int64_t bead_updates;                /* sum of support sizes n, plus N per k != 0 plane wave */
+    int64_t accepted_total;              /* all accepted moves: simulated time = this * dt_move */
+    int64_t rechecks;                    /* mixed precision: moves re-decided in FP64 */
+    int64_t partner_evals;               /* pair evaluations with beads outside the support */
+    double sim_time;                     /* in units of tau = pi eta a^3 / kT (Eq. 3) */
+    int64_t sweeps;
+    int64_t n_layers;
+    double dt_move;                      /* Eq. 57 with plane waves, Eq. 34 without */
+    double p_fourier;                    /* probability of a plane-wave move (Eq. 56) */
+    int32_t error_flags;                 /* device-side error bits, 0 = none */
+} wmcd_stats_t;
+
+typedef struct wmcd_handle wmcd_handle;
+
+/* Create a simulation. pos: N*3 doubles (host or device), each coordinate in [0, L).
+ * chain_len: n_chains int32 (host), the lengths of consecutive runs of bead ids that form
+ * chains (free beads are chains of length 1); the lengths must sum to N.
+ * Validates: N >= 1; 0 < lambda_min < lambda_max <= L/2; A0 > 0; kT > 0; colour_K in 2..4;
+ * grid_f >= 1 with L/grid_f >= the WCA cutoff 2^(1/6) sigma (when WCA is on);
+ * 1 <= n_cap <= 64; each grid_layer[l] is 0 or a multiple of colour_K in [colour_K, 256];
+ * at most 16 octave layers; lcut in 0..120 with plane waves. Returns WMCD_EINVAL otherwise.
+ * Synchronises `stream` before returning. *out receives the handle. */
+int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,
+                void* stream, wmcd_handle** out);
+
+/* Advance by n_sweeps sweeps. A sweep = the octave layers of P_lambda in ascending order,
+ * each with floor(N (1 - P_F) p_l) slots plus one more with probability of the fraction,
+ * run as colour phases then a serial phase; then the sweep's plane-wave slots. Asynchronous. */
+int wmcd_sweep(wmcd_handle* h, int64_t n_sweeps, void* stream);
+
+/* n_moves plane-wave moves (Sec. VI) outside the sweep schedule, one after another, with
+ * their own random stream. Needs planewave_mode = PERIODIC. Asynchronous. */
+int wmcd_planewave(wmcd_handle* h, int64_t n_moves, void* stream);
+
+/* Copy positions to `out` (N*3 doubles, host or device); unwrapped != 0 adds the periodic
+ * image counters times L. Synchronises `stream` when `out` is host memory. */
+int wmcd_positions(wmcd_handle* h, double* out, int unwrapped, void* stream);
+
+/* Replace the positions (N*3 doubles in [0, L), host or device) and zero the image counters;
+ * rebuilds the cell list. Carries, counters and the sweep index are kept. Asynchronous for
+ * device input; host input is copied before return. */
+int wmcd_set_positions(wmcd_handle* h, const double* pos, void* stream);
+
+/* Synchronises `stream`, then fills *out. */
+int wmcd_stats(wmcd_handle* h, wmcd_stats_t* out, void* stream);
+
+/* Per-slot outcome of the last sweep, for layer `layer` (wavelet moves) or layer = -1
+ * (that sweep's plane-wave moves): out[j] = 1 accepted / 2 rejected, +4 when a concurrent
+ * attempt was deferred and ran in the serial phase; n[j] = support size (plane waves: the
+ * wave vector packed as (lx+128) | (ly+128) << 8 | (lz+128) << 16). Buffers are host memory
+ * of `cap` entries; *count receives the number of slots. Synchronises `stream`. */
+int wmcd_trace(wmcd_handle* h, int layer, uint8_t* out, int32_t* n, int64_t cap, int64_t* count, void* stream);
+
+/* Checkpoint: the state is positions, image counters, carries, the sweep and plane-wave
+ * call counters and the statistics. wmcd_state_size gives the byte size; get writes it to
+ * a host buffer, set restores it. With the counter-based random stream a restored run
+ * continues bit-identically. Both synchronise `stream`. */
+int wmcd_state_size(wmcd_handle* h, int64_t* bytes);
+int wmcd_get_state(wmcd_handle* h, void* buf, int64_t bytes, void* stream);
+int wmcd_set_state(wmcd_handle* h, const void* buf, int64_t bytes, void* stream);
+
+/* Per-kernel timing: when enabled, the library records CUDA events around every launch of
+ * its concurrent wavelet kernel, serial kernel and plane-wave kernels on `stream`;
+ * wmcd_kernel_times synchronises and returns (launches, total milliseconds) for the
+ * kernel classes 0 = concurrent wavelet, 1 = serial wavelet, 2 = plane wave, 3 = cell list,
+ * 4 = schedule (slots and bucketing). */
+int wmcd_profile(wmcd_handle* h, int enable);
+int wmcd_kernel_times(wmcd_handle* h, int64_t* launches, double* ms, int n_classes, void* stream);
+
+/* Device bytes held by the handle. */
+int wmcd_device_bytes(wmcd_handle* h, int64_t* bytes);
+
+int wmcd_destroy(wmcd_handle* h);
+const char* wmcd_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WMCD_H */

@@ -1,0 +1,653 @@
+// Host side of the WMCD library: per-simulation constants and tables, device allocation,
+// the order of launches in a sweep, and the C ABI declared in include/wmcd.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+#include "../../include/wmcd.h"
+#include "wmcd_internal.h"
+
+namespace wmcd {
+
+// ---------------------------------------------------------------------------------------
+// Plane-wave weights G(Q) = Int_Q^inf q^3 phi~(q)^2 dq (Eqs. 49, 51) for the tapered
+// wavelet, phi~(k) = 4 pi k^-6 (5 k sin k - (k^2 - 8) cos k - 8) (Eq. 25).
+// Near k = 0 the bracket is replaced by its Taylor series, whose coefficients follow from
+// those of sin and cos:  bracket = sum_{p>=3} c_p k^{2p},
+//   c_p = (-1)^{p-1} [5/(2p-1)! - 1/(2p-2)! - 8/(2p)!].
+// ---------------------------------------------------------------------------------------
+static double phit(double k) {
+    k = std::fabs(k);
+    if (k < 1.5) {
+        double s = 0.0;
+        double f2m2 = 24.0;                   // (2p-2)! at p = 3
+        for (int p = 3; p < 24; p++) {
+            double f2m1 = f2m2 * (2 * p - 1), f2 = f2m1 * (2 * p);
+            double c = 5.0 / f2m1 - 1.0 / f2m2 - 8.0 / f2;
+            double term = c * std::pow(k, 2 * p - 6);
+            s += (p % 2 == 1) ? term : -term;
+            f2m2 = f2;
+        }
+        return 4.0 * kPi * s;
+    }
+    double k2 = k * k;
+    return 4.0 * kPi * (5.0 * k * std::sin(k) - (k2 - 8.0) * std::cos(k) - 8.0) / (k2 * k2 * k2);
+}
+// 10-point Gauss-Legendre nodes and weights on [-1, 1]
+static const double GL10_X[5] = {0.1488743389816312, 0.4333953941292472, 0.6794095682990244, 0.8650633666889845,
+                                 0.9739065285171717};
+static const double GL10_W[5] = {0.2955242247147529, 0.2692667193099963, 0.2190863625159820, 0.1494513491505806,
+                                 0.0666713443086881};
+static double gl10(double a, double b) {
+    double c = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+    for (int i = 0; i < 5; i++) {
+        for (int sg = -1; sg <= 1; sg += 2) {
+            double q = c + sg * h * GL10_X[i], f = phit(q);
+            s += GL10_W[i] * q * q * q * f * f;
+        }
+    }
+    return s * h;
+}
+// Smooth part of the tail beyond Kc: the non-oscillating terms of q^3 phi~^2 at large q,
+// 16 pi^2 (q^-5/2 + 9/2 q^-7 + 96 q^-9), integrated exactly.
+static double tail3(double Kc) {
+    return 16.0 * kPi * kPi * (0.125 * std::pow(Kc, -4) + 0.75 * std::pow(Kc, -6) + 12.0 * std::pow(Kc, -8));
+}
+static void G_table(const std::vector<double>& Q, std::vector<double>& out) {
+    const double h = kPi / 20.0;
+    const int panels = 40000;                 // up to Kc = 2000 pi (a multiple of pi)
+    std::vector<double> acc(panels + 1);
+    acc[panels] = tail3(panels * h);
+    for (int p = panels - 1; p >= 0; p--) acc[p] = acc[p + 1] + gl10(p * h, (p + 1) * h);
+    out.resize(Q.size());
+    for (size_t i = 0; i < Q.size(); i++) {
+        double q = Q[i];
+        if (q >= panels * h) { out[i] = tail3(q); continue; }
+        int p = (int)(q / h);
+        double top = (p + 1) * h;
+        out[i] = acc[p + 1] + (top > q ? gl10(q, top) : 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------------------
+struct Handle {
+    wmcd_params P;
+    SimView v;
+    int dev = 0;
+    int64_t N = 0;
+    int nL = 0;
+    double expect[kMaxLayers] = {0};
+    int Mmax[kMaxLayers] = {0};
+    double p_fourier = 0.0, dt_move = 0.0, R = 1.0;
+    uint64_t sweep = 0, pw_calls = 0;
+    int64_t tr_pw_count = 0;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    double* staging = nullptr;   // 3N doubles
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    int64_t prof_launches[8] = {0};
+    double prof_ms[8] = {0};
+};
+
+static int last_cuda_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
+}
+
+template <class T>
+static int dalloc(Handle* h, T** p, size_t count) {
+    size_t nb = std::max<size_t>(count, 1) * sizeof(T);
+    void* q = nullptr;
+    if (cudaMalloc(&q, nb) != cudaSuccess) { cudaGetLastError(); return WMCD_ENOMEM; }
+    h->allocs.push_back(q);
+    h->bytes += nb;
+    *p = (T*)q;
+    return WMCD_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static cudaEvent_t get_event(Handle* h) {
+    if (!h->ev_pool.empty()) { cudaEvent_t e = h->ev_pool.back(); h->ev_pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+static void prof_harvest(Handle* h) {
+    for (auto& u : h->ev_used) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess) {
+            h->prof_ms[u.first] += ms;
+            h->prof_launches[u.first]++;
+        } else {
+            cudaGetLastError();
+        }
+        h->ev_pool.push_back(u.second.first);
+        h->ev_pool.push_back(u.second.second);
+    }
+    h->ev_used.clear();
+}
+struct ProfScope {
+    Handle* h; int cls; cudaStream_t s; cudaEvent_t a{}, b{};
+    ProfScope(Handle* h_, int c, cudaStream_t s_) : h(h_), cls(c), s(s_) {
+        if (h->prof) { a = get_event(h); cudaEventRecord(a, s); }
+    }
+    ~ProfScope() {
+        if (h->prof) {
+            b = get_event(h);
+            cudaEventRecord(b, s);
+            h->ev_used.push_back({cls, {a, b}});
+            if (h->ev_used.size() > 20000) { cudaEventSynchronize(b); prof_harvest(h); }
+        }
+    }
+};
+
+// stratified slot count: floor(x) plus one more with probability frac(x)
+static int64_t slot_count(const Handle* h, uint32_t kind, int l, uint64_t ctr, double x) {
+    u4 w = draw(h->v.k0, h->v.k1, kind, l, ctr, 0u, 0u);
+    double u = u53(w.x, w.y), f = std::floor(x);
+    return (int64_t)f + ((u < x - f) ? 1 : 0);
+}
+
+__global__ void k_fill_beads(Bead* bead, const double* pos, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        bead[i].x = pos[3 * i]; bead[i].y = pos[3 * i + 1]; bead[i].z = pos[3 * i + 2];
+        bead[i].mark = 0u;
+    }
+}
+__global__ void k_read_beads(const Bead* bead, const int* img, double L, int unwrapped, double* out, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        Bead b = bead[i];
+        double x[3] = {b.x, b.y, b.z};
+        for (int a = 0; a < 3; a++) out[3 * i + a] = unwrapped ? add(x[a], mul((double)img[3 * i + a], L)) : x[a];
+    }
+}
+static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+}  // namespace wmcd
+
+using namespace wmcd;
+
+struct wmcd_handle { Handle h; };
+
+static int validate(const wmcd_params* p) {
+    if (!p || p->n_beads < 1 || p->n_beads > (int64_t)1 << 30) return WMCD_EINVAL;
+    if (!(p->box_L > 0.0) || !(p->lambda_min > 0.0) || !(p->lambda_max > p->lambda_min) ||
+        p->lambda_max > 0.5 * p->box_L || !(p->A0 > 0.0) || !(p->kT > 0.0))
+        return WMCD_EINVAL;
+    if (p->bond_type < 0 || p->bond_type > 2 || p->colour_K < 2 || p->colour_K > 4 || p->grid_f < 1 ||
+        p->n_cap < 1 || p->n_cap > kNCap || p->precision < 0 || p->precision > 1)
+        return WMCD_EINVAL;
+    if (p->planewave_mode == 1 && (p->lcut < 0 || p->lcut > 120)) return WMCD_EINVAL;
+    if (p->planewave_mode != 0 && p->planewave_mode != 1) return WMCD_EINVAL;
+    if ((int64_t)p->grid_f * p->grid_f * p->grid_f > ((int64_t)1 << 31) - 1) return WMCD_EINVAL;
+    if (p->wca_eps != 0.0 && p->box_L / p->grid_f < kWcaCut * p->wca_sigma * (1.0 - 1e-12)) return WMCD_EINVAL;
+    if (p->bond_type == 2 && !(p->fene_R0 > 0.0)) return WMCD_EINVAL;
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,
+                           void* stream, wmcd_handle** out) {
+    if (!out || !pos || !chain_len || n_chains < 1) return WMCD_EINVAL;
+    *out = nullptr;
+    int rc = validate(params);
+    if (rc) return rc;
+    const wmcd_params& P = *params;
+    int64_t tot = 0;
+    for (int64_t c = 0; c < n_chains; c++) { if (chain_len[c] < 1) return WMCD_EINVAL; tot += chain_len[c]; }
+    if (tot != P.n_beads) return WMCD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    wmcd_handle* H = new (std::nothrow) wmcd_handle();
+    if (!H) return WMCD_ENOMEM;
+    Handle* h = &H->h;
+    h->P = P;
+    h->N = P.n_beads;
+    cudaGetDevice(&h->dev);
+    SimView& v = h->v;
+    std::memset(&v, 0, sizeof v);
+    v.N = P.n_beads;
+    v.L = P.box_L;
+    v.halfL = 0.5 * P.box_L;
+    v.Gf = P.grid_f;
+    v.invf = (double)P.grid_f / P.box_L;
+    v.K = P.colour_K;
+    v.n_cap = P.n_cap;
+    v.precision = P.precision;
+    v.A0 = P.A0;
+    v.kT = P.kT;
+    v.rc = kWcaCut * P.wca_sigma;
+    v.r_reach = (P.wca_eps != 0.0 ? v.rc : 0.0) + 1e-6;
+    v.pot.sig2 = P.wca_sigma * P.wca_sigma;
+    v.pot.eps = P.wca_eps;
+    v.pot.rc2 = v.rc * v.rc;
+    v.pot.bond = P.bond_type;
+    v.pot.bk = P.bond_k;
+    v.pot.br0 = P.bond_r0;
+    v.pot.R02 = P.fene_R0 * P.fene_R0;
+    v.pot.kappa = P.ext_kappa;
+    v.pot.halfL = v.halfL;
+    v.pot.L = v.L;
+    v.k0 = (uint32_t)P.seed;
+    v.k1 = (uint32_t)(P.seed >> 32) ^ (uint32_t)P.sim_id;
+
+    // plane-wave tables and P_F (Eqs. 51, 55, 56)
+    std::vector<int> modes;
+    std::vector<double> cdf;
+    h->p_fourier = 0.0;
+    if (P.planewave_mode == 1) {
+        std::vector<double> Q;
+        for (int lx = -P.lcut; lx <= P.lcut; lx++)
+            for (int ly = -P.lcut; ly <= P.lcut; ly++)
+                for (int lz = -P.lcut; lz <= P.lcut; lz++) {
+                    int l2 = lx * lx + ly * ly + lz * lz;
+                    if (l2 > P.lcut * P.lcut) continue;
+                    modes.push_back(lx); modes.push_back(ly); modes.push_back(lz);
+                    Q.push_back(kTwoPi * std::sqrt((double)l2) / P.box_L * P.lambda_max);
+                }
+        std::vector<double> g;
+        G_table(Q, g);
+        double tot_w = 0.0;
+        for (double x : g) tot_w += x;
+        cdf.resize(g.size());
+        double acc = 0.0;
+        for (size_t i = 0; i < g.size(); i++) { acc += g[i]; cdf[i] = acc / tot_w; }
+        const double M6 = 8.0 * kPi * kPi * kPi / 5.0;
+        const double ratio = P.box_L / P.lambda_max;
+        h->R = (1.0 / (6.0 * kPi * kPi)) * (ratio * ratio * ratio) * M6 / tot_w;
+        const double rl = P.lambda_max / P.lambda_min;
+        h->p_fourier = 1.0 / (1.0 + h->R * (rl * rl * rl - 1.0));
+    }
+    // octave layers of P_lambda (Eq. 32)
+    int nL = 1;
+    while (P.lambda_min * std::ldexp(1.0, nL) < P.lambda_max) nL++;
+    if (nL > kMaxLayers) { delete H; return WMCD_EINVAL; }
+    h->nL = v.nL = nL;
+    const double imin3 = 1.0 / ((P.lambda_min * P.lambda_min) * P.lambda_min);
+    const double imax3 = 1.0 / ((P.lambda_max * P.lambda_max) * P.lambda_max);
+    int64_t tr_total = 0, carry_total = 0, keys_max = 1, Mall = 1;
+    for (int l = 0; l < nL; l++) {
+        LayerDev& Ly = v.layer[l];
+        Ly.lo = P.lambda_min * std::ldexp(1.0, l);
+        Ly.hi = (l + 1 == nL) ? P.lambda_max : P.lambda_min * std::ldexp(1.0, l + 1);
+        Ly.ilo3 = 1.0 / ((Ly.lo * Ly.lo) * Ly.lo);
+        Ly.ihi3 = 1.0 / ((Ly.hi * Ly.hi) * Ly.hi);
+        const double mass = (Ly.ilo3 - Ly.ihi3) / (imin3 - imax3);
+        h->expect[l] = ((double)h->N * (1.0 - h->p_fourier)) * mass;
+        h->Mmax[l] = (int)std::floor(h->expect[l]) + 1;
+        Mall = std::max<int64_t>(Mall, h->Mmax[l]);
+        Ly.G = P.grid_layer[l];
+        if (Ly.G < 0 || (Ly.G > 0 && (Ly.G % P.colour_K != 0 || Ly.G < P.colour_K)) || Ly.G > 256) {
+            delete H;
+            return WMCD_EINVAL;
+        }
+        Ly.invG = Ly.G > 0 ? (double)Ly.G / P.box_L : 0.0;
+        Ly.carry_off = (int)carry_total;
+        carry_total += (int64_t)Ly.G * Ly.G * Ly.G;
+        keys_max = std::max<int64_t>(keys_max, (int64_t)Ly.G * Ly.G * Ly.G);
+        Ly.tr_off = tr_total;
+        tr_total += h->Mmax[l];
+    }
+    // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2 pi)^3 = 1/105)
+    {
+        const double la = 1.0 / (1.125 - kLn2), A02 = P.A0 * P.A0, la2 = la * la;
+        if (P.planewave_mode == 1) h->dt_move = (6.0 * A02 * la2) / (105.0 * (double)h->N);
+        else {
+            double Nl = 3.0 / (imin3 - imax3);
+            h->dt_move = ((2.0 * A02 * la2) / (105.0 * (double)h->N)) * (Nl * imin3) * (1.0 - P.lambda_min / P.lambda_max);
+        }
+    }
+    // device state
+    const int64_t N = h->N;
+    const int64_t ncell = (int64_t)P.grid_f * P.grid_f * P.grid_f;
+    int pw_cap = (int)std::min<double>(1e6, 4.0 * h->p_fourier * (double)N + 64.0);
+    v.pw_blocks = (int)((N + 255) / 256);
+    bool ok = true;
+    ok = ok && !dalloc(h, &v.bead, N) && !dalloc(h, &v.prev, N) && !dalloc(h, &v.img, 3 * N) &&
+         !dalloc(h, &v.bnext, N) && !dalloc(h, &v.head, ncell);
+    ok = ok && !dalloc(h, &v.slot_lam, Mall) && !dalloc(h, &v.slot_bead, Mall) && !dalloc(h, &v.slot_key, Mall) &&
+         !dalloc(h, &v.q_slots, Mall) && !dalloc(h, &v.defer, Mall) && !dalloc(h, &v.serial_list, Mall);
+    ok = ok && !dalloc(h, &v.q_count, keys_max) && !dalloc(h, &v.q_start, keys_max) && !dalloc(h, &v.q_fill, keys_max);
+    ok = ok && !dalloc(h, &v.serial_count, 4) && !dalloc(h, &v.carry_q, carry_total) &&
+         !dalloc(h, &v.carry_serial, kMaxLayers);
+    ok = ok && !dalloc(h, &v.tr_out, tr_total) && !dalloc(h, &v.tr_n, tr_total) && !dalloc(h, &v.tr_pw_out, pw_cap) &&
+         !dalloc(h, &v.tr_pw_mode, pw_cap) && !dalloc(h, &v.tr_pw_count, 1);
+    ok = ok && !dalloc(h, &v.ctr, C_NCTR) && !dalloc(h, &v.err, 1);
+    ok = ok && !dalloc(h, &v.s_ids, N) && !dalloc(h, &v.s_d, 4 * N) && !dalloc(h, &v.s_new, 3 * N) &&
+         !dalloc(h, &v.s_img, N) && !dalloc(h, &v.s_slot, N) && !dalloc(h, &v.s_changed, 3 * N) &&
+         !dalloc(h, &v.serial_tag, 1);
+    ok = ok && !dalloc(h, &v.pw, 1) && !dalloc(h, &v.pw_new, 3 * N) && !dalloc(h, &v.pw_imgd, N) &&
+         !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1);
+    int* d_modes = nullptr;
+    double* d_cdf = nullptr;
+    ok = ok && !dalloc(h, &d_modes, modes.size() + 3) && !dalloc(h, &d_cdf, cdf.size() + 1);
+    ok = ok && !dalloc(h, &h->staging, 3 * N);
+    if (!ok) { wmcd_destroy(H); return WMCD_ENOMEM; }
+    v.tr_pw_cap = pw_cap;
+    v.modes = d_modes;
+    v.mode_cdf = d_cdf;
+    v.n_modes = (int)cdf.size();
+    // host -> device
+    std::vector<uint8_t> bn(N, 0);
+    {
+        int64_t b = 0;
+        for (int64_t c = 0; c < n_chains; c++) {
+            for (int32_t k = 0; k + 1 < chain_len[c]; k++) bn[b + k] = 1;
+            b += chain_len[c];
+        }
+    }
+    cudaMemcpyAsync(v.bnext, bn.data(), N, cudaMemcpyHostToDevice, s);
+    if (!modes.empty()) {
+        cudaMemcpyAsync(d_modes, modes.data(), modes.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_cdf, cdf.data(), cdf.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    cudaMemcpyAsync(h->staging, pos, 3 * N * sizeof(double), is_device_ptr(pos) ? cudaMemcpyDeviceToDevice
+                                                                                 : cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(v.img, 0, 3 * N * sizeof(int), s);
+    cudaMemsetAsync(v.carry_q, 0, std::max<int64_t>(carry_total, 1) * sizeof(double), s);
+    cudaMemsetAsync(v.carry_serial, 0, kMaxLayers * sizeof(double), s);
+    cudaMemsetAsync(v.ctr, 0, C_NCTR * sizeof(unsigned long long), s);
+    cudaMemsetAsync(v.err, 0, sizeof(int), s);
+    cudaMemsetAsync(v.serial_tag, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(v.pw, 0, sizeof(PWDev), s);
+    cudaMemsetAsync(v.tr_out, 0, std::max<int64_t>(tr_total, 1), s);
+    cudaMemsetAsync(v.tr_n, 0, std::max<int64_t>(tr_total, 1) * sizeof(int), s);
+    k_fill_beads<<<grid_for(N), 256, 0, s>>>(v.bead, h->staging, N);
+    launch_cl_rebuild(v, s, nullptr);
+    if (cudaStreamSynchronize(s) != cudaSuccess || last_cuda_status()) { cudaGetLastError(); wmcd_destroy(H); return WMCD_ECUDA; }
+    int err = 0;
+    cudaMemcpy(&err, v.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) { wmcd_destroy(H); return WMCD_EINVAL; }   // a coordinate outside [0, L) or not finite
+    *out = H;
+    return WMCD_OK;
+}
+
+static void run_sweep(Handle* h, cudaStream_t s) {
+    SimView& v = h->v;
+    const uint64_t sw = h->sweep;
+    for (int l = 0; l < h->nL; l++) {
+        const int64_t M = slot_count(h, K_COUNT, l, sw, h->expect[l]);
+        if (M <= 0) continue;
+        { ProfScope ps(h, 4, s); launch_slots(v, l, sw, (int)M, s); }
+        if (v.layer[l].G > 0) {
+            { ProfScope ps(h, 4, s); launch_bucket(v, l, (int)M, s); }
+            const int nc = v.K * v.K * v.K;
+            for (int c = 0; c < nc; c++) { ProfScope ps(h, 0, s); launch_colour(v, l, c, sw, s); }
+            { ProfScope ps(h, 4, s); launch_defer_compact(v, (int)M, s); }
+            { ProfScope ps(h, 1, s); launch_serial(v, l, sw, 1, (int)M, s); }
+        } else {
+            ProfScope ps(h, 1, s);
+            launch_serial(v, l, sw, 0, (int)M, s);
+        }
+    }
+    h->tr_pw_count = 0;
+    if (h->P.planewave_mode == 1) {
+        const int64_t MF = slot_count(h, K_PWCOUNT, 0, sw, (double)h->N * h->p_fourier);
+        for (int64_t m = 0; m < MF; m++) {
+            ProfScope ps(h, 2, s);
+            launch_planewave(v, K_PWMODE, K_PWDIR, K_PWACC, sw, (int)m, (int)m, s);
+        }
+        h->tr_pw_count = MF;
+    }
+    h->sweep++;
+}
+
+extern "C" int wmcd_sweep(wmcd_handle* H, int64_t n_sweeps, void* stream) {
+    if (!H || n_sweeps < 0) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int64_t k = 0; k < n_sweeps; k++) run_sweep(h, s);
+    return last_cuda_status();
+}
+
+extern "C" int wmcd_planewave(wmcd_handle* H, int64_t n_moves, void* stream) {
+    if (!H || n_moves < 0) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    if (h->P.planewave_mode != 1) return WMCD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_moves > h->v.tr_pw_cap) {
+        // grow the trace so every move of this call is recorded
+        cudaStreamSynchronize(s);
+        uint8_t* o = nullptr;
+        int* md = nullptr;
+        if (dalloc(h, &o, n_moves) || dalloc(h, &md, n_moves)) return WMCD_ENOMEM;
+        h->v.tr_pw_out = o;
+        h->v.tr_pw_mode = md;
+        h->v.tr_pw_cap = (int)std::min<int64_t>(n_moves, 1 << 30);
+    }
+    for (int64_t m = 0; m < n_moves; m++) {
+        ProfScope ps(h, 2, s);
+        launch_planewave(h->v, K_DPWMODE, K_DPWDIR, K_DPWACC, h->pw_calls, (int)m, (int)m, s);
+    }
+    h->tr_pw_count = n_moves;
+    h->pw_calls++;
+    return last_cuda_status();
+}
+
+extern "C" int wmcd_positions(wmcd_handle* H, double* out, int unwrapped, void* stream) {
+    if (!H || !out) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev = is_device_ptr(out);
+    double* dst = dev ? out : h->staging;
+    k_read_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->v.img, h->v.L, unwrapped, dst, h->N);
+    if (!dev) {
+        cudaMemcpyAsync(out, h->staging, 3 * h->N * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return WMCD_ECUDA;
+    }
+    return last_cuda_status();
+}
+
+extern "C" int wmcd_set_positions(wmcd_handle* H, const double* pos, void* stream) {
+    if (!H || !pos) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev = is_device_ptr(pos);
+    cudaMemcpyAsync(h->staging, pos, 3 * h->N * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (!dev && cudaStreamSynchronize(s) != cudaSuccess) return WMCD_ECUDA;
+    cudaMemsetAsync(h->v.img, 0, 3 * h->N * sizeof(int), s);
+    k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->staging, h->N);
+    launch_cl_rebuild(h->v, s, nullptr);
+    return last_cuda_status();
+}
+
+extern "C" int wmcd_stats(wmcd_handle* H, wmcd_stats_t* out, void* stream) {
+    if (!H || !out) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long c[C_NCTR];
+    int err = 0;
+    cudaMemcpyAsync(c, h->v.ctr, sizeof c, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&err, h->v.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return WMCD_ECUDA;
+    std::memset(out, 0, sizeof *out);
+    for (int l = 0; l < kMaxLayers; l++) {
+        out->attempts[l] = (int64_t)c[C_ATT + l];
+        out->accepts[l] = (int64_t)c[C_ACC + l];
+        out->deferred[l] = (int64_t)c[C_DEF + l];
+    }
+    out->pw_attempts = (int64_t)c[C_PWATT];
+    out->pw_accepts = (int64_t)c[C_PWACC];
+    out->bead_updates = (int64_t)c[C_BU];
+    out->accepted_total = (int64_t)c[C_ACCTOT];
+    out->rechecks = (int64_t)c[C_RECHECK];
+    out->partner_evals = (int64_t)c[C_PARTNER];
+    out->sim_time = (double)out->accepted_total * h->dt_move;
+    out->sweeps = (int64_t)h->sweep;
+    out->n_layers = h->nL;
+    out->dt_move = h->dt_move;
+    out->p_fourier = h->p_fourier;
+    out->error_flags = err;
+    if (err & E_WALK) return WMCD_ETIMEOUT;
+    if (err & E_NONFINITE) return WMCD_ESTATE;
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_trace(wmcd_handle* H, int layer, uint8_t* out, int32_t* n, int64_t cap, int64_t* count,
+                          void* stream) {
+    if (!H || !out || !n || !count || cap < 0) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (layer == -1) {
+        int64_t m = std::min<int64_t>(std::min<int64_t>(h->tr_pw_count, cap), h->v.tr_pw_cap);
+        if (m > 0) {
+            cudaMemcpyAsync(out, h->v.tr_pw_out, m, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(n, h->v.tr_pw_mode, m * sizeof(int), cudaMemcpyDeviceToHost, s);
+        }
+        *count = h->tr_pw_count;
+        return cudaStreamSynchronize(s) == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
+    }
+    if (layer < 0 || layer >= h->nL) return WMCD_EINVAL;
+    // the number of slots of the last sweep follows from the counter stream
+    const int64_t M = h->sweep == 0 ? 0 : slot_count(h, K_COUNT, layer, h->sweep - 1, h->expect[layer]);
+    const int64_t m = std::min<int64_t>(M, cap);
+    if (m > 0) {
+        cudaMemcpyAsync(out, h->v.tr_out + h->v.layer[layer].tr_off, m, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(n, h->v.tr_n + h->v.layer[layer].tr_off, m * sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    *count = M;
+    return cudaStreamSynchronize(s) == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
+}
+
+// ---- checkpoint ----
+struct StateHeader {
+    uint64_t magic, n_beads, n_carry, sweep, pw_calls;
+};
+static const uint64_t kStateMagic = 0x574D434453543031ull;   // "WMCDST01"
+
+static int64_t carry_count(const Handle* h) {
+    int64_t c = 0;
+    for (int l = 0; l < h->nL; l++) c += (int64_t)h->v.layer[l].G * h->v.layer[l].G * h->v.layer[l].G;
+    return c;
+}
+static int64_t state_bytes(const Handle* h) {
+    return (int64_t)sizeof(StateHeader) + 3 * h->N * (int64_t)(sizeof(double) + sizeof(int)) +
+           carry_count(h) * (int64_t)sizeof(double) + kMaxLayers * (int64_t)sizeof(double) + (int64_t)sizeof(PWDev) +
+           C_NCTR * (int64_t)sizeof(unsigned long long) + (int64_t)sizeof(uint32_t);
+}
+
+extern "C" int wmcd_state_size(wmcd_handle* H, int64_t* bytes) {
+    if (!H || !bytes) return WMCD_EINVAL;
+    *bytes = state_bytes(&H->h);
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_get_state(wmcd_handle* H, void* buf, int64_t bytes, void* stream) {
+    if (!H || !buf) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    if (bytes < state_bytes(h)) return WMCD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* p = (char*)buf;
+    StateHeader hd{kStateMagic, (uint64_t)h->N, (uint64_t)carry_count(h), h->sweep, h->pw_calls};
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    k_read_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->v.img, h->v.L, 0, h->staging, h->N);
+    cudaMemcpyAsync(p, h->staging, 3 * h->N * sizeof(double), cudaMemcpyDeviceToHost, s);
+    p += 3 * h->N * sizeof(double);
+    cudaMemcpyAsync(p, h->v.img, 3 * h->N * sizeof(int), cudaMemcpyDeviceToHost, s);
+    p += 3 * h->N * sizeof(int);
+    const int64_t nc = carry_count(h);
+    if (nc) cudaMemcpyAsync(p, h->v.carry_q, nc * sizeof(double), cudaMemcpyDeviceToHost, s);
+    p += nc * sizeof(double);
+    cudaMemcpyAsync(p, h->v.carry_serial, kMaxLayers * sizeof(double), cudaMemcpyDeviceToHost, s);
+    p += kMaxLayers * sizeof(double);
+    cudaMemcpyAsync(p, h->v.pw, sizeof(PWDev), cudaMemcpyDeviceToHost, s);
+    p += sizeof(PWDev);
+    cudaMemcpyAsync(p, h->v.ctr, C_NCTR * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    p += C_NCTR * sizeof(unsigned long long);
+    cudaMemcpyAsync(p, h->v.serial_tag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    return cudaStreamSynchronize(s) == cudaSuccess ? last_cuda_status() : WMCD_ECUDA;
+}
+
+extern "C" int wmcd_set_state(wmcd_handle* H, const void* buf, int64_t bytes, void* stream) {
+    if (!H || !buf) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    if (bytes < state_bytes(h)) return WMCD_EINVAL;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kStateMagic || hd.n_beads != (uint64_t)h->N || hd.n_carry != (uint64_t)carry_count(h))
+        return WMCD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const char* p = (const char*)buf + sizeof hd;
+    cudaMemcpyAsync(h->staging, p, 3 * h->N * sizeof(double), cudaMemcpyHostToDevice, s);
+    p += 3 * h->N * sizeof(double);
+    cudaMemcpyAsync(h->v.img, p, 3 * h->N * sizeof(int), cudaMemcpyHostToDevice, s);
+    p += 3 * h->N * sizeof(int);
+    const int64_t nc = carry_count(h);
+    if (nc) cudaMemcpyAsync(h->v.carry_q, p, nc * sizeof(double), cudaMemcpyHostToDevice, s);
+    p += nc * sizeof(double);
+    cudaMemcpyAsync(h->v.carry_serial, p, kMaxLayers * sizeof(double), cudaMemcpyHostToDevice, s);
+    p += kMaxLayers * sizeof(double);
+    cudaMemcpyAsync(h->v.pw, p, sizeof(PWDev), cudaMemcpyHostToDevice, s);
+    p += sizeof(PWDev);
+    cudaMemcpyAsync(h->v.ctr, p, C_NCTR * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+    p += C_NCTR * sizeof(unsigned long long);
+    cudaMemcpyAsync(h->v.serial_tag, p, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->staging, h->N);
+    launch_cl_rebuild(h->v, s, nullptr);
+    cudaMemsetAsync(h->v.err, 0, sizeof(int), s);
+    h->sweep = hd.sweep;
+    h->pw_calls = hd.pw_calls;
+    return cudaStreamSynchronize(s) == cudaSuccess ? last_cuda_status() : WMCD_ECUDA;
+}
+
+extern "C" int wmcd_profile(wmcd_handle* H, int enable) {
+    if (!H) return WMCD_EINVAL;
+    H->h.prof = enable != 0;
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_kernel_times(wmcd_handle* H, int64_t* launches, double* ms, int n_classes, void* stream) {
+    if (!H || n_classes < 0) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return WMCD_ECUDA;
+    prof_harvest(h);
+    for (int c = 0; c < n_classes && c < 8; c++) {
+        if (launches) launches[c] = h->prof_launches[c];
+        if (ms) ms[c] = h->prof_ms[c];
+        h->prof_launches[c] = 0;
+        h->prof_ms[c] = 0.0;
+    }
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_device_bytes(wmcd_handle* H, int64_t* bytes) {
+    if (!H || !bytes) return WMCD_EINVAL;
+    *bytes = (int64_t)H->h.bytes;
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_destroy(wmcd_handle* H) {
+    if (!H) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaDeviceSynchronize();
+    for (auto& u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    cudaGetLastError();
+    delete H;
+    return WMCD_OK;
+}
+
+extern "C" const char* wmcd_strerror(int status) {
+    switch (status) {
+        case WMCD_OK: return "ok";
+        case WMCD_EINVAL: return "invalid argument or parameter";
+        case WMCD_ENOMEM: return "out of memory";
+        case WMCD_ECUDA: return "CUDA runtime error";
+        case WMCD_ETIMEOUT: return "a bounded device-side wait or list walk gave up";
+        case WMCD_ESTATE: return "non-finite or out-of-box positions detected";
+        default: return "unknown status";
+    }
+}

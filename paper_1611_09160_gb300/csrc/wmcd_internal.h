@@ -1,0 +1,125 @@
+// Internal layout of a simulation's device state and the kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "wmcd_device.cuh"
+
+namespace wmcd {
+
+// One bead record: 32 bytes, so a gather of a bead is one sector. `next` links the bead into
+// the list of its fine cell; `mark` tags membership of the support of the current serial move.
+struct __align__(32) Bead {
+    double x, y, z;
+    int next;
+    uint32_t mark;
+};
+static_assert(sizeof(Bead) == 32, "bead record must be 32 bytes");
+
+constexpr int kMaxLayers = 16;
+constexpr int kNCap = 64;          // largest support of a concurrent (warp) move
+constexpr int kWarpsPerBlock = 4;  // concurrent kernel: one warp per queue
+constexpr int kSerialThreads = 512;
+constexpr int kMaxWalk = 1 << 22;  // bound on list-walk iterations inside one move
+
+enum Outcome { ACCEPT = 1, REJECT = 2, DEFER = 3 };
+
+// device counters
+enum Ctr {
+    C_ATT = 0, C_ACC = 16, C_DEF = 32, C_PWATT = 48, C_PWACC = 49, C_BU = 50, C_ACCTOT = 51, C_RECHECK = 52,
+    C_PARTNER = 53, C_NCTR = 64
+};
+// device error bits
+enum Err { E_WALK = 1, E_SCRATCH = 2, E_NONFINITE = 4 };
+
+struct LayerDev {
+    double lo, hi, ilo3, ihi3;   // band [lo, hi) and its inverse cubes
+    double invG;                 // G / L
+    int G;                       // coarse cells per axis, 0 = serial layer
+    int carry_off;               // offset of this layer's per-cell carries
+    int64_t tr_off;              // offset of this layer's trace
+};
+
+struct PWDev {
+    int lv[3];
+    int null_move;               // k = 0
+    int accept;
+    int mode_packed;
+    double AF, phi, e[3];
+    double reach;                // partner search reach rc + 2 |A_F|
+    int carry, carry_l[3];       // recycled |k| after a rejection
+};
+
+struct SimView {
+    // beads and cell list
+    Bead* bead;
+    int* prev;
+    int* img;                    // 3 per bead
+    uint8_t* bnext;              // bead i bonded to i + 1
+    int* head;                   // Gf^3 fine cells, -1 = empty
+    int64_t N;
+    double L, halfL, invf;
+    int Gf, K, n_cap, precision;
+    double A0, kT, r_reach, rc;
+    Pot pot;
+    uint32_t k0, k1;
+    int nL;
+    LayerDev layer[kMaxLayers];
+    // schedule scratch (sized for the largest layer)
+    double* slot_lam;
+    int* slot_bead;
+    int* slot_key;
+    int* q_count;
+    int* q_start;
+    int* q_fill;
+    int* q_slots;
+    uint8_t* defer;
+    int* serial_list;
+    int* serial_count;
+    double* carry_q;
+    double* carry_serial;
+    // trace of the last sweep
+    uint8_t* tr_out;
+    int* tr_n;
+    uint8_t* tr_pw_out;
+    int* tr_pw_mode;
+    int* tr_pw_count;
+    int tr_pw_cap;
+    // counters and errors
+    unsigned long long* ctr;
+    int* err;
+    // serial-phase scratch (n up to N)
+    int* s_ids;
+    double* s_d;                 // 4 per member: offset from the centre and its square
+    double* s_new;               // 3 per member: new wrapped position
+    int* s_img;                  // per member: packed image change
+    int* s_slot;                 // per bead: index in the support of the current serial move
+    int* s_changed;              // members whose fine cell changes
+    uint32_t* serial_tag;
+    // plane waves
+    PWDev* pw;
+    double* pw_new;              // 3 per bead
+    int* pw_imgd;                // per bead packed image change
+    double* pw_part;             // per-block partial sums
+    int* pw_rebuild;             // set by the commit when beads moved: the cell list is rebuilt
+    int pw_blocks;
+    const int* modes;            // 3 per mode
+    const double* mode_cdf;
+    int n_modes;
+};
+
+// packed image change: three 2-bit fields holding -1, 0, +1 (as 0, 1, 2)
+WMCD_HD int pack_img(int dx, int dy, int dz) { return (dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4); }
+WMCD_HD void unpack_img(int p, int* d) { d[0] = (p & 3) - 1; d[1] = ((p >> 2) & 3) - 1; d[2] = ((p >> 4) & 3) - 1; }
+
+// ---- launchers (wmcd_kernels.cu) ----
+void launch_cl_rebuild(const SimView& v, cudaStream_t s, const int* flag);
+void launch_slots(const SimView& v, int l, uint64_t sweep, int M, cudaStream_t s);
+void launch_bucket(const SimView& v, int l, int M, cudaStream_t s);
+void launch_colour(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s);
+void launch_defer_compact(const SimView& v, int M, cudaStream_t s);
+void launch_serial(const SimView& v, int l, uint64_t sweep, int use_list, int M, cudaStream_t s);
+void launch_planewave(const SimView& v, int kmode, int kdir, int kacc, uint64_t ctr, int m, int trace_index,
+                      cudaStream_t s);
+void launch_check_positions(const SimView& v, cudaStream_t s);
+
+}  // namespace wmcd

@@ -1,0 +1,1007 @@
+// WMCD kernels for sm_103a: cell list, slot generation and bucketing, the concurrent
+// (one warp per queue) wavelet kernel, the serial wavelet kernel and the plane-wave kernels.
+//
+// Nothing here is a dense contraction, so there are no tensor-core paths: the work is
+// gathers of 32-byte bead records through per-cell linked lists, pair energies and
+// warp / block reductions. See the host file for the order of launches in a sweep.
+#include <algorithm>
+#include <cfloat>
+#include "wmcd_internal.h"
+
+namespace wmcd {
+
+__device__ __forceinline__ void set_err(const SimView& v, int bit) { atomicOr(v.err, bit); }
+
+__device__ __forceinline__ int cell_lin(const SimView& v, double x, double y, double z) {
+    return fine_cell(x, v.invf, v.Gf) + v.Gf * (fine_cell(y, v.invf, v.Gf) + v.Gf * fine_cell(z, v.invf, v.Gf));
+}
+__device__ __forceinline__ int wrapi(int c, int G) { c %= G; return c < 0 ? c + G : c; }
+
+// ======================================================================================
+// Cell list: per fine cell a singly linked list through Bead::next plus prev[] for O(1)
+// removal. Built in canonical order (ascending bead id within a cell) so runs repeat.
+// ======================================================================================
+__global__ void k_cl_clear(SimView v, const int* flag) {
+    if (flag && !*flag) return;
+    int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        v.head[c] = -1;
+}
+__global__ void k_cl_insert(SimView v, const int* flag) {
+    if (flag && !*flag) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
+        Bead b = v.bead[i];
+        if (!(b.x >= 0.0 && b.x < v.L && b.y >= 0.0 && b.y < v.L && b.z >= 0.0 && b.z < v.L)) set_err(v, E_NONFINITE);
+        int c = cell_lin(v, b.x, b.y, b.z);
+        int old = atomicExch(&v.head[c], (int)i);
+        v.bead[i].next = old;
+    }
+}
+__global__ void k_cl_canon(SimView v, const int* flag) {
+    if (flag && !*flag) return;
+    int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        int ids[32];
+        int n = 0, p = v.head[c];
+        bool small = true;
+        while (p >= 0) {
+            if (n < 32) ids[n] = p;
+            n++;
+            if (n > 32) small = false;
+            if (n > kMaxWalk) { set_err(v, E_WALK); break; }
+            p = v.bead[p].next;
+        }
+        if (n == 0) continue;
+        if (small) {
+            for (int a = 1; a < n; a++) {      // insertion sort by bead id
+                int x = ids[a], b = a - 1;
+                while (b >= 0 && ids[b] > x) { ids[b + 1] = ids[b]; b--; }
+                ids[b + 1] = x;
+            }
+            v.head[c] = ids[0];
+            for (int a = 0; a < n; a++) {
+                v.bead[ids[a]].next = (a + 1 < n) ? ids[a + 1] : -1;
+                v.prev[ids[a]] = (a > 0) ? ids[a - 1] : -1;
+            }
+        } else {
+            int pr = -1;
+            for (int q = v.head[c]; q >= 0; q = v.bead[q].next) { v.prev[q] = pr; pr = q; }
+        }
+    }
+}
+void launch_cl_rebuild(const SimView& v, cudaStream_t s, const int* flag) {
+    int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
+    int bc = (int)std::min<int64_t>((nc + 255) / 256, 152 * 64);
+    int bb = (int)std::min<int64_t>((v.N + 255) / 256, 152 * 64);
+    k_cl_clear<<<bc, 256, 0, s>>>(v, flag);
+    k_cl_insert<<<bb, 256, 0, s>>>(v, flag);
+    k_cl_canon<<<bc, 256, 0, s>>>(v, flag);
+}
+
+__global__ void k_check_positions(SimView v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
+        Bead b = v.bead[i];
+        if (!(b.x >= 0.0 && b.x < v.L && b.y >= 0.0 && b.y < v.L && b.z >= 0.0 && b.z < v.L)) set_err(v, E_NONFINITE);
+    }
+}
+void launch_check_positions(const SimView& v, cudaStream_t s) {
+    int bb = (int)std::min<int64_t>((v.N + 255) / 256, 152 * 16);
+    k_check_positions<<<bb, 256, 0, s>>>(v);
+}
+
+// ======================================================================================
+// Slots of a layer: scale in the band (Eq. 32 restricted to [lo, hi), inverse transform of
+// Appendix D) and the picked bead; then bucketing by coarse cell in colour-major order.
+// ======================================================================================
+__global__ void k_slots(SimView v, int l, uint64_t sweep, int M) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const LayerDev& Ly = v.layer[l];
+    u4 w = draw(v.k0, v.k1, K_SLOT, l, sweep, (uint32_t)j, 0);
+    double u = u53(w.x, w.y);
+    double wv = sub(Ly.ilo3, mul(u, sub(Ly.ilo3, Ly.ihi3)));
+    v.slot_lam[j] = inv_cbrt_band(wv, Ly.lo);
+    v.slot_bead[j] = (int)pick(w.z, w.w, v.N);
+    v.tr_out[Ly.tr_off + j] = 0;
+    v.tr_n[Ly.tr_off + j] = 0;
+}
+void launch_slots(const SimView& v, int l, uint64_t sweep, int M, cudaStream_t s) {
+    k_slots<<<(M + 255) / 256, 256, 0, s>>>(v, l, sweep, M);
+}
+
+__global__ void k_bucket_count(SimView v, int l, int M) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const LayerDev& Ly = v.layer[l];
+    const int G = Ly.G, K = v.K, Q = G / K;
+    Bead b = v.bead[v.slot_bead[j]];
+    int c[3];
+    double xs[3] = {b.x, b.y, b.z};
+    for (int a = 0; a < 3; a++) {
+        double f = floor(mul(xs[a], Ly.invG));
+        int ci = (int)f;
+        if (f < 0.0) ci = 0;
+        if (ci >= G) ci = G - 1;
+        c[a] = ci;
+    }
+    int colour = (c[0] % K) + K * ((c[1] % K) + K * (c[2] % K));
+    int q = (c[0] / K) + Q * ((c[1] / K) + Q * (c[2] / K));
+    int key = colour * Q * Q * Q + q;
+    v.slot_key[j] = key;
+    atomicAdd(&v.q_count[key], 1);
+}
+// exclusive scan of n ints by one block (n up to a few million)
+__global__ void k_scan_single(const int* in, int* out, int n) {
+    __shared__ int part[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        int i = base + threadIdx.x;
+        int x = i < n ? in[i] : 0;
+        part[threadIdx.x] = x;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int y = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (i < n) out[i] = carry + part[threadIdx.x] - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+}
+__global__ void k_bucket_scatter(SimView v, int M) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    int key = v.slot_key[j];
+    int pos = v.q_start[key] + atomicAdd(&v.q_fill[key], 1);
+    v.q_slots[pos] = j;
+}
+// slots of one queue in ascending slot id (the order of the sequential schedule)
+__global__ void k_bucket_sort(SimView v, int nkeys) {
+    int key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= nkeys) return;
+    int s = v.q_start[key], n = v.q_count[key];
+    int* a = v.q_slots + s;
+    for (int i = 1; i < n; i++) {
+        int x = a[i], b = i - 1;
+        while (b >= 0 && a[b] > x) { a[b + 1] = a[b]; b--; }
+        a[b + 1] = x;
+    }
+}
+void launch_bucket(const SimView& v, int l, int M, cudaStream_t s) {
+    const int G = v.layer[l].G;
+    const int nkeys = G * G * G;
+    cudaMemsetAsync(v.q_count, 0, sizeof(int) * nkeys, s);
+    cudaMemsetAsync(v.q_fill, 0, sizeof(int) * nkeys, s);
+    cudaMemsetAsync(v.defer, 0, (size_t)M, s);
+    k_bucket_count<<<(M + 255) / 256, 256, 0, s>>>(v, l, M);
+    k_scan_single<<<1, 1024, 0, s>>>(v.q_count, v.q_start, nkeys);
+    k_bucket_scatter<<<(M + 255) / 256, 256, 0, s>>>(v, M);
+    k_bucket_sort<<<(nkeys + 127) / 128, 128, 0, s>>>(v, nkeys);
+}
+
+// deferred slots in schedule order -> serial list
+__global__ void k_defer_compact(SimView v, int M) {
+    __shared__ int part[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < M; base += 1024) {
+        int i = base + threadIdx.x;
+        int x = (i < M && v.defer[i]) ? 1 : 0;
+        part[threadIdx.x] = x;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int y = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (x) v.serial_list[carry + part[threadIdx.x] - 1] = v.q_slots[i];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *v.serial_count = carry;
+}
+void launch_defer_compact(const SimView& v, int M, cudaStream_t s) {
+    k_defer_compact<<<1, 1024, 0, s>>>(v, M);
+}
+
+}  // namespace wmcd
+
+namespace wmcd {
+
+// ======================================================================================
+// Concurrent wavelet moves: one warp per queue (coarse cell) of one colour.
+// ======================================================================================
+struct WarpSmem {
+    int ids[kNCap];          // support, in gather order
+    double d[kNCap][4];      // minimum-image offset from the centre, and its square
+    double op[kNCap][3];     // old positions
+    double np[kNCap][3];     // new (wrapped) positions
+    double nu[kNCap][3];     // new unwrapped positions (old + delta)
+    int dimg[kNCap];         // packed image change
+    int sid[kNCap];          // support ids ascending
+    int wpre[kNCap + 1];     // prefix of partner-search cells per member
+    int wbox[kNCap][6];      // partner-search cell box per member: c0[3], nc[3]
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ int warp_sum_i(int x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ bool sorted_has(const int* a, int n, int x) {
+    int lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int m = (lo + hi) >> 1;
+        if (a[m] == x) return true;
+        if (a[m] < x) lo = m + 1; else hi = m - 1;
+    }
+    return false;
+}
+
+// Uniform point of the unit ball by rejection (Appendix D): attempt a uses counter attempt a;
+// the warp tries 32 attempts at once and takes the first accepted one, which is what a
+// sequential loop over the attempts would return.
+__device__ void warp_ball_point(const SimView& v, uint32_t kind, int l, uint64_t sweep, uint32_t j, bool nonzero,
+                                int lane, double V[3]) {
+    for (int base = 0; base < 64; base += 32) {
+        u4 w = draw(v.k0, v.k1, kind, l, sweep, j, (uint32_t)(base + lane));
+        double x = sym(w.x), y = sym(w.y), z = sym(w.z);
+        double q = norm2(x, y, z);
+        unsigned ok = __ballot_sync(0xffffffffu, q <= 1.0 && (!nonzero || q > 0.0));
+        if (ok) {
+            int src = __ffs(ok) - 1;
+            V[0] = __shfl_sync(0xffffffffu, x, src);
+            V[1] = __shfl_sync(0xffffffffu, y, src);
+            V[2] = __shfl_sync(0xffffffffu, z, src);
+            return;
+        }
+    }
+    V[0] = 0.0; V[1] = 0.0; V[2] = nonzero ? 1.0 : 0.0;
+}
+
+// cell box [floor((lo) invf), floor((hi) invf)] per axis, at most Gf cells
+__device__ __forceinline__ void cell_box(const SimView& v, const double lo[3], const double hi[3], int c0[3], int nc[3]) {
+    for (int a = 0; a < 3; a++) {
+        int t0 = (int)floor(mul(lo[a], v.invf));
+        int t1 = (int)floor(mul(hi[a], v.invf));
+        c0[a] = t0;
+        nc[a] = min(t1 - t0 + 1, v.Gf);
+    }
+}
+__device__ __forceinline__ int box_cell(const SimView& v, const int c0[3], const int nc[3], int k) {
+    int kx = k % nc[0], ky = (k / nc[0]) % nc[1], kz = k / (nc[0] * nc[1]);
+    return wrapi(c0[0] + kx, v.Gf) + v.Gf * (wrapi(c0[1] + ky, v.Gf) + v.Gf * wrapi(c0[2] + kz, v.Gf));
+}
+
+template <int PREC>
+__device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i, double lam, uint64_t sweep,
+                            const int64_t rlo[3], const int64_t rhi[3], int lane, int* n_out, int* pe_out) {
+    const unsigned FULL = 0xffffffffu;
+    const double L = v.L, hL = v.halfL;
+    // centre b = r_i + lam V (Appendix D), wrapped into the box
+    const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
+    double V[3], b[3];
+    warp_ball_point(v, K_VB, l, sweep, (uint32_t)j, false, lane, V);
+    for (int a = 0; a < 3; a++) b[a] = wrap(add(ri[a], mul(lam, V[a])), L, nullptr);
+    // the influence ball must lie in fine cells wholly inside the queue's region
+    const double R = add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
+    for (int a = 0; a < 3; a++) {
+        int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
+        int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
+        if (!range_inside(t0, t1, rlo[a], rhi[a], v.Gf)) return DEFER;
+    }
+    // gather the support: beads strictly inside the ball (one image each, lambda <= L/2)
+    const double lam2 = mul(lam, lam);
+    int c0[3], nc[3];
+    {
+        const double eps = 1e-9;
+        double lo[3] = {sub(b[0], lam + eps), sub(b[1], lam + eps), sub(b[2], lam + eps)};
+        double hi[3] = {add(b[0], lam + eps), add(b[1], lam + eps), add(b[2], lam + eps)};
+        cell_box(v, lo, hi, c0, nc);
+    }
+    const int ncell = nc[0] * nc[1] * nc[2];
+    int n = 0;
+    {
+        int k = lane, ptr = -1, guard = 0;
+        while (ptr < 0 && k < ncell) { ptr = v.head[box_cell(v, c0, nc, k)]; if (ptr < 0) k += 32; }
+        while (true) {
+            bool has = ptr >= 0;
+            if (!__any_sync(FULL, has)) break;
+            bool in = false;
+            int nxt = -1;
+            double d[3] = {0, 0, 0}, d2 = 0, ox = 0, oy = 0, oz = 0;
+            if (has) {
+                Bead bb = v.bead[ptr];
+                ox = bb.x; oy = bb.y; oz = bb.z;
+                d[0] = mi(sub(bb.x, b[0]), L, hL); d[1] = mi(sub(bb.y, b[1]), L, hL); d[2] = mi(sub(bb.z, b[2]), L, hL);
+                d2 = norm2(d[0], d[1], d[2]);
+                in = d2 < lam2;
+                nxt = bb.next;
+            }
+            unsigned m = __ballot_sync(FULL, in);
+            int slot = n + __popc(m & ((1u << lane) - 1u));
+            if (in && slot < kNCap) {
+                sm.ids[slot] = ptr;
+                sm.d[slot][0] = d[0]; sm.d[slot][1] = d[1]; sm.d[slot][2] = d[2]; sm.d[slot][3] = d2;
+                sm.op[slot][0] = ox; sm.op[slot][1] = oy; sm.op[slot][2] = oz;
+            }
+            n += __popc(m);
+            if (has) {
+                ptr = nxt;
+                if (ptr < 0) { k += 32; while (ptr < 0 && k < ncell) { ptr = v.head[box_cell(v, c0, nc, k)]; if (ptr < 0) k += 32; } }
+            }
+            if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
+        }
+    }
+    *n_out = n;
+    if (n > v.n_cap) return DEFER;
+    __syncwarp();
+    if (n == 0) return ACCEPT;           // no bead moves; dU = 0 passes the Metropolis test
+    // polarisation and amplitude A_w = A0 lam / sqrt(n) (Eq. 29)
+    double p[3];
+    warp_ball_point(v, K_VP, l, sweep, (uint32_t)j, true, lane, p);
+    {
+        double q = norm2(p[0], p[1], p[2]), r = sqr_t(q);
+        p[0] = dvd(p[0], r); p[1] = dvd(p[1], r); p[2] = dvd(p[2], r);
+    }
+    const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+    for (int k = lane; k < n; k += 32) {
+        double dl[3];
+        if (PREC == 0) wavelet_disp64(sm.d[k], sm.d[k][3], lam, Aw, p, dl);
+        else wavelet_disp32(sm.d[k], lam, Aw, p, dl);
+        int im[3] = {0, 0, 0};
+        for (int a = 0; a < 3; a++) {
+            double u = add(sm.op[k][a], dl[a]);
+            sm.nu[k][a] = u;
+            sm.np[k][a] = wrap(u, L, &im[a]);
+        }
+        sm.dimg[k] = pack_img(im[0], im[1], im[2]);
+        // rank of this member by bead id
+        int me = sm.ids[k], r = 0;
+        for (int t = 0; t < n; t++) r += sm.ids[t] < me;
+        sm.sid[r] = me;
+    }
+    __syncwarp();
+    // bonded partners outside the support must lie in the region
+    bool bad = false;
+    for (int k = lane; k < n; k += 32) {
+        int m = sm.ids[k];
+        for (int e = 0; e < 2; e++) {
+            int q = e ? m + 1 : m - 1;
+            if (q < 0 || q >= v.N) continue;
+            if (!(e ? v.bnext[m] : v.bnext[q])) continue;
+            if (sorted_has(sm.sid, n, q)) continue;
+            Bead bq = v.bead[q];
+            int64_t cq[3] = {fine_cell(bq.x, v.invf, v.Gf), fine_cell(bq.y, v.invf, v.Gf), fine_cell(bq.z, v.invf, v.Gf)};
+            for (int a = 0; a < 3; a++) if (!range_inside(cq[a], cq[a], rlo[a], rhi[a], v.Gf)) bad = true;
+        }
+    }
+    if (__any_sync(FULL, bad)) return DEFER;
+    // energy change (Eqs. 1, 2): external, support-support pairs, bonds to outside, WCA to outside
+    const Pot& P = v.pot;
+    double dU = 0.0;
+    int pe = 0;
+    for (int k = lane; k < n; k += 32) {
+        dU += U_ext(P, sm.np[k][0], sm.np[k][1], sm.np[k][2]) - U_ext(P, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
+        int m = sm.ids[k];
+        for (int e = 0; e < 2; e++) {
+            int q = e ? m + 1 : m - 1;
+            if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q]) || sorted_has(sm.sid, n, q)) continue;
+            Bead bq = v.bead[q];
+            double r2n = norm2(mi(sm.np[k][0] - bq.x, L, hL), mi(sm.np[k][1] - bq.y, L, hL), mi(sm.np[k][2] - bq.z, L, hL));
+            double r2o = norm2(mi(sm.op[k][0] - bq.x, L, hL), mi(sm.op[k][1] - bq.y, L, hL), mi(sm.op[k][2] - bq.z, L, hL));
+            dU += U_bond(P, r2n) - U_bond(P, r2o);
+        }
+    }
+    const int npairs = n * (n - 1) / 2;
+    for (int t = lane; t < npairs; t += 32) {
+        // pair t -> (a, b), a < b
+        int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while (a * (a + 1) / 2 > t) a--;
+        while ((a + 1) * (a + 2) / 2 <= t) a++;
+        int bb = t - a * (a + 1) / 2;      // bb < a + 1
+        int k1 = bb, k2 = a + 1;
+        int m1 = sm.ids[k1], m2 = sm.ids[k2];
+        double r2n = norm2(mi(sm.np[k1][0] - sm.np[k2][0], L, hL), mi(sm.np[k1][1] - sm.np[k2][1], L, hL),
+                           mi(sm.np[k1][2] - sm.np[k2][2], L, hL));
+        double r2o = norm2(mi(sm.op[k1][0] - sm.op[k2][0], L, hL), mi(sm.op[k1][1] - sm.op[k2][1], L, hL),
+                           mi(sm.op[k1][2] - sm.op[k2][2], L, hL));
+        double u = U_wca(P, r2n) - U_wca(P, r2o);
+        int lo_ = min(m1, m2), hi_ = max(m1, m2);
+        if (hi_ == lo_ + 1 && v.bnext[lo_]) u += U_bond(P, r2n) - U_bond(P, r2o);
+        dU += u;
+    }
+    if (P.eps != 0.0) {
+        // partner-search boxes: [min(old, new) - rc, max(old, new) + rc] per member
+        for (int k = lane; k < n; k += 32) {
+            double lo[3], hi[3];
+            for (int a = 0; a < 3; a++) {
+                double o = sm.op[k][a], u = sm.nu[k][a];
+                lo[a] = sub(fmin(o, u), v.rc + 1e-9);
+                hi[a] = add(fmax(o, u), v.rc + 1e-9);
+            }
+            int c0b[3], ncb[3];
+            cell_box(v, lo, hi, c0b, ncb);
+            for (int a = 0; a < 3; a++) { sm.wbox[k][a] = c0b[a]; sm.wbox[k][3 + a] = ncb[a]; }
+            sm.wpre[k + 1] = ncb[0] * ncb[1] * ncb[2];
+        }
+        __syncwarp();
+        if (lane == 0) { sm.wpre[0] = 0; for (int k = 0; k < n; k++) sm.wpre[k + 1] += sm.wpre[k]; }
+        __syncwarp();
+        const int total = sm.wpre[n];
+        for (int w = lane; w < total; w += 32) {
+            int k = 0;
+            while (sm.wpre[k + 1] <= w) k++;
+            const int c0b[3] = {sm.wbox[k][0], sm.wbox[k][1], sm.wbox[k][2]};
+            const int ncb[3] = {sm.wbox[k][3], sm.wbox[k][4], sm.wbox[k][5]};
+            int cell = box_cell(v, c0b, ncb, w - sm.wpre[k]);
+            const int m = sm.ids[k];
+            int guard = 0;
+            for (int q = v.head[cell]; q >= 0;) {
+                Bead bq = v.bead[q];
+                if (q != m && !sorted_has(sm.sid, n, q)) {
+                    double r2n = norm2(mi(sm.np[k][0] - bq.x, L, hL), mi(sm.np[k][1] - bq.y, L, hL), mi(sm.np[k][2] - bq.z, L, hL));
+                    double r2o = norm2(mi(sm.op[k][0] - bq.x, L, hL), mi(sm.op[k][1] - bq.y, L, hL), mi(sm.op[k][2] - bq.z, L, hL));
+                    if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); pe++; }
+                }
+                q = bq.next;
+                if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+            }
+        }
+    }
+    // every lane takes lane 0's sum: a butterfly leaves lanes with differently rounded totals
+    dU = __shfl_sync(FULL, warp_sum(dU), 0);
+    *pe_out += warp_sum_i(pe);
+    // Metropolis (Eq. 20): accept iff dU <= -kT ln(1 - u)
+    u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+    const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
+    const bool acc = dU <= thr;
+    if (!acc) return REJECT;
+    // commit: positions, image counters, then cell-list moves (lane 0, in support order)
+    for (int k = lane; k < n; k += 32) {
+        int m = sm.ids[k];
+        v.bead[m].x = sm.np[k][0]; v.bead[m].y = sm.np[k][1]; v.bead[m].z = sm.np[k][2];
+        if (sm.dimg[k] != pack_img(0, 0, 0)) {
+            int dd[3];
+            unpack_img(sm.dimg[k], dd);
+            v.img[3 * m] += dd[0]; v.img[3 * m + 1] += dd[1]; v.img[3 * m + 2] += dd[2];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int k = 0; k < n; k++) {
+            int m = sm.ids[k];
+            int oc = cell_lin(v, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
+            int ncl = cell_lin(v, sm.np[k][0], sm.np[k][1], sm.np[k][2]);
+            if (oc == ncl) continue;
+            int pr = v.prev[m], nx = v.bead[m].next;
+            if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+            if (nx >= 0) v.prev[nx] = pr;
+            int h = v.head[ncl];
+            v.bead[m].next = h;
+            v.prev[m] = -1;
+            if (h >= 0) v.prev[h] = m;
+            v.head[ncl] = m;
+        }
+    }
+    __syncwarp();
+    return ACCEPT;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l, int colour, uint64_t sweep) {
+    __shared__ WarpSmem sm_all[kWarpsPerBlock];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem& sm = sm_all[wib];
+    const LayerDev& Ly = v.layer[l];
+    const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
+    const int q = blockIdx.x * kWarpsPerBlock + wib;
+    if (q >= nq) return;
+    const int key = colour * nq + q;
+    const int start = v.q_start[key], cnt = v.q_count[key];
+    if (cnt == 0) return;
+    const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
+    int64_t rlo[3], rhi[3];
+    for (int a = 0; a < 3; a++) {
+        rlo[a] = ceildiv((2 * (int64_t)c[a] - (K - 1)) * v.Gf, 2 * (int64_t)G);
+        rhi[a] = floordiv((2 * (int64_t)c[a] + 2 + (K - 1)) * v.Gf, 2 * (int64_t)G) - 1;
+    }
+    const int cell = c[0] + G * (c[1] + G * c[2]);
+    double carry = v.carry_q[Ly.carry_off + cell];
+    int att = 0, acc = 0, def = 0, pe = 0;
+    long long bu = 0;
+    for (int t = 0; t < cnt; t++) {
+        const int j = v.q_slots[start + t];
+        const double lam = carry > 0.0 ? carry : v.slot_lam[j];
+        const int i = v.slot_bead[j];
+        int n = 0;
+        int r = warp_attempt<PREC>(v, sm, l, j, i, lam, sweep, rlo, rhi, lane, &n, &pe);
+        __syncwarp();
+        if (r == DEFER) {
+            if (lane == 0) v.defer[start + t] = 1;
+            def++;
+            continue;
+        }
+        att++;
+        bu += n;
+        if (r == ACCEPT) acc++;
+        if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
+        carry = (r == ACCEPT) ? 0.0 : lam;
+    }
+    if (lane == 0) {
+        v.carry_q[Ly.carry_off + cell] = carry;
+        atomicAdd(&v.ctr[C_ATT + l], (unsigned long long)att);
+        atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc);
+        atomicAdd(&v.ctr[C_DEF + l], (unsigned long long)def);
+        atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
+        atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+        atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
+    }
+}
+void launch_colour(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s) {
+    const int G = v.layer[l].G, Q = G / v.K, nq = Q * Q * Q;
+    const int blocks = (nq + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (v.precision == 0) k_colour<0><<<blocks, kWarpsPerBlock * 32, 0, s>>>(v, l, colour, sweep);
+    else k_colour<1><<<blocks, kWarpsPerBlock * 32, 0, s>>>(v, l, colour, sweep);
+}
+
+}  // namespace wmcd
+
+namespace wmcd {
+
+// ======================================================================================
+// Serial wavelet moves: one block runs the layer's deferred slots (schedule order), or
+// every slot of a serial layer, one move after another. Supports of any size.
+// ======================================================================================
+template <int PREC>
+__global__ void __launch_bounds__(kSerialThreads) k_serial(SimView v, int l, uint64_t sweep, int use_list, int M) {
+    __shared__ double sh_b[3], sh_p[3], sh_carry;
+    __shared__ double sh_red[kSerialThreads / 32];
+    __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3];
+    __shared__ uint32_t sh_tag;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const LayerDev& Ly = v.layer[l];
+    const double L = v.L, hL = v.halfL;
+    const Pot& P = v.pot;
+    const int count = use_list ? *v.serial_count : M;
+    if (tid == 0) sh_carry = v.carry_serial[l];
+    __syncthreads();
+    long long att = 0, acc_n = 0, bu = 0, pe = 0;
+    for (int t = 0; t < count; t++) {
+        const int j = use_list ? v.serial_list[t] : t;
+        const double lam = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
+        const int i = v.slot_bead[j];
+        const double lam2 = mul(lam, lam);
+        if (tid == 0) {
+            double V[3] = {0.0, 0.0, 0.0};
+            for (uint32_t a = 0; a < 64; a++) {
+                u4 w = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
+                double x = sym(w.x), y = sym(w.y), z = sym(w.z);
+                if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+            }
+            const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
+            for (int a = 0; a < 3; a++) sh_b[a] = wrap(add(ri[a], mul(lam, V[a])), L, nullptr);
+            double p[3] = {0.0, 0.0, 1.0};
+            for (uint32_t a = 0; a < 64; a++) {
+                u4 w = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
+                double x = sym(w.x), y = sym(w.y), z = sym(w.z), q = norm2(x, y, z);
+                if (q <= 1.0 && q > 0.0) { p[0] = x; p[1] = y; p[2] = z; break; }
+            }
+            double r = sqr_t(norm2(p[0], p[1], p[2]));
+            for (int a = 0; a < 3; a++) sh_p[a] = dvd(p[a], r);
+            const double eps = 1e-9;
+            int64_t ncell = 1;
+            for (int a = 0; a < 3; a++) {
+                int t0 = (int)floor(mul(sub(sh_b[a], lam + eps), v.invf));
+                int t1 = (int)floor(mul(add(sh_b[a], lam + eps), v.invf));
+                sh_c0[a] = t0;
+                sh_nc[a] = min(t1 - t0 + 1, v.Gf);
+                ncell *= sh_nc[a];
+            }
+            sh_brute = ncell > v.N;
+            sh_n = 0;
+            sh_nch = 0;
+            uint32_t tag = *v.serial_tag + 1u;
+            if (tag == 0u) tag = 1u;
+            *v.serial_tag = tag;
+            sh_tag = tag;
+        }
+        __syncthreads();
+        const double b[3] = {sh_b[0], sh_b[1], sh_b[2]};
+        // gather the support
+        auto consider = [&](int m, const Bead& bb) {
+            double d0 = mi(sub(bb.x, b[0]), L, hL), d1 = mi(sub(bb.y, b[1]), L, hL), d2c = mi(sub(bb.z, b[2]), L, hL);
+            double d2 = norm2(d0, d1, d2c);
+            if (d2 < lam2) {
+                int idx = atomicAdd(&sh_n, 1);
+                v.s_ids[idx] = m;
+                v.s_d[4 * idx] = d0; v.s_d[4 * idx + 1] = d1; v.s_d[4 * idx + 2] = d2c; v.s_d[4 * idx + 3] = d2;
+            }
+        };
+        if (sh_brute) {
+            for (int64_t m = tid; m < v.N; m += kSerialThreads) consider((int)m, v.bead[m]);
+        } else {
+            const int c0[3] = {sh_c0[0], sh_c0[1], sh_c0[2]}, nc[3] = {sh_nc[0], sh_nc[1], sh_nc[2]};
+            const int ncell = nc[0] * nc[1] * nc[2];
+            for (int k = tid; k < ncell; k += kSerialThreads) {
+                int kx = k % nc[0], ky = (k / nc[0]) % nc[1], kz = k / (nc[0] * nc[1]);
+                int cell = wrapi(c0[0] + kx, v.Gf) + v.Gf * (wrapi(c0[1] + ky, v.Gf) + v.Gf * wrapi(c0[2] + kz, v.Gf));
+                int guard = 0;
+                for (int q = v.head[cell]; q >= 0;) {
+                    Bead bb = v.bead[q];
+                    consider(q, bb);
+                    q = bb.next;
+                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                }
+            }
+        }
+        __syncthreads();
+        const int n = sh_n;
+        if (n == 0) {      // nothing inside: dU = 0, accepted with no motion
+            if (tid == 0) {
+                att++; acc_n++;
+                v.tr_out[Ly.tr_off + j] = (uint8_t)(1 | (use_list ? 4 : 0));
+                v.tr_n[Ly.tr_off + j] = 0;
+                sh_carry = 0.0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t tag = sh_tag;
+        const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+        const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
+        for (int k = tid; k < n; k += kSerialThreads) {
+            int m = v.s_ids[k];
+            v.bead[m].mark = tag;
+            v.s_slot[m] = k;
+            double d[3] = {v.s_d[4 * k], v.s_d[4 * k + 1], v.s_d[4 * k + 2]}, dl[3];
+            if (PREC == 0) wavelet_disp64(d, v.s_d[4 * k + 3], lam, Aw, p, dl);
+            else wavelet_disp32(d, lam, Aw, p, dl);
+            const double o[3] = {v.bead[m].x, v.bead[m].y, v.bead[m].z};
+            int im[3] = {0, 0, 0};
+            for (int a = 0; a < 3; a++) {
+                v.s_new[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+                v.s_d[4 * k + a] = dl[a];        // keep the displacement for the partner boxes
+            }
+            v.s_img[k] = pack_img(im[0], im[1], im[2]);
+        }
+        __syncthreads();
+        // energy change
+        double dU = 0.0;
+        const double ext = add(v.rc, mul(0.25, Aw)) + 1e-9;
+        for (int k = tid; k < n; k += kSerialThreads) {
+            const int m = v.s_ids[k];
+            const Bead bm = v.bead[m];
+            const double o[3] = {bm.x, bm.y, bm.z};
+            const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
+            dU += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, o[0], o[1], o[2]);
+            for (int e = 0; e < 2; e++) {
+                int q = e ? m + 1 : m - 1;
+                if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q])) continue;
+                Bead bq = v.bead[q];
+                double qn[3] = {bq.x, bq.y, bq.z};
+                if (bq.mark == tag) {
+                    if (q < m) continue;
+                    int s = v.s_slot[q];
+                    qn[0] = v.s_new[3 * s]; qn[1] = v.s_new[3 * s + 1]; qn[2] = v.s_new[3 * s + 2];
+                }
+                double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                dU += U_bond(P, r2n) - U_bond(P, r2o);
+            }
+            if (P.eps != 0.0) {
+                double lo[3], hi[3];
+                for (int a = 0; a < 3; a++) {
+                    double u = add(o[a], v.s_d[4 * k + a]);
+                    lo[a] = sub(fmin(o[a], u), ext);
+                    hi[a] = add(fmax(o[a], u), ext);
+                }
+                int c0[3], nc[3];
+                cell_box(v, lo, hi, c0, nc);
+                const int ncell = nc[0] * nc[1] * nc[2];
+                for (int kk = 0; kk < ncell; kk++) {
+                    int cell = box_cell(v, c0, nc, kk);
+                    int guard = 0;
+                    for (int q = v.head[cell]; q >= 0;) {
+                        Bead bq = v.bead[q];
+                        int nx = bq.next;
+                        if (q != m) {
+                            double qn[3] = {bq.x, bq.y, bq.z};
+                            bool member = bq.mark == tag;
+                            if (!(member && q < m)) {
+                                if (member) {
+                                    int s = v.s_slot[q];
+                                    qn[0] = v.s_new[3 * s]; qn[1] = v.s_new[3 * s + 1]; qn[2] = v.s_new[3 * s + 2];
+                                }
+                                double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                                double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                                if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); if (!member) pe++; }
+                            }
+                        }
+                        q = nx;
+                        if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                    }
+                }
+            }
+        }
+        dU = warp_sum(dU);
+        if (lane == 0) sh_red[wid] = dU;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kSerialThreads / 32; w++) s += sh_red[w];
+            u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+            const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
+            sh_acc = s <= thr;
+        }
+        __syncthreads();
+        const bool acc = sh_acc;
+        if (acc) {
+            for (int k = tid; k < n; k += kSerialThreads) {
+                const int m = v.s_ids[k];
+                const Bead bm = v.bead[m];
+                const int oc = cell_lin(v, bm.x, bm.y, bm.z);
+                const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
+                const int ncl = cell_lin(v, nw[0], nw[1], nw[2]);
+                v.bead[m].x = nw[0]; v.bead[m].y = nw[1]; v.bead[m].z = nw[2];
+                if (v.s_img[k] != pack_img(0, 0, 0)) {
+                    int dd[3];
+                    unpack_img(v.s_img[k], dd);
+                    v.img[3 * m] += dd[0]; v.img[3 * m + 1] += dd[1]; v.img[3 * m + 2] += dd[2];
+                }
+                if (oc != ncl) {
+                    int idx = atomicAdd(&sh_nch, 1);
+                    v.s_changed[3 * idx] = m; v.s_changed[3 * idx + 1] = oc; v.s_changed[3 * idx + 2] = ncl;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int c = 0; c < sh_nch; c++) {
+                int m = v.s_changed[3 * c], oc = v.s_changed[3 * c + 1], ncl = v.s_changed[3 * c + 2];
+                int pr = v.prev[m], nx = v.bead[m].next;
+                if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+                if (nx >= 0) v.prev[nx] = pr;
+                int h = v.head[ncl];
+                v.bead[m].next = h;
+                v.prev[m] = -1;
+                if (h >= 0) v.prev[h] = m;
+                v.head[ncl] = m;
+            }
+            att++;
+            bu += n;
+            if (acc) acc_n++;
+            v.tr_out[Ly.tr_off + j] = (uint8_t)((acc ? 1 : 2) | (use_list ? 4 : 0));
+            v.tr_n[Ly.tr_off + j] = n;
+            sh_carry = acc ? 0.0 : lam;
+        }
+        __syncthreads();
+    }
+    // partner counts are per thread
+    unsigned long long pe_all = (unsigned long long)pe;
+    if (pe_all) atomicAdd(&v.ctr[C_PARTNER], pe_all);
+    if (tid == 0) {
+        v.carry_serial[l] = sh_carry;
+        atomicAdd(&v.ctr[C_ATT + l], (unsigned long long)att);
+        atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc_n);
+        atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc_n);
+        atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+    }
+}
+void launch_serial(const SimView& v, int l, uint64_t sweep, int use_list, int M, cudaStream_t s) {
+    if (v.precision == 0) k_serial<0><<<1, kSerialThreads, 0, s>>>(v, l, sweep, use_list, M);
+    else k_serial<1><<<1, kSerialThreads, 0, s>>>(v, l, sweep, use_list, M);
+}
+
+}  // namespace wmcd
+
+namespace wmcd {
+
+// ======================================================================================
+// Plane-wave moves (Sec. VI, Appendix D): every bead moves by A_F cos(k.r + Phi) e.
+// setup (1 thread) -> displacements (grid) -> energy change (grid, per-block partials)
+// -> decision (1 block, fixed-order sum) -> commit (grid) -> cell-list rebuild if moved.
+// ======================================================================================
+__global__ void k_pw_setup(SimView v, int kmode, int kdir, uint64_t ctr, int m, int trace_index) {
+    PWDev& P = *v.pw;
+    u4 w1 = draw(v.k0, v.k1, (uint32_t)kmode, 0, ctr, (uint32_t)m, 0);
+    u4 w2 = draw(v.k0, v.k1, (uint32_t)kdir, 0, ctr, (uint32_t)m, 0);
+    const double u_mode = u53(w1.x, w1.y), phi = u53(w1.z, w1.w), psi = u53(w2.x, w2.y);
+    const int perm = (int)(((uint64_t)w2.z * 6u) >> 32);
+    const uint32_t signs = w2.w & 7u;
+    const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    int lv[3];
+    if (P.carry) {
+        // recycle |k| after a rejection: permute the components, flip each sign with prob 1/2
+        for (int a = 0; a < 3; a++) {
+            int x = P.carry_l[PERM[perm][a]];
+            lv[a] = ((signs >> a) & 1u) ? -x : x;
+        }
+    } else {
+        int lo = 0, hi = v.n_modes - 1;           // first mode with u < cdf
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (u_mode < v.mode_cdf[mid]) hi = mid; else lo = mid + 1; }
+        for (int a = 0; a < 3; a++) lv[a] = v.modes[3 * lo + a];
+    }
+    for (int a = 0; a < 3; a++) P.lv[a] = lv[a];
+    P.mode_packed = (lv[0] + 128) | ((lv[1] + 128) << 8) | ((lv[2] + 128) << 16);
+    P.phi = phi;
+    P.null_move = (lv[0] == 0 && lv[1] == 0 && lv[2] == 0);
+    P.accept = 0;
+    atomicAdd(&v.ctr[C_PWATT], 1ull);
+    if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_mode[trace_index] = P.mode_packed;
+    if (P.null_move) {
+        // k = 0 moves nothing and is accepted (Sec. VI.A)
+        P.accept = 1;
+        P.carry = 0;
+        atomicAdd(&v.ctr[C_PWACC], 1ull);
+        atomicAdd(&v.ctr[C_ACCTOT], 1ull);
+        if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_out[trace_index] = 1;
+        return;
+    }
+    // A_F = (2/k) sqrt(dU_est/(mu N)), dU_est/mu = M6 A0^2/(2 pi)^3 = A0^2/5 (Eq. 48)
+    const int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
+    const double lm = sqr_t((double)l2);
+    const double kmag = dvd(mul(kTwoPi, lm), v.L);
+    P.AF = dvd(mul(2.0, v.A0), mul(kmag, sqr_t(mul(5.0, (double)v.N))));
+    // polarisation e perpendicular to k: e = cos(psi) u1 + sin(psi) u2, u1 = k x z / |k x z|
+    double kh[3] = {dvd((double)lv[0], lm), dvd((double)lv[1], lm), dvd((double)lv[2], lm)}, u1[3], u2[3];
+    if (lv[0] == 0 && lv[1] == 0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
+    else {
+        double nr = sqr_t((double)(lv[0] * lv[0] + lv[1] * lv[1]));
+        u1[0] = dvd((double)lv[1], nr); u1[1] = dvd((double)(-lv[0]), nr); u1[2] = 0.0;
+    }
+    u2[0] = sub(mul(kh[1], u1[2]), mul(kh[2], u1[1]));
+    u2[1] = sub(mul(kh[2], u1[0]), mul(kh[0], u1[2]));
+    u2[2] = sub(mul(kh[0], u1[1]), mul(kh[1], u1[0]));
+    const double cp = cos2pi(psi), sp = sin2pi(psi);
+    for (int a = 0; a < 3; a++) P.e[a] = add(mul(cp, u1[a]), mul(sp, u2[a]));
+    P.reach = v.rc + 2.0 * fabs(P.AF) + 1e-9;
+}
+
+__global__ void k_pw_disp(SimView v) {
+    const PWDev& P = *v.pw;
+    if (P.null_move) return;
+    const double lx = (double)P.lv[0], ly = (double)P.lv[1], lz = (double)P.lv[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const Bead b = v.bead[i];
+        const double r[3] = {b.x, b.y, b.z};
+        const double t = add(dvd(add(add(mul(lx, r[0]), mul(ly, r[1])), mul(lz, r[2])), v.L), P.phi);
+        double dl[3];
+        if (v.precision == 0) {
+            const double amp = mul(P.AF, cos2pi(t));
+            for (int a = 0; a < 3; a++) dl[a] = mul(amp, P.e[a]);
+        } else {
+            const float amp = mulf((float)P.AF, cos2pi_f(t));
+            for (int a = 0; a < 3; a++) dl[a] = (double)mulf(amp, (float)P.e[a]);
+        }
+        int im[3] = {0, 0, 0};
+        for (int a = 0; a < 3; a++) v.pw_new[3 * i + a] = wrap(add(r[a], dl[a]), v.L, &im[a]);
+        v.pw_imgd[i] = pack_img(im[0], im[1], im[2]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pw_energy(SimView v) {
+    __shared__ double red[8];
+    const PWDev& P = *v.pw;
+    double dU = 0.0;
+    long long pe = 0;
+    if (!P.null_move) {
+        const double L = v.L, hL = v.halfL;
+        const Pot& Po = v.pot;
+        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (i < v.N) {
+            const Bead b = v.bead[i];
+            const double o[3] = {b.x, b.y, b.z};
+            const double nw[3] = {v.pw_new[3 * i], v.pw_new[3 * i + 1], v.pw_new[3 * i + 2]};
+            dU += U_ext(Po, nw[0], nw[1], nw[2]) - U_ext(Po, o[0], o[1], o[2]);
+            if (i + 1 < v.N && v.bnext[i]) {
+                const Bead c = v.bead[i + 1];
+                const double* cn = &v.pw_new[3 * (i + 1)];
+                double r2n = norm2(mi(nw[0] - cn[0], L, hL), mi(nw[1] - cn[1], L, hL), mi(nw[2] - cn[2], L, hL));
+                double r2o = norm2(mi(o[0] - c.x, L, hL), mi(o[1] - c.y, L, hL), mi(o[2] - c.z, L, hL));
+                dU += U_bond(Po, r2n) - U_bond(Po, r2o);
+            }
+            if (Po.eps != 0.0) {
+                double lo[3], hi[3];
+                for (int a = 0; a < 3; a++) { lo[a] = sub(o[a], P.reach); hi[a] = add(o[a], P.reach); }
+                int c0[3], nc[3];
+                cell_box(v, lo, hi, c0, nc);
+                const int ncell = nc[0] * nc[1] * nc[2];
+                for (int k = 0; k < ncell; k++) {
+                    int guard = 0;
+                    for (int q = v.head[box_cell(v, c0, nc, k)]; q >= 0;) {
+                        const Bead bq = v.bead[q];
+                        if (q > i) {
+                            const double* qn = &v.pw_new[3 * (int64_t)q];
+                            double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                            double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                            if (r2n < Po.rc2 || r2o < Po.rc2) { dU += U_wca(Po, r2n) - U_wca(Po, r2o); pe++; }
+                        }
+                        q = bq.next;
+                        if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                    }
+                }
+            }
+        }
+    }
+    dU = warp_sum(dU);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dU;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; w++) s += red[w];
+        v.pw_part[blockIdx.x] = s;
+    }
+    if (pe) atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
+}
+
+__global__ void __launch_bounds__(256) k_pw_decide(SimView v, int kacc, uint64_t ctr, int m, int trace_index) {
+    __shared__ double red[8];
+    PWDev& P = *v.pw;
+    if (P.null_move) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < v.pw_blocks; b += 256) s += v.pw_part[b];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double dU = 0.0;
+    for (int w = 0; w < 8; w++) dU += red[w];
+    u4 w = draw(v.k0, v.k1, (uint32_t)kacc, 0, ctr, (uint32_t)m, 0);
+    const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
+    const bool acc = dU <= thr;
+    P.accept = acc;
+    atomicAdd(&v.ctr[C_BU], (unsigned long long)v.N);
+    if (acc) {
+        P.carry = 0;
+        atomicAdd(&v.ctr[C_PWACC], 1ull);
+        atomicAdd(&v.ctr[C_ACCTOT], 1ull);
+    } else {
+        P.carry = 1;
+        for (int a = 0; a < 3; a++) P.carry_l[a] = P.lv[a];
+    }
+    if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_out[trace_index] = (uint8_t)(acc ? 1 : 2);
+}
+
+__global__ void k_pw_commit(SimView v, int* rebuild) {
+    const PWDev& P = *v.pw;
+    const bool moved = P.accept && !P.null_move;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rebuild = moved;
+    if (!moved) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
+        v.bead[i].x = v.pw_new[3 * i]; v.bead[i].y = v.pw_new[3 * i + 1]; v.bead[i].z = v.pw_new[3 * i + 2];
+        const int pk = v.pw_imgd[i];
+        if (pk != pack_img(0, 0, 0)) {
+            int dd[3];
+            unpack_img(pk, dd);
+            v.img[3 * i] += dd[0]; v.img[3 * i + 1] += dd[1]; v.img[3 * i + 2] += dd[2];
+        }
+    }
+}
+
+void launch_planewave(const SimView& v, int kmode, int kdir, int kacc, uint64_t ctr, int m, int trace_index,
+                      cudaStream_t s) {
+    const int nb = v.pw_blocks;
+    const int gb = (int)std::min<int64_t>(nb, 152 * 16);
+    k_pw_setup<<<1, 1, 0, s>>>(v, kmode, kdir, ctr, m, trace_index);
+    k_pw_disp<<<gb, 256, 0, s>>>(v);
+    k_pw_energy<<<nb, 256, 0, s>>>(v);
+    k_pw_decide<<<1, 256, 0, s>>>(v, kacc, ctr, m, trace_index);
+    k_pw_commit<<<gb, 256, 0, s>>>(v, v.pw_rebuild);
+    launch_cl_rebuild(v, s, v.pw_rebuild);
+}
+
+}  // namespace wmcd
