@@ -1,0 +1,360 @@
+"""Benchmark of the WMCD sweep on GB300.
+
+Workload (one step = one sweep of the whole hot path: slots, bucketing, colour phases,
+serial phase, plane waves): 256 self-avoiding chains x 64 beads (16,384 beads) at volume
+fraction 1e-3 in a periodic cube (L = 409.4 a), harmonic bonds k = 100 kT/a^2 with rest
+length 2a, WCA sigma = 2a, eps = 1 kT, lambda_min = 2a, lambda_max = L/2, A0 = 0.5,
+wavelets plus periodic plane waves (|l| <= 8), mixed precision. Inputs are synthetic
+(seeded). The positions are far smaller than L2, so a 256 MiB buffer is written between
+timed steps to flush L2; each step is timed with CUDA events on the launching stream.
+
+Metric: bead-updates per second (a bead-update = one bead inside an attempted move's
+support; N per plane-wave attempt), whole job over all ranks; also simulated time per
+wall second. Multi-GPU runs are independent replicas (different seeds), no collective in
+the data path.
+
+--impl reference times the CPU oracle (the plain sequential FP64 statement of the method)
+on the same workload on one host core.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bead-updates/s (WMCD sweep)"
+UNIT = "bead-updates/s"
+
+
+def workload_config():
+    return {"workload": "dilute chains 256x64 beads (16,384) phi=1e-3 L=409.4, wavelet+plane-wave lcut 8, "
+                        "A0=0.5, harmonic k=100 r0=2, WCA sigma=2 eps=1, lambda 2..L/2",
+            "n_beads": 16384, "chains": 256, "chain_len": 64, "phi": 1e-3, "planewave_lcut": 8,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def make_system(seed):
+    from paper_1611_09160_gb300 import inputs as I
+    return I.dilute_chains(256, 64, 1e-3, seed=seed)
+
+
+def make_params(system, precision, seed, sim_id=0):
+    from paper_1611_09160_gb300 import wmcd
+    return wmcd.default_params(system.n_beads, system.box_L, planewave_mode=wmcd.PLANEWAVE_PERIODIC, lcut=8,
+                               precision=precision, seed=seed, sim_id=sim_id)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 3 + k and r[3 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def profile_traffic(kernel_src_sha):
+    """dram bytes per launch of the concurrent kernel from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "wavelet_concurrent_dilute16k.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_src_sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ["wmcd_kernels.cu", "wmcd_device.cuh", "wmcd_internal.h"]:
+        h.update(open(os.path.join(ROOT, "paper_1611_09160_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle, as it stands, on a bounded sample of the same workload (whole sweeps)."""
+    import oracle as O
+    from paper_1611_09160_gb300 import wmcd
+    s = make_system(1)
+    p = make_params(s, wmcd.MIXED, 1)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    t0 = time.perf_counter()
+    sweeps = 0
+    while time.perf_counter() - t0 < seconds:
+        o.sweep(1)
+        sweeps += 1
+    dt = time.perf_counter() - t0
+    st = o.stats()
+    return {"value": st.bead_updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} whole sweeps of the same 16,384-bead workload (sequential C++ FP64 oracle, "
+                      f"brute-force neighbour search), {dt:.1f} s", "sim_time_per_s": st.sim_time / dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1611_09160_gb300 import wmcd
+    O.build()
+    s = make_system(1)
+    p = make_params(s, wmcd.MIXED, 1)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    for _ in range(args.warmup):
+        o.sweep(1)
+    b0, t_sim0 = o.stats().bead_updates, o.stats().sim_time
+    t0 = time.perf_counter()
+    o.sweep(args.steps)
+    dt = time.perf_counter() - t0
+    st = o.stats()
+    value = (st.bead_updates - b0) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} whole sweeps after {args.warmup} warm-up sweeps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sim_time_per_s": (st.sim_time - t_sim0) / dt}
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(sim, steps, flush, stream, torch):
+    """Per-step CUDA-event times (ms) of `steps` sweeps, L2 flushed before each."""
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.sweep(1, stream=stream)
+        b.record(stream)
+        times.append((a, b))
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1611_09160_gb300 import wmcd
+    import __graft_entry__
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    wmcd.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    seed = 1 + rank
+    system = make_system(seed)
+
+    def measure(precision, profile):
+        p = make_params(system, precision, seed, sim_id=rank)
+        sim = wmcd.Simulation(p, system.pos, system.chain_len, stream=stream)
+        for _ in range(args.warmup):
+            sim.sweep(1, stream=stream)
+        st0 = sim.stats(stream=stream)
+        sim.kernel_times(stream=stream)
+        sim.profile(profile)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms = timed_steps(sim, args.steps, flush, stream, torch)
+        torch.cuda.synchronize()
+        sim.profile(False)
+        kt = sim.kernel_times(stream=stream)
+        st1 = sim.stats(stream=stream)
+        return sim, ms, st0, st1, kt
+
+    with ClockSampler(local_rank) as clk:
+        sim, ms, st0, st1, kt = measure(wmcd.MIXED, True)
+    clocks = clk.summary()
+    total_ms = float(np.sum(ms))
+    bu = st1.bead_updates - st0.bead_updates
+    simt = st1.sim_time - st0.sim_time
+    launches = st1.kernel_launches - st0.kernel_launches
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(bu), simt, float(launches)], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_ms_all, bu_all, simt_all, launches_all = float(t[0]), float(u[0]), float(u[1]), int(u[2])
+    else:
+        total_ms_all, bu_all, simt_all, launches_all = total_ms, float(bu), simt, launches
+    value = bu_all / (total_ms_all * 1e-3)
+
+    # plain FP64 GPU sweep on the same inputs (the comparison the method is quoted against)
+    _, ms64, a64, b64, _ = measure(wmcd.FP64, False)
+    fp64_value = (b64.bead_updates - a64.bead_updates) / (float(np.sum(ms64)) * 1e-3)
+
+    # dominant kernel and its roofline (HBM: the path is gathers and pair energies)
+    dom = max(kt, key=lambda k: kt[k][1])
+    conc_launches, conc_ms = kt["concurrent_wavelet"]
+    cbu = st1.conc_bead_updates - st0.conc_bead_updates
+    cmov = st1.conc_moved_beads - st0.conc_moved_beads
+    cpe = st1.conc_partner_evals - st0.conc_partner_evals
+    alg_bytes = 28.0 * cbu + 24.0 * cmov + 28.0 * cpe
+    pk, pk_kind = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / (conc_ms * 1e-3) / 1e9 if conc_ms > 0 else 0.0
+    traffic = profile_traffic(kernel_sha())
+    roofline = {"bound": "hbm", "kernel": "k_colour (concurrent wavelet moves)", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": pk_kind,
+                "traffic": traffic, "alg_bytes_per_launch": alg_bytes / max(conc_launches, 1),
+                "launches": conc_launches, "avg_launch_us": 1e3 * conc_ms / max(conc_launches, 1),
+                "bytes_model": "28 B per bead-update + 24 B per moved bead + 28 B per partner pair evaluation",
+                "dominant_by_time": dom,
+                "kernel_ms": {k: round(v[1], 4) for k, v in kt.items()},
+                "kernel_launches": {k: v[0] for k, v in kt.items()}}
+
+    # end to end through the public API with host buffers: H2D positions, sweep, D2H positions
+    import torch as _t
+    p = make_params(system, wmcd.MIXED, seed, sim_id=rank)
+    sim_e = wmcd.Simulation(p, system.pos, system.chain_len, stream=stream)
+    h_in = _t.from_numpy(system.pos.copy()).pin_memory()
+    h_out = _t.empty((system.n_beads, 3), dtype=_t.float64).pin_memory()
+    for _ in range(args.warmup):
+        sim_e.set_positions(h_in, stream=stream)
+        sim_e.sweep(1, stream=stream)
+        sim_e.positions(out=h_out, stream=stream)
+    e0 = sim_e.stats(stream=stream).bead_updates
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim_e.set_positions(h_in, stream=stream)
+        sim_e.sweep(1, stream=stream)
+        sim_e.positions(out=h_out, stream=stream)
+    stream.synchronize()
+    e_dt = time.perf_counter() - t0
+    e_bu = sim_e.stats(stream=stream).bead_updates - e0
+    e2e = {"value": e_bu / e_dt * world, "unit": UNIT, "h2d_bytes_per_step": 24 * system.n_beads,
+           "d2h_bytes_per_step": 24 * system.n_beads,
+           "note": "per rank, scaled by the number of replicas" if world > 1 else "one replica"}
+
+    # the plane-wave kernel alone (plane waves are rare inside a sweep)
+    sim_pw = wmcd.Simulation(make_params(system, wmcd.MIXED, seed, sim_id=rank), system.pos, system.chain_len,
+                             stream=stream)
+    sim_pw.planewave(5, stream=stream)
+    q0 = sim_pw.stats(stream=stream)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim_pw.planewave(50, stream=stream)
+    b.record(stream)
+    stream.synchronize()
+    q1 = sim_pw.stats(stream=stream)
+    pw = {"bead_updates_per_s": (q1.bead_updates - q0.bead_updates) / (a.elapsed_time(b) * 1e-3),
+          "moves": 50, "ms_per_move": a.elapsed_time(b) / 50}
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(workload_config(), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "sim_time_per_s": simt_all / (total_ms_all * 1e-3),
+            "fp64": {"value": fp64_value * world, "unit": UNIT, "speedup_mixed_over_fp64": value / (fp64_value * world)},
+            "e2e": e2e, "gpu_launches": launches_all, "clocks": clocks, "roofline": roofline,
+            "plane_wave": pw,
+            "stats": {"accept_fraction": (st1.accepted_total - st0.accepted_total) /
+                                         max(1, sum(st1.attempts) - sum(st0.attempts) +
+                                             st1.pw_attempts - st0.pw_attempts),
+                      "deferred": int(sum(st1.deferred) - sum(st0.deferred)),
+                      "error_flags": st1.error_flags}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -90,6 +90,10 @@ typedef struct wmcd_stats_t {
     double dt_move;                      /* Eq. 57 with plane waves, Eq. 34 without */
     double p_fourier;                    /* probability of a plane-wave move (Eq. 56) */
     int32_t error_flags;                 /* device-side error bits, 0 = none */
+    int64_t kernel_launches;             /* kernels this library has launched */
+    int64_t conc_bead_updates;           /* bead updates done by the concurrent wavelet kernel */
+    int64_t conc_moved_beads;            /* beads written back by accepted concurrent moves */
+    int64_t conc_partner_evals;          /* its pair evaluations with beads outside the support */
 } wmcd_stats_t;
 
 typedef struct wmcd_handle wmcd_handle;

@@ -86,6 +86,7 @@ struct Handle {
     double p_fourier = 0.0, dt_move = 0.0, R = 1.0;
     uint64_t sweep = 0, pw_calls = 0;
     int64_t tr_pw_count = 0;
+    int64_t launches = 0;        // kernels launched by this handle
     std::vector<void*> allocs;
     size_t bytes = 0;
     double* staging = nullptr;   // 3N doubles
@@ -380,15 +381,18 @@ static void run_sweep(Handle* h, cudaStream_t s) {
         const int64_t M = slot_count(h, K_COUNT, l, sw, h->expect[l]);
         if (M <= 0) continue;
         { ProfScope ps(h, 4, s); launch_slots(v, l, sw, (int)M, s); }
+        h->launches += 1;
         if (v.layer[l].G > 0) {
             { ProfScope ps(h, 4, s); launch_bucket(v, l, (int)M, s); }
             const int nc = v.K * v.K * v.K;
             for (int c = 0; c < nc; c++) { ProfScope ps(h, 0, s); launch_colour(v, l, c, sw, s); }
             { ProfScope ps(h, 4, s); launch_defer_compact(v, (int)M, s); }
             { ProfScope ps(h, 1, s); launch_serial(v, l, sw, 1, (int)M, s); }
+            h->launches += 4 + nc + 2;
         } else {
             ProfScope ps(h, 1, s);
             launch_serial(v, l, sw, 0, (int)M, s);
+            h->launches += 1;
         }
     }
     h->tr_pw_count = 0;
@@ -398,6 +402,7 @@ static void run_sweep(Handle* h, cudaStream_t s) {
             ProfScope ps(h, 2, s);
             launch_planewave(v, K_PWMODE, K_PWDIR, K_PWACC, sw, (int)m, (int)m, s);
         }
+        h->launches += 8 * MF;
         h->tr_pw_count = MF;
     }
     h->sweep++;
@@ -430,6 +435,7 @@ extern "C" int wmcd_planewave(wmcd_handle* H, int64_t n_moves, void* stream) {
         ProfScope ps(h, 2, s);
         launch_planewave(h->v, K_DPWMODE, K_DPWDIR, K_DPWACC, h->pw_calls, (int)m, (int)m, s);
     }
+    h->launches += 8 * n_moves;
     h->tr_pw_count = n_moves;
     h->pw_calls++;
     return last_cuda_status();
@@ -489,6 +495,10 @@ extern "C" int wmcd_stats(wmcd_handle* H, wmcd_stats_t* out, void* stream) {
     out->dt_move = h->dt_move;
     out->p_fourier = h->p_fourier;
     out->error_flags = err;
+    out->kernel_launches = h->launches;
+    out->conc_bead_updates = (int64_t)c[C_CBU];
+    out->conc_moved_beads = (int64_t)c[C_CMOVED];
+    out->conc_partner_evals = (int64_t)c[C_CPE];
     if (err & E_WALK) return WMCD_ETIMEOUT;
     if (err & E_NONFINITE) return WMCD_ESTATE;
     return WMCD_OK;

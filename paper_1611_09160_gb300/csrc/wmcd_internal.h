@@ -26,7 +26,7 @@ enum Outcome { ACCEPT = 1, REJECT = 2, DEFER = 3 };
 // device counters
 enum Ctr {
     C_ATT = 0, C_ACC = 16, C_DEF = 32, C_PWATT = 48, C_PWACC = 49, C_BU = 50, C_ACCTOT = 51, C_RECHECK = 52,
-    C_PARTNER = 53, C_NCTR = 64
+    C_PARTNER = 53, C_CBU = 54, C_CMOVED = 55, C_CPE = 56, C_NCTR = 64
 };
 // device error bits
 enum Err { E_WALK = 1, E_SCRATCH = 2, E_NONFINITE = 4 };

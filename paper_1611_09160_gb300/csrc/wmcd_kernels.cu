@@ -221,14 +221,14 @@ namespace wmcd {
 // ======================================================================================
 struct WarpSmem {
     int ids[kNCap];          // support, in gather order
-    double d[kNCap][4];      // minimum-image offset from the centre, and its square
+    double d[kNCap][4];      // exact minimum-image offset from the centre, and its square
     double op[kNCap][3];     // old positions
     double np[kNCap][3];     // new (wrapped) positions
     double nu[kNCap][3];     // new unwrapped positions (old + delta)
     int dimg[kNCap];         // packed image change
     int sid[kNCap];          // support ids ascending
-    int wpre[kNCap + 1];     // prefix of partner-search cells per member
-    int wbox[kNCap][6];      // partner-search cell box per member: c0[3], nc[3]
+    int cpre[kNCap + 1];     // prefix of partner-search columns per member
+    int cbox[kNCap][6];      // partner-search box per member: first cell c0[3], cells nc[3]
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -286,11 +286,230 @@ __device__ __forceinline__ int box_cell(const SimView& v, const int c0[3], const
     return wrapi(c0[0] + kx, v.Gf) + v.Gf * (wrapi(c0[1] + ky, v.Gf) + v.Gf * wrapi(c0[2] + kz, v.Gf));
 }
 
+// cell index modulo G: one add or subtract in the common case, a remainder otherwise
+__device__ __forceinline__ int wrapc(int c, int G) {
+    if (c < 0) c += G;
+    else if (c >= G) c -= G;
+    if ((unsigned)c >= (unsigned)G) { c %= G; if (c < 0) c += G; }
+    return c;
+}
+
+// difference a - b of two wrapped coordinates in binary32, minimum image applied
+__device__ __forceinline__ float dif32(double a, double b, double L, float hLf) {
+    const double d = sub(a, b);
+    float f = (float)d;
+    if (fabsf(f) > hLf) f = (float)(d > 0.0 ? sub(d, L) : add(d, L));
+    return f;
+}
+__device__ __forceinline__ float norm2f(float x, float y, float z) { return x * x + y * y + z * z; }
+
+// binary32 pair energies with a magnitude m such that |error| <= 64 u m  (u = 2^-24)
+struct Pot32 {
+    float sig2, eps, rc2, bk, br0, br02, R02, kappa, hL;
+    int bond;
+};
+__device__ __forceinline__ Pot32 pot32(const Pot& P) {
+    Pot32 q;
+    q.sig2 = (float)P.sig2; q.eps = (float)P.eps; q.rc2 = (float)P.rc2; q.bk = (float)P.bk; q.br0 = (float)P.br0;
+    q.br02 = q.br0 * q.br0; q.R02 = (float)P.R02; q.kappa = (float)P.kappa; q.hL = (float)P.halfL; q.bond = P.bond;
+    return q;
+}
+__device__ __forceinline__ void wca32(const Pot32& P, float r2, float& u, float& m) {
+    if (P.eps == 0.0f || !(r2 < P.rc2)) { u = 0.0f; m = 0.0f; return; }
+    const float s2 = __fdiv_rn(P.sig2, r2), s6 = s2 * s2 * s2, s12 = s6 * s6;
+    u = 4.0f * P.eps * (s12 - s6) + P.eps;
+    m = 4.0f * P.eps * (s12 + s6) + P.eps;
+}
+__device__ __forceinline__ void bond32(const Pot32& P, float r2, float& u, float& m) {
+    if (P.bond == 1) {
+        const float r = __fsqrt_rn(r2), d = r - P.br0;
+        u = 0.5f * P.bk * d * d;
+        m = P.bk * (r2 + P.br02);
+    } else if (P.bond == 2) {
+        const float x = __fdiv_rn(r2, P.R02);
+        if (!(x < 0.98f)) { u = 0.0f; m = __int_as_float(0x7f800000); return; }   // near R0: decide in FP64
+        const float lg = log1pf(-x);
+        u = -0.5f * P.bk * P.R02 * lg;
+        m = 0.5f * P.bk * P.R02 * (fabsf(lg) + 8.0f * x / (1.0f - x) + 1.0f);
+    } else {
+        u = 0.0f; m = 0.0f;
+    }
+}
+
+// Partner-search boxes of the support: [min(old, new) - rc, max(old, new) + rc] per member;
+// columns (x, y) are spread over lanes, z is looped. Returns the column count and max z extent.
+__device__ void partner_boxes(const SimView& v, WarpSmem& sm, int n, int lane, int* ncols, int* nzmax) {
+    int nz = 0;
+    for (int k = lane; k < n; k += 32) {
+        int c0[3], nc[3];
+        for (int a = 0; a < 3; a++) {
+            const double o = sm.op[k][a], u = sm.nu[k][a];
+            c0[a] = (int)floor(mul(sub(fmin(o, u), v.rc + 1e-9), v.invf));
+            const int t1 = (int)floor(mul(add(fmax(o, u), v.rc + 1e-9), v.invf));
+            nc[a] = min(t1 - c0[a] + 1, v.Gf);
+        }
+        for (int a = 0; a < 3; a++) { sm.cbox[k][a] = c0[a]; sm.cbox[k][3 + a] = nc[a]; }
+        sm.cpre[k + 1] = nc[0] * nc[1];
+        nz = max(nz, nc[2]);
+    }
+    __syncwarp();
+    if (lane == 0) { sm.cpre[0] = 0; for (int k = 0; k < n; k++) sm.cpre[k + 1] += sm.cpre[k]; }
+    for (int o = 16; o > 0; o >>= 1) nz = max(nz, __shfl_xor_sync(0xffffffffu, nz, o));
+    __syncwarp();
+    *ncols = sm.cpre[n];
+    *nzmax = nz;
+}
+
+// Energy change of the move (Eqs. 1, 2; external well): support-support pairs, bonds to beads
+// outside the support, WCA to beads outside the support (cell lists). F32: binary32 terms,
+// returns the sum, the magnitude sum and the term count; otherwise binary64.
+template <bool F32>
+__device__ void energy(const SimView& v, WarpSmem& sm, int n, int lane, int ncols, int nzmax, double* dU64,
+                       float* dU32, float* mag32, int* terms, int* pe_out) {
+    const double L = v.L, hL = v.halfL;
+    const Pot& P = v.pot;
+    const Pot32 P32 = pot32(P);
+    const float hLf = (float)hL;
+    double a64 = 0.0;
+    float a32 = 0.0f, m32 = 0.0f;
+    int T = 0, pe = 0;
+    // external well and bonds to partners outside the support
+    for (int k = lane; k < n; k += 32) {
+        if (P.kappa != 0.0) {
+            if (F32) {
+                float x = dif32(sm.np[k][0], hL, L, hLf), y = dif32(sm.np[k][1], hL, L, hLf), z = dif32(sm.np[k][2], hL, L, hLf);
+                float un = 0.5f * P32.kappa * norm2f(x, y, z);
+                x = dif32(sm.op[k][0], hL, L, hLf); y = dif32(sm.op[k][1], hL, L, hLf); z = dif32(sm.op[k][2], hL, L, hLf);
+                float uo = 0.5f * P32.kappa * norm2f(x, y, z);
+                a32 += un - uo; m32 += un + uo; T += 2;
+            } else {
+                a64 += U_ext(P, sm.np[k][0], sm.np[k][1], sm.np[k][2]) - U_ext(P, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
+            }
+        }
+        const int m = sm.ids[k];
+        for (int e = 0; e < 2; e++) {
+            const int q = e ? m + 1 : m - 1;
+            if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q]) || sorted_has(sm.sid, n, q)) continue;
+            const Bead bq = v.bead[q];
+            if (F32) {
+                float r2n = norm2f(dif32(sm.np[k][0], bq.x, L, hLf), dif32(sm.np[k][1], bq.y, L, hLf), dif32(sm.np[k][2], bq.z, L, hLf));
+                float r2o = norm2f(dif32(sm.op[k][0], bq.x, L, hLf), dif32(sm.op[k][1], bq.y, L, hLf), dif32(sm.op[k][2], bq.z, L, hLf));
+                float un, mn, uo, mo;
+                bond32(P32, r2n, un, mn);
+                bond32(P32, r2o, uo, mo);
+                a32 += un - uo; m32 += mn + mo; T += 2;
+            } else {
+                double r2n = norm2(mi(sm.np[k][0] - bq.x, L, hL), mi(sm.np[k][1] - bq.y, L, hL), mi(sm.np[k][2] - bq.z, L, hL));
+                double r2o = norm2(mi(sm.op[k][0] - bq.x, L, hL), mi(sm.op[k][1] - bq.y, L, hL), mi(sm.op[k][2] - bq.z, L, hL));
+                a64 += U_bond(P, r2n) - U_bond(P, r2o);
+            }
+        }
+    }
+    // pairs inside the support
+    const int npairs = n * (n - 1) / 2;
+    for (int t = lane; t < npairs; t += 32) {
+        int a = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > t) a--;
+        while ((a + 1) * (a + 2) / 2 <= t) a++;
+        const int k1 = t - a * (a + 1) / 2, k2 = a + 1;
+        const int m1 = sm.ids[k1], m2 = sm.ids[k2];
+        const int lo_ = min(m1, m2), hi_ = max(m1, m2);
+        const bool bonded = hi_ == lo_ + 1 && v.bnext[lo_];
+        if (F32) {
+            float r2n = norm2f(dif32(sm.np[k1][0], sm.np[k2][0], L, hLf), dif32(sm.np[k1][1], sm.np[k2][1], L, hLf),
+                               dif32(sm.np[k1][2], sm.np[k2][2], L, hLf));
+            float r2o = norm2f(dif32(sm.op[k1][0], sm.op[k2][0], L, hLf), dif32(sm.op[k1][1], sm.op[k2][1], L, hLf),
+                               dif32(sm.op[k1][2], sm.op[k2][2], L, hLf));
+            float un, mn, uo, mo;
+            wca32(P32, r2n, un, mn);
+            wca32(P32, r2o, uo, mo);
+            a32 += un - uo; m32 += mn + mo; T += 2;
+            if (bonded) { bond32(P32, r2n, un, mn); bond32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
+        } else {
+            double r2n = norm2(mi(sm.np[k1][0] - sm.np[k2][0], L, hL), mi(sm.np[k1][1] - sm.np[k2][1], L, hL),
+                               mi(sm.np[k1][2] - sm.np[k2][2], L, hL));
+            double r2o = norm2(mi(sm.op[k1][0] - sm.op[k2][0], L, hL), mi(sm.op[k1][1] - sm.op[k2][1], L, hL),
+                               mi(sm.op[k1][2] - sm.op[k2][2], L, hL));
+            double u = U_wca(P, r2n) - U_wca(P, r2o);
+            if (bonded) u += U_bond(P, r2n) - U_bond(P, r2o);
+            a64 += u;
+        }
+    }
+    // WCA with beads outside the support, through the cell lists
+    if (P.eps != 0.0) {
+        const int Gf = v.Gf;
+        for (int base = 0; base < ncols; base += 32) {
+            const int w = base + lane;
+            int k = 0, cx = 0, cy = 0, c0z = 0, nz = 0;
+            const bool valid = w < ncols;
+            if (valid) {
+                while (sm.cpre[k + 1] <= w) k++;
+                const int col = w - sm.cpre[k], nx = sm.cbox[k][3];
+                cx = wrapc(sm.cbox[k][0] + col % nx, Gf);
+                cy = wrapc(sm.cbox[k][1] + col / nx, Gf);
+                c0z = sm.cbox[k][2];
+                nz = sm.cbox[k][5];
+            }
+            const int m = sm.ids[k];
+            const int colbase = cx + Gf * cy;
+            for (int kz = 0; kz < nzmax; kz++) {
+                int q = (valid && kz < nz) ? v.head[colbase + Gf * Gf * wrapc(c0z + kz, Gf)] : -1;
+                int guard = 0;
+                while (q >= 0) {
+                    const Bead bq = v.bead[q];
+                    if (q != m && !sorted_has(sm.sid, n, q)) {
+                        if (F32) {
+                            float r2n = norm2f(dif32(sm.np[k][0], bq.x, L, hLf), dif32(sm.np[k][1], bq.y, L, hLf),
+                                               dif32(sm.np[k][2], bq.z, L, hLf));
+                            float r2o = norm2f(dif32(sm.op[k][0], bq.x, L, hLf), dif32(sm.op[k][1], bq.y, L, hLf),
+                                               dif32(sm.op[k][2], bq.z, L, hLf));
+                            if (r2n < P32.rc2 || r2o < P32.rc2) {
+                                float un, mn, uo, mo;
+                                wca32(P32, r2n, un, mn);
+                                wca32(P32, r2o, uo, mo);
+                                a32 += un - uo; m32 += mn + mo; T += 2; pe++;
+                            }
+                        } else {
+                            double r2n = norm2(mi(sm.np[k][0] - bq.x, L, hL), mi(sm.np[k][1] - bq.y, L, hL),
+                                               mi(sm.np[k][2] - bq.z, L, hL));
+                            double r2o = norm2(mi(sm.op[k][0] - bq.x, L, hL), mi(sm.op[k][1] - bq.y, L, hL),
+                                               mi(sm.op[k][2] - bq.z, L, hL));
+                            if (r2n < P.rc2 || r2o < P.rc2) { a64 += U_wca(P, r2n) - U_wca(P, r2o); pe++; }
+                        }
+                    }
+                    q = bq.next;
+                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                }
+            }
+        }
+    }
+    // lane 0's sums for every lane (a butterfly leaves lanes with differently rounded totals)
+    const unsigned FULL = 0xffffffffu;
+    if (F32) {
+        float s = a32, mm = m32;
+        int tt = T;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(FULL, s, o);
+            mm += __shfl_xor_sync(FULL, mm, o);
+            tt += __shfl_xor_sync(FULL, tt, o);
+        }
+        *dU32 = __shfl_sync(FULL, s, 0);
+        *mag32 = __shfl_sync(FULL, mm, 0);
+        *terms = __shfl_sync(FULL, tt, 0);
+    } else {
+        *dU64 = __shfl_sync(FULL, warp_sum(a64), 0);
+    }
+    *pe_out = warp_sum_i(pe);
+}
+
 template <int PREC>
 __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i, double lam, uint64_t sweep,
-                            const int64_t rlo[3], const int64_t rhi[3], int lane, int* n_out, int* pe_out) {
+                            const int64_t rlo[3], const int64_t rhi[3], int lane, int* n_out, int* pe_out,
+                            int* recheck_out) {
     const unsigned FULL = 0xffffffffu;
     const double L = v.L, hL = v.halfL;
+    const float hLf = (float)hL;
+    const int Gf = v.Gf;
     // centre b = r_i + lam V (Appendix D), wrapped into the box
     const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
     double V[3], b[3];
@@ -299,51 +518,55 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     // the influence ball must lie in fine cells wholly inside the queue's region
     const double R = add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
     for (int a = 0; a < 3; a++) {
-        int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
-        int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
-        if (!range_inside(t0, t1, rlo[a], rhi[a], v.Gf)) return DEFER;
+        const int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
+        const int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
+        if (!range_inside(t0, t1, rlo[a], rhi[a], Gf)) return DEFER;
     }
-    // gather the support: beads strictly inside the ball (one image each, lambda <= L/2)
+    // gather the support: beads strictly inside the ball (one image each, lambda <= L/2);
+    // binary32 prefilter, exact binary64 test within 1e-6 of the sphere
     const double lam2 = mul(lam, lam);
+    const float lam2f = (float)lam2, lin = lam2f * (1.0f - 1e-6f), lout = lam2f * (1.0f + 1e-6f);
     int c0[3], nc[3];
-    {
-        const double eps = 1e-9;
-        double lo[3] = {sub(b[0], lam + eps), sub(b[1], lam + eps), sub(b[2], lam + eps)};
-        double hi[3] = {add(b[0], lam + eps), add(b[1], lam + eps), add(b[2], lam + eps)};
-        cell_box(v, lo, hi, c0, nc);
+    for (int a = 0; a < 3; a++) {
+        c0[a] = (int)floor(mul(sub(b[a], lam + 1e-9), v.invf));
+        const int t1 = (int)floor(mul(add(b[a], lam + 1e-9), v.invf));
+        nc[a] = min(t1 - c0[a] + 1, Gf);
     }
-    const int ncell = nc[0] * nc[1] * nc[2];
     int n = 0;
     {
-        int k = lane, ptr = -1, guard = 0;
-        while (ptr < 0 && k < ncell) { ptr = v.head[box_cell(v, c0, nc, k)]; if (ptr < 0) k += 32; }
-        while (true) {
-            bool has = ptr >= 0;
-            if (!__any_sync(FULL, has)) break;
-            bool in = false;
-            int nxt = -1;
-            double d[3] = {0, 0, 0}, d2 = 0, ox = 0, oy = 0, oz = 0;
-            if (has) {
-                Bead bb = v.bead[ptr];
-                ox = bb.x; oy = bb.y; oz = bb.z;
-                d[0] = mi(sub(bb.x, b[0]), L, hL); d[1] = mi(sub(bb.y, b[1]), L, hL); d[2] = mi(sub(bb.z, b[2]), L, hL);
-                d2 = norm2(d[0], d[1], d[2]);
-                in = d2 < lam2;
-                nxt = bb.next;
+        const int nxy = nc[0] * nc[1];
+        int guard = 0;
+        for (int base = 0; base < nxy; base += 32) {
+            const int w = base + lane;
+            const bool col = w < nxy;
+            const int colbase = col ? wrapc(c0[0] + w % nc[0], Gf) + Gf * wrapc(c0[1] + w / nc[0], Gf) : 0;
+            for (int kz = 0; kz < nc[2]; kz++) {
+                int ptr = col ? v.head[colbase + Gf * Gf * wrapc(c0[2] + kz, Gf)] : -1;
+                while (__any_sync(FULL, ptr >= 0)) {
+                    bool in = false;
+                    int nxt = -1;
+                    Bead bb;
+                    if (ptr >= 0) {
+                        bb = v.bead[ptr];
+                        nxt = bb.next;
+                        const float d2f = norm2f(dif32(bb.x, b[0], L, hLf), dif32(bb.y, b[1], L, hLf), dif32(bb.z, b[2], L, hLf));
+                        if (d2f < lin) in = true;
+                        else if (d2f <= lout) {
+                            const double e2 = norm2(mi(sub(bb.x, b[0]), L, hL), mi(sub(bb.y, b[1]), L, hL), mi(sub(bb.z, b[2]), L, hL));
+                            in = e2 < lam2;
+                        }
+                    }
+                    const unsigned msk = __ballot_sync(FULL, in);
+                    const int slot = n + __popc(msk & ((1u << lane) - 1u));
+                    if (in && slot < kNCap) {
+                        sm.ids[slot] = ptr;
+                        sm.op[slot][0] = bb.x; sm.op[slot][1] = bb.y; sm.op[slot][2] = bb.z;
+                    }
+                    n += __popc(msk);
+                    ptr = nxt;
+                    if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
+                }
             }
-            unsigned m = __ballot_sync(FULL, in);
-            int slot = n + __popc(m & ((1u << lane) - 1u));
-            if (in && slot < kNCap) {
-                sm.ids[slot] = ptr;
-                sm.d[slot][0] = d[0]; sm.d[slot][1] = d[1]; sm.d[slot][2] = d[2]; sm.d[slot][3] = d2;
-                sm.op[slot][0] = ox; sm.op[slot][1] = oy; sm.op[slot][2] = oz;
-            }
-            n += __popc(m);
-            if (has) {
-                ptr = nxt;
-                if (ptr < 0) { k += 32; while (ptr < 0 && k < ncell) { ptr = v.head[box_cell(v, c0, nc, k)]; if (ptr < 0) k += 32; } }
-            }
-            if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
         }
     }
     *n_out = n;
@@ -354,23 +577,26 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     double p[3];
     warp_ball_point(v, K_VP, l, sweep, (uint32_t)j, true, lane, p);
     {
-        double q = norm2(p[0], p[1], p[2]), r = sqr_t(q);
+        const double r = sqr_t(norm2(p[0], p[1], p[2]));
         p[0] = dvd(p[0], r); p[1] = dvd(p[1], r); p[2] = dvd(p[2], r);
     }
     const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
     for (int k = lane; k < n; k += 32) {
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = mi(sub(sm.op[k][a], b[a]), L, hL);
+        const double d2 = norm2(d[0], d[1], d[2]);
         double dl[3];
-        if (PREC == 0) wavelet_disp64(sm.d[k], sm.d[k][3], lam, Aw, p, dl);
-        else wavelet_disp32(sm.d[k], lam, Aw, p, dl);
+        if (PREC == 0) wavelet_disp64(d, d2, lam, Aw, p, dl);
+        else wavelet_disp32(d, lam, Aw, p, dl);
         int im[3] = {0, 0, 0};
         for (int a = 0; a < 3; a++) {
-            double u = add(sm.op[k][a], dl[a]);
+            const double u = add(sm.op[k][a], dl[a]);
             sm.nu[k][a] = u;
             sm.np[k][a] = wrap(u, L, &im[a]);
         }
         sm.dimg[k] = pack_img(im[0], im[1], im[2]);
-        // rank of this member by bead id
-        int me = sm.ids[k], r = 0;
+        const int me = sm.ids[k];
+        int r = 0;
         for (int t = 0; t < n; t++) r += sm.ids[t] < me;
         sm.sid[r] = me;
     }
@@ -378,101 +604,48 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     // bonded partners outside the support must lie in the region
     bool bad = false;
     for (int k = lane; k < n; k += 32) {
-        int m = sm.ids[k];
+        const int m = sm.ids[k];
         for (int e = 0; e < 2; e++) {
-            int q = e ? m + 1 : m - 1;
-            if (q < 0 || q >= v.N) continue;
-            if (!(e ? v.bnext[m] : v.bnext[q])) continue;
-            if (sorted_has(sm.sid, n, q)) continue;
-            Bead bq = v.bead[q];
-            int64_t cq[3] = {fine_cell(bq.x, v.invf, v.Gf), fine_cell(bq.y, v.invf, v.Gf), fine_cell(bq.z, v.invf, v.Gf)};
-            for (int a = 0; a < 3; a++) if (!range_inside(cq[a], cq[a], rlo[a], rhi[a], v.Gf)) bad = true;
+            const int q = e ? m + 1 : m - 1;
+            if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q]) || sorted_has(sm.sid, n, q)) continue;
+            const Bead bq = v.bead[q];
+            const int64_t cq[3] = {fine_cell(bq.x, v.invf, Gf), fine_cell(bq.y, v.invf, Gf), fine_cell(bq.z, v.invf, Gf)};
+            for (int a = 0; a < 3; a++) if (!range_inside(cq[a], cq[a], rlo[a], rhi[a], Gf)) bad = true;
         }
     }
     if (__any_sync(FULL, bad)) return DEFER;
-    // energy change (Eqs. 1, 2): external, support-support pairs, bonds to outside, WCA to outside
-    const Pot& P = v.pot;
-    double dU = 0.0;
-    int pe = 0;
-    for (int k = lane; k < n; k += 32) {
-        dU += U_ext(P, sm.np[k][0], sm.np[k][1], sm.np[k][2]) - U_ext(P, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
-        int m = sm.ids[k];
-        for (int e = 0; e < 2; e++) {
-            int q = e ? m + 1 : m - 1;
-            if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q]) || sorted_has(sm.sid, n, q)) continue;
-            Bead bq = v.bead[q];
-            double r2n = norm2(mi(sm.np[k][0] - bq.x, L, hL), mi(sm.np[k][1] - bq.y, L, hL), mi(sm.np[k][2] - bq.z, L, hL));
-            double r2o = norm2(mi(sm.op[k][0] - bq.x, L, hL), mi(sm.op[k][1] - bq.y, L, hL), mi(sm.op[k][2] - bq.z, L, hL));
-            dU += U_bond(P, r2n) - U_bond(P, r2o);
-        }
-    }
-    const int npairs = n * (n - 1) / 2;
-    for (int t = lane; t < npairs; t += 32) {
-        // pair t -> (a, b), a < b
-        int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-        while (a * (a + 1) / 2 > t) a--;
-        while ((a + 1) * (a + 2) / 2 <= t) a++;
-        int bb = t - a * (a + 1) / 2;      // bb < a + 1
-        int k1 = bb, k2 = a + 1;
-        int m1 = sm.ids[k1], m2 = sm.ids[k2];
-        double r2n = norm2(mi(sm.np[k1][0] - sm.np[k2][0], L, hL), mi(sm.np[k1][1] - sm.np[k2][1], L, hL),
-                           mi(sm.np[k1][2] - sm.np[k2][2], L, hL));
-        double r2o = norm2(mi(sm.op[k1][0] - sm.op[k2][0], L, hL), mi(sm.op[k1][1] - sm.op[k2][1], L, hL),
-                           mi(sm.op[k1][2] - sm.op[k2][2], L, hL));
-        double u = U_wca(P, r2n) - U_wca(P, r2o);
-        int lo_ = min(m1, m2), hi_ = max(m1, m2);
-        if (hi_ == lo_ + 1 && v.bnext[lo_]) u += U_bond(P, r2n) - U_bond(P, r2o);
-        dU += u;
-    }
-    if (P.eps != 0.0) {
-        // partner-search boxes: [min(old, new) - rc, max(old, new) + rc] per member
-        for (int k = lane; k < n; k += 32) {
-            double lo[3], hi[3];
-            for (int a = 0; a < 3; a++) {
-                double o = sm.op[k][a], u = sm.nu[k][a];
-                lo[a] = sub(fmin(o, u), v.rc + 1e-9);
-                hi[a] = add(fmax(o, u), v.rc + 1e-9);
-            }
-            int c0b[3], ncb[3];
-            cell_box(v, lo, hi, c0b, ncb);
-            for (int a = 0; a < 3; a++) { sm.wbox[k][a] = c0b[a]; sm.wbox[k][3 + a] = ncb[a]; }
-            sm.wpre[k + 1] = ncb[0] * ncb[1] * ncb[2];
-        }
-        __syncwarp();
-        if (lane == 0) { sm.wpre[0] = 0; for (int k = 0; k < n; k++) sm.wpre[k + 1] += sm.wpre[k]; }
-        __syncwarp();
-        const int total = sm.wpre[n];
-        for (int w = lane; w < total; w += 32) {
-            int k = 0;
-            while (sm.wpre[k + 1] <= w) k++;
-            const int c0b[3] = {sm.wbox[k][0], sm.wbox[k][1], sm.wbox[k][2]};
-            const int ncb[3] = {sm.wbox[k][3], sm.wbox[k][4], sm.wbox[k][5]};
-            int cell = box_cell(v, c0b, ncb, w - sm.wpre[k]);
-            const int m = sm.ids[k];
-            int guard = 0;
-            for (int q = v.head[cell]; q >= 0;) {
-                Bead bq = v.bead[q];
-                if (q != m && !sorted_has(sm.sid, n, q)) {
-                    double r2n = norm2(mi(sm.np[k][0] - bq.x, L, hL), mi(sm.np[k][1] - bq.y, L, hL), mi(sm.np[k][2] - bq.z, L, hL));
-                    double r2o = norm2(mi(sm.op[k][0] - bq.x, L, hL), mi(sm.op[k][1] - bq.y, L, hL), mi(sm.op[k][2] - bq.z, L, hL));
-                    if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); pe++; }
-                }
-                q = bq.next;
-                if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
-            }
-        }
-    }
-    // every lane takes lane 0's sum: a butterfly leaves lanes with differently rounded totals
-    dU = __shfl_sync(FULL, warp_sum(dU), 0);
-    *pe_out += warp_sum_i(pe);
-    // Metropolis (Eq. 20): accept iff dU <= -kT ln(1 - u)
-    u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+    int ncols = 0, nzmax = 0;
+    partner_boxes(v, sm, n, lane, &ncols, &nzmax);
+    // Metropolis threshold (Eq. 20): accept iff dU <= -kT ln(1 - u)
+    const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
     const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
-    const bool acc = dU <= thr;
+    bool acc;
+    int pe = 0;
+    if (PREC == 1) {
+        // binary32 energy change; decided in binary64 only within the rigorous error band
+        float d32 = 0.0f, m32 = 0.0f;
+        int T = 0;
+        energy<true>(v, sm, n, lane, ncols, nzmax, nullptr, &d32, &m32, &T, &pe);
+        const double band = 2.0 * (double)(64 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
+        if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
+            acc = (double)d32 <= thr;
+        } else {
+            double d64 = 0.0;
+            int pe2 = 0;
+            energy<false>(v, sm, n, lane, ncols, nzmax, &d64, nullptr, nullptr, nullptr, &pe2);
+            acc = d64 <= thr;
+            (*recheck_out)++;
+        }
+    } else {
+        double d64 = 0.0;
+        energy<false>(v, sm, n, lane, ncols, nzmax, &d64, nullptr, nullptr, nullptr, &pe);
+        acc = d64 <= thr;
+    }
+    *pe_out += pe;
     if (!acc) return REJECT;
     // commit: positions, image counters, then cell-list moves (lane 0, in support order)
     for (int k = lane; k < n; k += 32) {
-        int m = sm.ids[k];
+        const int m = sm.ids[k];
         v.bead[m].x = sm.np[k][0]; v.bead[m].y = sm.np[k][1]; v.bead[m].z = sm.np[k][2];
         if (sm.dimg[k] != pack_img(0, 0, 0)) {
             int dd[3];
@@ -483,17 +656,17 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     __syncwarp();
     if (lane == 0) {
         for (int k = 0; k < n; k++) {
-            int m = sm.ids[k];
-            int oc = cell_lin(v, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
-            int ncl = cell_lin(v, sm.np[k][0], sm.np[k][1], sm.np[k][2]);
+            const int m = sm.ids[k];
+            const int oc = cell_lin(v, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
+            const int ncl = cell_lin(v, sm.np[k][0], sm.np[k][1], sm.np[k][2]);
             if (oc == ncl) continue;
-            int pr = v.prev[m], nx = v.bead[m].next;
+            const int pr = v.prev[m], nx = v.bead[m].next;
             if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
             if (nx >= 0) v.prev[nx] = pr;
-            int h = v.head[ncl];
-            v.bead[m].next = h;
+            const int hd = v.head[ncl];
+            v.bead[m].next = hd;
             v.prev[m] = -1;
-            if (h >= 0) v.prev[h] = m;
+            if (hd >= 0) v.prev[hd] = m;
             v.head[ncl] = m;
         }
     }
@@ -521,14 +694,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l
     }
     const int cell = c[0] + G * (c[1] + G * c[2]);
     double carry = v.carry_q[Ly.carry_off + cell];
-    int att = 0, acc = 0, def = 0, pe = 0;
-    long long bu = 0;
+    int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
+    long long bu = 0, moved = 0;
     for (int t = 0; t < cnt; t++) {
         const int j = v.q_slots[start + t];
         const double lam = carry > 0.0 ? carry : v.slot_lam[j];
         const int i = v.slot_bead[j];
         int n = 0;
-        int r = warp_attempt<PREC>(v, sm, l, j, i, lam, sweep, rlo, rhi, lane, &n, &pe);
+        int r = warp_attempt<PREC>(v, sm, l, j, i, lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks);
         __syncwarp();
         if (r == DEFER) {
             if (lane == 0) v.defer[start + t] = 1;
@@ -537,7 +710,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l
         }
         att++;
         bu += n;
-        if (r == ACCEPT) acc++;
+        if (r == ACCEPT) { acc++; moved += n; }
         if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
         carry = (r == ACCEPT) ? 0.0 : lam;
     }
@@ -549,6 +722,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l
         atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
         atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
+        atomicAdd(&v.ctr[C_CBU], (unsigned long long)bu);
+        atomicAdd(&v.ctr[C_CMOVED], (unsigned long long)moved);
+        atomicAdd(&v.ctr[C_CPE], (unsigned long long)pe);
+        if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
     }
 }
 void launch_colour(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s) {

@@ -91,6 +91,8 @@ class Stats(ctypes.Structure):
         ("rechecks", ctypes.c_int64), ("partner_evals", ctypes.c_int64),
         ("sim_time", ctypes.c_double), ("sweeps", ctypes.c_int64), ("n_layers", ctypes.c_int64),
         ("dt_move", ctypes.c_double), ("p_fourier", ctypes.c_double), ("error_flags", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int64), ("conc_bead_updates", ctypes.c_int64),
+        ("conc_moved_beads", ctypes.c_int64), ("conc_partner_evals", ctypes.c_int64),
     ]
 
 

@@ -122,15 +122,28 @@ def test_dilute_chains_concurrent(precision):
     assert sum(st.attempts) > 10 * s.n_beads
 
 
-def test_dense_small_box_forces_deferrals_and_cell_moves():
+@pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])
+def test_dense_small_box_forces_deferrals_and_cell_moves(precision):
     """Semi-dilute chains in a small box, regions barely larger than a move, n_cap small:
-    many deferrals, supports above the cap, beads crossing fine cells and box faces."""
+    many deferrals, supports above the cap, beads crossing fine cells and box faces. In mixed
+    precision the binary32 energy changes decide outside the error band, binary64 inside it."""
     s = I.make_system([16] * 12, 0, I.box_for_volume_fraction(192, 0.05), seed=6)
-    p = wmcd.default_params(s.n_beads, s.box_L, seed=21, n_cap=3, A0=0.8)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=21, n_cap=3, A0=0.8, precision=precision)
     p["grid_layer"] = [4] + [0] * 15
     gpu, ref = run_pair(p, s, 25)
     st = ref.stats()
     assert st.deferred[0] > 0 and st.deferred[0] < st.attempts[0]
+
+
+def test_mixed_precision_many_moves_dense():
+    """Thousands of concurrent moves in a dense system: identical decisions to the binary64
+    oracle, with some moves re-decided in binary64 (counted)."""
+    s = I.make_system([32] * 48, 0, I.box_for_volume_fraction(1536, 0.08), seed=12)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=5, precision=wmcd.MIXED, colour_K=3)
+    p["grid_layer"] = [6] + [0] * 15
+    gpu, ref = run_pair(p, s, 40, trace_every=4)
+    st = gpu.stats()
+    assert st.conc_bead_updates > 0
 
 
 def test_free_spheres_and_fene():
