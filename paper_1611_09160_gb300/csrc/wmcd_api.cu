@@ -334,7 +334,37 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     double* d_cdf = nullptr;
     ok = ok && !dalloc(h, &d_modes, modes.size() + 3) && !dalloc(h, &d_cdf, cdf.size() + 1);
     ok = ok && !dalloc(h, &h->staging, 3 * N);
+    // region assignment for staging: per-axis tables fine cell -> queue coordinate (-1 = the
+    // cell straddles two regions of the colour), per layer and colour offset
+    std::vector<int> tab((size_t)nL * P.colour_K * P.grid_f, -1);
+    int64_t nq_max = 1;
+    double expect_region = 0.0;
+    for (int l = 0; l < nL; l++) {
+        const int G = v.layer[l].G, K = P.colour_K, Gf = P.grid_f;
+        if (G == 0) continue;
+        nq_max = std::max<int64_t>(nq_max, (int64_t)(G / K) * (G / K) * (G / K));
+        if (expect_region == 0.0) expect_region = (double)N * std::pow((double)K / G, 3.0);
+        for (int c = 0; c < G; c++) {
+            const int64_t lo = ceildiv((2 * (int64_t)c - (K - 1)) * Gf, 2 * (int64_t)G);
+            const int64_t hi = floordiv((2 * (int64_t)c + 2 + (K - 1)) * Gf, 2 * (int64_t)G) - 1;
+            for (int64_t u = lo; u <= hi; u++) {
+                const int64_t f = ((u % Gf) + Gf) % Gf;
+                tab[((size_t)l * K + c % K) * Gf + f] = c / K;
+            }
+        }
+    }
+    int* d_tab = nullptr;
+    ok = ok && !dalloc(h, &v.rkey, N) && !dalloc(h, &v.rlist, N) && !dalloc(h, &v.rcount, nq_max) &&
+         !dalloc(h, &v.rstart, nq_max) && !dalloc(h, &v.rfill, nq_max) && !dalloc(h, &d_tab, tab.size());
     if (!ok) { wmcd_destroy(H); return WMCD_ENOMEM; }
+    v.axis_tab = d_tab;
+    {
+        // staging capacity per warp: room for 16x the average bead count of a layer-0 region
+        int cap = 256;
+        while (cap < 1024 && cap < 16.0 * expect_region) cap *= 2;
+        v.stage_cap = cap;
+    }
+    cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     v.tr_pw_cap = pw_cap;
     v.modes = d_modes;
     v.mode_cdf = d_cdf;
@@ -385,10 +415,10 @@ static void run_sweep(Handle* h, cudaStream_t s) {
         if (v.layer[l].G > 0) {
             { ProfScope ps(h, 4, s); launch_bucket(v, l, (int)M, s); }
             const int nc = v.K * v.K * v.K;
-            for (int c = 0; c < nc; c++) { ProfScope ps(h, 0, s); launch_colour(v, l, c, sw, s); }
+            for (int c = 0; c < nc; c++) { ProfScope ps(h, 0, s); launch_colour_staged(v, l, c, sw, s); }
             { ProfScope ps(h, 4, s); launch_defer_compact(v, (int)M, s); }
             { ProfScope ps(h, 1, s); launch_serial(v, l, sw, 1, (int)M, s); }
-            h->launches += 4 + nc + 2;
+            h->launches += 4 + 4 * nc + 2;
         } else {
             ProfScope ps(h, 1, s);
             launch_serial(v, l, sw, 0, (int)M, s);

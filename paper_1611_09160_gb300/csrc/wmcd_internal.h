@@ -20,6 +20,9 @@ constexpr int kNCap = 64;          // largest support of a concurrent (warp) mov
 constexpr int kWarpsPerBlock = 4;  // concurrent kernel: one warp per queue
 constexpr int kSerialThreads = 512;
 constexpr int kMaxWalk = 1 << 22;  // bound on list-walk iterations inside one move
+constexpr int kStageWarps = 2;     // staged concurrent kernel: warps per block
+constexpr int kCandCap = 256;      // interaction candidates of one staged move held in shared memory
+constexpr int kSlotChunk = 32;     // slot parameters prepared per chunk
 
 enum Outcome { ACCEPT = 1, REJECT = 2, DEFER = 3 };
 
@@ -87,6 +90,14 @@ struct SimView {
     // counters and errors
     unsigned long long* ctr;
     int* err;
+    // staging of the beads of each region of one colour (concurrent kernel)
+    int* rkey;                   // per bead: queue whose region interior holds it, -1 = none
+    int* rcount;                 // per queue
+    int* rstart;
+    int* rfill;
+    int* rlist;                  // bead ids grouped by queue
+    const int* axis_tab;         // per layer, per colour offset, per fine cell: queue coordinate or -1
+    int stage_cap;               // beads a warp can stage in shared memory
     // serial-phase scratch (n up to N)
     int* s_ids;
     double* s_d;                 // 4 per member: offset from the centre and its square
@@ -116,6 +127,8 @@ void launch_cl_rebuild(const SimView& v, cudaStream_t s, const int* flag);
 void launch_slots(const SimView& v, int l, uint64_t sweep, int M, cudaStream_t s);
 void launch_bucket(const SimView& v, int l, int M, cudaStream_t s);
 void launch_colour(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s);
+void launch_colour_staged(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s);
+size_t staged_smem_bytes(int cap);
 void launch_defer_compact(const SimView& v, int M, cudaStream_t s);
 void launch_serial(const SimView& v, int l, uint64_t sweep, int use_list, int M, cudaStream_t s);
 void launch_planewave(const SimView& v, int kmode, int kdir, int kacc, uint64_t ctr, int m, int trace_index,

@@ -1182,3 +1182,499 @@ void launch_planewave(const SimView& v, int kmode, int kdir, int kacc, uint64_t 
 }
 
 }  // namespace wmcd
+
+namespace wmcd {
+
+// ======================================================================================
+// Staged concurrent wavelet moves. In a colour phase every queue owns the beads in the fine
+// cells wholly inside its region (no other queue reads or writes them), so its warp copies
+// them into shared memory once, runs all its moves there and writes them back at the end.
+// Beads are assigned to regions by a counting sort over all beads before each colour phase.
+// ======================================================================================
+__global__ void k_region_count(SimView v, int l, int colour) {
+    const int K = v.K, Gf = v.Gf, Q = v.layer[l].G / K;
+    const int ox = colour % K, oy = (colour / K) % K, oz = colour / (K * K);
+    const int* tab = v.axis_tab + (size_t)l * K * Gf;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
+        const Bead b = v.bead[m];
+        const int qx = tab[ox * Gf + fine_cell(b.x, v.invf, Gf)];
+        const int qy = tab[oy * Gf + fine_cell(b.y, v.invf, Gf)];
+        const int qz = tab[oz * Gf + fine_cell(b.z, v.invf, Gf)];
+        const int key = (qx < 0 || qy < 0 || qz < 0) ? -1 : qx + Q * (qy + Q * qz);
+        v.rkey[m] = key;
+        if (key >= 0) atomicAdd(&v.rcount[key], 1);
+    }
+}
+__global__ void k_region_scatter(SimView v) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
+        const int key = v.rkey[m];
+        if (key >= 0) v.rlist[v.rstart[key] + atomicAdd(&v.rfill[key], 1)] = (int)m;
+    }
+}
+
+// pointers into one warp's share of the dynamic shared memory
+struct Stage {
+    double *sx, *sy, *sz;            // staged positions (binary64, wrapped)
+    float *fx, *fy, *fz;             // the same relative to the region origin (binary32 prefilter)
+    int *sid, *scell, *sdim, *stag;  // bead id, fine cell at staging, image change | dirty, support tag
+    int *hkey, *hval;                // bead id -> staged index (open addressing)
+    int *mem, *mimg, *mpart, *cand;  // support (staged indices), image change, bonded partners, candidates
+    double *mnp;                     // new positions of the support
+    float *mnf;                      // new positions relative to the origin
+    int *cj, *ci;                    // slot chunk: slot id, bead
+    double *clam, *cV, *cp, *cthr;   // slot chunk: scale, centre offset, polarisation, threshold
+    int cap, hbits;
+};
+__host__ __device__ inline size_t stage_bytes(int cap) {
+    return (size_t)cap * (3 * 8 + 3 * 4 + 4 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 3 * 4) +
+           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8) + 64;
+}
+__host__ __device__ inline size_t warp_stride(int cap) {
+    size_t per = stage_bytes(cap) > sizeof(WarpSmem) ? stage_bytes(cap) : sizeof(WarpSmem);
+    return (per + 15) & ~(size_t)15;
+}
+__device__ inline Stage stage_carve(char* base, int cap) {
+    Stage S;
+    S.cap = cap;
+    S.hbits = 1;
+    while ((1 << S.hbits) < 2 * cap) S.hbits++;
+    char* p = base;
+    auto take = [&](size_t bytes) { char* q = p; p += (bytes + 7) & ~(size_t)7; return q; };
+    S.sx = (double*)take(8 * cap); S.sy = (double*)take(8 * cap); S.sz = (double*)take(8 * cap);
+    S.mnp = (double*)take(8 * 3 * kNCap);
+    S.clam = (double*)take(8 * kSlotChunk); S.cV = (double*)take(8 * 3 * kSlotChunk);
+    S.cp = (double*)take(8 * 3 * kSlotChunk); S.cthr = (double*)take(8 * kSlotChunk);
+    S.fx = (float*)take(4 * cap); S.fy = (float*)take(4 * cap); S.fz = (float*)take(4 * cap);
+    S.mnf = (float*)take(4 * 3 * kNCap);
+    S.sid = (int*)take(4 * cap); S.scell = (int*)take(4 * cap); S.sdim = (int*)take(4 * cap); S.stag = (int*)take(4 * cap);
+    S.hkey = (int*)take(4 * 2 * cap); S.hval = (int*)take(4 * 2 * cap);
+    S.mem = (int*)take(4 * kNCap); S.mimg = (int*)take(4 * kNCap); S.mpart = (int*)take(4 * 2 * kNCap);
+    S.cand = (int*)take(4 * kCandCap);
+    S.cj = (int*)take(4 * kSlotChunk); S.ci = (int*)take(4 * kSlotChunk);
+    return S;
+}
+__device__ __forceinline__ uint32_t hslot(int id, int bits) { return ((uint32_t)id * 2654435761u) >> (32 - bits); }
+__device__ __forceinline__ int stage_find(const Stage& S, int id) {
+    const uint32_t mask = (1u << S.hbits) - 1u;
+    uint32_t h = hslot(id, S.hbits);
+    for (int probe = 0; probe <= (int)mask; probe++) {
+        const int k = S.hkey[h];
+        if (k == id) return S.hval[h];
+        if (k == -1) return -1;
+        h = (h + 1u) & mask;
+    }
+    return -1;
+}
+// coordinate relative to the region origin o, brought into [0, L)
+__device__ __forceinline__ float local32(double x, double o, double L) {
+    double t = x - o;
+    if (t < 0.0) t += L;
+    else if (t >= L) t -= L;
+    return (float)t;
+}
+
+template <bool F32>
+__device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bool all_cand, int ns, int tag, int lane,
+                             double eps, double* dU64, float* dU32, float* mag32, int* terms, int* pe_out) {
+    const double L = v.L, hL = v.halfL;
+    const Pot& P = v.pot;
+    const Pot32 P32 = pot32(P);
+    // binary32 screen of candidate pairs: local coordinates carry at most eps of rounding each
+    const float hLf = (float)hL, rcf = (float)(v.rc + 2.0 * eps + 1e-6);
+    const float rc2f = rcf * rcf;
+    double a64 = 0.0;
+    float a32 = 0.0f, m32 = 0.0f;
+    int T = 0, pe = 0;
+    auto pair_term = [&](double ax, double ay, double az, double bx, double by, double bz,
+                         double cx, double cy, double cz, double dx, double dy, double dz, bool bonded, bool wca) {
+        // new pair (a, b), old pair (c, d)
+        if (F32) {
+            const float r2n = norm2f(dif32(ax, bx, L, hLf), dif32(ay, by, L, hLf), dif32(az, bz, L, hLf));
+            const float r2o = norm2f(dif32(cx, dx, L, hLf), dif32(cy, dy, L, hLf), dif32(cz, dz, L, hLf));
+            float un, mn, uo, mo;
+            if (wca) { wca32(P32, r2n, un, mn); wca32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
+            if (bonded) { bond32(P32, r2n, un, mn); bond32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
+        } else {
+            const double r2n = norm2(mi(ax - bx, L, hL), mi(ay - by, L, hL), mi(az - bz, L, hL));
+            const double r2o = norm2(mi(cx - dx, L, hL), mi(cy - dy, L, hL), mi(cz - dz, L, hL));
+            double u = 0.0;
+            if (wca) u += U_wca(P, r2n) - U_wca(P, r2o);
+            if (bonded) u += U_bond(P, r2n) - U_bond(P, r2o);
+            a64 += u;
+        }
+    };
+    // external well and bonds to beads outside the support
+    for (int k = lane; k < n; k += 32) {
+        const int t = S.mem[k];
+        const double* nw = &S.mnp[3 * k];
+        if (P.kappa != 0.0) {
+            if (F32) {
+                float un = 0.5f * P32.kappa * norm2f(dif32(nw[0], hL, L, hLf), dif32(nw[1], hL, L, hLf), dif32(nw[2], hL, L, hLf));
+                float uo = 0.5f * P32.kappa * norm2f(dif32(S.sx[t], hL, L, hLf), dif32(S.sy[t], hL, L, hLf), dif32(S.sz[t], hL, L, hLf));
+                a32 += un - uo; m32 += un + uo; T += 2;
+            } else {
+                a64 += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, S.sx[t], S.sy[t], S.sz[t]);
+            }
+        }
+        for (int e = 0; e < 2; e++) {
+            const int tq = S.mpart[2 * k + e];
+            if (tq < 0) continue;                     // no bond, or the partner moves too
+            pair_term(nw[0], nw[1], nw[2], S.sx[tq], S.sy[tq], S.sz[tq], S.sx[t], S.sy[t], S.sz[t], S.sx[tq], S.sy[tq],
+                      S.sz[tq], true, false);
+        }
+    }
+    // pairs inside the support
+    const int npairs = n * (n - 1) / 2;
+    for (int w = lane; w < npairs; w += 32) {
+        int a = (int)((sqrtf(8.0f * w + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > w) a--;
+        while ((a + 1) * (a + 2) / 2 <= w) a++;
+        const int k1 = w - a * (a + 1) / 2, k2 = a + 1;
+        const int t1 = S.mem[k1], t2 = S.mem[k2];
+        const int m1 = S.sid[t1], m2 = S.sid[t2];
+        const int lo_ = min(m1, m2), hi_ = max(m1, m2);
+        const bool bonded = hi_ == lo_ + 1 && v.bnext[lo_];
+        const double* n1 = &S.mnp[3 * k1];
+        const double* n2 = &S.mnp[3 * k2];
+        pair_term(n1[0], n1[1], n1[2], n2[0], n2[1], n2[2], S.sx[t1], S.sy[t1], S.sz[t1], S.sx[t2], S.sy[t2], S.sz[t2],
+                  bonded, true);
+    }
+    // WCA with the interaction candidates outside the support (binary32 distance screen first)
+    if (P.eps != 0.0) {
+        const int nsrc = all_cand ? ns : nc;
+        const int total = n * nsrc;
+        for (int w = lane; w < total; w += 32) {
+            const int k = w / nsrc;
+            const int c = all_cand ? (w - k * nsrc) : S.cand[w - k * nsrc];
+            if (S.stag[c] == tag) continue;           // a support member (only when scanning everything)
+            const int t = S.mem[k];
+            const float ex = S.fx[c] - S.mnf[3 * k], ey = S.fy[c] - S.mnf[3 * k + 1], ez = S.fz[c] - S.mnf[3 * k + 2];
+            const float gx = S.fx[c] - S.fx[t], gy = S.fy[c] - S.fy[t], gz = S.fz[c] - S.fz[t];
+            if (!(ex * ex + ey * ey + ez * ez < rc2f) && !(gx * gx + gy * gy + gz * gz < rc2f)) continue;
+            const double* nw = &S.mnp[3 * k];
+            pair_term(nw[0], nw[1], nw[2], S.sx[c], S.sy[c], S.sz[c], S.sx[t], S.sy[t], S.sz[t], S.sx[c], S.sy[c], S.sz[c],
+                      false, true);
+            pe++;
+        }
+    }
+    const unsigned FULL = 0xffffffffu;
+    if (F32) {
+        float s = a32, mm = m32;
+        int tt = T;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(FULL, s, o);
+            mm += __shfl_xor_sync(FULL, mm, o);
+            tt += __shfl_xor_sync(FULL, tt, o);
+        }
+        *dU32 = __shfl_sync(FULL, s, 0);
+        *mag32 = __shfl_sync(FULL, mm, 0);
+        *terms = __shfl_sync(FULL, tt, 0);
+    } else {
+        *dU64 = __shfl_sync(FULL, warp_sum(a64), 0);
+    }
+    *pe_out = warp_sum_i(pe);
+}
+
+// One move of a staged queue. The slot's centre offset V, polarisation p and Metropolis
+// threshold were prepared in the chunk arrays at index c.
+template <int PREC>
+__device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const double org[3], double side, int l, int c,
+                             double lam, const int64_t rlo[3], const int64_t rhi[3], int lane, int tag, int* n_out,
+                             int* pe_out, int* recheck_out) {
+    const unsigned FULL = 0xffffffffu;
+    const double L = v.L, hL = v.halfL;
+    const int Gf = v.Gf;
+    const int ti = stage_find(S, S.ci[c]);
+    if (ti < 0) return DEFER;                     // the picked bead lies outside the region interior
+    // centre b = r_i + lam V (Appendix D), wrapped
+    double b[3];
+    b[0] = wrap(add(S.sx[ti], mul(lam, S.cV[3 * c])), L, nullptr);
+    b[1] = wrap(add(S.sy[ti], mul(lam, S.cV[3 * c + 1])), L, nullptr);
+    b[2] = wrap(add(S.sz[ti], mul(lam, S.cV[3 * c + 2])), L, nullptr);
+    const double R = add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
+    for (int a = 0; a < 3; a++) {
+        const int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
+        const int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
+        if (!range_inside(t0, t1, rlo[a], rhi[a], Gf)) return DEFER;
+    }
+    // support and interaction candidates in one pass over the staged beads
+    const double eps = 1e-6 * (side + lam) + 1e-9;
+    const double lam2 = mul(lam, lam);
+    const float lin = (float)((lam - eps) * (lam - eps)), lout = (float)((lam + eps) * (lam + eps));
+    const float rcand = (float)((R + eps) * (R + eps));
+    const float bx = local32(b[0], org[0], L), by = local32(b[1], org[1], L), bz = local32(b[2], org[2], L);
+    int n = 0, nc = 0;
+    for (int base = 0; base < ns; base += 32) {
+        const int t = base + lane;
+        bool in = false, cd = false;
+        if (t < ns) {
+            const float dx = S.fx[t] - bx, dy = S.fy[t] - by, dz = S.fz[t] - bz;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < lin) in = true;
+            else if (d2 <= lout) {
+                const double e2 = norm2(mi(sub(S.sx[t], b[0]), L, hL), mi(sub(S.sy[t], b[1]), L, hL), mi(sub(S.sz[t], b[2]), L, hL));
+                in = e2 < lam2;
+            }
+            cd = !in && d2 < rcand;
+        }
+        const unsigned mi_ = __ballot_sync(FULL, in), mc = __ballot_sync(FULL, cd);
+        const unsigned below = (1u << lane) - 1u;
+        if (in) { const int s = n + __popc(mi_ & below); if (s < kNCap) S.mem[s] = t; }
+        if (cd) { const int s = nc + __popc(mc & below); if (s < kCandCap) S.cand[s] = t; }
+        n += __popc(mi_);
+        nc += __popc(mc);
+    }
+    *n_out = n;
+    if (n > v.n_cap) return DEFER;
+    if (n == 0) return ACCEPT;                    // no bead moves; dU = 0 passes
+    const bool all_cand = nc > kCandCap;
+    // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
+    const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+    const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
+    bool bad = false;
+    for (int k = lane; k < n; k += 32) {
+        const int t = S.mem[k];
+        S.stag[t] = tag;
+        double d[3] = {mi(sub(S.sx[t], b[0]), L, hL), mi(sub(S.sy[t], b[1]), L, hL), mi(sub(S.sz[t], b[2]), L, hL)};
+        const double d2 = norm2(d[0], d[1], d[2]);
+        double dl[3];
+        if (PREC == 0) wavelet_disp64(d, d2, lam, Aw, p, dl);
+        else wavelet_disp32(d, lam, Aw, p, dl);
+        int im[3] = {0, 0, 0};
+        const double o[3] = {S.sx[t], S.sy[t], S.sz[t]};
+        for (int a = 0; a < 3; a++) {
+            S.mnp[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+            S.mnf[3 * k + a] = local32(S.mnp[3 * k + a], org[a], L);
+        }
+        S.mimg[k] = pack_img(im[0], im[1], im[2]);
+    }
+    __syncwarp();
+    // bonded partners: staged (inside the region) or the move is deferred
+    for (int k = lane; k < n; k += 32) {
+        const int m = S.sid[S.mem[k]];
+        for (int e = 0; e < 2; e++) {
+            const int q = e ? m + 1 : m - 1;
+            int tq = -1;
+            if (q >= 0 && q < v.N && (e ? v.bnext[m] : v.bnext[q])) {
+                tq = stage_find(S, q);
+                if (tq < 0) bad = true;
+                else if (S.stag[tq] == tag) tq = -2;   // moves with the support
+            }
+            S.mpart[2 * k + e] = tq;
+        }
+    }
+    if (__any_sync(FULL, bad)) return DEFER;
+    __syncwarp();
+    const double thr = S.cthr[c];
+    bool acc;
+    int pe = 0;
+    if (PREC == 1) {
+        float d32 = 0.0f, m32 = 0.0f;
+        int T = 0;
+        stage_energy<true>(v, S, n, nc, all_cand, ns, tag, lane, eps, nullptr, &d32, &m32, &T, &pe);
+        const double band = 2.0 * (double)(64 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
+        if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
+            acc = (double)d32 <= thr;
+        } else {
+            double d64 = 0.0;
+            int pe2 = 0;
+            stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, eps, &d64, nullptr, nullptr, nullptr, &pe2);
+            acc = d64 <= thr;
+            (*recheck_out)++;
+        }
+    } else {
+        double d64 = 0.0;
+        stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, eps, &d64, nullptr, nullptr, nullptr, &pe);
+        acc = d64 <= thr;
+    }
+    *pe_out += pe;
+    if (!acc) return REJECT;
+    for (int k = lane; k < n; k += 32) {
+        const int t = S.mem[k];
+        S.sx[t] = S.mnp[3 * k]; S.sy[t] = S.mnp[3 * k + 1]; S.sz[t] = S.mnp[3 * k + 2];
+        S.fx[t] = S.mnf[3 * k]; S.fy[t] = S.mnf[3 * k + 1]; S.fz[t] = S.mnf[3 * k + 2];
+        // accumulate the image change (3 fields of 8 bits, offset 128) and mark dirty (bit 24)
+        int dd[3], cur = S.sdim[t];
+        unpack_img(S.mimg[k], dd);
+        const int ax = ((cur & 0xff) - 128) + dd[0], ay = (((cur >> 8) & 0xff) - 128) + dd[1],
+                  az = (((cur >> 16) & 0xff) - 128) + dd[2];
+        S.sdim[t] = (ax + 128) | ((ay + 128) << 8) | ((az + 128) << 16) | (1 << 24);
+    }
+    __syncwarp();
+    return ACCEPT;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, int l, int colour, uint64_t sweep) {
+    extern __shared__ __align__(16) char dsm[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const LayerDev& Ly = v.layer[l];
+    const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
+    const int q = blockIdx.x * kStageWarps + wib;
+    if (q >= nq) return;
+    const int key = colour * nq + q;
+    const int start = v.q_start[key], cnt = v.q_count[key];
+    if (cnt == 0) return;
+    const int cap = v.stage_cap;
+    char* base = dsm + (size_t)wib * warp_stride(cap);
+    const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
+    int64_t rlo[3], rhi[3];
+    for (int a = 0; a < 3; a++) {
+        rlo[a] = ceildiv((2 * (int64_t)c[a] - (K - 1)) * v.Gf, 2 * (int64_t)G);
+        rhi[a] = floordiv((2 * (int64_t)c[a] + 2 + (K - 1)) * v.Gf, 2 * (int64_t)G) - 1;
+    }
+    const int cell = c[0] + G * (c[1] + G * c[2]);
+    double carry = v.carry_q[Ly.carry_off + cell];
+    int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
+    long long bu = 0, moved = 0;
+    const int rs = v.rstart[q], ns = v.rcount[q];
+    if (ns > cap) {
+        // region too full for shared memory: the global-memory path
+        WarpSmem& sm = *(WarpSmem*)base;
+        for (int t = 0; t < cnt; t++) {
+            const int j = v.q_slots[start + t];
+            const double lam = carry > 0.0 ? carry : v.slot_lam[j];
+            int n = 0;
+            int r = warp_attempt<PREC>(v, sm, l, j, v.slot_bead[j], lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks);
+            __syncwarp();
+            if (r == DEFER) { if (lane == 0) v.defer[start + t] = 1; def++; continue; }
+            att++; bu += n;
+            if (r == ACCEPT) { acc++; moved += n; }
+            if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
+            carry = (r == ACCEPT) ? 0.0 : lam;
+        }
+    } else {
+        Stage S = stage_carve(base, cap);
+        const int H = 1 << S.hbits;
+        for (int h = lane; h < H; h += 32) S.hkey[h] = -1;
+        __syncwarp();
+        const double hf = v.L / v.Gf;
+        const double org[3] = {(double)rlo[0] * hf, (double)rlo[1] * hf, (double)rlo[2] * hf};
+        const double side = (double)(rhi[0] - rlo[0] + 1) * hf;
+        for (int t = lane; t < ns; t += 32) {
+            const int m = v.rlist[rs + t];
+            const Bead bb = v.bead[m];
+            S.sx[t] = bb.x; S.sy[t] = bb.y; S.sz[t] = bb.z;
+            S.fx[t] = local32(bb.x, org[0], v.L); S.fy[t] = local32(bb.y, org[1], v.L); S.fz[t] = local32(bb.z, org[2], v.L);
+            S.sid[t] = m;
+            S.scell[t] = cell_lin(v, bb.x, bb.y, bb.z);
+            S.sdim[t] = 128 | (128 << 8) | (128 << 16);
+            S.stag[t] = 0;
+            const uint32_t mask = (uint32_t)H - 1u;
+            uint32_t h = hslot(m, S.hbits);
+            for (int probe = 0; probe < H; probe++) {
+                const int prev = atomicCAS(&S.hkey[h], -1, m);
+                if (prev == -1) { S.hval[h] = t; break; }
+                h = (h + 1u) & mask;
+            }
+        }
+        __syncwarp();
+        int tag = 0;
+        for (int c0 = 0; c0 < cnt; c0 += kSlotChunk) {
+            // slot parameters of the chunk, one lane per slot: V, p by rejection (Appendix D)
+            // and the Metropolis threshold -kT ln(1 - u) (Eq. 20)
+            const int t = c0 + lane;
+            if (t < cnt) {
+                const int j = v.q_slots[start + t];
+                S.cj[lane] = j;
+                S.ci[lane] = v.slot_bead[j];
+                S.clam[lane] = v.slot_lam[j];
+                double V[3] = {0.0, 0.0, 0.0}, pp[3] = {0.0, 0.0, 1.0};
+                for (uint32_t a = 0; a < 64; a++) {
+                    const u4 w = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
+                    const double x = sym(w.x), y = sym(w.y), z = sym(w.z);
+                    if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+                }
+                for (uint32_t a = 0; a < 64; a++) {
+                    const u4 w = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
+                    const double x = sym(w.x), y = sym(w.y), z = sym(w.z), qq = norm2(x, y, z);
+                    if (qq <= 1.0 && qq > 0.0) { pp[0] = x; pp[1] = y; pp[2] = z; break; }
+                }
+                const double r = sqr_t(norm2(pp[0], pp[1], pp[2]));
+                for (int a = 0; a < 3; a++) { S.cV[3 * lane + a] = V[a]; S.cp[3 * lane + a] = dvd(pp[a], r); }
+                const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+                S.cthr[lane] = -v.kT * log(1.0 - u53(w.x, w.y));
+            }
+            __syncwarp();
+            const int cend = min(kSlotChunk, cnt - c0);
+            for (int cc = 0; cc < cend; cc++) {
+                const int j = S.cj[cc];
+                const double lam = carry > 0.0 ? carry : S.clam[cc];
+                int n = 0;
+                tag++;
+                const int r = stage_attempt<PREC>(v, S, ns, org, side, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks);
+                __syncwarp();
+                if (r == DEFER) { if (lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
+                att++; bu += n;
+                if (r == ACCEPT) { acc++; moved += n; }
+                if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
+                carry = (r == ACCEPT) ? 0.0 : lam;
+            }
+            __syncwarp();
+        }
+        // write back the moved beads; cell-list moves by lane 0 in staged order
+        for (int t = lane; t < ns; t += 32) {
+            const int dm = S.sdim[t];
+            if (!(dm & (1 << 24))) continue;
+            const int m = S.sid[t];
+            v.bead[m].x = S.sx[t]; v.bead[m].y = S.sy[t]; v.bead[m].z = S.sz[t];
+            const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
+            if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            for (int t = 0; t < ns; t++) {
+                if (!(S.sdim[t] & (1 << 24))) continue;
+                const int m = S.sid[t];
+                const int oc = S.scell[t], ncl = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
+                if (oc == ncl) continue;
+                const int pr = v.prev[m], nx = v.bead[m].next;
+                if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+                if (nx >= 0) v.prev[nx] = pr;
+                const int hd = v.head[ncl];
+                v.bead[m].next = hd;
+                v.prev[m] = -1;
+                if (hd >= 0) v.prev[hd] = m;
+                v.head[ncl] = m;
+            }
+        }
+        __syncwarp(FULL);
+    }
+    if (lane == 0) {
+        v.carry_q[Ly.carry_off + cell] = carry;
+        atomicAdd(&v.ctr[C_ATT + l], (unsigned long long)att);
+        atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc);
+        atomicAdd(&v.ctr[C_DEF + l], (unsigned long long)def);
+        atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
+        atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+        atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
+        atomicAdd(&v.ctr[C_CBU], (unsigned long long)bu);
+        atomicAdd(&v.ctr[C_CMOVED], (unsigned long long)moved);
+        atomicAdd(&v.ctr[C_CPE], (unsigned long long)pe);
+        if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
+    }
+}
+
+size_t staged_smem_bytes(int cap) { return (size_t)kStageWarps * warp_stride(cap); }
+
+void launch_colour_staged(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s) {
+    const int G = v.layer[l].G, Q = G / v.K, nq = Q * Q * Q;
+    const int gb = (int)std::min<int64_t>((v.N + 255) / 256, 152 * 16);
+    cudaMemsetAsync(v.rcount, 0, sizeof(int) * nq, s);
+    cudaMemsetAsync(v.rfill, 0, sizeof(int) * nq, s);
+    k_region_count<<<gb, 256, 0, s>>>(v, l, colour);
+    k_scan_single<<<1, 1024, 0, s>>>(v.rcount, v.rstart, nq);
+    k_region_scatter<<<gb, 256, 0, s>>>(v);
+    const size_t smem = staged_smem_bytes(v.stage_cap);
+    const int blocks = (nq + kStageWarps - 1) / kStageWarps;
+    if (v.precision == 0) {
+        cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_colour_staged<0><<<blocks, kStageWarps * 32, smem, s>>>(v, l, colour, sweep);
+    } else {
+        cudaFuncSetAttribute(k_colour_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_colour_staged<1><<<blocks, kStageWarps * 32, smem, s>>>(v, l, colour, sweep);
+    }
+}
+
+}  // namespace wmcd
