@@ -137,6 +137,12 @@ int wmcd_stats(wmcd_handle* h, wmcd_stats_t* out, void* stream);
  * of `cap` entries; *count receives the number of slots. Synchronises `stream`. */
 int wmcd_trace(wmcd_handle* h, int layer, uint8_t* out, int32_t* n, int64_t cap, int64_t* count, void* stream);
 
+/* Energy change behind each wavelet decision of the last sweep, layer `layer` (host buffer of
+ * `cap` doubles, *count receives the number of slots; 0 where the support was empty). A
+ * deferred slot records the value of its serial attempt. In mixed precision the value is the
+ * binary32 sum when that decided, the binary64 recheck otherwise. Synchronises `stream`. */
+int wmcd_trace_du(wmcd_handle* h, int layer, double* out, int64_t cap, int64_t* count, void* stream);
+
 /* Checkpoint: the state is positions, image counters, carries, the sweep and plane-wave
  * call counters and the statistics. wmcd_state_size gives the byte size; get writes it to
  * a host buffer, set restores it. With the counter-based random stream a restored run

@@ -73,6 +73,7 @@ def _load():
         "oracle_stats": ([P, P], ctypes.c_int),
         "oracle_trace_layer": ([P, ctypes.c_int, P, P, I64], I64),
         "oracle_trace_pw": ([P, P, P, I64], I64),
+        "oracle_trace_du": ([P, ctypes.c_int, P, I64], I64),
         "oracle_philox": ([P, P, P], None),
         "oracle_phitilde": ([D], D),
         "oracle_moment": ([ctypes.c_int], D),
@@ -165,6 +166,12 @@ class Oracle:
         nn = np.zeros(cap, dtype=np.int32)
         m = self._lib.oracle_trace_layer(self.h, int(l), _ptr(out), _ptr(nn), cap)
         return out[:m].copy(), nn[:m].copy()
+
+    def trace_du(self, l: int):
+        cap = 4 * self.n + 16
+        out = np.zeros(cap)
+        m = self._lib.oracle_trace_du(self.h, int(l), _ptr(out), cap)
+        return out[:m].copy()
 
     def trace_pw(self):
         cap = 1 << 16

@@ -370,6 +370,8 @@ struct Sim {
     OStats st;
     std::vector<std::vector<uint8_t>> tr_out;
     std::vector<std::vector<int32_t>> tr_n;
+    std::vector<std::vector<double>> tr_du;
+    double last_du = 0.0;
     std::vector<uint8_t> tr_pw_out;
     std::vector<int32_t> tr_pw_mode;
     // scratch
@@ -575,6 +577,7 @@ static bool point_inside(const Sim& s, const Region& Rg, const double* p) {
 // Returns ACCEPT, REJECT or DEFER; n receives the number of beads in the support.
 static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, const Region* Rg, int* n_out) {
     const uint64_t sw = s.sweep;
+    s.last_du = 0.0;
     // centre: b = r_i + lam V, V uniform in the unit ball (wrapped into the box)
     double V[3], b[3];
     ball_point(s, K_VB, l, sw, j, V, false);
@@ -623,6 +626,7 @@ static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, con
         }
     }
     double dU = n > 0 ? delta_U(s, S, newp) : 0.0;
+    s.last_du = dU;
     U4 w = s.rng.draw(K_ACC, l, sw, j, 0);
     bool acc = metropolis(s, dU, u53(w.v[0], w.v[1]));
     if (acc) {
@@ -665,10 +669,12 @@ static void run_layer(Sim& s, int l) {
     for (int64_t j = 0; j < M; j++) slot_draw(s, l, sw, (uint32_t)j, &lam[j], &bead[j]);
     s.tr_out[l].assign(M, 0);
     s.tr_n[l].assign(M, 0);
+    s.tr_du[l].assign(M, 0.0);
     std::vector<int64_t> serial;
     auto record = [&](int64_t j, int r, int n, bool deferred) {
         s.tr_out[l][j] = (uint8_t)((r == ACCEPT ? 1 : 2) | (deferred ? 4 : 0));
         s.tr_n[l][j] = n;
+        s.tr_du[l][j] = s.last_du;
         s.st.attempts[l]++;
         s.st.bead_updates += n;
         if (r == ACCEPT) { s.st.accepts[l]++; s.st.accepted_total++; }
@@ -923,6 +929,7 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     s.carry_serial.assign(nL, 0.0);
     s.tr_out.resize(nL);
     s.tr_n.resize(nL);
+    s.tr_du.resize(nL);
     // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2pi)^3 = 1/105)
     double A02 = P.A0 * P.A0, la2 = LAMBDA_A * LAMBDA_A;
     if (P.planewave_mode == 1) s.dt_move = (6.0 * A02 * la2) / (105.0 * (double)s.N);
@@ -994,6 +1001,14 @@ int64_t oracle_trace_layer(void* h, int l, uint8_t* out, int32_t* n, int64_t cap
     if (l < 0 || l >= (int)s.layers.size()) return -1;
     int64_t M = (int64_t)s.tr_out[l].size();
     for (int64_t j = 0; j < M && j < cap; j++) { out[j] = s.tr_out[l][j]; n[j] = s.tr_n[l][j]; }
+    return M;
+}
+// energy change of each wavelet slot of the last sweep (0 when nothing moved)
+int64_t oracle_trace_du(void* h, int l, double* out, int64_t cap) {
+    Sim& s = *(Sim*)h;
+    if (l < 0 || l >= (int)s.layers.size()) return -1;
+    int64_t M = (int64_t)s.tr_du[l].size();
+    for (int64_t j = 0; j < M && j < cap; j++) out[j] = s.tr_du[l][j];
     return M;
 }
 int64_t oracle_trace_pw(void* h, uint8_t* out, int32_t* mode, int64_t cap) {

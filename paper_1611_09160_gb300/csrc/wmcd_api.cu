@@ -322,7 +322,7 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     ok = ok && !dalloc(h, &v.q_count, keys_max) && !dalloc(h, &v.q_start, keys_max) && !dalloc(h, &v.q_fill, keys_max);
     ok = ok && !dalloc(h, &v.serial_count, 4) && !dalloc(h, &v.carry_q, carry_total) &&
          !dalloc(h, &v.carry_serial, kMaxLayers);
-    ok = ok && !dalloc(h, &v.tr_out, tr_total) && !dalloc(h, &v.tr_n, tr_total) && !dalloc(h, &v.tr_pw_out, pw_cap) &&
+    ok = ok && !dalloc(h, &v.tr_out, tr_total) && !dalloc(h, &v.tr_n, tr_total) && !dalloc(h, &v.tr_du, tr_total) && !dalloc(h, &v.tr_pw_out, pw_cap) &&
          !dalloc(h, &v.tr_pw_mode, pw_cap) && !dalloc(h, &v.tr_pw_count, 1);
     ok = ok && !dalloc(h, &v.ctr, C_NCTR) && !dalloc(h, &v.err, 1);
     ok = ok && !dalloc(h, &v.s_ids, N) && !dalloc(h, &v.s_d, 4 * N) && !dalloc(h, &v.s_new, 3 * N) &&
@@ -556,6 +556,18 @@ extern "C" int wmcd_trace(wmcd_handle* H, int layer, uint8_t* out, int32_t* n, i
         cudaMemcpyAsync(out, h->v.tr_out + h->v.layer[layer].tr_off, m, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(n, h->v.tr_n + h->v.layer[layer].tr_off, m * sizeof(int), cudaMemcpyDeviceToHost, s);
     }
+    *count = M;
+    return cudaStreamSynchronize(s) == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
+}
+
+extern "C" int wmcd_trace_du(wmcd_handle* H, int layer, double* out, int64_t cap, int64_t* count, void* stream) {
+    if (!H || !out || !count || cap < 0) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    if (layer < 0 || layer >= h->nL) return WMCD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t M = h->sweep == 0 ? 0 : slot_count(h, K_COUNT, layer, h->sweep - 1, h->expect[layer]);
+    const int64_t m = std::min<int64_t>(M, cap);
+    if (m > 0) cudaMemcpyAsync(out, h->v.tr_du + h->v.layer[layer].tr_off, m * sizeof(double), cudaMemcpyDeviceToHost, s);
     *count = M;
     return cudaStreamSynchronize(s) == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
 }

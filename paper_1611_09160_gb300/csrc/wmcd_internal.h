@@ -83,6 +83,7 @@ struct SimView {
     // trace of the last sweep
     uint8_t* tr_out;
     int* tr_n;
+    double* tr_du;               // energy change used for each decision
     uint8_t* tr_pw_out;
     int* tr_pw_mode;
     int* tr_pw_count;

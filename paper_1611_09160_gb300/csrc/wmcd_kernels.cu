@@ -104,6 +104,7 @@ __global__ void k_slots(SimView v, int l, uint64_t sweep, int M) {
     v.slot_bead[j] = (int)pick(w.z, w.w, v.N);
     v.tr_out[Ly.tr_off + j] = 0;
     v.tr_n[Ly.tr_off + j] = 0;
+    v.tr_du[Ly.tr_off + j] = 0.0;
 }
 void launch_slots(const SimView& v, int l, uint64_t sweep, int M, cudaStream_t s) {
     k_slots<<<(M + 255) / 256, 256, 0, s>>>(v, l, sweep, M);
@@ -505,10 +506,11 @@ __device__ void energy(const SimView& v, WarpSmem& sm, int n, int lane, int ncol
 template <int PREC>
 __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i, double lam, uint64_t sweep,
                             const int64_t rlo[3], const int64_t rhi[3], int lane, int* n_out, int* pe_out,
-                            int* recheck_out) {
+                            int* recheck_out, double* du_out) {
     const unsigned FULL = 0xffffffffu;
     const double L = v.L, hL = v.halfL;
     const float hLf = (float)hL;
+    *du_out = 0.0;
     const int Gf = v.Gf;
     // centre b = r_i + lam V (Appendix D), wrapped into the box
     const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
@@ -629,17 +631,20 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
         const double band = 2.0 * (double)(64 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
         if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
             acc = (double)d32 <= thr;
+            *du_out = (double)d32;
         } else {
             double d64 = 0.0;
             int pe2 = 0;
             energy<false>(v, sm, n, lane, ncols, nzmax, &d64, nullptr, nullptr, nullptr, &pe2);
             acc = d64 <= thr;
+            *du_out = d64;
             (*recheck_out)++;
         }
     } else {
         double d64 = 0.0;
         energy<false>(v, sm, n, lane, ncols, nzmax, &d64, nullptr, nullptr, nullptr, &pe);
         acc = d64 <= thr;
+        *du_out = d64;
     }
     *pe_out += pe;
     if (!acc) return REJECT;
@@ -701,7 +706,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l
         const double lam = carry > 0.0 ? carry : v.slot_lam[j];
         const int i = v.slot_bead[j];
         int n = 0;
-        int r = warp_attempt<PREC>(v, sm, l, j, i, lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks);
+        double du = 0.0;
+        int r = warp_attempt<PREC>(v, sm, l, j, i, lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks, &du);
         __syncwarp();
         if (r == DEFER) {
             if (lane == 0) v.defer[start + t] = 1;
@@ -711,7 +717,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l
         att++;
         bu += n;
         if (r == ACCEPT) { acc++; moved += n; }
-        if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
+        if (lane == 0) {
+            v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
+            v.tr_n[Ly.tr_off + j] = n;
+            v.tr_du[Ly.tr_off + j] = du;
+        }
         carry = (r == ACCEPT) ? 0.0 : lam;
     }
     if (lane == 0) {
@@ -832,6 +842,7 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(SimView v, int l, uin
                 att++; acc_n++;
                 v.tr_out[Ly.tr_off + j] = (uint8_t)(1 | (use_list ? 4 : 0));
                 v.tr_n[Ly.tr_off + j] = 0;
+                v.tr_du[Ly.tr_off + j] = 0.0;
                 sh_carry = 0.0;
             }
             __syncthreads();
@@ -923,6 +934,7 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(SimView v, int l, uin
             u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
             const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
             sh_acc = s <= thr;
+            v.tr_du[Ly.tr_off + j] = s;
         }
         __syncthreads();
         const bool acc = sh_acc;
@@ -1380,8 +1392,9 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
 template <int PREC>
 __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const double org[3], double side, int l, int c,
                              double lam, const int64_t rlo[3], const int64_t rhi[3], int lane, int tag, int* n_out,
-                             int* pe_out, int* recheck_out) {
+                             int* pe_out, int* recheck_out, double* du_out) {
     const unsigned FULL = 0xffffffffu;
+    *du_out = 0.0;
     const double L = v.L, hL = v.halfL;
     const int Gf = v.Gf;
     const int ti = stage_find(S, S.ci[c]);
@@ -1424,6 +1437,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
         n += __popc(mi_);
         nc += __popc(mc);
     }
+    __syncwarp();                                 // support and candidate lists are read by every lane
     *n_out = n;
     if (n > v.n_cap) return DEFER;
     if (n == 0) return ACCEPT;                    // no bead moves; dU = 0 passes
@@ -1475,17 +1489,20 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
         const double band = 2.0 * (double)(64 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
         if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
             acc = (double)d32 <= thr;
+            *du_out = (double)d32;
         } else {
             double d64 = 0.0;
             int pe2 = 0;
             stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, eps, &d64, nullptr, nullptr, nullptr, &pe2);
             acc = d64 <= thr;
+            *du_out = d64;
             (*recheck_out)++;
         }
     } else {
         double d64 = 0.0;
         stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, eps, &d64, nullptr, nullptr, nullptr, &pe);
         acc = d64 <= thr;
+        *du_out = d64;
     }
     *pe_out += pe;
     if (!acc) return REJECT;
@@ -1536,12 +1553,17 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, i
             const int j = v.q_slots[start + t];
             const double lam = carry > 0.0 ? carry : v.slot_lam[j];
             int n = 0;
-            int r = warp_attempt<PREC>(v, sm, l, j, v.slot_bead[j], lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks);
+            double du = 0.0;
+            int r = warp_attempt<PREC>(v, sm, l, j, v.slot_bead[j], lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks, &du);
             __syncwarp();
             if (r == DEFER) { if (lane == 0) v.defer[start + t] = 1; def++; continue; }
             att++; bu += n;
             if (r == ACCEPT) { acc++; moved += n; }
-            if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
+            if (lane == 0) {
+                v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
+                v.tr_n[Ly.tr_off + j] = n;
+                v.tr_du[Ly.tr_off + j] = du;
+            }
             carry = (r == ACCEPT) ? 0.0 : lam;
         }
     } else {
@@ -1602,13 +1624,18 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, i
                 const int j = S.cj[cc];
                 const double lam = carry > 0.0 ? carry : S.clam[cc];
                 int n = 0;
+                double du = 0.0;
                 tag++;
-                const int r = stage_attempt<PREC>(v, S, ns, org, side, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks);
+                const int r = stage_attempt<PREC>(v, S, ns, org, side, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks, &du);
                 __syncwarp();
                 if (r == DEFER) { if (lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
                 att++; bu += n;
                 if (r == ACCEPT) { acc++; moved += n; }
-                if (lane == 0) { v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2); v.tr_n[Ly.tr_off + j] = n; }
+                if (lane == 0) {
+                    v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
+                    v.tr_n[Ly.tr_off + j] = n;
+                    v.tr_du[Ly.tr_off + j] = du;
+                }
                 carry = (r == ACCEPT) ? 0.0 : lam;
             }
             __syncwarp();

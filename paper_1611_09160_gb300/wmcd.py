@@ -105,6 +105,7 @@ _SIGS = {
     "wmcd_set_positions": ["p", "p", "p"],
     "wmcd_stats": ["p", "p", "p"],
     "wmcd_trace": ["p", "i", "p", "p", "i64", "p", "p"],
+    "wmcd_trace_du": ["p", "i", "p", "i64", "p", "p"],
     "wmcd_state_size": ["p", "p"],
     "wmcd_get_state": ["p", "p", "i64", "p"],
     "wmcd_set_state": ["p", "p", "i64", "p"],
@@ -257,6 +258,14 @@ class Simulation:
                                     _stream_ptr(stream)), "wmcd_trace")
         m = min(cnt.value, cap)
         return out[:m].copy(), nn[:m].copy()
+
+    def trace_du(self, layer: int, stream=None):
+        cap = 4 * self.n + 4096
+        out = np.zeros(cap)
+        cnt = ctypes.c_int64()
+        _check(self._lib.wmcd_trace_du(self.h, int(layer), out.ctypes.data, cap, ctypes.byref(cnt),
+                                       _stream_ptr(stream)), "wmcd_trace_du")
+        return out[:min(cnt.value, cap)].copy()
 
     def get_state(self, stream=None) -> bytes:
         sz = ctypes.c_int64()
