@@ -323,9 +323,11 @@ __device__ __forceinline__ void wca32(const Pot32& P, float r2, float& u, float&
 }
 __device__ __forceinline__ void bond32(const Pot32& P, float r2, float& u, float& m) {
     if (P.bond == 1) {
+        // |error| <= 5 ulp * k (|d| r + d^2): r2 carries ~7 ulp, sqrt halves it, one more for
+        // the subtraction and two for the products (scaled by 80 ulp in the band: ample)
         const float r = __fsqrt_rn(r2), d = r - P.br0;
         u = 0.5f * P.bk * d * d;
-        m = P.bk * (r2 + P.br02);
+        m = P.bk * (fabsf(d) * r + d * d + 1e-6f * P.br02);
     } else if (P.bond == 2) {
         const float x = __fdiv_rn(r2, P.R02);
         if (!(x < 0.98f)) { u = 0.0f; m = __int_as_float(0x7f800000); return; }   // near R0: decide in FP64
@@ -1227,19 +1229,20 @@ __global__ void k_region_scatter(SimView v) {
 // pointers into one warp's share of the dynamic shared memory
 struct Stage {
     double *sx, *sy, *sz;            // staged positions (binary64, wrapped)
-    float *fx, *fy, *fz;             // the same relative to the region origin (binary32 prefilter)
+    float *hx, *hy, *hz;             // position relative to the region origin: hi part ...
+    float *lx, *ly, *lz;             // ... and lo part (hi + lo carries the binary64 value)
     int *sid, *scell, *sdim, *stag;  // bead id, fine cell at staging, image change | dirty, support tag
     int *hkey, *hval;                // bead id -> staged index (open addressing)
     int *mem, *mimg, *mpart, *cand;  // support (staged indices), image change, bonded partners, candidates
-    double *mnp;                     // new positions of the support
-    float *mnf;                      // new positions relative to the origin
+    double *mnp;                     // new positions of the support (binary64, wrapped)
+    float *mnh, *mnl;                // the same relative to the origin, hi and lo
     int *cj, *ci;                    // slot chunk: slot id, bead
     double *clam, *cV, *cp, *cthr;   // slot chunk: scale, centre offset, polarisation, threshold
     int cap, hbits;
 };
 __host__ __device__ inline size_t stage_bytes(int cap) {
-    return (size_t)cap * (3 * 8 + 3 * 4 + 4 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 3 * 4) +
-           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8) + 64;
+    return (size_t)cap * (3 * 8 + 6 * 4 + 4 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
+           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8) + 128;
 }
 __host__ __device__ inline size_t warp_stride(int cap) {
     size_t per = stage_bytes(cap) > sizeof(WarpSmem) ? stage_bytes(cap) : sizeof(WarpSmem);
@@ -1256,8 +1259,9 @@ __device__ inline Stage stage_carve(char* base, int cap) {
     S.mnp = (double*)take(8 * 3 * kNCap);
     S.clam = (double*)take(8 * kSlotChunk); S.cV = (double*)take(8 * 3 * kSlotChunk);
     S.cp = (double*)take(8 * 3 * kSlotChunk); S.cthr = (double*)take(8 * kSlotChunk);
-    S.fx = (float*)take(4 * cap); S.fy = (float*)take(4 * cap); S.fz = (float*)take(4 * cap);
-    S.mnf = (float*)take(4 * 3 * kNCap);
+    S.hx = (float*)take(4 * cap); S.hy = (float*)take(4 * cap); S.hz = (float*)take(4 * cap);
+    S.lx = (float*)take(4 * cap); S.ly = (float*)take(4 * cap); S.lz = (float*)take(4 * cap);
+    S.mnh = (float*)take(4 * 3 * kNCap); S.mnl = (float*)take(4 * 3 * kNCap);
     S.sid = (int*)take(4 * cap); S.scell = (int*)take(4 * cap); S.sdim = (int*)take(4 * cap); S.stag = (int*)take(4 * cap);
     S.hkey = (int*)take(4 * 2 * cap); S.hval = (int*)take(4 * 2 * cap);
     S.mem = (int*)take(4 * kNCap); S.mimg = (int*)take(4 * kNCap); S.mpart = (int*)take(4 * 2 * kNCap);
@@ -1277,38 +1281,68 @@ __device__ __forceinline__ int stage_find(const Stage& S, int id) {
     }
     return -1;
 }
-// coordinate relative to the region origin o, brought into [0, L)
-__device__ __forceinline__ float local32(double x, double o, double L) {
+// coordinate relative to the region origin o, brought into [0, L), as a binary32 pair hi + lo
+__device__ __forceinline__ void local_split(double x, double o, double L, float& hi, float& lo) {
     double t = x - o;
     if (t < 0.0) t += L;
     else if (t >= L) t -= L;
-    return (float)t;
+    hi = (float)t;
+    lo = (float)(t - (double)hi);
 }
+// difference of two such coordinates: relative error about 2 ulp of binary32, no binary64 work
+__device__ __forceinline__ float dfd(float ha, float la, float hb, float lb) { return (ha - hb) + (la - lb); }
 
 template <bool F32>
 __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bool all_cand, int ns, int tag, int lane,
-                             double eps, double* dU64, float* dU32, float* mag32, int* terms, int* pe_out) {
+                             double* dU64, float* dU32, float* mag32, int* terms, int* pe_out) {
     const double L = v.L, hL = v.halfL;
     const Pot& P = v.pot;
     const Pot32 P32 = pot32(P);
-    // binary32 screen of candidate pairs: local coordinates carry at most eps of rounding each
-    const float hLf = (float)hL, rcf = (float)(v.rc + 2.0 * eps + 1e-6);
-    const float rc2f = rcf * rcf;
+    const float hLf = (float)hL;
+    const float rcs = (float)(v.rc * (1.0 + 1e-6) + 1e-6);
+    const float rcs2 = rcs * rcs;
     double a64 = 0.0;
     float a32 = 0.0f, m32 = 0.0f;
     int T = 0, pe = 0;
-    auto pair_term = [&](double ax, double ay, double az, double bx, double by, double bz,
-                         double cx, double cy, double cz, double dx, double dy, double dz, bool bonded, bool wca) {
-        // new pair (a, b), old pair (c, d)
+    // pair term between new positions (A, B) and old positions (C, D), indices into the
+    // support (k < 0 is a staged bead -1 - t) for the binary32 form, positions for binary64
+    auto coord = [&](int k, int a, float& h, float& lo) {
+        if (k >= 0) { h = S.mnh[3 * k + a]; lo = S.mnl[3 * k + a]; }
+        else {
+            const int t = -1 - k;
+            h = a == 0 ? S.hx[t] : (a == 1 ? S.hy[t] : S.hz[t]);
+            lo = a == 0 ? S.lx[t] : (a == 1 ? S.ly[t] : S.lz[t]);
+        }
+    };
+    auto r2_32 = [&](int ka, int kb) {
+        float s = 0.0f;
+        for (int a = 0; a < 3; a++) {
+            float ha, la, hb, lb;
+            coord(ka, a, ha, la);
+            coord(kb, a, hb, lb);
+            const float d = dfd(ha, la, hb, lb);
+            s += d * d;
+        }
+        return s;
+    };
+    auto pos64 = [&](int k, double* x) {
+        if (k >= 0) { x[0] = S.mnp[3 * k]; x[1] = S.mnp[3 * k + 1]; x[2] = S.mnp[3 * k + 2]; }
+        else { const int t = -1 - k; x[0] = S.sx[t]; x[1] = S.sy[t]; x[2] = S.sz[t]; }
+    };
+    auto r2_64 = [&](int ka, int kb) {
+        double x[3], y[3];
+        pos64(ka, x);
+        pos64(kb, y);
+        return norm2(mi(x[0] - y[0], L, hL), mi(x[1] - y[1], L, hL), mi(x[2] - y[2], L, hL));
+    };
+    auto term = [&](int na, int nb, int oa, int ob, bool bonded, bool wca) {
         if (F32) {
-            const float r2n = norm2f(dif32(ax, bx, L, hLf), dif32(ay, by, L, hLf), dif32(az, bz, L, hLf));
-            const float r2o = norm2f(dif32(cx, dx, L, hLf), dif32(cy, dy, L, hLf), dif32(cz, dz, L, hLf));
+            const float r2n = r2_32(na, nb), r2o = r2_32(oa, ob);
             float un, mn, uo, mo;
             if (wca) { wca32(P32, r2n, un, mn); wca32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
             if (bonded) { bond32(P32, r2n, un, mn); bond32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
         } else {
-            const double r2n = norm2(mi(ax - bx, L, hL), mi(ay - by, L, hL), mi(az - bz, L, hL));
-            const double r2o = norm2(mi(cx - dx, L, hL), mi(cy - dy, L, hL), mi(cz - dz, L, hL));
+            const double r2n = r2_64(na, nb), r2o = r2_64(oa, ob);
             double u = 0.0;
             if (wca) u += U_wca(P, r2n) - U_wca(P, r2o);
             if (bonded) u += U_bond(P, r2n) - U_bond(P, r2o);
@@ -1318,8 +1352,8 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
     // external well and bonds to beads outside the support
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
-        const double* nw = &S.mnp[3 * k];
         if (P.kappa != 0.0) {
+            const double* nw = &S.mnp[3 * k];
             if (F32) {
                 float un = 0.5f * P32.kappa * norm2f(dif32(nw[0], hL, L, hLf), dif32(nw[1], hL, L, hLf), dif32(nw[2], hL, L, hLf));
                 float uo = 0.5f * P32.kappa * norm2f(dif32(S.sx[t], hL, L, hLf), dif32(S.sy[t], hL, L, hLf), dif32(S.sz[t], hL, L, hLf));
@@ -1331,8 +1365,7 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
         for (int e = 0; e < 2; e++) {
             const int tq = S.mpart[2 * k + e];
             if (tq < 0) continue;                     // no bond, or the partner moves too
-            pair_term(nw[0], nw[1], nw[2], S.sx[tq], S.sy[tq], S.sz[tq], S.sx[t], S.sy[t], S.sz[t], S.sx[tq], S.sy[tq],
-                      S.sz[tq], true, false);
+            term(k, -1 - tq, -1 - t, -1 - tq, true, false);
         }
     }
     // pairs inside the support
@@ -1346,12 +1379,9 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
         const int m1 = S.sid[t1], m2 = S.sid[t2];
         const int lo_ = min(m1, m2), hi_ = max(m1, m2);
         const bool bonded = hi_ == lo_ + 1 && v.bnext[lo_];
-        const double* n1 = &S.mnp[3 * k1];
-        const double* n2 = &S.mnp[3 * k2];
-        pair_term(n1[0], n1[1], n1[2], n2[0], n2[1], n2[2], S.sx[t1], S.sy[t1], S.sz[t1], S.sx[t2], S.sy[t2], S.sz[t2],
-                  bonded, true);
+        term(k1, k2, -1 - t1, -1 - t2, bonded, true);
     }
-    // WCA with the interaction candidates outside the support (binary32 distance screen first)
+    // WCA with the interaction candidates outside the support
     if (P.eps != 0.0) {
         const int nsrc = all_cand ? ns : nc;
         const int total = n * nsrc;
@@ -1360,12 +1390,8 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
             const int c = all_cand ? (w - k * nsrc) : S.cand[w - k * nsrc];
             if (S.stag[c] == tag) continue;           // a support member (only when scanning everything)
             const int t = S.mem[k];
-            const float ex = S.fx[c] - S.mnf[3 * k], ey = S.fy[c] - S.mnf[3 * k + 1], ez = S.fz[c] - S.mnf[3 * k + 2];
-            const float gx = S.fx[c] - S.fx[t], gy = S.fy[c] - S.fy[t], gz = S.fz[c] - S.fz[t];
-            if (!(ex * ex + ey * ey + ez * ez < rc2f) && !(gx * gx + gy * gy + gz * gz < rc2f)) continue;
-            const double* nw = &S.mnp[3 * k];
-            pair_term(nw[0], nw[1], nw[2], S.sx[c], S.sy[c], S.sz[c], S.sx[t], S.sy[t], S.sz[t], S.sx[c], S.sy[c], S.sz[c],
-                      false, true);
+            if (!(r2_32(k, -1 - c) < rcs2) && !(r2_32(-1 - t, -1 - c) < rcs2)) continue;
+            term(k, -1 - c, -1 - t, -1 - c, false, true);
             pe++;
         }
     }
@@ -1390,43 +1416,51 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
 // One move of a staged queue. The slot's centre offset V, polarisation p and Metropolis
 // threshold were prepared in the chunk arrays at index c.
 template <int PREC>
-__device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const double org[3], double side, int l, int c,
+__device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const double org[3], float sidef, int l, int c,
                              double lam, const int64_t rlo[3], const int64_t rhi[3], int lane, int tag, int* n_out,
                              int* pe_out, int* recheck_out, double* du_out) {
     const unsigned FULL = 0xffffffffu;
-    *du_out = 0.0;
     const double L = v.L, hL = v.halfL;
     const int Gf = v.Gf;
+    *du_out = 0.0;
     const int ti = stage_find(S, S.ci[c]);
     if (ti < 0) return DEFER;                     // the picked bead lies outside the region interior
-    // centre b = r_i + lam V (Appendix D), wrapped
+    // centre b = r_i + lam V (Appendix D), wrapped; binary64 because the region rule and the
+    // support must match the sequential definition exactly
     double b[3];
     b[0] = wrap(add(S.sx[ti], mul(lam, S.cV[3 * c])), L, nullptr);
     b[1] = wrap(add(S.sy[ti], mul(lam, S.cV[3 * c + 1])), L, nullptr);
     b[2] = wrap(add(S.sz[ti], mul(lam, S.cV[3 * c + 2])), L, nullptr);
     const double R = add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
+    bool inside = true;
     for (int a = 0; a < 3; a++) {
         const int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
         const int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
-        if (!range_inside(t0, t1, rlo[a], rhi[a], Gf)) return DEFER;
+        inside = inside && range_inside(t0, t1, rlo[a], rhi[a], Gf);
     }
-    // support and interaction candidates in one pass over the staged beads
-    const double eps = 1e-6 * (side + lam) + 1e-9;
-    const double lam2 = mul(lam, lam);
-    const float lin = (float)((lam - eps) * (lam - eps)), lout = (float)((lam + eps) * (lam + eps));
-    const float rcand = (float)((R + eps) * (R + eps));
-    const float bx = local32(b[0], org[0], L), by = local32(b[1], org[1], L), bz = local32(b[2], org[2], L);
+    if (!inside) return DEFER;
+    // support and candidates in one binary32 pass over the staged beads (hi parts, with a
+    // margin eps for their rounding); ties within eps of the sphere decided in binary64
+    const float lamf = (float)lam;
+    const float eps = 1e-6f * (sidef + lamf) + 1e-9f;
+    const float lin = (lamf - eps) * (lamf - eps), lout = (lamf + eps) * (lamf + eps);
+    const float Rf = (float)R + eps;
+    const float rcand = Rf * Rf;
+    float bh[3], bl[3];
+    local_split(b[0], org[0], L, bh[0], bl[0]);
+    local_split(b[1], org[1], L, bh[1], bl[1]);
+    local_split(b[2], org[2], L, bh[2], bl[2]);
     int n = 0, nc = 0;
     for (int base = 0; base < ns; base += 32) {
         const int t = base + lane;
         bool in = false, cd = false;
         if (t < ns) {
-            const float dx = S.fx[t] - bx, dy = S.fy[t] - by, dz = S.fz[t] - bz;
+            const float dx = S.hx[t] - bh[0], dy = S.hy[t] - bh[1], dz = S.hz[t] - bh[2];
             const float d2 = dx * dx + dy * dy + dz * dz;
             if (d2 < lin) in = true;
             else if (d2 <= lout) {
                 const double e2 = norm2(mi(sub(S.sx[t], b[0]), L, hL), mi(sub(S.sy[t], b[1]), L, hL), mi(sub(S.sz[t], b[2]), L, hL));
-                in = e2 < lam2;
+                in = e2 < mul(lam, lam);
             }
             cd = !in && d2 < rcand;
         }
@@ -1445,25 +1479,25 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
     const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
-    bool bad = false;
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
         S.stag[t] = tag;
-        double d[3] = {mi(sub(S.sx[t], b[0]), L, hL), mi(sub(S.sy[t], b[1]), L, hL), mi(sub(S.sz[t], b[2]), L, hL)};
-        const double d2 = norm2(d[0], d[1], d[2]);
+        const double o[3] = {S.sx[t], S.sy[t], S.sz[t]};
+        double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)};
         double dl[3];
-        if (PREC == 0) wavelet_disp64(d, d2, lam, Aw, p, dl);
+        if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
         else wavelet_disp32(d, lam, Aw, p, dl);
         int im[3] = {0, 0, 0};
-        const double o[3] = {S.sx[t], S.sy[t], S.sz[t]};
         for (int a = 0; a < 3; a++) {
-            S.mnp[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
-            S.mnf[3 * k + a] = local32(S.mnp[3 * k + a], org[a], L);
+            const double x = wrap(add(o[a], dl[a]), L, &im[a]);
+            S.mnp[3 * k + a] = x;
+            local_split(x, org[a], L, S.mnh[3 * k + a], S.mnl[3 * k + a]);
         }
         S.mimg[k] = pack_img(im[0], im[1], im[2]);
     }
     __syncwarp();
     // bonded partners: staged (inside the region) or the move is deferred
+    bool bad = false;
     for (int k = lane; k < n; k += 32) {
         const int m = S.sid[S.mem[k]];
         for (int e = 0; e < 2; e++) {
@@ -1483,24 +1517,28 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
     bool acc;
     int pe = 0;
     if (PREC == 1) {
+        // binary32 energy change; the decision is taken in binary32 outside the rigorous error
+        // band (per term 80 ulp of its magnitude, plus the summation) and in binary64 inside it
         float d32 = 0.0f, m32 = 0.0f;
         int T = 0;
-        stage_energy<true>(v, S, n, nc, all_cand, ns, tag, lane, eps, nullptr, &d32, &m32, &T, &pe);
-        const double band = 2.0 * (double)(64 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
-        if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
-            acc = (double)d32 <= thr;
+        stage_energy<true>(v, S, n, nc, all_cand, ns, tag, lane, nullptr, &d32, &m32, &T, &pe);
+        const float thr32 = (float)thr;
+        const float band = 2.0f * (float)(80 + T + 6) * 5.9604645e-08f * m32 + 1e-9f * (float)v.kT +
+                           2.4e-7f * fabsf(thr32);
+        if (isfinite(d32) && isfinite(band) && fabsf(d32 - thr32) > band) {
+            acc = d32 <= thr32;
             *du_out = (double)d32;
         } else {
             double d64 = 0.0;
             int pe2 = 0;
-            stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, eps, &d64, nullptr, nullptr, nullptr, &pe2);
+            stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe2);
             acc = d64 <= thr;
             *du_out = d64;
             (*recheck_out)++;
         }
     } else {
         double d64 = 0.0;
-        stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, eps, &d64, nullptr, nullptr, nullptr, &pe);
+        stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe);
         acc = d64 <= thr;
         *du_out = d64;
     }
@@ -1509,7 +1547,8 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
         S.sx[t] = S.mnp[3 * k]; S.sy[t] = S.mnp[3 * k + 1]; S.sz[t] = S.mnp[3 * k + 2];
-        S.fx[t] = S.mnf[3 * k]; S.fy[t] = S.mnf[3 * k + 1]; S.fz[t] = S.mnf[3 * k + 2];
+        S.hx[t] = S.mnh[3 * k]; S.hy[t] = S.mnh[3 * k + 1]; S.hz[t] = S.mnh[3 * k + 2];
+        S.lx[t] = S.mnl[3 * k]; S.ly[t] = S.mnl[3 * k + 1]; S.lz[t] = S.mnl[3 * k + 2];
         // accumulate the image change (3 fields of 8 bits, offset 128) and mark dirty (bit 24)
         int dd[3], cur = S.sdim[t];
         unpack_img(S.mimg[k], dd);
@@ -1573,12 +1612,14 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, i
         __syncwarp();
         const double hf = v.L / v.Gf;
         const double org[3] = {(double)rlo[0] * hf, (double)rlo[1] * hf, (double)rlo[2] * hf};
-        const double side = (double)(rhi[0] - rlo[0] + 1) * hf;
+        const float sidef = (float)((double)(rhi[0] - rlo[0] + 1) * hf);
         for (int t = lane; t < ns; t += 32) {
             const int m = v.rlist[rs + t];
             const Bead bb = v.bead[m];
             S.sx[t] = bb.x; S.sy[t] = bb.y; S.sz[t] = bb.z;
-            S.fx[t] = local32(bb.x, org[0], v.L); S.fy[t] = local32(bb.y, org[1], v.L); S.fz[t] = local32(bb.z, org[2], v.L);
+            local_split(bb.x, org[0], v.L, S.hx[t], S.lx[t]);
+            local_split(bb.y, org[1], v.L, S.hy[t], S.ly[t]);
+            local_split(bb.z, org[2], v.L, S.hz[t], S.lz[t]);
             S.sid[t] = m;
             S.scell[t] = cell_lin(v, bb.x, bb.y, bb.z);
             S.sdim[t] = 128 | (128 << 8) | (128 << 16);
@@ -1626,7 +1667,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, i
                 int n = 0;
                 double du = 0.0;
                 tag++;
-                const int r = stage_attempt<PREC>(v, S, ns, org, side, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks, &du);
+                const int r = stage_attempt<PREC>(v, S, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks, &du);
                 __syncwarp();
                 if (r == DEFER) { if (lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
                 att++; bu += n;
@@ -1640,33 +1681,39 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, i
             }
             __syncwarp();
         }
-        // write back the moved beads; cell-list moves by lane 0 in staged order
-        for (int t = lane; t < ns; t += 32) {
-            const int dm = S.sdim[t];
-            if (!(dm & (1 << 24))) continue;
-            const int m = S.sid[t];
-            v.bead[m].x = S.sx[t]; v.bead[m].y = S.sy[t]; v.bead[m].z = S.sz[t];
-            const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
-            if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            for (int t = 0; t < ns; t++) {
-                if (!(S.sdim[t] & (1 << 24))) continue;
+        // write back the moved beads (lanes in parallel); cell-list moves by lane 0, in
+        // staged order, for the beads whose fine cell changed
+        for (int base2 = 0; base2 < ns; base2 += 32) {
+            const int t = base2 + lane;
+            int newcell = -1;
+            if (t < ns && (S.sdim[t] & (1 << 24))) {
+                const int dm = S.sdim[t];
                 const int m = S.sid[t];
-                const int oc = S.scell[t], ncl = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
-                if (oc == ncl) continue;
-                const int pr = v.prev[m], nx = v.bead[m].next;
-                if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
-                if (nx >= 0) v.prev[nx] = pr;
-                const int hd = v.head[ncl];
-                v.bead[m].next = hd;
-                v.prev[m] = -1;
-                if (hd >= 0) v.prev[hd] = m;
-                v.head[ncl] = m;
+                v.bead[m].x = S.sx[t]; v.bead[m].y = S.sy[t]; v.bead[m].z = S.sz[t];
+                const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
+                if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
+                const int nc2 = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
+                if (nc2 != S.scell[t]) newcell = nc2;
             }
+            const unsigned ch = __ballot_sync(FULL, newcell >= 0);
+            S.cand[lane] = newcell;
+            __syncwarp();
+            if (lane == 0) {
+                for (unsigned bits = ch; bits; bits &= bits - 1u) {
+                    const int ln = __ffs(bits) - 1, tt = base2 + ln;
+                    const int m = S.sid[tt], oc = S.scell[tt], ncl = S.cand[ln];
+                    const int pr = v.prev[m], nx = v.bead[m].next;
+                    if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+                    if (nx >= 0) v.prev[nx] = pr;
+                    const int hd = v.head[ncl];
+                    v.bead[m].next = hd;
+                    v.prev[m] = -1;
+                    if (hd >= 0) v.prev[hd] = m;
+                    v.head[ncl] = m;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp(FULL);
     }
     if (lane == 0) {
         v.carry_q[Ly.carry_off + cell] = carry;
