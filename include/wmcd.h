@@ -162,6 +162,25 @@ int wmcd_kernel_times(wmcd_handle* h, int64_t* launches, double* ms, int n_class
 /* Device bytes held by the handle. */
 int wmcd_device_bytes(wmcd_handle* h, int64_t* bytes);
 
+/* Plane-wave moves on caller-owned device positions without allocating anything (the paper
+ * has no counterpart: this is a deployment variant of wmcd_planewave). For callers that may not
+ * call cudaMalloc, e.g. code running while another framework owns the device memory, real-time
+ * loops that must not allocate after start-up, or hosts that forbid allocation in callbacks.
+ * pos: N*3 doubles in device memory, coordinates in [0, L), replaced in place by the positions
+ * after n_moves moves (wrapped; no image counters). chain_len: host, as for wmcd_create.
+ * call_index: the plane-wave call counter (0 for the first call, then 1, 2, ...); carry: host
+ * int32[4], the recycled wave vector (carry[0] != 0 means carry[1..3] is carried), read and
+ * updated. With the same params, positions, call_index and carry the result equals n_moves
+ * moves of wmcd_planewave on a handle whose plane-wave call counter is call_index.
+ * Scratch: one file-scope device array of about 1.9 MB that every GPU loading the library
+ * holds until exit; limits N <= 16384, grid_f^3 <= 48^3, lcut <= 8, plane waves periodic,
+ * else WMCD_EINVAL. The first call on a device looks the array up (cudaGetSymbolAddress):
+ * make that first call before any stream capture. All calls share the array, so calls that
+ * overlap on the GPU (other streams or threads) race; the function is not thread-safe.
+ * No cudaMalloc, cudaFree or allocating library call is made. Synchronises `stream`. */
+int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, const int32_t* chain_len, int64_t n_chains,
+                           int64_t call_index, int32_t* carry, int64_t n_moves, void* stream);
+
 int wmcd_destroy(wmcd_handle* h);
 const char* wmcd_strerror(int status);
 

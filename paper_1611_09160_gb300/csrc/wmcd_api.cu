@@ -703,3 +703,41 @@ extern "C" const char* wmcd_strerror(int status) {
         default: return "unknown status";
     }
 }
+
+namespace wmcd {
+// Plane-wave mode table written into caller buffers, using only static storage (for the
+// allocation-free entry point): modes |l| <= lcut in the enumeration order of wmcd_create
+// and their cumulative probabilities. Returns the number of modes, or -1 if cap is too small.
+// Not thread-safe (one static work array).
+int mode_table_static(double L, double lmax, int lcut, int* modes, double* cdf, int cap) {
+    static double acc[40001];
+    static double gq[((2 * 8 + 1) * (2 * 8 + 1) * (2 * 8 + 1))];
+    const double h = kPi / 20.0;
+    const int panels = 40000;
+    acc[panels] = tail3(panels * h);
+    for (int p = panels - 1; p >= 0; p--) acc[p] = acc[p + 1] + gl10(p * h, (p + 1) * h);
+    int n = 0;
+    double tot = 0.0;
+    for (int lx = -lcut; lx <= lcut; lx++)
+        for (int ly = -lcut; ly <= lcut; ly++)
+            for (int lz = -lcut; lz <= lcut; lz++) {
+                const int l2 = lx * lx + ly * ly + lz * lz;
+                if (l2 > lcut * lcut) continue;
+                if (n >= cap || n >= (int)(sizeof gq / sizeof gq[0])) return -1;
+                modes[3 * n] = lx; modes[3 * n + 1] = ly; modes[3 * n + 2] = lz;
+                const double q = kTwoPi * std::sqrt((double)l2) / L * lmax;
+                double g;
+                if (q >= panels * h) g = tail3(q);
+                else {
+                    const int p = (int)(q / h);
+                    const double top = (p + 1) * h;
+                    g = acc[p + 1] + (top > q ? gl10(q, top) : 0.0);
+                }
+                gq[n++] = g;
+                tot += g;
+            }
+    double a = 0.0;
+    for (int i = 0; i < n; i++) { a += gq[i]; cdf[i] = a / tot; }
+    return n;
+}
+}  // namespace wmcd

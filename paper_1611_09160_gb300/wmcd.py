@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libwmcd.so")
-_SOURCES = ["wmcd_kernels.cu", "wmcd_api.cu"]
+_SOURCES = ["wmcd_kernels.cu", "wmcd_api.cu", "wmcd_noalloc.cu"]
 _HEADERS = ["wmcd_device.cuh", "wmcd_internal.h"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
@@ -113,6 +113,7 @@ _SIGS = {
     "wmcd_kernel_times": ["p", "p", "p", "i", "p"],
     "wmcd_device_bytes": ["p", "p"],
     "wmcd_destroy": ["p"],
+    "wmcd_planewave_noalloc": ["p", "p", "p", "i64", "i64", "p", "i64", "p"],
 }
 EXPORTED = sorted(list(_SIGS) + ["wmcd_strerror"])
 
@@ -159,6 +160,17 @@ def make_params(fields: dict) -> Params:
     for i, g in enumerate(layers):
         p.grid_layer[i] = int(g)
     return p
+
+
+def planewave_noalloc(params: dict, pos, chain_len, call_index: int, carry, n_moves: int, stream=None):
+    """Plane-wave moves on caller-owned device positions (a torch CUDA tensor of N x 3 doubles,
+    updated in place) with no device allocation; ``carry`` is an int32 array of 4 (in/out)."""
+    lib = load()
+    pr = make_params(params)
+    cl = np.ascontiguousarray(chain_len, dtype=np.int32)
+    pp, _k = _buf_ptr(pos)
+    _check(lib.wmcd_planewave_noalloc(ctypes.byref(pr), pp, cl.ctypes.data, len(cl), int(call_index),
+                                      carry.ctypes.data, int(n_moves), _stream_ptr(stream)), "wmcd_planewave_noalloc")
 
 
 def default_params(n_beads: int, box_L: float, *, lambda_min: float = 2.0, lambda_max: float | None = None,
