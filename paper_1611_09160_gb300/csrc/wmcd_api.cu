@@ -77,7 +77,9 @@ static void G_table(const std::vector<double>& Q, std::vector<double>& out) {
 // ---------------------------------------------------------------------------------------
 struct Handle {
     wmcd_params P;
-    SimView v;
+    SimView v;                   // host copy of the view
+    SimView* dview = nullptr;    // device copy read by every kernel
+    GroupDims g;                 // launch bounds of this one simulation
     int dev = 0;
     int64_t N = 0;
     int nL = 0;
@@ -143,10 +145,10 @@ static void prof_harvest(Handle* h) {
 struct ProfScope {
     Handle* h; int cls; cudaStream_t s; cudaEvent_t a{}, b{};
     ProfScope(Handle* h_, int c, cudaStream_t s_) : h(h_), cls(c), s(s_) {
-        if (h->prof) { a = get_event(h); cudaEventRecord(a, s); }
+        if (h && h->prof) { a = get_event(h); cudaEventRecord(a, s); }
     }
     ~ProfScope() {
-        if (h->prof) {
+        if (h && h->prof) {
             b = get_event(h);
             cudaEventRecord(b, s);
             h->ev_used.push_back({cls, {a, b}});
@@ -287,6 +289,8 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
         const double mass = (Ly.ilo3 - Ly.ihi3) / (imin3 - imax3);
         h->expect[l] = ((double)h->N * (1.0 - h->p_fourier)) * mass;
         h->Mmax[l] = (int)std::floor(h->expect[l]) + 1;
+        Ly.expect = h->expect[l];
+        Ly.Mmax = h->Mmax[l];
         Mall = std::max<int64_t>(Mall, h->Mmax[l]);
         Ly.G = P.grid_layer[l];
         if (Ly.G < 0 || (Ly.G > 0 && (Ly.G % P.colour_K != 0 || Ly.G < P.colour_K)) || Ly.G > 256) {
@@ -330,6 +334,7 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
          !dalloc(h, &v.serial_tag, 1);
     ok = ok && !dalloc(h, &v.pw, 1) && !dalloc(h, &v.pw_new, 3 * N) && !dalloc(h, &v.pw_imgd, N) &&
          !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1);
+    ok = ok && !dalloc(h, &v.step, 2) && !dalloc(h, &v.counts, kMaxLayers + 1) && !dalloc(h, &h->dview, 1);
     int* d_modes = nullptr;
     double* d_cdf = nullptr;
     ok = ok && !dalloc(h, &d_modes, modes.size() + 3) && !dalloc(h, &d_cdf, cdf.size() + 1);
@@ -369,6 +374,32 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     v.modes = d_modes;
     v.mode_cdf = d_cdf;
     v.n_modes = (int)cdf.size();
+    v.expect_F = (double)N * h->p_fourier;
+    v.pw_on = P.planewave_mode == 1;
+    // launch bounds of this simulation
+    {
+        GroupDims& g = h->g;
+        g.S = 1;
+        g.maxN = N;
+        g.maxCells = std::max<int64_t>(ncell, 1);
+        g.maxL = nL;
+        g.maxK3 = P.colour_K * P.colour_K * P.colour_K;
+        g.pw = v.pw_on != 0;
+        g.maxMF = g.pw ? (int)std::floor(v.expect_F) + 1 : 0;
+        g.stage_cap = v.stage_cap;
+        g.pw_blocks = v.pw_blocks;
+        g.prec_mask = 1 << P.precision;
+        for (int l = 0; l < nL; l++) {
+            const int G = v.layer[l].G, Q = G / P.colour_K;
+            g.Mmax[l] = h->Mmax[l];
+            g.keys[l] = std::max(G * G * G, 1);
+            g.nq[l] = std::max(Q * Q * Q, 1);
+            g.coloured[l] = G > 0;
+        }
+    }
+    cudaMemsetAsync(v.step, 0, 2 * sizeof(uint64_t), s);
+    cudaMemsetAsync(v.counts, 0, (kMaxLayers + 1) * sizeof(int), s);
+    cudaMemcpyAsync(h->dview, &v, sizeof(SimView), cudaMemcpyHostToDevice, s);
     // host -> device
     std::vector<uint8_t> bn(N, 0);
     {
@@ -395,7 +426,7 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     cudaMemsetAsync(v.tr_out, 0, std::max<int64_t>(tr_total, 1), s);
     cudaMemsetAsync(v.tr_n, 0, std::max<int64_t>(tr_total, 1) * sizeof(int), s);
     k_fill_beads<<<grid_for(N), 256, 0, s>>>(v.bead, h->staging, N);
-    launch_cl_rebuild(v, s, nullptr);
+    launch_cl_rebuild(h->dview, h->g, s, 0);
     if (cudaStreamSynchronize(s) != cudaSuccess || last_cuda_status()) { cudaGetLastError(); wmcd_destroy(H); return WMCD_ECUDA; }
     int err = 0;
     cudaMemcpy(&err, v.err, sizeof(int), cudaMemcpyDeviceToHost);
@@ -404,37 +435,50 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     return WMCD_OK;
 }
 
-static void run_sweep(Handle* h, cudaStream_t s) {
-    SimView& v = h->v;
-    const uint64_t sw = h->sweep;
-    for (int l = 0; l < h->nL; l++) {
-        const int64_t M = slot_count(h, K_COUNT, l, sw, h->expect[l]);
-        if (M <= 0) continue;
-        { ProfScope ps(h, 4, s); launch_slots(v, l, sw, (int)M, s); }
-        h->launches += 1;
-        if (v.layer[l].G > 0) {
-            { ProfScope ps(h, 4, s); launch_bucket(v, l, (int)M, s); }
-            const int nc = v.K * v.K * v.K;
-            for (int c = 0; c < nc; c++) { ProfScope ps(h, 0, s); launch_colour_staged(v, l, c, sw, s); }
-            { ProfScope ps(h, 4, s); launch_defer_compact(v, (int)M, s); }
-            { ProfScope ps(h, 1, s); launch_serial(v, l, sw, 1, (int)M, s); }
-            h->launches += 4 + 4 * nc + 2;
-        } else {
-            ProfScope ps(h, 1, s);
-            launch_serial(v, l, sw, 0, (int)M, s);
-            h->launches += 1;
+static int popcount3(int m) { return (m & 1) + ((m >> 1) & 1); }
+
+// The launches of one sweep for every simulation of a group (Sec. V-VIII order: octave layers
+// in ascending order, each in its colour phases then its serial phase, then the plane-wave
+// slots), ending with the advance of the sweep counter. `hc` (a lone simulation only) holds
+// this sweep's exact slot counts, used to leave out launches with no work; a batch launches
+// every phase up to its bounds and the kernels return early where a simulation has none.
+// Returns the number of kernels launched.
+int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s) {
+    const int np = popcount3(g.prec_mask);
+    int64_t launches = 0;
+    { ProfScope ps(prof, 4, s); launch_counts(d, g, s); }
+    launches += 1;
+    for (int l = 0; l < g.maxL; l++) {
+        if (hc && hc[l] <= 0) continue;
+        { ProfScope ps(prof, 4, s); launch_slots(d, g, l, s); }
+        launches += 1;
+        if (g.coloured[l]) {
+            { ProfScope ps(prof, 4, s); launch_bucket(d, g, l, s); }
+            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launch_colour_staged(d, g, l, c, s); }
+            { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, l, s); }
+            launches += 5 + (int64_t)g.maxK3 * (4 + np) + 1;
         }
+        { ProfScope ps(prof, 1, s); launch_serial(d, g, l, s); }
+        launches += np;
     }
-    h->tr_pw_count = 0;
-    if (h->P.planewave_mode == 1) {
-        const int64_t MF = slot_count(h, K_PWCOUNT, 0, sw, (double)h->N * h->p_fourier);
+    if (g.pw) {
+        const int64_t MF = hc ? hc[kMaxLayers] : g.maxMF;
         for (int64_t m = 0; m < MF; m++) {
-            ProfScope ps(h, 2, s);
-            launch_planewave(v, K_PWMODE, K_PWDIR, K_PWACC, sw, (int)m, (int)m, s);
+            ProfScope ps(prof, 2, s);
+            launch_planewave(d, g, 0, (int)m, s);
         }
-        h->launches += 8 * MF;
-        h->tr_pw_count = MF;
+        launches += 8 * MF;
     }
+    launch_advance(d, g, 0, s);
+    return launches + 1;
+}
+
+static void run_sweep(Handle* h, cudaStream_t s) {
+    int64_t hc[kMaxLayers + 1] = {0};
+    for (int l = 0; l < h->nL; l++) hc[l] = slot_count(h, K_COUNT, l, h->sweep, h->expect[l]);
+    hc[kMaxLayers] = h->g.pw ? slot_count(h, K_PWCOUNT, 0, h->sweep, h->v.expect_F) : 0;
+    h->launches += enqueue_sweep(h->dview, h->g, hc, h, s);
+    h->tr_pw_count = hc[kMaxLayers];
     h->sweep++;
 }
 
@@ -460,12 +504,14 @@ extern "C" int wmcd_planewave(wmcd_handle* H, int64_t n_moves, void* stream) {
         h->v.tr_pw_out = o;
         h->v.tr_pw_mode = md;
         h->v.tr_pw_cap = (int)std::min<int64_t>(n_moves, 1 << 30);
+        cudaMemcpyAsync(h->dview, &h->v, sizeof(SimView), cudaMemcpyHostToDevice, s);
     }
     for (int64_t m = 0; m < n_moves; m++) {
         ProfScope ps(h, 2, s);
-        launch_planewave(h->v, K_DPWMODE, K_DPWDIR, K_DPWACC, h->pw_calls, (int)m, (int)m, s);
+        launch_planewave(h->dview, h->g, 1, (int)m, s);
     }
-    h->launches += 8 * n_moves;
+    launch_advance(h->dview, h->g, 1, s);
+    h->launches += 8 * n_moves + 1;
     h->tr_pw_count = n_moves;
     h->pw_calls++;
     return last_cuda_status();
@@ -494,7 +540,7 @@ extern "C" int wmcd_set_positions(wmcd_handle* H, const double* pos, void* strea
     if (!dev && cudaStreamSynchronize(s) != cudaSuccess) return WMCD_ECUDA;
     cudaMemsetAsync(h->v.img, 0, 3 * h->N * sizeof(int), s);
     k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->staging, h->N);
-    launch_cl_rebuild(h->v, s, nullptr);
+    launch_cl_rebuild(h->dview, h->g, s, 0);
     return last_cuda_status();
 }
 
@@ -647,10 +693,16 @@ extern "C" int wmcd_set_state(wmcd_handle* H, const void* buf, int64_t bytes, vo
     p += C_NCTR * sizeof(unsigned long long);
     cudaMemcpyAsync(h->v.serial_tag, p, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
     k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->staging, h->N);
-    launch_cl_rebuild(h->v, s, nullptr);
+    launch_cl_rebuild(h->dview, h->g, s, 0);
     cudaMemsetAsync(h->v.err, 0, sizeof(int), s);
     h->sweep = hd.sweep;
     h->pw_calls = hd.pw_calls;
+    {
+        static thread_local uint64_t st[2];
+        st[0] = hd.sweep;
+        st[1] = hd.pw_calls;
+        cudaMemcpyAsync(h->v.step, st, sizeof st, cudaMemcpyHostToDevice, s);
+    }
     return cudaStreamSynchronize(s) == cudaSuccess ? last_cuda_status() : WMCD_ECUDA;
 }
 

@@ -37,6 +37,8 @@ enum Err { E_WALK = 1, E_SCRATCH = 2, E_NONFINITE = 4 };
 struct LayerDev {
     double lo, hi, ilo3, ihi3;   // band [lo, hi) and its inverse cubes
     double invG;                 // G / L
+    double expect;               // expected slots per sweep, N (1 - P_F) p_l
+    int Mmax;                    // floor(expect) + 1: bound on the slots of one sweep
     int G;                       // coarse cells per axis, 0 = serial layer
     int carry_off;               // offset of this layer's per-cell carries
     int64_t tr_off;              // offset of this layer's trace
@@ -50,6 +52,7 @@ struct PWDev {
     double AF, phi, e[3];
     double reach;                // partner search reach rc + 2 |A_F|
     int carry, carry_l[3];       // recycled |k| after a rejection
+    int active;                  // this plane-wave slot exists in the current sweep / call
 };
 
 struct SimView {
@@ -67,6 +70,10 @@ struct SimView {
     uint32_t k0, k1;
     int nL;
     LayerDev layer[kMaxLayers];
+    uint64_t* step;              // [0] sweep counter, [1] direct plane-wave call counter
+    int* counts;                 // slots of the current sweep: [l] layer l, [kMaxLayers] plane waves
+    double expect_F;             // expected plane-wave slots per sweep, N P_F
+    int pw_on;                   // periodic plane waves enabled
     // schedule scratch (sized for the largest layer)
     double* slot_lam;
     int* slot_bead;
@@ -123,17 +130,29 @@ struct SimView {
 WMCD_HD int pack_img(int dx, int dy, int dz) { return (dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4); }
 WMCD_HD void unpack_img(int p, int* d) { d[0] = (p & 3) - 1; d[1] = ((p >> 2) & 3) - 1; d[2] = ((p >> 4) & 3) - 1; }
 
+// Launch bounds over the simulations of a group (one simulation, or a batch): every launch
+// covers all of them (blockIdx.y = simulation) and kernels return early where a simulation has
+// no work, so the launch sequence of a sweep is static and can be captured in a CUDA graph.
+struct GroupDims {
+    int S = 1;
+    int64_t maxN = 1, maxCells = 1;
+    int maxL = 0, maxK3 = 1, maxMF = 0, stage_cap = 256, pw_blocks = 1;
+    int Mmax[kMaxLayers] = {0}, keys[kMaxLayers] = {0}, nq[kMaxLayers] = {0};
+    bool coloured[kMaxLayers] = {false};
+    bool pw = false;
+    int prec_mask = 3;           // bit 0: some simulation runs in binary64, bit 1: some in mixed precision
+};
+
 // ---- launchers (wmcd_kernels.cu) ----
-void launch_cl_rebuild(const SimView& v, cudaStream_t s, const int* flag);
-void launch_slots(const SimView& v, int l, uint64_t sweep, int M, cudaStream_t s);
-void launch_bucket(const SimView& v, int l, int M, cudaStream_t s);
-void launch_colour(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s);
-void launch_colour_staged(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s);
+void launch_cl_rebuild(const SimView* d, const GroupDims& g, cudaStream_t s, int use_flag);
+void launch_counts(const SimView* d, const GroupDims& g, cudaStream_t s);
+void launch_advance(const SimView* d, const GroupDims& g, int which, cudaStream_t s);
+void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
+void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
+void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s);
+void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
+void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
+void launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
 size_t staged_smem_bytes(int cap);
-void launch_defer_compact(const SimView& v, int M, cudaStream_t s);
-void launch_serial(const SimView& v, int l, uint64_t sweep, int use_list, int M, cudaStream_t s);
-void launch_planewave(const SimView& v, int kmode, int kdir, int kacc, uint64_t ctr, int m, int trace_index,
-                      cudaStream_t s);
-void launch_check_positions(const SimView& v, cudaStream_t s);
 
 }  // namespace wmcd

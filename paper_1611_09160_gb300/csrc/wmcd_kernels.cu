@@ -12,6 +12,19 @@ namespace wmcd {
 
 __device__ __forceinline__ void set_err(const SimView& v, int bit) { atomicOr(v.err, bit); }
 
+// Every kernel serves a group of simulations: blockIdx.y selects one, whose view is copied
+// into shared memory once per block.
+#define SIM_PROLOGUE                                                                          \
+    __shared__ SimView sv_;                                                                   \
+    {                                                                                         \
+        const int* src_ = (const int*)(vs + blockIdx.y);                                      \
+        int* dst_ = (int*)&sv_;                                                               \
+        for (int w_ = threadIdx.x; w_ < (int)(sizeof(SimView) / 4); w_ += blockDim.x)        \
+            dst_[w_] = src_[w_];                                                              \
+    }                                                                                         \
+    __syncthreads();                                                                          \
+    const SimView& v = sv_;
+
 __device__ __forceinline__ int cell_lin(const SimView& v, double x, double y, double z) {
     return fine_cell(x, v.invf, v.Gf) + v.Gf * (fine_cell(y, v.invf, v.Gf) + v.Gf * fine_cell(z, v.invf, v.Gf));
 }
@@ -21,14 +34,16 @@ __device__ __forceinline__ int wrapi(int c, int G) { c %= G; return c < 0 ? c + 
 // Cell list: per fine cell a singly linked list through Bead::next plus prev[] for O(1)
 // removal. Built in canonical order (ascending bead id within a cell) so runs repeat.
 // ======================================================================================
-__global__ void k_cl_clear(SimView v, const int* flag) {
-    if (flag && !*flag) return;
+__global__ void k_cl_clear(const SimView* __restrict__ vs, int use_flag) {
+    SIM_PROLOGUE
+    if (use_flag && !*v.pw_rebuild) return;
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
         v.head[c] = -1;
 }
-__global__ void k_cl_insert(SimView v, const int* flag) {
-    if (flag && !*flag) return;
+__global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
+    SIM_PROLOGUE
+    if (use_flag && !*v.pw_rebuild) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         Bead b = v.bead[i];
         if (!(b.x >= 0.0 && b.x < v.L && b.y >= 0.0 && b.y < v.L && b.z >= 0.0 && b.z < v.L)) set_err(v, E_NONFINITE);
@@ -37,8 +52,9 @@ __global__ void k_cl_insert(SimView v, const int* flag) {
         v.bead[i].next = old;
     }
 }
-__global__ void k_cl_canon(SimView v, const int* flag) {
-    if (flag && !*flag) return;
+__global__ void k_cl_canon(const SimView* __restrict__ vs, int use_flag) {
+    SIM_PROLOGUE
+    if (use_flag && !*v.pw_rebuild) return;
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int ids[32];
@@ -69,31 +85,53 @@ __global__ void k_cl_canon(SimView v, const int* flag) {
         }
     }
 }
-void launch_cl_rebuild(const SimView& v, cudaStream_t s, const int* flag) {
-    int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
-    int bc = (int)std::min<int64_t>((nc + 255) / 256, 152 * 64);
-    int bb = (int)std::min<int64_t>((v.N + 255) / 256, 152 * 64);
-    k_cl_clear<<<bc, 256, 0, s>>>(v, flag);
-    k_cl_insert<<<bb, 256, 0, s>>>(v, flag);
-    k_cl_canon<<<bc, 256, 0, s>>>(v, flag);
+void launch_cl_rebuild(const SimView* d, const GroupDims& g, cudaStream_t s, int use_flag) {
+    const dim3 bc((unsigned)std::min<int64_t>((g.maxCells + 255) / 256, 152 * 64), g.S);
+    const dim3 bb((unsigned)std::min<int64_t>((g.maxN + 255) / 256, 152 * 64), g.S);
+    k_cl_clear<<<bc, 256, 0, s>>>(d, use_flag);
+    k_cl_insert<<<bb, 256, 0, s>>>(d, use_flag);
+    k_cl_canon<<<bc, 256, 0, s>>>(d, use_flag);
 }
 
-__global__ void k_check_positions(SimView v) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
-        Bead b = v.bead[i];
-        if (!(b.x >= 0.0 && b.x < v.L && b.y >= 0.0 && b.y < v.L && b.z >= 0.0 && b.z < v.L)) set_err(v, E_NONFINITE);
+// Slot counts of the sweep about to run, from the counter stream: floor(x) plus one more
+// with probability frac(x), per layer and for the plane waves.
+__global__ void k_counts(const SimView* __restrict__ vs) {
+    SIM_PROLOGUE
+    if (threadIdx.x != 0) return;
+    const uint64_t sw = v.step[0];
+    for (int l = 0; l < v.nL; l++) {
+        const u4 w = draw(v.k0, v.k1, K_COUNT, l, sw, 0u, 0u);
+        const double x = v.layer[l].expect, f = floor(x);
+        v.counts[l] = (int)f + ((u53(w.x, w.y) < x - f) ? 1 : 0);
     }
+    int mf = 0;
+    if (v.pw_on) {
+        const u4 w = draw(v.k0, v.k1, K_PWCOUNT, 0, sw, 0u, 0u);
+        const double x = v.expect_F, f = floor(x);
+        mf = (int)f + ((u53(w.x, w.y) < x - f) ? 1 : 0);
+    }
+    v.counts[kMaxLayers] = mf;
 }
-void launch_check_positions(const SimView& v, cudaStream_t s) {
-    int bb = (int)std::min<int64_t>((v.N + 255) / 256, 152 * 16);
-    k_check_positions<<<bb, 256, 0, s>>>(v);
+__global__ void k_advance(const SimView* __restrict__ vs, int which) {
+    SIM_PROLOGUE
+    if (threadIdx.x == 0) v.step[which] += 1;
+}
+void launch_counts(const SimView* d, const GroupDims& g, cudaStream_t s) {
+    k_counts<<<dim3(1, g.S), 32, 0, s>>>(d);
+}
+void launch_advance(const SimView* d, const GroupDims& g, int which, cudaStream_t s) {
+    k_advance<<<dim3(1, g.S), 32, 0, s>>>(d, which);
 }
 
 // ======================================================================================
 // Slots of a layer: scale in the band (Eq. 32 restricted to [lo, hi), inverse transform of
 // Appendix D) and the picked bead; then bucketing by coarse cell in colour-major order.
 // ======================================================================================
-__global__ void k_slots(SimView v, int l, uint64_t sweep, int M) {
+__global__ void k_slots(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL) return;
+    const int M = v.counts[l];
+    const uint64_t sweep = v.step[0];
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const LayerDev& Ly = v.layer[l];
@@ -106,11 +144,14 @@ __global__ void k_slots(SimView v, int l, uint64_t sweep, int M) {
     v.tr_n[Ly.tr_off + j] = 0;
     v.tr_du[Ly.tr_off + j] = 0.0;
 }
-void launch_slots(const SimView& v, int l, uint64_t sweep, int M, cudaStream_t s) {
-    k_slots<<<(M + 255) / 256, 256, 0, s>>>(v, l, sweep, M);
+void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+    k_slots<<<dim3((g.Mmax[l] + 255) / 256, g.S), 256, 0, s>>>(d, l);
 }
 
-__global__ void k_bucket_count(SimView v, int l, int M) {
+__global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0) return;
+    const int M = v.counts[l];
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const LayerDev& Ly = v.layer[l];
@@ -131,8 +172,15 @@ __global__ void k_bucket_count(SimView v, int l, int M) {
     v.slot_key[j] = key;
     atomicAdd(&v.q_count[key], 1);
 }
-// exclusive scan of n ints by one block (n up to a few million)
-__global__ void k_scan_single(const int* in, int* out, int n) {
+// exclusive scan of n ints by one block per simulation: mode 0 = bucket counts of layer l
+// (G^3 keys), mode 1 = region counts of layer l (Q^3 queues)
+__global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0) return;
+    const int G = v.layer[l].G, Q = G / v.K;
+    const int n = mode == 0 ? G * G * G : Q * Q * Q;
+    const int* in = mode == 0 ? v.q_count : v.rcount;
+    int* out = mode == 0 ? v.q_start : v.rstart;
     __shared__ int part[1024];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -154,7 +202,25 @@ __global__ void k_scan_single(const int* in, int* out, int n) {
         __syncthreads();
     }
 }
-__global__ void k_bucket_scatter(SimView v, int M) {
+// zero the per-phase counters: mode 0 = bucket counts, fills and deferral flags of layer l,
+// mode 1 = region counts and fills
+__global__ void k_zero(const SimView* __restrict__ vs, int mode, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0) return;
+    const int G = v.layer[l].G, Q = G / v.K;
+    const int n = mode == 0 ? G * G * G : Q * Q * Q;
+    int* a = mode == 0 ? v.q_count : v.rcount;
+    int* b = mode == 0 ? v.q_fill : v.rfill;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) { a[i] = 0; b[i] = 0; }
+    if (mode == 0) {
+        const int M = v.layer[l].Mmax;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) v.defer[i] = 0;
+    }
+}
+__global__ void k_bucket_scatter(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0) return;
+    const int M = v.counts[l];
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     int key = v.slot_key[j];
@@ -162,7 +228,10 @@ __global__ void k_bucket_scatter(SimView v, int M) {
     v.q_slots[pos] = j;
 }
 // slots of one queue in ascending slot id (the order of the sequential schedule)
-__global__ void k_bucket_sort(SimView v, int nkeys) {
+__global__ void k_bucket_sort(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0) return;
+    const int nkeys = v.layer[l].G * v.layer[l].G * v.layer[l].G;
     int key = blockIdx.x * blockDim.x + threadIdx.x;
     if (key >= nkeys) return;
     int s = v.q_start[key], n = v.q_count[key];
@@ -173,20 +242,20 @@ __global__ void k_bucket_sort(SimView v, int nkeys) {
         a[b + 1] = x;
     }
 }
-void launch_bucket(const SimView& v, int l, int M, cudaStream_t s) {
-    const int G = v.layer[l].G;
-    const int nkeys = G * G * G;
-    cudaMemsetAsync(v.q_count, 0, sizeof(int) * nkeys, s);
-    cudaMemsetAsync(v.q_fill, 0, sizeof(int) * nkeys, s);
-    cudaMemsetAsync(v.defer, 0, (size_t)M, s);
-    k_bucket_count<<<(M + 255) / 256, 256, 0, s>>>(v, l, M);
-    k_scan_single<<<1, 1024, 0, s>>>(v.q_count, v.q_start, nkeys);
-    k_bucket_scatter<<<(M + 255) / 256, 256, 0, s>>>(v, M);
-    k_bucket_sort<<<(nkeys + 127) / 128, 128, 0, s>>>(v, nkeys);
+void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+    const int keys = g.keys[l], M = g.Mmax[l];
+    k_zero<<<dim3((unsigned)std::min(1024, (std::max(keys, M) + 255) / 256), g.S), 256, 0, s>>>(d, 0, l);
+    k_bucket_count<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
+    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 0, l);
+    k_bucket_scatter<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
+    k_bucket_sort<<<dim3((keys + 127) / 128, g.S), 128, 0, s>>>(d, l);
 }
 
 // deferred slots in schedule order -> serial list
-__global__ void k_defer_compact(SimView v, int M) {
+__global__ void k_defer_compact(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0) return;
+    const int M = v.counts[l];
     __shared__ int part[1024];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -209,8 +278,8 @@ __global__ void k_defer_compact(SimView v, int M) {
     }
     if (threadIdx.x == 0) *v.serial_count = carry;
 }
-void launch_defer_compact(const SimView& v, int M, cudaStream_t s) {
-    k_defer_compact<<<1, 1024, 0, s>>>(v, M);
+void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+    k_defer_compact<<<dim3(1, g.S), 1024, 0, s>>>(d, l);
 }
 
 }  // namespace wmcd
@@ -681,72 +750,6 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     return ACCEPT;
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_colour(SimView v, int l, int colour, uint64_t sweep) {
-    __shared__ WarpSmem sm_all[kWarpsPerBlock];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem& sm = sm_all[wib];
-    const LayerDev& Ly = v.layer[l];
-    const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
-    const int q = blockIdx.x * kWarpsPerBlock + wib;
-    if (q >= nq) return;
-    const int key = colour * nq + q;
-    const int start = v.q_start[key], cnt = v.q_count[key];
-    if (cnt == 0) return;
-    const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
-    int64_t rlo[3], rhi[3];
-    for (int a = 0; a < 3; a++) {
-        rlo[a] = ceildiv((2 * (int64_t)c[a] - (K - 1)) * v.Gf, 2 * (int64_t)G);
-        rhi[a] = floordiv((2 * (int64_t)c[a] + 2 + (K - 1)) * v.Gf, 2 * (int64_t)G) - 1;
-    }
-    const int cell = c[0] + G * (c[1] + G * c[2]);
-    double carry = v.carry_q[Ly.carry_off + cell];
-    int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
-    long long bu = 0, moved = 0;
-    for (int t = 0; t < cnt; t++) {
-        const int j = v.q_slots[start + t];
-        const double lam = carry > 0.0 ? carry : v.slot_lam[j];
-        const int i = v.slot_bead[j];
-        int n = 0;
-        double du = 0.0;
-        int r = warp_attempt<PREC>(v, sm, l, j, i, lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks, &du);
-        __syncwarp();
-        if (r == DEFER) {
-            if (lane == 0) v.defer[start + t] = 1;
-            def++;
-            continue;
-        }
-        att++;
-        bu += n;
-        if (r == ACCEPT) { acc++; moved += n; }
-        if (lane == 0) {
-            v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
-            v.tr_n[Ly.tr_off + j] = n;
-            v.tr_du[Ly.tr_off + j] = du;
-        }
-        carry = (r == ACCEPT) ? 0.0 : lam;
-    }
-    if (lane == 0) {
-        v.carry_q[Ly.carry_off + cell] = carry;
-        atomicAdd(&v.ctr[C_ATT + l], (unsigned long long)att);
-        atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc);
-        atomicAdd(&v.ctr[C_DEF + l], (unsigned long long)def);
-        atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
-        atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
-        atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
-        atomicAdd(&v.ctr[C_CBU], (unsigned long long)bu);
-        atomicAdd(&v.ctr[C_CMOVED], (unsigned long long)moved);
-        atomicAdd(&v.ctr[C_CPE], (unsigned long long)pe);
-        if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
-    }
-}
-void launch_colour(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s) {
-    const int G = v.layer[l].G, Q = G / v.K, nq = Q * Q * Q;
-    const int blocks = (nq + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (v.precision == 0) k_colour<0><<<blocks, kWarpsPerBlock * 32, 0, s>>>(v, l, colour, sweep);
-    else k_colour<1><<<blocks, kWarpsPerBlock * 32, 0, s>>>(v, l, colour, sweep);
-}
-
 }  // namespace wmcd
 
 namespace wmcd {
@@ -756,7 +759,12 @@ namespace wmcd {
 // every slot of a serial layer, one move after another. Supports of any size.
 // ======================================================================================
 template <int PREC>
-__global__ void __launch_bounds__(kSerialThreads) k_serial(SimView v, int l, uint64_t sweep, int use_list, int M) {
+__global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.precision != PREC) return;
+    const int M = v.counts[l];
+    const int use_list = v.layer[l].G > 0;
+    const uint64_t sweep = v.step[0];
     __shared__ double sh_b[3], sh_p[3], sh_carry;
     __shared__ double sh_red[kSerialThreads / 32];
     __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3];
@@ -992,9 +1000,10 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(SimView v, int l, uin
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
     }
 }
-void launch_serial(const SimView& v, int l, uint64_t sweep, int use_list, int M, cudaStream_t s) {
-    if (v.precision == 0) k_serial<0><<<1, kSerialThreads, 0, s>>>(v, l, sweep, use_list, M);
-    else k_serial<1><<<1, kSerialThreads, 0, s>>>(v, l, sweep, use_list, M);
+void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+    // one launch per precision; each returns at once for simulations of the other precision
+    if (g.prec_mask & 1) k_serial<0><<<dim3(1, g.S), kSerialThreads, 0, s>>>(d, l);
+    if (g.prec_mask & 2) k_serial<1><<<dim3(1, g.S), kSerialThreads, 0, s>>>(d, l);
 }
 
 }  // namespace wmcd
@@ -1006,8 +1015,17 @@ namespace wmcd {
 // setup (1 thread) -> displacements (grid) -> energy change (grid, per-block partials)
 // -> decision (1 block, fixed-order sum) -> commit (grid) -> cell-list rebuild if moved.
 // ======================================================================================
-__global__ void k_pw_setup(SimView v, int kmode, int kdir, uint64_t ctr, int m, int trace_index) {
+// direct = 0: the m-th plane-wave slot of the current sweep (active if m < the sweep's count);
+// direct = 1: the m-th move of a direct call. The counter is the sweep or the call index.
+__global__ void k_pw_setup(const SimView* __restrict__ vs, int direct, int m) {
+    SIM_PROLOGUE
+    if (threadIdx.x != 0) return;
     PWDev& P = *v.pw;
+    P.active = direct ? 1 : (v.pw_on && m < v.counts[kMaxLayers]);
+    if (!P.active) return;
+    const uint64_t ctr = v.step[direct ? 1 : 0];
+    const int kmode = direct ? K_DPWMODE : K_PWMODE, kdir = direct ? K_DPWDIR : K_PWDIR;
+    const int trace_index = m;
     u4 w1 = draw(v.k0, v.k1, (uint32_t)kmode, 0, ctr, (uint32_t)m, 0);
     u4 w2 = draw(v.k0, v.k1, (uint32_t)kdir, 0, ctr, (uint32_t)m, 0);
     const double u_mode = u53(w1.x, w1.y), phi = u53(w1.z, w1.w), psi = u53(w2.x, w2.y);
@@ -1062,9 +1080,10 @@ __global__ void k_pw_setup(SimView v, int kmode, int kdir, uint64_t ctr, int m, 
     P.reach = v.rc + 2.0 * fabs(P.AF) + 1e-9;
 }
 
-__global__ void k_pw_disp(SimView v) {
+__global__ void k_pw_disp(const SimView* __restrict__ vs) {
+    SIM_PROLOGUE
     const PWDev& P = *v.pw;
-    if (P.null_move) return;
+    if (!P.active || P.null_move) return;
     const double lx = (double)P.lv[0], ly = (double)P.lv[1], lz = (double)P.lv[2];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         const Bead b = v.bead[i];
@@ -1084,9 +1103,11 @@ __global__ void k_pw_disp(SimView v) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_pw_energy(SimView v) {
+__global__ void __launch_bounds__(256) k_pw_energy(const SimView* __restrict__ vs) {
+    SIM_PROLOGUE
     __shared__ double red[8];
     const PWDev& P = *v.pw;
+    if (!P.active || blockIdx.x >= v.pw_blocks) return;
     double dU = 0.0;
     long long pe = 0;
     if (!P.null_move) {
@@ -1139,10 +1160,14 @@ __global__ void __launch_bounds__(256) k_pw_energy(SimView v) {
     if (pe) atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
 }
 
-__global__ void __launch_bounds__(256) k_pw_decide(SimView v, int kacc, uint64_t ctr, int m, int trace_index) {
+__global__ void __launch_bounds__(256) k_pw_decide(const SimView* __restrict__ vs, int direct, int m) {
+    SIM_PROLOGUE
     __shared__ double red[8];
     PWDev& P = *v.pw;
-    if (P.null_move) return;
+    if (!P.active || P.null_move) return;
+    const uint64_t ctr = v.step[direct ? 1 : 0];
+    const int kacc = direct ? K_DPWACC : K_PWACC;
+    const int trace_index = m;
     double s = 0.0;
     for (int b = threadIdx.x; b < v.pw_blocks; b += 256) s += v.pw_part[b];
     s = warp_sum(s);
@@ -1167,10 +1192,11 @@ __global__ void __launch_bounds__(256) k_pw_decide(SimView v, int kacc, uint64_t
     if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_out[trace_index] = (uint8_t)(acc ? 1 : 2);
 }
 
-__global__ void k_pw_commit(SimView v, int* rebuild) {
+__global__ void k_pw_commit(const SimView* __restrict__ vs) {
+    SIM_PROLOGUE
     const PWDev& P = *v.pw;
-    const bool moved = P.accept && !P.null_move;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *rebuild = moved;
+    const bool moved = P.active && P.accept && !P.null_move;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *v.pw_rebuild = moved;
     if (!moved) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         v.bead[i].x = v.pw_new[3 * i]; v.bead[i].y = v.pw_new[3 * i + 1]; v.bead[i].z = v.pw_new[3 * i + 2];
@@ -1183,16 +1209,15 @@ __global__ void k_pw_commit(SimView v, int* rebuild) {
     }
 }
 
-void launch_planewave(const SimView& v, int kmode, int kdir, int kacc, uint64_t ctr, int m, int trace_index,
-                      cudaStream_t s) {
-    const int nb = v.pw_blocks;
+void launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s) {
+    const int nb = g.pw_blocks;
     const int gb = (int)std::min<int64_t>(nb, 152 * 16);
-    k_pw_setup<<<1, 1, 0, s>>>(v, kmode, kdir, ctr, m, trace_index);
-    k_pw_disp<<<gb, 256, 0, s>>>(v);
-    k_pw_energy<<<nb, 256, 0, s>>>(v);
-    k_pw_decide<<<1, 256, 0, s>>>(v, kacc, ctr, m, trace_index);
-    k_pw_commit<<<gb, 256, 0, s>>>(v, v.pw_rebuild);
-    launch_cl_rebuild(v, s, v.pw_rebuild);
+    k_pw_setup<<<dim3(1, g.S), 32, 0, s>>>(d, direct, m);
+    k_pw_disp<<<dim3(gb, g.S), 256, 0, s>>>(d);
+    k_pw_energy<<<dim3(nb, g.S), 256, 0, s>>>(d);
+    k_pw_decide<<<dim3(1, g.S), 256, 0, s>>>(d, direct, m);
+    k_pw_commit<<<dim3(gb, g.S), 256, 0, s>>>(d);
+    launch_cl_rebuild(d, g, s, 1);
 }
 
 }  // namespace wmcd
@@ -1205,7 +1230,9 @@ namespace wmcd {
 // them into shared memory once, runs all its moves there and writes them back at the end.
 // Beads are assigned to regions by a counting sort over all beads before each colour phase.
 // ======================================================================================
-__global__ void k_region_count(SimView v, int l, int colour) {
+__global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0 || colour >= v.K * v.K * v.K) return;
     const int K = v.K, Gf = v.Gf, Q = v.layer[l].G / K;
     const int ox = colour % K, oy = (colour / K) % K, oz = colour / (K * K);
     const int* tab = v.axis_tab + (size_t)l * K * Gf;
@@ -1219,7 +1246,9 @@ __global__ void k_region_count(SimView v, int l, int colour) {
         if (key >= 0) atomicAdd(&v.rcount[key], 1);
     }
 }
-__global__ void k_region_scatter(SimView v) {
+__global__ void k_region_scatter(const SimView* __restrict__ vs, int l, int colour) {
+    SIM_PROLOGUE
+    if (l >= v.nL || v.layer[l].G == 0 || colour >= v.K * v.K * v.K) return;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
         const int key = v.rkey[m];
         if (key >= 0) v.rlist[v.rstart[key] + atomicAdd(&v.rfill[key], 1)] = (int)m;
@@ -1561,8 +1590,11 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, int l, int colour, uint64_t sweep) {
+__global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour) {
+    SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
+    if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
+    const uint64_t sweep = v.step[0];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const LayerDev& Ly = v.layer[l];
@@ -1732,22 +1764,23 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(SimView v, i
 
 size_t staged_smem_bytes(int cap) { return (size_t)kStageWarps * warp_stride(cap); }
 
-void launch_colour_staged(const SimView& v, int l, int colour, uint64_t sweep, cudaStream_t s) {
-    const int G = v.layer[l].G, Q = G / v.K, nq = Q * Q * Q;
-    const int gb = (int)std::min<int64_t>((v.N + 255) / 256, 152 * 16);
-    cudaMemsetAsync(v.rcount, 0, sizeof(int) * nq, s);
-    cudaMemsetAsync(v.rfill, 0, sizeof(int) * nq, s);
-    k_region_count<<<gb, 256, 0, s>>>(v, l, colour);
-    k_scan_single<<<1, 1024, 0, s>>>(v.rcount, v.rstart, nq);
-    k_region_scatter<<<gb, 256, 0, s>>>(v);
-    const size_t smem = staged_smem_bytes(v.stage_cap);
-    const int blocks = (nq + kStageWarps - 1) / kStageWarps;
-    if (v.precision == 0) {
+void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s) {
+    const int nq = g.nq[l];
+    const int gb = (int)std::min<int64_t>((g.maxN + 255) / 256, 152 * 16);
+    k_zero<<<dim3((unsigned)std::min(1024, (nq + 255) / 256), g.S), 256, 0, s>>>(d, 1, l);
+    k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
+    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l);
+    k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
+    const size_t smem = staged_smem_bytes(g.stage_cap);
+    const dim3 grid((nq + kStageWarps - 1) / kStageWarps, g.S);
+    // one launch per precision; each returns at once for simulations of the other precision
+    if (g.prec_mask & 1) {
         cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_colour_staged<0><<<blocks, kStageWarps * 32, smem, s>>>(v, l, colour, sweep);
-    } else {
+        k_colour_staged<0><<<grid, kStageWarps * 32, smem, s>>>(d, l, colour);
+    }
+    if (g.prec_mask & 2) {
         cudaFuncSetAttribute(k_colour_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_colour_staged<1><<<blocks, kStageWarps * 32, smem, s>>>(v, l, colour, sweep);
+        k_colour_staged<1><<<grid, kStageWarps * 32, smem, s>>>(d, l, colour);
     }
 }
 

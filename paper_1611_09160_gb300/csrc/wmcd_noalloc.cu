@@ -35,7 +35,10 @@ constexpr int64_t oErr = oCtr + al(8 * C_NCTR);
 constexpr int64_t oRebuild = oErr + al(4);
 constexpr int64_t oModes = oRebuild + al(4);
 constexpr int64_t oCdf = oModes + al(12 * kNaModes);
-constexpr int64_t kNaBytes = oCdf + al(8 * kNaModes);   // about 1.9 MB
+constexpr int64_t oView = oCdf + al(8 * kNaModes);
+constexpr int64_t oStep = oView + al(sizeof(SimView));
+constexpr int64_t oCounts = oStep + al(16);
+constexpr int64_t kNaBytes = oCounts + al(4 * (kMaxLayers + 1));   // about 1.9 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -82,6 +85,8 @@ static double h_key[3] = {-1.0, -1.0, -1.0};
 // host staging of the call's small inputs (copied to the device before the call returns)
 static uint8_t h_bnext[kNaBeads];
 static int h_carry[4];
+static SimView h_view;
+static uint64_t h_step[2];
 
 }  // namespace wmcd
 
@@ -122,7 +127,7 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     int rc = na_scratch(&base);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    SimView v;
+    SimView& v = h_view;
     std::memset(&v, 0, sizeof v);
     v.bead = (Bead*)(base + oBead);
     v.prev = (int*)(base + oPrev);
@@ -162,11 +167,27 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     v.k0 = (uint32_t)P.seed;
     v.k1 = (uint32_t)(P.seed >> 32) ^ (uint32_t)P.sim_id;
     v.pw_blocks = (int)((N + 255) / 256);
+    v.step = (uint64_t*)(base + oStep);
+    v.counts = (int*)(base + oCounts);
+    v.pw_on = 1;
+    SimView* dview = (SimView*)(base + oView);
+    GroupDims g;
+    g.S = 1;
+    g.maxN = N;
+    g.maxCells = (int64_t)P.grid_f * P.grid_f * P.grid_f;
+    g.pw = true;
+    g.pw_blocks = v.pw_blocks;
+    g.prec_mask = 1 << P.precision;
+    h_step[0] = 0;
+    h_step[1] = (uint64_t)call_index;
     // inputs: bond flags, mode table, carry; zero what must start at zero
     h_carry[0] = carry[0]; h_carry[1] = carry[1]; h_carry[2] = carry[2]; h_carry[3] = carry[3];
     cudaMemcpyAsync(v.bnext, h_bnext, (size_t)N, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(base + oModes, h_modes, sizeof(int) * 3 * h_nmodes, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(base + oCdf, h_cdf, sizeof(double) * h_nmodes, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dview, &v, sizeof(SimView), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(v.step, h_step, sizeof h_step, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(v.counts, 0, 4 * (kMaxLayers + 1), s);
     cudaMemsetAsync(v.pw, 0, sizeof(PWDev), s);
     cudaMemcpyAsync(v.ctr, h_carry, sizeof h_carry, cudaMemcpyHostToDevice, s);   // carry staged in ctr[0..1]
     k_na_carry<<<1, 1, 0, s>>>(v.pw, (const int*)v.ctr);
@@ -176,9 +197,8 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     const int gb = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
     k_na_check<<<gb, 256, 0, s>>>(pos, N, v.L, v.err);
     k_na_fill<<<gb, 256, 0, s>>>(v.bead, pos, N);
-    launch_cl_rebuild(v, s, nullptr);
-    for (int64_t m = 0; m < n_moves; m++)
-        launch_planewave(v, K_DPWMODE, K_DPWDIR, K_DPWACC, (uint64_t)call_index, (int)m, -1, s);
+    launch_cl_rebuild(dview, g, s, 0);
+    for (int64_t m = 0; m < n_moves; m++) launch_planewave(dview, g, 1, (int)m, s);
     k_na_read<<<gb, 256, 0, s>>>(v.bead, pos, N);
     // outputs: the carried wave vector, and the error flags
     int out[5] = {0, 0, 0, 0, 0};
