@@ -35,7 +35,8 @@ typedef enum wmcd_status {
     WMCD_ENOMEM = -2,     /* device or host allocation failed */
     WMCD_ECUDA = -3,      /* a CUDA runtime call failed */
     WMCD_ETIMEOUT = -4,   /* a bounded device-side wait or list walk gave up */
-    WMCD_ESTATE = -5      /* non-finite positions or a corrupted cell list were detected */
+    WMCD_ESTATE = -5,     /* non-finite positions or a corrupted cell list were detected */
+    WMCD_EFULL = -6       /* a batch has no free slot, or its pool no room, for the simulation */
 } wmcd_status;
 
 enum { WMCD_BOND_NONE = 0, WMCD_BOND_HARMONIC = 1, WMCD_BOND_FENE = 2 };
@@ -181,8 +182,56 @@ int wmcd_device_bytes(wmcd_handle* h, int64_t* bytes);
 int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, const int32_t* chain_len, int64_t n_chains,
                            int64_t call_index, int32_t* carry, int64_t n_moves, void* stream);
 
+/* Launch shapes: warps per block of the concurrent wavelet kernel (one coarse-cell queue per
+ * warp), 1..4, lowered where the block's shared memory would exceed 227 KB (default 2); and
+ * threads of the serial-phase block, 32, 128 or 512 (default 512). Choices of launch shape
+ * only: decisions and positions do not depend on them (an energy change is summed in another
+ * order, which moves it by rounding). WMCD_EINVAL for other values. */
+int wmcd_set_block(wmcd_handle* h, int stage_warps, int serial_threads);
+
+/* Releases the handle and its device state. WMCD_EINVAL for a handle a batch owns. */
 int wmcd_destroy(wmcd_handle* h);
 const char* wmcd_strerror(int status);
+
+/* ---- batches (many simulations, one launch per phase) and serving --------------------
+ * A batch keeps up to `capacity` independent simulations (any N, box, parameters, precision)
+ * resident on the current device and advances all of them together: every phase of a sweep
+ * (slot generation, bucketing, each colour, the serial phase, each plane-wave slot) is one
+ * kernel launch over all resident simulations, and the whole sweep is recorded once as a CUDA
+ * graph, which wmcd_batch_step replays. Each simulation's random stream, schedule and
+ * reduction order are its own, so a simulation follows exactly the trajectory it follows
+ * alone under wmcd_sweep, whatever else is in the batch (Sec. V-VIII order per simulation).
+ *
+ * Device memory: the batch reserves one pool of `pool_bytes` at creation and places each
+ * admitted simulation's whole state in one block of it (first fit, blocks merged on release);
+ * admission fails with WMCD_EFULL when no slot is free or no free block is large enough.
+ *
+ * Streams: admission runs on a stream of the batch's own, so it overlaps with steps already
+ * queued on the caller's stream, and returns when the new state is on the device. Steps are
+ * asynchronous on `stream`. Retiring synchronises `stream` before the memory is reused.
+ * Not thread-safe. */
+typedef struct wmcd_batch wmcd_batch;
+int wmcd_batch_create(int capacity, int64_t pool_bytes, wmcd_batch** out);
+/* pool bytes a simulation with these parameters takes (its state placed in one block) */
+int wmcd_batch_need(const wmcd_params* params, int64_t* bytes);
+/* admit a simulation (arguments as wmcd_create); *slot receives its slot id, 0..capacity-1 */
+int wmcd_batch_admit(wmcd_batch* b, const wmcd_params* params, const double* pos, const int32_t* chain_len,
+                     int64_t n_chains, int* slot);
+/* n_sweeps sweeps of every resident simulation, one graph launch per sweep */
+int wmcd_batch_step(wmcd_batch* b, int64_t n_sweeps, void* stream);
+/* the handle of a resident simulation (borrowed, valid until retired): positions, stats,
+ * trace and checkpoint calls work on it as on a lone simulation */
+int wmcd_batch_handle(wmcd_batch* b, int slot, wmcd_handle** h);
+/* release a simulation's slot and pool block (synchronises `stream` first) */
+int wmcd_batch_retire(wmcd_batch* b, int slot, void* stream);
+/* launch shapes for the whole batch (as wmcd_set_block); the graph is recorded again */
+int wmcd_batch_set_block(wmcd_batch* b, int stage_warps, int serial_threads);
+/* resident simulations, free pool bytes, largest free block, and kernel launches (graph
+ * nodes) per batched sweep (0 before the first step after a change) */
+int wmcd_batch_info(wmcd_batch* b, int64_t* resident, int64_t* pool_free, int64_t* largest_free,
+                    int64_t* launches_per_sweep);
+/* releases every resident simulation and the pool */
+int wmcd_batch_destroy(wmcd_batch* b);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,149 @@
+"""Autotuner for the concurrent schedule and the launch shapes, by measurement on the GPU.
+
+Two kinds of choice are tuned, and they are kept apart because they differ in what they
+change:
+
+* The schedule of a simulation: fine-cell size (``cell_scale`` times the interaction reach),
+  colouring stride (``colour_K``), which layers run coloured (``min_queues_per_axis``,
+  ``serial_only``). The schedule fixes the order of moves, so it is part of a simulation's
+  definition: it is chosen per system *shape* (bead count, box, potential, precision) from a
+  table, never from what else shares a batch, so a request gets the same schedule, and the
+  same trajectory, alone or in any batch.
+* Launch shapes (warps per block of the concurrent kernel, threads of the serial block):
+  results do not depend on them, so they are tuned per batch.
+
+Every candidate is timed on a throw-away simulation of a synthetic system of the shape (the
+same generator as the workloads), a few sweeps after warm-up, with CUDA events; the score is
+bead-updates per second.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from . import inputs as I
+from . import schedule as S
+from . import wmcd
+
+SCHEDULE_CANDIDATES = (
+    {"colour_K": 2},
+    {"colour_K": 2, "cell_scale": 1.5},
+    {"colour_K": 2, "cell_scale": 2.0},
+    {"colour_K": 3},
+    {"colour_K": 2, "min_queues_per_axis": 3},
+    {"colour_K": 2, "serial_only": True},
+)
+LAUNCH_CANDIDATES = ((2, 512), (2, 128), (2, 32), (1, 32), (4, 32), (1, 128))
+
+
+def shape_key(n_beads: int, box_L: float, precision: int, planewave_mode: int) -> str:
+    """Table key: bead count to the nearest power of two, box side on a half-octave grid."""
+    nb = 1 << max(0, int(round(math.log2(max(1, n_beads)))))
+    lb = round(2 * math.log2(box_L)) / 2
+    return f"N{nb}_L{lb:.3f}_p{precision}_w{planewave_mode}"
+
+
+def _time_sim(params: dict, system, warm: int, sweeps: int) -> float:
+    import torch
+    sim = wmcd.Simulation(params, system.pos, system.chain_len)
+    try:
+        sim.sweep(warm)
+        torch.cuda.synchronize()
+        b0 = sim.stats().bead_updates
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.sweep(sweeps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        return (sim.stats().bead_updates - b0) / (ms / 1e3)
+    finally:
+        sim.close()
+
+
+class Tuner:
+    """Per-shape schedule table (optionally kept in a JSON file) and launch-shape tuning."""
+
+    def __init__(self, path: str | None = None, warm: int = 2, sweeps: int = 4):
+        self.path = path
+        self.warm, self.sweeps = warm, sweeps
+        self.table = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.table = json.load(f)
+
+    def save(self):
+        if self.path:
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.table, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+
+    def schedule(self, base: dict, system=None, chain_lengths=None) -> dict:
+        """Parameters ``base`` with the tuned schedule of its shape (measured on first use)."""
+        key = shape_key(base["n_beads"], base["box_L"], base.get("precision", 0), base.get("planewave_mode", 0))
+        if key not in self.table:
+            self.table[key] = self._tune_schedule(base, system, chain_lengths)
+            self.save()
+        return self.apply(base, self.table[key]["choice"])
+
+    @staticmethod
+    def apply(base: dict, choice: dict) -> dict:
+        p = dict(base)
+        p.update(S.choose(p["box_L"], p["lambda_min"], p["lambda_max"], p["A0"], p["wca_sigma"], p["wca_eps"],
+                          **choice))
+        return p
+
+    def _tune_schedule(self, base: dict, system, chain_lengths) -> dict:
+        if system is None:
+            lens = chain_lengths if chain_lengths is not None else [base["n_beads"]]
+            system = I.make_system(list(lens), 0, base["box_L"], seed=12345)
+        scores = []
+        for cand in SCHEDULE_CANDIDATES:
+            try:
+                p = self.apply(base, cand)
+            except ValueError:
+                continue
+            scores.append((_time_sim(p, system, self.warm, self.sweeps), cand))
+        best = max(scores, key=lambda t: t[0])
+        return {"choice": best[1], "scores": [[s, c] for s, c in scores]}
+
+    def launch_shape(self, batch, sweeps: int = 2):
+        """Time each launch shape on ``batch`` (advancing its simulations: results do not
+        depend on the shape) and keep the fastest. Returns (stage_warps, serial_threads)."""
+        import torch
+        best, best_ms = None, float("inf")
+        for shape in LAUNCH_CANDIDATES:
+            batch.set_block(*shape)
+            batch.step(1)                      # records the graph for this shape
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.step(sweeps)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms < best_ms:
+                best, best_ms = shape, ms
+        batch.set_block(*best)
+        return best
+
+
+def ensemble_params(systems, precision: int, planewave_mode: int, seed: int, tuner: Tuner | None = None):
+    """Parameters of an ensemble of single-chain systems (the uneven-size batch workload)."""
+    out = []
+    for k, s in enumerate(systems):
+        p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, sim_id=k, precision=precision,
+                                planewave_mode=planewave_mode)
+        if tuner is not None:
+            p = tuner.schedule(p, chain_lengths=s.chain_len)
+        out.append(p)
+    return out
+
+
+def sample_shapes(n_beads: np.ndarray, n: int) -> np.ndarray:
+    """Representative bead counts (quantiles) to tune ahead of a run."""
+    return np.unique(np.quantile(n_beads, np.linspace(0, 1, n)).astype(int))

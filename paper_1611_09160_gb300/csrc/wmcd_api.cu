@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 #include "../../include/wmcd.h"
-#include "wmcd_internal.h"
+#include "wmcd_host.h"
 
 namespace wmcd {
 
@@ -56,12 +56,22 @@ static double gl10(double a, double b) {
 static double tail3(double Kc) {
     return 16.0 * kPi * kPi * (0.125 * std::pow(Kc, -4) + 0.75 * std::pow(Kc, -6) + 12.0 * std::pow(Kc, -8));
 }
+static const std::vector<double>& G_panels() {
+    // acc[p] = G(p h), summed from the tail inwards once per process
+    static const std::vector<double> acc = [] {
+        const double h = kPi / 20.0;
+        const int panels = 40000;             // up to Kc = 2000 pi (a multiple of pi)
+        std::vector<double> a(panels + 1);
+        a[panels] = tail3(panels * h);
+        for (int p = panels - 1; p >= 0; p--) a[p] = a[p + 1] + gl10(p * h, (p + 1) * h);
+        return a;
+    }();
+    return acc;
+}
 static void G_table(const std::vector<double>& Q, std::vector<double>& out) {
     const double h = kPi / 20.0;
-    const int panels = 40000;                 // up to Kc = 2000 pi (a multiple of pi)
-    std::vector<double> acc(panels + 1);
-    acc[panels] = tail3(panels * h);
-    for (int p = panels - 1; p >= 0; p--) acc[p] = acc[p + 1] + gl10(p * h, (p + 1) * h);
+    const int panels = 40000;
+    const std::vector<double>& acc = G_panels();
     out.resize(Q.size());
     for (size_t i = 0; i < Q.size(); i++) {
         double q = Q[i];
@@ -72,35 +82,7 @@ static void G_table(const std::vector<double>& Q, std::vector<double>& out) {
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// handle
-// ---------------------------------------------------------------------------------------
-struct Handle {
-    wmcd_params P;
-    SimView v;                   // host copy of the view
-    SimView* dview = nullptr;    // device copy read by every kernel
-    GroupDims g;                 // launch bounds of this one simulation
-    int dev = 0;
-    int64_t N = 0;
-    int nL = 0;
-    double expect[kMaxLayers] = {0};
-    int Mmax[kMaxLayers] = {0};
-    double p_fourier = 0.0, dt_move = 0.0, R = 1.0;
-    uint64_t sweep = 0, pw_calls = 0;
-    int64_t tr_pw_count = 0;
-    int64_t launches = 0;        // kernels launched by this handle
-    std::vector<void*> allocs;
-    size_t bytes = 0;
-    double* staging = nullptr;   // 3N doubles
-    // profiling
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
-    int64_t prof_launches[8] = {0};
-    double prof_ms[8] = {0};
-};
-
-static int last_cuda_status() {
+int last_cuda_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
 }
@@ -108,6 +90,16 @@ static int last_cuda_status() {
 template <class T>
 static int dalloc(Handle* h, T** p, size_t count) {
     size_t nb = std::max<size_t>(count, 1) * sizeof(T);
+    if (h->arena) {
+        Arena& a = *h->arena;
+        const size_t off = (a.used + 255) & ~(size_t)255;
+        a.used = off + nb;
+        h->bytes += nb;
+        if (a.count_only) { *p = nullptr; return WMCD_OK; }
+        if (a.used > a.size) return WMCD_ENOMEM;
+        *p = (T*)(a.base + off);
+        return WMCD_OK;
+    }
     void* q = nullptr;
     if (cudaMalloc(&q, nb) != cudaSuccess) { cudaGetLastError(); return WMCD_ENOMEM; }
     h->allocs.push_back(q);
@@ -158,7 +150,7 @@ struct ProfScope {
 };
 
 // stratified slot count: floor(x) plus one more with probability frac(x)
-static int64_t slot_count(const Handle* h, uint32_t kind, int l, uint64_t ctr, double x) {
+int64_t slot_count(const Handle* h, uint32_t kind, int l, uint64_t ctr, double x) {
     u4 w = draw(h->v.k0, h->v.k1, kind, l, ctr, 0u, 0u);
     double u = u53(w.x, w.y), f = std::floor(x);
     return (int64_t)f + ((u < x - f) ? 1 : 0);
@@ -183,7 +175,6 @@ static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64
 
 using namespace wmcd;
 
-struct wmcd_handle { Handle h; };
 
 static int validate(const wmcd_params* p) {
     if (!p || p->n_beads < 1 || p->n_beads > (int64_t)1 << 30) return WMCD_EINVAL;
@@ -201,20 +192,20 @@ static int validate(const wmcd_params* p) {
     return WMCD_OK;
 }
 
-extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,
-                           void* stream, wmcd_handle** out) {
-    if (!out || !pos || !chain_len || n_chains < 1) return WMCD_EINVAL;
-    *out = nullptr;
+int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double* pos, const int32_t* chain_len,
+                        int64_t n_chains, cudaStream_t s, Arena* arena) {
+    const bool counting = arena && arena->count_only;
     int rc = validate(params);
     if (rc) return rc;
     const wmcd_params& P = *params;
-    int64_t tot = 0;
-    for (int64_t c = 0; c < n_chains; c++) { if (chain_len[c] < 1) return WMCD_EINVAL; tot += chain_len[c]; }
-    if (tot != P.n_beads) return WMCD_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    wmcd_handle* H = new (std::nothrow) wmcd_handle();
-    if (!H) return WMCD_ENOMEM;
+    if (!counting) {
+        if (!pos || !chain_len || n_chains < 1) return WMCD_EINVAL;
+        int64_t tot = 0;
+        for (int64_t c = 0; c < n_chains; c++) { if (chain_len[c] < 1) return WMCD_EINVAL; tot += chain_len[c]; }
+        if (tot != P.n_beads) return WMCD_EINVAL;
+    }
     Handle* h = &H->h;
+    h->arena = arena;
     h->P = P;
     h->N = P.n_beads;
     cudaGetDevice(&h->dev);
@@ -275,7 +266,7 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     // octave layers of P_lambda (Eq. 32)
     int nL = 1;
     while (P.lambda_min * std::ldexp(1.0, nL) < P.lambda_max) nL++;
-    if (nL > kMaxLayers) { delete H; return WMCD_EINVAL; }
+    if (nL > kMaxLayers) return WMCD_EINVAL;
     h->nL = v.nL = nL;
     const double imin3 = 1.0 / ((P.lambda_min * P.lambda_min) * P.lambda_min);
     const double imax3 = 1.0 / ((P.lambda_max * P.lambda_max) * P.lambda_max);
@@ -294,7 +285,6 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
         Mall = std::max<int64_t>(Mall, h->Mmax[l]);
         Ly.G = P.grid_layer[l];
         if (Ly.G < 0 || (Ly.G > 0 && (Ly.G % P.colour_K != 0 || Ly.G < P.colour_K)) || Ly.G > 256) {
-            delete H;
             return WMCD_EINVAL;
         }
         Ly.invG = Ly.G > 0 ? (double)Ly.G / P.box_L : 0.0;
@@ -321,6 +311,7 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     bool ok = true;
     ok = ok && !dalloc(h, &v.bead, N) && !dalloc(h, &v.prev, N) && !dalloc(h, &v.img, 3 * N) &&
          !dalloc(h, &v.bnext, N) && !dalloc(h, &v.head, ncell);
+    ok = ok && !dalloc(h, &v.slot_V, 3 * Mall) && !dalloc(h, &v.slot_p, 3 * Mall) && !dalloc(h, &v.slot_thr, Mall);
     ok = ok && !dalloc(h, &v.slot_lam, Mall) && !dalloc(h, &v.slot_bead, Mall) && !dalloc(h, &v.slot_key, Mall) &&
          !dalloc(h, &v.q_slots, Mall) && !dalloc(h, &v.defer, Mall) && !dalloc(h, &v.serial_list, Mall);
     ok = ok && !dalloc(h, &v.q_count, keys_max) && !dalloc(h, &v.q_start, keys_max) && !dalloc(h, &v.q_fill, keys_max);
@@ -331,6 +322,7 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     ok = ok && !dalloc(h, &v.ctr, C_NCTR) && !dalloc(h, &v.err, 1);
     ok = ok && !dalloc(h, &v.s_ids, N) && !dalloc(h, &v.s_d, 4 * N) && !dalloc(h, &v.s_new, 3 * N) &&
          !dalloc(h, &v.s_img, N) && !dalloc(h, &v.s_slot, N) && !dalloc(h, &v.s_changed, 3 * N) &&
+         !dalloc(h, &v.s_box, 6 * N) && !dalloc(h, &v.s_pre, N + 1) &&
          !dalloc(h, &v.serial_tag, 1);
     ok = ok && !dalloc(h, &v.pw, 1) && !dalloc(h, &v.pw_new, 3 * N) && !dalloc(h, &v.pw_imgd, N) &&
          !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1);
@@ -361,7 +353,8 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     int* d_tab = nullptr;
     ok = ok && !dalloc(h, &v.rkey, N) && !dalloc(h, &v.rlist, N) && !dalloc(h, &v.rcount, nq_max) &&
          !dalloc(h, &v.rstart, nq_max) && !dalloc(h, &v.rfill, nq_max) && !dalloc(h, &d_tab, tab.size());
-    if (!ok) { wmcd_destroy(H); return WMCD_ENOMEM; }
+    if (!ok) return WMCD_ENOMEM;
+    if (counting) return WMCD_OK;
     v.axis_tab = d_tab;
     {
         // staging capacity per warp: room for 16x the average bead count of a layer-0 region
@@ -427,10 +420,23 @@ extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const i
     cudaMemsetAsync(v.tr_n, 0, std::max<int64_t>(tr_total, 1) * sizeof(int), s);
     k_fill_beads<<<grid_for(N), 256, 0, s>>>(v.bead, h->staging, N);
     launch_cl_rebuild(h->dview, h->g, s, 0);
-    if (cudaStreamSynchronize(s) != cudaSuccess || last_cuda_status()) { cudaGetLastError(); wmcd_destroy(H); return WMCD_ECUDA; }
+    if (cudaStreamSynchronize(s) != cudaSuccess || last_cuda_status()) { cudaGetLastError(); return WMCD_ECUDA; }
     int err = 0;
-    cudaMemcpy(&err, v.err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) { wmcd_destroy(H); return WMCD_EINVAL; }   // a coordinate outside [0, L) or not finite
+    cudaMemcpyAsync(&err, v.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+    if (err) return WMCD_EINVAL;   // a coordinate outside [0, L) or not finite
+    h->arena = nullptr;            // later allocations (trace growth) are the handle's own
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,
+                           void* stream, wmcd_handle** out) {
+    if (!out || !pos || !chain_len || n_chains < 1) return WMCD_EINVAL;
+    *out = nullptr;
+    wmcd_handle* H = new (std::nothrow) wmcd_handle();
+    if (!H) return WMCD_ENOMEM;
+    const int rc = create_handle(H, params, pos, chain_len, n_chains, (cudaStream_t)stream, nullptr);
+    if (rc) { destroy_handle(H); return rc; }
     *out = H;
     return WMCD_OK;
 }
@@ -443,7 +449,7 @@ static int popcount3(int m) { return (m & 1) + ((m >> 1) & 1); }
 // this sweep's exact slot counts, used to leave out launches with no work; a batch launches
 // every phase up to its bounds and the kernels return early where a simulation has none.
 // Returns the number of kernels launched.
-int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s) {
+int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s) {
     const int np = popcount3(g.prec_mask);
     int64_t launches = 0;
     { ProfScope ps(prof, 4, s); launch_counts(d, g, s); }
@@ -459,7 +465,7 @@ int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, H
             launches += 5 + (int64_t)g.maxK3 * (4 + np) + 1;
         }
         { ProfScope ps(prof, 1, s); launch_serial(d, g, l, s); }
-        launches += np;
+        launches += 1 + np;
     }
     if (g.pw) {
         const int64_t MF = hc ? hc[kMaxLayers] : g.maxMF;
@@ -505,6 +511,7 @@ extern "C" int wmcd_planewave(wmcd_handle* H, int64_t n_moves, void* stream) {
         h->v.tr_pw_mode = md;
         h->v.tr_pw_cap = (int)std::min<int64_t>(n_moves, 1 << 30);
         cudaMemcpyAsync(h->dview, &h->v, sizeof(SimView), cudaMemcpyHostToDevice, s);
+        if (h->batch) batch_view_changed(h->batch);
     }
     for (int64_t m = 0; m < n_moves; m++) {
         ProfScope ps(h, 2, s);
@@ -732,8 +739,7 @@ extern "C" int wmcd_device_bytes(wmcd_handle* H, int64_t* bytes) {
     return WMCD_OK;
 }
 
-extern "C" int wmcd_destroy(wmcd_handle* H) {
-    if (!H) return WMCD_EINVAL;
+void wmcd::destroy_handle(wmcd_handle* H) {
     Handle* h = &H->h;
     cudaDeviceSynchronize();
     for (auto& u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
@@ -741,6 +747,20 @@ extern "C" int wmcd_destroy(wmcd_handle* H) {
     for (void* p : h->allocs) cudaFree(p);
     cudaGetLastError();
     delete H;
+}
+
+extern "C" int wmcd_set_block(wmcd_handle* H, int stage_warps, int serial_threads) {
+    if (!H || stage_warps < 1 || stage_warps > kMaxStageWarps) return WMCD_EINVAL;
+    if (serial_threads != 32 && serial_threads != 128 && serial_threads != 512) return WMCD_EINVAL;
+    H->h.g.block_warps = stage_warps;
+    H->h.g.serial_threads = serial_threads;
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_destroy(wmcd_handle* H) {
+    if (!H) return WMCD_EINVAL;
+    if (H->h.batch) return WMCD_EINVAL;   // owned by a batch: wmcd_batch_retire releases it
+    destroy_handle(H);
     return WMCD_OK;
 }
 
@@ -752,6 +772,7 @@ extern "C" const char* wmcd_strerror(int status) {
         case WMCD_ECUDA: return "CUDA runtime error";
         case WMCD_ETIMEOUT: return "a bounded device-side wait or list walk gave up";
         case WMCD_ESTATE: return "non-finite or out-of-box positions detected";
+        case WMCD_EFULL: return "the batch has no free slot or pool room for the simulation";
         default: return "unknown status";
     }
 }

@@ -20,7 +20,8 @@ constexpr int kNCap = 64;          // largest support of a concurrent (warp) mov
 constexpr int kWarpsPerBlock = 4;  // concurrent kernel: one warp per queue
 constexpr int kSerialThreads = 512;
 constexpr int kMaxWalk = 1 << 22;  // bound on list-walk iterations inside one move
-constexpr int kStageWarps = 2;     // staged concurrent kernel: warps per block
+constexpr int kStageWarps = 2;     // staged concurrent kernel: default warps per block
+constexpr int kMaxStageWarps = 4;  // ... and the most a block may have
 constexpr int kCandCap = 256;      // interaction candidates of one staged move held in shared memory
 constexpr int kSlotChunk = 32;     // slot parameters prepared per chunk
 
@@ -77,6 +78,9 @@ struct SimView {
     // schedule scratch (sized for the largest layer)
     double* slot_lam;
     int* slot_bead;
+    double* slot_V;              // serial phase: 3 per slot, centre offset in the unit ball
+    double* slot_p;              // 3 per slot, unit polarisation
+    double* slot_thr;            // per slot, Metropolis threshold -kT ln(1 - u)
     int* slot_key;
     int* q_count;
     int* q_start;
@@ -113,6 +117,8 @@ struct SimView {
     int* s_img;                  // per member: packed image change
     int* s_slot;                 // per bead: index in the support of the current serial move
     int* s_changed;              // members whose fine cell changes
+    int* s_box;                  // 6 per member: partner cell box (first cell, cells per axis)
+    int* s_pre;                  // n + 1: prefix of the partner-box sizes
     uint32_t* serial_tag;
     // plane waves
     PWDev* pw;
@@ -141,6 +147,8 @@ struct GroupDims {
     bool coloured[kMaxLayers] = {false};
     bool pw = false;
     int prec_mask = 3;           // bit 0: some simulation runs in binary64, bit 1: some in mixed precision
+    int block_warps = kStageWarps;  // warps (queues) per block of the staged concurrent kernel, 1..4
+    int serial_threads = kSerialThreads;  // threads of the serial-phase block: 32, 128 or 512
 };
 
 // ---- launchers (wmcd_kernels.cu) ----
@@ -153,6 +161,8 @@ void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colou
 void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
-size_t staged_smem_bytes(int cap);
+size_t staged_smem_bytes(int cap, int warps);
+// open the staged kernels for the dynamic shared memory of g (call before a graph capture)
+void prepare_staged(const GroupDims& g);
 
 }  // namespace wmcd

@@ -758,16 +758,49 @@ namespace wmcd {
 // Serial wavelet moves: one block runs the layer's deferred slots (schedule order), or
 // every slot of a serial layer, one move after another. Supports of any size.
 // ======================================================================================
-template <int PREC>
-__global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __restrict__ vs, int l) {
+// Slot parameters of the serial phase, one thread per slot, ahead of the sequential loop:
+// the centre offset V and the polarisation by rejection from the unit ball (Appendix D), p
+// normalised, and the Metropolis threshold -kT ln(1 - u) (Eq. 20). They depend only on the
+// slot's counter, not on the state, so computing them early changes nothing.
+__global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    if (l >= v.nL) return;
+    const bool use_list = v.layer[l].G > 0;
+    const int count = use_list ? *v.serial_count : v.counts[l];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int j = use_list ? v.serial_list[t] : t;
+    const uint64_t sweep = v.step[0];
+    double V[3] = {0.0, 0.0, 0.0}, p[3] = {0.0, 0.0, 1.0};
+    for (uint32_t a = 0; a < 64; a++) {
+        const u4 w = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
+        const double x = sym(w.x), y = sym(w.y), z = sym(w.z);
+        if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+    }
+    for (uint32_t a = 0; a < 64; a++) {
+        const u4 w = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
+        const double x = sym(w.x), y = sym(w.y), z = sym(w.z), q = norm2(x, y, z);
+        if (q <= 1.0 && q > 0.0) { p[0] = x; p[1] = y; p[2] = z; break; }
+    }
+    const double r = sqr_t(norm2(p[0], p[1], p[2]));
+    for (int a = 0; a < 3; a++) {
+        v.slot_V[3 * j + a] = V[a];
+        v.slot_p[3 * j + a] = dvd(p[a], r);
+    }
+    const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+    v.slot_thr[j] = -v.kT * log(1.0 - u53(w.x, w.y));
+}
+
+template <int PREC, int NT>
+__global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, int l) {
     SIM_PROLOGUE
     if (l >= v.nL || v.precision != PREC) return;
     const int M = v.counts[l];
     const int use_list = v.layer[l].G > 0;
-    const uint64_t sweep = v.step[0];
     __shared__ double sh_b[3], sh_p[3], sh_carry;
-    __shared__ double sh_red[kSerialThreads / 32];
-    __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3];
+    __shared__ double sh_red[NT / 32];
+    __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total;
+    __shared__ int sh_scan[NT];
     __shared__ uint32_t sh_tag;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const LayerDev& Ly = v.layer[l];
@@ -783,22 +816,11 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
         const int i = v.slot_bead[j];
         const double lam2 = mul(lam, lam);
         if (tid == 0) {
-            double V[3] = {0.0, 0.0, 0.0};
-            for (uint32_t a = 0; a < 64; a++) {
-                u4 w = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
-                double x = sym(w.x), y = sym(w.y), z = sym(w.z);
-                if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
-            }
             const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
-            for (int a = 0; a < 3; a++) sh_b[a] = wrap(add(ri[a], mul(lam, V[a])), L, nullptr);
-            double p[3] = {0.0, 0.0, 1.0};
-            for (uint32_t a = 0; a < 64; a++) {
-                u4 w = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
-                double x = sym(w.x), y = sym(w.y), z = sym(w.z), q = norm2(x, y, z);
-                if (q <= 1.0 && q > 0.0) { p[0] = x; p[1] = y; p[2] = z; break; }
+            for (int a = 0; a < 3; a++) {
+                sh_b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), L, nullptr);
+                sh_p[a] = v.slot_p[3 * j + a];
             }
-            double r = sqr_t(norm2(p[0], p[1], p[2]));
-            for (int a = 0; a < 3; a++) sh_p[a] = dvd(p[a], r);
             const double eps = 1e-9;
             int64_t ncell = 1;
             for (int a = 0; a < 3; a++) {
@@ -810,6 +832,7 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
             }
             sh_brute = ncell > v.N;
             sh_n = 0;
+            sh_total = 0;
             sh_nch = 0;
             uint32_t tag = *v.serial_tag + 1u;
             if (tag == 0u) tag = 1u;
@@ -829,11 +852,11 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
             }
         };
         if (sh_brute) {
-            for (int64_t m = tid; m < v.N; m += kSerialThreads) consider((int)m, v.bead[m]);
+            for (int64_t m = tid; m < v.N; m += NT) consider((int)m, v.bead[m]);
         } else {
             const int c0[3] = {sh_c0[0], sh_c0[1], sh_c0[2]}, nc[3] = {sh_nc[0], sh_nc[1], sh_nc[2]};
             const int ncell = nc[0] * nc[1] * nc[2];
-            for (int k = tid; k < ncell; k += kSerialThreads) {
+            for (int k = tid; k < ncell; k += NT) {
                 int kx = k % nc[0], ky = (k / nc[0]) % nc[1], kz = k / (nc[0] * nc[1]);
                 int cell = wrapi(c0[0] + kx, v.Gf) + v.Gf * (wrapi(c0[1] + ky, v.Gf) + v.Gf * wrapi(c0[2] + kz, v.Gf));
                 int guard = 0;
@@ -861,7 +884,7 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
         const uint32_t tag = sh_tag;
         const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
-        for (int k = tid; k < n; k += kSerialThreads) {
+        for (int k = tid; k < n; k += NT) {
             int m = v.s_ids[k];
             v.bead[m].mark = tag;
             v.s_slot[m] = k;
@@ -877,10 +900,12 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
             v.s_img[k] = pack_img(im[0], im[1], im[2]);
         }
         __syncthreads();
-        // energy change
+        // energy change: bonds and the external well per member; pair terms by one thread per
+        // (member, fine cell of its partner box), so a small support still spreads its list
+        // walks over the block
         double dU = 0.0;
         const double ext = add(v.rc, mul(0.25, Aw)) + 1e-9;
-        for (int k = tid; k < n; k += kSerialThreads) {
+        for (int k = tid; k < n; k += NT) {
             const int m = v.s_ids[k];
             const Bead bm = v.bead[m];
             const double o[3] = {bm.x, bm.y, bm.z};
@@ -900,6 +925,7 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
                 double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
                 dU += U_bond(P, r2n) - U_bond(P, r2o);
             }
+            int cnt = 0;
             if (P.eps != 0.0) {
                 double lo[3], hi[3];
                 for (int a = 0; a < 3; a++) {
@@ -909,29 +935,66 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
                 }
                 int c0[3], nc[3];
                 cell_box(v, lo, hi, c0, nc);
-                const int ncell = nc[0] * nc[1] * nc[2];
-                for (int kk = 0; kk < ncell; kk++) {
-                    int cell = box_cell(v, c0, nc, kk);
-                    int guard = 0;
-                    for (int q = v.head[cell]; q >= 0;) {
-                        Bead bq = v.bead[q];
-                        int nx = bq.next;
-                        if (q != m) {
-                            double qn[3] = {bq.x, bq.y, bq.z};
-                            bool member = bq.mark == tag;
-                            if (!(member && q < m)) {
-                                if (member) {
-                                    int s = v.s_slot[q];
-                                    qn[0] = v.s_new[3 * s]; qn[1] = v.s_new[3 * s + 1]; qn[2] = v.s_new[3 * s + 2];
-                                }
-                                double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
-                                double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
-                                if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); if (!member) pe++; }
+                for (int a = 0; a < 3; a++) { v.s_box[6 * k + a] = c0[a]; v.s_box[6 * k + 3 + a] = nc[a]; }
+                cnt = nc[0] * nc[1] * nc[2];
+            }
+            v.s_pre[k] = cnt;
+        }
+        __syncthreads();
+        if (P.eps != 0.0) {
+            // exclusive prefix of the box sizes, NT members per pass
+            for (int base = 0; base < n; base += NT) {
+                const int k = base + tid;
+                const int x = k < n ? v.s_pre[k] : 0;
+                sh_scan[tid] = x;
+                __syncthreads();
+                for (int off = 1; off < NT; off <<= 1) {
+                    const int y = tid >= off ? sh_scan[tid - off] : 0;
+                    __syncthreads();
+                    sh_scan[tid] += y;
+                    __syncthreads();
+                }
+                if (k < n) v.s_pre[k] = sh_total + sh_scan[tid] - x;
+                __syncthreads();
+                if (tid == NT - 1) sh_total += sh_scan[NT - 1];
+                __syncthreads();
+            }
+            const int W = sh_total;
+            if (tid == 0) v.s_pre[n] = W;
+            __syncthreads();
+            for (int t = tid; t < W; t += NT) {
+                int lo_k = 0, hi_k = n - 1;                 // last member with s_pre <= t
+                while (lo_k < hi_k) {
+                    const int mid = (lo_k + hi_k + 1) >> 1;
+                    if (v.s_pre[mid] <= t) lo_k = mid; else hi_k = mid - 1;
+                }
+                const int k = lo_k;
+                const int c0[3] = {v.s_box[6 * k], v.s_box[6 * k + 1], v.s_box[6 * k + 2]};
+                const int nc[3] = {v.s_box[6 * k + 3], v.s_box[6 * k + 4], v.s_box[6 * k + 5]};
+                const int cell = box_cell(v, c0, nc, t - v.s_pre[k]);
+                const int m = v.s_ids[k];
+                const Bead bm = v.bead[m];
+                const double o[3] = {bm.x, bm.y, bm.z};
+                const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
+                int guard = 0;
+                for (int q = v.head[cell]; q >= 0;) {
+                    Bead bq = v.bead[q];
+                    int nx = bq.next;
+                    if (q != m) {
+                        double qn[3] = {bq.x, bq.y, bq.z};
+                        bool member = bq.mark == tag;
+                        if (!(member && q < m)) {
+                            if (member) {
+                                int s = v.s_slot[q];
+                                qn[0] = v.s_new[3 * s]; qn[1] = v.s_new[3 * s + 1]; qn[2] = v.s_new[3 * s + 2];
                             }
+                            double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                            double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                            if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); if (!member) pe++; }
                         }
-                        q = nx;
-                        if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
                     }
+                    q = nx;
+                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
                 }
             }
         }
@@ -940,16 +1003,14 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;
-            for (int w = 0; w < kSerialThreads / 32; w++) s += sh_red[w];
-            u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
-            const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
-            sh_acc = s <= thr;
+            for (int w = 0; w < NT / 32; w++) s += sh_red[w];
+            sh_acc = s <= v.slot_thr[j];
             v.tr_du[Ly.tr_off + j] = s;
         }
         __syncthreads();
         const bool acc = sh_acc;
         if (acc) {
-            for (int k = tid; k < n; k += kSerialThreads) {
+            for (int k = tid; k < n; k += NT) {
                 const int m = v.s_ids[k];
                 const Bead bm = v.bead[m];
                 const int oc = cell_lin(v, bm.x, bm.y, bm.z);
@@ -1001,9 +1062,19 @@ __global__ void __launch_bounds__(kSerialThreads) k_serial(const SimView* __rest
     }
 }
 void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+    k_serial_prep<<<dim3((g.Mmax[l] + 127) / 128, g.S), 128, 0, s>>>(d, l);
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_serial<0><<<dim3(1, g.S), kSerialThreads, 0, s>>>(d, l);
-    if (g.prec_mask & 2) k_serial<1><<<dim3(1, g.S), kSerialThreads, 0, s>>>(d, l);
+    const dim3 grid(1, g.S);
+    if (g.serial_threads <= 32) {
+        if (g.prec_mask & 1) k_serial<0, 32><<<grid, 32, 0, s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 32><<<grid, 32, 0, s>>>(d, l);
+    } else if (g.serial_threads <= 128) {
+        if (g.prec_mask & 1) k_serial<0, 128><<<grid, 128, 0, s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 128><<<grid, 128, 0, s>>>(d, l);
+    } else {
+        if (g.prec_mask & 1) k_serial<0, 512><<<grid, 512, 0, s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 512><<<grid, 512, 0, s>>>(d, l);
+    }
 }
 
 }  // namespace wmcd
@@ -1590,7 +1661,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour) {
+__global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour) {
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
@@ -1599,7 +1670,7 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(const SimVie
     const unsigned FULL = 0xffffffffu;
     const LayerDev& Ly = v.layer[l];
     const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
-    const int q = blockIdx.x * kStageWarps + wib;
+    const int q = blockIdx.x * (int)(blockDim.x >> 5) + wib;
     if (q >= nq) return;
     const int key = colour * nq + q;
     const int start = v.q_start[key], cnt = v.q_count[key];
@@ -1762,7 +1833,32 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_colour_staged(const SimVie
     }
 }
 
-size_t staged_smem_bytes(int cap) { return (size_t)kStageWarps * warp_stride(cap); }
+size_t staged_smem_bytes(int cap, int warps) { return (size_t)warps * warp_stride(cap); }
+// warps per block actually used: the requested count, lowered until the block's shared memory
+// (dynamic + the static view copy) fits the 227 KB a block may have
+static int staged_warps(const GroupDims& g) {
+    int nw = std::max(1, std::min(g.block_warps, kMaxStageWarps));
+    while (nw > 1 && staged_smem_bytes(g.stage_cap, nw) + sizeof(SimView) + 1024 > 227u * 1024u) nw--;
+    return nw;
+}
+
+// The largest dynamic shared memory each staged kernel was opened for, per device: raised
+// before a launch needs more, so that launches recorded into a graph set nothing.
+static int g_staged_smem[64][2];
+void prepare_staged(const GroupDims& g) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    const int smem = (int)staged_smem_bytes(g.stage_cap, staged_warps(g));
+    if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
+        cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        g_staged_smem[dev][0] = smem;
+    }
+    if ((g.prec_mask & 2) && smem > g_staged_smem[dev][1]) {
+        cudaFuncSetAttribute(k_colour_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        g_staged_smem[dev][1] = smem;
+    }
+}
 
 void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s) {
     const int nq = g.nq[l];
@@ -1771,17 +1867,13 @@ void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colou
     k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
     k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l);
     k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
-    const size_t smem = staged_smem_bytes(g.stage_cap);
-    const dim3 grid((nq + kStageWarps - 1) / kStageWarps, g.S);
+    const int nw = staged_warps(g);
+    const size_t smem = staged_smem_bytes(g.stage_cap, nw);
+    const dim3 grid((nq + nw - 1) / nw, g.S);
+    prepare_staged(g);
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) {
-        cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_colour_staged<0><<<grid, kStageWarps * 32, smem, s>>>(d, l, colour);
-    }
-    if (g.prec_mask & 2) {
-        cudaFuncSetAttribute(k_colour_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_colour_staged<1><<<grid, kStageWarps * 32, smem, s>>>(d, l, colour);
-    }
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, nw * 32, smem, s>>>(d, l, colour);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, nw * 32, smem, s>>>(d, l, colour);
 }
 
 }  // namespace wmcd

@@ -38,12 +38,17 @@ def interaction_reach(wca_sigma: float, wca_eps: float) -> float:
 
 def choose(box_L: float, lambda_min: float, lambda_max: float, A0: float, wca_sigma: float, wca_eps: float,
            colour_K: int = 2, slack: float = 1.0, max_fine: int = 512, n_cap: int = 64,
-           min_queues_per_axis: int = 2) -> dict:
-    """Return the schedule fields: colour_K, grid_f, n_cap, grid_layer (list of 16)."""
+           min_queues_per_axis: int = 2, cell_scale: float = 1.0, serial_only: bool = False) -> dict:
+    """Return the schedule fields: colour_K, grid_f, n_cap, grid_layer (list of 16).
+
+    cell_scale widens the fine cells beyond the interaction reach (fewer, fuller cells to walk
+    in dilute systems); serial_only runs every layer in the serial phase."""
     if colour_K not in (2, 3, 4):
         raise ValueError("colour_K must be 2, 3 or 4")
+    if cell_scale < 1.0:
+        raise ValueError("fine cells may not be narrower than the interaction reach")
     reach = interaction_reach(wca_sigma, wca_eps)
-    hf = max(reach, 1.0)
+    hf = max(reach, 1.0) * cell_scale
     grid_f = max(1, min(max_fine, int(math.floor(box_L / hf))))
     _, hi = layer_bounds(lambda_min, lambda_max)
     grid_layer = [0] * MAX_LAYERS
@@ -53,6 +58,6 @@ def choose(box_L: float, lambda_min: float, lambda_max: float, A0: float, wca_si
         margin = 2.0 * lh + 0.25 * A0 * lh + reach + slack
         h_min = 2.0 * margin / (colour_K - 1)
         G = colour_K * int(math.floor(box_L / (colour_K * h_min)))
-        if G >= min_queues_per_axis * colour_K:
+        if G >= min_queues_per_axis * colour_K and not serial_only:
             grid_layer[l] = G
     return {"colour_K": colour_K, "grid_f": grid_f, "n_cap": n_cap, "grid_layer": grid_layer}

@@ -19,8 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libwmcd.so")
-_SOURCES = ["wmcd_kernels.cu", "wmcd_api.cu", "wmcd_noalloc.cu"]
-_HEADERS = ["wmcd_device.cuh", "wmcd_internal.h"]
+_SOURCES = ["wmcd_kernels.cu", "wmcd_api.cu", "wmcd_batch.cu", "wmcd_noalloc.cu"]
+_HEADERS = ["wmcd_device.cuh", "wmcd_internal.h", "wmcd_host.h"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 
@@ -28,7 +28,8 @@ MAX_LAYERS = 16
 BOND_NONE, BOND_HARMONIC, BOND_FENE = 0, 1, 2
 PLANEWAVE_OFF, PLANEWAVE_PERIODIC = 0, 1
 FP64, MIXED = 0, 1
-STATUS = {0: "WMCD_OK", -1: "WMCD_EINVAL", -2: "WMCD_ENOMEM", -3: "WMCD_ECUDA", -4: "WMCD_ETIMEOUT", -5: "WMCD_ESTATE"}
+STATUS = {0: "WMCD_OK", -1: "WMCD_EINVAL", -2: "WMCD_ENOMEM", -3: "WMCD_ECUDA", -4: "WMCD_ETIMEOUT", -5: "WMCD_ESTATE",
+          -6: "WMCD_EFULL"}
 KERNEL_CLASSES = ["concurrent_wavelet", "serial_wavelet", "plane_wave", "cell_list", "schedule"]
 
 
@@ -114,6 +115,16 @@ _SIGS = {
     "wmcd_device_bytes": ["p", "p"],
     "wmcd_destroy": ["p"],
     "wmcd_planewave_noalloc": ["p", "p", "p", "i64", "i64", "p", "i64", "p"],
+    "wmcd_set_block": ["p", "i", "i"],
+    "wmcd_batch_create": ["i", "i64", "p"],
+    "wmcd_batch_need": ["p", "p"],
+    "wmcd_batch_admit": ["p", "p", "p", "p", "i64", "p"],
+    "wmcd_batch_step": ["p", "i64", "p"],
+    "wmcd_batch_handle": ["p", "i", "p"],
+    "wmcd_batch_retire": ["p", "i", "p"],
+    "wmcd_batch_set_block": ["p", "i", "i"],
+    "wmcd_batch_info": ["p", "p", "p", "p", "p"],
+    "wmcd_batch_destroy": ["p"],
 }
 EXPORTED = sorted(list(_SIGS) + ["wmcd_strerror"])
 
@@ -209,6 +220,8 @@ def _buf_ptr(x):
 class Simulation:
     """One WMCD simulation held on the GPU (a wmcd_handle)."""
 
+    _owned = True
+
     def __init__(self, params: dict, pos, chain_len, stream=None):
         lib = load()
         self._lib = lib
@@ -224,9 +237,17 @@ class Simulation:
         _check(rc, "wmcd_create")
         self.h = h
 
+    @classmethod
+    def _borrowed(cls, lib, h, params: dict):
+        """A view of a simulation owned by a batch (not released by close)."""
+        sim = cls.__new__(cls)
+        sim._lib, sim.h, sim.params, sim.n, sim._owned = lib, h, dict(params), int(params["n_beads"]), False
+        return sim
+
     def close(self):
         if getattr(self, "h", None):
-            self._lib.wmcd_destroy(self.h)
+            if self._owned:
+                self._lib.wmcd_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -304,3 +325,87 @@ class Simulation:
         b = ctypes.c_int64()
         _check(self._lib.wmcd_device_bytes(self.h, ctypes.byref(b)), "wmcd_device_bytes")
         return b.value
+
+    def set_block(self, stage_warps: int = 2, serial_threads: int = 512):
+        """Launch shapes (results do not depend on them)."""
+        _check(self._lib.wmcd_set_block(self.h, int(stage_warps), int(serial_threads)), "wmcd_set_block")
+
+
+def batch_need(params: dict) -> int:
+    """Pool bytes a simulation with these parameters takes in a batch."""
+    lib = load()
+    pr = make_params(params)
+    b = ctypes.c_int64()
+    _check(lib.wmcd_batch_need(ctypes.byref(pr), ctypes.byref(b)), "wmcd_batch_need")
+    return b.value
+
+
+class Batch:
+    """Many simulations resident on the GPU, advanced together (a wmcd_batch): one launch per
+    phase of a sweep over all of them, the sweep replayed as a CUDA graph."""
+
+    def __init__(self, capacity: int, pool_bytes: int):
+        lib = load()
+        self._lib = lib
+        b = ctypes.c_void_p()
+        _check(lib.wmcd_batch_create(int(capacity), int(pool_bytes), ctypes.byref(b)), "wmcd_batch_create")
+        self.b = b
+        self.capacity = int(capacity)
+        self._members = {}
+
+    def admit(self, params: dict, pos, chain_len):
+        """Admit a simulation; returns its slot, or None when the batch is full (no slot or no
+        pool room). Other errors raise."""
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        cl = np.ascontiguousarray(chain_len, dtype=np.int32)
+        pr = make_params(params)
+        pp, _keep = _buf_ptr(pos)
+        slot = ctypes.c_int()
+        rc = self._lib.wmcd_batch_admit(self.b, ctypes.byref(pr), pp, cl.ctypes.data, len(cl), ctypes.byref(slot))
+        if rc == -6:
+            return None
+        _check(rc, "wmcd_batch_admit")
+        h = ctypes.c_void_p()
+        _check(self._lib.wmcd_batch_handle(self.b, slot.value, ctypes.byref(h)), "wmcd_batch_handle")
+        self._members[slot.value] = Simulation._borrowed(self._lib, h, params)
+        return slot.value
+
+    def sim(self, slot: int) -> Simulation:
+        return self._members[slot]
+
+    def step(self, n: int = 1, stream=None):
+        _check(self._lib.wmcd_batch_step(self.b, int(n), _stream_ptr(stream)), "wmcd_batch_step")
+
+    def retire(self, slot: int, stream=None):
+        sim = self._members.pop(slot)
+        sim.h = None
+        _check(self._lib.wmcd_batch_retire(self.b, int(slot), _stream_ptr(stream)), "wmcd_batch_retire")
+
+    def set_block(self, stage_warps: int = 2, serial_threads: int = 512):
+        """Launch shapes for the whole batch (results do not depend on them)."""
+        _check(self._lib.wmcd_batch_set_block(self.b, int(stage_warps), int(serial_threads)), "wmcd_batch_set_block")
+
+    def info(self) -> dict:
+        r, f, lg, lp = (ctypes.c_int64() for _ in range(4))
+        _check(self._lib.wmcd_batch_info(self.b, ctypes.byref(r), ctypes.byref(f), ctypes.byref(lg), ctypes.byref(lp)),
+               "wmcd_batch_info")
+        return {"resident": r.value, "pool_free": f.value, "largest_free": lg.value, "launches_per_sweep": lp.value}
+
+    @property
+    def slots(self):
+        return sorted(self._members)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for sim in self._members.values():
+                sim.h = None
+            self._members.clear()
+            self._lib.wmcd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
