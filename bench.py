@@ -13,6 +13,13 @@ support; N per plane-wave attempt), whole job over all ranks; also simulated tim
 wall second. Multi-GPU runs are independent replicas (different seeds), no collective in
 the data path.
 
+Two more legs use the batch and serving entry points on the uneven-size ensemble (single
+chains, lengths log-uniform in [16, 2048], box scaled to volume fraction 1e-3, wavelets plus
+plane waves, mixed precision): `batched` advances the whole ensemble together (one CUDA graph
+per batched sweep) and reports bead-updates/s and simulated time per second against the plain
+FP64 batch; `serve` replays a Poisson stream of requests through the continuous-batching loop
+and reports per-sweep and per-request latency percentiles beside throughput.
+
 --impl reference times the CPU oracle (the plain sequential FP64 statement of the method)
 on the same workload on one host core.
 """
@@ -178,6 +185,74 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def ensemble_leg(args, torch, stream, flush, tuner):
+    """The uneven-size ensemble advanced as one batch: mixed precision against plain FP64."""
+    from paper_1611_09160_gb300 import autotune as A
+    from paper_1611_09160_gb300 import inputs as I
+    from paper_1611_09160_gb300 import wmcd
+    systems = I.ensemble(args.ensemble, 16, 2048, 1e-3, seed=1)
+    t0 = time.perf_counter()
+    params = A.ensemble_params(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, seed=100, tuner=tuner)
+    tune_s = time.perf_counter() - t0
+    out = {"sims": len(systems), "beads": int(sum(s.n_beads for s in systems)), "tune_s": round(tune_s, 2),
+           "schedules": {k: v["choice"] for k, v in tuner.table.items()}}
+    for name, prec in (("mixed", wmcd.MIXED), ("fp64", wmcd.FP64)):
+        ps = [dict(p, precision=prec) for p in params]
+        need = sum(wmcd.batch_need(p) for p in ps)
+        b = wmcd.Batch(capacity=len(systems), pool_bytes=need + (1 << 24))
+        t0 = time.perf_counter()
+        slots = [b.admit(p, s.pos, s.chain_len) for p, s in zip(ps, systems)]
+        admit_s = time.perf_counter() - t0
+        shape = tuner.launch_shape(b, sweeps=1) if name == "mixed" else out["mixed"]["launch_shape"]
+        b.set_block(*shape)
+        b.step(args.warmup, stream=stream)
+        torch.cuda.synchronize()
+        st0 = [b.sim(k).stats() for k in slots]
+        times = []
+        for _ in range(args.ensemble_sweeps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(1, stream=stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        stream.synchronize()
+        ms = float(sum(a.elapsed_time(c) for a, c in times))
+        st1 = [b.sim(k).stats() for k in slots]
+        bu = sum(x.bead_updates - y.bead_updates for x, y in zip(st1, st0))
+        simt = sum(x.sim_time - y.sim_time for x, y in zip(st1, st0))
+        out[name] = {"bead_updates_per_s": bu / (ms * 1e-3), "sim_time_per_s": simt / (ms * 1e-3),
+                     "ms_per_batched_sweep": ms / args.ensemble_sweeps, "sweeps": args.ensemble_sweeps,
+                     "launches_per_sweep": b.info()["launches_per_sweep"], "launch_shape": list(shape),
+                     "pool_mb": round(need / 2**20, 1), "admit_s": round(admit_s, 2),
+                     "error_flags": int(max(x.error_flags for x in st1))}
+        b.close()
+    out["speedup_mixed_over_fp64"] = out["mixed"]["bead_updates_per_s"] / out["fp64"]["bead_updates_per_s"]
+    return out
+
+
+def serve_leg(args, torch, tuner):
+    """Poisson arrivals through the continuous-batching loop (a bounded sample of the stream)."""
+    from paper_1611_09160_gb300 import autotune as A
+    from paper_1611_09160_gb300 import inputs as I
+    from paper_1611_09160_gb300 import serve, wmcd
+    systems = I.ensemble(args.serve_requests, 16, 2048, 1e-3, seed=2)
+    params = A.ensemble_params(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, seed=200, tuner=tuner)
+    arrivals = serve.poisson_arrivals(len(systems), args.serve_rate, seed=3)
+    reqs = [serve.Request(k, p, s.pos, s.chain_len, args.serve_sweeps, float(t))
+            for k, (p, s, t) in enumerate(zip(params, systems, arrivals))]
+    needs = [wmcd.batch_need(p) for p in params]
+    pool = int(np.percentile(needs, 50) * args.serve_capacity)
+    srv = serve.Server(capacity=args.serve_capacity, pool_bytes=max(pool, max(needs)), chunk=args.serve_chunk)
+    rep = srv.run(reqs, realtime=True)
+    srv.close()
+    sm = rep.summary()
+    sm.update({"rate_per_s": args.serve_rate, "sweeps_per_request": args.serve_sweeps,
+               "capacity": args.serve_capacity, "pool_mb": round(pool / 2**20, 1),
+               "sample": f"{len(reqs)} requests of the ensemble shape (of 1,024 at 10^3 sweeps in the full stream)"})
+    return sm
+
+
 def timed_steps(sim, steps, flush, stream, torch):
     """Per-step CUDA-event times (ms) of `steps` sweeps, L2 flushed before each."""
     times = []
@@ -309,6 +384,11 @@ def run_gpu(args, rank, world, local_rank):
     pw = {"bead_updates_per_s": (q1.bead_updates - q0.bead_updates) / (a.elapsed_time(b) * 1e-3),
           "moves": 50, "ms_per_move": a.elapsed_time(b) / 50}
 
+    from paper_1611_09160_gb300 import autotune as A
+    tuner = A.Tuner(path=None, warm=1, sweeps=2, copies=32)   # schedule per shape, measured among copies
+    ens = ensemble_leg(args, torch, stream, flush, tuner) if args.ensemble > 0 else None
+    srv = serve_leg(args, torch, tuner) if args.serve_requests > 0 else None
+
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -318,7 +398,7 @@ def run_gpu(args, rank, world, local_rank):
             "sim_time_per_s": simt_all / (total_ms_all * 1e-3),
             "fp64": {"value": fp64_value * world, "unit": UNIT, "speedup_mixed_over_fp64": value / (fp64_value * world)},
             "e2e": e2e, "gpu_launches": launches_all, "clocks": clocks, "roofline": roofline,
-            "plane_wave": pw,
+            "plane_wave": pw, "batched": ens, "serve": srv,
             "stats": {"accept_fraction": (st1.accepted_total - st0.accepted_total) /
                                          max(1, sum(st1.attempts) - sum(st0.attempts) +
                                              st1.pw_attempts - st0.pw_attempts),
@@ -337,6 +417,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=1024, help="simulations in the batched leg (0: skip)")
+    ap.add_argument("--ensemble-sweeps", type=int, default=10)
+    ap.add_argument("--serve-requests", type=int, default=256, help="requests in the serving leg (0: skip)")
+    ap.add_argument("--serve-sweeps", type=int, default=100)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-capacity", type=int, default=512)
+    ap.add_argument("--serve-chunk", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -230,6 +230,11 @@ int wmcd_batch_set_block(wmcd_batch* b, int stage_warps, int serial_threads);
  * nodes) per batched sweep (0 before the first step after a change) */
 int wmcd_batch_info(wmcd_batch* b, int64_t* resident, int64_t* pool_free, int64_t* largest_free,
                     int64_t* launches_per_sweep);
+/* per-kernel timing of batched sweeps (as wmcd_profile / wmcd_kernel_times): while enabled,
+ * steps launch the sweep kernel by kernel with CUDA events around each class instead of
+ * replaying the graph */
+int wmcd_batch_profile(wmcd_batch* b, int enable);
+int wmcd_batch_kernel_times(wmcd_batch* b, int64_t* launches, double* ms, int n_classes, void* stream);
 /* releases every resident simulation and the pool */
 int wmcd_batch_destroy(wmcd_batch* b);
 

@@ -12,9 +12,11 @@ change:
 * Launch shapes (warps per block of the concurrent kernel, threads of the serial block):
   results do not depend on them, so they are tuned per batch.
 
-Every candidate is timed on a throw-away simulation of a synthetic system of the shape (the
+Every candidate is timed on throw-away simulations of a synthetic system of the shape (the
 same generator as the workloads), a few sweeps after warm-up, with CUDA events; the score is
-bead-updates per second.
+bead-updates per second. With ``copies`` > 1 the candidate runs as a batch of that many
+independent copies of the shape, which measures the schedule where it will run: among many
+other simulations, whose own work already fills the GPU.
 """
 from __future__ import annotations
 
@@ -46,6 +48,26 @@ def shape_key(n_beads: int, box_L: float, precision: int, planewave_mode: int) -
     return f"N{nb}_L{lb:.3f}_p{precision}_w{planewave_mode}"
 
 
+def _time_batch(params: dict, system, warm: int, sweeps: int, copies: int) -> float:
+    import torch
+    ps = [dict(params, sim_id=int(params.get("sim_id", 0)) + 7919 * c) for c in range(copies)]
+    b = wmcd.Batch(copies, sum(wmcd.batch_need(p) for p in ps))
+    try:
+        slots = [b.admit(p, system.pos, system.chain_len) for p in ps]
+        b.step(warm)
+        torch.cuda.synchronize()
+        b0 = sum(b.sim(k).stats().bead_updates for k in slots)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(sweeps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        return (sum(b.sim(k).stats().bead_updates for k in slots) - b0) / (ms / 1e3)
+    finally:
+        b.close()
+
+
 def _time_sim(params: dict, system, warm: int, sweeps: int) -> float:
     import torch
     sim = wmcd.Simulation(params, system.pos, system.chain_len)
@@ -67,9 +89,9 @@ def _time_sim(params: dict, system, warm: int, sweeps: int) -> float:
 class Tuner:
     """Per-shape schedule table (optionally kept in a JSON file) and launch-shape tuning."""
 
-    def __init__(self, path: str | None = None, warm: int = 2, sweeps: int = 4):
+    def __init__(self, path: str | None = None, warm: int = 2, sweeps: int = 4, copies: int = 1):
         self.path = path
-        self.warm, self.sweeps = warm, sweeps
+        self.warm, self.sweeps, self.copies = warm, sweeps, int(copies)
         self.table = {}
         if path and os.path.exists(path):
             with open(path) as f:
@@ -85,6 +107,8 @@ class Tuner:
     def schedule(self, base: dict, system=None, chain_lengths=None) -> dict:
         """Parameters ``base`` with the tuned schedule of its shape (measured on first use)."""
         key = shape_key(base["n_beads"], base["box_L"], base.get("precision", 0), base.get("planewave_mode", 0))
+        if self.copies > 1:
+            key += f"_x{self.copies}"
         if key not in self.table:
             self.table[key] = self._tune_schedule(base, system, chain_lengths)
             self.save()
@@ -107,7 +131,10 @@ class Tuner:
                 p = self.apply(base, cand)
             except ValueError:
                 continue
-            scores.append((_time_sim(p, system, self.warm, self.sweeps), cand))
+            if self.copies > 1:
+                scores.append((_time_batch(p, system, self.warm, self.sweeps, self.copies), cand))
+            else:
+                scores.append((_time_sim(p, system, self.warm, self.sweeps), cand))
         best = max(scores, key=lambda t: t[0])
         return {"choice": best[1], "scores": [[s, c] for s, c in scores]}
 

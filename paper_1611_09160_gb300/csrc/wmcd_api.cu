@@ -120,7 +120,7 @@ static cudaEvent_t get_event(Handle* h) {
     cudaEventCreate(&e);
     return e;
 }
-static void prof_harvest(Handle* h) {
+void prof_harvest(Handle* h) {
     for (auto& u : h->ev_used) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess) {
@@ -325,7 +325,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
          !dalloc(h, &v.s_box, 6 * N) && !dalloc(h, &v.s_pre, N + 1) &&
          !dalloc(h, &v.serial_tag, 1);
     ok = ok && !dalloc(h, &v.pw, 1) && !dalloc(h, &v.pw_new, 3 * N) && !dalloc(h, &v.pw_imgd, N) &&
-         !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1);
+         !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1) && !dalloc(h, &v.cl_stale, 1);
     ok = ok && !dalloc(h, &v.step, 2) && !dalloc(h, &v.counts, kMaxLayers + 1) && !dalloc(h, &h->dview, 1);
     int* d_modes = nullptr;
     double* d_cdf = nullptr;
@@ -369,6 +369,16 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     v.n_modes = (int)cdf.size();
     v.expect_F = (double)N * h->p_fourier;
     v.pw_on = P.planewave_mode == 1;
+    {
+        // shared-memory serial phase: small simulations without coloured layers, for the layers
+        // of small scale (a support of a few beads; the large scales keep the cell lists)
+        bool all_serial = true;
+        for (int l = 0; l < nL; l++) all_serial = all_serial && v.layer[l].G == 0;
+        v.smem_layers = 0;
+        if (all_serial && N <= kSmemSerialMaxN)
+            for (int l = 0; l < nL; l++)
+                if (v.layer[l].hi <= 4.0 * P.lambda_min) v.smem_layers |= 1 << l;
+    }
     // launch bounds of this simulation
     {
         GroupDims& g = h->g;
@@ -382,6 +392,8 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         g.stage_cap = v.stage_cap;
         g.pw_blocks = v.pw_blocks;
         g.prec_mask = 1 << P.precision;
+        g.smem_maxN = v.smem_layers ? N : 0;
+        g.any_global_serial = v.smem_layers != (1 << nL) - 1;
         for (int l = 0; l < nL; l++) {
             const int G = v.layer[l].G, Q = G / P.colour_K;
             g.Mmax[l] = h->Mmax[l];
@@ -392,6 +404,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     }
     cudaMemsetAsync(v.step, 0, 2 * sizeof(uint64_t), s);
     cudaMemsetAsync(v.counts, 0, (kMaxLayers + 1) * sizeof(int), s);
+    cudaMemsetAsync(v.cl_stale, 0, sizeof(int), s);
     cudaMemcpyAsync(h->dview, &v, sizeof(SimView), cudaMemcpyHostToDevice, s);
     // host -> device
     std::vector<uint8_t> bn(N, 0);
@@ -464,16 +477,14 @@ int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t*
             { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, l, s); }
             launches += 5 + (int64_t)g.maxK3 * (4 + np) + 1;
         }
-        { ProfScope ps(prof, 1, s); launch_serial(d, g, l, s); }
-        launches += 1 + np;
+        { ProfScope ps(prof, 1, s); launches += launch_serial(d, g, l, s); }
     }
     if (g.pw) {
         const int64_t MF = hc ? hc[kMaxLayers] : g.maxMF;
         for (int64_t m = 0; m < MF; m++) {
             ProfScope ps(prof, 2, s);
-            launch_planewave(d, g, 0, (int)m, s);
+            launches += launch_planewave(d, g, 0, (int)m, s);
         }
-        launches += 8 * MF;
     }
     launch_advance(d, g, 0, s);
     return launches + 1;
@@ -515,10 +526,10 @@ extern "C" int wmcd_planewave(wmcd_handle* H, int64_t n_moves, void* stream) {
     }
     for (int64_t m = 0; m < n_moves; m++) {
         ProfScope ps(h, 2, s);
-        launch_planewave(h->dview, h->g, 1, (int)m, s);
+        h->launches += launch_planewave(h->dview, h->g, 1, (int)m, s);
     }
     launch_advance(h->dview, h->g, 1, s);
-    h->launches += 8 * n_moves + 1;
+    h->launches += 1;
     h->tr_pw_count = n_moves;
     h->pw_calls++;
     return last_cuda_status();
@@ -719,10 +730,7 @@ extern "C" int wmcd_profile(wmcd_handle* H, int enable) {
     return WMCD_OK;
 }
 
-extern "C" int wmcd_kernel_times(wmcd_handle* H, int64_t* launches, double* ms, int n_classes, void* stream) {
-    if (!H || n_classes < 0) return WMCD_EINVAL;
-    Handle* h = &H->h;
-    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return WMCD_ECUDA;
+int wmcd::take_kernel_times(Handle* h, int64_t* launches, double* ms, int n_classes) {
     prof_harvest(h);
     for (int c = 0; c < n_classes && c < 8; c++) {
         if (launches) launches[c] = h->prof_launches[c];
@@ -731,6 +739,12 @@ extern "C" int wmcd_kernel_times(wmcd_handle* H, int64_t* launches, double* ms, 
         h->prof_ms[c] = 0.0;
     }
     return WMCD_OK;
+}
+
+extern "C" int wmcd_kernel_times(wmcd_handle* H, int64_t* launches, double* ms, int n_classes, void* stream) {
+    if (!H || n_classes < 0) return WMCD_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return WMCD_ECUDA;
+    return take_kernel_times(&H->h, launches, ms, n_classes);
 }
 
 extern "C" int wmcd_device_bytes(wmcd_handle* H, int64_t* bytes) {

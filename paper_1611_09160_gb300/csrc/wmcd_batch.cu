@@ -94,6 +94,7 @@ struct Batch {
     cudaStream_t admit_stream = nullptr, capture_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches_per_sweep = 0;
+    Handle prof;                     // event pool and per-class times while profiling
 };
 
 void batch_view_changed(void* batch) { static_cast<Batch*>(batch)->stale = true; }
@@ -113,8 +114,12 @@ static GroupDims group_bounds(const std::vector<Member>& ms, int block_warps, in
     g.prec_mask = 0;
     g.block_warps = block_warps;
     g.serial_threads = serial_threads;
+    g.smem_maxN = 0;
+    g.any_global_serial = false;
     for (const Member& m : ms) {
         const GroupDims& o = m.H->h.g;
+        g.smem_maxN = std::max(g.smem_maxN, o.smem_maxN);
+        g.any_global_serial = g.any_global_serial || o.any_global_serial;
         g.maxN = std::max(g.maxN, o.maxN);
         g.maxCells = std::max(g.maxCells, o.maxCells);
         g.maxL = std::max(g.maxL, o.maxL);
@@ -143,6 +148,11 @@ static int rebuild(Batch* b, cudaStream_t s) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     b->launches_per_sweep = 0;
     if (b->members.empty()) { b->stale = false; return WMCD_OK; }
+    // largest simulations first: their blocks are scheduled first and the long ones do not
+    // start in a late wave (blockIdx.y follows this order)
+    std::stable_sort(b->members.begin(), b->members.end(),
+                     [](const Member& x, const Member& y) { return x.H->h.N > y.H->h.N; });
+    for (size_t i = 0; i < b->members.size(); i++) b->slot_pos[b->members[i].slot] = (int)i;
     std::vector<SimView> views(b->members.size());
     for (size_t i = 0; i < b->members.size(); i++) views[i] = b->members[i].H->h.v;
     // pageable source: the copy is staged before the call returns, ordered after earlier steps
@@ -275,8 +285,13 @@ extern "C" int wmcd_batch_step(wmcd_batch* B, int64_t n_sweeps, void* stream) {
         if (rc) return rc;
     }
     if (!b->exec || n_sweeps == 0) return last_cuda_status();
-    for (int64_t k = 0; k < n_sweeps; k++)
-        if (cudaGraphLaunch(b->exec, s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+    if (b->prof.prof) {
+        // timed launch by launch, outside the graph (same kernels, same order)
+        for (int64_t k = 0; k < n_sweeps; k++) enqueue_sweep(b->dviews, b->g, nullptr, &b->prof, s);
+    } else {
+        for (int64_t k = 0; k < n_sweeps; k++)
+            if (cudaGraphLaunch(b->exec, s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+    }
     // host-side counters of each member follow its device sweep counter
     for (Member& m : b->members) {
         Handle* h = &m.H->h;
@@ -322,10 +337,24 @@ extern "C" int wmcd_batch_info(wmcd_batch* B, int64_t* resident, int64_t* pool_f
     return WMCD_OK;
 }
 
+extern "C" int wmcd_batch_profile(wmcd_batch* B, int enable) {
+    if (!B) return WMCD_EINVAL;
+    B->b.prof.prof = enable != 0;
+    return WMCD_OK;
+}
+
+extern "C" int wmcd_batch_kernel_times(wmcd_batch* B, int64_t* launches, double* ms, int n_classes, void* stream) {
+    if (!B || n_classes < 0) return WMCD_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return WMCD_ECUDA;
+    return take_kernel_times(&B->b.prof, launches, ms, n_classes);
+}
+
 extern "C" int wmcd_batch_destroy(wmcd_batch* B) {
     if (!B) return WMCD_EINVAL;
     Batch* b = &B->b;
     cudaDeviceSynchronize();
+    for (auto& u : b->prof.ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+    for (auto e : b->prof.ev_pool) cudaEventDestroy(e);
     while (!b->members.empty()) release_member(b, b->members.size() - 1);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->admit_stream) cudaStreamDestroy(b->admit_stream);

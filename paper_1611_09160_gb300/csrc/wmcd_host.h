@@ -54,6 +54,8 @@ int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, H
 int create_handle(struct ::wmcd_handle* H, const wmcd_params* params, const double* pos, const int32_t* chain_len,
                   int64_t n_chains, cudaStream_t s, Arena* arena);
 void destroy_handle(struct ::wmcd_handle* H);
+void prof_harvest(Handle* h);
+int take_kernel_times(Handle* h, int64_t* launches, double* ms, int n_classes);
 // a batch is told when a member's view changed (its copy in the batch is refreshed)
 void batch_view_changed(void* batch);
 

@@ -24,6 +24,7 @@ constexpr int kStageWarps = 2;     // staged concurrent kernel: default warps pe
 constexpr int kMaxStageWarps = 4;  // ... and the most a block may have
 constexpr int kCandCap = 256;      // interaction candidates of one staged move held in shared memory
 constexpr int kSlotChunk = 32;     // slot parameters prepared per chunk
+constexpr int kSmemSerialMaxN = 2560;  // largest simulation whose serial phase runs in shared memory
 
 enum Outcome { ACCEPT = 1, REJECT = 2, DEFER = 3 };
 
@@ -126,6 +127,9 @@ struct SimView {
     int* pw_imgd;                // per bead packed image change
     double* pw_part;             // per-block partial sums
     int* pw_rebuild;             // set by the commit when beads moved: the cell list is rebuilt
+    int* cl_stale;               // set by the shared-memory serial phase when beads changed fine cell
+    int smem_layers;             // bit l: layer l's serial phase runs in shared memory (small N, no
+                                 // coloured layer, small scales)
     int pw_blocks;
     const int* modes;            // 3 per mode
     const double* mode_cdf;
@@ -149,6 +153,8 @@ struct GroupDims {
     int prec_mask = 3;           // bit 0: some simulation runs in binary64, bit 1: some in mixed precision
     int block_warps = kStageWarps;  // warps (queues) per block of the staged concurrent kernel, 1..4
     int serial_threads = kSerialThreads;  // threads of the serial-phase block: 32, 128 or 512
+    int64_t smem_maxN = 0;       // largest N among simulations with the shared-memory serial phase
+    bool any_global_serial = true;  // some simulation runs its serial phase through global memory
 };
 
 // ---- launchers (wmcd_kernels.cu) ----
@@ -159,10 +165,12 @@ void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s);
 void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
-void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
-void launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
+int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s);      // returns kernels launched
+int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
 size_t staged_smem_bytes(int cap, int warps);
-// open the staged kernels for the dynamic shared memory of g (call before a graph capture)
+size_t smem_serial_bytes(int64_t n);
+// open the kernels that take large dynamic shared memory for the sizes of g (before a graph
+// capture: a recorded launch sets nothing)
 void prepare_staged(const GroupDims& g);
 
 }  // namespace wmcd

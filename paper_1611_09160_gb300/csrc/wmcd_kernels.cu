@@ -33,17 +33,26 @@ __device__ __forceinline__ int wrapi(int c, int G) { c %= G; return c < 0 ? c + 
 // ======================================================================================
 // Cell list: per fine cell a singly linked list through Bead::next plus prev[] for O(1)
 // removal. Built in canonical order (ascending bead id within a cell) so runs repeat.
+// use_flag 0: always rebuilt; 1: after an accepted plane wave moved the beads; 2: before an
+// active plane-wave move if the shared-memory serial phase left the lists stale; 3 + l: before
+// the global-memory serial phase of layer l if they are stale.
 // ======================================================================================
+__device__ __forceinline__ bool cl_skip(const SimView& v, int use_flag) {
+    if (use_flag == 1) return !*v.pw_rebuild;
+    if (use_flag == 2) return !(v.pw->active && !v.pw->null_move && *v.cl_stale);
+    if (use_flag >= 3) return !(*v.cl_stale && !((v.smem_layers >> (use_flag - 3)) & 1));
+    return false;
+}
 __global__ void k_cl_clear(const SimView* __restrict__ vs, int use_flag) {
     SIM_PROLOGUE
-    if (use_flag && !*v.pw_rebuild) return;
+    if (cl_skip(v, use_flag)) return;
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
         v.head[c] = -1;
 }
 __global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
     SIM_PROLOGUE
-    if (use_flag && !*v.pw_rebuild) return;
+    if (cl_skip(v, use_flag)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         Bead b = v.bead[i];
         if (!(b.x >= 0.0 && b.x < v.L && b.y >= 0.0 && b.y < v.L && b.z >= 0.0 && b.z < v.L)) set_err(v, E_NONFINITE);
@@ -54,7 +63,7 @@ __global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
 }
 __global__ void k_cl_canon(const SimView* __restrict__ vs, int use_flag) {
     SIM_PROLOGUE
-    if (use_flag && !*v.pw_rebuild) return;
+    if (cl_skip(v, use_flag)) return;
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int ids[32];
@@ -794,7 +803,8 @@ __global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, int l) {
     SIM_PROLOGUE
-    if (l >= v.nL || v.precision != PREC) return;
+    if (l >= v.nL || v.precision != PREC || ((v.smem_layers >> l) & 1)) return;
+    if (threadIdx.x == 0) *v.cl_stale = 0;      // rebuilt just before this launch if it was stale
     const int M = v.counts[l];
     const int use_list = v.layer[l].G > 0;
     __shared__ double sh_b[3], sh_p[3], sh_carry;
@@ -1061,10 +1071,360 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
     }
 }
-void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+// Serial phase of a small simulation whose layers are all serial: the whole simulation is
+// staged in shared memory for the launch (positions in binary64 and a binary32 copy), every
+// slot of the layer runs on-chip, and the beads are written back at the end. Supports and
+// pair partners are found by a binary32 pass over all staged beads with a margin that covers
+// the rounding of the copy, then decided in binary64 exactly as the global-memory kernel
+// does, so the two kernels take the same decisions. The global cell lists are not updated
+// here; they are marked stale and rebuilt before the next plane-wave move that needs them.
+// Shared bytes per bead: see smem_serial_bytes.
+template <int PREC, int NT>
+__global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ vs, int l) {
+    SIM_PROLOGUE
+    extern __shared__ __align__(16) char dsm[];
+    if (l >= v.nL || v.precision != PREC || !((v.smem_layers >> l) & 1)) return;
+    const int count = v.counts[l];
+    if (count == 0) return;
+    const int N = (int)v.N;
+    // 8-byte arrays first, then 4-, 2- and 1-byte ones, so every array is aligned for any N
+    double* px = (double*)dsm;
+    double* py = px + N;
+    double* pz = py + N;
+    double* mnew = pz + N;                       // 3 per support member
+    float* fx = (float*)(mnew + 3 * (size_t)N);
+    float* fy = fx + N;
+    float* fz = fy + N;
+    float* mnf = fz + N;                         // 3 per member: new position in binary32
+    int* mid = (int*)(mnf + 3 * (size_t)N);      // support, in gather order
+    int* sslot = mid + N;                        // per bead: index in the support or -1
+    short* dimg = (short*)(sslot + N);           // 3 per bead: image change over the launch
+    uint8_t* mimg = (uint8_t*)(dimg + 3 * (size_t)N);   // per member: packed image change of the move
+    uint8_t* bn = mimg + N;                      // bond to the next bead
+    __shared__ double sh_b[3], sh_p[3], sh_carry;
+    __shared__ double sh_red[NT / 32];
+    __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
+    __shared__ int sh_T[NT / 32];
+    __shared__ int sh_n, sh_acc, sh_stale, sh_need64;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const LayerDev& Ly = v.layer[l];
+    const double L = v.L, hL = v.halfL;
+    const float Lf = (float)L, hLf = (float)hL;
+    const Pot& P = v.pot;
+    // binary32 screens: a distance error of the copies below 8 L 2^-24 (rounding of the copies,
+    // of the difference and of the image shift), so screening at r + 8 L 2^-24 + 1e-6 and a
+    // relative 2^-20 on the square keeps every bead the binary64 test accepts
+    const float marg = (float)(8.0 * L * 5.9604644775390625e-8 + 1e-6);
+    for (int m = tid; m < N; m += NT) {
+        const Bead b = v.bead[m];
+        px[m] = b.x; py[m] = b.y; pz[m] = b.z;
+        fx[m] = (float)b.x; fy[m] = (float)b.y; fz[m] = (float)b.z;
+        sslot[m] = -1;
+        dimg[3 * m] = 0; dimg[3 * m + 1] = 0; dimg[3 * m + 2] = 0;
+        bn[m] = v.bnext[m];
+    }
+    if (tid == 0) { sh_carry = v.carry_serial[l]; sh_stale = 0; }
+    __syncthreads();
+    const float rcf = (float)v.rc + marg;
+    const float rc2f = rcf * rcf * (1.0f + 9.5367431640625e-7f);
+    long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
+    for (int j = 0; j < count; j++) {
+        const double lam = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
+        const int i = v.slot_bead[j];
+        const double lam2 = mul(lam, lam);
+        if (tid == 0) {
+            const double ri[3] = {px[i], py[i], pz[i]};
+            for (int a = 0; a < 3; a++) {
+                sh_b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), L, nullptr);
+                sh_p[a] = v.slot_p[3 * j + a];
+            }
+            sh_n = 0;
+        }
+        __syncthreads();
+        const double b[3] = {sh_b[0], sh_b[1], sh_b[2]};
+        {
+            const float bx = (float)b[0], by = (float)b[1], bz = (float)b[2];
+            const float rl = (float)lam + marg;
+            const float rl2 = rl * rl * (1.0f + 9.5367431640625e-7f);
+            for (int m = tid; m < N; m += NT) {
+                float dx = fx[m] - bx, dy = fy[m] - by, dz = fz[m] - bz;
+                dx = fabsf(dx) > hLf ? dx - copysignf(Lf, dx) : dx;
+                dy = fabsf(dy) > hLf ? dy - copysignf(Lf, dy) : dy;
+                dz = fabsf(dz) > hLf ? dz - copysignf(Lf, dz) : dz;
+                if (dx * dx + dy * dy + dz * dz > rl2) continue;
+                const double d0 = mi(sub(px[m], b[0]), L, hL), d1 = mi(sub(py[m], b[1]), L, hL),
+                             d2c = mi(sub(pz[m], b[2]), L, hL);
+                if (norm2(d0, d1, d2c) < lam2) mid[atomicAdd(&sh_n, 1)] = m;
+            }
+        }
+        __syncthreads();
+        const int n = sh_n;
+        if (n == 0) {      // nothing inside: dU = 0, accepted with no motion
+            if (tid == 0) {
+                att++; acc_n++;
+                v.tr_out[Ly.tr_off + j] = 1;
+                v.tr_n[Ly.tr_off + j] = 0;
+                v.tr_du[Ly.tr_off + j] = 0.0;
+                sh_carry = 0.0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+        const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
+        for (int k = tid; k < n; k += NT) {
+            const int m = mid[k];
+            const double o[3] = {px[m], py[m], pz[m]};
+            double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)}, dl[3];
+            if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
+            else wavelet_disp32(d, lam, Aw, p, dl);
+            int im[3] = {0, 0, 0};
+            for (int a = 0; a < 3; a++) {
+                mnew[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+                mnf[3 * k + a] = (float)mnew[3 * k + a];
+            }
+            mimg[k] = (uint8_t)pack_img(im[0], im[1], im[2]);
+            sslot[m] = k;
+        }
+        __syncthreads();
+        // energy change. Mixed precision: a binary32 pass (differences of the binary64
+        // positions rounded once, then binary32 terms with their magnitudes) decides outside
+        // the rigorous error band; inside it, and in binary64 mode, the binary64 pass decides.
+        const double thr = v.slot_thr[j];
+        bool need64 = PREC == 0;
+        if (PREC == 1) {
+            const Pot32 P32 = pot32(P);
+            float a32 = 0.0f, m32 = 0.0f;
+            int T = 0;
+            auto r2f = [&](double ax, double ay, double az, double bx, double by, double bz) {
+                const double e[3] = {sub(ax, bx), sub(ay, by), sub(az, bz)};
+                float r2 = 0.0f;
+                for (int a = 0; a < 3; a++) {
+                    float f = (float)e[a];
+                    if (fabsf(f) > hLf) f = (float)(e[a] > 0.0 ? sub(e[a], L) : add(e[a], L));
+                    r2 += f * f;
+                }
+                return r2;
+            };
+            for (int k = tid; k < n; k += NT) {
+                const int m = mid[k];
+                const double o[3] = {px[m], py[m], pz[m]};
+                const double nw[3] = {mnew[3 * k], mnew[3 * k + 1], mnew[3 * k + 2]};
+                if (P.kappa != 0.0) {
+                    const float un = 0.5f * P32.kappa * r2f(nw[0], nw[1], nw[2], hL, hL, hL);
+                    const float uo = 0.5f * P32.kappa * r2f(o[0], o[1], o[2], hL, hL, hL);
+                    a32 += un - uo; m32 += un + uo; T += 2;
+                }
+                for (int e = 0; e < 2; e++) {
+                    const int q = e ? m + 1 : m - 1;
+                    if (q < 0 || q >= N || !(e ? bn[m] : bn[q])) continue;
+                    const int sq = sslot[q];
+                    if (sq >= 0 && q < m) continue;
+                    const double qo[3] = {px[q], py[q], pz[q]};
+                    const double qn[3] = {sq >= 0 ? mnew[3 * sq] : qo[0], sq >= 0 ? mnew[3 * sq + 1] : qo[1],
+                                          sq >= 0 ? mnew[3 * sq + 2] : qo[2]};
+                    float un, mn, uo, mo;
+                    bond32(P32, r2f(nw[0], nw[1], nw[2], qn[0], qn[1], qn[2]), un, mn);
+                    bond32(P32, r2f(o[0], o[1], o[2], qo[0], qo[1], qo[2]), uo, mo);
+                    a32 += un - uo; m32 += mn + mo; T += 2;
+                }
+            }
+            if (P.eps != 0.0) {
+                const int total = n * N;
+                int k = tid / N, q = tid - k * N;
+                const int kstep = NT / N, qstep = NT - kstep * N;
+                for (int t = tid; t < total; t += NT) {
+                    const int m = mid[k];
+                    const int sq = sslot[q];
+                    if (q != m && !(sq >= 0 && q < m)) {
+                        const float qfx = fx[q], qfy = fy[q], qfz = fz[q];
+                        float ax = fx[m] - qfx, ay = fy[m] - qfy, az = fz[m] - qfz;
+                        ax = fabsf(ax) > hLf ? ax - copysignf(Lf, ax) : ax;
+                        ay = fabsf(ay) > hLf ? ay - copysignf(Lf, ay) : ay;
+                        az = fabsf(az) > hLf ? az - copysignf(Lf, az) : az;
+                        const float qnx = sq >= 0 ? mnf[3 * sq] : qfx, qny = sq >= 0 ? mnf[3 * sq + 1] : qfy,
+                                    qnz = sq >= 0 ? mnf[3 * sq + 2] : qfz;
+                        float cx = mnf[3 * k] - qnx, cy = mnf[3 * k + 1] - qny, cz = mnf[3 * k + 2] - qnz;
+                        cx = fabsf(cx) > hLf ? cx - copysignf(Lf, cx) : cx;
+                        cy = fabsf(cy) > hLf ? cy - copysignf(Lf, cy) : cy;
+                        cz = fabsf(cz) > hLf ? cz - copysignf(Lf, cz) : cz;
+                        if (ax * ax + ay * ay + az * az <= rc2f || cx * cx + cy * cy + cz * cz <= rc2f) {
+                            const double qo[3] = {px[q], py[q], pz[q]};
+                            const double qn[3] = {sq >= 0 ? mnew[3 * sq] : qo[0], sq >= 0 ? mnew[3 * sq + 1] : qo[1],
+                                                  sq >= 0 ? mnew[3 * sq + 2] : qo[2]};
+                            float un, mn, uo, mo;
+                            wca32(P32, r2f(mnew[3 * k], mnew[3 * k + 1], mnew[3 * k + 2], qn[0], qn[1], qn[2]), un, mn);
+                            wca32(P32, r2f(px[m], py[m], pz[m], qo[0], qo[1], qo[2]), uo, mo);
+                            a32 += un - uo; m32 += mn + mo; T += 2;
+                            if (sq < 0 && (un != 0.0f || uo != 0.0f)) pe++;
+                        }
+                    }
+                    k += kstep;
+                    q += qstep;
+                    if (q >= N) { q -= N; k++; }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                a32 += __shfl_xor_sync(0xffffffffu, a32, o);
+                m32 += __shfl_xor_sync(0xffffffffu, m32, o);
+                T += __shfl_xor_sync(0xffffffffu, T, o);
+            }
+            if (lane == 0) { sh_f32[wid] = a32; sh_m32[wid] = m32; sh_T[wid] = T; }
+            __syncthreads();
+            if (tid == 0) {
+                float d32 = 0.0f, mm = 0.0f;
+                int tt = 0;
+                for (int w = 0; w < NT / 32; w++) { d32 += sh_f32[w]; mm += sh_m32[w]; tt += sh_T[w]; }
+                const float thr32 = (float)thr;
+                const float band = 2.0f * (float)(80 + tt + 6) * 5.9604645e-08f * mm + 1e-9f * (float)v.kT +
+                                   2.4e-7f * fabsf(thr32);
+                if (isfinite(d32) && isfinite(band) && fabsf(d32 - thr32) > band) {
+                    sh_acc = d32 <= thr32;
+                    sh_need64 = 0;
+                    v.tr_du[Ly.tr_off + j] = (double)d32;
+                } else {
+                    sh_need64 = 1;
+                    rechecks++;
+                }
+            }
+            __syncthreads();
+            need64 = sh_need64;
+        }
+        if (need64) {
+            double dU = 0.0;
+            for (int k = tid; k < n; k += NT) {
+                const int m = mid[k];
+                const double o[3] = {px[m], py[m], pz[m]};
+                const double nw[3] = {mnew[3 * k], mnew[3 * k + 1], mnew[3 * k + 2]};
+                dU += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, o[0], o[1], o[2]);
+                for (int e = 0; e < 2; e++) {
+                    const int q = e ? m + 1 : m - 1;
+                    if (q < 0 || q >= N || !(e ? bn[m] : bn[q])) continue;
+                    const int sq = sslot[q];
+                    if (sq >= 0 && q < m) continue;
+                    const double qo[3] = {px[q], py[q], pz[q]};
+                    const double qn[3] = {sq >= 0 ? mnew[3 * sq] : qo[0], sq >= 0 ? mnew[3 * sq + 1] : qo[1],
+                                          sq >= 0 ? mnew[3 * sq + 2] : qo[2]};
+                    const double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                    const double r2o = norm2(mi(o[0] - qo[0], L, hL), mi(o[1] - qo[1], L, hL), mi(o[2] - qo[2], L, hL));
+                    dU += U_bond(P, r2n) - U_bond(P, r2o);
+                }
+            }
+            if (P.eps != 0.0) {
+                // one (member, bead) pair per thread and step, all members at once
+                const int total = n * N;
+                int k = tid / N, q = tid - k * N;
+                const int kstep = NT / N, qstep = NT - kstep * N;
+                for (int t = tid; t < total; t += NT) {
+                    const int m = mid[k];
+                    const int sq = sslot[q];
+                    if (q != m && !(sq >= 0 && q < m)) {
+                        const float qfx = fx[q], qfy = fy[q], qfz = fz[q];
+                        float ax = fx[m] - qfx, ay = fy[m] - qfy, az = fz[m] - qfz;
+                        ax = fabsf(ax) > hLf ? ax - copysignf(Lf, ax) : ax;
+                        ay = fabsf(ay) > hLf ? ay - copysignf(Lf, ay) : ay;
+                        az = fabsf(az) > hLf ? az - copysignf(Lf, az) : az;
+                        const float qnx = sq >= 0 ? mnf[3 * sq] : qfx, qny = sq >= 0 ? mnf[3 * sq + 1] : qfy,
+                                    qnz = sq >= 0 ? mnf[3 * sq + 2] : qfz;
+                        float cx = mnf[3 * k] - qnx, cy = mnf[3 * k + 1] - qny, cz = mnf[3 * k + 2] - qnz;
+                        cx = fabsf(cx) > hLf ? cx - copysignf(Lf, cx) : cx;
+                        cy = fabsf(cy) > hLf ? cy - copysignf(Lf, cy) : cy;
+                        cz = fabsf(cz) > hLf ? cz - copysignf(Lf, cz) : cz;
+                        if (ax * ax + ay * ay + az * az <= rc2f || cx * cx + cy * cy + cz * cz <= rc2f) {
+                            const double o[3] = {px[m], py[m], pz[m]};
+                            const double nw[3] = {mnew[3 * k], mnew[3 * k + 1], mnew[3 * k + 2]};
+                            const double qo[3] = {px[q], py[q], pz[q]};
+                            const double qn[3] = {sq >= 0 ? mnew[3 * sq] : qo[0], sq >= 0 ? mnew[3 * sq + 1] : qo[1],
+                                                  sq >= 0 ? mnew[3 * sq + 2] : qo[2]};
+                            const double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                            const double r2o = norm2(mi(o[0] - qo[0], L, hL), mi(o[1] - qo[1], L, hL), mi(o[2] - qo[2], L, hL));
+                            if (r2n < P.rc2 || r2o < P.rc2) {
+                                dU += U_wca(P, r2n) - U_wca(P, r2o);
+                                if (sq < 0 && PREC == 0) pe++;
+                            }
+                        }
+                    }
+                    k += kstep;
+                    q += qstep;
+                    if (q >= N) { q -= N; k++; }
+                }
+            }
+            dU = warp_sum(dU);
+            if (lane == 0) sh_red[wid] = dU;
+            __syncthreads();
+            if (tid == 0) {
+                double su = 0.0;
+                for (int w = 0; w < NT / 32; w++) su += sh_red[w];
+                sh_acc = su <= thr;
+                v.tr_du[Ly.tr_off + j] = su;
+            }
+            __syncthreads();
+        }
+        const bool acc = sh_acc;
+        for (int k = tid; k < n; k += NT) {
+            const int m = mid[k];
+            if (acc) {
+                px[m] = mnew[3 * k]; py[m] = mnew[3 * k + 1]; pz[m] = mnew[3 * k + 2];
+                fx[m] = (float)px[m]; fy[m] = (float)py[m]; fz[m] = (float)pz[m];
+                int dd[3];
+                unpack_img(mimg[k], dd);
+                dimg[3 * m] += (short)dd[0]; dimg[3 * m + 1] += (short)dd[1]; dimg[3 * m + 2] += (short)dd[2];
+            }
+            sslot[m] = -1;
+        }
+        if (tid == 0) {
+            att++;
+            bu += n;
+            if (acc) acc_n++;
+            v.tr_out[Ly.tr_off + j] = (uint8_t)(acc ? 1 : 2);
+            v.tr_n[Ly.tr_off + j] = n;
+            sh_carry = acc ? 0.0 : lam;
+        }
+        __syncthreads();
+    }
+    // write back what moved; the cell lists go stale if a bead changed fine cell
+    for (int m = tid; m < N; m += NT) {
+        const Bead ob = v.bead[m];
+        if (ob.x == px[m] && ob.y == py[m] && ob.z == pz[m]) continue;
+        v.bead[m].x = px[m]; v.bead[m].y = py[m]; v.bead[m].z = pz[m];
+        if (dimg[3 * m] | dimg[3 * m + 1] | dimg[3 * m + 2]) {
+            v.img[3 * m] += dimg[3 * m]; v.img[3 * m + 1] += dimg[3 * m + 1]; v.img[3 * m + 2] += dimg[3 * m + 2];
+        }
+        if (cell_lin(v, ob.x, ob.y, ob.z) != cell_lin(v, px[m], py[m], pz[m])) sh_stale = 1;
+    }
+    unsigned long long pe_all = (unsigned long long)pe;
+    if (pe_all) atomicAdd(&v.ctr[C_PARTNER], pe_all);
+    __syncthreads();
+    if (tid == 0) {
+        if (sh_stale) *v.cl_stale = 1;
+        if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
+        v.carry_serial[l] = sh_carry;
+        atomicAdd(&v.ctr[C_ATT + l], (unsigned long long)att);
+        atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc_n);
+        atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc_n);
+        atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+    }
+}
+
+size_t smem_serial_bytes(int64_t n) { return (size_t)n * (3 * 8 + 3 * 8 + 3 * 4 + 4 + 4 + 3 * 2 + 3 * 4 + 1 + 1) + 64; }
+
+int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+    const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
+    int launched = 1 + (g.smem_maxN > 0 ? np : 0) + (g.any_global_serial ? np : 0);
+    prepare_staged(g);
     k_serial_prep<<<dim3((g.Mmax[l] + 127) / 128, g.S), 128, 0, s>>>(d, l);
     // one launch per precision; each returns at once for simulations of the other precision
     const dim3 grid(1, g.S);
+    if (g.smem_maxN > 0) {
+        const size_t sm = smem_serial_bytes(g.smem_maxN);
+        if (g.prec_mask & 1) k_serial_smem<0, 256><<<grid, 256, sm, s>>>(d, l);
+        if (g.prec_mask & 2) k_serial_smem<1, 256><<<grid, 256, sm, s>>>(d, l);
+    }
+    if (!g.any_global_serial) return launched;
+    if (g.smem_maxN > 0) {
+        launch_cl_rebuild(d, g, s, 3 + l);
+        launched += 3;
+    }
     if (g.serial_threads <= 32) {
         if (g.prec_mask & 1) k_serial<0, 32><<<grid, 32, 0, s>>>(d, l);
         if (g.prec_mask & 2) k_serial<1, 32><<<grid, 32, 0, s>>>(d, l);
@@ -1075,6 +1435,7 @@ void launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s) 
         if (g.prec_mask & 1) k_serial<0, 512><<<grid, 512, 0, s>>>(d, l);
         if (g.prec_mask & 2) k_serial<1, 512><<<grid, 512, 0, s>>>(d, l);
     }
+    return launched;
 }
 
 }  // namespace wmcd
@@ -1155,6 +1516,7 @@ __global__ void k_pw_disp(const SimView* __restrict__ vs) {
     SIM_PROLOGUE
     const PWDev& P = *v.pw;
     if (!P.active || P.null_move) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *v.cl_stale = 0;   // rebuilt just before, if it was stale
     const double lx = (double)P.lv[0], ly = (double)P.lv[1], lz = (double)P.lv[2];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         const Bead b = v.bead[i];
@@ -1280,15 +1642,17 @@ __global__ void k_pw_commit(const SimView* __restrict__ vs) {
     }
 }
 
-void launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s) {
+int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s) {
     const int nb = g.pw_blocks;
     const int gb = (int)std::min<int64_t>(nb, 152 * 16);
     k_pw_setup<<<dim3(1, g.S), 32, 0, s>>>(d, direct, m);
+    launch_cl_rebuild(d, g, s, 2);
     k_pw_disp<<<dim3(gb, g.S), 256, 0, s>>>(d);
     k_pw_energy<<<dim3(nb, g.S), 256, 0, s>>>(d);
     k_pw_decide<<<dim3(1, g.S), 256, 0, s>>>(d, direct, m);
     k_pw_commit<<<dim3(gb, g.S), 256, 0, s>>>(d);
     launch_cl_rebuild(d, g, s, 1);
+    return 11;
 }
 
 }  // namespace wmcd
@@ -1845,10 +2209,22 @@ static int staged_warps(const GroupDims& g) {
 // The largest dynamic shared memory each staged kernel was opened for, per device: raised
 // before a launch needs more, so that launches recorded into a graph set nothing.
 static int g_staged_smem[64][2];
+static int g_serial_smem[64][2];
 void prepare_staged(const GroupDims& g) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
+    if (g.smem_maxN > 0) {
+        const int sm = (int)smem_serial_bytes(g.smem_maxN);
+        if ((g.prec_mask & 1) && sm > g_serial_smem[dev][0]) {
+            cudaFuncSetAttribute(k_serial_smem<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            g_serial_smem[dev][0] = sm;
+        }
+        if ((g.prec_mask & 2) && sm > g_serial_smem[dev][1]) {
+            cudaFuncSetAttribute(k_serial_smem<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            g_serial_smem[dev][1] = sm;
+        }
+    }
     const int smem = (int)staged_smem_bytes(g.stage_cap, staged_warps(g));
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
         cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -38,7 +38,8 @@ constexpr int64_t oCdf = oModes + al(12 * kNaModes);
 constexpr int64_t oView = oCdf + al(8 * kNaModes);
 constexpr int64_t oStep = oView + al(sizeof(SimView));
 constexpr int64_t oCounts = oStep + al(16);
-constexpr int64_t kNaBytes = oCounts + al(4 * (kMaxLayers + 1));   // about 1.9 MB
+constexpr int64_t oClStale = oCounts + al(4 * (kMaxLayers + 1));
+constexpr int64_t kNaBytes = oClStale + al(4);   // about 1.9 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -169,6 +170,7 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     v.pw_blocks = (int)((N + 255) / 256);
     v.step = (uint64_t*)(base + oStep);
     v.counts = (int*)(base + oCounts);
+    v.cl_stale = (int*)(base + oClStale);
     v.pw_on = 1;
     SimView* dview = (SimView*)(base + oView);
     GroupDims g;
@@ -188,6 +190,7 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     cudaMemcpyAsync(dview, &v, sizeof(SimView), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.step, h_step, sizeof h_step, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(v.counts, 0, 4 * (kMaxLayers + 1), s);
+    cudaMemsetAsync(v.cl_stale, 0, 4, s);
     cudaMemsetAsync(v.pw, 0, sizeof(PWDev), s);
     cudaMemcpyAsync(v.ctr, h_carry, sizeof h_carry, cudaMemcpyHostToDevice, s);   // carry staged in ctr[0..1]
     k_na_carry<<<1, 1, 0, s>>>(v.pw, (const int*)v.ctr);

@@ -125,6 +125,8 @@ _SIGS = {
     "wmcd_batch_set_block": ["p", "i", "i"],
     "wmcd_batch_info": ["p", "p", "p", "p", "p"],
     "wmcd_batch_destroy": ["p"],
+    "wmcd_batch_profile": ["p", "i"],
+    "wmcd_batch_kernel_times": ["p", "p", "p", "i", "p"],
 }
 EXPORTED = sorted(list(_SIGS) + ["wmcd_strerror"])
 
@@ -381,6 +383,16 @@ class Batch:
         sim = self._members.pop(slot)
         sim.h = None
         _check(self._lib.wmcd_batch_retire(self.b, int(slot), _stream_ptr(stream)), "wmcd_batch_retire")
+
+    def profile(self, enable: bool = True):
+        _check(self._lib.wmcd_batch_profile(self.b, int(enable)), "wmcd_batch_profile")
+
+    def kernel_times(self, stream=None) -> dict:
+        n = len(KERNEL_CLASSES)
+        la = (ctypes.c_int64 * n)()
+        ms = (ctypes.c_double * n)()
+        _check(self._lib.wmcd_batch_kernel_times(self.b, la, ms, n, _stream_ptr(stream)), "wmcd_batch_kernel_times")
+        return {KERNEL_CLASSES[i]: (int(la[i]), float(ms[i])) for i in range(n)}
 
     def set_block(self, stage_warps: int = 2, serial_threads: int = 512):
         """Launch shapes for the whole batch (results do not depend on them)."""
