@@ -192,9 +192,11 @@ def ensemble_leg(args, torch, stream, flush, tuner):
     from paper_1611_09160_gb300 import wmcd
     systems = I.ensemble(args.ensemble, 16, 2048, 1e-3, seed=1)
     t0 = time.perf_counter()
-    params = A.ensemble_params(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, seed=100, tuner=tuner)
+    policy, policy_scores = A.choose_policy(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, tuner)
+    params = A.ensemble_params(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, seed=100, tuner=tuner, policy=policy)
     tune_s = time.perf_counter() - t0
     out = {"sims": len(systems), "beads": int(sum(s.n_beads for s in systems)), "tune_s": round(tune_s, 2),
+           "policy": policy, "policy_bead_updates_per_s": policy_scores,
            "schedules": {k: v["choice"] for k, v in tuner.table.items()}}
     for name, prec in (("mixed", wmcd.MIXED), ("fp64", wmcd.FP64)):
         ps = [dict(p, precision=prec) for p in params]
@@ -231,13 +233,13 @@ def ensemble_leg(args, torch, stream, flush, tuner):
     return out
 
 
-def serve_leg(args, torch, tuner):
+def serve_leg(args, torch, tuner, policy):
     """Poisson arrivals through the continuous-batching loop (a bounded sample of the stream)."""
     from paper_1611_09160_gb300 import autotune as A
     from paper_1611_09160_gb300 import inputs as I
     from paper_1611_09160_gb300 import serve, wmcd
     systems = I.ensemble(args.serve_requests, 16, 2048, 1e-3, seed=2)
-    params = A.ensemble_params(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, seed=200, tuner=tuner)
+    params = A.ensemble_params(systems, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC, seed=200, tuner=tuner, policy=policy)
     arrivals = serve.poisson_arrivals(len(systems), args.serve_rate, seed=3)
     reqs = [serve.Request(k, p, s.pos, s.chain_len, args.serve_sweeps, float(t))
             for k, (p, s, t) in enumerate(zip(params, systems, arrivals))]
@@ -247,7 +249,7 @@ def serve_leg(args, torch, tuner):
     rep = srv.run(reqs, realtime=True)
     srv.close()
     sm = rep.summary()
-    sm.update({"rate_per_s": args.serve_rate, "sweeps_per_request": args.serve_sweeps,
+    sm.update({"policy": policy, "rate_per_s": args.serve_rate, "sweeps_per_request": args.serve_sweeps,
                "capacity": args.serve_capacity, "pool_mb": round(pool / 2**20, 1),
                "sample": f"{len(reqs)} requests of the ensemble shape (of 1,024 at 10^3 sweeps in the full stream)"})
     return sm
@@ -385,9 +387,11 @@ def run_gpu(args, rank, world, local_rank):
           "moves": 50, "ms_per_move": a.elapsed_time(b) / 50}
 
     from paper_1611_09160_gb300 import autotune as A
-    tuner = A.Tuner(path=None, warm=1, sweeps=2, copies=32)   # schedule per shape, measured among copies
+    # schedule per shape, measured among 152 copies of the shape (one per SM); shapes already in
+    # the table shipped with the package are not measured again
+    tuner = A.Tuner(path=None, warm=1, sweeps=2, copies=152, seed_table=A.DEFAULT_TABLE)
     ens = ensemble_leg(args, torch, stream, flush, tuner) if args.ensemble > 0 else None
-    srv = serve_leg(args, torch, tuner) if args.serve_requests > 0 else None
+    srv = serve_leg(args, torch, tuner, ens["policy"] if ens else "serial_small") if args.serve_requests > 0 else None
 
     if rank != 0:
         return

@@ -38,7 +38,15 @@ SCHEDULE_CANDIDATES = (
     {"colour_K": 2, "min_queues_per_axis": 3},
     {"colour_K": 2, "serial_only": True},
 )
+# in a batch the other simulations fill the GPU, so only the schedules that differ in kind
+# (all serial, coloured with two or three colours per axis) are worth timing there
+BATCH_SCHEDULE_CANDIDATES = (
+    {"colour_K": 2, "serial_only": True},
+    {"colour_K": 2},
+    {"colour_K": 3},
+)
 LAUNCH_CANDIDATES = ((2, 512), (2, 128), (2, 32), (1, 32), (4, 32), (1, 128))
+DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
 
 
 def shape_key(n_beads: int, box_L: float, precision: int, planewave_mode: int) -> str:
@@ -89,13 +97,18 @@ def _time_sim(params: dict, system, warm: int, sweeps: int) -> float:
 class Tuner:
     """Per-shape schedule table (optionally kept in a JSON file) and launch-shape tuning."""
 
-    def __init__(self, path: str | None = None, warm: int = 2, sweeps: int = 4, copies: int = 1):
+    def __init__(self, path: str | None = None, warm: int = 2, sweeps: int = 4, copies: int = 1,
+                 seed_table: str | None = None):
+        """path: table read at start and written after each new measurement; seed_table: a
+        read-only table (e.g. the one measured on GB300 and shipped with the package) whose
+        entries are used as they are."""
         self.path = path
         self.warm, self.sweeps, self.copies = warm, sweeps, int(copies)
         self.table = {}
-        if path and os.path.exists(path):
-            with open(path) as f:
-                self.table = json.load(f)
+        for src in (seed_table, path):
+            if src and os.path.exists(src):
+                with open(src) as f:
+                    self.table.update(json.load(f))
 
     def save(self):
         if self.path:
@@ -126,7 +139,7 @@ class Tuner:
             lens = chain_lengths if chain_lengths is not None else [base["n_beads"]]
             system = I.make_system(list(lens), 0, base["box_L"], seed=12345)
         scores = []
-        for cand in SCHEDULE_CANDIDATES:
+        for cand in (BATCH_SCHEDULE_CANDIDATES if self.copies > 1 else SCHEDULE_CANDIDATES):
             try:
                 p = self.apply(base, cand)
             except ValueError:
@@ -159,18 +172,93 @@ class Tuner:
         return best
 
 
-def ensemble_params(systems, precision: int, planewave_mode: int, seed: int, tuner: Tuner | None = None):
-    """Parameters of an ensemble of single-chain systems (the uneven-size batch workload)."""
+SMEM_SERIAL_MAX_N = 2048   # largest simulation whose small-scale serial phase runs in shared memory
+
+
+def ensemble_params(systems, precision: int, planewave_mode: int, seed: int, tuner: Tuner | None = None,
+                    policy: str = "per_shape"):
+    """Parameters of an ensemble of single-chain systems (the uneven-size batch workload).
+
+    policy "per_shape": each simulation gets its shape's tuned schedule; "serial_small": every
+    simulation small enough for the shared-memory serial phase runs all its layers serially,
+    the others get their shape's tuned schedule. Either way the schedule depends only on the
+    simulation's own shape and the policy, never on the other members of a batch."""
     out = []
     for k, s in enumerate(systems):
         p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, sim_id=k, precision=precision,
                                 planewave_mode=planewave_mode)
-        if tuner is not None:
+        if policy == "serial_small" and s.n_beads <= SMEM_SERIAL_MAX_N:
+            p = Tuner.apply(p, {"colour_K": 2, "serial_only": True})
+        elif tuner is not None:
             p = tuner.schedule(p, chain_lengths=s.chain_len)
         out.append(p)
     return out
 
 
+def batch_throughput(params, systems, warm: int = 1, sweeps: int = 3) -> float:
+    """Bead-updates per second of one batch holding all the given simulations."""
+    import torch
+    b = wmcd.Batch(len(params), sum(wmcd.batch_need(p) for p in params) + (1 << 20))
+    try:
+        slots = [b.admit(p, s.pos, s.chain_len) for p, s in zip(params, systems)]
+        b.step(warm)
+        torch.cuda.synchronize()
+        b0 = sum(b.sim(k).stats().bead_updates for k in slots)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(sweeps)
+        e1.record()
+        e1.synchronize()
+        return (sum(b.sim(k).stats().bead_updates for k in slots) - b0) / (e0.elapsed_time(e1) / 1e3)
+    finally:
+        b.close()
+
+
+def choose_policy(systems, precision: int, planewave_mode: int, tuner: Tuner, sample: int = 256, seed: int = 7):
+    """Pick the ensemble schedule policy by measuring whole batches of a sample of the workload:
+    per-shape schedules interact in a batch (a coloured simulation adds colour phases that every
+    batched sweep waits for), which a per-shape measurement cannot see."""
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(systems), size=min(sample, len(systems)), replace=False)
+    sub = [systems[i] for i in idx]
+    scores = {}
+    for policy in ("per_shape", "serial_small"):
+        ps = ensemble_params(sub, precision, planewave_mode, seed=1, tuner=tuner, policy=policy)
+        scores[policy] = batch_throughput(ps, sub)
+    best = max(scores, key=scores.get)
+    return best, scores
+
+
 def sample_shapes(n_beads: np.ndarray, n: int) -> np.ndarray:
     """Representative bead counts (quantiles) to tune ahead of a run."""
     return np.unique(np.quantile(n_beads, np.linspace(0, 1, n)).astype(int))
+
+
+def main(argv=None):
+    """Measure the schedule table for the uneven-size ensemble shapes (single chains, lengths
+    log-uniform in [lo, hi], volume fraction phi) in batch context and write it as JSON."""
+    import argparse
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--sims", type=int, default=1024)
+    ap.add_argument("--lo", type=int, default=16)
+    ap.add_argument("--hi", type=int, default=2048)
+    ap.add_argument("--phi", type=float, default=1e-3)
+    ap.add_argument("--copies", type=int, default=152)
+    ap.add_argument("--precision", type=int, default=wmcd.MIXED)
+    ap.add_argument("--planewave", type=int, default=wmcd.PLANEWAVE_PERIODIC)
+    a = ap.parse_args(argv)
+    wmcd.build()
+    wmcd.load()
+    tuner = Tuner(path=a.out, warm=1, sweeps=2, copies=a.copies)
+    for seed in (1, 2):
+        lens = I.loguniform_lengths(a.sims, a.lo, a.hi, seed)
+        for n in sorted(set(int(x) for x in lens)):
+            L = I.box_for_volume_fraction(n, a.phi)
+            p = wmcd.default_params(n, L, seed=1, precision=a.precision, planewave_mode=a.planewave)
+            tuner.schedule(p, chain_lengths=[n])
+    print(json.dumps({k: v["choice"] for k, v in tuner.table.items()}, indent=1, sort_keys=True))
+
+
+if __name__ == "__main__":
+    main()

@@ -393,6 +393,8 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         g.pw_blocks = v.pw_blocks;
         g.prec_mask = 1 << P.precision;
         g.smem_maxN = v.smem_layers ? N : 0;
+        for (int c = 0; c < 3; c++)
+            if (v.smem_layers && N <= kSmemClassHi[c] && (c == 0 || N > kSmemClassHi[c - 1])) g.smem_cls[c] = N;
         g.any_global_serial = v.smem_layers != (1 << nL) - 1;
         for (int l = 0; l < nL; l++) {
             const int G = v.layer[l].G, Q = G / P.colour_K;
@@ -462,7 +464,8 @@ static int popcount3(int m) { return (m & 1) + ((m >> 1) & 1); }
 // this sweep's exact slot counts, used to leave out launches with no work; a batch launches
 // every phase up to its bounds and the kernels return early where a simulation has none.
 // Returns the number of kernels launched.
-int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s) {
+int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s,
+                            const ForkJoin* fj) {
     const int np = popcount3(g.prec_mask);
     int64_t launches = 0;
     { ProfScope ps(prof, 4, s); launch_counts(d, g, s); }
@@ -477,7 +480,7 @@ int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t*
             { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, l, s); }
             launches += 5 + (int64_t)g.maxK3 * (4 + np) + 1;
         }
-        { ProfScope ps(prof, 1, s); launches += launch_serial(d, g, l, s); }
+        { ProfScope ps(prof, 1, s); launches += launch_serial(d, g, l, s, fj); }
     }
     if (g.pw) {
         const int64_t MF = hc ? hc[kMaxLayers] : g.maxMF;

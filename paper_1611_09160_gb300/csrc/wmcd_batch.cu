@@ -95,6 +95,7 @@ struct Batch {
     cudaGraphExec_t exec = nullptr;
     int64_t launches_per_sweep = 0;
     Handle prof;                     // event pool and per-class times while profiling
+    ForkJoin fj;                     // side streams for launches that run side by side
 };
 
 void batch_view_changed(void* batch) { static_cast<Batch*>(batch)->stale = true; }
@@ -119,6 +120,7 @@ static GroupDims group_bounds(const std::vector<Member>& ms, int block_warps, in
     for (const Member& m : ms) {
         const GroupDims& o = m.H->h.g;
         g.smem_maxN = std::max(g.smem_maxN, o.smem_maxN);
+        for (int c = 0; c < 3; c++) g.smem_cls[c] = std::max(g.smem_cls[c], o.smem_cls[c]);
         g.any_global_serial = g.any_global_serial || o.any_global_serial;
         g.maxN = std::max(g.maxN, o.maxN);
         g.maxCells = std::max(g.maxCells, o.maxCells);
@@ -168,7 +170,7 @@ static int rebuild(Batch* b, cudaStream_t s) {
         cudaGetLastError();
         return WMCD_ECUDA;
     }
-    const int64_t n = enqueue_sweep(b->dviews, b->g, nullptr, nullptr, b->capture_stream);
+    const int64_t n = enqueue_sweep(b->dviews, b->g, nullptr, nullptr, b->capture_stream, &b->fj);
     if (cudaStreamEndCapture(b->capture_stream, &graph) != cudaSuccess || !graph) {
         cudaGetLastError();
         return WMCD_ECUDA;
@@ -217,7 +219,12 @@ extern "C" int wmcd_batch_create(int capacity, int64_t pool_bytes, wmcd_batch** 
     bool ok = cudaMalloc(&b->pool_mem, (size_t)pool_bytes) == cudaSuccess &&
               cudaMalloc((void**)&b->dviews, sizeof(SimView) * (size_t)capacity) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->admit_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->fj.side[0], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->fj.side[1], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fj.fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fj.join[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fj.join[1], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         wmcd_batch_destroy(B);
@@ -287,7 +294,7 @@ extern "C" int wmcd_batch_step(wmcd_batch* B, int64_t n_sweeps, void* stream) {
     if (!b->exec || n_sweeps == 0) return last_cuda_status();
     if (b->prof.prof) {
         // timed launch by launch, outside the graph (same kernels, same order)
-        for (int64_t k = 0; k < n_sweeps; k++) enqueue_sweep(b->dviews, b->g, nullptr, &b->prof, s);
+        for (int64_t k = 0; k < n_sweeps; k++) enqueue_sweep(b->dviews, b->g, nullptr, &b->prof, s, nullptr);
     } else {
         for (int64_t k = 0; k < n_sweeps; k++)
             if (cudaGraphLaunch(b->exec, s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
@@ -359,6 +366,11 @@ extern "C" int wmcd_batch_destroy(wmcd_batch* B) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->admit_stream) cudaStreamDestroy(b->admit_stream);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (int c = 0; c < 2; c++) {
+        if (b->fj.side[c]) cudaStreamDestroy(b->fj.side[c]);
+        if (b->fj.join[c]) cudaEventDestroy(b->fj.join[c]);
+    }
+    if (b->fj.fork) cudaEventDestroy(b->fj.fork);
     if (b->dviews) cudaFree(b->dviews);
     if (b->pool_mem) cudaFree(b->pool_mem);
     cudaGetLastError();

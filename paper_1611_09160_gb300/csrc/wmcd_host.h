@@ -47,7 +47,8 @@ struct Handle {
 
 int last_cuda_status();
 int64_t slot_count(const Handle* h, uint32_t kind, int l, uint64_t ctr, double x);
-int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s);
+int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s,
+                      const ForkJoin* fj = nullptr);
 // Set up a simulation in *H (tables, device state, cell list). With an arena the device state
 // is placed in it; a counting arena only sizes it (nothing is launched or copied). On failure
 // the caller releases H with destroy_handle.

@@ -24,7 +24,9 @@ constexpr int kStageWarps = 2;     // staged concurrent kernel: default warps pe
 constexpr int kMaxStageWarps = 4;  // ... and the most a block may have
 constexpr int kCandCap = 256;      // interaction candidates of one staged move held in shared memory
 constexpr int kSlotChunk = 32;     // slot parameters prepared per chunk
-constexpr int kSmemSerialMaxN = 2560;  // largest simulation whose serial phase runs in shared memory
+constexpr int kSmemSerialMaxN = 2048;
+constexpr int kSmemThreads = 512;  // threads of the shared-memory serial block (many warps hide the
+                                   // latency of the scans over all staged beads)  // largest simulation whose serial phase runs in shared memory
 
 enum Outcome { ACCEPT = 1, REJECT = 2, DEFER = 3 };
 
@@ -154,6 +156,7 @@ struct GroupDims {
     int block_warps = kStageWarps;  // warps (queues) per block of the staged concurrent kernel, 1..4
     int serial_threads = kSerialThreads;  // threads of the serial-phase block: 32, 128 or 512
     int64_t smem_maxN = 0;       // largest N among simulations with the shared-memory serial phase
+    int64_t smem_cls[3] = {0, 0, 0};  // ... per size class (N <= 320, <= 1024, larger), 0 = none
     bool any_global_serial = true;  // some simulation runs its serial phase through global memory
 };
 
@@ -165,7 +168,14 @@ void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s);
 void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
-int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s);      // returns kernels launched
+// Side streams and events to run independent launches of a phase side by side (recorded as
+// parallel branches of a graph); null members mean one stream.
+struct ForkJoin {
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+};
+constexpr int64_t kSmemClassHi[3] = {320, 1024, 1 << 30};
+int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj);  // kernels launched
 int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
 size_t staged_smem_bytes(int cap, int warps);
 size_t smem_serial_bytes(int64_t n);

@@ -13,7 +13,13 @@ namespace wmcd {
 __device__ __forceinline__ void set_err(const SimView& v, int bit) { atomicOr(v.err, bit); }
 
 // Every kernel serves a group of simulations: blockIdx.y selects one, whose view is copied
-// into shared memory once per block.
+// into shared memory once per block. SIM_EXIT_IF tests a condition on the view in global
+// memory first, so blocks of a simulation with no work in this launch leave without the copy.
+#define SIM_EXIT_IF(cond)                                                                     \
+    {                                                                                         \
+        const SimView& gv = vs[blockIdx.y];                                                   \
+        if (cond) return;                                                                     \
+    }
 #define SIM_PROLOGUE                                                                          \
     __shared__ SimView sv_;                                                                   \
     {                                                                                         \
@@ -44,15 +50,15 @@ __device__ __forceinline__ bool cl_skip(const SimView& v, int use_flag) {
     return false;
 }
 __global__ void k_cl_clear(const SimView* __restrict__ vs, int use_flag) {
+    SIM_EXIT_IF(cl_skip(gv, use_flag))
     SIM_PROLOGUE
-    if (cl_skip(v, use_flag)) return;
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
         v.head[c] = -1;
 }
 __global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
+    SIM_EXIT_IF(cl_skip(gv, use_flag))
     SIM_PROLOGUE
-    if (cl_skip(v, use_flag)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         Bead b = v.bead[i];
         if (!(b.x >= 0.0 && b.x < v.L && b.y >= 0.0 && b.y < v.L && b.z >= 0.0 && b.z < v.L)) set_err(v, E_NONFINITE);
@@ -62,8 +68,8 @@ __global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
     }
 }
 __global__ void k_cl_canon(const SimView* __restrict__ vs, int use_flag) {
+    SIM_EXIT_IF(cl_skip(gv, use_flag))
     SIM_PROLOGUE
-    if (cl_skip(v, use_flag)) return;
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int ids[32];
@@ -94,9 +100,15 @@ __global__ void k_cl_canon(const SimView* __restrict__ vs, int use_flag) {
         }
     }
 }
+// blocks per simulation for a grid-stride kernel: what the largest simulation needs, but no
+// more than keeps about 8k blocks over the whole group
+static unsigned gx(int64_t needed_blocks, int S) {
+    const int64_t cap = std::max<int64_t>(1, 8192 / std::max(S, 1));
+    return (unsigned)std::max<int64_t>(1, std::min(needed_blocks, cap));
+}
 void launch_cl_rebuild(const SimView* d, const GroupDims& g, cudaStream_t s, int use_flag) {
-    const dim3 bc((unsigned)std::min<int64_t>((g.maxCells + 255) / 256, 152 * 64), g.S);
-    const dim3 bb((unsigned)std::min<int64_t>((g.maxN + 255) / 256, 152 * 64), g.S);
+    const dim3 bc(gx((g.maxCells + 255) / 256, g.S), g.S);
+    const dim3 bb(gx((g.maxN + 255) / 256, g.S), g.S);
     k_cl_clear<<<bc, 256, 0, s>>>(d, use_flag);
     k_cl_insert<<<bb, 256, 0, s>>>(d, use_flag);
     k_cl_canon<<<bc, 256, 0, s>>>(d, use_flag);
@@ -137,6 +149,7 @@ void launch_advance(const SimView* d, const GroupDims& g, int which, cudaStream_
 // Appendix D) and the picked bead; then bucketing by coarse cell in colour-major order.
 // ======================================================================================
 __global__ void k_slots(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || (int)(blockIdx.x * blockDim.x) >= gv.counts[l])
     SIM_PROLOGUE
     if (l >= v.nL) return;
     const int M = v.counts[l];
@@ -158,6 +171,7 @@ void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
 }
 
 __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || (int)(blockIdx.x * blockDim.x) >= gv.counts[l])
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int M = v.counts[l];
@@ -184,6 +198,7 @@ __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
 // exclusive scan of n ints by one block per simulation: mode 0 = bucket counts of layer l
 // (G^3 keys), mode 1 = region counts of layer l (Q^3 queues)
 __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int G = v.layer[l].G, Q = G / v.K;
@@ -214,6 +229,7 @@ __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
 // zero the per-phase counters: mode 0 = bucket counts, fills and deferral flags of layer l,
 // mode 1 = region counts and fills
 __global__ void k_zero(const SimView* __restrict__ vs, int mode, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int G = v.layer[l].G, Q = G / v.K;
@@ -227,6 +243,7 @@ __global__ void k_zero(const SimView* __restrict__ vs, int mode, int l) {
     }
 }
 __global__ void k_bucket_scatter(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || (int)(blockIdx.x * blockDim.x) >= gv.counts[l])
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int M = v.counts[l];
@@ -238,6 +255,7 @@ __global__ void k_bucket_scatter(const SimView* __restrict__ vs, int l) {
 }
 // slots of one queue in ascending slot id (the order of the sequential schedule)
 __global__ void k_bucket_sort(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int nkeys = v.layer[l].G * v.layer[l].G * v.layer[l].G;
@@ -253,7 +271,7 @@ __global__ void k_bucket_sort(const SimView* __restrict__ vs, int l) {
 }
 void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
     const int keys = g.keys[l], M = g.Mmax[l];
-    k_zero<<<dim3((unsigned)std::min(1024, (std::max(keys, M) + 255) / 256), g.S), 256, 0, s>>>(d, 0, l);
+    k_zero<<<dim3(gx((std::max(keys, M) + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 0, l);
     k_bucket_count<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
     k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 0, l);
     k_bucket_scatter<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
@@ -262,6 +280,7 @@ void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) 
 
 // deferred slots in schedule order -> serial list
 __global__ void k_defer_compact(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int M = v.counts[l];
@@ -772,6 +791,7 @@ namespace wmcd {
 // normalised, and the Metropolis threshold -kT ln(1 - u) (Eq. 20). They depend only on the
 // slot's counter, not on the state, so computing them early changes nothing.
 __global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || (gv.layer[l].G == 0 && (int)(blockIdx.x * blockDim.x) >= gv.counts[l]))
     SIM_PROLOGUE
     if (l >= v.nL) return;
     const bool use_list = v.layer[l].G > 0;
@@ -802,6 +822,7 @@ __global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
 
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || ((gv.smem_layers >> l) & 1))
     SIM_PROLOGUE
     if (l >= v.nL || v.precision != PREC || ((v.smem_layers >> l) & 1)) return;
     if (threadIdx.x == 0) *v.cl_stale = 0;      // rebuilt just before this launch if it was stale
@@ -1080,7 +1101,9 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
 // here; they are marked stale and rebuilt before the next plane-wave move that needs them.
 // Shared bytes per bead: see smem_serial_bytes.
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ vs, int l) {
+__global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ vs, int l, int64_t nlo, int64_t nhi) {
+    SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || !((gv.smem_layers >> l) & 1) || gv.counts[l] == 0 ||
+                gv.N <= nlo || gv.N > nhi)
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (l >= v.nL || v.precision != PREC || !((v.smem_layers >> l) & 1)) return;
@@ -1092,11 +1115,15 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     double* py = px + N;
     double* pz = py + N;
     double* mnew = pz + N;                       // 3 per support member
-    float* fx = (float*)(mnew + 3 * (size_t)N);
+    float* fx = (float*)(mnew + 3 * (size_t)N);  // binary32 pairs (hi, lo) of the positions
     float* fy = fx + N;
     float* fz = fy + N;
-    float* mnf = fz + N;                         // 3 per member: new position in binary32
-    int* mid = (int*)(mnf + 3 * (size_t)N);      // support, in gather order
+    float* lx = fz + N;
+    float* ly = lx + N;
+    float* lz = ly + N;
+    float* mnf = lz + N;                         // 3 per member: new position, hi ...
+    float* mnl = mnf + 3 * (size_t)N;            // ... and lo
+    int* mid = (int*)(mnl + 3 * (size_t)N);      // support, in gather order
     int* sslot = mid + N;                        // per bead: index in the support or -1
     short* dimg = (short*)(sslot + N);           // 3 per bead: image change over the launch
     uint8_t* mimg = (uint8_t*)(dimg + 3 * (size_t)N);   // per member: packed image change of the move
@@ -1119,12 +1146,14 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
         const Bead b = v.bead[m];
         px[m] = b.x; py[m] = b.y; pz[m] = b.z;
         fx[m] = (float)b.x; fy[m] = (float)b.y; fz[m] = (float)b.z;
+        lx[m] = (float)(b.x - (double)fx[m]); ly[m] = (float)(b.y - (double)fy[m]); lz[m] = (float)(b.z - (double)fz[m]);
         sslot[m] = -1;
         dimg[3 * m] = 0; dimg[3 * m + 1] = 0; dimg[3 * m + 2] = 0;
         bn[m] = v.bnext[m];
     }
     if (tid == 0) { sh_carry = v.carry_serial[l]; sh_stale = 0; }
     __syncthreads();
+    const Pot32 P32 = pot32(P);
     const float rcf = (float)v.rc + marg;
     const float rc2f = rcf * rcf * (1.0f + 9.5367431640625e-7f);
     long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
@@ -1182,6 +1211,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             for (int a = 0; a < 3; a++) {
                 mnew[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
                 mnf[3 * k + a] = (float)mnew[3 * k + a];
+                mnl[3 * k + a] = (float)(mnew[3 * k + a] - (double)mnf[3 * k + a]);
             }
             mimg[k] = (uint8_t)pack_img(im[0], im[1], im[2]);
             sslot[m] = k;
@@ -1193,7 +1223,6 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
         const double thr = v.slot_thr[j];
         bool need64 = PREC == 0;
         if (PREC == 1) {
-            const Pot32 P32 = pot32(P);
             float a32 = 0.0f, m32 = 0.0f;
             int T = 0;
             auto r2f = [&](double ax, double ay, double az, double bx, double by, double bz) {
@@ -1205,6 +1234,17 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                     r2 += f * f;
                 }
                 return r2;
+            };
+
+            // squared distance between two staged points given as (hi, lo) binary32 pairs: the hi
+            // difference is rounded once relative to the result and the lo parts add the rest, so
+            // the difference carries about one ulp; a component across a face (the hi difference
+            // beyond L/2, rare for pairs in range) is wrapped in binary64 from the positions
+            auto comp = [&](float ha, float la, float hb, float lb, double xa, double xb) {
+                const float dh = ha - hb;
+                if (fabsf(dh) <= hLf) return dh + (la - lb);
+                const double e = sub(xa, xb);
+                return (float)(e > 0.0 ? sub(e, L) : add(e, L));
             };
             for (int k = tid; k < n; k += NT) {
                 const int m = mid[k];
@@ -1223,9 +1263,19 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                     const double qo[3] = {px[q], py[q], pz[q]};
                     const double qn[3] = {sq >= 0 ? mnew[3 * sq] : qo[0], sq >= 0 ? mnew[3 * sq + 1] : qo[1],
                                           sq >= 0 ? mnew[3 * sq + 2] : qo[2]};
+                    const float qnh[3] = {sq >= 0 ? mnf[3 * sq] : fx[q], sq >= 0 ? mnf[3 * sq + 1] : fy[q],
+                                          sq >= 0 ? mnf[3 * sq + 2] : fz[q]};
+                    const float qnl[3] = {sq >= 0 ? mnl[3 * sq] : lx[q], sq >= 0 ? mnl[3 * sq + 1] : ly[q],
+                                          sq >= 0 ? mnl[3 * sq + 2] : lz[q]};
+                    const float ex = comp(mnf[3 * k], mnl[3 * k], qnh[0], qnl[0], nw[0], qn[0]);
+                    const float ey = comp(mnf[3 * k + 1], mnl[3 * k + 1], qnh[1], qnl[1], nw[1], qn[1]);
+                    const float ez = comp(mnf[3 * k + 2], mnl[3 * k + 2], qnh[2], qnl[2], nw[2], qn[2]);
+                    const float gx_ = comp(fx[m], lx[m], fx[q], lx[q], o[0], qo[0]);
+                    const float gy_ = comp(fy[m], ly[m], fy[q], ly[q], o[1], qo[1]);
+                    const float gz_ = comp(fz[m], lz[m], fz[q], lz[q], o[2], qo[2]);
                     float un, mn, uo, mo;
-                    bond32(P32, r2f(nw[0], nw[1], nw[2], qn[0], qn[1], qn[2]), un, mn);
-                    bond32(P32, r2f(o[0], o[1], o[2], qo[0], qo[1], qo[2]), uo, mo);
+                    bond32(P32, ex * ex + ey * ey + ez * ez, un, mn);
+                    bond32(P32, gx_ * gx_ + gy_ * gy_ + gz_ * gz_, uo, mo);
                     a32 += un - uo; m32 += mn + mo; T += 2;
                 }
             }
@@ -1252,9 +1302,17 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                             const double qo[3] = {px[q], py[q], pz[q]};
                             const double qn[3] = {sq >= 0 ? mnew[3 * sq] : qo[0], sq >= 0 ? mnew[3 * sq + 1] : qo[1],
                                                   sq >= 0 ? mnew[3 * sq + 2] : qo[2]};
+                            const float qnl[3] = {sq >= 0 ? mnl[3 * sq] : lx[q], sq >= 0 ? mnl[3 * sq + 1] : ly[q],
+                                                  sq >= 0 ? mnl[3 * sq + 2] : lz[q]};
+                            const float ex = comp(mnf[3 * k], mnl[3 * k], qnx, qnl[0], mnew[3 * k], qn[0]);
+                            const float ey = comp(mnf[3 * k + 1], mnl[3 * k + 1], qny, qnl[1], mnew[3 * k + 1], qn[1]);
+                            const float ez = comp(mnf[3 * k + 2], mnl[3 * k + 2], qnz, qnl[2], mnew[3 * k + 2], qn[2]);
+                            const float gx_ = comp(fx[m], lx[m], qfx, lx[q], px[m], qo[0]);
+                            const float gy_ = comp(fy[m], ly[m], qfy, ly[q], py[m], qo[1]);
+                            const float gz_ = comp(fz[m], lz[m], qfz, lz[q], pz[m], qo[2]);
                             float un, mn, uo, mo;
-                            wca32(P32, r2f(mnew[3 * k], mnew[3 * k + 1], mnew[3 * k + 2], qn[0], qn[1], qn[2]), un, mn);
-                            wca32(P32, r2f(px[m], py[m], pz[m], qo[0], qo[1], qo[2]), uo, mo);
+                            wca32(P32, ex * ex + ey * ey + ez * ez, un, mn);
+                            wca32(P32, gx_ * gx_ + gy_ * gy_ + gz_ * gz_, uo, mo);
                             a32 += un - uo; m32 += mn + mo; T += 2;
                             if (sq < 0 && (un != 0.0f || uo != 0.0f)) pe++;
                         }
@@ -1365,7 +1423,8 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             const int m = mid[k];
             if (acc) {
                 px[m] = mnew[3 * k]; py[m] = mnew[3 * k + 1]; pz[m] = mnew[3 * k + 2];
-                fx[m] = (float)px[m]; fy[m] = (float)py[m]; fz[m] = (float)pz[m];
+                fx[m] = mnf[3 * k]; fy[m] = mnf[3 * k + 1]; fz[m] = mnf[3 * k + 2];
+                lx[m] = mnl[3 * k]; ly[m] = mnl[3 * k + 1]; lz[m] = mnl[3 * k + 2];
                 int dd[3];
                 unpack_img(mimg[k], dd);
                 dimg[3 * m] += (short)dd[0]; dimg[3 * m + 1] += (short)dd[1]; dimg[3 * m + 2] += (short)dd[2];
@@ -1406,19 +1465,51 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     }
 }
 
-size_t smem_serial_bytes(int64_t n) { return (size_t)n * (3 * 8 + 3 * 8 + 3 * 4 + 4 + 4 + 3 * 2 + 3 * 4 + 1 + 1) + 64; }
+size_t smem_serial_bytes(int64_t n) { return (size_t)n * (3 * 8 + 3 * 8 + 6 * 4 + 6 * 4 + 4 + 4 + 3 * 2 + 1 + 1) + 64; }
 
-int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
+int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj) {
     const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
-    int launched = 1 + (g.smem_maxN > 0 ? np : 0) + (g.any_global_serial ? np : 0);
+    int launched = 1 + (g.any_global_serial ? np : 0);
     prepare_staged(g);
     k_serial_prep<<<dim3((g.Mmax[l] + 127) / 128, g.S), 128, 0, s>>>(d, l);
     // one launch per precision; each returns at once for simulations of the other precision
     const dim3 grid(1, g.S);
     if (g.smem_maxN > 0) {
-        const size_t sm = smem_serial_bytes(g.smem_maxN);
-        if (g.prec_mask & 1) k_serial_smem<0, 256><<<grid, 256, sm, s>>>(d, l);
-        if (g.prec_mask & 2) k_serial_smem<1, 256><<<grid, 256, sm, s>>>(d, l);
+        // one launch per size class, each with the shared memory of its largest simulation, so
+        // small simulations pack many blocks per SM; with side streams the classes run side by side
+        int ncls = 0;
+        for (int c = 0; c < 3; c++) ncls += g.smem_cls[c] > 0;
+        const bool fork = fj && fj->side[0] && ncls > 1;
+        if (fork) {
+            cudaEventRecord(fj->fork, s);
+            cudaStreamWaitEvent(fj->side[0], fj->fork, 0);
+            cudaStreamWaitEvent(fj->side[1], fj->fork, 0);
+        }
+        for (int c = 2; c >= 0; c--) {
+            if (!g.smem_cls[c]) continue;
+            cudaStream_t cs = fork ? (c == 2 ? s : fj->side[c]) : s;
+            const size_t sm = smem_serial_bytes(g.smem_cls[c]);
+            const int64_t lo = c ? kSmemClassHi[c - 1] : 0, hi = kSmemClassHi[c];
+            // threads per class: few for small simulations (several blocks share an SM), many
+            // for large ones (one block per SM, whose warps must hide the latency of the scans)
+            if (c == 0) {
+                if (g.prec_mask & 1) k_serial_smem<0, 128><<<grid, 128, sm, cs>>>(d, l, lo, hi);
+                if (g.prec_mask & 2) k_serial_smem<1, 128><<<grid, 128, sm, cs>>>(d, l, lo, hi);
+            } else if (c == 1) {
+                if (g.prec_mask & 1) k_serial_smem<0, 256><<<grid, 256, sm, cs>>>(d, l, lo, hi);
+                if (g.prec_mask & 2) k_serial_smem<1, 256><<<grid, 256, sm, cs>>>(d, l, lo, hi);
+            } else {
+                if (g.prec_mask & 1) k_serial_smem<0, 512><<<grid, 512, sm, cs>>>(d, l, lo, hi);
+                if (g.prec_mask & 2) k_serial_smem<1, 512><<<grid, 512, sm, cs>>>(d, l, lo, hi);
+            }
+            launched += np;
+        }
+        if (fork) {
+            for (int c = 0; c < 2; c++) {
+                cudaEventRecord(fj->join[c], fj->side[c]);
+                cudaStreamWaitEvent(s, fj->join[c], 0);
+            }
+        }
     }
     if (!g.any_global_serial) return launched;
     if (g.smem_maxN > 0) {
@@ -1453,6 +1544,7 @@ __global__ void k_pw_setup(const SimView* __restrict__ vs, int direct, int m) {
     SIM_PROLOGUE
     if (threadIdx.x != 0) return;
     PWDev& P = *v.pw;
+    *v.pw_rebuild = 0;
     P.active = direct ? 1 : (v.pw_on && m < v.counts[kMaxLayers]);
     if (!P.active) return;
     const uint64_t ctr = v.step[direct ? 1 : 0];
@@ -1513,6 +1605,7 @@ __global__ void k_pw_setup(const SimView* __restrict__ vs, int direct, int m) {
 }
 
 __global__ void k_pw_disp(const SimView* __restrict__ vs) {
+    SIM_EXIT_IF(!gv.pw->active || gv.pw->null_move)
     SIM_PROLOGUE
     const PWDev& P = *v.pw;
     if (!P.active || P.null_move) return;
@@ -1537,6 +1630,7 @@ __global__ void k_pw_disp(const SimView* __restrict__ vs) {
 }
 
 __global__ void __launch_bounds__(256) k_pw_energy(const SimView* __restrict__ vs) {
+    SIM_EXIT_IF(!gv.pw->active || (int)blockIdx.x >= gv.pw_blocks)
     SIM_PROLOGUE
     __shared__ double red[8];
     const PWDev& P = *v.pw;
@@ -1594,6 +1688,7 @@ __global__ void __launch_bounds__(256) k_pw_energy(const SimView* __restrict__ v
 }
 
 __global__ void __launch_bounds__(256) k_pw_decide(const SimView* __restrict__ vs, int direct, int m) {
+    SIM_EXIT_IF(!gv.pw->active || gv.pw->null_move)
     SIM_PROLOGUE
     __shared__ double red[8];
     PWDev& P = *v.pw;
@@ -1626,6 +1721,7 @@ __global__ void __launch_bounds__(256) k_pw_decide(const SimView* __restrict__ v
 }
 
 __global__ void k_pw_commit(const SimView* __restrict__ vs) {
+    SIM_EXIT_IF(!(gv.pw->active && gv.pw->accept && !gv.pw->null_move))
     SIM_PROLOGUE
     const PWDev& P = *v.pw;
     const bool moved = P.active && P.accept && !P.null_move;
@@ -1644,7 +1740,7 @@ __global__ void k_pw_commit(const SimView* __restrict__ vs) {
 
 int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s) {
     const int nb = g.pw_blocks;
-    const int gb = (int)std::min<int64_t>(nb, 152 * 16);
+    const int gb = (int)gx(nb, g.S);
     k_pw_setup<<<dim3(1, g.S), 32, 0, s>>>(d, direct, m);
     launch_cl_rebuild(d, g, s, 2);
     k_pw_disp<<<dim3(gb, g.S), 256, 0, s>>>(d);
@@ -1666,6 +1762,7 @@ namespace wmcd {
 // Beads are assigned to regions by a counting sort over all beads before each colour phase.
 // ======================================================================================
 __global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || colour >= gv.K * gv.K * gv.K)
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0 || colour >= v.K * v.K * v.K) return;
     const int K = v.K, Gf = v.Gf, Q = v.layer[l].G / K;
@@ -1682,6 +1779,7 @@ __global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour
     }
 }
 __global__ void k_region_scatter(const SimView* __restrict__ vs, int l, int colour) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || colour >= gv.K * gv.K * gv.K)
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0 || colour >= v.K * v.K * v.K) return;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
@@ -2026,6 +2124,8 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
 
 template <int PREC>
 __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour) {
+    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
+                (int)(blockIdx.x * (blockDim.x >> 5)) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K))
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
@@ -2217,11 +2317,15 @@ void prepare_staged(const GroupDims& g) {
     if (g.smem_maxN > 0) {
         const int sm = (int)smem_serial_bytes(g.smem_maxN);
         if ((g.prec_mask & 1) && sm > g_serial_smem[dev][0]) {
+            cudaFuncSetAttribute(k_serial_smem<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             cudaFuncSetAttribute(k_serial_smem<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_serial_smem<0, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             g_serial_smem[dev][0] = sm;
         }
         if ((g.prec_mask & 2) && sm > g_serial_smem[dev][1]) {
+            cudaFuncSetAttribute(k_serial_smem<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             cudaFuncSetAttribute(k_serial_smem<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_serial_smem<1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             g_serial_smem[dev][1] = sm;
         }
     }
@@ -2238,8 +2342,8 @@ void prepare_staged(const GroupDims& g) {
 
 void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s) {
     const int nq = g.nq[l];
-    const int gb = (int)std::min<int64_t>((g.maxN + 255) / 256, 152 * 16);
-    k_zero<<<dim3((unsigned)std::min(1024, (nq + 255) / 256), g.S), 256, 0, s>>>(d, 1, l);
+    const int gb = (int)gx((g.maxN + 255) / 256, g.S);
+    k_zero<<<dim3(gx((nq + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 1, l);
     k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
     k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l);
     k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
