@@ -73,6 +73,11 @@ typedef struct wmcd_params {
     int32_t n_cap;            /* largest support a concurrent move handles (1..64) */
     int32_t grid_layer[WMCD_MAX_LAYERS];  /* coarse cells per axis per layer; 0 = serial;
                                              otherwise a multiple of colour_K, at most 256 */
+    int32_t big_support;      /* a serial layer whose expected support (N times the volume of a
+                                 ball of the layer's middle scale over L^3) reaches this many
+                                 beads runs each of its moves on the whole GPU (Sec. VIII: large
+                                 moves in parallel); 0 = 2048, negative = never. A launch choice:
+                                 decisions do not depend on it */
 } wmcd_params;
 
 /* Counters since creation (or the last wmcd_set_state). */
@@ -156,7 +161,7 @@ int wmcd_set_state(wmcd_handle* h, const void* buf, int64_t bytes, void* stream)
  * its concurrent wavelet kernel, serial kernel and plane-wave kernels on `stream`;
  * wmcd_kernel_times synchronises and returns (launches, total milliseconds) for the
  * kernel classes 0 = concurrent wavelet, 1 = serial wavelet, 2 = plane wave, 3 = cell list,
- * 4 = schedule (slots and bucketing). */
+ * 4 = schedule (slots and bucketing), 5 = serial moves of large scale run on the whole GPU. */
 int wmcd_profile(wmcd_handle* h, int enable);
 int wmcd_kernel_times(wmcd_handle* h, int64_t* launches, double* ms, int n_classes, void* stream);
 

@@ -325,7 +325,8 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
          !dalloc(h, &v.s_box, 6 * N) && !dalloc(h, &v.s_pre, N + 1) &&
          !dalloc(h, &v.serial_tag, 1);
     ok = ok && !dalloc(h, &v.pw, 1) && !dalloc(h, &v.pw_new, 3 * N) && !dalloc(h, &v.pw_imgd, N) &&
-         !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1) && !dalloc(h, &v.cl_stale, 1);
+         !dalloc(h, &v.pw_part, v.pw_blocks) && !dalloc(h, &v.pw_rebuild, 1) && !dalloc(h, &v.cl_stale, 1) &&
+         !dalloc(h, &v.big, 1);
     ok = ok && !dalloc(h, &v.step, 2) && !dalloc(h, &v.counts, kMaxLayers + 1) && !dalloc(h, &h->dview, 1);
     int* d_modes = nullptr;
     double* d_cdf = nullptr;
@@ -378,6 +379,17 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         if (all_serial && N <= kSmemSerialMaxN)
             for (int l = 0; l < nL; l++)
                 if (v.layer[l].hi <= 4.0 * P.lambda_min) v.smem_layers |= 1 << l;
+        // whole-GPU moves: serial layers whose expected support (N times the volume fraction of
+        // a ball of the band's geometric-mean scale) reaches big_support beads
+        v.big_layers = 0;
+        const double bs = P.big_support == 0 ? 2048.0 : (double)P.big_support;
+        if (P.big_support >= 0)
+            for (int l = 0; l < nL; l++) {
+                if (v.layer[l].G != 0 || ((v.smem_layers >> l) & 1)) continue;
+                const double lm = std::sqrt(v.layer[l].lo * v.layer[l].hi);
+                const double ns = (double)N * (4.0 / 3.0) * kPi * lm * lm * lm / (P.box_L * P.box_L * P.box_L);
+                if (ns >= bs) v.big_layers |= 1 << l;
+            }
     }
     // launch bounds of this simulation
     {
@@ -395,13 +407,14 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         g.smem_maxN = v.smem_layers ? N : 0;
         for (int c = 0; c < 3; c++)
             if (v.smem_layers && N <= kSmemClassHi[c] && (c == 0 || N > kSmemClassHi[c - 1])) g.smem_cls[c] = N;
-        g.any_global_serial = v.smem_layers != (1 << nL) - 1;
+        g.any_global_serial = (v.smem_layers | v.big_layers) != (1 << nL) - 1;
         for (int l = 0; l < nL; l++) {
             const int G = v.layer[l].G, Q = G / P.colour_K;
             g.Mmax[l] = h->Mmax[l];
             g.keys[l] = std::max(G * G * G, 1);
             g.nq[l] = std::max(Q * Q * Q, 1);
             g.coloured[l] = G > 0;
+            g.bigM[l] = ((v.big_layers >> l) & 1) ? h->Mmax[l] : 0;
         }
     }
     cudaMemsetAsync(v.step, 0, 2 * sizeof(uint64_t), s);
@@ -481,6 +494,11 @@ int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t*
             launches += 5 + (int64_t)g.maxK3 * (4 + np) + 1;
         }
         { ProfScope ps(prof, 1, s); launches += launch_serial(d, g, l, s, fj); }
+        if (g.bigM[l] > 0) {
+            const int64_t M = hc ? hc[l] : g.bigM[l];
+            ProfScope ps(prof, 5, s);
+            for (int64_t t = 0; t < M; t++) launches += launch_big(d, g, l, (int)t, s);
+        }
     }
     if (g.pw) {
         const int64_t MF = hc ? hc[kMaxLayers] : g.maxMF;

@@ -136,6 +136,7 @@ static GroupDims group_bounds(const std::vector<Member>& ms, int block_warps, in
             g.keys[l] = std::max(g.keys[l], o.keys[l]);
             g.nq[l] = std::max(g.nq[l], o.nq[l]);
             g.coloured[l] = g.coloured[l] || o.coloured[l];
+            g.bigM[l] = std::max(g.bigM[l], o.bigM[l]);
         }
     }
     for (int l = 0; l < g.maxL; l++) {

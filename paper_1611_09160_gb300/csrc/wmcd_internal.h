@@ -48,6 +48,14 @@ struct LayerDev {
     int64_t tr_off;              // offset of this layer's trace
 };
 
+// The serial move of a large-scale layer that runs on the whole GPU, one kernel per step.
+struct BigMove {
+    int active;                  // this slot exists in the current sweep
+    int j, n, acc;               // slot, support size (gathered), decision
+    uint32_t tag;                // support mark of this move
+    double lam, thr, b[3], p[3];
+};
+
 struct PWDev {
     int lv[3];
     int null_move;               // k = 0
@@ -130,6 +138,8 @@ struct SimView {
     double* pw_part;             // per-block partial sums
     int* pw_rebuild;             // set by the commit when beads moved: the cell list is rebuilt
     int* cl_stale;               // set by the shared-memory serial phase when beads changed fine cell
+    BigMove* big;
+    int big_layers;              // bit l: layer l's moves run one at a time on the whole GPU
     int smem_layers;             // bit l: layer l's serial phase runs in shared memory (small N, no
                                  // coloured layer, small scales)
     int pw_blocks;
@@ -157,6 +167,7 @@ struct GroupDims {
     int serial_threads = kSerialThreads;  // threads of the serial-phase block: 32, 128 or 512
     int64_t smem_maxN = 0;       // largest N among simulations with the shared-memory serial phase
     int64_t smem_cls[3] = {0, 0, 0};  // ... per size class (N <= 320, <= 1024, larger), 0 = none
+    int bigM[kMaxLayers] = {0};  // slots of a whole-GPU layer (largest over the group), 0 = none
     bool any_global_serial = true;  // some simulation runs its serial phase through global memory
 };
 
@@ -177,6 +188,7 @@ struct ForkJoin {
 constexpr int64_t kSmemClassHi[3] = {320, 1024, 1 << 30};
 int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj);  // kernels launched
 int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
+int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t s);     // kernels launched
 size_t staged_smem_bytes(int cap, int warps);
 size_t smem_serial_bytes(int64_t n);
 // open the kernels that take large dynamic shared memory for the sizes of g (before a graph

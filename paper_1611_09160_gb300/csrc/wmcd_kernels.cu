@@ -822,9 +822,9 @@ __global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
 
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || ((gv.smem_layers >> l) & 1))
+    SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || (((gv.smem_layers | gv.big_layers) >> l) & 1))
     SIM_PROLOGUE
-    if (l >= v.nL || v.precision != PREC || ((v.smem_layers >> l) & 1)) return;
+    if (l >= v.nL || v.precision != PREC || (((v.smem_layers | v.big_layers) >> l) & 1)) return;
     if (threadIdx.x == 0) *v.cl_stale = 0;      // rebuilt just before this launch if it was stale
     const int M = v.counts[l];
     const int use_list = v.layer[l].G > 0;
@@ -1749,6 +1749,234 @@ int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cu
     k_pw_commit<<<dim3(gb, g.S), 256, 0, s>>>(d);
     launch_cl_rebuild(d, g, s, 1);
     return 11;
+}
+
+}  // namespace wmcd
+
+namespace wmcd {
+
+// ======================================================================================
+// Serial moves of a large-scale layer on the whole GPU (Sec. VIII: a single large wavelet
+// move executed in parallel). One move is a short sequence of launches over all beads or
+// all support members: centre and slot parameters (one thread), support by a scan of all
+// beads, displacements, energy change with per-block partial sums, the decision (fixed-order
+// sum of the partials), the commit, and a cell-list rebuild if the move was accepted. The
+// arithmetic of every step is that of the one-block serial kernel, so decisions agree.
+// ======================================================================================
+__global__ void k_big_setup(const SimView* __restrict__ vs, int l, int t) {
+    SIM_PROLOGUE
+    if (threadIdx.x != 0) return;
+    *v.pw_rebuild = 0;                          // every simulation: the rebuild below is only for this move
+    if (l >= v.nL || !((v.big_layers >> l) & 1)) return;
+    BigMove& B = *v.big;
+    B.active = t < v.counts[l];
+    if (!B.active) return;
+    const int j = t;
+    const double carry = v.carry_serial[l];
+    const double lam = carry > 0.0 ? carry : v.slot_lam[j];
+    const Bead bi = v.bead[v.slot_bead[j]];
+    const double ri[3] = {bi.x, bi.y, bi.z};
+    for (int a = 0; a < 3; a++) {
+        B.b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), v.L, nullptr);
+        B.p[a] = v.slot_p[3 * j + a];
+    }
+    B.lam = lam;
+    B.j = j;
+    B.thr = v.slot_thr[j];
+    B.n = 0;
+    B.acc = 0;
+    uint32_t tag = *v.serial_tag + 1u;
+    if (tag == 0u) tag = 1u;
+    *v.serial_tag = tag;
+    B.tag = tag;
+}
+
+// support: every bead strictly inside the ball (minimum image), in no particular order
+__global__ void k_big_gather(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active)
+    SIM_PROLOGUE
+    BigMove* B = v.big;
+    const double b[3] = {B->b[0], B->b[1], B->b[2]};
+    const double lam = B->lam, lam2 = mul(lam, lam);
+    const double L = v.L, hL = v.halfL;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
+        const Bead bb = v.bead[m];
+        const double d0 = mi(sub(bb.x, b[0]), L, hL), d1 = mi(sub(bb.y, b[1]), L, hL), d2c = mi(sub(bb.z, b[2]), L, hL);
+        const double d2 = norm2(d0, d1, d2c);
+        if (d2 < lam2) {
+            const int idx = atomicAdd(&B->n, 1);
+            v.s_ids[idx] = (int)m;
+            v.s_d[4 * idx] = d0; v.s_d[4 * idx + 1] = d1; v.s_d[4 * idx + 2] = d2c; v.s_d[4 * idx + 3] = d2;
+        }
+    }
+}
+
+__global__ void k_big_disp(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active || gv.big->n == 0)
+    SIM_PROLOGUE
+    const BigMove& B = *v.big;
+    const int n = B.n;
+    const double lam = B.lam;
+    const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+    const double p[3] = {B.p[0], B.p[1], B.p[2]};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int m = v.s_ids[k];
+        v.bead[m].mark = B.tag;
+        v.s_slot[m] = k;
+        double d[3] = {v.s_d[4 * k], v.s_d[4 * k + 1], v.s_d[4 * k + 2]}, dl[3];
+        if (v.precision == 0) wavelet_disp64(d, v.s_d[4 * k + 3], lam, Aw, p, dl);
+        else wavelet_disp32(d, lam, Aw, p, dl);
+        const Bead bm = v.bead[m];
+        const double o[3] = {bm.x, bm.y, bm.z};
+        int im[3] = {0, 0, 0};
+        for (int a = 0; a < 3; a++) {
+            v.s_new[3 * k + a] = wrap(add(o[a], dl[a]), v.L, &im[a]);
+            v.s_d[4 * k + a] = dl[a];          // the displacement, for the partner box
+        }
+        v.s_img[k] = pack_img(im[0], im[1], im[2]);
+    }
+}
+
+// energy change, one thread per member: external well, bonds, WCA with every bead in the
+// member's partner box; per-block partial sums in pw_part
+__global__ void __launch_bounds__(256) k_big_energy(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active ||
+                (int)(blockIdx.x * blockDim.x) >= gv.big->n)
+    SIM_PROLOGUE
+    __shared__ double red[8];
+    const BigMove& B = *v.big;
+    const int n = B.n;
+    const uint32_t tag = B.tag;
+    const double L = v.L, hL = v.halfL;
+    const Pot& P = v.pot;
+    const double Aw = dvd(mul(v.A0, B.lam), sqr_t((double)n));
+    const double ext = add(v.rc, mul(0.25, Aw)) + 1e-9;
+    double dU = 0.0;
+    long long pe = 0;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const int m = v.s_ids[k];
+        const Bead bm = v.bead[m];
+        const double o[3] = {bm.x, bm.y, bm.z};
+        const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
+        dU += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, o[0], o[1], o[2]);
+        for (int e = 0; e < 2; e++) {
+            const int q = e ? m + 1 : m - 1;
+            if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q])) continue;
+            const Bead bq = v.bead[q];
+            double qn[3] = {bq.x, bq.y, bq.z};
+            if (bq.mark == tag) {
+                if (q < m) continue;
+                const int sq = v.s_slot[q];
+                qn[0] = v.s_new[3 * sq]; qn[1] = v.s_new[3 * sq + 1]; qn[2] = v.s_new[3 * sq + 2];
+            }
+            const double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+            const double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+            dU += U_bond(P, r2n) - U_bond(P, r2o);
+        }
+        if (P.eps != 0.0) {
+            double lo[3], hi[3];
+            for (int a = 0; a < 3; a++) {
+                const double u = add(o[a], v.s_d[4 * k + a]);
+                lo[a] = sub(fmin(o[a], u), ext);
+                hi[a] = add(fmax(o[a], u), ext);
+            }
+            int c0[3], nc[3];
+            cell_box(v, lo, hi, c0, nc);
+            const int ncell = nc[0] * nc[1] * nc[2];
+            for (int kk = 0; kk < ncell; kk++) {
+                int guard = 0;
+                for (int q = v.head[box_cell(v, c0, nc, kk)]; q >= 0;) {
+                    const Bead bq = v.bead[q];
+                    const int nx = bq.next;
+                    if (q != m) {
+                        const bool member = bq.mark == tag;
+                        if (!(member && q < m)) {
+                            double qn[3] = {bq.x, bq.y, bq.z};
+                            if (member) {
+                                const int sq = v.s_slot[q];
+                                qn[0] = v.s_new[3 * sq]; qn[1] = v.s_new[3 * sq + 1]; qn[2] = v.s_new[3 * sq + 2];
+                            }
+                            const double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                            const double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                            if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); if (!member) pe++; }
+                        }
+                    }
+                    q = nx;
+                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                }
+            }
+        }
+    }
+    dU = warp_sum(dU);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dU;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double su = 0.0;
+        for (int w = 0; w < 8; w++) su += red[w];
+        v.pw_part[blockIdx.x] = su;
+    }
+    if (pe) atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
+}
+
+// decision: the partials of the blocks that held members, summed in a fixed order
+__global__ void __launch_bounds__(256) k_big_decide(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active)
+    SIM_PROLOGUE
+    __shared__ double red[8];
+    BigMove& B = *v.big;
+    const int n = B.n;
+    const int nb = (n + 255) / 256;
+    double su = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) su += v.pw_part[b];
+    su = warp_sum(su);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = su;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double dU = 0.0;
+    for (int w = 0; w < 8; w++) dU += red[w];
+    const LayerDev& Ly = v.layer[l];
+    const bool acc = n == 0 || dU <= B.thr;     // an empty support moves nothing and is accepted
+    B.acc = acc;
+    v.tr_out[Ly.tr_off + B.j] = (uint8_t)(acc ? 1 : 2);
+    v.tr_n[Ly.tr_off + B.j] = n;
+    v.tr_du[Ly.tr_off + B.j] = n == 0 ? 0.0 : dU;
+    v.carry_serial[l] = acc ? 0.0 : B.lam;
+    atomicAdd(&v.ctr[C_ATT + l], 1ull);
+    atomicAdd(&v.ctr[C_BU], (unsigned long long)n);
+    if (acc) {
+        atomicAdd(&v.ctr[C_ACC + l], 1ull);
+        atomicAdd(&v.ctr[C_ACCTOT], 1ull);
+    }
+}
+
+__global__ void k_big_commit(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active || !gv.big->acc || gv.big->n == 0)
+    SIM_PROLOGUE
+    const int n = v.big->n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *v.pw_rebuild = 1;   // the cell lists are rebuilt next
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int m = v.s_ids[k];
+        v.bead[m].x = v.s_new[3 * k]; v.bead[m].y = v.s_new[3 * k + 1]; v.bead[m].z = v.s_new[3 * k + 2];
+        const int pk = v.s_img[k];
+        if (pk != pack_img(0, 0, 0)) {
+            int dd[3];
+            unpack_img(pk, dd);
+            v.img[3 * m] += dd[0]; v.img[3 * m + 1] += dd[1]; v.img[3 * m + 2] += dd[2];
+        }
+    }
+}
+
+int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t s) {
+    const int gb = (int)gx((g.maxN + 255) / 256, g.S);
+    k_big_setup<<<dim3(1, g.S), 32, 0, s>>>(d, l, t);
+    k_big_gather<<<dim3(gb, g.S), 256, 0, s>>>(d, l);
+    k_big_disp<<<dim3(gb, g.S), 256, 0, s>>>(d, l);
+    k_big_energy<<<dim3(g.pw_blocks, g.S), 256, 0, s>>>(d, l);
+    k_big_decide<<<dim3(1, g.S), 256, 0, s>>>(d, l);
+    k_big_commit<<<dim3(gb, g.S), 256, 0, s>>>(d, l);
+    launch_cl_rebuild(d, g, s, 1);
+    return 9;
 }
 
 }  // namespace wmcd

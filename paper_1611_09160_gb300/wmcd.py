@@ -30,7 +30,7 @@ PLANEWAVE_OFF, PLANEWAVE_PERIODIC = 0, 1
 FP64, MIXED = 0, 1
 STATUS = {0: "WMCD_OK", -1: "WMCD_EINVAL", -2: "WMCD_ENOMEM", -3: "WMCD_ECUDA", -4: "WMCD_ETIMEOUT", -5: "WMCD_ESTATE",
           -6: "WMCD_EFULL"}
-KERNEL_CLASSES = ["concurrent_wavelet", "serial_wavelet", "plane_wave", "cell_list", "schedule"]
+KERNEL_CLASSES = ["concurrent_wavelet", "serial_wavelet", "plane_wave", "cell_list", "schedule", "whole_gpu_serial"]
 
 
 def _nvcc() -> str:
@@ -79,7 +79,7 @@ class Params(ctypes.Structure):
         ("planewave_mode", ctypes.c_int32), ("lcut", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("sim_id", ctypes.c_uint64),
         ("colour_K", ctypes.c_int32), ("grid_f", ctypes.c_int32), ("n_cap", ctypes.c_int32),
-        ("grid_layer", ctypes.c_int32 * MAX_LAYERS),
+        ("grid_layer", ctypes.c_int32 * MAX_LAYERS), ("big_support", ctypes.c_int32),
     ]
 
 

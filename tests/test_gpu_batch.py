@@ -35,6 +35,11 @@ def mixed_systems():
     out.append((p, s))
     s = I.free_spheres(300, 3e-3, seed=7)
     out.append((wmcd.default_params(s.n_beads, s.box_L, seed=15, bond_type=wmcd.BOND_NONE), s))
+    s = I.make_system([16] * 12, 0, I.box_for_volume_fraction(192, 0.05), seed=8)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=16, precision=wmcd.MIXED, planewave_mode=wmcd.PLANEWAVE_PERIODIC)
+    p["grid_layer"] = [0] * 16
+    p["big_support"] = 4          # its largest scales run as whole-GPU moves
+    out.append((p, s))
     return out
 
 

@@ -156,6 +156,24 @@ def test_mixed_precision_many_moves_dense():
     assert st.conc_bead_updates > 0
 
 
+@pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])
+def test_whole_gpu_serial_moves(precision):
+    """Serial layers of large scale run each move as a sequence of whole-GPU launches (support
+    scan over all beads, per-member energies, block partials summed in a fixed order). A small
+    threshold on the expected support sends the upper layers of small systems down that path."""
+    s = I.make_system([16] * 12, 0, I.box_for_volume_fraction(192, 0.05), seed=9)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=23, precision=precision, planewave_mode=wmcd.PLANEWAVE_PERIODIC)
+    p["grid_layer"] = [0] * 16
+    p["big_support"] = 4
+    run_pair(p, s, 40, planewaves=4)
+    c = I.dilute_chains(n_chains=24, chain_len=64, phi=1e-3, seed=10)
+    p = wmcd.default_params(c.n_beads, c.box_L, seed=29, precision=precision)
+    p["big_support"] = 64
+    assert p["grid_layer"][0] > 0 and p["grid_layer"][4] == 0
+    gpu, ref = run_pair(p, c, 12)
+    assert sum(ref.stats().attempts[4:6]) > 0
+
+
 def test_free_spheres_and_fene():
     s = I.free_spheres(500, 3e-3, seed=7)
     p = wmcd.default_params(s.n_beads, s.box_L, seed=2, bond_type=wmcd.BOND_NONE)
