@@ -233,6 +233,39 @@ def ensemble_leg(args, torch, stream, flush, tuner):
     return out
 
 
+def semidilute_leg(args, torch, stream, flush):
+    """C3: homogeneous semi-dilute solution, 4,096 chains x 256 beads (1,048,576) at volume
+    fraction 0.05, wavelets + plane waves; schedule autotuned over two colour strides; mixed
+    precision against plain FP64 on the same inputs."""
+    from paper_1611_09160_gb300 import autotune as A
+    from paper_1611_09160_gb300 import inputs as I
+    from paper_1611_09160_gb300 import wmcd
+    s = I.semidilute_chains(4096, 256, 0.05, seed=1)
+    tuner = A.Tuner(path=None, warm=1, sweeps=1, seed_table=A.DEFAULT_TABLE)
+    t0 = time.perf_counter()
+    base = wmcd.default_params(s.n_beads, s.box_L, seed=1, precision=wmcd.MIXED,
+                               planewave_mode=wmcd.PLANEWAVE_PERIODIC)
+    p = tuner.schedule(base, system=s, candidates=({"colour_K": 3}, {"colour_K": 2}))
+    out = {"workload": "semi-dilute chains 4096x256 beads (1,048,576) phi=0.05 L=444.5, wavelet+plane-wave lcut 8",
+           "schedule": {"colour_K": p["colour_K"], "grid_f": p["grid_f"], "grid_layer": p["grid_layer"][:8]},
+           "tune_s": round(time.perf_counter() - t0, 1)}
+    for name, prec, sweeps in (("mixed", wmcd.MIXED, args.semidilute_sweeps), ("fp64", wmcd.FP64, 1)):
+        sim = wmcd.Simulation(dict(p, precision=prec), s.pos, s.chain_len, stream=stream)
+        sim.sweep(1, stream=stream)
+        st0 = sim.stats(stream=stream)
+        ms = timed_steps(sim, sweeps, flush, stream, torch)
+        st1 = sim.stats(stream=stream)
+        tot = float(np.sum(ms))
+        att = sum(st1.attempts) - sum(st0.attempts)
+        out[name] = {"bead_updates_per_s": (st1.bead_updates - st0.bead_updates) / (tot * 1e-3),
+                     "sim_time_per_s": (st1.sim_time - st0.sim_time) / (tot * 1e-3), "ms_per_sweep": tot / sweeps,
+                     "sweeps": sweeps, "deferred_fraction": (sum(st1.deferred) - sum(st0.deferred)) / max(att, 1),
+                     "error_flags": st1.error_flags}
+        sim.close()
+    out["speedup_mixed_over_fp64"] = out["mixed"]["bead_updates_per_s"] / out["fp64"]["bead_updates_per_s"]
+    return out
+
+
 def serve_leg(args, torch, tuner, policy):
     """Poisson arrivals through the continuous-batching loop (a bounded sample of the stream)."""
     from paper_1611_09160_gb300 import autotune as A
@@ -253,6 +286,20 @@ def serve_leg(args, torch, tuner, policy):
                "capacity": args.serve_capacity, "pool_mb": round(pool / 2**20, 1),
                "sample": f"{len(reqs)} requests of the ensemble shape (of 1,024 at 10^3 sweeps in the full stream)"})
     return sm
+
+
+def combine_ranks(maxed, summed, world, device):
+    """Whole-job figures of independent replicas: the slowest rank's times (max) and the
+    units of all ranks (sum). No collective is used for a single rank."""
+    if world <= 1:
+        return list(maxed), list(summed)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(maxed), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor(list(summed), dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], [float(x) for x in u]
 
 
 def timed_steps(sim, steps, flush, stream, torch):
@@ -312,15 +359,9 @@ def run_gpu(args, rank, world, local_rank):
     bu = st1.bead_updates - st0.bead_updates
     simt = st1.sim_time - st0.sim_time
     launches = st1.kernel_launches - st0.kernel_launches
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([float(bu), simt, float(launches)], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_ms_all, bu_all, simt_all, launches_all = float(t[0]), float(u[0]), float(u[1]), int(u[2])
-    else:
-        total_ms_all, bu_all, simt_all, launches_all = total_ms, float(bu), simt, launches
+    (total_ms_all,), (bu_all, simt_all, launches_all) = combine_ranks([total_ms], [float(bu), simt, float(launches)],
+                                                                     world, dev)
+    launches_all = int(launches_all)
     value = bu_all / (total_ms_all * 1e-3)
 
     # plain FP64 GPU sweep on the same inputs (the comparison the method is quoted against)
@@ -391,6 +432,7 @@ def run_gpu(args, rank, world, local_rank):
     # the table shipped with the package are not measured again
     tuner = A.Tuner(path=None, warm=1, sweeps=2, copies=152, seed_table=A.DEFAULT_TABLE)
     ens = ensemble_leg(args, torch, stream, flush, tuner) if args.ensemble > 0 else None
+    semi = semidilute_leg(args, torch, stream, flush) if args.semidilute_sweeps > 0 else None
     srv = serve_leg(args, torch, tuner, ens["policy"] if ens else "serial_small") if args.serve_requests > 0 else None
 
     if rank != 0:
@@ -402,7 +444,7 @@ def run_gpu(args, rank, world, local_rank):
             "sim_time_per_s": simt_all / (total_ms_all * 1e-3),
             "fp64": {"value": fp64_value * world, "unit": UNIT, "speedup_mixed_over_fp64": value / (fp64_value * world)},
             "e2e": e2e, "gpu_launches": launches_all, "clocks": clocks, "roofline": roofline,
-            "plane_wave": pw, "batched": ens, "serve": srv,
+            "plane_wave": pw, "batched": ens, "serve": srv, "semidilute": semi,
             "stats": {"accept_fraction": (st1.accepted_total - st0.accepted_total) /
                                          max(1, sum(st1.attempts) - sum(st0.attempts) +
                                              st1.pw_attempts - st0.pw_attempts),
@@ -428,6 +470,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-capacity", type=int, default=512)
     ap.add_argument("--serve-chunk", type=int, default=10)
+    ap.add_argument("--semidilute-sweeps", type=int, default=3, help="timed sweeps of the 1M-bead leg (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

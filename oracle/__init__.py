@@ -84,6 +84,7 @@ def _load():
         "oracle_inv_cbrt": ([D, D], D),
         "oracle_lambda_a": ([], D),
         "oracle_layers": ([P, P, P, P, P, ctypes.c_int], ctypes.c_int),
+        "oracle_slot_counts": ([P, ctypes.c_uint64, P], ctypes.c_int),
         "oracle_sample_slots": ([P, ctypes.c_int, I64, P, P], I64),
         "oracle_sample_ball": ([P, U64, I64, P], I64),
         "oracle_sample_polarisation": ([P, U64, I64, P], I64),
@@ -184,6 +185,12 @@ class Oracle:
         lo, hi, mass, ex = (np.zeros(16) for _ in range(4))
         n = self._lib.oracle_layers(self.h, _ptr(lo), _ptr(hi), _ptr(mass), _ptr(ex), 16)
         return lo[:n], hi[:n], mass[:n], ex[:n]
+
+    def slot_counts(self, sweep: int):
+        """Slots of sweep `sweep`: per wavelet layer, and the plane-wave slots."""
+        out = np.zeros(17, dtype=np.int64)
+        n = self._lib.oracle_slot_counts(self.h, int(sweep), _ptr(out))
+        return out[:n].copy(), int(out[16])
 
     def sample_slots(self, layer: int, n: int):
         lam = np.zeros(n)

@@ -1044,6 +1044,14 @@ int oracle_layers(void* h, double* lo, double* hi, double* mass, double* expect,
     for (int l = 0; l < nL && l < cap; l++) { lo[l] = s.layers[l].lo; hi[l] = s.layers[l].hi; mass[l] = s.layers[l].mass; expect[l] = s.layers[l].expect; }
     return nL;
 }
+// slot counts of sweep `sw`: out[l] for the wavelet layers, out[16] for the plane waves
+int oracle_slot_counts(void* h, uint64_t sw, int64_t* out) {
+    Sim& s = *(Sim*)h;
+    int nL = (int)s.layers.size();
+    for (int l = 0; l < 16; l++) out[l] = l < nL ? slot_count(s, K_COUNT, l, sw, s.layers[l].expect) : 0;
+    out[16] = s.P.planewave_mode == 1 ? slot_count(s, K_PWCOUNT, 0, sw, (double)s.N * s.p_fourier) : 0;
+    return nL;
+}
 // scales and beads of slots 0..n-1 of layer l in the current sweep
 int64_t oracle_sample_slots(void* h, int l, int64_t n, double* lam, int64_t* bead) {
     Sim& s = *(Sim*)h;

@@ -117,13 +117,14 @@ class Tuner:
                 json.dump(self.table, f, indent=1, sort_keys=True)
             os.replace(tmp, self.path)
 
-    def schedule(self, base: dict, system=None, chain_lengths=None) -> dict:
-        """Parameters ``base`` with the tuned schedule of its shape (measured on first use)."""
+    def schedule(self, base: dict, system=None, chain_lengths=None, candidates=None) -> dict:
+        """Parameters ``base`` with the tuned schedule of its shape (measured on first use, over
+        ``candidates`` if given, e.g. a short list for systems too large to time many ways)."""
         key = shape_key(base["n_beads"], base["box_L"], base.get("precision", 0), base.get("planewave_mode", 0))
         if self.copies > 1:
             key += f"_x{self.copies}"
         if key not in self.table:
-            self.table[key] = self._tune_schedule(base, system, chain_lengths)
+            self.table[key] = self._tune_schedule(base, system, chain_lengths, candidates)
             self.save()
         return self.apply(base, self.table[key]["choice"])
 
@@ -134,12 +135,14 @@ class Tuner:
                           **choice))
         return p
 
-    def _tune_schedule(self, base: dict, system, chain_lengths) -> dict:
+    def _tune_schedule(self, base: dict, system, chain_lengths, candidates=None) -> dict:
         if system is None:
             lens = chain_lengths if chain_lengths is not None else [base["n_beads"]]
             system = I.make_system(list(lens), 0, base["box_L"], seed=12345)
         scores = []
-        for cand in (BATCH_SCHEDULE_CANDIDATES if self.copies > 1 else SCHEDULE_CANDIDATES):
+        if candidates is None:
+            candidates = BATCH_SCHEDULE_CANDIDATES if self.copies > 1 else SCHEDULE_CANDIDATES
+        for cand in candidates:
             try:
                 p = self.apply(base, cand)
             except ValueError:
