@@ -156,9 +156,9 @@ int64_t slot_count(const Handle* h, uint32_t kind, int l, uint64_t ctr, double x
     return (int64_t)f + ((u < x - f) ? 1 : 0);
 }
 
-__global__ void k_fill_beads(Bead* bead, const double* pos, int64_t N) {
+__global__ void k_fill_beads(Bead* bead, BeadF* bf, const double* pos, int64_t N) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        bead[i].x = pos[3 * i]; bead[i].y = pos[3 * i + 1]; bead[i].z = pos[3 * i + 2];
+        put_bead(bead, bf, i, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
         bead[i].mark = 0u;
     }
 }
@@ -309,7 +309,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     int pw_cap = (int)std::min<double>(1e6, 4.0 * h->p_fourier * (double)N + 64.0);
     v.pw_blocks = (int)((N + 255) / 256);
     bool ok = true;
-    ok = ok && !dalloc(h, &v.bead, N) && !dalloc(h, &v.prev, N) && !dalloc(h, &v.img, 3 * N) &&
+    ok = ok && !dalloc(h, &v.bead, N) && !dalloc(h, &v.bf, N) && !dalloc(h, &v.prev, N) && !dalloc(h, &v.img, 3 * N) &&
          !dalloc(h, &v.bnext, N) && !dalloc(h, &v.head, ncell);
     ok = ok && !dalloc(h, &v.slot_V, 3 * Mall) && !dalloc(h, &v.slot_p, 3 * Mall) && !dalloc(h, &v.slot_thr, Mall);
     ok = ok && !dalloc(h, &v.slot_lam, Mall) && !dalloc(h, &v.slot_bead, Mall) && !dalloc(h, &v.slot_key, Mall) &&
@@ -446,7 +446,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     cudaMemsetAsync(v.pw, 0, sizeof(PWDev), s);
     cudaMemsetAsync(v.tr_out, 0, std::max<int64_t>(tr_total, 1), s);
     cudaMemsetAsync(v.tr_n, 0, std::max<int64_t>(tr_total, 1) * sizeof(int), s);
-    k_fill_beads<<<grid_for(N), 256, 0, s>>>(v.bead, h->staging, N);
+    k_fill_beads<<<grid_for(N), 256, 0, s>>>(v.bead, v.bf, h->staging, N);
     launch_cl_rebuild(h->dview, h->g, s, 0);
     if (cudaStreamSynchronize(s) != cudaSuccess || last_cuda_status()) { cudaGetLastError(); return WMCD_ECUDA; }
     int err = 0;
@@ -578,7 +578,7 @@ extern "C" int wmcd_set_positions(wmcd_handle* H, const double* pos, void* strea
     cudaMemcpyAsync(h->staging, pos, 3 * h->N * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (!dev && cudaStreamSynchronize(s) != cudaSuccess) return WMCD_ECUDA;
     cudaMemsetAsync(h->v.img, 0, 3 * h->N * sizeof(int), s);
-    k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->staging, h->N);
+    k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->v.bf, h->staging, h->N);
     launch_cl_rebuild(h->dview, h->g, s, 0);
     return last_cuda_status();
 }
@@ -731,7 +731,7 @@ extern "C" int wmcd_set_state(wmcd_handle* H, const void* buf, int64_t bytes, vo
     cudaMemcpyAsync(h->v.ctr, p, C_NCTR * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
     p += C_NCTR * sizeof(unsigned long long);
     cudaMemcpyAsync(h->v.serial_tag, p, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-    k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->staging, h->N);
+    k_fill_beads<<<grid_for(h->N), 256, 0, s>>>(h->v.bead, h->v.bf, h->staging, h->N);
     launch_cl_rebuild(h->dview, h->g, s, 0);
     cudaMemsetAsync(h->v.err, 0, sizeof(int), s);
     h->sweep = hd.sweep;

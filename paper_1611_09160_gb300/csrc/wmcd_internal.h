@@ -15,6 +15,27 @@ struct __align__(32) Bead {
 };
 static_assert(sizeof(Bead) == 32, "bead record must be 32 bytes");
 
+// binary32 shadow of a bead's position: hi = the binary64 coordinate rounded, lo = the rounded
+// remainder, so hi + lo carries it to ~48 bits. Differences of nearby beads formed from the
+// pairs carry about one binary32 ulp, with no binary64 arithmetic (slow on this part). Written
+// with every position; read by the binary32 screens and energies.
+struct __align__(32) BeadF {
+    float hx, hy, hz, lx, ly, lz, pad0, pad1;
+};
+static_assert(sizeof(BeadF) == 32, "shadow record must be 32 bytes");
+
+// write a bead's binary64 position and its binary32 shadow (if the view has one)
+__device__ __forceinline__ void put_bead(Bead* bead, BeadF* bf, int64_t m, double x, double y, double z) {
+    bead[m].x = x; bead[m].y = y; bead[m].z = z;
+    if (bf) {
+        BeadF f;
+        f.hx = (float)x; f.hy = (float)y; f.hz = (float)z;
+        f.lx = (float)(x - (double)f.hx); f.ly = (float)(y - (double)f.hy); f.lz = (float)(z - (double)f.hz);
+        f.pad0 = 0.0f; f.pad1 = 0.0f;
+        bf[m] = f;
+    }
+}
+
 constexpr int kMaxLayers = 16;
 constexpr int kNCap = 64;          // largest support of a concurrent (warp) move
 constexpr int kWarpsPerBlock = 4;  // concurrent kernel: one warp per queue
@@ -70,6 +91,7 @@ struct PWDev {
 struct SimView {
     // beads and cell list
     Bead* bead;
+    BeadF* bf;                   // binary32 shadow of the positions (null: none)
     int* prev;
     int* img;                    // 3 per bead
     uint8_t* bnext;              // bead i bonded to i + 1

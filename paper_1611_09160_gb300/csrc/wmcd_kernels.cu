@@ -591,11 +591,11 @@ __device__ void energy(const SimView& v, WarpSmem& sm, int n, int lane, int ncol
         for (int o = 16; o > 0; o >>= 1) {
             s += __shfl_xor_sync(FULL, s, o);
             mm += __shfl_xor_sync(FULL, mm, o);
-            tt += __shfl_xor_sync(FULL, tt, o);
+            tt = max(tt, __shfl_xor_sync(FULL, tt, o));
         }
         *dU32 = __shfl_sync(FULL, s, 0);
         *mag32 = __shfl_sync(FULL, mm, 0);
-        *terms = __shfl_sync(FULL, tt, 0);
+        *terms = __shfl_sync(FULL, tt, 0) + 5;   // summation depth: one lane's terms, then the butterfly
     } else {
         *dU64 = __shfl_sync(FULL, warp_sum(a64), 0);
     }
@@ -727,7 +727,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
         float d32 = 0.0f, m32 = 0.0f;
         int T = 0;
         energy<true>(v, sm, n, lane, ncols, nzmax, nullptr, &d32, &m32, &T, &pe);
-        const double band = 2.0 * (double)(64 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
+        const double band = 2.0 * (double)(80 + T + 6) * 5.9604644775390625e-08 * (double)m32 + 1e-9 * v.kT;
         if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
             acc = (double)d32 <= thr;
             *du_out = (double)d32;
@@ -750,7 +750,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     // commit: positions, image counters, then cell-list moves (lane 0, in support order)
     for (int k = lane; k < n; k += 32) {
         const int m = sm.ids[k];
-        v.bead[m].x = sm.np[k][0]; v.bead[m].y = sm.np[k][1]; v.bead[m].z = sm.np[k][2];
+        put_bead(v.bead, v.bf, m, sm.np[k][0], sm.np[k][1], sm.np[k][2]);
         if (sm.dimg[k] != pack_img(0, 0, 0)) {
             int dd[3];
             unpack_img(sm.dimg[k], dd);
@@ -830,7 +830,9 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
     const int use_list = v.layer[l].G > 0;
     __shared__ double sh_b[3], sh_p[3], sh_carry;
     __shared__ double sh_red[NT / 32];
-    __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total;
+    __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total, sh_need64;
+    __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
+    __shared__ int sh_T[NT / 32];
     __shared__ int sh_scan[NT];
     __shared__ uint32_t sh_tag;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -840,7 +842,8 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
     const int count = use_list ? *v.serial_count : M;
     if (tid == 0) sh_carry = v.carry_serial[l];
     __syncthreads();
-    long long att = 0, acc_n = 0, bu = 0, pe = 0;
+    long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
+    const float hLf = (float)hL, Lf = (float)L;
     for (int t = 0; t < count; t++) {
         const int j = use_list ? v.serial_list[t] : t;
         const double lam = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
@@ -873,7 +876,18 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         __syncthreads();
         const double b[3] = {sh_b[0], sh_b[1], sh_b[2]};
         // gather the support
+        // binary32 screen on the shadow (margin 8 L 2^-24 + 1e-6 on the distance covers the rounding
+        // of the shadow, of b and of the difference), then the binary64 test
+        const float bxf = (float)b[0], byf = (float)b[1], bzf = (float)b[2];
+        const float rlf = (float)lam + (float)(8.0 * L * 5.9604644775390625e-8 + 1e-6);
+        const float rl2f = rlf * rlf * (1.0f + 9.5367431640625e-7f);
+        auto wrapg = [&](float f) { return fabsf(f) > hLf ? f - copysignf(Lf, f) : f; };
         auto consider = [&](int m, const Bead& bb) {
+            {
+                const BeadF f = v.bf[m];
+                const float sx = wrapg(f.hx - bxf), sy = wrapg(f.hy - byf), sz = wrapg(f.hz - bzf);
+                if (sx * sx + sy * sy + sz * sz > rl2f) return;
+            }
             double d0 = mi(sub(bb.x, b[0]), L, hL), d1 = mi(sub(bb.y, b[1]), L, hL), d2c = mi(sub(bb.z, b[2]), L, hL);
             double d2 = norm2(d0, d1, d2c);
             if (d2 < lam2) {
@@ -932,32 +946,35 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         }
         __syncthreads();
         // energy change: bonds and the external well per member; pair terms by one thread per
-        // (member, fine cell of its partner box), so a small support still spreads its list
-        // walks over the block
-        double dU = 0.0;
+        // (member, fine cell of its partner box) item, so a small support still spreads its list
+        // walks over the block. Mixed precision: a binary32 pass first (each difference of
+        // binary64 positions rounded once, the new one formed from the old one and the binary32
+        // displacements), deciding outside the rigorous error band; the binary64 pass decides
+        // inside it and in binary64 mode.
         const double ext = add(v.rc, mul(0.25, Aw)) + 1e-9;
+        const double thr = v.slot_thr[j];
+        // old-position difference a - b, minimum image, rounded once to binary32
+        auto d32 = [&](double a, double b) {
+            const double e = sub(a, b);
+            float f = (float)e;
+            if (fabsf(f) > hLf) f = (float)(e > 0.0 ? sub(e, L) : add(e, L));
+            return f;
+        };
+        auto wrapf = [&](float f) { return fabsf(f) > hLf ? f - copysignf(Lf, f) : f; };
+        // the same difference from the binary32 shadows (hi, lo): no binary64 arithmetic unless
+        // the pair straddles a face, where it is wrapped in binary64
+        auto dsh = [&](float ha, float la, float hb, float lb, double a, double b) {
+            const float dh = ha - hb;
+            if (fabsf(dh) <= hLf) return dh + (la - lb);
+            return d32(a, b);
+        };
+        // partner boxes and their exclusive prefix (items), shared by both passes
         for (int k = tid; k < n; k += NT) {
-            const int m = v.s_ids[k];
-            const Bead bm = v.bead[m];
-            const double o[3] = {bm.x, bm.y, bm.z};
-            const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
-            dU += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, o[0], o[1], o[2]);
-            for (int e = 0; e < 2; e++) {
-                int q = e ? m + 1 : m - 1;
-                if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q])) continue;
-                Bead bq = v.bead[q];
-                double qn[3] = {bq.x, bq.y, bq.z};
-                if (bq.mark == tag) {
-                    if (q < m) continue;
-                    int s = v.s_slot[q];
-                    qn[0] = v.s_new[3 * s]; qn[1] = v.s_new[3 * s + 1]; qn[2] = v.s_new[3 * s + 2];
-                }
-                double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
-                double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
-                dU += U_bond(P, r2n) - U_bond(P, r2o);
-            }
             int cnt = 0;
             if (P.eps != 0.0) {
+                const int m = v.s_ids[k];
+                const Bead bm = v.bead[m];
+                const double o[3] = {bm.x, bm.y, bm.z};
                 double lo[3], hi[3];
                 for (int a = 0; a < 3; a++) {
                     double u = add(o[a], v.s_d[4 * k + a]);
@@ -972,6 +989,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
             v.s_pre[k] = cnt;
         }
         __syncthreads();
+        int W = 0;
         if (P.eps != 0.0) {
             // exclusive prefix of the box sizes, NT members per pass
             for (int base = 0; base < n; base += NT) {
@@ -990,55 +1008,226 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
                 if (tid == NT - 1) sh_total += sh_scan[NT - 1];
                 __syncthreads();
             }
-            const int W = sh_total;
+            W = sh_total;
             if (tid == 0) v.s_pre[n] = W;
             __syncthreads();
-            for (int t = tid; t < W; t += NT) {
-                int lo_k = 0, hi_k = n - 1;                 // last member with s_pre <= t
-                while (lo_k < hi_k) {
-                    const int mid = (lo_k + hi_k + 1) >> 1;
-                    if (v.s_pre[mid] <= t) lo_k = mid; else hi_k = mid - 1;
+        }
+        // every (member, bead) pair of the partner boxes: each thread takes a contiguous run of
+        // items, with one search for its first member, member data reloaded only when the run
+        // crosses to the next member, and the head of the next item's cell loaded before the
+        // current cell is walked. visit(k, m, q, bead q)
+        auto for_pairs = [&](auto&& visit) {
+            const int t0 = (int)((int64_t)tid * W / NT), t1 = (int)((int64_t)(tid + 1) * W / NT);
+            if (t0 >= t1) return;
+            int lo_k = 0, hi_k = n - 1;                 // last member with s_pre <= t0
+            while (lo_k < hi_k) {
+                const int mid = (lo_k + hi_k + 1) >> 1;
+                if (v.s_pre[mid] <= t0) lo_k = mid; else hi_k = mid - 1;
+            }
+            int kn = lo_k, kn_start = v.s_pre[kn], kn_end = v.s_pre[kn + 1];
+            int c0n[3] = {v.s_box[6 * kn], v.s_box[6 * kn + 1], v.s_box[6 * kn + 2]};
+            int ncn[3] = {v.s_box[6 * kn + 3], v.s_box[6 * kn + 4], v.s_box[6 * kn + 5]};
+            auto next_cell = [&](int t) {
+                while (t >= kn_end) {
+                    kn++;
+                    kn_start = kn_end;
+                    kn_end = v.s_pre[kn + 1];
+                    for (int a = 0; a < 3; a++) { c0n[a] = v.s_box[6 * kn + a]; ncn[a] = v.s_box[6 * kn + 3 + a]; }
                 }
-                const int k = lo_k;
-                const int c0[3] = {v.s_box[6 * k], v.s_box[6 * k + 1], v.s_box[6 * k + 2]};
-                const int nc[3] = {v.s_box[6 * k + 3], v.s_box[6 * k + 4], v.s_box[6 * k + 5]};
-                const int cell = box_cell(v, c0, nc, t - v.s_pre[k]);
+                return box_cell(v, c0n, ncn, t - kn_start);
+            };
+            int h = v.head[next_cell(t0)];
+            int cur_k = kn;
+            for (int t = t0; t < t1; t++) {
+                int hn = -1, nk = cur_k;
+                if (t + 1 < t1) { hn = v.head[next_cell(t + 1)]; nk = kn; }
+                const int m = v.s_ids[cur_k];
+                int guard = 0;
+                for (int q = h; q >= 0;) {
+                    const Bead bq = v.bead[q];
+                    const int nx = bq.next;
+                    if (q != m) visit(cur_k, m, q, bq);
+                    q = nx;
+                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                }
+                h = hn;
+                cur_k = nk;
+            }
+        };
+        bool need64 = PREC == 0;
+        if (PREC == 1) {
+            const Pot32 P32 = pot32(P);
+            float a32 = 0.0f, m32 = 0.0f;
+            int T = 0;
+            for (int k = tid; k < n; k += NT) {
+                const int m = v.s_ids[k];
+                const Bead bm = v.bead[m];
+                const double o[3] = {bm.x, bm.y, bm.z};
+                const float dlm[3] = {(float)v.s_d[4 * k], (float)v.s_d[4 * k + 1], (float)v.s_d[4 * k + 2]};
+                const BeadF fm = v.bf[m];
+                const float mh[3] = {fm.hx, fm.hy, fm.hz}, ml[3] = {fm.lx, fm.ly, fm.lz};
+                if (P.kappa != 0.0) {
+                    float ro = 0.0f, rn = 0.0f;
+                    for (int a = 0; a < 3; a++) {
+                        const float c = d32(o[a], hL);
+                        ro += c * c;
+                        const float cn = wrapf(c + dlm[a]);
+                        rn += cn * cn;
+                    }
+                    const float un = 0.5f * P32.kappa * rn, uo = 0.5f * P32.kappa * ro;
+                    a32 += un - uo; m32 += un + uo; T += 2;
+                }
+                for (int e = 0; e < 2; e++) {
+                    const int q = e ? m + 1 : m - 1;
+                    if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q])) continue;
+                    const Bead bq = v.bead[q];
+                    float dlq[3] = {0.0f, 0.0f, 0.0f};
+                    if (bq.mark == tag) {
+                        if (q < m) continue;
+                        const int sq = v.s_slot[q];
+                        for (int a = 0; a < 3; a++) dlq[a] = (float)v.s_d[4 * sq + a];
+                    }
+                    const double qo[3] = {bq.x, bq.y, bq.z};
+                    const BeadF fq = v.bf[q];
+                    const float qh[3] = {fq.hx, fq.hy, fq.hz}, ql[3] = {fq.lx, fq.ly, fq.lz};
+                    float ro = 0.0f, rn = 0.0f;
+                    for (int a = 0; a < 3; a++) {
+                        const float c = dsh(mh[a], ml[a], qh[a], ql[a], o[a], qo[a]);
+                        ro += c * c;
+                        const float cn = wrapf(c + dlm[a] - dlq[a]);
+                        rn += cn * cn;
+                    }
+                    float un, mn, uo, mo;
+                    bond32(P32, rn, un, mn);
+                    bond32(P32, ro, uo, mo);
+                    a32 += un - uo; m32 += mn + mo; T += 2;
+                }
+            }
+            if (P.eps != 0.0) {
+                int mk = -1;
+                double o[3] = {0.0, 0.0, 0.0};
+                float dlm[3] = {0.0f, 0.0f, 0.0f}, mh[3] = {0.0f, 0.0f, 0.0f}, ml[3] = {0.0f, 0.0f, 0.0f};
+                for_pairs([&](int k, int m, int q, const Bead& bq) {
+                    const bool member = bq.mark == tag;
+                    if (member && q < m) return;
+                    if (k != mk) {
+                        mk = k;
+                        const Bead bm = v.bead[m];
+                        o[0] = bm.x; o[1] = bm.y; o[2] = bm.z;
+                        const BeadF fm = v.bf[m];
+                        mh[0] = fm.hx; mh[1] = fm.hy; mh[2] = fm.hz; ml[0] = fm.lx; ml[1] = fm.ly; ml[2] = fm.lz;
+                        for (int a = 0; a < 3; a++) dlm[a] = (float)v.s_d[4 * k + a];
+                    }
+                    float dlq[3] = {0.0f, 0.0f, 0.0f};
+                    if (member) {
+                        const int sq = v.s_slot[q];
+                        for (int a = 0; a < 3; a++) dlq[a] = (float)v.s_d[4 * sq + a];
+                    }
+                    const double qo[3] = {bq.x, bq.y, bq.z};
+                    const BeadF fq = v.bf[q];
+                    const float qh[3] = {fq.hx, fq.hy, fq.hz}, ql[3] = {fq.lx, fq.ly, fq.lz};
+                    float ro = 0.0f, rn = 0.0f;
+                    for (int a = 0; a < 3; a++) {
+                        const float c = dsh(mh[a], ml[a], qh[a], ql[a], o[a], qo[a]);
+                        ro += c * c;
+                        const float cn = wrapf(c + dlm[a] - dlq[a]);
+                        rn += cn * cn;
+                    }
+                    float un, mn, uo, mo;
+                    wca32(P32, rn, un, mn);
+                    wca32(P32, ro, uo, mo);
+                    if (un != 0.0f || uo != 0.0f || mn != 0.0f || mo != 0.0f) {
+                        a32 += un - uo; m32 += mn + mo; T += 2;
+                        if (!member) pe++;
+                    }
+                });
+            }
+            for (int sft = 16; sft > 0; sft >>= 1) {
+                a32 += __shfl_xor_sync(0xffffffffu, a32, sft);
+                m32 += __shfl_xor_sync(0xffffffffu, m32, sft);
+                T = max(T, __shfl_xor_sync(0xffffffffu, T, sft));
+            }
+            if (lane == 0) { sh_f32[wid] = a32; sh_m32[wid] = m32; sh_T[wid] = T; }
+            __syncthreads();
+            if (tid == 0) {
+                float du = 0.0f, mm = 0.0f;
+                int tt = 0;
+                for (int w = 0; w < NT / 32; w++) { du += sh_f32[w]; mm += sh_m32[w]; tt = max(tt, sh_T[w]); }
+                tt += 5 + NT / 32;     // summation depth: one thread's terms, the butterfly, the warp totals
+                const float thr32 = (float)thr;
+                const float band = 2.0f * (float)(80 + tt + 6) * 5.9604645e-08f * mm + 1e-9f * (float)v.kT +
+                                   2.4e-7f * fabsf(thr32);
+                if (isfinite(du) && isfinite(band) && fabsf(du - thr32) > band) {
+                    sh_acc = du <= thr32;
+                    sh_need64 = 0;
+                    v.tr_du[Ly.tr_off + j] = (double)du;
+                } else {
+                    sh_need64 = 1;
+                    rechecks++;
+                }
+            }
+            __syncthreads();
+            need64 = sh_need64;
+        }
+        if (need64) {
+            double dU = 0.0;
+            for (int k = tid; k < n; k += NT) {
                 const int m = v.s_ids[k];
                 const Bead bm = v.bead[m];
                 const double o[3] = {bm.x, bm.y, bm.z};
                 const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
-                int guard = 0;
-                for (int q = v.head[cell]; q >= 0;) {
+                dU += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, o[0], o[1], o[2]);
+                for (int e = 0; e < 2; e++) {
+                    int q = e ? m + 1 : m - 1;
+                    if (q < 0 || q >= v.N || !(e ? v.bnext[m] : v.bnext[q])) continue;
                     Bead bq = v.bead[q];
-                    int nx = bq.next;
-                    if (q != m) {
-                        double qn[3] = {bq.x, bq.y, bq.z};
-                        bool member = bq.mark == tag;
-                        if (!(member && q < m)) {
-                            if (member) {
-                                int s = v.s_slot[q];
-                                qn[0] = v.s_new[3 * s]; qn[1] = v.s_new[3 * s + 1]; qn[2] = v.s_new[3 * s + 2];
-                            }
-                            double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
-                            double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
-                            if (r2n < P.rc2 || r2o < P.rc2) { dU += U_wca(P, r2n) - U_wca(P, r2o); if (!member) pe++; }
-                        }
+                    double qn[3] = {bq.x, bq.y, bq.z};
+                    if (bq.mark == tag) {
+                        if (q < m) continue;
+                        int sq = v.s_slot[q];
+                        qn[0] = v.s_new[3 * sq]; qn[1] = v.s_new[3 * sq + 1]; qn[2] = v.s_new[3 * sq + 2];
                     }
-                    q = nx;
-                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                    double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                    double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                    dU += U_bond(P, r2n) - U_bond(P, r2o);
                 }
             }
+            if (P.eps != 0.0) {
+                int mk = -1;
+                double o[3] = {0.0, 0.0, 0.0}, nw[3] = {0.0, 0.0, 0.0};
+                for_pairs([&](int k, int m, int q, const Bead& bq) {
+                    const bool member = bq.mark == tag;
+                    if (member && q < m) return;
+                    if (k != mk) {
+                        mk = k;
+                        const Bead bm = v.bead[m];
+                        o[0] = bm.x; o[1] = bm.y; o[2] = bm.z;
+                        nw[0] = v.s_new[3 * k]; nw[1] = v.s_new[3 * k + 1]; nw[2] = v.s_new[3 * k + 2];
+                    }
+                    double qn[3] = {bq.x, bq.y, bq.z};
+                    if (member) {
+                        const int sq = v.s_slot[q];
+                        qn[0] = v.s_new[3 * sq]; qn[1] = v.s_new[3 * sq + 1]; qn[2] = v.s_new[3 * sq + 2];
+                    }
+                    const double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                    const double r2o = norm2(mi(o[0] - bq.x, L, hL), mi(o[1] - bq.y, L, hL), mi(o[2] - bq.z, L, hL));
+                    if (r2n < P.rc2 || r2o < P.rc2) {
+                        dU += U_wca(P, r2n) - U_wca(P, r2o);
+                        if (!member && PREC == 0) pe++;
+                    }
+                });
+            }
+            dU = warp_sum(dU);
+            if (lane == 0) sh_red[wid] = dU;
+            __syncthreads();
+            if (tid == 0) {
+                double su = 0.0;
+                for (int w = 0; w < NT / 32; w++) su += sh_red[w];
+                sh_acc = su <= thr;
+                v.tr_du[Ly.tr_off + j] = su;
+            }
+            __syncthreads();
         }
-        dU = warp_sum(dU);
-        if (lane == 0) sh_red[wid] = dU;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < NT / 32; w++) s += sh_red[w];
-            sh_acc = s <= v.slot_thr[j];
-            v.tr_du[Ly.tr_off + j] = s;
-        }
-        __syncthreads();
         const bool acc = sh_acc;
         if (acc) {
             for (int k = tid; k < n; k += NT) {
@@ -1047,7 +1236,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
                 const int oc = cell_lin(v, bm.x, bm.y, bm.z);
                 const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
                 const int ncl = cell_lin(v, nw[0], nw[1], nw[2]);
-                v.bead[m].x = nw[0]; v.bead[m].y = nw[1]; v.bead[m].z = nw[2];
+                put_bead(v.bead, v.bf, m, nw[0], nw[1], nw[2]);
                 if (v.s_img[k] != pack_img(0, 0, 0)) {
                     int dd[3];
                     unpack_img(v.s_img[k], dd);
@@ -1090,6 +1279,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc_n);
         atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc_n);
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+        if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
     }
 }
 // Serial phase of a small simulation whose layers are all serial: the whole simulation is
@@ -1325,14 +1515,15 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             for (int o = 16; o > 0; o >>= 1) {
                 a32 += __shfl_xor_sync(0xffffffffu, a32, o);
                 m32 += __shfl_xor_sync(0xffffffffu, m32, o);
-                T += __shfl_xor_sync(0xffffffffu, T, o);
+                T = max(T, __shfl_xor_sync(0xffffffffu, T, o));
             }
             if (lane == 0) { sh_f32[wid] = a32; sh_m32[wid] = m32; sh_T[wid] = T; }
             __syncthreads();
             if (tid == 0) {
                 float d32 = 0.0f, mm = 0.0f;
                 int tt = 0;
-                for (int w = 0; w < NT / 32; w++) { d32 += sh_f32[w]; mm += sh_m32[w]; tt += sh_T[w]; }
+                for (int w = 0; w < NT / 32; w++) { d32 += sh_f32[w]; mm += sh_m32[w]; tt = max(tt, sh_T[w]); }
+                tt += 5 + NT / 32;     // summation depth: one thread's terms, the butterfly, the warp totals
                 const float thr32 = (float)thr;
                 const float band = 2.0f * (float)(80 + tt + 6) * 5.9604645e-08f * mm + 1e-9f * (float)v.kT +
                                    2.4e-7f * fabsf(thr32);
@@ -1445,7 +1636,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     for (int m = tid; m < N; m += NT) {
         const Bead ob = v.bead[m];
         if (ob.x == px[m] && ob.y == py[m] && ob.z == pz[m]) continue;
-        v.bead[m].x = px[m]; v.bead[m].y = py[m]; v.bead[m].z = pz[m];
+        put_bead(v.bead, v.bf, m, px[m], py[m], pz[m]);
         if (dimg[3 * m] | dimg[3 * m + 1] | dimg[3 * m + 2]) {
             v.img[3 * m] += dimg[3 * m]; v.img[3 * m + 1] += dimg[3 * m + 1]; v.img[3 * m + 2] += dimg[3 * m + 2];
         }
@@ -1728,7 +1919,7 @@ __global__ void k_pw_commit(const SimView* __restrict__ vs) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *v.pw_rebuild = moved;
     if (!moved) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
-        v.bead[i].x = v.pw_new[3 * i]; v.bead[i].y = v.pw_new[3 * i + 1]; v.bead[i].z = v.pw_new[3 * i + 2];
+        put_bead(v.bead, v.bf, i, v.pw_new[3 * i], v.pw_new[3 * i + 1], v.pw_new[3 * i + 2]);
         const int pk = v.pw_imgd[i];
         if (pk != pack_img(0, 0, 0)) {
             int dd[3];
@@ -1957,7 +2148,7 @@ __global__ void k_big_commit(const SimView* __restrict__ vs, int l) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *v.pw_rebuild = 1;   // the cell lists are rebuilt next
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int m = v.s_ids[k];
-        v.bead[m].x = v.s_new[3 * k]; v.bead[m].y = v.s_new[3 * k + 1]; v.bead[m].z = v.s_new[3 * k + 2];
+        put_bead(v.bead, v.bf, m, v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]);
         const int pk = v.s_img[k];
         if (pk != pack_img(0, 0, 0)) {
             int dd[3];
@@ -2192,11 +2383,11 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
         for (int o = 16; o > 0; o >>= 1) {
             s += __shfl_xor_sync(FULL, s, o);
             mm += __shfl_xor_sync(FULL, mm, o);
-            tt += __shfl_xor_sync(FULL, tt, o);
+            tt = max(tt, __shfl_xor_sync(FULL, tt, o));
         }
         *dU32 = __shfl_sync(FULL, s, 0);
         *mag32 = __shfl_sync(FULL, mm, 0);
-        *terms = __shfl_sync(FULL, tt, 0);
+        *terms = __shfl_sync(FULL, tt, 0) + 5;   // summation depth: one lane's terms, then the butterfly
     } else {
         *dU64 = __shfl_sync(FULL, warp_sum(a64), 0);
     }
@@ -2484,7 +2675,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
             if (t < ns && (S.sdim[t] & (1 << 24))) {
                 const int dm = S.sdim[t];
                 const int m = S.sid[t];
-                v.bead[m].x = S.sx[t]; v.bead[m].y = S.sy[t]; v.bead[m].z = S.sz[t];
+                put_bead(v.bead, v.bf, m, S.sx[t], S.sy[t], S.sz[t]);
                 const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
                 if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
                 const int nc2 = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
