@@ -185,17 +185,42 @@ WMCD_HD float cos2pi_f(double t) {
 }
 
 // ---- periodic box ----
+// On the device the comparisons below are taken on the bit patterns: for IEEE doubles and a
+// positive bound, the order of the patterns as signed integers is the order of the values for
+// every input but a NaN, so the results are those of the binary64 comparisons, without using
+// the binary64 pipe (slow on this part) for them.
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ bool ge_pos(double x, double b) {      // x >= b, b > 0 finite
+    return __double_as_longlong(x) >= __double_as_longlong(b);
+}
+__device__ __forceinline__ bool lt_zero(double x) {               // x < 0
+    const long long xb = __double_as_longlong(x);
+    return xb < 0 && (xb & 0x7fffffffffffffffLL) != 0;
+}
+__device__ __forceinline__ bool gt_pos(double x, double b) {      // x > b, b > 0 finite
+    return __double_as_longlong(x) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool lt_neg(double x, double b) {      // x < -b, b > 0 finite
+    const long long xb = __double_as_longlong(x);
+    return xb < 0 && (xb & 0x7fffffffffffffffLL) > __double_as_longlong(b);
+}
+#else
+inline bool ge_pos(double x, double b) { return x >= b; }
+inline bool lt_zero(double x) { return x < 0.0; }
+inline bool gt_pos(double x, double b) { return x > b; }
+inline bool lt_neg(double x, double b) { return x < -b; }
+#endif
 // wrap into [0, L); image counter change returned through *im (may be null)
 WMCD_HD double wrap(double x, double L, int* im) {
-    if (x >= L) { x = sub(x, L); if (im) *im += 1; }
-    else if (x < 0.0) { x = add(x, L); if (im) *im -= 1; }
-    if (x >= L) x = 0.0;
+    if (ge_pos(x, L)) { x = sub(x, L); if (im) *im += 1; }
+    else if (lt_zero(x)) { x = add(x, L); if (im) *im -= 1; }
+    if (ge_pos(x, L)) x = 0.0;
     return x;
 }
 // minimum image of a difference of two wrapped coordinates
 WMCD_HD double mi(double d, double L, double h) {
-    if (d > h) return sub(d, L);
-    if (d < -h) return add(d, L);
+    if (gt_pos(d, h)) return sub(d, L);
+    if (lt_neg(d, h)) return add(d, L);
     return d;
 }
 WMCD_HD double norm2(double x, double y, double z) { return add(add(mul(x, x), mul(y, y)), mul(z, z)); }
@@ -224,6 +249,18 @@ WMCD_HD void wavelet_disp64(const double d[3], double d2, double lam, double Aw,
     out[0] = mul(sc, cx); out[1] = mul(sc, cy); out[2] = mul(sc, cz);
 }
 // mixed precision: the same expression in binary32 on inputs rounded once
+// the same with lam, A_w and p already rounded to binary32 (once per move, not per member)
+WMCD_HD void wavelet_disp32f(const double d[3], float lf, float af, const float pf[3], double out[3]) {
+    float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
+    float d2f = addf(addf(mulf(dx, dx), mulf(dy, dy)), mulf(dz, dz));
+    float px = pf[0], py = pf[1], pz = pf[2];
+    float rho = dvdf(sqrtf_(d2f), lf);
+    float sc = dvdf(mulf(af, subf(1.0f, rho)), lf);
+    float cx = subf(mulf(py, dz), mulf(pz, dy));
+    float cy = subf(mulf(pz, dx), mulf(px, dz));
+    float cz = subf(mulf(px, dy), mulf(py, dx));
+    out[0] = (double)mulf(sc, cx); out[1] = (double)mulf(sc, cy); out[2] = (double)mulf(sc, cz);
+}
 WMCD_HD void wavelet_disp32(const double d[3], double lam, double Aw, const double p[3], double out[3]) {
     float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
     float d2f = addf(addf(mulf(dx, dx), mulf(dy, dy)), mulf(dz, dz));

@@ -2427,10 +2427,13 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
     const float lin = (lamf - eps) * (lamf - eps), lout = (lamf + eps) * (lamf + eps);
     const float Rf = (float)R + eps;
     const float rcand = Rf * Rf;
-    float bh[3], bl[3];
-    local_split(b[0], org[0], L, bh[0], bl[0]);
-    local_split(b[1], org[1], L, bh[1], bl[1]);
-    local_split(b[2], org[2], L, bh[2], bl[2]);
+    // the centre relative to the region origin for the binary32 screen, from the picked bead's
+    // staged local coordinates and lam V in binary32: its error (a few 1e-7 of the region side
+    // plus lam) is well inside the screen margin eps
+    float bh[3];
+    bh[0] = (S.hx[ti] + S.lx[ti]) + lamf * (float)S.cV[3 * c];
+    bh[1] = (S.hy[ti] + S.ly[ti]) + lamf * (float)S.cV[3 * c + 1];
+    bh[2] = (S.hz[ti] + S.lz[ti]) + lamf * (float)S.cV[3 * c + 2];
     int n = 0, nc = 0;
     for (int base = 0; base < ns; base += 32) {
         const int t = base + lane;
@@ -2460,6 +2463,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
     const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
+    const float af = (float)Aw, pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
         S.stag[t] = tag;
@@ -2467,12 +2471,20 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
         double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)};
         double dl[3];
         if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
-        else wavelet_disp32(d, lam, Aw, p, dl);
+        else wavelet_disp32f(d, lamf, af, pf, dl);
         int im[3] = {0, 0, 0};
+        const float oh[3] = {S.hx[t], S.hy[t], S.hz[t]}, ol[3] = {S.lx[t], S.ly[t], S.lz[t]};
         for (int a = 0; a < 3; a++) {
-            const double x = wrap(add(o[a], dl[a]), L, &im[a]);
-            S.mnp[3 * k + a] = x;
-            local_split(x, org[a], L, S.mnh[3 * k + a], S.mnl[3 * k + a]);
+            S.mnp[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+            // new local coordinate = old + displacement, in binary32 pairs (two-sum, then
+            // renormalised); local coordinates are continuous inside the region, no wrap
+            const float dlf = (float)dl[a];
+            const float s1 = oh[a] + dlf, bb = s1 - oh[a];
+            const float err = (oh[a] - (s1 - bb)) + (dlf - bb);
+            const float l1 = ol[a] + err;
+            const float h2 = s1 + l1;
+            S.mnh[3 * k + a] = h2;
+            S.mnl[3 * k + a] = l1 - (h2 - s1);
         }
         S.mimg[k] = pack_img(im[0], im[1], im[2]);
     }
