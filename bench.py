@@ -233,37 +233,56 @@ def ensemble_leg(args, torch, stream, flush, tuner):
     return out
 
 
-def semidilute_leg(args, torch, stream, flush):
-    """C3: homogeneous semi-dilute solution, 4,096 chains x 256 beads (1,048,576) at volume
-    fraction 0.05, wavelets + plane waves; schedule autotuned over two colour strides; mixed
-    precision against plain FP64 on the same inputs."""
+def large_leg(args, torch, stream, flush, system, workload, candidates, sweeps):
+    """One large system, schedule autotuned over a few candidates (table shipped with the
+    package, measured when a shape is missing); mixed precision against plain FP64 on the same
+    inputs. Inputs are larger than L2 and L2 is flushed between timed sweeps anyway."""
     from paper_1611_09160_gb300 import autotune as A
-    from paper_1611_09160_gb300 import inputs as I
     from paper_1611_09160_gb300 import wmcd
-    s = I.semidilute_chains(4096, 256, 0.05, seed=1)
+    s = system
     tuner = A.Tuner(path=None, warm=1, sweeps=1, seed_table=A.DEFAULT_TABLE)
     t0 = time.perf_counter()
     base = wmcd.default_params(s.n_beads, s.box_L, seed=1, precision=wmcd.MIXED,
                                planewave_mode=wmcd.PLANEWAVE_PERIODIC)
-    p = tuner.schedule(base, system=s, candidates=({"colour_K": 3}, {"colour_K": 2}))
-    out = {"workload": "semi-dilute chains 4096x256 beads (1,048,576) phi=0.05 L=444.5, wavelet+plane-wave lcut 8",
-           "schedule": {"colour_K": p["colour_K"], "grid_f": p["grid_f"], "grid_layer": p["grid_layer"][:8]},
-           "tune_s": round(time.perf_counter() - t0, 1)}
-    for name, prec, sweeps in (("mixed", wmcd.MIXED, args.semidilute_sweeps), ("fp64", wmcd.FP64, 1)):
+    p = tuner.schedule(base, system=s, candidates=candidates)
+    key = A.shape_key(s.n_beads, s.box_L, wmcd.MIXED, wmcd.PLANEWAVE_PERIODIC)
+    out = {"workload": workload, "n_beads": s.n_beads,
+           "schedule": {"colour_K": p["colour_K"], "grid_f": p["grid_f"], "grid_layer": p["grid_layer"][:10]},
+           "tuning": {key: tuner.table[key]}, "tune_s": round(time.perf_counter() - t0, 1)}
+    for name, prec, n in (("mixed", wmcd.MIXED, sweeps), ("fp64", wmcd.FP64, 1)):
         sim = wmcd.Simulation(dict(p, precision=prec), s.pos, s.chain_len, stream=stream)
         sim.sweep(1, stream=stream)
         st0 = sim.stats(stream=stream)
-        ms = timed_steps(sim, sweeps, flush, stream, torch)
+        ms = timed_steps(sim, n, flush, stream, torch)
         st1 = sim.stats(stream=stream)
         tot = float(np.sum(ms))
         att = sum(st1.attempts) - sum(st0.attempts)
         out[name] = {"bead_updates_per_s": (st1.bead_updates - st0.bead_updates) / (tot * 1e-3),
-                     "sim_time_per_s": (st1.sim_time - st0.sim_time) / (tot * 1e-3), "ms_per_sweep": tot / sweeps,
-                     "sweeps": sweeps, "deferred_fraction": (sum(st1.deferred) - sum(st0.deferred)) / max(att, 1),
-                     "error_flags": st1.error_flags}
+                     "sim_time_per_s": (st1.sim_time - st0.sim_time) / (tot * 1e-3), "ms_per_sweep": tot / n,
+                     "sweeps": n, "deferred_fraction": (sum(st1.deferred) - sum(st0.deferred)) / max(att, 1),
+                     "device_mb": sim.device_bytes() // 2**20, "error_flags": st1.error_flags}
         sim.close()
     out["speedup_mixed_over_fp64"] = out["mixed"]["bead_updates_per_s"] / out["fp64"]["bead_updates_per_s"]
     return out
+
+
+def semidilute_leg(args, torch, stream, flush):
+    """C3: homogeneous semi-dilute solution, 4,096 chains x 256 beads (1,048,576) at volume
+    fraction 0.05, wavelets + plane waves."""
+    from paper_1611_09160_gb300 import inputs as I
+    return large_leg(args, torch, stream, flush, I.semidilute_chains(4096, 256, 0.05, seed=1),
+                     "semi-dilute chains 4096x256 beads (1,048,576) phi=0.05 L=444.5, wavelet+plane-wave lcut 8",
+                     ({"colour_K": 3}, {"colour_K": 2}), args.semidilute_sweeps)
+
+
+def suspension_leg(args, torch, stream, flush):
+    """C5: 4,000,000 free spheres (WCA only) and 1,000 chains x 1,024 beads (5,024,000) at
+    volume fraction 1e-3, wavelets + plane waves."""
+    from paper_1611_09160_gb300 import inputs as I
+    return large_leg(args, torch, stream, flush, I.suspension(seed=1),
+                     "suspension 4,000,000 spheres + 1000x1024 chains (5,024,000) phi=1e-3 L=2760.9, wavelet+plane-wave lcut 8",
+                     ({"colour_K": 2}, {"colour_K": 2, "max_fine": 1024}, {"colour_K": 3, "max_fine": 1024}),
+                     args.suspension_sweeps)
 
 
 def serve_leg(args, torch, tuner, policy):
@@ -433,6 +452,7 @@ def run_gpu(args, rank, world, local_rank):
     tuner = A.Tuner(path=None, warm=1, sweeps=2, copies=152, seed_table=A.DEFAULT_TABLE)
     ens = ensemble_leg(args, torch, stream, flush, tuner) if args.ensemble > 0 else None
     semi = semidilute_leg(args, torch, stream, flush) if args.semidilute_sweeps > 0 else None
+    susp = suspension_leg(args, torch, stream, flush) if args.suspension_sweeps > 0 else None
     srv = serve_leg(args, torch, tuner, ens["policy"] if ens else "serial_small") if args.serve_requests > 0 else None
 
     if rank != 0:
@@ -444,7 +464,7 @@ def run_gpu(args, rank, world, local_rank):
             "sim_time_per_s": simt_all / (total_ms_all * 1e-3),
             "fp64": {"value": fp64_value * world, "unit": UNIT, "speedup_mixed_over_fp64": value / (fp64_value * world)},
             "e2e": e2e, "gpu_launches": launches_all, "clocks": clocks, "roofline": roofline,
-            "plane_wave": pw, "batched": ens, "serve": srv, "semidilute": semi,
+            "plane_wave": pw, "batched": ens, "serve": srv, "semidilute": semi, "suspension": susp,
             "stats": {"accept_fraction": (st1.accepted_total - st0.accepted_total) /
                                          max(1, sum(st1.attempts) - sum(st0.attempts) +
                                              st1.pw_attempts - st0.pw_attempts),
@@ -471,6 +491,7 @@ def main():
     ap.add_argument("--serve-capacity", type=int, default=512)
     ap.add_argument("--serve-chunk", type=int, default=10)
     ap.add_argument("--semidilute-sweeps", type=int, default=3, help="timed sweeps of the 1M-bead leg (0: skip)")
+    ap.add_argument("--suspension-sweeps", type=int, default=2, help="timed sweeps of the 5M-bead leg (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

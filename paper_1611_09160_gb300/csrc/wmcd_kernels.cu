@@ -1391,17 +1391,29 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
         }
         const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
+        const float lamf = (float)lam, af = (float)Aw, pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
         for (int k = tid; k < n; k += NT) {
             const int m = mid[k];
             const double o[3] = {px[m], py[m], pz[m]};
             double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)}, dl[3];
             if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
-            else wavelet_disp32(d, lam, Aw, p, dl);
+            else wavelet_disp32f(d, lamf, af, pf, dl);
             int im[3] = {0, 0, 0};
+            const float oh[3] = {fx[m], fy[m], fz[m]}, ol[3] = {lx[m], ly[m], lz[m]};
             for (int a = 0; a < 3; a++) {
                 mnew[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
-                mnf[3 * k + a] = (float)mnew[3 * k + a];
-                mnl[3 * k + a] = (float)(mnew[3 * k + a] - (double)mnf[3 * k + a]);
+                if (im[a] == 0) {
+                    // old (hi, lo) plus the displacement by a binary32 two-sum, renormalised
+                    const float dlf = (float)dl[a];
+                    const float s1 = oh[a] + dlf, bb = s1 - oh[a];
+                    const float l1 = ol[a] + ((oh[a] - (s1 - bb)) + (dlf - bb));
+                    const float h2 = s1 + l1;
+                    mnf[3 * k + a] = h2;
+                    mnl[3 * k + a] = l1 - (h2 - s1);
+                } else {                       // wrapped across a face: split the binary64 value
+                    mnf[3 * k + a] = (float)mnew[3 * k + a];
+                    mnl[3 * k + a] = (float)(mnew[3 * k + a] - (double)mnf[3 * k + a]);
+                }
             }
             mimg[k] = (uint8_t)pack_img(im[0], im[1], im[2]);
             sslot[m] = k;
