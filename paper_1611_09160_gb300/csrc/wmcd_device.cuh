@@ -249,7 +249,19 @@ WMCD_HD void wavelet_disp64(const double d[3], double d2, double lam, double Aw,
     out[0] = mul(sc, cx); out[1] = mul(sc, cy); out[2] = mul(sc, cz);
 }
 // mixed precision: the same expression in binary32 on inputs rounded once
-// the same with lam, A_w and p already rounded to binary32 (once per move, not per member)
+// the same with lam, A_w and p already rounded to binary32 (once per move, not per member),
+// returning the binary32 displacement
+WMCD_HD void wavelet_disp32ff(const double d[3], float lf, float af, const float pf[3], float out[3]) {
+    float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
+    float d2f = addf(addf(mulf(dx, dx), mulf(dy, dy)), mulf(dz, dz));
+    float px = pf[0], py = pf[1], pz = pf[2];
+    float rho = dvdf(sqrtf_(d2f), lf);
+    float sc = dvdf(mulf(af, subf(1.0f, rho)), lf);
+    float cx = subf(mulf(py, dz), mulf(pz, dy));
+    float cy = subf(mulf(pz, dx), mulf(px, dz));
+    float cz = subf(mulf(px, dy), mulf(py, dx));
+    out[0] = mulf(sc, cx); out[1] = mulf(sc, cy); out[2] = mulf(sc, cz);
+}
 WMCD_HD void wavelet_disp32f(const double d[3], float lf, float af, const float pf[3], double out[3]) {
     float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
     float d2f = addf(addf(mulf(dx, dx), mulf(dy, dy)), mulf(dz, dz));

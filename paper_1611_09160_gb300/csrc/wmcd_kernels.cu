@@ -2231,11 +2231,13 @@ struct Stage {
     float *mnh, *mnl;                // the same relative to the origin, hi and lo
     int *cj, *ci;                    // slot chunk: slot id, bead
     double *clam, *cV, *cp, *cthr;   // slot chunk: scale, centre offset, polarisation, threshold
+    double *cR, *clamV;              // ... influence radius and lam V for the slot's own scale
+    int* cti;                        // ... staged index of the picked bead (-1: not staged)
     int cap, hbits;
 };
 __host__ __device__ inline size_t stage_bytes(int cap) {
     return (size_t)cap * (3 * 8 + 6 * 4 + 4 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
-           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8) + 128;
+           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8 + 8 + 24 + 4) + 160;
 }
 __host__ __device__ inline size_t warp_stride(int cap) {
     size_t per = stage_bytes(cap) > sizeof(WarpSmem) ? stage_bytes(cap) : sizeof(WarpSmem);
@@ -2260,6 +2262,8 @@ __device__ inline Stage stage_carve(char* base, int cap) {
     S.mem = (int*)take(4 * kNCap); S.mimg = (int*)take(4 * kNCap); S.mpart = (int*)take(4 * 2 * kNCap);
     S.cand = (int*)take(4 * kCandCap);
     S.cj = (int*)take(4 * kSlotChunk); S.ci = (int*)take(4 * kSlotChunk);
+    S.cR = (double*)take(8 * kSlotChunk); S.clamV = (double*)take(8 * 3 * kSlotChunk);
+    S.cti = (int*)take(4 * kSlotChunk);
     return S;
 }
 __device__ __forceinline__ uint32_t hslot(int id, int bits) { return ((uint32_t)id * 2654435761u) >> (32 - bits); }
@@ -2285,38 +2289,52 @@ __device__ __forceinline__ void local_split(double x, double o, double L, float&
 // difference of two such coordinates: relative error about 2 ulp of binary32, no binary64 work
 __device__ __forceinline__ float dfd(float ha, float la, float hb, float lb) { return (ha - hb) + (la - lb); }
 
+// binary32 constants of a launch, converted once
+struct Stage32 {
+    Pot32 P32;
+    float hLf, rcs2;
+    const double* sqrt_n;            // sqrt(n) for n <= kNCap, correctly rounded (as sqr_t)
+    float side[3];                   // region side per axis
+};
+__device__ inline Stage32 stage32(const SimView& v) {
+    Stage32 c;
+    c.P32 = pot32(v.pot);
+    c.hLf = (float)v.halfL;
+    const float rcs = (float)(v.rc * (1.0 + 1e-6) + 1e-6);
+    c.rcs2 = rcs * rcs;
+    return c;
+}
+
 template <bool F32>
-__device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bool all_cand, int ns, int tag, int lane,
-                             double* dU64, float* dU32, float* mag32, int* terms, int* pe_out) {
+__device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand, int ns,
+                             int tag, int lane, double* dU64, float* dU32, float* mag32, int* terms, int* pe_out) {
     const double L = v.L, hL = v.halfL;
     const Pot& P = v.pot;
-    const Pot32 P32 = pot32(P);
-    const float hLf = (float)hL;
-    const float rcs = (float)(v.rc * (1.0 + 1e-6) + 1e-6);
-    const float rcs2 = rcs * rcs;
+    const Pot32& P32 = C.P32;
+    const float hLf = C.hLf;
+    const float rcs2 = C.rcs2;
     double a64 = 0.0;
     float a32 = 0.0f, m32 = 0.0f;
     int T = 0, pe = 0;
     // pair term between new positions (A, B) and old positions (C, D), indices into the
     // support (k < 0 is a staged bead -1 - t) for the binary32 form, positions for binary64
-    auto coord = [&](int k, int a, float& h, float& lo) {
-        if (k >= 0) { h = S.mnh[3 * k + a]; lo = S.mnl[3 * k + a]; }
-        else {
+    auto fetch = [&](int k, float h[3], float lo[3]) {
+        if (k >= 0) {
+            h[0] = S.mnh[3 * k]; h[1] = S.mnh[3 * k + 1]; h[2] = S.mnh[3 * k + 2];
+            lo[0] = S.mnl[3 * k]; lo[1] = S.mnl[3 * k + 1]; lo[2] = S.mnl[3 * k + 2];
+        } else {
             const int t = -1 - k;
-            h = a == 0 ? S.hx[t] : (a == 1 ? S.hy[t] : S.hz[t]);
-            lo = a == 0 ? S.lx[t] : (a == 1 ? S.ly[t] : S.lz[t]);
+            h[0] = S.hx[t]; h[1] = S.hy[t]; h[2] = S.hz[t];
+            lo[0] = S.lx[t]; lo[1] = S.ly[t]; lo[2] = S.lz[t];
         }
     };
     auto r2_32 = [&](int ka, int kb) {
-        float s = 0.0f;
-        for (int a = 0; a < 3; a++) {
-            float ha, la, hb, lb;
-            coord(ka, a, ha, la);
-            coord(kb, a, hb, lb);
-            const float d = dfd(ha, la, hb, lb);
-            s += d * d;
-        }
-        return s;
+        float ha[3], la[3], hb[3], lb[3];
+        fetch(ka, ha, la);
+        fetch(kb, hb, lb);
+        const float dx = dfd(ha[0], la[0], hb[0], lb[0]), dy = dfd(ha[1], la[1], hb[1], lb[1]),
+                    dz = dfd(ha[2], la[2], hb[2], lb[2]);
+        return dx * dx + dy * dy + dz * dz;
     };
     auto pos64 = [&](int k, double* x) {
         if (k >= 0) { x[0] = S.mnp[3 * k]; x[1] = S.mnp[3 * k + 1]; x[2] = S.mnp[3 * k + 2]; }
@@ -2409,43 +2427,57 @@ __device__ void stage_energy(const SimView& v, const Stage& S, int n, int nc, bo
 // One move of a staged queue. The slot's centre offset V, polarisation p and Metropolis
 // threshold were prepared in the chunk arrays at index c.
 template <int PREC>
-__device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const double org[3], float sidef, int l, int c,
-                             double lam, const int64_t rlo[3], const int64_t rhi[3], int lane, int tag, int* n_out,
-                             int* pe_out, int* recheck_out, double* du_out) {
+__device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C, int ns, const double org[3], float sidef,
+                             int l, int c, double lam, const int64_t rlo[3], const int64_t rhi[3], int lane, int tag,
+                             int* n_out, int* pe_out, int* recheck_out, double* du_out) {
     const unsigned FULL = 0xffffffffu;
     const double L = v.L, hL = v.halfL;
     const int Gf = v.Gf;
     *du_out = 0.0;
-    const int ti = stage_find(S, S.ci[c]);
+    const int ti = S.cti[c];
     if (ti < 0) return DEFER;                     // the picked bead lies outside the region interior
     // centre b = r_i + lam V (Appendix D), wrapped; binary64 because the region rule and the
-    // support must match the sequential definition exactly
-    double b[3];
-    b[0] = wrap(add(S.sx[ti], mul(lam, S.cV[3 * c])), L, nullptr);
-    b[1] = wrap(add(S.sy[ti], mul(lam, S.cV[3 * c + 1])), L, nullptr);
-    b[2] = wrap(add(S.sz[ti], mul(lam, S.cV[3 * c + 2])), L, nullptr);
-    const double R = add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
-    bool inside = true;
-    for (int a = 0; a < 3; a++) {
-        const int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
-        const int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
-        inside = inside && range_inside(t0, t1, rlo[a], rhi[a], Gf);
-    }
-    if (!inside) return DEFER;
-    // support and candidates in one binary32 pass over the staged beads (hi parts, with a
-    // margin eps for their rounding); ties within eps of the sphere decided in binary64
+    // support must match the sequential definition exactly. For the slot's own scale lam V and
+    // the influence radius R were formed ahead (same operations, same values); a carried scale
+    // forms them here.
+    const bool own = __double_as_longlong(lam) == __double_as_longlong(S.clam[c]);
+    double b[3], lv[3];
+    for (int a = 0; a < 3; a++) lv[a] = own ? S.clamV[3 * c + a] : mul(lam, S.cV[3 * c + a]);
+    b[0] = wrap(add(S.sx[ti], lv[0]), L, nullptr);
+    b[1] = wrap(add(S.sy[ti], lv[1]), L, nullptr);
+    b[2] = wrap(add(S.sz[ti], lv[2]), L, nullptr);
+    const double R = own ? S.cR[c] : add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
     const float lamf = (float)lam;
-    const float eps = 1e-6f * (sidef + lamf) + 1e-9f;
-    const float lin = (lamf - eps) * (lamf - eps), lout = (lamf + eps) * (lamf + eps);
-    const float Rf = (float)R + eps;
-    const float rcand = Rf * Rf;
-    // the centre relative to the region origin for the binary32 screen, from the picked bead's
-    // staged local coordinates and lam V in binary32: its error (a few 1e-7 of the region side
-    // plus lam) is well inside the screen margin eps
+    // the centre relative to the region origin in binary32 (from the picked bead's staged local
+    // coordinates): its error, a few 1e-7 of the region side plus lam, is far inside the margins
+    // of the screens below
     float bh[3];
     bh[0] = (S.hx[ti] + S.lx[ti]) + lamf * (float)S.cV[3 * c];
     bh[1] = (S.hy[ti] + S.ly[ti]) + lamf * (float)S.cV[3 * c + 1];
     bh[2] = (S.hz[ti] + S.lz[ti]) + lamf * (float)S.cV[3 * c + 2];
+    // region rule: a binary32 screen proves most balls well inside the region's interior; the
+    // others take the binary64 cell indices of the definition
+    const float Rf = (float)R;
+    bool surely_inside = true;
+    for (int a = 0; a < 3; a++) {
+        const float dm = 1e-6f * (C.side[a] + Rf) + 1e-6f;
+        surely_inside = surely_inside && (bh[a] - Rf >= dm) && (bh[a] + Rf <= C.side[a] - dm);
+    }
+    if (!surely_inside) {
+        bool inside = true;
+        for (int a = 0; a < 3; a++) {
+            const int64_t t0 = (int64_t)floor(mul(sub(b[a], R), v.invf));
+            const int64_t t1 = (int64_t)floor(mul(add(b[a], R), v.invf));
+            inside = inside && range_inside(t0, t1, rlo[a], rhi[a], Gf);
+        }
+        if (!inside) return DEFER;
+    }
+    // support and candidates in one binary32 pass over the staged beads (hi parts, with a
+    // margin eps for their rounding); ties within eps of the sphere decided in binary64
+    const float eps = 1e-6f * (sidef + lamf) + 1e-9f;
+    const float lin = (lamf - eps) * (lamf - eps), lout = (lamf + eps) * (lamf + eps);
+    const float Rc = Rf + eps;
+    const float rcand = Rc * Rc;
     int n = 0, nc = 0;
     for (int base = 0; base < ns; base += 32) {
         const int t = base + lane;
@@ -2473,7 +2505,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
     if (n == 0) return ACCEPT;                    // no bead moves; dU = 0 passes
     const bool all_cand = nc > kCandCap;
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
-    const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+    const double Aw = dvd(mul(v.A0, lam), C.sqrt_n[n]);
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
     const float af = (float)Aw, pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
     for (int k = lane; k < n; k += 32) {
@@ -2482,15 +2514,21 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
         const double o[3] = {S.sx[t], S.sy[t], S.sz[t]};
         double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)};
         double dl[3];
-        if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
-        else wavelet_disp32f(d, lamf, af, pf, dl);
+        float dlf3[3];
+        if (PREC == 0) {
+            wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
+            for (int a = 0; a < 3; a++) dlf3[a] = (float)dl[a];
+        } else {
+            wavelet_disp32ff(d, lamf, af, pf, dlf3);
+            for (int a = 0; a < 3; a++) dl[a] = (double)dlf3[a];
+        }
         int im[3] = {0, 0, 0};
         const float oh[3] = {S.hx[t], S.hy[t], S.hz[t]}, ol[3] = {S.lx[t], S.ly[t], S.lz[t]};
         for (int a = 0; a < 3; a++) {
             S.mnp[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
             // new local coordinate = old + displacement, in binary32 pairs (two-sum, then
             // renormalised); local coordinates are continuous inside the region, no wrap
-            const float dlf = (float)dl[a];
+            const float dlf = dlf3[a];
             const float s1 = oh[a] + dlf, bb = s1 - oh[a];
             const float err = (oh[a] - (s1 - bb)) + (dlf - bb);
             const float l1 = ol[a] + err;
@@ -2526,7 +2564,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
         // band (per term 80 ulp of its magnitude, plus the summation) and in binary64 inside it
         float d32 = 0.0f, m32 = 0.0f;
         int T = 0;
-        stage_energy<true>(v, S, n, nc, all_cand, ns, tag, lane, nullptr, &d32, &m32, &T, &pe);
+        stage_energy<true>(v, S, C, n, nc, all_cand, ns, tag, lane, nullptr, &d32, &m32, &T, &pe);
         const float thr32 = (float)thr;
         const float band = 2.0f * (float)(80 + T + 6) * 5.9604645e-08f * m32 + 1e-9f * (float)v.kT +
                            2.4e-7f * fabsf(thr32);
@@ -2536,14 +2574,14 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, int ns, const dou
         } else {
             double d64 = 0.0;
             int pe2 = 0;
-            stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe2);
+            stage_energy<false>(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe2);
             acc = d64 <= thr;
             *du_out = d64;
             (*recheck_out)++;
         }
     } else {
         double d64 = 0.0;
-        stage_energy<false>(v, S, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe);
+        stage_energy<false>(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe);
         acc = d64 <= thr;
         *du_out = d64;
     }
@@ -2572,6 +2610,10 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
+    // sqrt(n) for the amplitude A_w = A0 lam / sqrt(n) (Eq. 29), once per block
+    __shared__ double s_sqrt[kNCap + 1];
+    for (int i = threadIdx.x; i <= kNCap; i += blockDim.x) s_sqrt[i] = sqr_t((double)i);
+    __syncthreads();
     const uint64_t sweep = v.step[0];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -2617,6 +2659,9 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
         }
     } else {
         Stage S = stage_carve(base, cap);
+        Stage32 C32 = stage32(v);
+        C32.sqrt_n = s_sqrt;
+        for (int a = 0; a < 3; a++) C32.side[a] = (float)((double)(rhi[a] - rlo[a] + 1) * (v.L / v.Gf));
         const int H = 1 << S.hbits;
         for (int h = lane; h < H; h += 32) S.hkey[h] = -1;
         __syncwarp();
@@ -2668,6 +2713,11 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
                 for (int a = 0; a < 3; a++) { S.cV[3 * lane + a] = V[a]; S.cp[3 * lane + a] = dvd(pp[a], r); }
                 const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
                 S.cthr[lane] = -v.kT * log(1.0 - u53(w.x, w.y));
+                // what the move needs from its own scale, ahead of the sequential loop
+                const double lam_s = S.clam[lane];
+                S.cR[lane] = add(add(lam_s, mul(mul(0.25, v.A0), lam_s)), v.r_reach);
+                for (int a = 0; a < 3; a++) S.clamV[3 * lane + a] = mul(lam_s, V[a]);
+                S.cti[lane] = stage_find(S, S.ci[lane]);
             }
             __syncwarp();
             const int cend = min(kSlotChunk, cnt - c0);
@@ -2677,7 +2727,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
                 int n = 0;
                 double du = 0.0;
                 tag++;
-                const int r = stage_attempt<PREC>(v, S, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks, &du);
+                const int r = stage_attempt<PREC>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks, &du);
                 __syncwarp();
                 if (r == DEFER) { if (lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
                 att++; bu += n;
