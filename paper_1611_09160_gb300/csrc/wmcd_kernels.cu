@@ -2295,6 +2295,7 @@ struct Stage32 {
     float hLf, rcs2;
     const double* sqrt_n;            // sqrt(n) for n <= kNCap, correctly rounded (as sqr_t)
     float side[3];                   // region side per axis
+    int kappa_on, eps_on;            // external well, WCA
 };
 __device__ inline Stage32 stage32(const SimView& v) {
     Stage32 c;
@@ -2302,6 +2303,8 @@ __device__ inline Stage32 stage32(const SimView& v) {
     c.hLf = (float)v.halfL;
     const float rcs = (float)(v.rc * (1.0 + 1e-6) + 1e-6);
     c.rcs2 = rcs * rcs;
+    c.kappa_on = v.pot.kappa != 0.0;
+    c.eps_on = v.pot.eps != 0.0;
     return c;
 }
 
@@ -2363,7 +2366,7 @@ __device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C,
     // external well and bonds to beads outside the support
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
-        if (P.kappa != 0.0) {
+        if (C.kappa_on) {
             const double* nw = &S.mnp[3 * k];
             if (F32) {
                 float un = 0.5f * P32.kappa * norm2f(dif32(nw[0], hL, L, hLf), dif32(nw[1], hL, L, hLf), dif32(nw[2], hL, L, hLf));
@@ -2388,12 +2391,13 @@ __device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C,
         const int k1 = w - a * (a + 1) / 2, k2 = a + 1;
         const int t1 = S.mem[k1], t2 = S.mem[k2];
         const int m1 = S.sid[t1], m2 = S.sid[t2];
-        const int lo_ = min(m1, m2), hi_ = max(m1, m2);
-        const bool bonded = hi_ == lo_ + 1 && v.bnext[lo_];
+        // bonded members: the lower one's partner above moves with the support (partner table)
+        const int klo = m1 < m2 ? k1 : k2;
+        const bool bonded = max(m1, m2) == min(m1, m2) + 1 && S.mpart[2 * klo + 1] == -2;
         term(k1, k2, -1 - t1, -1 - t2, bonded, true);
     }
     // WCA with the interaction candidates outside the support
-    if (P.eps != 0.0) {
+    if (C.eps_on) {
         const int nsrc = all_cand ? ns : nc;
         const int total = n * nsrc;
         for (int w = lane; w < total; w += 32) {
@@ -2401,8 +2405,18 @@ __device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C,
             const int c = all_cand ? (w - k * nsrc) : S.cand[w - k * nsrc];
             if (S.stag[c] == tag) continue;           // a support member (only when scanning everything)
             const int t = S.mem[k];
-            if (!(r2_32(k, -1 - c) < rcs2) && !(r2_32(-1 - t, -1 - c) < rcs2)) continue;
-            term(k, -1 - c, -1 - t, -1 - c, false, true);
+            if (F32) {
+                // the screen's distances are the term's distances
+                const float r2n = r2_32(k, -1 - c), r2o = r2_32(-1 - t, -1 - c);
+                if (!(r2n < rcs2) && !(r2o < rcs2)) continue;
+                float un, mn, uo, mo;
+                wca32(P32, r2n, un, mn);
+                wca32(P32, r2o, uo, mo);
+                a32 += un - uo; m32 += mn + mo; T += 2;
+            } else {
+                if (!(r2_32(k, -1 - c) < rcs2) && !(r2_32(-1 - t, -1 - c) < rcs2)) continue;
+                term(k, -1 - c, -1 - t, -1 - c, false, true);
+            }
             pe++;
         }
     }
