@@ -844,16 +844,25 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
     __syncthreads();
     long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
     const float hLf = (float)hL, Lf = (float)L;
+    const bool kappa_on = P.kappa != 0.0, eps_on = P.eps != 0.0;
+    __shared__ double sh_lam, sh_lam2;
+    __shared__ float sh_bf[3], sh_rl2f;
+    // the binary64 values the whole block needs for a move are formed once, by thread 0, and
+    // shared: on this part each binary64 instruction of every warp would occupy the pipe
     for (int t = 0; t < count; t++) {
         const int j = use_list ? v.serial_list[t] : t;
-        const double lam = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
         const int i = v.slot_bead[j];
-        const double lam2 = mul(lam, lam);
         if (tid == 0) {
+            const double lam = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
+            sh_lam = lam;
+            sh_lam2 = mul(lam, lam);
+            const float rlf = (float)lam + (float)(8.0 * L * 5.9604644775390625e-8 + 1e-6);
+            sh_rl2f = rlf * rlf * (1.0f + 9.5367431640625e-7f);
             const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
             for (int a = 0; a < 3; a++) {
                 sh_b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), L, nullptr);
                 sh_p[a] = v.slot_p[3 * j + a];
+                sh_bf[a] = (float)sh_b[a];
             }
             const double eps = 1e-9;
             int64_t ncell = 1;
@@ -874,13 +883,13 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
             sh_tag = tag;
         }
         __syncthreads();
+        const double lam = sh_lam, lam2 = sh_lam2;
         const double b[3] = {sh_b[0], sh_b[1], sh_b[2]};
         // gather the support
         // binary32 screen on the shadow (margin 8 L 2^-24 + 1e-6 on the distance covers the rounding
         // of the shadow, of b and of the difference), then the binary64 test
-        const float bxf = (float)b[0], byf = (float)b[1], bzf = (float)b[2];
-        const float rlf = (float)lam + (float)(8.0 * L * 5.9604644775390625e-8 + 1e-6);
-        const float rl2f = rlf * rlf * (1.0f + 9.5367431640625e-7f);
+        const float bxf = sh_bf[0], byf = sh_bf[1], bzf = sh_bf[2];
+        const float rl2f = sh_rl2f;
         auto wrapg = [&](float f) { return fabsf(f) > hLf ? f - copysignf(Lf, f) : f; };
         auto consider = [&](int m, const Bead& bb) {
             {
@@ -927,7 +936,9 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
             continue;
         }
         const uint32_t tag = sh_tag;
-        const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+        // A_w and the partner-box reach only in warps that hold a member
+        const bool member_warp = (tid & ~31) < n;
+        const double Aw = member_warp ? dvd(mul(v.A0, lam), sqr_t((double)n)) : 0.0;
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
         for (int k = tid; k < n; k += NT) {
             int m = v.s_ids[k];
@@ -951,7 +962,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         // binary64 positions rounded once, the new one formed from the old one and the binary32
         // displacements), deciding outside the rigorous error band; the binary64 pass decides
         // inside it and in binary64 mode.
-        const double ext = add(v.rc, mul(0.25, Aw)) + 1e-9;
+        const double ext = member_warp ? add(v.rc, mul(0.25, Aw)) + 1e-9 : 0.0;
         const double thr = v.slot_thr[j];
         // old-position difference a - b, minimum image, rounded once to binary32
         auto d32 = [&](double a, double b) {
@@ -971,7 +982,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         // partner boxes and their exclusive prefix (items), shared by both passes
         for (int k = tid; k < n; k += NT) {
             int cnt = 0;
-            if (P.eps != 0.0) {
+            if (eps_on) {
                 const int m = v.s_ids[k];
                 const Bead bm = v.bead[m];
                 const double o[3] = {bm.x, bm.y, bm.z};
@@ -990,7 +1001,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         }
         __syncthreads();
         int W = 0;
-        if (P.eps != 0.0) {
+        if (eps_on) {
             // exclusive prefix of the box sizes, NT members per pass
             for (int base = 0; base < n; base += NT) {
                 const int k = base + tid;
@@ -1066,7 +1077,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
                 const float dlm[3] = {(float)v.s_d[4 * k], (float)v.s_d[4 * k + 1], (float)v.s_d[4 * k + 2]};
                 const BeadF fm = v.bf[m];
                 const float mh[3] = {fm.hx, fm.hy, fm.hz}, ml[3] = {fm.lx, fm.ly, fm.lz};
-                if (P.kappa != 0.0) {
+                if (kappa_on) {
                     float ro = 0.0f, rn = 0.0f;
                     for (int a = 0; a < 3; a++) {
                         const float c = d32(o[a], hL);
@@ -1103,7 +1114,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
                     a32 += un - uo; m32 += mn + mo; T += 2;
                 }
             }
-            if (P.eps != 0.0) {
+            if (eps_on) {
                 int mk = -1;
                 double o[3] = {0.0, 0.0, 0.0};
                 float dlm[3] = {0.0f, 0.0f, 0.0f}, mh[3] = {0.0f, 0.0f, 0.0f}, ml[3] = {0.0f, 0.0f, 0.0f};
@@ -1192,7 +1203,7 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
                     dU += U_bond(P, r2n) - U_bond(P, r2o);
                 }
             }
-            if (P.eps != 0.0) {
+            if (eps_on) {
                 int mk = -1;
                 double o[3] = {0.0, 0.0, 0.0}, nw[3] = {0.0, 0.0, 0.0};
                 for_pairs([&](int k, int m, int q, const Bead& bq) {
@@ -1323,6 +1334,10 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
     __shared__ int sh_T[NT / 32];
     __shared__ int sh_n, sh_acc, sh_stale, sh_need64;
+    __shared__ double sh_lam, sh_lam2;
+    __shared__ float sh_bf[3], sh_rl2;
+    __shared__ double s_sqrt[kNCap + 1];         // sqrt(n), correctly rounded, for small supports
+    for (int i2 = threadIdx.x; i2 <= kNCap; i2 += NT) s_sqrt[i2] = sqr_t((double)i2);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const LayerDev& Ly = v.layer[l];
     const double L = v.L, hL = v.halfL;
@@ -1344,27 +1359,34 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     if (tid == 0) { sh_carry = v.carry_serial[l]; sh_stale = 0; }
     __syncthreads();
     const Pot32 P32 = pot32(P);
+    const bool kappa_on = P.kappa != 0.0, eps_on = P.eps != 0.0;
     const float rcf = (float)v.rc + marg;
     const float rc2f = rcf * rcf * (1.0f + 9.5367431640625e-7f);
     long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
+    // every binary64 value the whole block needs for a move is formed once, by thread 0, and
+    // shared: on this part each binary64 instruction of every warp would occupy the pipe
     for (int j = 0; j < count; j++) {
-        const double lam = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
         const int i = v.slot_bead[j];
-        const double lam2 = mul(lam, lam);
         if (tid == 0) {
+            const double lam0 = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
             const double ri[3] = {px[i], py[i], pz[i]};
             for (int a = 0; a < 3; a++) {
-                sh_b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), L, nullptr);
+                sh_b[a] = wrap(add(ri[a], mul(lam0, v.slot_V[3 * j + a])), L, nullptr);
                 sh_p[a] = v.slot_p[3 * j + a];
+                sh_bf[a] = (float)sh_b[a];
             }
+            sh_lam = lam0;
+            sh_lam2 = mul(lam0, lam0);
+            const float rl = (float)lam0 + marg;
+            sh_rl2 = rl * rl * (1.0f + 9.5367431640625e-7f);
             sh_n = 0;
         }
         __syncthreads();
+        const double lam = sh_lam, lam2 = sh_lam2;
         const double b[3] = {sh_b[0], sh_b[1], sh_b[2]};
         {
-            const float bx = (float)b[0], by = (float)b[1], bz = (float)b[2];
-            const float rl = (float)lam + marg;
-            const float rl2 = rl * rl * (1.0f + 9.5367431640625e-7f);
+            const float bx = sh_bf[0], by = sh_bf[1], bz = sh_bf[2];
+            const float rl2 = sh_rl2;
             for (int m = tid; m < N; m += NT) {
                 float dx = fx[m] - bx, dy = fy[m] - by, dz = fz[m] - bz;
                 dx = fabsf(dx) > hLf ? dx - copysignf(Lf, dx) : dx;
@@ -1389,9 +1411,14 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             __syncthreads();
             continue;
         }
-        const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+        // A_w and the binary32 constants: only in warps that hold a member
+        double Aw = 0.0;
+        float lamf = 0.0f, af = 0.0f, pf[3] = {0.0f, 0.0f, 0.0f};
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
-        const float lamf = (float)lam, af = (float)Aw, pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+        if ((tid & ~31) < n) {
+            Aw = dvd(mul(v.A0, lam), n <= kNCap ? s_sqrt[n] : sqr_t((double)n));
+            lamf = (float)lam; af = (float)Aw; pf[0] = (float)p[0]; pf[1] = (float)p[1]; pf[2] = (float)p[2];
+        }
         for (int k = tid; k < n; k += NT) {
             const int m = mid[k];
             const double o[3] = {px[m], py[m], pz[m]};
@@ -1452,7 +1479,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                 const int m = mid[k];
                 const double o[3] = {px[m], py[m], pz[m]};
                 const double nw[3] = {mnew[3 * k], mnew[3 * k + 1], mnew[3 * k + 2]};
-                if (P.kappa != 0.0) {
+                if (kappa_on) {
                     const float un = 0.5f * P32.kappa * r2f(nw[0], nw[1], nw[2], hL, hL, hL);
                     const float uo = 0.5f * P32.kappa * r2f(o[0], o[1], o[2], hL, hL, hL);
                     a32 += un - uo; m32 += un + uo; T += 2;
@@ -1481,7 +1508,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                     a32 += un - uo; m32 += mn + mo; T += 2;
                 }
             }
-            if (P.eps != 0.0) {
+            if (eps_on) {
                 const int total = n * N;
                 int k = tid / N, q = tid - k * N;
                 const int kstep = NT / N, qstep = NT - kstep * N;
@@ -1571,7 +1598,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                     dU += U_bond(P, r2n) - U_bond(P, r2o);
                 }
             }
-            if (P.eps != 0.0) {
+            if (eps_on) {
                 // one (member, bead) pair per thread and step, all members at once
                 const int total = n * N;
                 int k = tid / N, q = tid - k * N;
