@@ -394,6 +394,9 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     // launch bounds of this simulation
     {
         GroupDims& g = h->g;
+        int dev = 0, n_sm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 0;
         g.S = 1;
         g.maxN = N;
         g.maxCells = std::max<int64_t>(ncell, 1);
@@ -415,6 +418,13 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
             g.nq[l] = std::max(Q * Q * Q, 1);
             g.coloured[l] = G > 0;
             g.bigM[l] = ((v.big_layers >> l) & 1) ? h->Mmax[l] : 0;
+            // a layer whose regions mostly overflow the base capacity but fit one block's shared
+            // memory, and whose queues of one colour are no more than the SMs, stages each
+            // region in a block of its own (a coarse layer of a dilute system): no queue waits
+            // for an SM, and moves avoid the global cell walks
+            const double region = G > 0 ? (double)N * std::pow((double)P.colour_K / G, 3.0) : 0.0;
+            const int cmax = staged_cap_max();
+            g.cap_l[l] = (G > 0 && Q * Q * Q <= n_sm && region > 0.8 * v.stage_cap && region <= 0.8 * cmax) ? cmax : 0;
         }
     }
     cudaMemsetAsync(v.step, 0, 2 * sizeof(uint64_t), s);

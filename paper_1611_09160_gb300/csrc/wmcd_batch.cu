@@ -137,6 +137,7 @@ static GroupDims group_bounds(const std::vector<Member>& ms, int block_warps, in
             g.nq[l] = std::max(g.nq[l], o.nq[l]);
             g.coloured[l] = g.coloured[l] || o.coloured[l];
             g.bigM[l] = std::max(g.bigM[l], o.bigM[l]);
+            g.cap_l[l] = std::max(g.cap_l[l], o.cap_l[l]);
         }
     }
     for (int l = 0; l < g.maxL; l++) {

@@ -181,6 +181,7 @@ struct GroupDims {
     int S = 1;
     int64_t maxN = 1, maxCells = 1;
     int maxL = 0, maxK3 = 1, maxMF = 0, stage_cap = 256, pw_blocks = 1;
+    int cap_l[kMaxLayers] = {0};  // staging capacity of a coloured layer when above stage_cap
     int Mmax[kMaxLayers] = {0}, keys[kMaxLayers] = {0}, nq[kMaxLayers] = {0};
     bool coloured[kMaxLayers] = {false};
     bool pw = false;
@@ -212,6 +213,7 @@ int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, c
 int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
 int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t s);     // kernels launched
 size_t staged_smem_bytes(int cap, int warps);
+int staged_cap_max();            // most beads one queue can stage (a block of one queue)
 size_t smem_serial_bytes(int64_t n);
 // open the kernels that take large dynamic shared memory for the sizes of g (before a graph
 // capture: a recorded launch sets nothing)

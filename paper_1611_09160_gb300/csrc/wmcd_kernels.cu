@@ -2251,20 +2251,21 @@ struct Stage {
     double *sx, *sy, *sz;            // staged positions (binary64, wrapped)
     float *hx, *hy, *hz;             // position relative to the region origin: hi part ...
     float *lx, *ly, *lz;             // ... and lo part (hi + lo carries the binary64 value)
-    int *sid, *scell, *sdim, *stag;  // bead id, fine cell at staging, image change | dirty, support tag
+    int *sid, *sdim, *stag;          // bead id, image change | dirty, support tag
     int *hkey, *hval;                // bead id -> staged index (open addressing)
     int *mem, *mimg, *mpart, *cand;  // support (staged indices), image change, bonded partners, candidates
     double *mnp;                     // new positions of the support (binary64, wrapped)
     float *mnh, *mnl;                // the same relative to the origin, hi and lo
     int *cj, *ci;                    // slot chunk: slot id, bead
     double *clam, *cV, *cp, *cthr;   // slot chunk: scale, centre offset, polarisation, threshold
-    double *cR, *clamV;              // ... influence radius and lam V for the slot's own scale
+    double *cR, *clamV, *cA0l;       // ... influence radius, lam V and A0 lam for the slot's own scale
+    float *clamf, *cRf, *cVf, *cpf;  // ... binary32 forms of lam, R, V and p
     int* cti;                        // ... staged index of the picked bead (-1: not staged)
     int cap, hbits;
 };
 __host__ __device__ inline size_t stage_bytes(int cap) {
-    return (size_t)cap * (3 * 8 + 6 * 4 + 4 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
-           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8 + 8 + 24 + 4) + 160;
+    return (size_t)cap * (3 * 8 + 6 * 4 + 3 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
+           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8 + 8 + 24 + 8 + 4 + 4 + 4 + 12 + 12) + 160;
 }
 __host__ __device__ inline size_t warp_stride(int cap) {
     size_t per = stage_bytes(cap) > sizeof(WarpSmem) ? stage_bytes(cap) : sizeof(WarpSmem);
@@ -2273,8 +2274,10 @@ __host__ __device__ inline size_t warp_stride(int cap) {
 __device__ inline Stage stage_carve(char* base, int cap) {
     Stage S;
     S.cap = cap;
+    // hash table: the largest power of two that fits its 2 cap entries (load factor <= 1/2 for
+    // power-of-two capacities, < 1 for any other)
     S.hbits = 1;
-    while ((1 << S.hbits) < 2 * cap) S.hbits++;
+    while ((2 << S.hbits) <= 2 * cap) S.hbits++;
     char* p = base;
     auto take = [&](size_t bytes) { char* q = p; p += (bytes + 7) & ~(size_t)7; return q; };
     S.sx = (double*)take(8 * cap); S.sy = (double*)take(8 * cap); S.sz = (double*)take(8 * cap);
@@ -2284,12 +2287,15 @@ __device__ inline Stage stage_carve(char* base, int cap) {
     S.hx = (float*)take(4 * cap); S.hy = (float*)take(4 * cap); S.hz = (float*)take(4 * cap);
     S.lx = (float*)take(4 * cap); S.ly = (float*)take(4 * cap); S.lz = (float*)take(4 * cap);
     S.mnh = (float*)take(4 * 3 * kNCap); S.mnl = (float*)take(4 * 3 * kNCap);
-    S.sid = (int*)take(4 * cap); S.scell = (int*)take(4 * cap); S.sdim = (int*)take(4 * cap); S.stag = (int*)take(4 * cap);
+    S.sid = (int*)take(4 * cap); S.sdim = (int*)take(4 * cap); S.stag = (int*)take(4 * cap);
     S.hkey = (int*)take(4 * 2 * cap); S.hval = (int*)take(4 * 2 * cap);
     S.mem = (int*)take(4 * kNCap); S.mimg = (int*)take(4 * kNCap); S.mpart = (int*)take(4 * 2 * kNCap);
     S.cand = (int*)take(4 * kCandCap);
     S.cj = (int*)take(4 * kSlotChunk); S.ci = (int*)take(4 * kSlotChunk);
     S.cR = (double*)take(8 * kSlotChunk); S.clamV = (double*)take(8 * 3 * kSlotChunk);
+    S.cA0l = (double*)take(8 * kSlotChunk);
+    S.clamf = (float*)take(4 * kSlotChunk); S.cRf = (float*)take(4 * kSlotChunk);
+    S.cVf = (float*)take(4 * 3 * kSlotChunk); S.cpf = (float*)take(4 * 3 * kSlotChunk);
     S.cti = (int*)take(4 * kSlotChunk);
     return S;
 }
@@ -2307,11 +2313,11 @@ __device__ __forceinline__ int stage_find(const Stage& S, int id) {
 }
 // coordinate relative to the region origin o, brought into [0, L), as a binary32 pair hi + lo
 __device__ __forceinline__ void local_split(double x, double o, double L, float& hi, float& lo) {
-    double t = x - o;
-    if (t < 0.0) t += L;
-    else if (t >= L) t -= L;
+    double t = sub(x, o);
+    if (lt_zero(t)) t = add(t, L);
+    else if (ge_pos(t, L)) t = sub(t, L);
     hi = (float)t;
-    lo = (float)(t - (double)hi);
+    lo = (float)sub(t, (double)hi);
 }
 // difference of two such coordinates: relative error about 2 ulp of binary32, no binary64 work
 __device__ __forceinline__ float dfd(float ha, float la, float hb, float lb) { return (ha - hb) + (la - lb); }
@@ -2335,37 +2341,15 @@ __device__ inline Stage32 stage32(const SimView& v) {
     return c;
 }
 
-template <bool F32>
-__device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand, int ns,
-                             int tag, int lane, double* dU64, float* dU32, float* mag32, int* terms, int* pe_out) {
+// Energy change of a staged move in binary64 (Eqs. 2, 5): bonds to beads outside the support,
+// pairs inside it, WCA with the interaction candidates; fixed order per lane, warp sum.
+__device__ void stage_energy64(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand, int ns,
+                               int tag, int lane, double* dU64, int* pe_out) {
     const double L = v.L, hL = v.halfL;
     const Pot& P = v.pot;
-    const Pot32& P32 = C.P32;
-    const float hLf = C.hLf;
     const float rcs2 = C.rcs2;
     double a64 = 0.0;
-    float a32 = 0.0f, m32 = 0.0f;
-    int T = 0, pe = 0;
-    // pair term between new positions (A, B) and old positions (C, D), indices into the
-    // support (k < 0 is a staged bead -1 - t) for the binary32 form, positions for binary64
-    auto fetch = [&](int k, float h[3], float lo[3]) {
-        if (k >= 0) {
-            h[0] = S.mnh[3 * k]; h[1] = S.mnh[3 * k + 1]; h[2] = S.mnh[3 * k + 2];
-            lo[0] = S.mnl[3 * k]; lo[1] = S.mnl[3 * k + 1]; lo[2] = S.mnl[3 * k + 2];
-        } else {
-            const int t = -1 - k;
-            h[0] = S.hx[t]; h[1] = S.hy[t]; h[2] = S.hz[t];
-            lo[0] = S.lx[t]; lo[1] = S.ly[t]; lo[2] = S.lz[t];
-        }
-    };
-    auto r2_32 = [&](int ka, int kb) {
-        float ha[3], la[3], hb[3], lb[3];
-        fetch(ka, ha, la);
-        fetch(kb, hb, lb);
-        const float dx = dfd(ha[0], la[0], hb[0], lb[0]), dy = dfd(ha[1], la[1], hb[1], lb[1]),
-                    dz = dfd(ha[2], la[2], hb[2], lb[2]);
-        return dx * dx + dy * dy + dz * dz;
-    };
+    int pe = 0;
     auto pos64 = [&](int k, double* x) {
         if (k >= 0) { x[0] = S.mnp[3 * k]; x[1] = S.mnp[3 * k + 1]; x[2] = S.mnp[3 * k + 2]; }
         else { const int t = -1 - k; x[0] = S.sx[t]; x[1] = S.sy[t]; x[2] = S.sz[t]; }
@@ -2376,32 +2360,37 @@ __device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C,
         pos64(kb, y);
         return norm2(mi(x[0] - y[0], L, hL), mi(x[1] - y[1], L, hL), mi(x[2] - y[2], L, hL));
     };
-    auto term = [&](int na, int nb, int oa, int ob, bool bonded, bool wca) {
-        if (F32) {
-            const float r2n = r2_32(na, nb), r2o = r2_32(oa, ob);
-            float un, mn, uo, mo;
-            if (wca) { wca32(P32, r2n, un, mn); wca32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
-            if (bonded) { bond32(P32, r2n, un, mn); bond32(P32, r2o, uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
-        } else {
-            const double r2n = r2_64(na, nb), r2o = r2_64(oa, ob);
-            double u = 0.0;
-            if (wca) u += U_wca(P, r2n) - U_wca(P, r2o);
-            if (bonded) u += U_bond(P, r2n) - U_bond(P, r2o);
-            a64 += u;
+    // the binary32 distance of the candidate screen (the same screen as the binary32 pass)
+    auto r2_32 = [&](int ka, int kb) {
+        float h[2][3], lo[2][3];
+        const int ks[2] = {ka, kb};
+        for (int u = 0; u < 2; u++) {
+            const int k = ks[u];
+            if (k >= 0) {
+                for (int a = 0; a < 3; a++) { h[u][a] = S.mnh[3 * k + a]; lo[u][a] = S.mnl[3 * k + a]; }
+            } else {
+                const int t = -1 - k;
+                h[u][0] = S.hx[t]; h[u][1] = S.hy[t]; h[u][2] = S.hz[t];
+                lo[u][0] = S.lx[t]; lo[u][1] = S.ly[t]; lo[u][2] = S.lz[t];
+            }
         }
+        const float dx = dfd(h[0][0], lo[0][0], h[1][0], lo[1][0]), dy = dfd(h[0][1], lo[0][1], h[1][1], lo[1][1]),
+                    dz = dfd(h[0][2], lo[0][2], h[1][2], lo[1][2]);
+        return dx * dx + dy * dy + dz * dz;
+    };
+    auto term = [&](int na, int nb, int oa, int ob, bool bonded, bool wca) {
+        const double r2n = r2_64(na, nb), r2o = r2_64(oa, ob);
+        double u = 0.0;
+        if (wca) u += U_wca(P, r2n) - U_wca(P, r2o);
+        if (bonded) u += U_bond(P, r2n) - U_bond(P, r2o);
+        a64 += u;
     };
     // external well and bonds to beads outside the support
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
         if (C.kappa_on) {
             const double* nw = &S.mnp[3 * k];
-            if (F32) {
-                float un = 0.5f * P32.kappa * norm2f(dif32(nw[0], hL, L, hLf), dif32(nw[1], hL, L, hLf), dif32(nw[2], hL, L, hLf));
-                float uo = 0.5f * P32.kappa * norm2f(dif32(S.sx[t], hL, L, hLf), dif32(S.sy[t], hL, L, hLf), dif32(S.sz[t], hL, L, hLf));
-                a32 += un - uo; m32 += un + uo; T += 2;
-            } else {
-                a64 += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, S.sx[t], S.sy[t], S.sz[t]);
-            }
+            a64 += U_ext(P, nw[0], nw[1], nw[2]) - U_ext(P, S.sx[t], S.sy[t], S.sz[t]);
         }
         for (int e = 0; e < 2; e++) {
             const int tq = S.mpart[2 * k + e];
@@ -2432,37 +2421,111 @@ __device__ void stage_energy(const SimView& v, const Stage& S, const Stage32& C,
             const int c = all_cand ? (w - k * nsrc) : S.cand[w - k * nsrc];
             if (S.stag[c] == tag) continue;           // a support member (only when scanning everything)
             const int t = S.mem[k];
-            if (F32) {
-                // the screen's distances are the term's distances
-                const float r2n = r2_32(k, -1 - c), r2o = r2_32(-1 - t, -1 - c);
-                if (!(r2n < rcs2) && !(r2o < rcs2)) continue;
-                float un, mn, uo, mo;
-                wca32(P32, r2n, un, mn);
-                wca32(P32, r2o, uo, mo);
-                a32 += un - uo; m32 += mn + mo; T += 2;
-            } else {
-                if (!(r2_32(k, -1 - c) < rcs2) && !(r2_32(-1 - t, -1 - c) < rcs2)) continue;
-                term(k, -1 - c, -1 - t, -1 - c, false, true);
-            }
+            if (!(r2_32(k, -1 - c) < rcs2) && !(r2_32(-1 - t, -1 - c) < rcs2)) continue;
+            term(k, -1 - c, -1 - t, -1 - c, false, true);
             pe++;
         }
     }
-    const unsigned FULL = 0xffffffffu;
-    if (F32) {
-        float s = a32, mm = m32;
-        int tt = T;
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(FULL, s, o);
-            mm += __shfl_xor_sync(FULL, mm, o);
-            tt = max(tt, __shfl_xor_sync(FULL, tt, o));
+    *dU64 = __shfl_sync(0xffffffffu, warp_sum(a64), 0);
+    *pe_out = __reduce_add_sync(0xffffffffu, (unsigned)pe);
+}
+
+// The same energy change in binary32 from the staged hi + lo local coordinates, with the
+// magnitude sum and summation depth its error band needs. All terms (bonds to outside beads,
+// pairs inside the support, candidates) form one list dealt to the lanes, so a lane resolves
+// its item and then every lane evaluates the same potentials together.
+__device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand, int ns,
+                               int tag, int lane, float* dU32, float* mag32, int* terms, int* pe_out) {
+    const double L = v.L, hL = v.halfL;
+    const Pot32& P32 = C.P32;
+    const float hLf = C.hLf;
+    const float rcs2 = C.rcs2;
+    float a32 = 0.0f, m32 = 0.0f;
+    int T = 0, pe = 0;
+    // external well (rare: only with kappa != 0), from the binary64 positions
+    if (C.kappa_on) {
+        for (int k = lane; k < n; k += 32) {
+            const int t = S.mem[k];
+            const double* nw = &S.mnp[3 * k];
+            float un = 0.5f * P32.kappa * norm2f(dif32(nw[0], hL, L, hLf), dif32(nw[1], hL, L, hLf), dif32(nw[2], hL, L, hLf));
+            float uo = 0.5f * P32.kappa * norm2f(dif32(S.sx[t], hL, L, hLf), dif32(S.sy[t], hL, L, hLf), dif32(S.sz[t], hL, L, hLf));
+            a32 += un - uo; m32 += un + uo; T += 2;
         }
-        *dU32 = __shfl_sync(FULL, s, 0);
-        *mag32 = __shfl_sync(FULL, mm, 0);
-        *terms = __shfl_sync(FULL, tt, 0) + 5;   // summation depth: one lane's terms, then the butterfly
-    } else {
-        *dU64 = __shfl_sync(FULL, warp_sum(a64), 0);
     }
-    *pe_out = warp_sum_i(pe);
+    const int nB = 2 * n, nP = n * (n - 1) / 2;
+    const int nsrc = all_cand ? ns : nc;
+    const int nD = C.eps_on ? n * nsrc : 0;
+    const int total = nB + nP + nD;
+    for (int w = lane; w < total; w += 32) {
+        // the item: new positions (na, nb), old positions (oa, ob); k >= 0 is a support member
+        // (new position), k < 0 the staged bead -1 - k
+        int na = 0, nb = 0, oa = 0, ob = 0;
+        bool use = true, wca = false, bnd = false, screen = false;
+        if (w < nB) {
+            const int k = w >> 1, tq = S.mpart[w];
+            use = tq >= 0;                            // no bond, or the partner moves too
+            na = k; nb = -1 - tq; oa = -1 - S.mem[k]; ob = nb;
+            bnd = true;
+        } else if (w < nB + nP) {
+            const int u = w - nB;
+            int a = (int)((sqrtf(8.0f * u + 1.0f) - 1.0f) * 0.5f);
+            while (a * (a + 1) / 2 > u) a--;
+            while ((a + 1) * (a + 2) / 2 <= u) a++;
+            const int k1 = u - a * (a + 1) / 2, k2 = a + 1;
+            const int t1 = S.mem[k1], t2 = S.mem[k2];
+            const int m1 = S.sid[t1], m2 = S.sid[t2];
+            // bonded members: the lower one's partner above moves with the support
+            const int klo = m1 < m2 ? k1 : k2;
+            bnd = max(m1, m2) == min(m1, m2) + 1 && S.mpart[2 * klo + 1] == -2;
+            wca = true;
+            na = k1; nb = k2; oa = -1 - t1; ob = -1 - t2;
+        } else {
+            const int u = w - nB - nP;
+            const int k = u / nsrc;
+            const int c = all_cand ? (u - k * nsrc) : S.cand[u - k * nsrc];
+            use = S.stag[c] != tag;                   // a support member (only when scanning everything)
+            na = k; nb = -1 - c; oa = -1 - S.mem[k]; ob = nb;
+            wca = true; screen = true;
+        }
+        if (!use) continue;
+        float hn[2][3], ln[2][3];
+        const int ks[4] = {na, nb, oa, ob};
+        float r2[2];
+        for (int pr = 0; pr < 2; pr++) {
+            for (int u = 0; u < 2; u++) {
+                const int k = ks[2 * pr + u];
+                if (k >= 0) {
+                    hn[u][0] = S.mnh[3 * k]; hn[u][1] = S.mnh[3 * k + 1]; hn[u][2] = S.mnh[3 * k + 2];
+                    ln[u][0] = S.mnl[3 * k]; ln[u][1] = S.mnl[3 * k + 1]; ln[u][2] = S.mnl[3 * k + 2];
+                } else {
+                    const int t = -1 - k;
+                    hn[u][0] = S.hx[t]; hn[u][1] = S.hy[t]; hn[u][2] = S.hz[t];
+                    ln[u][0] = S.lx[t]; ln[u][1] = S.ly[t]; ln[u][2] = S.lz[t];
+                }
+            }
+            const float dx = dfd(hn[0][0], ln[0][0], hn[1][0], ln[1][0]), dy = dfd(hn[0][1], ln[0][1], hn[1][1], ln[1][1]),
+                        dz = dfd(hn[0][2], ln[0][2], hn[1][2], ln[1][2]);
+            r2[pr] = dx * dx + dy * dy + dz * dz;
+        }
+        // a candidate counts only within the interaction reach, new or old (the screen's
+        // distances are the term's distances)
+        if (screen && !(r2[0] < rcs2) && !(r2[1] < rcs2)) continue;
+        if (screen) pe++;
+        float un, mn, uo, mo;
+        if (wca) { wca32(P32, r2[0], un, mn); wca32(P32, r2[1], uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
+        if (bnd) { bond32(P32, r2[0], un, mn); bond32(P32, r2[1], uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
+    }
+    const unsigned FULL = 0xffffffffu;
+    float sm = a32, mm = m32;
+    for (int o = 16; o > 0; o >>= 1) {
+        sm += __shfl_xor_sync(FULL, sm, o);
+        mm += __shfl_xor_sync(FULL, mm, o);
+    }
+    *dU32 = __shfl_sync(FULL, sm, 0);
+    *mag32 = __shfl_sync(FULL, mm, 0);
+    // summation depth: the most terms one lane added, then the five butterfly levels
+    *terms = (int)__reduce_max_sync(FULL, (unsigned)T) + 5;
+    *pe_out = (int)__reduce_add_sync(FULL, (unsigned)pe);
 }
 
 // One move of a staged queue. The slot's centre offset V, polarisation p and Metropolis
@@ -2488,17 +2551,21 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     b[1] = wrap(add(S.sy[ti], lv[1]), L, nullptr);
     b[2] = wrap(add(S.sz[ti], lv[2]), L, nullptr);
     const double R = own ? S.cR[c] : add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
-    const float lamf = (float)lam;
+    const float lamf = own ? S.clamf[c] : (float)lam;
+    // A_w = A0 lam / sqrt(n) (Eq. 29) for every support size up to 32, one per lane, formed
+    // while the scan below runs; the scan's n picks one
+    const double a0l = own ? S.cA0l[c] : mul(v.A0, lam);
+    const double aw_lane = dvd(a0l, C.sqrt_n[lane + 1]);
     // the centre relative to the region origin in binary32 (from the picked bead's staged local
     // coordinates): its error, a few 1e-7 of the region side plus lam, is far inside the margins
     // of the screens below
     float bh[3];
-    bh[0] = (S.hx[ti] + S.lx[ti]) + lamf * (float)S.cV[3 * c];
-    bh[1] = (S.hy[ti] + S.ly[ti]) + lamf * (float)S.cV[3 * c + 1];
-    bh[2] = (S.hz[ti] + S.lz[ti]) + lamf * (float)S.cV[3 * c + 2];
+    bh[0] = (S.hx[ti] + S.lx[ti]) + lamf * S.cVf[3 * c];
+    bh[1] = (S.hy[ti] + S.ly[ti]) + lamf * S.cVf[3 * c + 1];
+    bh[2] = (S.hz[ti] + S.lz[ti]) + lamf * S.cVf[3 * c + 2];
     // region rule: a binary32 screen proves most balls well inside the region's interior; the
     // others take the binary64 cell indices of the definition
-    const float Rf = (float)R;
+    const float Rf = own ? S.cRf[c] : (float)R;
     bool surely_inside = true;
     for (int a = 0; a < 3; a++) {
         const float dm = 1e-6f * (C.side[a] + Rf) + 1e-6f;
@@ -2522,17 +2589,22 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     int n = 0, nc = 0;
     for (int base = 0; base < ns; base += 32) {
         const int t = base + lane;
-        bool in = false, cd = false;
+        bool in = false, cd = false, tie = false;
+        float d2 = 0.0f;
         if (t < ns) {
             const float dx = S.hx[t] - bh[0], dy = S.hy[t] - bh[1], dz = S.hz[t] - bh[2];
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 < lin) in = true;
-            else if (d2 <= lout) {
+            d2 = dx * dx + dy * dy + dz * dz;
+            in = d2 < lin;
+            tie = !in && d2 <= lout;
+        }
+        // the binary64 test only in the rare passes that hold a tie (a branch the whole warp takes)
+        if (__any_sync(FULL, tie)) {
+            if (tie) {
                 const double e2 = norm2(mi(sub(S.sx[t], b[0]), L, hL), mi(sub(S.sy[t], b[1]), L, hL), mi(sub(S.sz[t], b[2]), L, hL));
                 in = e2 < mul(lam, lam);
             }
-            cd = !in && d2 < rcand;
         }
+        cd = t < ns && !in && d2 < rcand;
         const unsigned mi_ = __ballot_sync(FULL, in), mc = __ballot_sync(FULL, cd);
         const unsigned below = (1u << lane) - 1u;
         if (in) { const int s = n + __popc(mi_ & below); if (s < kNCap) S.mem[s] = t; }
@@ -2546,9 +2618,9 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     if (n == 0) return ACCEPT;                    // no bead moves; dU = 0 passes
     const bool all_cand = nc > kCandCap;
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
-    const double Aw = dvd(mul(v.A0, lam), C.sqrt_n[n]);
+    const double Aw = n <= 32 ? __shfl_sync(FULL, aw_lane, n - 1) : dvd(a0l, C.sqrt_n[n]);
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
-    const float af = (float)Aw, pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+    const float af = (float)Aw, pf[3] = {S.cpf[3 * c], S.cpf[3 * c + 1], S.cpf[3 * c + 2]};
     for (int k = lane; k < n; k += 32) {
         const int t = S.mem[k];
         S.stag[t] = tag;
@@ -2583,11 +2655,12 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     // bonded partners: staged (inside the region) or the move is deferred
     bool bad = false;
     for (int k = lane; k < n; k += 32) {
-        const int m = S.sid[S.mem[k]];
+        const int tk = S.mem[k];
+        const int m = S.sid[tk], fl = S.sdim[tk] >> 25;   // staged bond flags: 1 up, 2 down
         for (int e = 0; e < 2; e++) {
             const int q = e ? m + 1 : m - 1;
             int tq = -1;
-            if (q >= 0 && q < v.N && (e ? v.bnext[m] : v.bnext[q])) {
+            if (q >= 0 && q < v.N && ((fl >> (1 - e)) & 1)) {
                 tq = stage_find(S, q);
                 if (tq < 0) bad = true;
                 else if (S.stag[tq] == tag) tq = -2;   // moves with the support
@@ -2605,7 +2678,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         // band (per term 80 ulp of its magnitude, plus the summation) and in binary64 inside it
         float d32 = 0.0f, m32 = 0.0f;
         int T = 0;
-        stage_energy<true>(v, S, C, n, nc, all_cand, ns, tag, lane, nullptr, &d32, &m32, &T, &pe);
+        stage_energy32(v, S, C, n, nc, all_cand, ns, tag, lane, &d32, &m32, &T, &pe);
         const float thr32 = (float)thr;
         const float band = 2.0f * (float)(80 + T + 6) * 5.9604645e-08f * m32 + 1e-9f * (float)v.kT +
                            2.4e-7f * fabsf(thr32);
@@ -2615,14 +2688,14 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         } else {
             double d64 = 0.0;
             int pe2 = 0;
-            stage_energy<false>(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe2);
+            stage_energy64(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, &pe2);
             acc = d64 <= thr;
             *du_out = d64;
             (*recheck_out)++;
         }
     } else {
         double d64 = 0.0;
-        stage_energy<false>(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, nullptr, nullptr, nullptr, &pe);
+        stage_energy64(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, &pe);
         acc = d64 <= thr;
         *du_out = d64;
     }
@@ -2638,16 +2711,20 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         unpack_img(S.mimg[k], dd);
         const int ax = ((cur & 0xff) - 128) + dd[0], ay = (((cur >> 8) & 0xff) - 128) + dd[1],
                   az = (((cur >> 16) & 0xff) - 128) + dd[2];
-        S.sdim[t] = (ax + 128) | ((ay + 128) << 8) | ((az + 128) << 16) | (1 << 24);
+        S.sdim[t] = (ax + 128) | ((ay + 128) << 8) | ((az + 128) << 16) | (1 << 24) | (cur & (3 << 25));
     }
     __syncwarp();
     return ACCEPT;
 }
 
+// A block serves qpb queues with one warp each, or (qpb = 1) one queue with all its warps: then
+// every warp stages a share of the region (the binary64 work of staging spreads over the SM's
+// four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue.
 template <int PREC>
-__global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour) {
+__global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
+                                                                        int cap, int qpb) {
     SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
-                (int)(blockIdx.x * (blockDim.x >> 5)) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K))
+                (int)(blockIdx.x * qpb) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K))
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
@@ -2656,16 +2733,16 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
     for (int i = threadIdx.x; i <= kNCap; i += blockDim.x) s_sqrt[i] = sqr_t((double)i);
     __syncthreads();
     const uint64_t sweep = v.step[0];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int H = (int)(blockDim.x >> 5) / qpb;     // warps per queue: 1, or all of the block
+    const int wib = (int)(threadIdx.x >> 5) / H, role = (int)(threadIdx.x >> 5) % H, lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const LayerDev& Ly = v.layer[l];
     const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
-    const int q = blockIdx.x * (int)(blockDim.x >> 5) + wib;
-    if (q >= nq) return;
+    const int q = blockIdx.x * qpb + wib;
+    if (q >= nq) return;                          // uniform over the warps of a queue
     const int key = colour * nq + q;
     const int start = v.q_start[key], cnt = v.q_count[key];
     if (cnt == 0) return;
-    const int cap = v.stage_cap;
     char* base = dsm + (size_t)wib * warp_stride(cap);
     const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
     int64_t rlo[3], rhi[3];
@@ -2680,6 +2757,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
     const int rs = v.rstart[q], ns = v.rcount[q];
     if (ns > cap) {
         // region too full for shared memory: the global-memory path
+        if (role != 0) return;
         WarpSmem& sm = *(WarpSmem*)base;
         for (int t = 0; t < cnt; t++) {
             const int j = v.q_slots[start + t];
@@ -2703,13 +2781,14 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
         Stage32 C32 = stage32(v);
         C32.sqrt_n = s_sqrt;
         for (int a = 0; a < 3; a++) C32.side[a] = (float)((double)(rhi[a] - rlo[a] + 1) * (v.L / v.Gf));
-        const int H = 1 << S.hbits;
-        for (int h = lane; h < H; h += 32) S.hkey[h] = -1;
-        __syncwarp();
+        const int HT = 1 << S.hbits;
+        const int ql = role * 32 + lane, qstride = 32 * H;   // this thread among the queue's warps
+        for (int h = ql; h < HT; h += qstride) S.hkey[h] = -1;
+        if (H > 1) __syncthreads(); else __syncwarp();
         const double hf = v.L / v.Gf;
         const double org[3] = {(double)rlo[0] * hf, (double)rlo[1] * hf, (double)rlo[2] * hf};
         const float sidef = (float)((double)(rhi[0] - rlo[0] + 1) * hf);
-        for (int t = lane; t < ns; t += 32) {
+        for (int t = ql; t < ns; t += qstride) {
             const int m = v.rlist[rs + t];
             const Bead bb = v.bead[m];
             S.sx[t] = bb.x; S.sy[t] = bb.y; S.sz[t] = bb.z;
@@ -2717,18 +2796,19 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
             local_split(bb.y, org[1], v.L, S.hy[t], S.ly[t]);
             local_split(bb.z, org[2], v.L, S.hz[t], S.lz[t]);
             S.sid[t] = m;
-            S.scell[t] = cell_lin(v, bb.x, bb.y, bb.z);
-            S.sdim[t] = 128 | (128 << 8) | (128 << 16);
+            const int bflag = (v.bnext[m] ? 1 : 0) | (m > 0 && v.bnext[m - 1] ? 2 : 0);
+            S.sdim[t] = 128 | (128 << 8) | (128 << 16) | (bflag << 25);
             S.stag[t] = 0;
-            const uint32_t mask = (uint32_t)H - 1u;
+            const uint32_t mask = (uint32_t)HT - 1u;
             uint32_t h = hslot(m, S.hbits);
-            for (int probe = 0; probe < H; probe++) {
+            for (int probe = 0; probe < HT; probe++) {
                 const int prev = atomicCAS(&S.hkey[h], -1, m);
                 if (prev == -1) { S.hval[h] = t; break; }
                 h = (h + 1u) & mask;
             }
         }
-        __syncwarp();
+        if (H > 1) __syncthreads(); else __syncwarp();
+        if (role != 0) return;                    // the moves run on one warp
         int tag = 0;
         for (int c0 = 0; c0 < cnt; c0 += kSlotChunk) {
             // slot parameters of the chunk, one lane per slot: V, p by rejection (Appendix D)
@@ -2756,15 +2836,23 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
                 S.cthr[lane] = -v.kT * log(1.0 - u53(w.x, w.y));
                 // what the move needs from its own scale, ahead of the sequential loop
                 const double lam_s = S.clam[lane];
-                S.cR[lane] = add(add(lam_s, mul(mul(0.25, v.A0), lam_s)), v.r_reach);
-                for (int a = 0; a < 3; a++) S.clamV[3 * lane + a] = mul(lam_s, V[a]);
+                const double R_s = add(add(lam_s, mul(mul(0.25, v.A0), lam_s)), v.r_reach);
+                S.cR[lane] = R_s;
+                S.cRf[lane] = (float)R_s;
+                S.clamf[lane] = (float)lam_s;
+                S.cA0l[lane] = mul(v.A0, lam_s);
+                for (int a = 0; a < 3; a++) {
+                    S.clamV[3 * lane + a] = mul(lam_s, V[a]);
+                    S.cVf[3 * lane + a] = (float)V[a];
+                    S.cpf[3 * lane + a] = (float)S.cp[3 * lane + a];
+                }
                 S.cti[lane] = stage_find(S, S.ci[lane]);
             }
             __syncwarp();
             const int cend = min(kSlotChunk, cnt - c0);
             for (int cc = 0; cc < cend; cc++) {
                 const int j = S.cj[cc];
-                const double lam = carry > 0.0 ? carry : S.clam[cc];
+                const double lam = __double_as_longlong(carry) > 0 ? carry : S.clam[cc];
                 int n = 0;
                 double du = 0.0;
                 tag++;
@@ -2783,26 +2871,30 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
             __syncwarp();
         }
         // write back the moved beads (lanes in parallel); cell-list moves by lane 0, in
-        // staged order, for the beads whose fine cell changed
+        // staged order, for the beads whose fine cell changed (the old cell from the bead's
+        // record, which nothing else writes during the phase)
         for (int base2 = 0; base2 < ns; base2 += 32) {
             const int t = base2 + lane;
-            int newcell = -1;
+            int newcell = -1, oldcell = -1;
             if (t < ns && (S.sdim[t] & (1 << 24))) {
                 const int dm = S.sdim[t];
                 const int m = S.sid[t];
+                const Bead ob = v.bead[m];
+                oldcell = cell_lin(v, ob.x, ob.y, ob.z);
                 put_bead(v.bead, v.bf, m, S.sx[t], S.sy[t], S.sz[t]);
                 const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
                 if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
                 const int nc2 = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
-                if (nc2 != S.scell[t]) newcell = nc2;
+                if (nc2 != oldcell) newcell = nc2;
             }
             const unsigned ch = __ballot_sync(FULL, newcell >= 0);
             S.cand[lane] = newcell;
+            S.cand[32 + lane] = oldcell;
             __syncwarp();
             if (lane == 0) {
                 for (unsigned bits = ch; bits; bits &= bits - 1u) {
                     const int ln = __ffs(bits) - 1, tt = base2 + ln;
-                    const int m = S.sid[tt], oc = S.scell[tt], ncl = S.cand[ln];
+                    const int m = S.sid[tt], oc = S.cand[32 + ln], ncl = S.cand[ln];
                     const int pr = v.prev[m], nx = v.bead[m].next;
                     if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
                     if (nx >= 0) v.prev[nx] = pr;
@@ -2832,12 +2924,25 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const Sim
 }
 
 size_t staged_smem_bytes(int cap, int warps) { return (size_t)warps * warp_stride(cap); }
-// warps per block actually used: the requested count, lowered until the block's shared memory
-// (dynamic + the static view copy) fits the 227 KB a block may have
-static int staged_warps(const GroupDims& g) {
+static bool staged_fits(int cap, int queues) {
+    // dynamic shared memory + the static view copy and sqrt table within the 227 KB of a block
+    return staged_smem_bytes(cap, queues) + sizeof(SimView) + 1024 <= 227u * 1024u;
+}
+int staged_cap_max() {
+    int cap = 256;
+    while (staged_fits(cap + 32, 1)) cap += 32;
+    return cap;
+}
+// staging capacity of layer l's launches (the largest over the group)
+static int layer_cap(const GroupDims& g, int l) { return std::max(g.stage_cap, g.cap_l[l]); }
+// queues per block actually used: the requested count, lowered until the block's shared memory
+// fits; a block of one queue with a region larger than 1,024 beads gets kMaxStageWarps warps,
+// which share the staging
+static void staged_shape(const GroupDims& g, int cap, int* qpb, int* warps) {
     int nw = std::max(1, std::min(g.block_warps, kMaxStageWarps));
-    while (nw > 1 && staged_smem_bytes(g.stage_cap, nw) + sizeof(SimView) + 1024 > 227u * 1024u) nw--;
-    return nw;
+    while (nw > 1 && !staged_fits(cap, nw)) nw--;
+    *qpb = nw;
+    *warps = (nw == 1 && cap > 1024) ? kMaxStageWarps : nw;
 }
 
 // The largest dynamic shared memory each staged kernel was opened for, per device: raised
@@ -2863,7 +2968,14 @@ void prepare_staged(const GroupDims& g) {
             g_serial_smem[dev][1] = sm;
         }
     }
-    const int smem = (int)staged_smem_bytes(g.stage_cap, staged_warps(g));
+    int smem = 0;
+    for (int l = 0; l < g.maxL; l++) {
+        if (!g.coloured[l]) continue;
+        const int cap = layer_cap(g, l);
+        int qpb = 1, warps = 1;
+        staged_shape(g, cap, &qpb, &warps);
+        smem = std::max(smem, (int)staged_smem_bytes(cap, qpb));
+    }
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
         cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         g_staged_smem[dev][0] = smem;
@@ -2881,13 +2993,15 @@ void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colou
     k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
     k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l);
     k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
-    const int nw = staged_warps(g);
-    const size_t smem = staged_smem_bytes(g.stage_cap, nw);
-    const dim3 grid((nq + nw - 1) / nw, g.S);
+    const int cap = layer_cap(g, l);
+    int qpb = 1, warps = 1;
+    staged_shape(g, cap, &qpb, &warps);
+    const size_t smem = staged_smem_bytes(cap, qpb);
+    const dim3 grid((nq + qpb - 1) / qpb, g.S);
     prepare_staged(g);
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, nw * 32, smem, s>>>(d, l, colour);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, nw * 32, smem, s>>>(d, l, colour);
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb);
 }
 
 }  // namespace wmcd

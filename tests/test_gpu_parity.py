@@ -174,6 +174,19 @@ def test_whole_gpu_serial_moves(precision):
     assert sum(ref.stats().attempts[4:6]) > 0
 
 
+@pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])
+def test_coarse_layer_regions_staged_in_blocks_of_their_own(precision):
+    """64 chains x 64 beads at volume fraction 1e-3 with colour stride 3: the regions of the
+    coarsest coloured layer (about 512 beads each, 27 queues per colour) overflow the base
+    staging capacity, so each is staged by a whole block (all its warps stage, one runs the
+    moves) with the largest capacity shared memory allows."""
+    s = I.dilute_chains(64, 64, 1e-3, seed=7)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=5, precision=precision,
+                            planewave_mode=wmcd.PLANEWAVE_PERIODIC, colour_K=3)
+    assert p["grid_layer"][2] == 6
+    run_pair(p, s, 3)
+
+
 def test_free_spheres_and_fene():
     s = I.free_spheres(500, 3e-3, seed=7)
     p = wmcd.default_params(s.n_beads, s.box_L, seed=2, bond_type=wmcd.BOND_NONE)
