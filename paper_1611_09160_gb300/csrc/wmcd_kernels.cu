@@ -2721,7 +2721,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
 // every warp stages a share of the region (the binary64 work of staging spreads over the SM's
 // four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue.
 template <int PREC>
-__global__ void __launch_bounds__(kMaxStageWarps * 32) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
+__global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
                                                                         int cap, int qpb) {
     SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
                 (int)(blockIdx.x * qpb) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K))
