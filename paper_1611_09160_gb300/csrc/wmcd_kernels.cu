@@ -2260,12 +2260,13 @@ struct Stage {
     double *clam, *cV, *cp, *cthr;   // slot chunk: scale, centre offset, polarisation, threshold
     double *cR, *clamV, *cA0l;       // ... influence radius, lam V and A0 lam for the slot's own scale
     float *clamf, *cRf, *cVf, *cpf;  // ... binary32 forms of lam, R, V and p
+    float* cthrf;                    // ... and of the threshold
     int* cti;                        // ... staged index of the picked bead (-1: not staged)
     int cap, hbits;
 };
 __host__ __device__ inline size_t stage_bytes(int cap) {
     return (size_t)cap * (3 * 8 + 6 * 4 + 3 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
-           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8 + 8 + 24 + 8 + 4 + 4 + 4 + 12 + 12) + 160;
+           (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8 + 8 + 24 + 8 + 4 + 4 + 4 + 12 + 12 + 4) + 160;
 }
 __host__ __device__ inline size_t warp_stride(int cap) {
     size_t per = stage_bytes(cap) > sizeof(WarpSmem) ? stage_bytes(cap) : sizeof(WarpSmem);
@@ -2296,6 +2297,7 @@ __device__ inline Stage stage_carve(char* base, int cap) {
     S.cA0l = (double*)take(8 * kSlotChunk);
     S.clamf = (float*)take(4 * kSlotChunk); S.cRf = (float*)take(4 * kSlotChunk);
     S.cVf = (float*)take(4 * 3 * kSlotChunk); S.cpf = (float*)take(4 * 3 * kSlotChunk);
+    S.cthrf = (float*)take(4 * kSlotChunk);
     S.cti = (int*)take(4 * kSlotChunk);
     return S;
 }
@@ -2321,6 +2323,17 @@ __device__ __forceinline__ void local_split(double x, double o, double L, float&
 }
 // difference of two such coordinates: relative error about 2 ulp of binary32, no binary64 work
 __device__ __forceinline__ float dfd(float ha, float la, float hb, float lb) { return (ha - hb) + (la - lb); }
+// wrap and minimum image with the rare correction behind a branch that the lanes of `mask` take
+// together: written plainly, the correction's binary64 add is predicated and, on this part,
+// occupies the binary64 pipe even when no lane needs it
+__device__ __forceinline__ double wrap_u(double x, double L, unsigned mask, int* im) {
+    if (__any_sync(mask, ge_pos(x, L) || lt_zero(x))) x = wrap(x, L, im);
+    return x;
+}
+__device__ __forceinline__ double mi_u(double d, double L, double h, unsigned mask) {
+    if (__any_sync(mask, gt_pos(d, h) || lt_neg(d, h))) d = mi(d, L, h);
+    return d;
+}
 
 // binary32 constants of a launch, converted once
 struct Stage32 {
@@ -2329,6 +2342,7 @@ struct Stage32 {
     const double* sqrt_n;            // sqrt(n) for n <= kNCap, correctly rounded (as sqr_t)
     float side[3];                   // region side per axis
     int kappa_on, eps_on;            // external well, WCA
+    float kT9;                       // 1e-9 kT, the band's absolute floor
 };
 __device__ inline Stage32 stage32(const SimView& v) {
     Stage32 c;
@@ -2338,6 +2352,7 @@ __device__ inline Stage32 stage32(const SimView& v) {
     c.rcs2 = rcs * rcs;
     c.kappa_on = v.pot.kappa != 0.0;
     c.eps_on = v.pot.eps != 0.0;
+    c.kT9 = 1e-9f * (float)v.kT;
     return c;
 }
 
@@ -2547,9 +2562,9 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     const bool own = __double_as_longlong(lam) == __double_as_longlong(S.clam[c]);
     double b[3], lv[3];
     for (int a = 0; a < 3; a++) lv[a] = own ? S.clamV[3 * c + a] : mul(lam, S.cV[3 * c + a]);
-    b[0] = wrap(add(S.sx[ti], lv[0]), L, nullptr);
-    b[1] = wrap(add(S.sy[ti], lv[1]), L, nullptr);
-    b[2] = wrap(add(S.sz[ti], lv[2]), L, nullptr);
+    b[0] = wrap_u(add(S.sx[ti], lv[0]), L, FULL, nullptr);
+    b[1] = wrap_u(add(S.sy[ti], lv[1]), L, FULL, nullptr);
+    b[2] = wrap_u(add(S.sz[ti], lv[2]), L, FULL, nullptr);
     const double R = own ? S.cR[c] : add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
     const float lamf = own ? S.clamf[c] : (float)lam;
     // A_w = A0 lam / sqrt(n) (Eq. 29) for every support size up to 32, one per lane, formed
@@ -2622,10 +2637,11 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
     const float af = (float)Aw, pf[3] = {S.cpf[3 * c], S.cpf[3 * c + 1], S.cpf[3 * c + 2]};
     for (int k = lane; k < n; k += 32) {
+        const unsigned am = __activemask();
         const int t = S.mem[k];
         S.stag[t] = tag;
         const double o[3] = {S.sx[t], S.sy[t], S.sz[t]};
-        double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)};
+        double d[3] = {mi_u(sub(o[0], b[0]), L, hL, am), mi_u(sub(o[1], b[1]), L, hL, am), mi_u(sub(o[2], b[2]), L, hL, am)};
         double dl[3];
         float dlf3[3];
         if (PREC == 0) {
@@ -2638,7 +2654,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         int im[3] = {0, 0, 0};
         const float oh[3] = {S.hx[t], S.hy[t], S.hz[t]}, ol[3] = {S.lx[t], S.ly[t], S.lz[t]};
         for (int a = 0; a < 3; a++) {
-            S.mnp[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+            S.mnp[3 * k + a] = wrap_u(add(o[a], dl[a]), L, am, &im[a]);
             // new local coordinate = old + displacement, in binary32 pairs (two-sum, then
             // renormalised); local coordinates are continuous inside the region, no wrap
             const float dlf = dlf3[a];
@@ -2679,9 +2695,8 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         float d32 = 0.0f, m32 = 0.0f;
         int T = 0;
         stage_energy32(v, S, C, n, nc, all_cand, ns, tag, lane, &d32, &m32, &T, &pe);
-        const float thr32 = (float)thr;
-        const float band = 2.0f * (float)(80 + T + 6) * 5.9604645e-08f * m32 + 1e-9f * (float)v.kT +
-                           2.4e-7f * fabsf(thr32);
+        const float thr32 = S.cthrf[c];
+        const float band = 2.0f * (float)(80 + T + 6) * 5.9604645e-08f * m32 + C.kT9 + 2.4e-7f * fabsf(thr32);
         if (isfinite(d32) && isfinite(band) && fabsf(d32 - thr32) > band) {
             acc = d32 <= thr32;
             *du_out = (double)d32;
@@ -2834,6 +2849,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                 for (int a = 0; a < 3; a++) { S.cV[3 * lane + a] = V[a]; S.cp[3 * lane + a] = dvd(pp[a], r); }
                 const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
                 S.cthr[lane] = -v.kT * log(1.0 - u53(w.x, w.y));
+                S.cthrf[lane] = (float)S.cthr[lane];
                 // what the move needs from its own scale, ahead of the sequential loop
                 const double lam_s = S.clam[lane];
                 const double R_s = add(add(lam_s, mul(mul(0.25, v.A0), lam_s)), v.r_reach);
