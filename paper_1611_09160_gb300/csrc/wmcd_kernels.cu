@@ -2449,17 +2449,19 @@ __device__ void stage_energy64(const SimView& v, const Stage& S, const Stage32& 
 // magnitude sum and summation depth its error band needs. All terms (bonds to outside beads,
 // pairs inside the support, candidates) form one list dealt to the lanes, so a lane resolves
 // its item and then every lane evaluates the same potentials together.
-__device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand, int ns,
-                               int tag, int lane, float* dU32, float* mag32, int* terms, int* pe_out) {
+// This thread's share of the items (item w for w = i0, i0 + stride, ...): partial sums of the
+// change and of the magnitudes, terms added, candidates within reach.
+__device__ void stage_energy32_items(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand,
+                                     int ns, int tag, int i0, int stride, float& a32, float& m32, int& T, int& pe) {
     const double L = v.L, hL = v.halfL;
     const Pot32& P32 = C.P32;
     const float hLf = C.hLf;
     const float rcs2 = C.rcs2;
-    float a32 = 0.0f, m32 = 0.0f;
-    int T = 0, pe = 0;
+    a32 = 0.0f; m32 = 0.0f;
+    T = 0; pe = 0;
     // external well (rare: only with kappa != 0), from the binary64 positions
     if (C.kappa_on) {
-        for (int k = lane; k < n; k += 32) {
+        for (int k = i0; k < n; k += stride) {
             const int t = S.mem[k];
             const double* nw = &S.mnp[3 * k];
             float un = 0.5f * P32.kappa * norm2f(dif32(nw[0], hL, L, hLf), dif32(nw[1], hL, L, hLf), dif32(nw[2], hL, L, hLf));
@@ -2471,7 +2473,7 @@ __device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& 
     const int nsrc = all_cand ? ns : nc;
     const int nD = C.eps_on ? n * nsrc : 0;
     const int total = nB + nP + nD;
-    for (int w = lane; w < total; w += 32) {
+    for (int w = i0; w < total; w += stride) {
         // the item: new positions (na, nb), old positions (oa, ob); k >= 0 is a support member
         // (new position), k < 0 the staged bead -1 - k
         int na = 0, nb = 0, oa = 0, ob = 0;
@@ -2530,6 +2532,12 @@ __device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& 
         if (wca) { wca32(P32, r2[0], un, mn); wca32(P32, r2[1], uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
         if (bnd) { bond32(P32, r2[0], un, mn); bond32(P32, r2[1], uo, mo); a32 += un - uo; m32 += mn + mo; T += 2; }
     }
+}
+__device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& C, int n, int nc, bool all_cand, int ns,
+                               int tag, int lane, float* dU32, float* mag32, int* terms, int* pe_out) {
+    float a32, m32;
+    int T, pe;
+    stage_energy32_items(v, S, C, n, nc, all_cand, ns, tag, lane, 32, a32, m32, T, pe);
     const unsigned FULL = 0xffffffffu;
     float sm = a32, mm = m32;
     for (int o = 16; o > 0; o >>= 1) {
@@ -2543,12 +2551,27 @@ __device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& 
     *pe_out = (int)__reduce_add_sync(FULL, (unsigned)pe);
 }
 
+// What the warps of a block that serves one queue together share during a move.
+struct CoopSh {
+    int memw[kMaxStageWarps][kNCap];     // per warp: members found in its share of the scan
+    int candw[kMaxStageWarps][kCandCap]; // ... and candidates
+    int cnt[kMaxStageWarps][2];          // ... and their counts
+    float part[kMaxStageWarps][2];       // per warp: binary32 change and magnitude sums
+    int partT[kMaxStageWarps], partPE[kMaxStageWarps];
+    int bad;                             // a bonded partner is not staged: the move is deferred
+    int r[2];                            // outcome of the move, by parity of the move's tag
+};
+
 // One move of a staged queue. The slot's centre offset V, polarisation p and Metropolis
-// threshold were prepared in the chunk arrays at index c.
-template <int PREC>
+// threshold were prepared in the chunk arrays at index c. COOP: all H warps of the block call
+// this together (role = warp index); each scans a contiguous share of the staged beads and takes
+// a share of the binary32 energy items, warp 0 does the rest. Every branch around a block
+// barrier depends only on values every warp computed alike or read after a barrier, so all
+// warps meet every barrier. Warps other than 0 return 0 once their part is done.
+template <int PREC, bool COOP>
 __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C, int ns, const double org[3], float sidef,
                              int l, int c, double lam, const int64_t rlo[3], const int64_t rhi[3], int lane, int tag,
-                             int* n_out, int* pe_out, int* recheck_out, double* du_out) {
+                             int* n_out, int* pe_out, int* recheck_out, double* du_out, int H, int role, CoopSh* X) {
     const unsigned FULL = 0xffffffffu;
     const double L = v.L, hL = v.halfL;
     const int Gf = v.Gf;
@@ -2602,11 +2625,17 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     const float Rc = Rf + eps;
     const float rcand = Rc * Rc;
     int n = 0, nc = 0;
-    for (int base = 0; base < ns; base += 32) {
+    // the scan's share: all staged beads, or (COOP) a contiguous range, so that the warps' lists
+    // concatenated in warp order are the single scan's lists
+    const int qs = COOP ? ((ns + 32 * H - 1) / (32 * H)) * 32 : ns;
+    const int t_lo = COOP ? min(ns, role * qs) : 0, t_hi = COOP ? min(ns, t_lo + qs) : ns;
+    int* const lmem = COOP ? X->memw[role] : S.mem;
+    int* const lcand = COOP ? X->candw[role] : S.cand;
+    for (int base = t_lo; base < t_hi; base += 32) {
         const int t = base + lane;
         bool in = false, cd = false, tie = false;
         float d2 = 0.0f;
-        if (t < ns) {
+        if (t < t_hi) {
             const float dx = S.hx[t] - bh[0], dy = S.hy[t] - bh[1], dz = S.hz[t] - bh[2];
             d2 = dx * dx + dy * dy + dz * dz;
             in = d2 < lin;
@@ -2619,13 +2648,32 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
                 in = e2 < mul(lam, lam);
             }
         }
-        cd = t < ns && !in && d2 < rcand;
+        cd = t < t_hi && !in && d2 < rcand;
         const unsigned mi_ = __ballot_sync(FULL, in), mc = __ballot_sync(FULL, cd);
         const unsigned below = (1u << lane) - 1u;
-        if (in) { const int s = n + __popc(mi_ & below); if (s < kNCap) S.mem[s] = t; }
-        if (cd) { const int s = nc + __popc(mc & below); if (s < kCandCap) S.cand[s] = t; }
+        if (in) { const int s = n + __popc(mi_ & below); if (s < kNCap) lmem[s] = t; }
+        if (cd) { const int s = nc + __popc(mc & below); if (s < kCandCap) lcand[s] = t; }
         n += __popc(mi_);
         nc += __popc(mc);
+    }
+    if (COOP) {
+        if (lane == 0) { X->cnt[role][0] = n; X->cnt[role][1] = nc; }
+        __syncthreads();
+        const int nw = n, ncw = nc;
+        int om = 0, oc = 0;
+        n = 0; nc = 0;
+        for (int w = 0; w < H; w++) {
+            if (w == role) { om = n; oc = nc; }
+            n += X->cnt[w][0];
+            nc += X->cnt[w][1];
+        }
+        // in place only when the whole list fits (otherwise the move is deferred, or the
+        // candidates are taken from all staged beads)
+        if (n <= v.n_cap)
+            for (int k = lane; k < nw; k += 32) S.mem[om + k] = X->memw[role][k];
+        if (nc <= kCandCap)
+            for (int k = lane; k < ncw; k += 32) S.cand[oc + k] = X->candw[role][k];
+        __syncthreads();
     }
     __syncwarp();                                 // support and candidate lists are read by every lane
     *n_out = n;
@@ -2636,6 +2684,8 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     const double Aw = n <= 32 ? __shfl_sync(FULL, aw_lane, n - 1) : dvd(a0l, C.sqrt_n[n]);
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
     const float af = (float)Aw, pf[3] = {S.cpf[3 * c], S.cpf[3 * c + 1], S.cpf[3 * c + 2]};
+    bool bad = false;
+    if (!COOP || role == 0) {
     for (int k = lane; k < n; k += 32) {
         const unsigned am = __activemask();
         const int t = S.mem[k];
@@ -2669,7 +2719,6 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     }
     __syncwarp();
     // bonded partners: staged (inside the region) or the move is deferred
-    bool bad = false;
     for (int k = lane; k < n; k += 32) {
         const int tk = S.mem[k];
         const int m = S.sid[tk], fl = S.sdim[tk] >> 25;   // staged bond flags: 1 up, 2 down
@@ -2684,7 +2733,14 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
             S.mpart[2 * k + e] = tq;
         }
     }
-    if (__any_sync(FULL, bad)) return DEFER;
+    bad = __any_sync(FULL, bad);
+    }
+    if (COOP) {
+        if (role == 0 && lane == 0) X->bad = bad;
+        __syncthreads();
+        bad = X->bad != 0;
+    }
+    if (bad) return DEFER;
     __syncwarp();
     const double thr = S.cthr[c];
     bool acc;
@@ -2694,7 +2750,30 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         // band (per term 80 ulp of its magnitude, plus the summation) and in binary64 inside it
         float d32 = 0.0f, m32 = 0.0f;
         int T = 0;
-        stage_energy32(v, S, C, n, nc, all_cand, ns, tag, lane, &d32, &m32, &T, &pe);
+        if (COOP) {
+            // the items over every thread of the block; warp totals added by warp 0 in warp order
+            float a, m;
+            int Tt, pt;
+            stage_energy32_items(v, S, C, n, nc, all_cand, ns, tag, role * 32 + lane, 32 * H, a, m, Tt, pt);
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(FULL, a, o);
+                m += __shfl_xor_sync(FULL, m, o);
+            }
+            Tt = (int)__reduce_max_sync(FULL, (unsigned)Tt);
+            pt = (int)__reduce_add_sync(FULL, (unsigned)pt);
+            if (lane == 0) { X->part[role][0] = a; X->part[role][1] = m; X->partT[role] = Tt; X->partPE[role] = pt; }
+            __syncthreads();
+            if (role != 0) return 0;
+            for (int w = 0; w < H; w++) {
+                d32 += X->part[w][0];
+                m32 += X->part[w][1];
+                T = max(T, X->partT[w]);
+                pe += X->partPE[w];
+            }
+            T += 5 + H;      // summation depth: a thread's terms, the butterfly, the warp totals
+        } else {
+            stage_energy32(v, S, C, n, nc, all_cand, ns, tag, lane, &d32, &m32, &T, &pe);
+        }
         const float thr32 = S.cthrf[c];
         const float band = 2.0f * (float)(80 + T + 6) * 5.9604645e-08f * m32 + C.kT9 + 2.4e-7f * fabsf(thr32);
         if (isfinite(d32) && isfinite(band) && fabsf(d32 - thr32) > band) {
@@ -2709,6 +2788,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
             (*recheck_out)++;
         }
     } else {
+        if (COOP && role != 0) return 0;
         double d64 = 0.0;
         stage_energy64(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, &pe);
         acc = d64 <= thr;
@@ -2745,6 +2825,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
     // sqrt(n) for the amplitude A_w = A0 lam / sqrt(n) (Eq. 29), once per block
     __shared__ double s_sqrt[kNCap + 1];
+    __shared__ CoopSh s_coop;
     for (int i = threadIdx.x; i <= kNCap; i += blockDim.x) s_sqrt[i] = sqr_t((double)i);
     __syncthreads();
     const uint64_t sweep = v.step[0];
@@ -2823,13 +2904,12 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
             }
         }
         if (H > 1) __syncthreads(); else __syncwarp();
-        if (role != 0) return;                    // the moves run on one warp
         int tag = 0;
         for (int c0 = 0; c0 < cnt; c0 += kSlotChunk) {
-            // slot parameters of the chunk, one lane per slot: V, p by rejection (Appendix D)
-            // and the Metropolis threshold -kT ln(1 - u) (Eq. 20)
+            // slot parameters of the chunk, one lane of warp 0 per slot: V, p by rejection
+            // (Appendix D) and the Metropolis threshold -kT ln(1 - u) (Eq. 20)
             const int t = c0 + lane;
-            if (t < cnt) {
+            if (role == 0 && t < cnt) {
                 const int j = v.q_slots[start + t];
                 S.cj[lane] = j;
                 S.ci[lane] = v.slot_bead[j];
@@ -2864,7 +2944,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                 }
                 S.cti[lane] = stage_find(S, S.ci[lane]);
             }
-            __syncwarp();
+            if (H > 1) __syncthreads(); else __syncwarp();
             const int cend = min(kSlotChunk, cnt - c0);
             for (int cc = 0; cc < cend; cc++) {
                 const int j = S.cj[cc];
@@ -2872,20 +2952,34 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                 int n = 0;
                 double du = 0.0;
                 tag++;
-                const int r = stage_attempt<PREC>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe, &rechecks, &du);
-                __syncwarp();
-                if (r == DEFER) { if (lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
+                int r;
+                if (H > 1) {
+                    r = stage_attempt<PREC, true>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
+                                                  &rechecks, &du, H, role, &s_coop);
+                    __syncwarp();
+                    // warp 0's outcome (and its commit) reach every warp before the next move
+                    if (role == 0 && lane == 0) s_coop.r[tag & 1] = r;
+                    __syncthreads();
+                    r = s_coop.r[tag & 1];
+                } else {
+                    r = stage_attempt<PREC, false>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
+                                                   &rechecks, &du, 1, 0, nullptr);
+                    __syncwarp();
+                }
+                if (r == DEFER) { if (role == 0 && lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
                 att++; bu += n;
                 if (r == ACCEPT) { acc++; moved += n; }
-                if (lane == 0) {
+                if (role == 0 && lane == 0) {
                     v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
                     v.tr_n[Ly.tr_off + j] = n;
                     v.tr_du[Ly.tr_off + j] = du;
                 }
                 carry = (r == ACCEPT) ? 0.0 : lam;
             }
-            __syncwarp();
+            // the chunk arrays are refilled only after every warp has finished this chunk
+            if (H > 1) __syncthreads(); else __syncwarp();
         }
+        if (role != 0) return;                    // the write-back runs on warp 0
         // write back the moved beads (lanes in parallel); cell-list moves by lane 0, in
         // staged order, for the beads whose fine cell changed (the old cell from the bead's
         // record, which nothing else writes during the phase)
@@ -2941,8 +3035,9 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
 
 size_t staged_smem_bytes(int cap, int warps) { return (size_t)warps * warp_stride(cap); }
 static bool staged_fits(int cap, int queues) {
-    // dynamic shared memory + the static view copy and sqrt table within the 227 KB of a block
-    return staged_smem_bytes(cap, queues) + sizeof(SimView) + 1024 <= 227u * 1024u;
+    // dynamic shared memory + the static view copy, sqrt table and cooperative scratch within the
+    // 227 KB of a block
+    return staged_smem_bytes(cap, queues) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
 }
 int staged_cap_max() {
     int cap = 256;
