@@ -12,6 +12,18 @@ namespace wmcd {
 
 __device__ __forceinline__ void set_err(const SimView& v, int bit) { atomicOr(v.err, bit); }
 
+// wrap and minimum image with the rare correction behind a branch that the lanes of `mask` take
+// together: written plainly, the correction's binary64 add is predicated and, on this part,
+// occupies the binary64 pipe even when no lane needs it
+__device__ __forceinline__ double wrap_u(double x, double L, unsigned mask, int* im) {
+    if (__any_sync(mask, ge_pos(x, L) || lt_zero(x))) x = wrap(x, L, im);
+    return x;
+}
+__device__ __forceinline__ double mi_u(double d, double L, double h, unsigned mask) {
+    if (__any_sync(mask, gt_pos(d, h) || lt_neg(d, h))) d = mi(d, L, h);
+    return d;
+}
+
 // Every kernel serves a group of simulations: blockIdx.y selects one, whose view is copied
 // into shared memory once per block. SIM_EXIT_IF tests a condition on the view in global
 // memory first, so blocks of a simulation with no work in this launch leave without the copy.
@@ -821,7 +833,7 @@ __global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
 }
 
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, int l) {
+__global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs, int l) {
     SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || (((gv.smem_layers | gv.big_layers) >> l) & 1))
     SIM_PROLOGUE
     if (l >= v.nL || v.precision != PREC || (((v.smem_layers | v.big_layers) >> l) & 1)) return;
@@ -891,12 +903,11 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
         const float bxf = sh_bf[0], byf = sh_bf[1], bzf = sh_bf[2];
         const float rl2f = sh_rl2f;
         auto wrapg = [&](float f) { return fabsf(f) > hLf ? f - copysignf(Lf, f) : f; };
-        auto consider = [&](int m, const Bead& bb) {
-            {
-                const BeadF f = v.bf[m];
-                const float sx = wrapg(f.hx - bxf), sy = wrapg(f.hy - byf), sz = wrapg(f.hz - bzf);
-                if (sx * sx + sy * sy + sz * sz > rl2f) return;
-            }
+        auto screened = [&](const BeadF& f) {
+            const float sx = wrapg(f.hx - bxf), sy = wrapg(f.hy - byf), sz = wrapg(f.hz - bzf);
+            return sx * sx + sy * sy + sz * sz <= rl2f;
+        };
+        auto consider_exact = [&](int m, const Bead& bb) {
             double d0 = mi(sub(bb.x, b[0]), L, hL), d1 = mi(sub(bb.y, b[1]), L, hL), d2c = mi(sub(bb.z, b[2]), L, hL);
             double d2 = norm2(d0, d1, d2c);
             if (d2 < lam2) {
@@ -905,20 +916,44 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
                 v.s_d[4 * idx] = d0; v.s_d[4 * idx + 1] = d1; v.s_d[4 * idx + 2] = d2c; v.s_d[4 * idx + 3] = d2;
             }
         };
+        // four independent loads in flight per thread (the shadows of four beads, or the heads
+        // of four cells) before any is used
         if (sh_brute) {
-            for (int64_t m = tid; m < v.N; m += NT) consider((int)m, v.bead[m]);
+            for (int64_t m0 = tid; m0 < v.N; m0 += 4 * (int64_t)NT) {
+                BeadF f[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t m = m0 + (int64_t)u * NT;
+                    if (m < v.N) f[u] = v.bf[m];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t m = m0 + (int64_t)u * NT;
+                    if (m < v.N && screened(f[u])) consider_exact((int)m, v.bead[m]);
+                }
+            }
         } else {
             const int c0[3] = {sh_c0[0], sh_c0[1], sh_c0[2]}, nc[3] = {sh_nc[0], sh_nc[1], sh_nc[2]};
             const int ncell = nc[0] * nc[1] * nc[2];
-            for (int k = tid; k < ncell; k += NT) {
-                int kx = k % nc[0], ky = (k / nc[0]) % nc[1], kz = k / (nc[0] * nc[1]);
-                int cell = wrapi(c0[0] + kx, v.Gf) + v.Gf * (wrapi(c0[1] + ky, v.Gf) + v.Gf * wrapi(c0[2] + kz, v.Gf));
-                int guard = 0;
-                for (int q = v.head[cell]; q >= 0;) {
-                    Bead bb = v.bead[q];
-                    consider(q, bb);
-                    q = bb.next;
-                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+            for (int k0 = tid; k0 < ncell; k0 += 4 * NT) {
+                int hd[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int k = k0 + u * NT;
+                    hd[u] = -1;
+                    if (k < ncell) {
+                        const int kx = k % nc[0], ky = (k / nc[0]) % nc[1], kz = k / (nc[0] * nc[1]);
+                        hd[u] = v.head[wrapi(c0[0] + kx, v.Gf) + v.Gf * (wrapi(c0[1] + ky, v.Gf) + v.Gf * wrapi(c0[2] + kz, v.Gf))];
+                    }
+                }
+                for (int u = 0; u < 4; u++) {
+                    int guard = 0;
+                    for (int q = hd[u]; q >= 0;) {
+                        const Bead bb = v.bead[q];
+                        if (screened(v.bf[q])) consider_exact(q, bb);
+                        q = bb.next;
+                        if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                    }
                 }
             }
         }
@@ -949,8 +984,9 @@ __global__ void __launch_bounds__(NT) k_serial(const SimView* __restrict__ vs, i
             else wavelet_disp32(d, lam, Aw, p, dl);
             const double o[3] = {v.bead[m].x, v.bead[m].y, v.bead[m].z};
             int im[3] = {0, 0, 0};
+            const unsigned am = __activemask();
             for (int a = 0; a < 3; a++) {
-                v.s_new[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+                v.s_new[3 * k + a] = wrap_u(add(o[a], dl[a]), L, am, &im[a]);
                 v.s_d[4 * k + a] = dl[a];        // keep the displacement for the partner boxes
             }
             v.s_img[k] = pack_img(im[0], im[1], im[2]);
@@ -2323,17 +2359,6 @@ __device__ __forceinline__ void local_split(double x, double o, double L, float&
 }
 // difference of two such coordinates: relative error about 2 ulp of binary32, no binary64 work
 __device__ __forceinline__ float dfd(float ha, float la, float hb, float lb) { return (ha - hb) + (la - lb); }
-// wrap and minimum image with the rare correction behind a branch that the lanes of `mask` take
-// together: written plainly, the correction's binary64 add is predicated and, on this part,
-// occupies the binary64 pipe even when no lane needs it
-__device__ __forceinline__ double wrap_u(double x, double L, unsigned mask, int* im) {
-    if (__any_sync(mask, ge_pos(x, L) || lt_zero(x))) x = wrap(x, L, im);
-    return x;
-}
-__device__ __forceinline__ double mi_u(double d, double L, double h, unsigned mask) {
-    if (__any_sync(mask, gt_pos(d, h) || lt_neg(d, h))) d = mi(d, L, h);
-    return d;
-}
 
 // binary32 constants of a launch, converted once
 struct Stage32 {
