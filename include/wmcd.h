@@ -70,7 +70,7 @@ typedef struct wmcd_params {
        phase, so results do not depend on these values except through that order */
     int32_t colour_K;         /* colours per axis, 2..4 */
     int32_t grid_f;           /* fine (cell-list) cells per axis, L / grid_f >= WCA cutoff */
-    int32_t n_cap;            /* largest support a concurrent move handles (1..64) */
+    int32_t n_cap;            /* largest support a concurrent move handles (1..256) */
     int32_t grid_layer[WMCD_MAX_LAYERS];  /* coarse cells per axis per layer; 0 = serial;
                                              otherwise a multiple of colour_K, at most 256 */
     int32_t big_support;      /* a serial layer whose expected support (N times the volume of a
@@ -109,7 +109,7 @@ typedef struct wmcd_handle wmcd_handle;
  * chains (free beads are chains of length 1); the lengths must sum to N.
  * Validates: N >= 1; 0 < lambda_min < lambda_max <= L/2; A0 > 0; kT > 0; colour_K in 2..4;
  * grid_f >= 1 with L/grid_f >= the WCA cutoff 2^(1/6) sigma (when WCA is on);
- * 1 <= n_cap <= 64; each grid_layer[l] is 0 or a multiple of colour_K in [colour_K, 256];
+ * 1 <= n_cap <= 256; each grid_layer[l] is 0 or a multiple of colour_K in [colour_K, 256];
  * at most 16 octave layers; lcut in 0..120 with plane waves. Returns WMCD_EINVAL otherwise.
  * Synchronises `stream` before returning. *out receives the handle. */
 int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,

@@ -182,7 +182,7 @@ static int validate(const wmcd_params* p) {
         p->lambda_max > 0.5 * p->box_L || !(p->A0 > 0.0) || !(p->kT > 0.0))
         return WMCD_EINVAL;
     if (p->bond_type < 0 || p->bond_type > 2 || p->colour_K < 2 || p->colour_K > 4 || p->grid_f < 1 ||
-        p->n_cap < 1 || p->n_cap > kNCap || p->precision < 0 || p->precision > 1)
+        p->n_cap < 1 || p->n_cap > kNCapMax || p->precision < 0 || p->precision > 1)
         return WMCD_EINVAL;
     if (p->planewave_mode == 1 && (p->lcut < 0 || p->lcut > 120)) return WMCD_EINVAL;
     if (p->planewave_mode != 0 && p->planewave_mode != 1) return WMCD_EINVAL;
@@ -398,6 +398,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 0;
         g.S = 1;
+        g.ncap = P.n_cap;
         g.maxN = N;
         g.maxCells = std::max<int64_t>(ncell, 1);
         g.maxL = nL;
@@ -423,7 +424,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
             // region in a block of its own (a coarse layer of a dilute system): no queue waits
             // for an SM, and moves avoid the global cell walks
             const double region = G > 0 ? (double)N * std::pow((double)P.colour_K / G, 3.0) : 0.0;
-            const int cmax = staged_cap_max();
+            const int cmax = staged_cap_max(P.n_cap);
             g.cap_l[l] = (G > 0 && Q * Q * Q <= n_sm && region > 0.8 * v.stage_cap && region <= 0.8 * cmax) ? cmax : 0;
         }
     }

@@ -128,6 +128,7 @@ static GroupDims group_bounds(const std::vector<Member>& ms, int block_warps, in
         g.maxK3 = std::max(g.maxK3, o.maxK3);
         g.maxMF = std::max(g.maxMF, o.maxMF);
         g.stage_cap = std::max(g.stage_cap, o.stage_cap);
+        g.ncap = std::max(g.ncap, o.ncap);
         g.pw_blocks = std::max(g.pw_blocks, o.pw_blocks);
         g.pw = g.pw || o.pw;
         g.prec_mask |= o.prec_mask;

@@ -37,7 +37,8 @@ __device__ __forceinline__ void put_bead(Bead* bead, BeadF* bf, int64_t m, doubl
 }
 
 constexpr int kMaxLayers = 16;
-constexpr int kNCap = 64;          // largest support of a concurrent (warp) move
+constexpr int kNCap = 64;          // supports up to this size take sqrt(n) from a table
+constexpr int kNCapMax = 256;      // largest n_cap: support of a concurrent move
 constexpr int kWarpsPerBlock = 4;  // concurrent kernel: one warp per queue
 constexpr int kSerialThreads = 512;
 constexpr int kMaxWalk = 1 << 22;  // bound on list-walk iterations inside one move
@@ -182,6 +183,7 @@ struct GroupDims {
     int64_t maxN = 1, maxCells = 1;
     int maxL = 0, maxK3 = 1, maxMF = 0, stage_cap = 256, pw_blocks = 1;
     int cap_l[kMaxLayers] = {0};  // staging capacity of a coloured layer when above stage_cap
+    int ncap = kNCap;            // largest n_cap of the group (sizes the staged support arrays)
     int Mmax[kMaxLayers] = {0}, keys[kMaxLayers] = {0}, nq[kMaxLayers] = {0};
     bool coloured[kMaxLayers] = {false};
     bool pw = false;
@@ -212,8 +214,8 @@ constexpr int64_t kSmemClassHi[3] = {320, 1024, 1 << 30};
 int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj);  // kernels launched
 int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
 int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t s);     // kernels launched
-size_t staged_smem_bytes(int cap, int warps);
-int staged_cap_max();            // most beads one queue can stage (a block of one queue)
+size_t staged_smem_bytes(int cap, int warps, int ncap);
+int staged_cap_max(int ncap);    // most beads one queue can stage (a block of one queue)
 size_t smem_serial_bytes(int64_t n);
 // open the kernels that take large dynamic shared memory for the sizes of g (before a graph
 // capture: a recorded launch sets nothing)

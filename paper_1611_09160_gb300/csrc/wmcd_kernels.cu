@@ -330,15 +330,15 @@ namespace wmcd {
 // Concurrent wavelet moves: one warp per queue (coarse cell) of one colour.
 // ======================================================================================
 struct WarpSmem {
-    int ids[kNCap];          // support, in gather order
-    double d[kNCap][4];      // exact minimum-image offset from the centre, and its square
-    double op[kNCap][3];     // old positions
-    double np[kNCap][3];     // new (wrapped) positions
-    double nu[kNCap][3];     // new unwrapped positions (old + delta)
-    int dimg[kNCap];         // packed image change
-    int sid[kNCap];          // support ids ascending
-    int cpre[kNCap + 1];     // prefix of partner-search columns per member
-    int cbox[kNCap][6];      // partner-search box per member: first cell c0[3], cells nc[3]
+    int ids[kNCapMax];          // support, in gather order
+    double d[kNCapMax][4];      // exact minimum-image offset from the centre, and its square
+    double op[kNCapMax][3];     // old positions
+    double np[kNCapMax][3];     // new (wrapped) positions
+    double nu[kNCapMax][3];     // new unwrapped positions (old + delta)
+    int dimg[kNCapMax];         // packed image change
+    int sid[kNCapMax];          // support ids ascending
+    int cpre[kNCapMax + 1];     // prefix of partner-search columns per member
+    int cbox[kNCapMax][6];      // partner-search box per member: first cell c0[3], cells nc[3]
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -671,7 +671,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
                     }
                     const unsigned msk = __ballot_sync(FULL, in);
                     const int slot = n + __popc(msk & ((1u << lane) - 1u));
-                    if (in && slot < kNCap) {
+                    if (in && slot < kNCapMax) {
                         sm.ids[slot] = ptr;
                         sm.op[slot][0] = bb.x; sm.op[slot][1] = bb.y; sm.op[slot][2] = bb.z;
                     }
@@ -2298,19 +2298,20 @@ struct Stage {
     float *clamf, *cRf, *cVf, *cpf;  // ... binary32 forms of lam, R, V and p
     float* cthrf;                    // ... and of the threshold
     int* cti;                        // ... staged index of the picked bead (-1: not staged)
-    int cap, hbits;
+    int cap, hbits, ncap;            // staged beads, hash bits, support capacity
 };
-__host__ __device__ inline size_t stage_bytes(int cap) {
-    return (size_t)cap * (3 * 8 + 6 * 4 + 3 * 4 + 2 * 2 * 4) + (size_t)kNCap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
+__host__ __device__ inline size_t stage_bytes(int cap, int ncap) {
+    return (size_t)cap * (3 * 8 + 6 * 4 + 3 * 4 + 2 * 2 * 4) + (size_t)ncap * (4 + 4 + 2 * 4 + 3 * 8 + 6 * 4) +
            (size_t)kCandCap * 4 + (size_t)kSlotChunk * (4 + 4 + 8 + 24 + 24 + 8 + 8 + 24 + 8 + 4 + 4 + 4 + 12 + 12 + 4) + 160;
 }
-__host__ __device__ inline size_t warp_stride(int cap) {
-    size_t per = stage_bytes(cap) > sizeof(WarpSmem) ? stage_bytes(cap) : sizeof(WarpSmem);
+__host__ __device__ inline size_t warp_stride(int cap, int ncap) {
+    size_t per = stage_bytes(cap, ncap) > sizeof(WarpSmem) ? stage_bytes(cap, ncap) : sizeof(WarpSmem);
     return (per + 15) & ~(size_t)15;
 }
-__device__ inline Stage stage_carve(char* base, int cap) {
+__device__ inline Stage stage_carve(char* base, int cap, int ncap) {
     Stage S;
     S.cap = cap;
+    S.ncap = ncap;
     // hash table: the largest power of two that fits its 2 cap entries (load factor <= 1/2 for
     // power-of-two capacities, < 1 for any other)
     S.hbits = 1;
@@ -2318,15 +2319,15 @@ __device__ inline Stage stage_carve(char* base, int cap) {
     char* p = base;
     auto take = [&](size_t bytes) { char* q = p; p += (bytes + 7) & ~(size_t)7; return q; };
     S.sx = (double*)take(8 * cap); S.sy = (double*)take(8 * cap); S.sz = (double*)take(8 * cap);
-    S.mnp = (double*)take(8 * 3 * kNCap);
+    S.mnp = (double*)take(8 * 3 * ncap);
     S.clam = (double*)take(8 * kSlotChunk); S.cV = (double*)take(8 * 3 * kSlotChunk);
     S.cp = (double*)take(8 * 3 * kSlotChunk); S.cthr = (double*)take(8 * kSlotChunk);
     S.hx = (float*)take(4 * cap); S.hy = (float*)take(4 * cap); S.hz = (float*)take(4 * cap);
     S.lx = (float*)take(4 * cap); S.ly = (float*)take(4 * cap); S.lz = (float*)take(4 * cap);
-    S.mnh = (float*)take(4 * 3 * kNCap); S.mnl = (float*)take(4 * 3 * kNCap);
+    S.mnh = (float*)take(4 * 3 * ncap); S.mnl = (float*)take(4 * 3 * ncap);
     S.sid = (int*)take(4 * cap); S.sdim = (int*)take(4 * cap); S.stag = (int*)take(4 * cap);
     S.hkey = (int*)take(4 * 2 * cap); S.hval = (int*)take(4 * 2 * cap);
-    S.mem = (int*)take(4 * kNCap); S.mimg = (int*)take(4 * kNCap); S.mpart = (int*)take(4 * 2 * kNCap);
+    S.mem = (int*)take(4 * ncap); S.mimg = (int*)take(4 * ncap); S.mpart = (int*)take(4 * 2 * ncap);
     S.cand = (int*)take(4 * kCandCap);
     S.cj = (int*)take(4 * kSlotChunk); S.ci = (int*)take(4 * kSlotChunk);
     S.cR = (double*)take(8 * kSlotChunk); S.clamV = (double*)take(8 * 3 * kSlotChunk);
@@ -2578,7 +2579,7 @@ __device__ void stage_energy32(const SimView& v, const Stage& S, const Stage32& 
 
 // What the warps of a block that serves one queue together share during a move.
 struct CoopSh {
-    int memw[kMaxStageWarps][kNCap];     // per warp: members found in its share of the scan
+    int memw[kMaxStageWarps][kNCapMax];  // per warp: members found in its share of the scan
     int candw[kMaxStageWarps][kCandCap]; // ... and candidates
     int cnt[kMaxStageWarps][2];          // ... and their counts
     float part[kMaxStageWarps][2];       // per warp: binary32 change and magnitude sums
@@ -2676,7 +2677,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         cd = t < t_hi && !in && d2 < rcand;
         const unsigned mi_ = __ballot_sync(FULL, in), mc = __ballot_sync(FULL, cd);
         const unsigned below = (1u << lane) - 1u;
-        if (in) { const int s = n + __popc(mi_ & below); if (s < kNCap) lmem[s] = t; }
+        if (in) { const int s = n + __popc(mi_ & below); if (s < S.ncap) lmem[s] = t; }
         if (cd) { const int s = nc + __popc(mc & below); if (s < kCandCap) lcand[s] = t; }
         n += __popc(mi_);
         nc += __popc(mc);
@@ -2706,7 +2707,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     if (n == 0) return ACCEPT;                    // no bead moves; dU = 0 passes
     const bool all_cand = nc > kCandCap;
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
-    const double Aw = n <= 32 ? __shfl_sync(FULL, aw_lane, n - 1) : dvd(a0l, C.sqrt_n[n]);
+    const double Aw = n <= 32 ? __shfl_sync(FULL, aw_lane, n - 1) : dvd(a0l, n <= kNCap ? C.sqrt_n[n] : sqr_t((double)n));
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
     const float af = (float)Aw, pf[3] = {S.cpf[3 * c], S.cpf[3 * c + 1], S.cpf[3 * c + 2]};
     bool bad = false;
@@ -2842,7 +2843,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
 // four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue.
 template <int PREC>
 __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
-                                                                        int cap, int qpb) {
+                                                                        int cap, int qpb, int ncap) {
     SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
                 (int)(blockIdx.x * qpb) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K))
     SIM_PROLOGUE
@@ -2864,7 +2865,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     const int key = colour * nq + q;
     const int start = v.q_start[key], cnt = v.q_count[key];
     if (cnt == 0) return;
-    char* base = dsm + (size_t)wib * warp_stride(cap);
+    char* base = dsm + (size_t)wib * warp_stride(cap, ncap);
     const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
     int64_t rlo[3], rhi[3];
     for (int a = 0; a < 3; a++) {
@@ -2898,7 +2899,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
             carry = (r == ACCEPT) ? 0.0 : lam;
         }
     } else {
-        Stage S = stage_carve(base, cap);
+        Stage S = stage_carve(base, cap, ncap);
         Stage32 C32 = stage32(v);
         C32.sqrt_n = s_sqrt;
         for (int a = 0; a < 3; a++) C32.side[a] = (float)((double)(rhi[a] - rlo[a] + 1) * (v.L / v.Gf));
@@ -3058,25 +3059,28 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     }
 }
 
-size_t staged_smem_bytes(int cap, int warps) { return (size_t)warps * warp_stride(cap); }
-static bool staged_fits(int cap, int queues) {
+size_t staged_smem_bytes(int cap, int warps, int ncap) { return (size_t)warps * warp_stride(cap, ncap); }
+static bool staged_fits(int cap, int queues, int ncap) {
     // dynamic shared memory + the static view copy, sqrt table and cooperative scratch within the
     // 227 KB of a block
-    return staged_smem_bytes(cap, queues) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
+    return staged_smem_bytes(cap, queues, ncap) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
 }
-int staged_cap_max() {
+int staged_cap_max(int ncap) {
     int cap = 256;
-    while (staged_fits(cap + 32, 1)) cap += 32;
+    while (staged_fits(cap + 32, 1, ncap)) cap += 32;
     return cap;
 }
-// staging capacity of layer l's launches (the largest over the group)
-static int layer_cap(const GroupDims& g, int l) { return std::max(g.stage_cap, g.cap_l[l]); }
+// staging capacity of layer l's launches (the largest over the group, within one block's shared
+// memory: a region above it takes the global-memory path)
+static int layer_cap(const GroupDims& g, int l) {
+    return std::min(std::max(g.stage_cap, g.cap_l[l]), staged_cap_max(g.ncap));
+}
 // queues per block actually used: the requested count, lowered until the block's shared memory
 // fits; a block of one queue with a region larger than 1,024 beads gets kMaxStageWarps warps,
 // which share the staging
 static void staged_shape(const GroupDims& g, int cap, int* qpb, int* warps) {
     int nw = std::max(1, std::min(g.block_warps, kMaxStageWarps));
-    while (nw > 1 && !staged_fits(cap, nw)) nw--;
+    while (nw > 1 && !staged_fits(cap, nw, g.ncap)) nw--;
     *qpb = nw;
     *warps = (nw == 1 && cap > 1024) ? kMaxStageWarps : nw;
 }
@@ -3110,7 +3114,7 @@ void prepare_staged(const GroupDims& g) {
         const int cap = layer_cap(g, l);
         int qpb = 1, warps = 1;
         staged_shape(g, cap, &qpb, &warps);
-        smem = std::max(smem, (int)staged_smem_bytes(cap, qpb));
+        smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, g.ncap));
     }
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
         cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -3132,12 +3136,12 @@ void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colou
     const int cap = layer_cap(g, l);
     int qpb = 1, warps = 1;
     staged_shape(g, cap, &qpb, &warps);
-    const size_t smem = staged_smem_bytes(cap, qpb);
+    const size_t smem = staged_smem_bytes(cap, qpb, g.ncap);
     const dim3 grid((nq + qpb - 1) / qpb, g.S);
     prepare_staged(g);
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb);
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap);
 }
 
 }  // namespace wmcd

@@ -175,6 +175,20 @@ def test_whole_gpu_serial_moves(precision):
 
 
 @pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])
+def test_large_supports_run_concurrently(precision):
+    """Chains at volume fraction 0.15 with a coloured layer of scales 4-8 (supports up to about
+    100 beads) and n_cap = 256: moves with more than 64 members run in the concurrent phase (the
+    whole-box region staged by one block whose warps cooperate) instead of being deferred."""
+    s = I.make_system([32] * 64, 0, I.box_for_volume_fraction(2048, 0.15), seed=13)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=7, precision=precision, colour_K=3, n_cap=256)
+    p["grid_layer"] = [6, 3] + [0] * 14
+    gpu, ref = run_pair(p, s, 3)
+    a, na = gpu.trace(1)
+    concurrent = ((a & 3) != 0) & ((a & 4) == 0)
+    assert (na[concurrent] > 64).any()
+
+
+@pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])
 def test_coarse_layer_regions_staged_in_blocks_of_their_own(precision):
     """64 chains x 64 beads at volume fraction 1e-3 with colour stride 3: the regions of the
     coarsest coloured layer (about 512 beads each, 27 queues per colour) overflow the base

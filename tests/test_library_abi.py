@@ -57,7 +57,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     h = ctypes.c_void_p()
     pos = np.zeros((10, 3))
     cl = np.array([10], np.int32)
-    bad = [dict(lambda_max=30.0), dict(lambda_min=0.0), dict(A0=-1.0), dict(colour_K=5), dict(n_cap=65),
+    bad = [dict(lambda_max=30.0), dict(lambda_min=0.0), dict(A0=-1.0), dict(colour_K=5), dict(n_cap=257),
            dict(grid_f=100)]       # L/grid_f below the WCA cutoff
     for b in bad:
         q = wmcd.make_params(dict(wmcd.default_params(10, 50.0), **b))
