@@ -1404,10 +1404,10 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     for (int j = 0; j < count; j++) {
         const int i = v.slot_bead[j];
         if (tid == 0) {
-            const double lam0 = sh_carry > 0.0 ? sh_carry : v.slot_lam[j];
+            const double lam0 = __double_as_longlong(sh_carry) > 0 ? sh_carry : v.slot_lam[j];
             const double ri[3] = {px[i], py[i], pz[i]};
             for (int a = 0; a < 3; a++) {
-                sh_b[a] = wrap(add(ri[a], mul(lam0, v.slot_V[3 * j + a])), L, nullptr);
+                sh_b[a] = wrap_u(add(ri[a], mul(lam0, v.slot_V[3 * j + a])), L, 1u, nullptr);
                 sh_p[a] = v.slot_p[3 * j + a];
                 sh_bf[a] = (float)sh_b[a];
             }
@@ -1429,8 +1429,9 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                 dy = fabsf(dy) > hLf ? dy - copysignf(Lf, dy) : dy;
                 dz = fabsf(dz) > hLf ? dz - copysignf(Lf, dz) : dz;
                 if (dx * dx + dy * dy + dz * dz > rl2) continue;
-                const double d0 = mi(sub(px[m], b[0]), L, hL), d1 = mi(sub(py[m], b[1]), L, hL),
-                             d2c = mi(sub(pz[m], b[2]), L, hL);
+                const unsigned am = __activemask();
+                const double d0 = mi_u(sub(px[m], b[0]), L, hL, am), d1 = mi_u(sub(py[m], b[1]), L, hL, am),
+                             d2c = mi_u(sub(pz[m], b[2]), L, hL, am);
                 if (norm2(d0, d1, d2c) < lam2) mid[atomicAdd(&sh_n, 1)] = m;
             }
         }
@@ -1456,15 +1457,17 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             lamf = (float)lam; af = (float)Aw; pf[0] = (float)p[0]; pf[1] = (float)p[1]; pf[2] = (float)p[2];
         }
         for (int k = tid; k < n; k += NT) {
+            const unsigned am = __activemask();
             const int m = mid[k];
             const double o[3] = {px[m], py[m], pz[m]};
-            double d[3] = {mi(sub(o[0], b[0]), L, hL), mi(sub(o[1], b[1]), L, hL), mi(sub(o[2], b[2]), L, hL)}, dl[3];
+            double d[3] = {mi_u(sub(o[0], b[0]), L, hL, am), mi_u(sub(o[1], b[1]), L, hL, am), mi_u(sub(o[2], b[2]), L, hL, am)},
+                   dl[3];
             if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
             else wavelet_disp32f(d, lamf, af, pf, dl);
             int im[3] = {0, 0, 0};
             const float oh[3] = {fx[m], fy[m], fz[m]}, ol[3] = {lx[m], ly[m], lz[m]};
             for (int a = 0; a < 3; a++) {
-                mnew[3 * k + a] = wrap(add(o[a], dl[a]), L, &im[a]);
+                mnew[3 * k + a] = wrap_u(add(o[a], dl[a]), L, am, &im[a]);
                 if (im[a] == 0) {
                     // old (hi, lo) plus the displacement by a binary32 two-sum, renormalised
                     const float dlf = (float)dl[a];
