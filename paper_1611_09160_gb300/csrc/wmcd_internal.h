@@ -47,6 +47,7 @@ constexpr int kMaxStageWarps = 4;  // ... and the most a block may have
 constexpr int kCandCap = 256;      // interaction candidates of one staged move held in shared memory
 constexpr int kSlotChunk = 32;     // slot parameters prepared per chunk
 constexpr int kSmemSerialMaxN = 2048;
+constexpr int kSmemCand = 1024;    // interaction candidates of one shared-memory serial move
 constexpr int kSmemThreads = 512;  // threads of the shared-memory serial block (many warps hide the
                                    // latency of the scans over all staged beads)  // largest simulation whose serial phase runs in shared memory
 

@@ -1361,10 +1361,13 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     float* mnf = lz + N;                         // 3 per member: new position, hi ...
     float* mnl = mnf + 3 * (size_t)N;            // ... and lo
     int* mid = (int*)(mnl + 3 * (size_t)N);      // support, in gather order
-    int* sslot = mid + N;                        // per bead: index in the support or -1
-    short* dimg = (short*)(sslot + N);           // 3 per bead: image change over the launch
+    short* sslot = (short*)(mid + N);            // per bead: index in the support or -1
+    short* dimg = sslot + N;                     // 3 per bead: image change over the launch
     uint8_t* mimg = (uint8_t*)(dimg + 3 * (size_t)N);   // per member: packed image change of the move
     uint8_t* bn = mimg + N;                      // bond to the next bead
+    __shared__ int s_cand[kSmemCand];            // beads within reach of the move, not in the support
+    __shared__ int sh_nc;
+    __shared__ float sh_rR2;
     __shared__ double sh_b[3], sh_p[3], sh_carry;
     __shared__ double sh_red[NT / 32];
     __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
@@ -1415,24 +1418,40 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             sh_lam2 = mul(lam0, lam0);
             const float rl = (float)lam0 + marg;
             sh_rl2 = rl * rl * (1.0f + 9.5367431640625e-7f);
+            // every WCA partner of a member, old or new position, lies within lam + A0 lam / 4 +
+            // r_c of the centre (|displacement| <= A_w / 4 <= A0 lam / 4); three margins cover the
+            // rounding of this screen and of the energy pass's own
+            const float lf = (float)lam0;
+            const float rR = lf + 0.25f * (float)v.A0 * lf + (float)v.rc + 3.0f * marg;
+            sh_rR2 = rR * rR * (1.0f + 9.5367431640625e-7f);
             sh_n = 0;
+            sh_nc = 0;
         }
         __syncthreads();
         const double lam = sh_lam, lam2 = sh_lam2;
         const double b[3] = {sh_b[0], sh_b[1], sh_b[2]};
         {
             const float bx = sh_bf[0], by = sh_bf[1], bz = sh_bf[2];
-            const float rl2 = sh_rl2;
+            const float rl2 = sh_rl2, rR2 = sh_rR2;
             for (int m = tid; m < N; m += NT) {
                 float dx = fx[m] - bx, dy = fy[m] - by, dz = fz[m] - bz;
                 dx = fabsf(dx) > hLf ? dx - copysignf(Lf, dx) : dx;
                 dy = fabsf(dy) > hLf ? dy - copysignf(Lf, dy) : dy;
                 dz = fabsf(dz) > hLf ? dz - copysignf(Lf, dz) : dz;
-                if (dx * dx + dy * dy + dz * dz > rl2) continue;
-                const unsigned am = __activemask();
-                const double d0 = mi_u(sub(px[m], b[0]), L, hL, am), d1 = mi_u(sub(py[m], b[1]), L, hL, am),
-                             d2c = mi_u(sub(pz[m], b[2]), L, hL, am);
-                if (norm2(d0, d1, d2c) < lam2) mid[atomicAdd(&sh_n, 1)] = m;
+                const float d2f = dx * dx + dy * dy + dz * dz;
+                if (d2f > rR2) continue;
+                bool in = false;
+                if (d2f <= rl2) {
+                    const unsigned am = __activemask();
+                    const double d0 = mi_u(sub(px[m], b[0]), L, hL, am), d1 = mi_u(sub(py[m], b[1]), L, hL, am),
+                                 d2c = mi_u(sub(pz[m], b[2]), L, hL, am);
+                    in = norm2(d0, d1, d2c) < lam2;
+                }
+                if (in) mid[atomicAdd(&sh_n, 1)] = m;
+                else {
+                    const int c = atomicAdd(&sh_nc, 1);
+                    if (c < kSmemCand) s_cand[c] = m;
+                }
             }
         }
         __syncthreads();
@@ -1482,9 +1501,37 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                 }
             }
             mimg[k] = (uint8_t)pack_img(im[0], im[1], im[2]);
-            sslot[m] = k;
+            sslot[m] = (short)k;
         }
         __syncthreads();
+        // the (member, bead) pairs of the WCA sums: each member against the candidates within
+        // reach of the move and against the later members, or against every staged bead when
+        // the candidate list overflowed; the same pairs pass the energy screens either way
+        const int ncand = sh_nc;
+        auto for_wca_pairs = [&](auto&& f) {
+            if (ncand <= kSmemCand) {
+                const int nl = ncand + n, total = n * nl;
+                for (int t = tid; t < total; t += NT) {
+                    const int k = t / nl, u = t - k * nl;
+                    const int q = u < ncand ? s_cand[u] : mid[u - ncand];
+                    const int m = mid[k];
+                    const int sq = sslot[q];
+                    if (q != m && !(sq >= 0 && q < m)) f(k, m, q, sq);
+                }
+            } else {
+                const int total = n * N;
+                int k = tid / N, q = tid - k * N;
+                const int kstep = NT / N, qstep = NT - kstep * N;
+                for (int t = tid; t < total; t += NT) {
+                    const int m = mid[k];
+                    const int sq = sslot[q];
+                    if (q != m && !(sq >= 0 && q < m)) f(k, m, q, sq);
+                    k += kstep;
+                    q += qstep;
+                    if (q >= N) { q -= N; k++; }
+                }
+            }
+        };
         // energy change. Mixed precision: a binary32 pass (differences of the binary64
         // positions rounded once, then binary32 terms with their magnitudes) decides outside
         // the rigorous error band; inside it, and in binary64 mode, the binary64 pass decides.
@@ -1548,13 +1595,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                 }
             }
             if (eps_on) {
-                const int total = n * N;
-                int k = tid / N, q = tid - k * N;
-                const int kstep = NT / N, qstep = NT - kstep * N;
-                for (int t = tid; t < total; t += NT) {
-                    const int m = mid[k];
-                    const int sq = sslot[q];
-                    if (q != m && !(sq >= 0 && q < m)) {
+                for_wca_pairs([&](int k, int m, int q, int sq) {
                         const float qfx = fx[q], qfy = fy[q], qfz = fz[q];
                         float ax = fx[m] - qfx, ay = fy[m] - qfy, az = fz[m] - qfz;
                         ax = fabsf(ax) > hLf ? ax - copysignf(Lf, ax) : ax;
@@ -1584,11 +1625,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                             a32 += un - uo; m32 += mn + mo; T += 2;
                             if (sq < 0 && (un != 0.0f || uo != 0.0f)) pe++;
                         }
-                    }
-                    k += kstep;
-                    q += qstep;
-                    if (q >= N) { q -= N; k++; }
-                }
+                });
             }
             for (int o = 16; o > 0; o >>= 1) {
                 a32 += __shfl_xor_sync(0xffffffffu, a32, o);
@@ -1639,13 +1676,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             }
             if (eps_on) {
                 // one (member, bead) pair per thread and step, all members at once
-                const int total = n * N;
-                int k = tid / N, q = tid - k * N;
-                const int kstep = NT / N, qstep = NT - kstep * N;
-                for (int t = tid; t < total; t += NT) {
-                    const int m = mid[k];
-                    const int sq = sslot[q];
-                    if (q != m && !(sq >= 0 && q < m)) {
+                for_wca_pairs([&](int k, int m, int q, int sq) {
                         const float qfx = fx[q], qfy = fy[q], qfz = fz[q];
                         float ax = fx[m] - qfx, ay = fy[m] - qfy, az = fz[m] - qfz;
                         ax = fabsf(ax) > hLf ? ax - copysignf(Lf, ax) : ax;
@@ -1670,11 +1701,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
                                 if (sq < 0 && PREC == 0) pe++;
                             }
                         }
-                    }
-                    k += kstep;
-                    q += qstep;
-                    if (q >= N) { q -= N; k++; }
-                }
+                });
             }
             dU = warp_sum(dU);
             if (lane == 0) sh_red[wid] = dU;
@@ -1734,7 +1761,7 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     }
 }
 
-size_t smem_serial_bytes(int64_t n) { return (size_t)n * (3 * 8 + 3 * 8 + 6 * 4 + 6 * 4 + 4 + 4 + 3 * 2 + 1 + 1) + 64; }
+size_t smem_serial_bytes(int64_t n) { return (size_t)n * (3 * 8 + 3 * 8 + 6 * 4 + 6 * 4 + 4 + 2 + 3 * 2 + 1 + 1) + 64; }
 
 int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj) {
     const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
