@@ -1338,7 +1338,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
 // here; they are marked stale and rebuilt before the next plane-wave move that needs them.
 // Shared bytes per bead: see smem_serial_bytes.
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ vs, int l, int64_t nlo, int64_t nhi) {
+__global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const SimView* __restrict__ vs, int l, int64_t nlo, int64_t nhi) {
     SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || !((gv.smem_layers >> l) & 1) || gv.counts[l] == 0 ||
                 gv.N <= nlo || gv.N > nhi)
     SIM_PROLOGUE
@@ -1368,6 +1368,8 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
     __shared__ int s_cand[kSmemCand];            // beads within reach of the move, not in the support
     __shared__ int sh_nc;
     __shared__ float sh_rR2;
+    __shared__ double sh_aw[33];                 // A_w for supports of 1..32 beads
+    __shared__ float sh_awf[33], sh_lamf, sh_pf[3];
     __shared__ double sh_b[3], sh_p[3], sh_carry;
     __shared__ double sh_red[NT / 32];
     __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
@@ -1426,6 +1428,18 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
             sh_rR2 = rR * rR * (1.0f + 9.5367431640625e-7f);
             sh_n = 0;
             sh_nc = 0;
+        } else if (tid >= 32 && tid < 64) {
+            // beside thread 0 (another scheduler): A_w = A0 lam / sqrt(n) (Eq. 29) for n = 1..32
+            // and the move's binary32 constants
+            const double lam0 = __double_as_longlong(sh_carry) > 0 ? sh_carry : v.slot_lam[j];
+            const int nn = tid - 31;
+            const double aw = dvd(mul(v.A0, lam0), s_sqrt[nn]);
+            sh_aw[nn] = aw;
+            sh_awf[nn] = (float)aw;
+            if (tid == 32) {
+                sh_lamf = (float)lam0;
+                for (int a = 0; a < 3; a++) sh_pf[a] = (float)v.slot_p[3 * j + a];
+            }
         }
         __syncthreads();
         const double lam = sh_lam, lam2 = sh_lam2;
@@ -1472,8 +1486,14 @@ __global__ void __launch_bounds__(NT) k_serial_smem(const SimView* __restrict__ 
         float lamf = 0.0f, af = 0.0f, pf[3] = {0.0f, 0.0f, 0.0f};
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
         if ((tid & ~31) < n) {
-            Aw = dvd(mul(v.A0, lam), n <= kNCap ? s_sqrt[n] : sqr_t((double)n));
-            lamf = (float)lam; af = (float)Aw; pf[0] = (float)p[0]; pf[1] = (float)p[1]; pf[2] = (float)p[2];
+            if (n <= 32) {
+                Aw = sh_aw[n];
+                af = sh_awf[n];
+            } else {
+                Aw = dvd(mul(v.A0, lam), n <= kNCap ? s_sqrt[n] : sqr_t((double)n));
+                af = (float)Aw;
+            }
+            lamf = sh_lamf; pf[0] = sh_pf[0]; pf[1] = sh_pf[1]; pf[2] = sh_pf[2];
         }
         for (int k = tid; k < n; k += NT) {
             const unsigned am = __activemask();
