@@ -1404,30 +1404,34 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
     const float rcf = (float)v.rc + marg;
     const float rc2f = rcf * rcf * (1.0f + 9.5367431640625e-7f);
     long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
-    // every binary64 value the whole block needs for a move is formed once, by thread 0, and
-    // shared: on this part each binary64 instruction of every warp would occupy the pipe
+    const float A0f = (float)v.A0, rcr = (float)v.rc;
+    // every binary64 value the whole block needs for a move is formed once, by threads 0-2 (one
+    // axis each) and shared: on this part each binary64 instruction of every warp would occupy
+    // the pipe
     for (int j = 0; j < count; j++) {
         const int i = v.slot_bead[j];
-        if (tid == 0) {
+        if (tid < 3) {
+            const int a = tid;
             const double lam0 = __double_as_longlong(sh_carry) > 0 ? sh_carry : v.slot_lam[j];
-            const double ri[3] = {px[i], py[i], pz[i]};
-            for (int a = 0; a < 3; a++) {
-                sh_b[a] = wrap_u(add(ri[a], mul(lam0, v.slot_V[3 * j + a])), L, 1u, nullptr);
-                sh_p[a] = v.slot_p[3 * j + a];
-                sh_bf[a] = (float)sh_b[a];
+            const double ri = a == 0 ? px[i] : (a == 1 ? py[i] : pz[i]);
+            const double ba = wrap_u(add(ri, mul(lam0, v.slot_V[3 * j + a])), L, 7u, nullptr);
+            sh_b[a] = ba;
+            sh_p[a] = v.slot_p[3 * j + a];
+            sh_bf[a] = (float)ba;
+            if (a == 0) {
+                sh_lam = lam0;
+                sh_lam2 = mul(lam0, lam0);
+                const float lf = (float)lam0;
+                const float rl = lf + marg;
+                sh_rl2 = rl * rl * (1.0f + 9.5367431640625e-7f);
+                // every WCA partner of a member, old or new position, lies within lam + A0 lam / 4 +
+                // r_c of the centre (|displacement| <= A_w / 4 <= A0 lam / 4); three margins cover
+                // the rounding of this screen and of the energy pass's own
+                const float rR = lf + 0.25f * A0f * lf + rcr + 3.0f * marg;
+                sh_rR2 = rR * rR * (1.0f + 9.5367431640625e-7f);
+                sh_n = 0;
+                sh_nc = 0;
             }
-            sh_lam = lam0;
-            sh_lam2 = mul(lam0, lam0);
-            const float rl = (float)lam0 + marg;
-            sh_rl2 = rl * rl * (1.0f + 9.5367431640625e-7f);
-            // every WCA partner of a member, old or new position, lies within lam + A0 lam / 4 +
-            // r_c of the centre (|displacement| <= A_w / 4 <= A0 lam / 4); three margins cover the
-            // rounding of this screen and of the energy pass's own
-            const float lf = (float)lam0;
-            const float rR = lf + 0.25f * (float)v.A0 * lf + (float)v.rc + 3.0f * marg;
-            sh_rR2 = rR * rR * (1.0f + 9.5367431640625e-7f);
-            sh_n = 0;
-            sh_nc = 0;
         } else if (tid >= 32 && tid < 64) {
             // beside thread 0 (another scheduler): A_w = A0 lam / sqrt(n) (Eq. 29) for n = 1..32
             // and the move's binary32 constants
