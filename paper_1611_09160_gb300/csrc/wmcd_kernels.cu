@@ -23,6 +23,19 @@ __device__ __forceinline__ double mi_u(double d, double L, double h, unsigned ma
     if (__any_sync(mask, gt_pos(d, h) || lt_neg(d, h))) d = mi(d, L, h);
     return d;
 }
+// the same for the three components of a vector, with one vote for all three
+__device__ __forceinline__ void wrap3_u(double x[3], double L, unsigned mask, int* im) {
+    const bool need = ge_pos(x[0], L) || lt_zero(x[0]) || ge_pos(x[1], L) || lt_zero(x[1]) || ge_pos(x[2], L) ||
+                      lt_zero(x[2]);
+    if (__any_sync(mask, need))
+        for (int a = 0; a < 3; a++) x[a] = wrap(x[a], L, im ? &im[a] : nullptr);
+}
+__device__ __forceinline__ void mi3_u(double d[3], double L, double h, unsigned mask) {
+    const bool need = gt_pos(d[0], h) || lt_neg(d[0], h) || gt_pos(d[1], h) || lt_neg(d[1], h) || gt_pos(d[2], h) ||
+                      lt_neg(d[2], h);
+    if (__any_sync(mask, need))
+        for (int a = 0; a < 3; a++) d[a] = mi(d[a], L, h);
+}
 
 // Every kernel serves a group of simulations: blockIdx.y selects one, whose view is copied
 // into shared memory once per block. SIM_EXIT_IF tests a condition on the view in global
@@ -985,8 +998,10 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             const double o[3] = {v.bead[m].x, v.bead[m].y, v.bead[m].z};
             int im[3] = {0, 0, 0};
             const unsigned am = __activemask();
+            double nx[3] = {add(o[0], dl[0]), add(o[1], dl[1]), add(o[2], dl[2])};
+            wrap3_u(nx, L, am, im);
             for (int a = 0; a < 3; a++) {
-                v.s_new[3 * k + a] = wrap_u(add(o[a], dl[a]), L, am, &im[a]);
+                v.s_new[3 * k + a] = nx[a];
                 v.s_d[4 * k + a] = dl[a];        // keep the displacement for the partner boxes
             }
             v.s_img[k] = pack_img(im[0], im[1], im[2]);
@@ -1461,9 +1476,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
                 bool in = false;
                 if (d2f <= rl2) {
                     const unsigned am = __activemask();
-                    const double d0 = mi_u(sub(px[m], b[0]), L, hL, am), d1 = mi_u(sub(py[m], b[1]), L, hL, am),
-                                 d2c = mi_u(sub(pz[m], b[2]), L, hL, am);
-                    in = norm2(d0, d1, d2c) < lam2;
+                    double dd[3] = {sub(px[m], b[0]), sub(py[m], b[1]), sub(pz[m], b[2])};
+                    mi3_u(dd, L, hL, am);
+                    in = norm2(dd[0], dd[1], dd[2]) < lam2;
                 }
                 if (in) mid[atomicAdd(&sh_n, 1)] = m;
                 else {
@@ -1503,14 +1518,16 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
             const unsigned am = __activemask();
             const int m = mid[k];
             const double o[3] = {px[m], py[m], pz[m]};
-            double d[3] = {mi_u(sub(o[0], b[0]), L, hL, am), mi_u(sub(o[1], b[1]), L, hL, am), mi_u(sub(o[2], b[2]), L, hL, am)},
-                   dl[3];
+            double d[3] = {sub(o[0], b[0]), sub(o[1], b[1]), sub(o[2], b[2])}, dl[3];
+            mi3_u(d, L, hL, am);
             if (PREC == 0) wavelet_disp64(d, norm2(d[0], d[1], d[2]), lam, Aw, p, dl);
             else wavelet_disp32f(d, lamf, af, pf, dl);
             int im[3] = {0, 0, 0};
             const float oh[3] = {fx[m], fy[m], fz[m]}, ol[3] = {lx[m], ly[m], lz[m]};
+            double nx[3] = {add(o[0], dl[0]), add(o[1], dl[1]), add(o[2], dl[2])};
+            wrap3_u(nx, L, am, im);
             for (int a = 0; a < 3; a++) {
-                mnew[3 * k + a] = wrap_u(add(o[a], dl[a]), L, am, &im[a]);
+                mnew[3 * k + a] = nx[a];
                 if (im[a] == 0) {
                     // old (hi, lo) plus the displacement by a binary32 two-sum, renormalised
                     const float dlf = (float)dl[a];
@@ -2665,9 +2682,10 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     const bool own = __double_as_longlong(lam) == __double_as_longlong(S.clam[c]);
     double b[3], lv[3];
     for (int a = 0; a < 3; a++) lv[a] = own ? S.clamV[3 * c + a] : mul(lam, S.cV[3 * c + a]);
-    b[0] = wrap_u(add(S.sx[ti], lv[0]), L, FULL, nullptr);
-    b[1] = wrap_u(add(S.sy[ti], lv[1]), L, FULL, nullptr);
-    b[2] = wrap_u(add(S.sz[ti], lv[2]), L, FULL, nullptr);
+    b[0] = add(S.sx[ti], lv[0]);
+    b[1] = add(S.sy[ti], lv[1]);
+    b[2] = add(S.sz[ti], lv[2]);
+    wrap3_u(b, L, FULL, nullptr);
     const double R = own ? S.cR[c] : add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
     const float lamf = own ? S.clamf[c] : (float)lam;
     // A_w = A0 lam / sqrt(n) (Eq. 29) for every support size up to 32, one per lane, formed
@@ -2771,7 +2789,8 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         const int t = S.mem[k];
         S.stag[t] = tag;
         const double o[3] = {S.sx[t], S.sy[t], S.sz[t]};
-        double d[3] = {mi_u(sub(o[0], b[0]), L, hL, am), mi_u(sub(o[1], b[1]), L, hL, am), mi_u(sub(o[2], b[2]), L, hL, am)};
+        double d[3] = {sub(o[0], b[0]), sub(o[1], b[1]), sub(o[2], b[2])};
+        mi3_u(d, L, hL, am);
         double dl[3];
         float dlf3[3];
         if (PREC == 0) {
@@ -2783,8 +2802,10 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         }
         int im[3] = {0, 0, 0};
         const float oh[3] = {S.hx[t], S.hy[t], S.hz[t]}, ol[3] = {S.lx[t], S.ly[t], S.lz[t]};
+        double nx[3] = {add(o[0], dl[0]), add(o[1], dl[1]), add(o[2], dl[2])};
+        wrap3_u(nx, L, am, im);
         for (int a = 0; a < 3; a++) {
-            S.mnp[3 * k + a] = wrap_u(add(o[a], dl[a]), L, am, &im[a]);
+            S.mnp[3 * k + a] = nx[a];
             // new local coordinate = old + displacement, in binary32 pairs (two-sum, then
             // renormalised); local coordinates are continuous inside the region, no wrap
             const float dlf = dlf3[a];
