@@ -188,10 +188,11 @@ int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, const int32_t
                            int64_t call_index, int32_t* carry, int64_t n_moves, void* stream);
 
 /* Launch shapes: warps per block of the concurrent wavelet kernel (one coarse-cell queue per
- * warp), 1..4, lowered where the block's shared memory would exceed 227 KB (default 2); and
- * threads of the serial-phase block, 32, 128 or 512 (default 512). Choices of launch shape
- * only: decisions and positions do not depend on them (an energy change is summed in another
- * order, which moves it by rounding). WMCD_EINVAL for other values. */
+ * warp), 1..4, lowered where the block's shared memory would exceed 227 KB (default 2; a layer
+ * whose regions need a block each runs one queue per block on 4 cooperating warps whatever this
+ * is); and threads of the serial-phase block, 32, 128 or 512 (default 512). Choices of launch
+ * shape only: decisions and positions do not depend on them (an energy change is summed in
+ * another order, which moves it by rounding). WMCD_EINVAL for other values. */
 int wmcd_set_block(wmcd_handle* h, int stage_warps, int serial_threads);
 
 /* Releases the handle and its device state. WMCD_EINVAL for a handle a batch owns. */
