@@ -188,6 +188,18 @@ def test_large_supports_run_concurrently(precision):
     assert (na[concurrent] > 64).any()
 
 
+def test_large_supports_concurrent_through_global_memory():
+    """As above with 4,096 beads: the coloured layer's region (the whole box) is too large to
+    stage, so its moves, supports above 64 beads included, run through the global cell lists."""
+    s = I.make_system([32] * 128, 0, I.box_for_volume_fraction(4096, 0.15), seed=14)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=8, precision=wmcd.MIXED, colour_K=3, n_cap=256)
+    p["grid_layer"] = [9, 3] + [0] * 14
+    gpu, ref = run_pair(p, s, 2)
+    a, na = gpu.trace(1)
+    concurrent = ((a & 3) != 0) & ((a & 4) == 0)
+    assert (na[concurrent] > 64).any()
+
+
 @pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])
 def test_coarse_layer_regions_staged_in_blocks_of_their_own(precision):
     """64 chains x 64 beads at volume fraction 1e-3 with colour stride 3: the regions of the
