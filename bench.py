@@ -307,6 +307,29 @@ def serve_leg(args, torch, tuner, policy):
     return sm
 
 
+def drift_leg(args):
+    """Mixed precision against plain binary64 from the same start: the 32-bead chain in L = 64
+    with wavelets and plane waves, the largest position difference after the given sweeps as a
+    fraction of the box. Each run decides on its own positions (both decide exactly as the
+    binary64 definition would on them), so the two part once a decision close to its threshold
+    falls differently; until then they differ by the binary32 rounding of the displacements."""
+    import numpy as np
+    from paper_1611_09160_gb300 import inputs as I
+    from paper_1611_09160_gb300 import wmcd
+    s = I.single_chain(32, 64.0, seed=1)
+    pos, acc = {}, {}
+    for prec in (wmcd.FP64, wmcd.MIXED):
+        p = wmcd.default_params(s.n_beads, s.box_L, seed=1, precision=prec, planewave_mode=wmcd.PLANEWAVE_PERIODIC)
+        sim = wmcd.Simulation(p, s.pos, s.chain_len)
+        sim.sweep(args.drift_sweeps)
+        pos[prec] = sim.positions(unwrapped=True)
+        acc[prec] = int(sim.stats().accepted_total)
+        sim.close()
+    return {"workload": "single chain 32 beads, L = 64, wavelets + plane waves, same seed", "sweeps": args.drift_sweeps,
+            "max_abs_dx_over_L": float(np.max(np.abs(pos[wmcd.MIXED] - pos[wmcd.FP64]))) / s.box_L,
+            "accepted_fp64": acc[wmcd.FP64], "accepted_mixed": acc[wmcd.MIXED]}
+
+
 def combine_ranks(maxed, summed, world, device):
     """Whole-job figures of independent replicas: the slowest rank's times (max) and the
     units of all ranks (sum). No collective is used for a single rank."""
@@ -454,6 +477,7 @@ def run_gpu(args, rank, world, local_rank):
     semi = semidilute_leg(args, torch, stream, flush) if args.semidilute_sweeps > 0 else None
     susp = suspension_leg(args, torch, stream, flush) if args.suspension_sweeps > 0 else None
     srv = serve_leg(args, torch, tuner, ens["policy"] if ens else "serial_small") if args.serve_requests > 0 else None
+    drift = drift_leg(args) if args.drift_sweeps > 0 and rank == 0 else None
 
     if rank != 0:
         return
@@ -465,6 +489,7 @@ def run_gpu(args, rank, world, local_rank):
             "fp64": {"value": fp64_value * world, "unit": UNIT, "speedup_mixed_over_fp64": value / (fp64_value * world)},
             "e2e": e2e, "gpu_launches": launches_all, "clocks": clocks, "roofline": roofline,
             "plane_wave": pw, "batched": ens, "serve": srv, "semidilute": semi, "suspension": susp,
+            "mixed_vs_fp64": drift,
             "stats": {"accept_fraction": (st1.accepted_total - st0.accepted_total) /
                                          max(1, sum(st1.attempts) - sum(st0.attempts) +
                                              st1.pw_attempts - st0.pw_attempts),
@@ -492,6 +517,8 @@ def main():
     ap.add_argument("--serve-chunk", type=int, default=10)
     ap.add_argument("--semidilute-sweeps", type=int, default=3, help="timed sweeps of the 1M-bead leg (0: skip)")
     ap.add_argument("--suspension-sweeps", type=int, default=2, help="timed sweeps of the 5M-bead leg (0: skip)")
+    ap.add_argument("--drift-sweeps", type=int, default=10000,
+                    help="sweeps of the mixed-against-binary64 drift check on the 32-bead chain (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
