@@ -166,20 +166,25 @@ def run_reference(args, rank, world):
     s = make_system(1)
     p = make_params(s, wmcd.MIXED, 1)
     o = O.Oracle(p, s.pos, s.chain_len)
+    tw = time.perf_counter()
     for _ in range(args.warmup):
         o.sweep(1)
+    per_sweep = (time.perf_counter() - tw) / max(1, args.warmup)
+    # the timed sample: the requested sweeps, bounded so that the run ends within a few minutes
+    timed = max(1, min(args.steps, int(args.reference_seconds / max(per_sweep, 1e-9))))
     b0, t_sim0 = o.stats().bead_updates, o.stats().sim_time
     t0 = time.perf_counter()
-    o.sweep(args.steps)
+    o.sweep(timed)
     dt = time.perf_counter() - t0
     st = o.stats()
     value = (st.bead_updates - b0) / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / timed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole sweeps after {args.warmup} warm-up sweeps"},
+                             "sample": f"{timed} whole sweeps timed (of {args.steps} requested, bounded to about "
+                                       f"{args.reference_seconds:.0f} s) after {args.warmup} warm-up sweeps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sim_time_per_s": (st.sim_time - t_sim0) / dt}
     print(json.dumps(line), flush=True)
@@ -515,6 +520,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--reference-seconds", type=float, default=150.0,
+                    help="bound on the timed part of --impl reference (whole oracle sweeps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=1024, help="simulations in the batched leg (0: skip)")
     ap.add_argument("--ensemble-sweeps", type=int, default=10)
