@@ -94,6 +94,8 @@ def _load():
         "oracle_pw_modes": ([P, P, P, I64, P, P], I64),
         "oracle_propose_moments": ([P, I64, U64, P], ctypes.c_int),
         "oracle_sweep_record": ([P, I64, P], ctypes.c_int),
+        "oracle_pw_polarisation": ([P, D, P], None),
+        "oracle_planewave_field": ([P, P, D, D, P, P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -238,6 +240,13 @@ class Oracle:
             raise ValueError("needs at least two beads")
         return out[:9].reshape(3, 3), out[9:18].reshape(3, 3), out[18:].reshape(3, 3)
 
+    def planewave_field(self, l, phi, psi, pt):
+        lv = np.ascontiguousarray(l, dtype=np.int32)
+        pt = np.ascontiguousarray(pt, dtype=np.float64)
+        out = np.zeros(3)
+        self._lib.oracle_planewave_field(self.h, _ptr(lv), float(phi), float(psi), _ptr(pt), _ptr(out))
+        return out
+
     def sweep_record(self, n: int):
         out = np.zeros((n, 3))
         self._lib.oracle_sweep_record(self.h, int(n), _ptr(out))
@@ -284,6 +293,13 @@ def cos2pi_f(t: float) -> float:
 
 def inv_cbrt(w: float, lo: float) -> float:
     return float(_load().oracle_inv_cbrt(float(w), float(lo)))
+
+
+def pw_polarisation(l, psi: float) -> np.ndarray:
+    lv = np.ascontiguousarray(l, dtype=np.int32)
+    out = np.zeros(3)
+    _load().oracle_pw_polarisation(_ptr(lv), float(psi), _ptr(out))
+    return out
 
 
 def lambda_a() -> float:

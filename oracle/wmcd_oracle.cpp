@@ -740,6 +740,45 @@ static void run_layer(Sim& s, int l) {
 /* ---- plane-wave moves (Sec. VI; Appendix D, periodic system) ---- */
 static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
+// Polarisation of a periodic plane wave with integer wave vector l != 0 and angle psi (in
+// turns), Appendix D (choosing e): the unit vector at angle 2 pi psi about k in the plane
+// perpendicular to k, from the basis u1 = normalise(k x z) (x when k is along z), u2 = k^ x u1.
+static void pw_polarisation(const int lv[3], double psi, double e[3]) {
+    int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
+    double lm = std::sqrt((double)l2);
+    double kh[3] = {lv[0] / lm, lv[1] / lm, lv[2] / lm}, u1[3], u2[3];
+    if (lv[0] == 0 && lv[1] == 0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
+    else {
+        double nr = std::sqrt((double)(lv[0] * lv[0] + lv[1] * lv[1]));
+        u1[0] = lv[1] / nr; u1[1] = -lv[0] / nr; u1[2] = 0.0;
+    }
+    u2[0] = kh[1] * u1[2] - kh[2] * u1[1];
+    u2[1] = kh[2] * u1[0] - kh[0] * u1[2];
+    u2[2] = kh[0] * u1[1] - kh[1] * u1[0];
+    double cp = cos2pi(psi), sp = sin2pi(psi);
+    for (int a = 0; a < 3; a++) e[a] = cp * u1[a] + sp * u2[a];
+}
+// Amplitude A_F = (2/k) sqrt(dU_est/(mu N)) with dU_est/mu = M6 A0^2/(2 pi)^3 = A0^2/5 (Eq. 48),
+// k = 2 pi |l| / L.
+static double pw_amplitude(const Sim& s, const int lv[3]) {
+    int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
+    double lm = std::sqrt((double)l2);
+    double kmag = (TWO_PI * lm) / s.L;
+    return (2.0 * s.P.A0) / (kmag * std::sqrt(5.0 * (double)s.N));
+}
+// Displacement A_F cos(k.r + Phi) e of a bead at r (Eq. 47), phase in turns.
+static void pw_displacement(const Sim& s, const int lv[3], double phi, double AF, const double e[3], const double* r,
+                            double dl[3]) {
+    double t = ((lv[0] * r[0] + lv[1] * r[1]) + lv[2] * r[2]) / s.L + phi;
+    if (s.P.precision == 0) {
+        double amp = AF * cos2pi(t);
+        for (int a = 0; a < 3; a++) dl[a] = amp * e[a];
+    } else {
+        float amp = (float)AF * cos2pi_f(t);
+        for (int a = 0; a < 3; a++) dl[a] = (double)(amp * (float)e[a]);
+    }
+}
+
 // Returns ACCEPT or REJECT; mode receives the packed wave vector index.
 static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr, uint32_t m, int32_t* mode_out) {
     U4 w1 = s.rng.draw(kmode, 0, ctr, m, 0);
@@ -770,37 +809,16 @@ static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr
         return ACCEPT;
     }
     s.st.bead_updates += s.N;
-    // amplitude A_F = (2/k) sqrt(dU_est/(mu N)) with dU_est/mu = M6 A0^2/(2pi)^3 = A0^2/5 (Eq. 48)
-    int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
-    double lm = std::sqrt((double)l2);
-    double kmag = (TWO_PI * lm) / s.L;
-    double AF = (2.0 * s.P.A0) / (kmag * std::sqrt(5.0 * (double)s.N));
-    // polarisation e, uniform in the plane perpendicular to k (Appendix D)
-    double kh[3] = {lv[0] / lm, lv[1] / lm, lv[2] / lm}, u1[3], u2[3];
-    if (lv[0] == 0 && lv[1] == 0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
-    else {
-        double nr = std::sqrt((double)(lv[0] * lv[0] + lv[1] * lv[1]));
-        u1[0] = lv[1] / nr; u1[1] = -lv[0] / nr; u1[2] = 0.0;
-    }
-    u2[0] = kh[1] * u1[2] - kh[2] * u1[1];
-    u2[1] = kh[2] * u1[0] - kh[0] * u1[2];
-    u2[2] = kh[0] * u1[1] - kh[1] * u1[0];
-    double cp = cos2pi(psi), sp = sin2pi(psi), e[3];
-    for (int a = 0; a < 3; a++) e[a] = cp * u1[a] + sp * u2[a];
+    double AF = pw_amplitude(s, lv);
+    double e[3];
+    pw_polarisation(lv, psi, e);
     // displacement A_F cos(k.r + Phi) e of every bead (Eq. 47)
     std::vector<double> newp(3 * (size_t)s.N);
     std::vector<int32_t> newimg(3 * (size_t)s.N);
     for (int64_t i = 0; i < s.N; i++) {
         const double* r = &s.pos[3 * i];
-        double t = ((lv[0] * r[0] + lv[1] * r[1]) + lv[2] * r[2]) / s.L + phi;
         double dl[3];
-        if (s.P.precision == 0) {
-            double amp = AF * cos2pi(t);
-            for (int a = 0; a < 3; a++) dl[a] = amp * e[a];
-        } else {
-            float amp = (float)AF * cos2pi_f(t);
-            for (int a = 0; a < 3; a++) dl[a] = (double)(amp * (float)e[a]);
-        }
+        pw_displacement(s, lv, phi, AF, e, r, dl);
         for (int a = 0; a < 3; a++) {
             int32_t im = s.img[3 * i + a];
             newp[3 * i + a] = wrap(r[a] + dl[a], s.L, &im);
@@ -1086,6 +1104,21 @@ double oracle_delta_u(void* h, int64_t n, const int64_t* ids, const double* newp
     return delta_U(s, S, np);
 }
 double oracle_total_energy(void* h) { return total_energy(*(Sim*)h); }
+
+// polarisation of the periodic plane wave with wave vector l (three ints) at angle psi (turns)
+void oracle_pw_polarisation(const int32_t* l, double psi, double* e) {
+    int lv[3] = {l[0], l[1], l[2]};
+    pw_polarisation(lv, psi, e);
+}
+// displacement of a bead at `pt` by the periodic plane wave (l, phase phi, angle psi) of this
+// simulation, as a move applies it (amplitude of Eq. 48, field of Eq. 47)
+void oracle_planewave_field(void* h, const int32_t* l, double phi, double psi, const double* pt, double* out) {
+    Sim& s = *(Sim*)h;
+    int lv[3] = {l[0], l[1], l[2]};
+    double e[3];
+    pw_polarisation(lv, psi, e);
+    pw_displacement(s, lv, phi, pw_amplitude(s, lv), e, pt, out);
+}
 
 int64_t oracle_pw_modes(void* h, int32_t* modes, double* prob, int64_t cap, double* R, double* PF) {
     Sim& s = *(Sim*)h;

@@ -132,7 +132,7 @@ class Tuner:
     def apply(base: dict, choice: dict) -> dict:
         p = dict(base)
         p.update(S.choose(p["box_L"], p["lambda_min"], p["lambda_max"], p["A0"], p["wca_sigma"], p["wca_eps"],
-                          **choice))
+                          **dict({"n_beads": p["n_beads"]}, **choice)))
         return p
 
     def _tune_schedule(self, base: dict, system, chain_lengths, candidates=None) -> dict:

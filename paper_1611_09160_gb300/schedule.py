@@ -38,11 +38,16 @@ def interaction_reach(wca_sigma: float, wca_eps: float) -> float:
 
 def choose(box_L: float, lambda_min: float, lambda_max: float, A0: float, wca_sigma: float, wca_eps: float,
            colour_K: int = 2, slack: float = 1.0, max_fine: int = 512, n_cap: int = 64,
-           min_queues_per_axis: int = 2, cell_scale: float = 1.0, serial_only: bool = False) -> dict:
+           min_queues_per_axis: int = 2, cell_scale: float = 1.0, serial_only: bool = False,
+           n_beads: int | None = None) -> dict:
     """Return the schedule fields: colour_K, grid_f, n_cap, grid_layer (list of 16).
 
     cell_scale widens the fine cells beyond the interaction reach (fewer, fuller cells to walk
-    in dilute systems); serial_only runs every layer in the serial phase."""
+    in dilute systems); serial_only runs every layer in the serial phase. With n_beads given,
+    a layer whose mean support at the lower edge of its band (the beads of a ball of that
+    radius at the mean density) already exceeds n_cap is left serial: a concurrent move with
+    more than n_cap beads is deferred, so colouring such a layer would only add phases whose
+    moves nearly all run again in the serial phase."""
     if colour_K not in (2, 3, 4):
         raise ValueError("colour_K must be 2, 3 or 4")
     if cell_scale < 1.0:
@@ -50,9 +55,12 @@ def choose(box_L: float, lambda_min: float, lambda_max: float, A0: float, wca_si
     reach = interaction_reach(wca_sigma, wca_eps)
     hf = max(reach, 1.0) * cell_scale
     grid_f = max(1, min(max_fine, int(math.floor(box_L / hf))))
-    _, hi = layer_bounds(lambda_min, lambda_max)
+    lo, hi = layer_bounds(lambda_min, lambda_max)
+    density = None if n_beads is None else float(n_beads) / box_L ** 3
     grid_layer = [0] * MAX_LAYERS
     for l, lh in enumerate(hi):
+        if density is not None and density * (4.0 / 3.0) * math.pi * lo[l] ** 3 > n_cap:
+            continue
         # everything a move reads or writes lies within R of its centre, and the centre
         # within lambda of the picked bead: margin = lambda + R + slack for drift
         margin = 2.0 * lh + 0.25 * A0 * lh + reach + slack

@@ -199,6 +199,7 @@ def default_params(n_beads: int, box_L: float, *, lambda_min: float = 2.0, lambd
              bond_type=bond_type, bond_k=bond_k, bond_r0=bond_r0, fene_R0=fene_R0, wca_sigma=wca_sigma,
              wca_eps=wca_eps, ext_kappa=ext_kappa, planewave_mode=planewave_mode, lcut=lcut, precision=precision,
              seed=seed, sim_id=sim_id)
+    sched.setdefault("n_beads", int(n_beads))
     d.update(_schedule.choose(box_L, lambda_min, lmax, A0, wca_sigma, wca_eps, colour_K=colour_K, **sched))
     return d
 

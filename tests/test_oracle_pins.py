@@ -461,3 +461,176 @@ def test_coloured_schedule_keeps_free_diffusion_and_defers_correctly():
     assert st2.deferred[0] == st2.attempts[0] > 0
     out, n = o2.trace_layer(0)
     assert np.all(out & 4)
+
+
+# ---- plane-wave polarisation, field and recycling (Sec. VI; Appendix D) -----------------
+
+def test_plane_wave_polarisation_is_transverse_unit_and_uniform():
+    """Appendix D: e is a unit vector perpendicular to k, at a uniform angle about k; then
+    <e (x) e> over the angle is (1 - k^ (x) k^)/2, the identity Sec. VI uses to turn the
+    Fourier-space tensor into an expectation over e."""
+    o = O.Oracle(params(n_beads=1, planewave_mode=1, lcut=8), np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+    modes, _, _, _ = o.pw_modes()
+    psis = (np.arange(64) + 0.5) / 64            # a uniform grid of angles (in turns)
+    for l in modes:
+        if not np.any(l):
+            continue
+        kh = l / np.linalg.norm(l)
+        E = np.array([O.pw_polarisation(l, s) for s in psis])
+        assert np.allclose(np.linalg.norm(E, axis=1), 1.0, atol=2e-15)
+        assert np.max(np.abs(E @ kh)) < 2e-15
+        assert np.allclose(E.T @ E / len(E), (np.eye(3) - np.outer(kh, kh)) / 2, atol=1e-14)
+    # the angle turns e about k: a quarter turn gives an orthogonal vector, half a turn -e
+    l = np.array([2, -1, 3], np.int32)
+    e0, e1, e2 = (O.pw_polarisation(l, s) for s in (0.1, 0.35, 0.6))
+    assert abs(e0 @ e1) < 1e-15 and np.allclose(e2, -e0, atol=1e-15)
+
+
+def test_plane_wave_field_divergence_free_periodic_and_amplitude():
+    """Eq. 47 with the amplitude of Eq. 48: delta = A_F cos(k.r + Phi) e is transverse to k,
+    divergence-free (central differences), periodic in the box (k commensurate), and its
+    largest magnitude over the phase is A_F = 2 A0 / (k sqrt(5 N)) (dU_est/mu = A0^2 M6/(2 pi)^3,
+    M6/(2 pi)^3 = 1/5)."""
+    L, N, A0 = 24.0, 7, 0.6
+    s = I.make_system([], N, L, seed=3)
+    o = O.Oracle(params(n_beads=N, box_L=L, lambda_max=12.0, A0=A0, planewave_mode=1, lcut=8, grid_f=8),
+                 s.pos, s.chain_len)
+    rng = np.random.default_rng(5)
+    for l in [(1, 0, 0), (0, 0, 2), (1, -2, 3), (4, 4, -1)]:
+        l = np.array(l, np.int32)
+        k = 2 * np.pi * l / L
+        AF = 2 * A0 / (np.linalg.norm(k) * math.sqrt(5 * N))
+        for _ in range(5):
+            phi, psi = rng.random(), rng.random()
+            pt = rng.random(3) * L
+            d = o.planewave_field(l, phi, psi, pt)
+            assert abs(d @ k) < 1e-13
+            h = 1e-5
+            div = sum((o.planewave_field(l, phi, psi, pt + h * e)[a] - o.planewave_field(l, phi, psi, pt - h * e)[a])
+                      / (2 * h) for a, e in enumerate(np.eye(3)))
+            assert abs(div) < 1e-8
+            for a in range(3):
+                shifted = pt.copy()
+                shifted[a] += L
+                assert np.allclose(o.planewave_field(l, phi, psi, shifted), d, atol=1e-12)
+        # over the phase, |delta| reaches A_F (at k.r + Phi = 0) and never exceeds it
+        pt = np.array([1.0, 2.0, 3.0])
+        phase0 = (l @ pt) / L
+        mags = [np.linalg.norm(o.planewave_field(l, ph, 0.3, pt)) for ph in np.linspace(0, 1, 101)]
+        assert max(mags) <= AF * (1 + 1e-14)
+        assert np.linalg.norm(o.planewave_field(l, -phase0, 0.3, pt)) == pytest.approx(AF, rel=1e-13)
+
+
+def _signed_perm(a, b):
+    """(permutation, signs) taking the components of a to those of b, when the three absolute
+    components of a are distinct (so the order is identified); a sign is None for a zero
+    component. None when the order cannot be identified."""
+    aa = np.abs(a)
+    if len(set(aa.tolist())) < 3:
+        return None
+    if sorted(np.abs(b).tolist()) != sorted(aa.tolist()):
+        return None
+    perm = tuple(int(np.where(aa == abs(x))[0][0]) for x in b)
+    signs = tuple(None if x == 0 else int(np.sign(x) != np.sign(a[p])) for x, p in zip(b, perm))
+    return perm, signs
+
+
+def test_plane_wave_recycling_of_k():
+    """Appendix D, parameter recycling: after a rejected periodic plane wave the next one keeps
+    |k| by permuting the components (each of the six orders equally likely) and flipping each
+    sign with probability 1/2; after an acceptance the next mode is drawn afresh."""
+    L, N = 12.0, 40
+    s = I.make_system([N], 0, L, seed=7)       # one dense chain: large plane waves reject often
+    p = params(n_beads=N, box_L=L, lambda_max=6.0, A0=0.35, bond_type=1, bond_k=100.0, wca_eps=1.0,
+               planewave_mode=1, lcut=8, grid_f=5, seed=23)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    o.planewave(60000)
+    out, packed = o.trace_pw()
+    assert len(out) == 60000
+    lv = np.stack([(packed & 0xFF) - 128, ((packed >> 8) & 0xFF) - 128, ((packed >> 16) & 0xFF) - 128], axis=1)
+    rej = np.where(out[:-1] == 2)[0]
+    acc = np.where(out[:-1] == 1)[0]
+    assert len(rej) > 5000 and len(acc) > 5000
+    # every rejection: the next wave vector has the same components up to order and sign
+    same = np.sort(np.abs(lv[rej]), axis=1) == np.sort(np.abs(lv[rej + 1]), axis=1)
+    assert np.all(same)
+    # uniform over the 6 orders and the 8 sign patterns, independently
+    counts_p, counts_s = {}, np.zeros((3, 2))
+    for m in rej:
+        r = _signed_perm(lv[m], lv[m + 1])
+        if r is None:
+            continue
+        counts_p[r[0]] = counts_p.get(r[0], 0) + 1
+        for a in range(3):
+            if r[1][a] is not None:
+                counts_s[a, r[1][a]] += 1
+    cp = np.array(list(counts_p.values()))
+    assert len(cp) == 6 and cp.sum() > 1500
+    assert stats.chisquare(cp).pvalue > 1e-4
+    for a in range(3):
+        assert stats.binomtest(int(counts_s[a, 1]), int(counts_s[a].sum()), 0.5).pvalue > 1e-4
+    # after an acceptance the carry is cleared: the next mode is a signed permutation of the
+    # previous one only as often as a fresh draw from P(k_l) lands on one
+    modes, prob, _, _ = o.pw_modes()
+    key = {tuple(m): q for m, q in zip(modes.tolist(), prob)}
+    cls = {}
+    for m, q in zip(modes.tolist(), prob):
+        c = tuple(sorted(abs(x) for x in m))
+        cls[c] = cls.get(c, 0.0) + q
+    expect = sum(cls[tuple(sorted(abs(int(x)) for x in lv[m]))] for m in acc)
+    seen = int(np.sum(np.all(np.sort(np.abs(lv[acc]), axis=1) == np.sort(np.abs(lv[acc + 1]), axis=1), axis=1)))
+    assert abs(seen - expect) < 5 * math.sqrt(expect) + 5
+    assert seen < 0.6 * len(acc)
+    assert key[(0, 0, 0)] > 0
+
+
+def test_boltzmann_one_bead_in_a_well_with_plane_waves():
+    """One bead in a harmonic well moved by periodic plane waves only, with an amplitude large
+    enough that about half of them reject, so the |k| carry is in play. For a fixed wave vector
+    the displacement A_F cos(theta) e with theta uniform is symmetric and position-independent,
+    so each move leaves exp(-U/kT) invariant (Eq. 20); the variance must be kT/kappa."""
+    kappa, kT = 0.3, 1.0
+    p = params(n_beads=1, box_L=24.0, lambda_max=12.0, A0=2.0, ext_kappa=kappa, kT=kT, planewave_mode=1, lcut=8,
+               grid_f=8, seed=71)
+    o = O.Oracle(p, np.array([[12.0, 12.0, 12.0]]), np.array([1], np.int32))
+    o.planewave(2000)
+    xs, nacc, ntot = [], 0, 0
+    for _ in range(10000):
+        o.planewave(250)
+        out, _ = o.trace_pw()
+        nacc += int(np.sum(out == 1))
+        ntot += len(out)
+        xs.append(o.positions()[0] - 12.0)
+    xs = np.array(xs)
+    assert 0.3 < nacc / ntot < 0.6
+    v, se = np.mean(xs ** 2, axis=0), np.std(xs ** 2, axis=0) / np.sqrt(len(xs))
+    assert np.all(np.abs(v - kT / kappa) < 4.5 * se + 0.01 * kT / kappa)
+    edges = np.linspace(-3, 3, 13) * math.sqrt(kT / kappa)
+    h, _ = np.histogram(xs[:, 0], bins=edges)
+    pr = np.diff(stats.norm.cdf(edges / math.sqrt(kT / kappa)))
+    pr = pr / pr.sum() * h.sum()
+    assert np.sum((h - pr) ** 2 / pr) < 40.0
+
+
+def test_slot_counts_have_the_stratified_mean():
+    """A sweep has floor(x) or floor(x) + 1 slots per layer, x = N (1 - P_F) p_l with p_l the mass
+    of the band under Eq. 32, and floor(N P_F) or one more plane waves; the mean over sweeps is x."""
+    N, L = 1000, 64.0
+    s = I.make_system([], N, L, seed=2)
+    o = O.Oracle(params(n_beads=N, box_L=L, lambda_max=32.0, planewave_mode=1, lcut=8, grid_f=8), s.pos, s.chain_len)
+    _, _, _, PF = o.pw_modes()
+    lo, hi, _, _ = o.layers()
+    Nl = 3 / (2.0 ** -3 - 32.0 ** -3)
+    x = np.array([N * (1 - PF) * integrate.quad(lambda t: Nl * t ** -4, a, b)[0] for a, b in zip(lo, hi)])
+    S = 20000
+    c = np.array([o.slot_counts(sw)[0] for sw in range(S)])
+    f = np.array([o.slot_counts(sw)[1] for sw in range(S)])
+    fl = np.floor(x)
+    assert np.all((c == fl) | (c == fl + 1))
+    fr = x - fl
+    sd = np.sqrt(fr * (1 - fr) / S) + 1e-12
+    assert np.all(np.abs(c.mean(0) - x) < 4.5 * sd)
+    xf = N * PF
+    assert np.all((f == math.floor(xf)) | (f == math.floor(xf) + 1))
+    frf = xf - math.floor(xf)
+    assert abs(f.mean() - xf) < 4.5 * math.sqrt(frf * (1 - frf) / S)
