@@ -115,9 +115,12 @@ typedef struct wmcd_handle wmcd_handle;
 int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,
                 void* stream, wmcd_handle** out);
 
-/* Advance by n_sweeps sweeps. A sweep = the octave layers of P_lambda in ascending order,
- * each with floor(N (1 - P_F) p_l) slots plus one more with probability of the fraction,
- * run as colour phases then a serial phase; then the sweep's plane-wave slots. Asynchronous. */
+/* Advance by n_sweeps sweeps. A sweep = the octave layers of P_lambda (Eq. 32) in ascending
+ * order, each with floor(N (1 - P_F) p_l) slots plus one more with probability of the
+ * fraction (P_F of Eq. 56), run as colour phases then a serial phase; then the sweep's
+ * plane-wave slots (Sec. VI). Each slot is one move generated as in Appendix D (scale by
+ * inverse transform within the band, bead, centre, polarisation; lambda recycled after a
+ * rejection) and decided by the Metropolis test of Eq. 20. Asynchronous. */
 int wmcd_sweep(wmcd_handle* h, int64_t n_sweeps, void* stream);
 
 /* n_moves plane-wave moves (Sec. VI) outside the sweep schedule, one after another, with
@@ -172,18 +175,25 @@ int wmcd_device_bytes(wmcd_handle* h, int64_t* bytes);
  * has no counterpart: this is a deployment variant of wmcd_planewave). For callers that may not
  * call cudaMalloc, e.g. code running while another framework owns the device memory, real-time
  * loops that must not allocate after start-up, or hosts that forbid allocation in callbacks.
- * pos: N*3 doubles in device memory, coordinates in [0, L), replaced in place by the positions
- * after n_moves moves (wrapped; no image counters). chain_len: host, as for wmcd_create.
- * call_index: the plane-wave call counter (0 for the first call, then 1, 2, ...); carry: host
- * int32[4], the recycled wave vector (carry[0] != 0 means carry[1..3] is carried), read and
- * updated. With the same params, positions, call_index and carry the result equals n_moves
- * moves of wmcd_planewave on a handle whose plane-wave call counter is call_index.
+ * params: checked as by wmcd_create, plus the limits below. pos: N*3 doubles in device memory
+ * of the current device (or managed memory), coordinates in [0, L), replaced in place by the
+ * positions after n_moves moves (wrapped; no image counters). chain_len: host, as for
+ * wmcd_create. call_index: the plane-wave call counter (0 for the first call, then 1, 2, ...);
+ * carry: host int32[4], the recycled wave vector (carry[0] = 1 means carry[1..3] is carried,
+ * 0 means none), read and updated; a carried vector must be nonzero with |l| <= lcut. With the
+ * same params, positions, call_index and carry the result equals n_moves moves of
+ * wmcd_planewave on a handle whose plane-wave call counter is call_index.
+ * Errors: WMCD_EINVAL for parameters, carry or a pointer that is not memory of the current
+ * device; WMCD_ESTATE for a non-finite or out-of-box coordinate (found before anything runs);
+ * WMCD_ETIMEOUT when a bounded cell-list walk gave up. On any error `pos` and `carry` are left
+ * unchanged.
  * Scratch: one file-scope device array of about 1.9 MB that every GPU loading the library
  * holds until exit; limits N <= 16384, grid_f^3 <= 48^3, lcut <= 8, plane waves periodic,
- * else WMCD_EINVAL. The first call on a device looks the array up (cudaGetSymbolAddress):
- * make that first call before any stream capture. All calls share the array, so calls that
- * overlap on the GPU (other streams or threads) race; the function is not thread-safe.
- * No cudaMalloc, cudaFree or allocating library call is made. Synchronises `stream`. */
+ * else WMCD_EINVAL. The first call on a device (and the first after its context was torn
+ * down, e.g. by cudaDeviceReset) looks the array up (cudaGetSymbolAddress): make that call
+ * before any stream capture. All calls share the array, so calls that overlap on the GPU
+ * (other streams or threads) race; the function is not thread-safe. No cudaMalloc, cudaFree
+ * or allocating library call is made. Synchronises `stream`. */
 int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, const int32_t* chain_len, int64_t n_chains,
                            int64_t call_index, int32_t* carry, int64_t n_moves, void* stream);
 

@@ -176,7 +176,7 @@ static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64
 using namespace wmcd;
 
 
-static int validate(const wmcd_params* p) {
+int wmcd::validate_params(const wmcd_params* p) {
     if (!p || p->n_beads < 1 || p->n_beads > (int64_t)1 << 30) return WMCD_EINVAL;
     if (!(p->box_L > 0.0) || !(p->lambda_min > 0.0) || !(p->lambda_max > p->lambda_min) ||
         p->lambda_max > 0.5 * p->box_L || !(p->A0 > 0.0) || !(p->kT > 0.0))
@@ -195,7 +195,7 @@ static int validate(const wmcd_params* p) {
 int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double* pos, const int32_t* chain_len,
                         int64_t n_chains, cudaStream_t s, Arena* arena) {
     const bool counting = arena && arena->count_only;
-    int rc = validate(params);
+    int rc = validate_params(params);
     if (rc) return rc;
     const wmcd_params& P = *params;
     if (!counting) {

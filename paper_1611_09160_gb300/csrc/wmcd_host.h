@@ -46,6 +46,8 @@ struct Handle {
 };
 
 int last_cuda_status();
+// WMCD_OK, or WMCD_EINVAL for parameters wmcd_create refuses (the checks listed in wmcd.h)
+int validate_params(const wmcd_params* p);
 int64_t slot_count(const Handle* h, uint32_t kind, int l, uint64_t ctr, double x);
 int64_t enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t* hc, Handle* prof, cudaStream_t s,
                       const ForkJoin* fj = nullptr);

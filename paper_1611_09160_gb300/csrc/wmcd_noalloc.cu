@@ -5,9 +5,10 @@
 // forbid allocation inside their own callbacks. For them this file keeps every scratch buffer
 // the plane-wave kernels need in one file-scope device array of fixed size, which the driver
 // reserves when the library is loaded and keeps on every GPU that loads it until exit.
+#include <cuda.h>
 #include <cstring>
 #include "../../include/wmcd.h"
-#include "wmcd_internal.h"
+#include "wmcd_host.h"
 
 namespace wmcd {
 
@@ -49,7 +50,10 @@ static __global__ void k_na_fill(Bead* bead, const double* pos, int64_t N) {
         bead[i].mark = 0u;
     }
 }
-static __global__ void k_na_read(const Bead* bead, double* pos, int64_t N) {
+// copies the moved beads back into the caller's buffer unless an error was flagged, so that
+// on any error return the caller's positions are left as they were
+static __global__ void k_na_read(const Bead* bead, double* pos, int64_t N, const int* err) {
+    if (*err) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         pos[3 * i] = bead[i].x; pos[3 * i + 1] = bead[i].y; pos[3 * i + 2] = bead[i].z;
     }
@@ -63,16 +67,48 @@ static __global__ void k_na_check(const double* pos, int64_t N, double L, int* e
         if (!(pos[i] >= 0.0 && pos[i] < L)) atomicOr(err, E_NONFINITE);
 }
 
-// device address of the scratch array, looked up once per device (host code may not use the
-// symbol itself: in host code it names a host-side stand-in, not device memory)
+// Identifier of the calling thread's current context (0 if it cannot be read): a device reset
+// or any other teardown of the primary context gives the next context a new identifier. The
+// driver functions are reached through the runtime's entry-point query, so nothing links the
+// driver library directly.
+static unsigned long long current_context_id() {
+    typedef CUresult (*CtxCur)(CUcontext*);
+    typedef CUresult (*CtxId)(CUcontext, unsigned long long*);
+    static CtxCur f_cur = nullptr;
+    static CtxId f_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess)
+            f_cur = (CtxCur)a;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess)
+            f_id = (CtxId)b;
+        cudaGetLastError();
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (f_cur && f_id && f_cur(&c) == CUDA_SUCCESS && c && f_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+// Device address of the scratch array, looked up with the device current when a device is
+// first used, and again whenever its context has changed since (host code may not use the
+// symbol itself: in host code it names a host-side stand-in, not device memory).
 static void* g_na_ptr[64];
-static int na_scratch(unsigned char** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return WMCD_ECUDA; }
-    if (!g_na_ptr[dev]) {
+static unsigned long long g_na_ctx[64];
+static int na_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 64) return WMCD_ECUDA;
+    const unsigned long long ctx = current_context_id();
+    if (!g_na_ptr[dev] || ctx != g_na_ctx[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return WMCD_ECUDA; }
         g_na_ptr[dev] = p;
+        g_na_ctx[dev] = ctx;
     }
     *out = (unsigned char*)g_na_ptr[dev];
     return WMCD_OK;
@@ -97,17 +133,26 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
                                       int64_t n_chains, int64_t call_index, int32_t* carry, int64_t n_moves,
                                       void* stream) {
     if (!params || !pos || !chain_len || !carry || n_chains < 1 || n_moves < 0 || call_index < 0) return WMCD_EINVAL;
+    // the checks of wmcd_create, then the limits of the static scratch
+    if (validate_params(params)) return WMCD_EINVAL;
     const wmcd_params& P = *params;
-    if (P.n_beads < 1 || P.n_beads > kNaBeads) return WMCD_EINVAL;
-    if ((int64_t)P.grid_f * P.grid_f * P.grid_f > kNaCells || P.grid_f < 1) return WMCD_EINVAL;
-    if (P.planewave_mode != WMCD_PLANEWAVE_PERIODIC || P.lcut < 0 || P.lcut > kNaLcut) return WMCD_EINVAL;
-    if (!(P.box_L > 0.0) || !(P.lambda_max > 0.0) || P.lambda_max > 0.5 * P.box_L || !(P.A0 > 0.0) || !(P.kT > 0.0))
-        return WMCD_EINVAL;
-    if (P.bond_type < 0 || P.bond_type > 2 || P.precision < 0 || P.precision > 1) return WMCD_EINVAL;
-    if (P.wca_eps != 0.0 && P.box_L / P.grid_f < kWcaCut * P.wca_sigma * (1.0 - 1e-12)) return WMCD_EINVAL;
+    if (P.n_beads > kNaBeads) return WMCD_EINVAL;
+    if ((int64_t)P.grid_f * P.grid_f * P.grid_f > kNaCells) return WMCD_EINVAL;
+    if (P.planewave_mode != WMCD_PLANEWAVE_PERIODIC || P.lcut > kNaLcut) return WMCD_EINVAL;
+    // the carried wave vector must be one of the mode table's (|l| <= lcut, not zero)
+    if (carry[0] != 0 && carry[0] != 1) return WMCD_EINVAL;
+    if (carry[0] == 1) {
+        const int64_t c2 = (int64_t)carry[1] * carry[1] + (int64_t)carry[2] * carry[2] + (int64_t)carry[3] * carry[3];
+        if (c2 == 0 || c2 > (int64_t)P.lcut * P.lcut) return WMCD_EINVAL;
+    }
+    // positions: device memory of the current device (or managed memory); another GPU's
+    // memory is refused rather than read without peer access
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
     cudaPointerAttributes pa;
     if (cudaPointerGetAttributes(&pa, pos) != cudaSuccess) { cudaGetLastError(); return WMCD_EINVAL; }
     if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return WMCD_EINVAL;
+    if (pa.type == cudaMemoryTypeDevice && pa.device != dev) return WMCD_EINVAL;
     const int64_t N = P.n_beads;
     {
         int64_t tot = 0, b = 0;
@@ -125,7 +170,7 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
         h_key[0] = P.box_L; h_key[1] = P.lambda_max; h_key[2] = (double)P.lcut;
     }
     unsigned char* base = nullptr;
-    int rc = na_scratch(&base);
+    int rc = na_scratch(dev, &base);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     SimView& v = h_view;
@@ -198,11 +243,18 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     cudaMemsetAsync(v.err, 0, sizeof(int), s);
     cudaMemsetAsync(v.img, 0, 12 * N, s);
     const int gb = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
+    // refuse non-finite or out-of-box coordinates before anything runs on them
     k_na_check<<<gb, 256, 0, s>>>(pos, N, v.L, v.err);
+    {
+        int e0 = 0;
+        cudaMemcpyAsync(&e0, v.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+        if (e0) return WMCD_ESTATE;
+    }
     k_na_fill<<<gb, 256, 0, s>>>(v.bead, pos, N);
     launch_cl_rebuild(dview, g, s, 0);
     for (int64_t m = 0; m < n_moves; m++) launch_planewave(dview, g, 1, (int)m, s);
-    k_na_read<<<gb, 256, 0, s>>>(v.bead, pos, N);
+    k_na_read<<<gb, 256, 0, s>>>(v.bead, pos, N, v.err);
     // outputs: the carried wave vector, and the error flags
     int out[5] = {0, 0, 0, 0, 0};
     cudaMemcpyAsync(out, &v.pw->carry, sizeof(int) * 4, cudaMemcpyDeviceToHost, s);

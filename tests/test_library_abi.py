@@ -101,3 +101,25 @@ def test_input_generator_geometry():
     # same seed, same system
     s2 = I.dilute_chains(n_chains=8, chain_len=40, phi=1e-3, seed=4)
     assert np.array_equal(s.pos, s2.pos)
+
+
+def test_noalloc_entry_refuses_bad_parameters_and_carry_before_any_cuda_call(lib):
+    """The allocation-free plane-wave entry point checks its parameters as wmcd_create does
+    (plus its own limits) and refuses a carried wave vector that is not in the mode table, all
+    before it makes any CUDA call (so these run without a GPU)."""
+    import ctypes
+    base = wmcd.default_params(10, 50.0, planewave_mode=wmcd.PLANEWAVE_PERIODIC, lcut=6)
+    pos = np.zeros((10, 3))
+    cl = np.array([10], np.int32)
+
+    def call(p, carry):
+        q = wmcd.make_params(p)
+        c = np.ascontiguousarray(carry, dtype=np.int32)
+        return lib.wmcd_planewave_noalloc(ctypes.byref(q), pos.ctypes.data, cl.ctypes.data, 1, 0, c.ctypes.data, 1,
+                                          None)
+    ok_carry = [0, 0, 0, 0]
+    for b in [dict(bond_type=wmcd.BOND_FENE, fene_R0=0.0), dict(lambda_min=0.0), dict(colour_K=7),
+              dict(lcut=9), dict(planewave_mode=wmcd.PLANEWAVE_OFF), dict(n_beads=20000)]:
+        assert call(dict(base, **b), ok_carry) == -1, b
+    for carry in ([2, 0, 0, 0], [-1, 1, 0, 0], [1, 0, 0, 0], [1, 7, 0, 0], [1, 4, 4, 3]):
+        assert call(base, carry) == -1, carry

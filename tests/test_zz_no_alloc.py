@@ -45,3 +45,33 @@ def test_noalloc_rejects_oversized_inputs():
     pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
     with pytest.raises(wmcd.WMCDError):
         wmcd.planewave_noalloc(p, pos, s.chain_len, 0, np.zeros(4, np.int32), 1)
+
+
+@pytest.mark.parametrize("bad", ["edge", "nan"])
+def test_noalloc_error_leaves_caller_buffers_unchanged(bad):
+    """A coordinate equal to L (outside [0, L)) or a NaN is refused with WMCD_ESTATE before any
+    move runs, and neither the caller's positions nor its carry are touched."""
+    import torch
+    s = I.dilute_chains(n_chains=4, chain_len=16, phi=5e-3, seed=5)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=3, planewave_mode=wmcd.PLANEWAVE_PERIODIC, lcut=6)
+    host = s.pos.copy()
+    host[7, 1] = s.box_L if bad == "edge" else float("nan")
+    pos = torch.tensor(host, dtype=torch.float64, device="cuda")
+    before = pos.cpu().numpy().copy()
+    carry = np.array([1, 1, -2, 0], dtype=np.int32)
+    with pytest.raises(wmcd.WMCDError) as ei:
+        wmcd.planewave_noalloc(p, pos, s.chain_len, 0, carry, 4)
+    assert ei.value.code == -5
+    after = pos.cpu().numpy()
+    assert np.array_equal(after.view(np.uint64), before.view(np.uint64))
+    assert carry.tolist() == [1, 1, -2, 0]
+
+
+def test_noalloc_refuses_host_memory():
+    s = I.dilute_chains(n_chains=2, chain_len=8, phi=5e-3, seed=6)
+    p = wmcd.default_params(s.n_beads, s.box_L, planewave_mode=wmcd.PLANEWAVE_PERIODIC, lcut=4)
+    host = s.pos.copy()
+    with pytest.raises(wmcd.WMCDError) as ei:
+        wmcd.planewave_noalloc(p, host, s.chain_len, 0, np.zeros(4, np.int32), 1)
+    assert ei.value.code == -1
+    assert np.array_equal(host, s.pos)
