@@ -100,6 +100,8 @@ typedef struct wmcd_stats_t {
     int64_t conc_bead_updates;           /* bead updates done by the concurrent wavelet kernel */
     int64_t conc_moved_beads;            /* beads written back by accepted concurrent moves */
     int64_t conc_partner_evals;          /* its pair evaluations with beads outside the support */
+    int64_t moved_beads;                 /* beads moved by accepted moves of every kind (support
+                                            sizes of accepted wavelets, N per accepted plane wave) */
 } wmcd_stats_t;
 
 typedef struct wmcd_handle wmcd_handle;
@@ -167,6 +169,25 @@ int wmcd_set_state(wmcd_handle* h, const void* buf, int64_t bytes, void* stream)
  * 4 = schedule (slots and bucketing), 5 = serial moves of large scale run on the whole GPU. */
 int wmcd_profile(wmcd_handle* h, int enable);
 int wmcd_kernel_times(wmcd_handle* h, int64_t* launches, double* ms, int n_classes, void* stream);
+
+/* Audit of the mixed-precision decisions (a checking switch; the paper has no counterpart:
+ * it checks this library's precision scheme). With the audit on, every move decided in mixed
+ * precision also evaluates its binary64 energy change dU64 beside the binary32 one dU32, and
+ * the library counts: decisions; those taken in binary32 (|dU32 - threshold| above the error
+ * band); violations, |dU32 - dU64| at or above the band; flips, binary32 decisions whose
+ * outcome dU64 would not give. The decisions themselves, and so the trajectory, are exactly
+ * those without the audit; only the binary64 work is added. wmcd_audit(h, capacity) turns it
+ * on with counters reset and room for the first `capacity` records (allocates; capacity >= 0)
+ * or off (capacity < 0); synchronises `stream`. wmcd_audit_read fills *out and copies up to
+ * `cap` records (4 doubles each: dU32, dU64, band, binary64 threshold -kT ln(1 - u)) to the
+ * host buffer `rec`; WMCD_EINVAL if the audit was never turned on. Synchronises `stream`. */
+typedef struct wmcd_audit_t {
+    int64_t decisions, outside, violations, flips;
+    double max_ratio;                    /* largest |dU32 - dU64| / band over the decisions */
+    int64_t records;                     /* records kept: min(decisions, capacity) */
+} wmcd_audit_t;
+int wmcd_audit(wmcd_handle* h, int64_t capacity, void* stream);
+int wmcd_audit_read(wmcd_handle* h, wmcd_audit_t* out, double* rec, int64_t cap, void* stream);
 
 /* Device bytes held by the handle. */
 int wmcd_device_bytes(wmcd_handle* h, int64_t* bytes);

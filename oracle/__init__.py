@@ -54,7 +54,7 @@ class OStats(ctypes.Structure):
         ("pw_attempts", ctypes.c_int64), ("pw_accepts", ctypes.c_int64),
         ("bead_updates", ctypes.c_int64), ("accepted_total", ctypes.c_int64),
         ("sim_time", ctypes.c_double), ("sweeps", ctypes.c_int64), ("n_layers", ctypes.c_int64),
-        ("dt_move", ctypes.c_double), ("p_fourier", ctypes.c_double),
+        ("dt_move", ctypes.c_double), ("p_fourier", ctypes.c_double), ("moved_beads", ctypes.c_int64),
     ]
 
 
@@ -95,6 +95,7 @@ def _load():
         "oracle_propose_moments": ([P, I64, U64, P], ctypes.c_int),
         "oracle_sweep_record": ([P, I64, P], ctypes.c_int),
         "oracle_pw_polarisation": ([P, D, P], None),
+        "oracle_sweep_sample": ([P, I64], I64),
         "oracle_planewave_field": ([P, P, D, D, P, P], None),
     }
     for name, (args, res) in sig.items():
@@ -148,6 +149,11 @@ class Oracle:
 
     def sweep(self, n: int = 1):
         self._lib.oracle_sweep(self.h, int(n))
+
+    def sweep_sample(self, max_moves: int) -> int:
+        """The first max_moves wavelet attempts of the next sweep (the rest of it skipped): a
+        bounded sample for timing. Returns the attempts made."""
+        return int(self._lib.oracle_sweep_sample(self.h, int(max_moves)))
 
     def planewave(self, n: int = 1):
         if self._lib.oracle_planewave(self.h, int(n)) != 0:

@@ -327,6 +327,7 @@ typedef struct OStats {
     int64_t sweeps;
     int64_t n_layers;
     double dt_move, p_fourier;
+    int64_t moved_beads;          // beads moved by accepted moves (support sizes; N per plane wave)
 } OStats;
 }
 
@@ -376,6 +377,9 @@ struct Sim {
     std::vector<int32_t> tr_pw_mode;
     // scratch
     std::vector<uint8_t> inS;
+    // wavelet attempts left before the current sweep is cut short (-1: no limit); only for
+    // timing a bounded sample of a sweep, never set by the tests of the method
+    int64_t move_budget = -1;
 };
 
 static inline double wrap(double x, double L, int32_t* im) {
@@ -677,7 +681,7 @@ static void run_layer(Sim& s, int l) {
         s.tr_du[l][j] = s.last_du;
         s.st.attempts[l]++;
         s.st.bead_updates += n;
-        if (r == ACCEPT) { s.st.accepts[l]++; s.st.accepted_total++; }
+        if (r == ACCEPT) { s.st.accepts[l]++; s.st.accepted_total++; s.st.moved_beads += n; }
     };
     const int G = Ly.G;
     if (G > 0) {
@@ -711,6 +715,8 @@ static void run_layer(Sim& s, int l) {
             int64_t cell = c[0] + (int64_t)G * (c[1] + (int64_t)G * c[2]);
             double carry = s.carry_q[l][cell];
             for (int64_t t = a; t < e; t++) {
+                if (s.move_budget == 0) return;
+                if (s.move_budget > 0) s.move_budget--;
                 int64_t j = keyed[t].second;
                 double lam_eff = carry > 0.0 ? carry : lam[j];
                 int n = 0;
@@ -728,6 +734,8 @@ static void run_layer(Sim& s, int l) {
     // serial phase: deferred slots in schedule order (or all slots of a serial layer)
     double carry = s.carry_serial[l];
     for (int64_t j : serial) {
+        if (s.move_budget == 0) return;
+        if (s.move_budget > 0) s.move_budget--;
         double lam_eff = carry > 0.0 ? carry : lam[j];
         int n = 0;
         int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, nullptr, &n);
@@ -840,6 +848,7 @@ static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr
         s.pw_carry = -1;
         s.st.pw_accepts++;
         s.st.accepted_total++;
+        s.st.moved_beads += s.N;
     } else {
         s.pw_carry = 1;
         for (int a = 0; a < 3; a++) s.pw_carry_l[a] = lv[a];
@@ -1181,6 +1190,20 @@ int oracle_propose_moments(void* h, int64_t n_props, uint64_t offset, double* ou
     }
     for (int k = 0; k < 27; k++) out[k] = acc[k] / (double)n_props;
     return 0;
+}
+
+// The first `max_moves` wavelet attempts of the next sweep, in schedule order; the rest of that
+// sweep is skipped (its counter still advances). For timing a bounded sample of a large
+// system's sweep; returns the attempts made.
+int64_t oracle_sweep_sample(void* h, int64_t max_moves) {
+    Sim& s = *(Sim*)h;
+    int64_t before = 0, after = 0;
+    for (int l = 0; l < 16; l++) before += s.st.attempts[l] + s.st.deferred[l];
+    s.move_budget = max_moves < 0 ? 0 : max_moves;
+    sweep_once(s);
+    s.move_budget = -1;
+    for (int l = 0; l < 16; l++) after += s.st.attempts[l] + s.st.deferred[l];
+    return after - before;
 }
 
 // run n sweeps, recording the unwrapped position of bead 0 after each

@@ -625,6 +625,7 @@ extern "C" int wmcd_stats(wmcd_handle* H, wmcd_stats_t* out, void* stream) {
     out->conc_bead_updates = (int64_t)c[C_CBU];
     out->conc_moved_beads = (int64_t)c[C_CMOVED];
     out->conc_partner_evals = (int64_t)c[C_CPE];
+    out->moved_beads = (int64_t)c[C_MOVED];
     if (err & E_WALK) return WMCD_ETIMEOUT;
     if (err & E_NONFINITE) return WMCD_ESTATE;
     return WMCD_OK;
@@ -777,6 +778,53 @@ extern "C" int wmcd_kernel_times(wmcd_handle* H, int64_t* launches, double* ms, 
     if (!H || n_classes < 0) return WMCD_EINVAL;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return WMCD_ECUDA;
     return take_kernel_times(&H->h, launches, ms, n_classes);
+}
+
+extern "C" int wmcd_audit(wmcd_handle* H, int64_t capacity, void* stream) {
+    if (!H) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capacity < 0) {
+        h->v.audit = nullptr;
+    } else {
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+        AuditDev* a = nullptr;
+        double* rec = nullptr;
+        if (dalloc(h, &a, 1) || dalloc(h, &rec, 4 * (size_t)std::max<int64_t>(capacity, 1))) return WMCD_ENOMEM;
+        AuditDev init;
+        std::memset(&init, 0, sizeof init);
+        init.rec = rec;
+        init.cap = capacity;
+        cudaMemcpyAsync(a, &init, sizeof init, cudaMemcpyHostToDevice, s);
+        h->v.audit = a;
+    }
+    cudaMemcpyAsync(h->dview, &h->v, sizeof(SimView), cudaMemcpyHostToDevice, s);
+    if (h->batch) batch_view_changed(h->batch);
+    return cudaStreamSynchronize(s) == cudaSuccess ? last_cuda_status() : WMCD_ECUDA;
+}
+
+extern "C" int wmcd_audit_read(wmcd_handle* H, wmcd_audit_t* out, double* rec, int64_t cap, void* stream) {
+    if (!H || !out || cap < 0 || (cap > 0 && !rec)) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    if (!h->v.audit) return WMCD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    AuditDev a;
+    cudaMemcpyAsync(&a, h->v.audit, sizeof a, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+    float mr;
+    std::memcpy(&mr, &a.max_ratio, sizeof mr);
+    out->decisions = (int64_t)a.n;
+    out->outside = (int64_t)a.outside;
+    out->violations = (int64_t)a.viol;
+    out->flips = (int64_t)a.flip;
+    out->max_ratio = (double)mr;
+    out->records = (int64_t)std::min<unsigned long long>(a.n, (unsigned long long)a.cap);
+    const int64_t k = std::min<int64_t>(cap, out->records);
+    if (k > 0) {
+        cudaMemcpyAsync(rec, a.rec, 4 * sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+    }
+    return last_cuda_status();
 }
 
 extern "C" int wmcd_device_bytes(wmcd_handle* H, int64_t* bytes) {

@@ -56,7 +56,7 @@ enum Outcome { ACCEPT = 1, REJECT = 2, DEFER = 3 };
 // device counters
 enum Ctr {
     C_ATT = 0, C_ACC = 16, C_DEF = 32, C_PWATT = 48, C_PWACC = 49, C_BU = 50, C_ACCTOT = 51, C_RECHECK = 52,
-    C_PARTNER = 53, C_CBU = 54, C_CMOVED = 55, C_CPE = 56, C_NCTR = 64
+    C_PARTNER = 53, C_CBU = 54, C_CMOVED = 55, C_CPE = 56, C_MOVED = 57, C_NCTR = 64
 };
 // device error bits
 enum Err { E_WALK = 1, E_SCRATCH = 2, E_NONFINITE = 4 };
@@ -77,6 +77,20 @@ struct BigMove {
     int j, n, acc;               // slot, support size (gathered), decision
     uint32_t tag;                // support mark of this move
     double lam, thr, b[3], p[3];
+};
+
+// Audit of the mixed-precision decisions (a checking switch, off by default): with it on, every
+// binary32 decision also evaluates the binary64 energy change, and the pair (with the band and
+// the threshold) is counted and recorded. The decision itself is taken exactly as without it.
+struct AuditDev {
+    unsigned long long n;        // mixed-precision decisions audited
+    unsigned long long outside;  // of which taken in binary32 (|dU32 - thr| above the band)
+    unsigned long long viol;     // |dU32 - dU64| at or above the band
+    unsigned long long flip;     // taken in binary32 with an outcome the binary64 value would not give
+    unsigned int max_ratio;      // bits of the largest |dU32 - dU64| / band (a non-negative float)
+    unsigned int pad;
+    double* rec;                 // 4 per record: dU32, dU64, band, threshold (the first `cap` decisions)
+    long long cap;
 };
 
 struct PWDev {
@@ -170,6 +184,7 @@ struct SimView {
     const int* modes;            // 3 per mode
     const double* mode_cdf;
     int n_modes;
+    AuditDev* audit;             // null: no audit of mixed-precision decisions
 };
 
 // packed image change: three 2-bit fields holding -1, 0, +1 (as 0, 1, 2)

@@ -12,6 +12,23 @@ namespace wmcd {
 
 __device__ __forceinline__ void set_err(const SimView& v, int bit) { atomicOr(v.err, bit); }
 
+// One audited mixed-precision decision: d32 and band as the decision used them, thr_cmp the
+// threshold d32 was compared with, d64 the binary64 energy change and thr64 its threshold.
+__device__ void audit_record(const SimView& v, double d32, double band, double thr_cmp, double d64, double thr64) {
+    AuditDev* A = v.audit;
+    const unsigned long long k = atomicAdd(&A->n, 1ull);
+    const bool outside = isfinite(d32) && isfinite(band) && fabs(d32 - thr_cmp) > band;
+    double ratio = 0.0;
+    if (isfinite(d32) && isfinite(d64) && isfinite(band) && band > 0.0) ratio = fabs(d32 - d64) / band;
+    if (outside) atomicAdd(&A->outside, 1ull);
+    if (ratio >= 1.0) atomicAdd(&A->viol, 1ull);
+    if (outside && ((d32 <= thr_cmp) != (d64 <= thr64))) atomicAdd(&A->flip, 1ull);
+    atomicMax(&A->max_ratio, __float_as_uint((float)ratio));
+    if ((long long)k < A->cap) {
+        A->rec[4 * k] = d32; A->rec[4 * k + 1] = d64; A->rec[4 * k + 2] = band; A->rec[4 * k + 3] = thr64;
+    }
+}
+
 // wrap and minimum image with the rare correction behind a branch that the lanes of `mask` take
 // together: written plainly, the correction's binary64 add is predicated and, on this part,
 // occupies the binary64 pipe even when no lane needs it
@@ -756,6 +773,12 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
         if (isfinite(d32) && isfinite(m32) && fabs((double)d32 - thr) > band) {
             acc = (double)d32 <= thr;
             *du_out = (double)d32;
+            if (v.audit) {
+                double d64 = 0.0;
+                int pe2 = 0;
+                energy<false>(v, sm, n, lane, ncols, nzmax, &d64, nullptr, nullptr, nullptr, &pe2);
+                if (lane == 0) audit_record(v, (double)d32, band, thr, d64, thr);
+            }
         } else {
             double d64 = 0.0;
             int pe2 = 0;
@@ -763,6 +786,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
             acc = d64 <= thr;
             *du_out = d64;
             (*recheck_out)++;
+            if (v.audit && lane == 0) audit_record(v, (double)d32, isfinite(m32) ? band : (double)INFINITY, thr, d64, thr);
         }
     } else {
         double d64 = 0.0;
@@ -856,6 +880,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     __shared__ double sh_b[3], sh_p[3], sh_carry;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total, sh_need64;
+    __shared__ float sh_a32[3];                   // binary32 energy change, band, threshold (audit)
     __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
     __shared__ int sh_T[NT / 32];
     __shared__ int sh_scan[NT];
@@ -867,7 +892,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     const int count = use_list ? *v.serial_count : M;
     if (tid == 0) sh_carry = v.carry_serial[l];
     __syncthreads();
-    long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
+    long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0, moved_n = 0;
     const float hLf = (float)hL, Lf = (float)L;
     const bool kappa_on = P.kappa != 0.0, eps_on = P.eps != 0.0;
     __shared__ double sh_lam, sh_lam2;
@@ -1219,9 +1244,10 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                 const float thr32 = (float)thr;
                 const float band = 2.0f * (float)(80 + tt + 6) * 5.9604645e-08f * mm + 1e-9f * (float)v.kT +
                                    2.4e-7f * fabsf(thr32);
+                sh_a32[0] = du; sh_a32[1] = band; sh_a32[2] = thr32;
                 if (isfinite(du) && isfinite(band) && fabsf(du - thr32) > band) {
                     sh_acc = du <= thr32;
-                    sh_need64 = 0;
+                    sh_need64 = v.audit ? 2 : 0;     // 2: the binary64 pass runs for the audit only
                     v.tr_du[Ly.tr_off + j] = (double)du;
                 } else {
                     sh_need64 = 1;
@@ -1285,8 +1311,11 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             if (tid == 0) {
                 double su = 0.0;
                 for (int w = 0; w < NT / 32; w++) su += sh_red[w];
-                sh_acc = su <= thr;
-                v.tr_du[Ly.tr_off + j] = su;
+                if (PREC == 1 && v.audit) audit_record(v, (double)sh_a32[0], (double)sh_a32[1], (double)sh_a32[2], su, thr);
+                if (PREC == 0 || sh_need64 != 2) {
+                    sh_acc = su <= thr;
+                    v.tr_du[Ly.tr_off + j] = su;
+                }
             }
             __syncthreads();
         }
@@ -1325,7 +1354,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             }
             att++;
             bu += n;
-            if (acc) acc_n++;
+            if (acc) { acc_n++; moved_n += n; }
             v.tr_out[Ly.tr_off + j] = (uint8_t)((acc ? 1 : 2) | (use_list ? 4 : 0));
             v.tr_n[Ly.tr_off + j] = n;
             sh_carry = acc ? 0.0 : lam;
@@ -1341,6 +1370,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc_n);
         atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc_n);
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+        if (moved_n) atomicAdd(&v.ctr[C_MOVED], (unsigned long long)moved_n);
         if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
     }
 }
@@ -1390,6 +1420,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
     __shared__ float sh_f32[NT / 32], sh_m32[NT / 32];
     __shared__ int sh_T[NT / 32];
     __shared__ int sh_n, sh_acc, sh_stale, sh_need64;
+    __shared__ float sh_a32[3];                   // binary32 energy change, band, threshold (audit)
     __shared__ double sh_lam, sh_lam2;
     __shared__ float sh_bf[3], sh_rl2;
     __shared__ double s_sqrt[kNCap + 1];         // sqrt(n), correctly rounded, for small supports
@@ -1418,7 +1449,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
     const bool kappa_on = P.kappa != 0.0, eps_on = P.eps != 0.0;
     const float rcf = (float)v.rc + marg;
     const float rc2f = rcf * rcf * (1.0f + 9.5367431640625e-7f);
-    long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0;
+    long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0, moved_n = 0;
     const float A0f = (float)v.A0, rcr = (float)v.rc;
     // every binary64 value the whole block needs for a move is formed once, by threads 0-2 (one
     // axis each) and shared: on this part each binary64 instruction of every warp would occupy
@@ -1683,9 +1714,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
                 const float thr32 = (float)thr;
                 const float band = 2.0f * (float)(80 + tt + 6) * 5.9604645e-08f * mm + 1e-9f * (float)v.kT +
                                    2.4e-7f * fabsf(thr32);
+                sh_a32[0] = d32; sh_a32[1] = band; sh_a32[2] = thr32;
                 if (isfinite(d32) && isfinite(band) && fabsf(d32 - thr32) > band) {
                     sh_acc = d32 <= thr32;
-                    sh_need64 = 0;
+                    sh_need64 = v.audit ? 2 : 0;     // 2: the binary64 pass runs for the audit only
                     v.tr_du[Ly.tr_off + j] = (double)d32;
                 } else {
                     sh_need64 = 1;
@@ -1750,8 +1782,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
             if (tid == 0) {
                 double su = 0.0;
                 for (int w = 0; w < NT / 32; w++) su += sh_red[w];
-                sh_acc = su <= thr;
-                v.tr_du[Ly.tr_off + j] = su;
+                if (PREC == 1 && v.audit) audit_record(v, (double)sh_a32[0], (double)sh_a32[1], (double)sh_a32[2], su, thr);
+                if (PREC == 0 || sh_need64 != 2) {
+                    sh_acc = su <= thr;
+                    v.tr_du[Ly.tr_off + j] = su;
+                }
             }
             __syncthreads();
         }
@@ -1771,7 +1806,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
         if (tid == 0) {
             att++;
             bu += n;
-            if (acc) acc_n++;
+            if (acc) { acc_n++; moved_n += n; }
             v.tr_out[Ly.tr_off + j] = (uint8_t)(acc ? 1 : 2);
             v.tr_n[Ly.tr_off + j] = n;
             sh_carry = acc ? 0.0 : lam;
@@ -1799,6 +1834,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
         atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc_n);
         atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc_n);
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+        if (moved_n) atomicAdd(&v.ctr[C_MOVED], (unsigned long long)moved_n);
     }
 }
 
@@ -2050,6 +2086,7 @@ __global__ void __launch_bounds__(256) k_pw_decide(const SimView* __restrict__ v
         P.carry = 0;
         atomicAdd(&v.ctr[C_PWACC], 1ull);
         atomicAdd(&v.ctr[C_ACCTOT], 1ull);
+        atomicAdd(&v.ctr[C_MOVED], (unsigned long long)v.N);
     } else {
         P.carry = 1;
         for (int a = 0; a < 3; a++) P.carry_l[a] = P.lv[a];
@@ -2284,6 +2321,7 @@ __global__ void __launch_bounds__(256) k_big_decide(const SimView* __restrict__ 
     if (acc) {
         atomicAdd(&v.ctr[C_ACC + l], 1ull);
         atomicAdd(&v.ctr[C_ACCTOT], 1ull);
+        if (n) atomicAdd(&v.ctr[C_MOVED], (unsigned long long)n);
     }
 }
 
@@ -2880,6 +2918,12 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         if (isfinite(d32) && isfinite(band) && fabsf(d32 - thr32) > band) {
             acc = d32 <= thr32;
             *du_out = (double)d32;
+            if (v.audit) {
+                double d64 = 0.0;
+                int pe2 = 0;
+                stage_energy64(v, S, C, n, nc, all_cand, ns, tag, lane, &d64, &pe2);
+                if (lane == 0) audit_record(v, (double)d32, (double)band, (double)thr32, d64, thr);
+            }
         } else {
             double d64 = 0.0;
             int pe2 = 0;
@@ -2887,6 +2931,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
             acc = d64 <= thr;
             *du_out = d64;
             (*recheck_out)++;
+            if (v.audit && lane == 0) audit_record(v, (double)d32, (double)band, (double)thr32, d64, thr);
         }
     } else {
         if (COOP && role != 0) return 0;
@@ -3129,6 +3174,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
         atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
         atomicAdd(&v.ctr[C_CBU], (unsigned long long)bu);
         atomicAdd(&v.ctr[C_CMOVED], (unsigned long long)moved);
+        atomicAdd(&v.ctr[C_MOVED], (unsigned long long)moved);
         atomicAdd(&v.ctr[C_CPE], (unsigned long long)pe);
         if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
     }

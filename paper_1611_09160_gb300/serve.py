@@ -80,7 +80,8 @@ class ServeReport:
 
 
 class CudaStepTimer:
-    """Device time of a batched step, from CUDA events on the step's stream."""
+    """Device time of each sweep of a batched step: a CUDA event on the step's stream before
+    the first sweep and after every sweep."""
 
     def __init__(self):
         import torch
@@ -88,16 +89,20 @@ class CudaStepTimer:
         self.stream = torch.cuda.current_stream()
 
     def start(self):
-        self.e0 = self._torch.cuda.Event(enable_timing=True)
-        self.e1 = self._torch.cuda.Event(enable_timing=True)
-        self.e0.record(self.stream)
+        e = self._torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.events = [e]
 
-    def stop(self):
-        self.e1.record(self.stream)
+    def mark(self):
+        """End of one sweep."""
+        e = self._torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.events.append(e)
 
-    def wait_ms(self) -> float:
-        self.e1.synchronize()
-        return self.e0.elapsed_time(self.e1)
+    def wait_ms(self) -> list:
+        """Milliseconds of each sweep marked since start()."""
+        self.events[-1].synchronize()
+        return [a.elapsed_time(b) for a, b in zip(self.events[:-1], self.events[1:])]
 
 
 class Server:
@@ -163,14 +168,17 @@ class Server:
                 continue
             k = min(self.chunk, min(v[1] for v in resident.values()))
             in_step = list(resident)
+            # one graph launch per sweep, with a CUDA event after each, so that the latency of
+            # every batched sweep is measured on its own
             self.timer.start()
-            self.batch.step(k)
-            self.timer.stop()
+            for _ in range(k):
+                self.batch.step(1)
+                self.timer.mark()
             # requests arriving while the step runs are admitted now, on the batch's own stream
             admit_arrived()
-            ms = self.timer.wait_ms()
-            rep.gpu_ms += ms
-            rep.sweep_ms.extend([ms / k] * k)
+            per_sweep = self.timer.wait_ms()
+            rep.gpu_ms += float(sum(per_sweep))
+            rep.sweep_ms.extend(per_sweep)
             rep.steps += 1
             for slot in in_step:
                 resident[slot][1] -= k

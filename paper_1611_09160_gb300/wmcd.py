@@ -94,7 +94,13 @@ class Stats(ctypes.Structure):
         ("dt_move", ctypes.c_double), ("p_fourier", ctypes.c_double), ("error_flags", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int64), ("conc_bead_updates", ctypes.c_int64),
         ("conc_moved_beads", ctypes.c_int64), ("conc_partner_evals", ctypes.c_int64),
+        ("moved_beads", ctypes.c_int64),
     ]
+
+
+class Audit(ctypes.Structure):
+    _fields_ = [("decisions", ctypes.c_int64), ("outside", ctypes.c_int64), ("violations", ctypes.c_int64),
+                ("flips", ctypes.c_int64), ("max_ratio", ctypes.c_double), ("records", ctypes.c_int64)]
 
 
 _lib = None
@@ -113,6 +119,8 @@ _SIGS = {
     "wmcd_profile": ["p", "i"],
     "wmcd_kernel_times": ["p", "p", "p", "i", "p"],
     "wmcd_device_bytes": ["p", "p"],
+    "wmcd_audit": ["p", "i64", "p"],
+    "wmcd_audit_read": ["p", "p", "p", "i64", "p"],
     "wmcd_destroy": ["p"],
     "wmcd_planewave_noalloc": ["p", "p", "p", "i64", "i64", "p", "i64", "p"],
     "wmcd_set_block": ["p", "i", "i"],
@@ -323,6 +331,20 @@ class Simulation:
         ms = (ctypes.c_double * n)()
         _check(self._lib.wmcd_kernel_times(self.h, la, ms, n, _stream_ptr(stream)), "wmcd_kernel_times")
         return {KERNEL_CLASSES[i]: (int(la[i]), float(ms[i])) for i in range(n)}
+
+    def audit(self, capacity: int = 0, stream=None):
+        """Audit every mixed-precision decision (binary32 against binary64, see wmcd.h);
+        capacity < 0 turns it off."""
+        _check(self._lib.wmcd_audit(self.h, int(capacity), _stream_ptr(stream)), "wmcd_audit")
+
+    def audit_read(self, cap: int = 0, stream=None):
+        """(counters as a dict, records as an array of rows dU32, dU64, band, threshold)."""
+        a = Audit()
+        rec = np.zeros((max(int(cap), 0), 4))
+        _check(self._lib.wmcd_audit_read(self.h, ctypes.byref(a), rec.ctypes.data, int(cap), _stream_ptr(stream)),
+               "wmcd_audit_read")
+        d = {k: getattr(a, k) for k, _ in Audit._fields_}
+        return d, rec[:min(int(cap), a.records)]
 
     def device_bytes(self) -> int:
         b = ctypes.c_int64()

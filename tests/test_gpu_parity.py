@@ -65,6 +65,7 @@ def compare_stats(gpu, ref):
     assert (g.pw_attempts, g.pw_accepts) == (o.pw_attempts, o.pw_accepts)
     assert g.bead_updates == o.bead_updates
     assert g.accepted_total == o.accepted_total
+    assert g.moved_beads == o.moved_beads
     assert g.sim_time == o.sim_time
     assert g.dt_move == o.dt_move
     assert g.p_fourier == pytest.approx(o.p_fourier, rel=1e-12)
@@ -109,6 +110,28 @@ def test_single_chain_fp64_10k_sweeps():
         compare_sweep(gpu, ref, ref.stats().n_layers, f"block {block}")
     compare_positions(gpu, ref, s.box_L)
     compare_stats(gpu, ref)
+
+
+def test_single_chain_mixed_10k_sweeps():
+    """Mixed precision over 10^4 sweeps, with a coloured layer and plane waves, against the
+    oracle's mixed mode (the same binary32 displacements, decisions in binary64): decisions
+    checked every 500 sweeps, positions within 1e-5 of the box at each check (in fact equal to
+    1e-12 L), identical counters at the end."""
+    s = I.single_chain(32, 64.0, seed=6)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=15, planewave_mode=wmcd.PLANEWAVE_PERIODIC,
+                            precision=wmcd.MIXED)
+    p["grid_layer"] = [2] + [0] * 15
+    gpu, ref = pair(p, s)
+    for block in range(20):
+        gpu.sweep(499)
+        ref.sweep(499)
+        gpu.sweep(1)
+        ref.sweep(1)
+        compare_sweep(gpu, ref, ref.stats().n_layers, f"block {block}")
+        compare_positions(gpu, ref, s.box_L, tol=1e-5)
+    compare_positions(gpu, ref, s.box_L)
+    compare_stats(gpu, ref)
+    assert gpu.stats().pw_attempts > 0
 
 
 @pytest.mark.parametrize("precision", [wmcd.FP64, wmcd.MIXED])

@@ -64,14 +64,20 @@ class FakeBatch:
 
 
 class FakeTimer:
-    def start(self):
-        pass
+    """Stand-in timer: every batched step takes 2 ms, split evenly over its sweeps."""
 
-    def stop(self):
-        pass
+    def __init__(self):
+        self.steps = []                  # sweeps of each batched step, in order
+
+    def start(self):
+        self.n = 0
+
+    def mark(self):
+        self.n += 1
 
     def wait_ms(self):
-        return 2.0
+        self.steps.append(self.n)
+        return [2.0 / self.n] * self.n
 
 
 def make_requests(n, seed=0):
@@ -88,7 +94,8 @@ def make_requests(n, seed=0):
 def test_every_request_runs_exactly_its_sweeps(capacity, pool, chunk):
     reqs = make_requests(40)
     fb = FakeBatch(capacity, pool)
-    srv = serve.Server(chunk=chunk, batch=fb, timer=FakeTimer())
+    timer = FakeTimer()
+    srv = serve.Server(chunk=chunk, batch=fb, timer=timer)
     rep = srv.run(reqs, realtime=False)
     assert set(rep.results) == {r.rid for r in reqs}
     for r in reqs:
@@ -101,9 +108,10 @@ def test_every_request_runs_exactly_its_sweeps(capacity, pool, chunk):
     # admission follows arrival order
     admitted = [e[1] for e in fb.log if e[0] == "admit"]
     assert admitted == sorted(admitted)
-    assert all(e[1] <= chunk for e in fb.log if e[0] == "step")
+    assert all(e[1] == 1 for e in fb.log if e[0] == "step")        # one launch per sweep
     s = rep.summary()
-    steps = [e[1] for e in fb.log if e[0] == "step"]
+    steps = timer.steps
+    assert sum(steps) == sum(1 for e in fb.log if e[0] == "step") and max(steps) <= chunk
     assert s["requests"] == 40 and s["steps"] == len(steps) and s["batched_sweeps"] == sum(steps)
     assert s["gpu_ms"] == pytest.approx(2.0 * len(steps))          # the stand-in timer: 2 ms per step
     assert 2.0 / max(steps) <= s["sweep_ms_p50"] <= s["sweep_ms_p99"] <= 2.0
