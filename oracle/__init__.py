@@ -96,6 +96,12 @@ def _load():
         "oracle_sweep_record": ([P, I64, P], ctypes.c_int),
         "oracle_pw_polarisation": ([P, D, P], None),
         "oracle_sweep_sample": ([P, I64], I64),
+        "oracle_pw_tables": ([P, P], None),
+        "oracle_k_cdf_exact": ([D], D),
+        "oracle_k_inverse": ([P, D], D),
+        "oracle_solid_angle_in_cube": ([D], D),
+        "oracle_sample_pw_k": ([P, U64, I64, P], I64),
+        "oracle_trace_pw_k": ([P, P, I64], I64),
         "oracle_planewave_field": ([P, P, D, D, P, P], None),
     }
     for name, (args, res) in sig.items():
@@ -253,6 +259,28 @@ class Oracle:
         self._lib.oracle_planewave_field(self.h, _ptr(lv), float(phi), float(psi), _ptr(pt), _ptr(out))
         return out
 
+    def pw_tables(self):
+        """(probability of the discrete cube, cube weight sum, shell weight integral, F(Q0))."""
+        out = np.zeros(4)
+        self._lib.oracle_pw_tables(self.h, _ptr(out))
+        return tuple(out)
+
+    def k_inverse(self, u: float) -> float:
+        return float(self._lib.oracle_k_inverse(self.h, float(u)))
+
+    def sample_pw_k(self, ctr: int, n: int) -> np.ndarray:
+        """n fresh plane-wave wave vectors (units of 2 pi / L) as the moves draw them."""
+        out = np.zeros((n, 3))
+        if self._lib.oracle_sample_pw_k(self.h, int(ctr), int(n), _ptr(out)) < 0:
+            raise ValueError("plane waves are off")
+        return out
+
+    def trace_pw_k(self) -> np.ndarray:
+        cap = 1 << 16
+        out = np.zeros((cap, 3))
+        m = self._lib.oracle_trace_pw_k(self.h, _ptr(out), cap)
+        return out[:m].copy()
+
     def sweep_record(self, n: int):
         out = np.zeros((n, 3))
         self._lib.oracle_sweep_record(self.h, int(n), _ptr(out))
@@ -299,6 +327,14 @@ def cos2pi_f(t: float) -> float:
 
 def inv_cbrt(w: float, lo: float) -> float:
     return float(_load().oracle_inv_cbrt(float(w), float(lo)))
+
+
+def k_cdf_exact(Q: float) -> float:
+    return float(_load().oracle_k_cdf_exact(float(Q)))
+
+
+def solid_angle_in_cube(t: float) -> float:
+    return float(_load().oracle_solid_angle_in_cube(float(t)))
 
 
 def pw_polarisation(l, psi: float) -> np.ndarray:

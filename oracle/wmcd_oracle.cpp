@@ -145,6 +145,106 @@ void G_many(const std::vector<double>& Q, std::vector<double>& out) {
 }
 
 /* ------------------------------------------------------------------------------------
+ * Distribution of |k| for the infinite system and the quasi-continuous shell (Sec. VI.B,
+ * Eqs. 52-53; Appendix D, choosing k). With Q = k lambda_max, P_k^inf is proportional to
+ * Q^2 G(Q) with integral M6/3 (Eq. 53). Integrating by parts (G' = -Q^3 phi~^2),
+ *     F(Q) = [Q^3 G(Q) + Int_0^Q q^6 phi~(q)^2 dq] / M6,
+ * which is tabulated on Q_i = i KT_H up to Q_max = KT_N KT_H. The paper converts a uniform
+ * number to k through a pre-computed table with interpolation; here: linear interpolation of
+ * F^(1/3) between the grid points (exact for the leading F ~ Q^3 G(0)/M6 at small Q, where
+ * the amplitude A_F ~ 1/k is largest), and beyond Q_max the Q^-1 tail of 1 - F that
+ * G ~ 2 pi^2 Q^-4 gives, matched at Q_max.
+ * ------------------------------------------------------------------------------------ */
+static const int KT_N = 8192;
+static const double KT_H = PI / 128.0;
+static const double M6_EXACT = 8.0 * PI * PI * PI / 5.0;   // (2 pi)^3 / 5, pinned against quadrature
+
+static void k_cdf_table(std::vector<double>& F) {
+    std::vector<double> Q(KT_N + 1), Gv, gx, gw;
+    for (int i = 0; i <= KT_N; i++) Q[i] = i * KT_H;
+    G_many(Q, Gv);
+    gauss_legendre(16, gx, gw);
+    F.assign(KT_N + 1, 0.0);
+    double cum = 0.0;
+    for (int i = 1; i <= KT_N; i++) {
+        double a = Q[i - 1], c = a + 0.5 * KT_H;
+        for (int k = 0; k < 16; k++) {
+            double q = c + 0.5 * KT_H * gx[k], f = phitilde(q);
+            double q3 = q * q * q;
+            cum += 0.5 * KT_H * gw[k] * (q3 * q3) * f * f;
+        }
+        F[i] = (Q[i] * Q[i] * Q[i] * Gv[i] + cum) / M6_EXACT;
+    }
+}
+// F(Q) by direct quadrature (no table): the normalisation of the shell uses it
+static double k_cdf_exact(double Q) {
+    std::vector<double> gx, gw, Gv;
+    gauss_legendre(16, gx, gw);
+    int panels = (int)std::ceil(Q / KT_H);
+    double cum = 0.0;
+    for (int p = 0; p < panels; p++) {
+        double a = p * KT_H, b = std::min(Q, (p + 1) * KT_H), c = 0.5 * (a + b), hh = 0.5 * (b - a);
+        for (int k = 0; k < 16; k++) {
+            double q = c + hh * gx[k], f = phitilde(q), q3 = q * q * q;
+            cum += hh * gw[k] * (q3 * q3) * f * f;
+        }
+    }
+    G_many(std::vector<double>{Q}, Gv);
+    return (Q * Q * Q * Gv[0] + cum) / M6_EXACT;
+}
+// F of the table (F^(1/3) linear between grid points; the Q^-1 tail beyond Q_max)
+static double k_cdf_interp(const std::vector<double>& F, double Q) {
+    if (Q >= KT_N * KT_H) return 1.0 - (1.0 - F[KT_N]) * (KT_N * KT_H) / Q;
+    int i = (int)(Q / KT_H);
+    if (i >= KT_N) i = KT_N - 1;
+    double a = std::cbrt(F[i]), b = std::cbrt(F[i + 1]);
+    double t = a + (b - a) * ((Q - i * KT_H) / KT_H);
+    return (t * t) * t;
+}
+// inverse of the tabulated F for u in (0, 1): the largest i with F_i <= u, then
+// Q = Q_i + KT_H (u^(1/3) - F_i^(1/3)) / (F_{i+1}^(1/3) - F_i^(1/3))
+static double k_inverse(const std::vector<double>& F, double u) {
+    if (u >= F[KT_N]) return (KT_N * KT_H) * ((1.0 - F[KT_N]) / (1.0 - u));
+    int i = (int)(std::upper_bound(F.begin(), F.end(), u) - F.begin()) - 1;
+    if (i < 0) i = 0;
+    if (i >= KT_N) i = KT_N - 1;
+    double a = std::cbrt(F[i]), b = std::cbrt(F[i + 1]);
+    return i * KT_H + KT_H * ((std::cbrt(u) - a) / (b - a));
+}
+
+// Solid angle of the directions n with |n_x|, |n_y|, |n_z| <= t (t <= 1): by Archimedes the
+// sphere's area is uniform in n_z; at height n_z the circle of radius rho = sqrt(1 - n_z^2)
+// lies in the square [-t, t]^2 for rho <= t, is cut by its four sides (arcs 2 arccos(t/rho)
+// each) for t < rho <= t sqrt 2, and lies outside beyond.
+static double solid_angle_in_cube(double t) {
+    std::vector<double> gx, gw;
+    gauss_legendre(16, gx, gw);
+    auto arc = [&](double z) {
+        double rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+        if (rho <= t) return TWO_PI;
+        if (rho <= t * std::sqrt(2.0)) return TWO_PI - 8.0 * std::acos(t / rho);
+        return 0.0;
+    };
+    // breakpoints in n_z where the regime changes, then 64 sub-panels per piece
+    std::vector<double> edges = {0.0};
+    double z1 = t < 1.0 ? std::sqrt(1.0 - t * t) : 1.0;                 // rho = t
+    double z2 = 2.0 * t * t < 1.0 ? std::sqrt(1.0 - 2.0 * t * t) : 0.0;  // rho = t sqrt 2
+    if (z2 > 0.0 && z2 < t) edges.push_back(z2);
+    if (z1 < t) edges.push_back(z1);
+    edges.push_back(std::min(t, 1.0));
+    std::sort(edges.begin(), edges.end());
+    double sum = 0.0;
+    for (size_t e = 0; e + 1 < edges.size(); e++) {
+        double a = edges[e], b = edges[e + 1];
+        for (int p = 0; p < 64; p++) {
+            double pa = a + (b - a) * p / 64.0, pb = a + (b - a) * (p + 1) / 64.0, c = 0.5 * (pa + pb), hh = 0.5 * (pb - pa);
+            for (int k = 0; k < 16; k++) sum += hh * gw[k] * arc(c + hh * gx[k]);
+        }
+    }
+    return 2.0 * sum;                                                     // n_z and -n_z
+}
+
+/* ------------------------------------------------------------------------------------
  * Random numbers. The paper only says "a pseudo random number generator" (App. D).
  * Reading: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter-based, so that
  * every draw is a pure function of (seed, simulation, sweep, layer, slot, attempt).
@@ -169,7 +269,8 @@ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
 
 // stream kinds (bits 24..31 of counter word 2)
 enum { K_COUNT = 1, K_SLOT = 2, K_VB = 3, K_VP = 4, K_ACC = 5, K_PWCOUNT = 6, K_PWMODE = 7, K_PWDIR = 8,
-       K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12, K_PROPOSE = 13 };
+       K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12, K_PROPOSE = 13,
+       K_PWSHELL = 14, K_PWKDIR = 15, K_DPWSHELL = 16, K_DPWKDIR = 17 };
 
 struct Stream {
     uint32_t k0, k1;
@@ -193,6 +294,11 @@ static Stream make_stream(uint64_t seed, uint64_t sim_id) {
 static double u53(uint32_t hi, uint32_t lo) {
     uint64_t m = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
     return (double)m * (1.0 / 9007199254740992.0);
+}
+// uniform in (0, 1): the same 53 bits with the lowest forced to 1 (never 0, never 1)
+static double u_open(uint32_t hi, uint32_t lo) {
+    uint64_t m = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
+    return (double)(m | 1u) * (1.0 / 9007199254740992.0);
 }
 // uniform integer in [0, n): high 64 bits of (64-bit draw) * n
 static int64_t pick(uint32_t hi, uint32_t lo, int64_t n) {
@@ -363,6 +469,13 @@ struct Sim {
     std::vector<double> carry_serial;           // per layer
     int pw_carry = -1;                          // carried plane-wave mode (index), -1 none
     int pw_carry_l[3] = {0, 0, 0};
+    double pw_carry_Q = 0.0;                    // infinite system: carried |k| lambda_max
+    // full periodic scheme (discrete cube + quasi-continuous shell) and infinite system
+    std::vector<double> kF;                     // tabulated F(Q), Q = |k| lambda_max
+    double kF0 = 0.0;                           // F at the shell's inner edge (periodic full)
+    double p_disc = 1.0;                        // probability of the discrete cube (periodic full)
+    double z_cube = 0.0, z_shell = 0.0;         // the two parts of the mode normalisation
+    std::vector<double> tr_pw_k;                // 3 per traced plane wave, in units of 2 pi / L
     // plane-wave tables
     std::vector<int> modes;                     // 3 per mode
     std::vector<double> mode_prob, mode_cdf;
@@ -787,29 +900,108 @@ static void pw_displacement(const Sim& s, const int lv[3], double phi, double AF
     }
 }
 
-// Returns ACCEPT or REJECT; mode receives the packed wave vector index.
+// Polarisation for a continuous unit wave vector kh (infinite system): the same construction
+// as pw_polarisation, u1 = normalise(kh x z) (x when kh is along z), u2 = kh x u1.
+static void pw_polarisation_k(const double kh[3], double psi, double e[3]) {
+    double u1[3], u2[3];
+    if (kh[0] == 0.0 && kh[1] == 0.0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
+    else {
+        double nr = std::sqrt(kh[0] * kh[0] + kh[1] * kh[1]);
+        u1[0] = kh[1] / nr; u1[1] = -kh[0] / nr; u1[2] = 0.0;
+    }
+    u2[0] = kh[1] * u1[2] - kh[2] * u1[1];
+    u2[1] = kh[2] * u1[0] - kh[0] * u1[2];
+    u2[2] = kh[0] * u1[1] - kh[1] * u1[0];
+    double cp = cos2pi(psi), sp = sin2pi(psi);
+    for (int a = 0; a < 3; a++) e[a] = cp * u1[a] + sp * u2[a];
+}
+
+// A mode of the quasi-continuous shell (Appendix D): |k| from the distribution restricted to
+// Q >= Q0 (the shell's inner edge, |l| = N_layers + 1/2), a direction as for p, the point
+// snapped to the nearest lattice mode; a mode inside the discrete cube is drawn again (up to
+// 64 attempts, after which the last one stands).
+static void shell_mode(const Sim& s, int kshell, int kkdir, uint64_t ctr, uint32_t m, int lv[3]) {
+    const int Nl = s.P.lcut;
+    for (uint32_t a = 0; a < 64; a++) {
+        U4 w = s.rng.draw(kshell, 0, ctr, m, a);
+        double us = u_open(w.v[0], w.v[1]);
+        double Q = k_inverse(s.kF, s.kF0 + us * (1.0 - s.kF0));
+        double V[3] = {0.0, 0.0, 1.0};
+        for (uint32_t b = 0; b < 64; b++) {
+            U4 d = s.rng.draw(kkdir, 0, ctr, m, 64u * a + b);
+            double x = sym(d.v[0]), y = sym(d.v[1]), z = sym(d.v[2]), q = (x * x + y * y) + z * z;
+            if (q <= 1.0 && q > 0.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+        }
+        double r = std::sqrt((V[0] * V[0] + V[1] * V[1]) + V[2] * V[2]);
+        double sc = (Q * s.L) / (TWO_PI * s.P.lambda_max);    // |k| in units of 2 pi / L
+        int inside = 1;
+        for (int c = 0; c < 3; c++) {
+            lv[c] = (int)std::floor(sc * (V[c] / r) + 0.5);
+            if (std::abs(lv[c]) > Nl) inside = 0;
+        }
+        if (!inside) return;
+    }
+}
+
+// Wave vector of a fresh (not recycled) plane wave. Periodic modes (1, 2) set lv; the infinite
+// system (3) sets the unit direction kh and Q = |k| lambda_max.
+static void pw_fresh_k(const Sim& s, int kshell, int kkdir, uint64_t ctr, uint32_t m, const U4& w1, int lv[3],
+                       double kh[3], double* Q) {
+    const int pwm = s.P.planewave_mode;
+    double u_mode = u53(w1.v[0], w1.v[1]);
+    if (pwm == 3) {
+        *Q = k_inverse(s.kF, u_open(w1.v[0], w1.v[1]));
+        double V[3];
+        ball_point(s, kkdir, 0, ctr, m, V, true);
+        double r = std::sqrt((V[0] * V[0] + V[1] * V[1]) + V[2] * V[2]);
+        for (int a = 0; a < 3; a++) kh[a] = V[a] / r;
+        return;
+    }
+    if (pwm == 2 && !(u_mode < s.p_disc)) { shell_mode(s, kshell, kkdir, ctr, m, lv); return; }
+    size_t nm = s.mode_prob.size(), idx = nm - 1;
+    for (size_t i = 0; i < nm; i++) if (u_mode < s.mode_cdf[i]) { idx = i; break; }
+    for (int a = 0; a < 3; a++) lv[a] = s.modes[3 * idx + a];
+}
+
+// Returns ACCEPT or REJECT; mode receives the packed wave vector index (-1 when a component is
+// beyond 127 or the wave vector is not a lattice mode).
 static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr, uint32_t m, int32_t* mode_out) {
+    const bool direct = kmode == K_DPWMODE;
+    const int kshell = direct ? K_DPWSHELL : K_PWSHELL, kkdir = direct ? K_DPWKDIR : K_PWKDIR;
+    const bool cont = s.P.planewave_mode == 3;
     U4 w1 = s.rng.draw(kmode, 0, ctr, m, 0);
     U4 w2 = s.rng.draw(kdir, 0, ctr, m, 0);
-    double u_mode = u53(w1.v[0], w1.v[1]), phi = u53(w1.v[2], w1.v[3]);   // phase in turns
+    double phi = u53(w1.v[2], w1.v[3]);                                     // phase in turns
     double psi = u53(w2.v[0], w2.v[1]);                                     // polarisation angle in turns
     int perm = (int)(((uint64_t)w2.v[2] * 6u) >> 32);
     uint32_t signs = w2.v[3] & 7u;
-    int lv[3];
-    if (s.pw_carry >= 0) {
+    int lv[3] = {0, 0, 0};
+    double kh[3] = {0.0, 0.0, 1.0}, Q = 0.0;
+    if (s.pw_carry >= 0 && !cont) {
         // recycle |k| after a rejection: permute the components, flip each sign with prob 1/2
         for (int a = 0; a < 3; a++) {
             int v = s.pw_carry_l[PERM[perm][a]];
             lv[a] = ((signs >> a) & 1u) ? -v : v;
         }
+    } else if (s.pw_carry >= 0 && cont) {
+        // infinite system: the same |k| with a new direction (Appendix D, parameter recycling)
+        double dummyQ;
+        pw_fresh_k(s, kshell, kkdir, ctr, m, w1, lv, kh, &dummyQ);
+        Q = s.pw_carry_Q;
     } else {
-        size_t nm = s.mode_prob.size(), idx = nm - 1;
-        for (size_t i = 0; i < nm; i++) if (u_mode < s.mode_cdf[i]) { idx = i; break; }
-        for (int a = 0; a < 3; a++) lv[a] = s.modes[3 * idx + a];
+        pw_fresh_k(s, kshell, kkdir, ctr, m, w1, lv, kh, &Q);
     }
-    *mode_out = (lv[0] + 128) | ((lv[1] + 128) << 8) | ((lv[2] + 128) << 16);
+    if (cont) {
+        *mode_out = -1;
+        double sc = (Q * s.L) / (TWO_PI * s.P.lambda_max);
+        s.tr_pw_k.insert(s.tr_pw_k.end(), {sc * kh[0], sc * kh[1], sc * kh[2]});
+    } else {
+        bool fits = std::abs(lv[0]) <= 127 && std::abs(lv[1]) <= 127 && std::abs(lv[2]) <= 127;
+        *mode_out = fits ? (lv[0] + 128) | ((lv[1] + 128) << 8) | ((lv[2] + 128) << 16) : -1;
+        s.tr_pw_k.insert(s.tr_pw_k.end(), {(double)lv[0], (double)lv[1], (double)lv[2]});
+    }
     s.st.pw_attempts++;
-    if (lv[0] == 0 && lv[1] == 0 && lv[2] == 0) {
+    if (!cont && lv[0] == 0 && lv[1] == 0 && lv[2] == 0) {
         // the k = 0 mode moves nothing and is accepted (Sec. VI.A)
         s.pw_carry = -1;
         s.st.pw_accepts++;
@@ -817,16 +1009,38 @@ static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr
         return ACCEPT;
     }
     s.st.bead_updates += s.N;
-    double AF = pw_amplitude(s, lv);
-    double e[3];
-    pw_polarisation(lv, psi, e);
+    double AF, e[3], kappa = 0.0;
+    if (cont) {
+        // A_F = (2/k) sqrt(dU_est/(mu N)) with k = Q / lambda_max (Eq. 48); the field is applied at
+        // the unwrapped positions (an infinite system: the box only organises the neighbours)
+        double kmag = Q / s.P.lambda_max;
+        AF = (2.0 * s.P.A0) / (kmag * std::sqrt(5.0 * (double)s.N));
+        pw_polarisation_k(kh, psi, e);
+        kappa = Q / (TWO_PI * s.P.lambda_max);                              // turns per unit length
+    } else {
+        AF = pw_amplitude(s, lv);
+        pw_polarisation(lv, psi, e);
+    }
     // displacement A_F cos(k.r + Phi) e of every bead (Eq. 47)
     std::vector<double> newp(3 * (size_t)s.N);
     std::vector<int32_t> newimg(3 * (size_t)s.N);
     for (int64_t i = 0; i < s.N; i++) {
         const double* r = &s.pos[3 * i];
         double dl[3];
-        pw_displacement(s, lv, phi, AF, e, r, dl);
+        if (cont) {
+            double X[3];
+            for (int a = 0; a < 3; a++) X[a] = r[a] + (double)s.img[3 * i + a] * s.L;
+            double t = kappa * ((kh[0] * X[0] + kh[1] * X[1]) + kh[2] * X[2]) + phi;
+            if (s.P.precision == 0) {
+                double amp = AF * cos2pi(t);
+                for (int a = 0; a < 3; a++) dl[a] = amp * e[a];
+            } else {
+                float amp = (float)AF * cos2pi_f(t);
+                for (int a = 0; a < 3; a++) dl[a] = (double)(amp * (float)e[a]);
+            }
+        } else {
+            pw_displacement(s, lv, phi, AF, e, r, dl);
+        }
         for (int a = 0; a < 3; a++) {
             int32_t im = s.img[3 * i + a];
             newp[3 * i + a] = wrap(r[a] + dl[a], s.L, &im);
@@ -852,6 +1066,7 @@ static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr
     } else {
         s.pw_carry = 1;
         for (int a = 0; a < 3; a++) s.pw_carry_l[a] = lv[a];
+        s.pw_carry_Q = Q;
     }
     return acc ? ACCEPT : REJECT;
 }
@@ -860,7 +1075,8 @@ static void sweep_once(Sim& s) {
     for (int l = 0; l < (int)s.layers.size(); l++) run_layer(s, l);
     s.tr_pw_out.clear();
     s.tr_pw_mode.clear();
-    if (s.P.planewave_mode == 1) {
+    s.tr_pw_k.clear();
+    if (s.P.planewave_mode != 0) {
         int64_t MF = slot_count(s, K_PWCOUNT, 0, s.sweep, (double)s.N * s.p_fourier);
         for (int64_t m = 0; m < MF; m++) {
             int32_t mode = 0;
@@ -909,13 +1125,19 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     s.r_reach = (P.wca_eps != 0.0 ? s.rc : 0.0) + 1e-6;
     // plane-wave tables and the probability of a plane-wave move (Eqs. 51, 55, 56)
     s.p_fourier = 0.0;
-    if (P.planewave_mode == 1) {
-        if (P.lcut < 0 || P.lcut > 120) return -1;
+    if (P.planewave_mode < 0 || P.planewave_mode > 3) return -1;
+    const double M6 = 8.0 * PI * PI * PI / 5.0;
+    const double rl = P.lambda_max / P.lambda_min;
+    if (P.planewave_mode == 1 || P.planewave_mode == 2) {
+        // mode 1: the sphere |l| <= lcut, normalised over itself (a truncated set);
+        // mode 2: the cube |l_i| <= lcut (= N_layers) of Appendix D plus the quasi-continuous
+        // shell outside it, normalised over all modes
+        if (P.lcut < 0 || P.lcut > (P.planewave_mode == 1 ? 120 : 40)) return -1;
         std::vector<double> Q;
         for (int lx = -P.lcut; lx <= P.lcut; lx++)
             for (int ly = -P.lcut; ly <= P.lcut; ly++)
                 for (int lz = -P.lcut; lz <= P.lcut; lz++)
-                    if (lx * lx + ly * ly + lz * lz <= P.lcut * P.lcut) {
+                    if (P.planewave_mode == 2 || lx * lx + ly * ly + lz * lz <= P.lcut * P.lcut) {
                         s.modes.insert(s.modes.end(), {lx, ly, lz});
                         Q.push_back(TWO_PI * std::sqrt((double)(lx * lx + ly * ly + lz * lz)) / s.L * P.lambda_max);
                     }
@@ -923,15 +1145,51 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
         G_many(Q, Gv);
         double tot = 0.0;
         for (double g : Gv) tot += g;
+        s.z_cube = tot;
+        double Z = tot;
+        s.p_disc = 1.0;
+        if (P.planewave_mode == 2) {
+            // shell normalisation in mode-index units u = k L / (2 pi): the integral of
+            // G(2 pi |u| lambda_max / L) over all u outside the cube C = [-c, c]^3, c = N_layers + 1/2,
+            // = (the integral outside the ball |u| = c) - (the part of C outside that ball)
+            const double c = P.lcut + 0.5, scale = TWO_PI * P.lambda_max / s.L;
+            s.kF.clear();
+            k_cdf_table(s.kF);
+            const double Q0 = scale * c;
+            s.kF0 = k_cdf_interp(s.kF, Q0);
+            const double ball_out = 4.0 * PI * (M6 / 3.0) * (1.0 - k_cdf_exact(Q0)) / (scale * scale * scale);
+            std::vector<double> gx, gw, U, W;
+            gauss_legendre(16, gx, gw);
+            const double ub = c * std::sqrt(3.0);
+            for (int p = 0; p < 256; p++) {
+                double a = c + (ub - c) * p / 256.0, b = c + (ub - c) * (p + 1) / 256.0, m = 0.5 * (a + b), hh = 0.5 * (b - a);
+                for (int k = 0; k < 16; k++) { double u = m + hh * gx[k]; U.push_back(u); W.push_back(hh * gw[k]); }
+            }
+            std::vector<double> QU(U.size()), GU;
+            for (size_t i = 0; i < U.size(); i++) QU[i] = scale * U[i];
+            G_many(QU, GU);
+            double corner = 0.0;
+            for (size_t i = 0; i < U.size(); i++) corner += W[i] * U[i] * U[i] * solid_angle_in_cube(c / U[i]) * GU[i];
+            s.z_shell = ball_out - corner;
+            Z = tot + s.z_shell;
+            s.p_disc = tot / Z;
+        }
         s.mode_prob.resize(Gv.size());
         s.mode_cdf.resize(Gv.size());
         double acc = 0.0;
-        for (size_t i = 0; i < Gv.size(); i++) { s.mode_prob[i] = Gv[i] / tot; acc += Gv[i]; s.mode_cdf[i] = acc / tot; }
-        const double M6 = 8.0 * PI * PI * PI / 5.0;
+        for (size_t i = 0; i < Gv.size(); i++) {
+            s.mode_prob[i] = Gv[i] / Z;
+            acc += Gv[i];
+            s.mode_cdf[i] = s.p_disc * (acc / tot);
+        }
         double ratio = s.L / P.lambda_max;
-        s.R = (1.0 / (6.0 * PI * PI)) * (ratio * ratio * ratio) * M6 / tot;
-        double rl = P.lambda_max / P.lambda_min;
+        s.R = (1.0 / (6.0 * PI * PI)) * (ratio * ratio * ratio) * M6 / Z;
         s.p_fourier = 1.0 / (1.0 + s.R * (rl * rl * rl - 1.0));
+    } else if (P.planewave_mode == 3) {
+        // infinite system: |k| from P_k^inf (Eq. 52), P_F^inf = (lambda_min / lambda_max)^3 (Eq. 54)
+        k_cdf_table(s.kF);
+        s.R = 1.0;
+        s.p_fourier = 1.0 / (rl * rl * rl);
     }
     // octave layers of P_lambda (Eq. 32): [lmin 2^l, lmin 2^(l+1)), the last one ending at lmax
     int nL = 1;
@@ -959,7 +1217,7 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     s.tr_du.resize(nL);
     // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2pi)^3 = 1/105)
     double A02 = P.A0 * P.A0, la2 = LAMBDA_A * LAMBDA_A;
-    if (P.planewave_mode == 1) s.dt_move = (6.0 * A02 * la2) / (105.0 * (double)s.N);
+    if (P.planewave_mode != 0) s.dt_move = (6.0 * A02 * la2) / (105.0 * (double)s.N);
     else {
         double Nl = 3.0 / (imin3 - imax3);
         s.dt_move = ((2.0 * A02 * la2) / (105.0 * (double)s.N)) * (Nl * imin3) * (1.0 - P.lambda_min / P.lambda_max);
@@ -1003,9 +1261,10 @@ int oracle_sweep(void* h, int64_t n) {
 // n plane-wave moves outside the sweep schedule (their own counter stream)
 int oracle_planewave(void* h, int64_t n) {
     Sim& s = *(Sim*)h;
-    if (s.P.planewave_mode != 1) return -1;
+    if (s.P.planewave_mode == 0) return -1;
     s.tr_pw_out.clear();
     s.tr_pw_mode.clear();
+    s.tr_pw_k.clear();
     for (int64_t m = 0; m < n; m++) {
         int32_t mode = 0;
         int r = planewave_attempt(s, K_DPWMODE, K_DPWDIR, K_DPWACC, s.pw_calls, (uint32_t)m, &mode);
@@ -1076,7 +1335,7 @@ int oracle_slot_counts(void* h, uint64_t sw, int64_t* out) {
     Sim& s = *(Sim*)h;
     int nL = (int)s.layers.size();
     for (int l = 0; l < 16; l++) out[l] = l < nL ? slot_count(s, K_COUNT, l, sw, s.layers[l].expect) : 0;
-    out[16] = s.P.planewave_mode == 1 ? slot_count(s, K_PWCOUNT, 0, sw, (double)s.N * s.p_fourier) : 0;
+    out[16] = s.P.planewave_mode != 0 ? slot_count(s, K_PWCOUNT, 0, sw, (double)s.N * s.p_fourier) : 0;
     return nL;
 }
 // scales and beads of slots 0..n-1 of layer l in the current sweep
@@ -1204,6 +1463,43 @@ int64_t oracle_sweep_sample(void* h, int64_t max_moves) {
     s.move_budget = -1;
     for (int l = 0; l < 16; l++) after += s.st.attempts[l] + s.st.deferred[l];
     return after - before;
+}
+
+// normalisation parts of the plane-wave scheme: [p_disc, z_cube, z_shell, F(Q0) of the table]
+void oracle_pw_tables(void* h, double* out) {
+    Sim& s = *(Sim*)h;
+    out[0] = s.p_disc; out[1] = s.z_cube; out[2] = s.z_shell; out[3] = s.kF0;
+}
+// tabulated F(Q) and its inverse (Q = |k| lambda_max), and the direct quadrature of F
+double oracle_k_cdf_exact(double Q) { return k_cdf_exact(Q); }
+double oracle_k_inverse(void* h, double u) { return k_inverse(((Sim*)h)->kF, u); }
+double oracle_solid_angle_in_cube(double t) { return solid_angle_in_cube(t); }
+// n fresh wave vectors as plane waves draw them (direct-call streams at counter ctr, no
+// recycling), in units of 2 pi / L, 3 per draw
+int64_t oracle_sample_pw_k(void* h, uint64_t ctr, int64_t n, double* out) {
+    Sim& s = *(Sim*)h;
+    if (s.P.planewave_mode == 0) return -1;
+    for (int64_t j = 0; j < n; j++) {
+        U4 w1 = s.rng.draw(K_DPWMODE, 0, ctr, (uint32_t)j, 0);
+        int lv[3] = {0, 0, 0};
+        double kh[3] = {0.0, 0.0, 1.0}, Q = 0.0;
+        pw_fresh_k(s, K_DPWSHELL, K_DPWKDIR, ctr, (uint32_t)j, w1, lv, kh, &Q);
+        if (s.P.planewave_mode == 3) {
+            double sc = (Q * s.L) / (TWO_PI * s.P.lambda_max);
+            for (int a = 0; a < 3; a++) out[3 * j + a] = sc * kh[a];
+        } else {
+            for (int a = 0; a < 3; a++) out[3 * j + a] = (double)lv[a];
+        }
+    }
+    return n;
+}
+// wave vectors (units of 2 pi / L) of the last sweep's or call's plane waves
+int64_t oracle_trace_pw_k(void* h, double* out, int64_t cap) {
+    Sim& s = *(Sim*)h;
+    int64_t M = (int64_t)s.tr_pw_k.size() / 3;
+    for (int64_t j = 0; j < M && j < cap; j++)
+        for (int a = 0; a < 3; a++) out[3 * j + a] = s.tr_pw_k[3 * j + a];
+    return M;
 }
 
 // run n sweeps, recording the unwrapped position of bead 0 after each

@@ -634,3 +634,156 @@ def test_slot_counts_have_the_stratified_mean():
     assert np.all((f == math.floor(xf)) | (f == math.floor(xf) + 1))
     frf = xf - math.floor(xf)
     assert abs(f.mean() - xf) < 4.5 * math.sqrt(frf * (1 - frf) / S)
+
+
+# ---- full periodic k sampling and the infinite system (Sec. VI.B-C; Appendix D) ----------
+
+def test_k_distribution_cdf_and_its_inverse():
+    """P_k^inf (Eq. 52) with N_k^inf = 3 lambda_max^3 / M6 (Eq. 53), in Q = k lambda_max: its CDF
+    F(Q) = (3/M6) Int_0^Q q^2 G(q) dq. Checked by swapping the order of integration (scipy):
+    Int_0^Q q^2 G = (1/3) Int_0^Q p^6 phi~^2 dp + (Q^3/3) G(Q), with G from scipy; by its
+    derivative 3 Q^2 G(Q) / M6; F(inf) = 1. The tabulated inverse maps F(Q) back to Q."""
+    M6 = (2 * math.pi) ** 3 / 5
+    for Q in (0.7, 2.0, 6.0, 25.0):
+        if Q < 2.0:
+            inner = integrate.quad(lambda p: p ** 6 * phitilde_by_quadrature(p) ** 2, 0, Q, epsabs=1e-13)[0]
+        else:
+            inner = (integrate.quad(lambda p: p ** 6 * phitilde_by_quadrature(p) ** 2, 0, 1.0, epsabs=1e-13)[0] +
+                     integrate.quad(lambda p: p ** 6 * phitilde_np(p) ** 2, 1.0, Q, limit=400, epsabs=1e-13)[0])
+        f = lambda x: x ** 3 * phitilde_np(x) ** 2
+        edges = np.arange(Q, 2000.0, math.pi / 2)
+        GQ = sum(integrate.quad(f, a, b, epsabs=0, epsrel=1e-12)[0] for a, b in zip(edges[:-1], edges[1:]))
+        GQ += 2 * math.pi ** 2 * edges[-1] ** -4
+        want = (inner / 3 + Q ** 3 * GQ / 3) / (M6 / 3)
+        assert O.k_cdf_exact(Q) == pytest.approx(want, rel=2e-7)
+        h = 1e-4
+        dF = (O.k_cdf_exact(Q + h) - O.k_cdf_exact(Q - h)) / (2 * h)
+        assert dF == pytest.approx(3 * Q ** 2 * O.G([Q])[0] / M6, rel=1e-5)
+    assert O.k_cdf_exact(1e4) == pytest.approx(1.0, abs=2e-4)
+    o = O.Oracle(params(n_beads=1, planewave_mode=3), np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+    for Q in (0.05, 0.9, 3.3, 47.0, 180.0, 900.0):
+        assert o.k_inverse(O.k_cdf_exact(Q)) == pytest.approx(Q, rel=2e-4 if Q < 200 else 2e-2)
+    u = np.linspace(1e-6, 1 - 1e-6, 2001)
+    q = np.array([o.k_inverse(x) for x in u])
+    assert np.all(np.diff(q) > 0)
+
+
+def test_solid_angle_of_a_sphere_inside_a_cube():
+    """The corner correction of the shell: for c < u <= c sqrt 2 the sphere of radius u loses six
+    non-overlapping caps, leaving 4 pi (3 c/u - 2); at u >= c sqrt 3 nothing is left; brute
+    force by sampling directions otherwise."""
+    for t in (1.0, 0.95, 0.8, 0.72):
+        assert O.solid_angle_in_cube(t) == pytest.approx(4 * math.pi * (3 * t - 2), rel=1e-6, abs=1e-9)
+    assert O.solid_angle_in_cube(1 / math.sqrt(3)) == pytest.approx(0.0, abs=1e-12)
+    n = np.random.default_rng(2).normal(size=(2_000_000, 3))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    for t in (0.68, 0.63, 0.6):
+        frac = np.mean(np.all(np.abs(n) <= t, axis=1))
+        assert O.solid_angle_in_cube(t) / (4 * math.pi) == pytest.approx(frac, abs=4 * math.sqrt(frac / len(n)) + 1e-5)
+
+
+def test_full_periodic_normalisation_is_the_lattice_sum():
+    """Appendix D's discrete cube (|l_i| <= N_layers) plus quasi-continuous shell: the shell's
+    weight (the integral of G over mode space outside the cube) matches the lattice sum of
+    G(k_l lambda_max) over the modes outside the cube, and the whole normalisation gives R = 1
+    (the lattice sum of G equals its integral when lambda_max <= L/2: the inverse transform of
+    G vanishes beyond 2 lambda_max, where the wavelet tensor is the harmonic Oseen tensor), so
+    P_F (Eq. 56) reaches the infinite-system value (lambda_min/lambda_max)^3 of Eq. 54 whatever
+    N_layers is."""
+    for L, lmax, Nl in ((40.0, 20.0, 8), (64.0, 16.0, 6)):
+        o = O.Oracle(params(n_beads=1, box_L=L, lambda_max=lmax, planewave_mode=2, lcut=Nl, grid_f=8),
+                     np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+        modes, prob, R, PF = o.pw_modes()
+        p_disc, zc, zs, _ = o.pw_tables()
+        assert len(modes) == (2 * Nl + 1) ** 3 and np.abs(modes).max() == Nl
+        # lattice sum over a large cube of modes, minus the discrete cube; the far tail in closed form
+        M = 60
+        r = np.arange(-M, M + 1)
+        lx, ly, lz = np.meshgrid(r, r, r, indexing="ij")
+        l = np.sqrt(lx ** 2 + ly ** 2 + lz ** 2).ravel()
+        outside = (np.maximum(np.maximum(np.abs(lx), np.abs(ly)), np.abs(lz)) > Nl).ravel()
+        scale = 2 * math.pi * lmax / L
+        ls, inv = np.unique(l[outside], return_inverse=True)
+        g = O.G(scale * ls)[inv]
+        # beyond the big cube G ~ 2 pi^2 Q^-4: the integral of |u|^-4 outside a cube of half-side a is
+        # K / a, K = 6 Int Int_[-1,1]^2 (1 + s^2 + t^2)^-2 ds dt (one face at a time, scaled)
+        K = 6 * integrate.dblquad(lambda t_, s_: (1 + s_ * s_ + t_ * t_) ** -2, -1, 1, -1, 1)[0]
+        lattice = g.sum() + 2 * math.pi ** 2 / scale ** 4 * K / (M + 0.5)
+        assert zs == pytest.approx(lattice, rel=6e-3)     # the continuum stands in for the lattice outside
+        assert zc == pytest.approx(O.G(scale * np.sqrt((modes.astype(float) ** 2).sum(1))).sum(), rel=1e-12)
+        assert p_disc == pytest.approx(zc / (zc + zs), rel=1e-14)
+        assert prob.sum() == pytest.approx(p_disc, rel=1e-12)
+        assert R == pytest.approx(1.0, abs=5e-4)
+        assert PF == pytest.approx((2.0 / lmax) ** 3, rel=6e-4)
+    Rs = []
+    for Nl in (4, 8, 15):
+        o = O.Oracle(params(n_beads=1, box_L=40.0, lambda_max=20.0, planewave_mode=2, lcut=Nl, grid_f=8),
+                     np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+        Rs.append(o.pw_modes()[2])
+    assert abs(Rs[2] - 1) < abs(Rs[1] - 1) < abs(Rs[0] - 1) < 1e-3
+
+
+def test_full_periodic_samples_and_mobility():
+    """Sampled wave vectors: modes of the cube with their probabilities, shell modes never inside
+    the cube and with the shell's radial law; from the sampled modes the periodic self-mobility
+    at the default N_layers = 15 is the infinite one times 1 - 2.837 a / L (Eq. 60)."""
+    L, A0, lmin, N = 40.0, 0.5, 2.0, 1
+    o = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, planewave_mode=2, lcut=15, grid_f=8),
+                 np.array([[1.0, 1, 1]]), np.array([1], np.int32))
+    modes, prob, R, PF = o.pw_modes()
+    p_disc, zc, zs, _ = o.pw_tables()
+    k = np.concatenate([o.sample_pw_k(ctr, 200_000) for ctr in range(5)])
+    assert np.all(k == np.round(k))
+    inside = np.all(np.abs(k) <= 15, axis=1)
+    assert abs(inside.mean() - p_disc) < 4.5 * math.sqrt(p_disc * (1 - p_disc) / len(k))
+    # the cube: the frequencies of |l|^2 classes against their summed probabilities
+    l2 = (k[inside] ** 2).sum(1).astype(int)
+    m2 = (modes.astype(int) ** 2).sum(1)
+    cls = np.unique(m2)
+    want = np.array([prob[m2 == c].sum() for c in cls]) / p_disc * inside.sum()
+    got = np.array([(l2 == c).sum() for c in cls])
+    keep = want > 20
+    chi2 = np.sum((got[keep] - want[keep]) ** 2 / want[keep])
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
+    # Eq. 60 from the sampled modes: <dr^2>_F = <A_F^2 / 2>, A_F = 2 A0 / (k sqrt(5 N))
+    kk = (2 * math.pi / L) ** 2 * (k ** 2).sum(1)
+    af2 = np.where(kk > 0, 4 * A0 ** 2 / (5 * N * np.where(kk > 0, kk, 1.0)), 0.0) / 2
+    drF, se = af2.mean(), af2.std() / math.sqrt(len(af2))
+    Nl_ = 3 / (lmin ** -3 - (L / 2) ** -3)
+    drw = 2 / 105 * A0 ** 2 * Nl_ * (1 / lmin - 2 / L)
+    total = 6 * A0 ** 2 * lmin ** 2 / 105
+    ratio = ((1 - PF) * drw + PF * drF) / total
+    a = lmin / O.lambda_a()
+    assert ratio == pytest.approx(1 - 2.837 * a / L, abs=4.5 * PF * se / total + 2e-4)
+
+
+def test_infinite_system_k_law_and_time_step():
+    """Infinite system (Sec. VI.B): |k| from P_k^inf through the tabulated inverse, k^ isotropic,
+    P_F^inf = (lambda_min/lambda_max)^3 (Eq. 54), and the time identity behind Eq. 57:
+    (1 - P_F)<dr^2>_w + P_F <dr^2>_F = 6 A0^2 lambda_min^2 / (105 N), with <dr^2>_F the mean of
+    A_F^2 / 2 over the sampled law (Eq. 54 gives 6 A0^2 lambda_max^2 / (105 N))."""
+    L, lmax, lmin, A0, N = 64.0, 32.0, 2.0, 0.5, 3
+    s = I.make_system([], N, L, seed=4)
+    o = O.Oracle(params(n_beads=N, box_L=L, lambda_max=lmax, planewave_mode=3, grid_f=8), s.pos, s.chain_len)
+    _, _, R, PF = o.pw_modes()
+    assert PF == pytest.approx((lmin / lmax) ** 3, rel=1e-15)
+    k = np.concatenate([o.sample_pw_k(ctr, 100_000) for ctr in range(3)]) * (2 * math.pi / L)
+    kn = np.linalg.norm(k, axis=1)
+    Q = kn * lmax
+    qs = np.concatenate([np.linspace(0.05, 30, 600), np.geomspace(30, 5000, 200)])
+    Fq = np.array([O.k_cdf_exact(x) for x in qs])
+    ecdf = np.searchsorted(np.sort(Q), qs) / len(Q)
+    assert np.max(np.abs(ecdf - Fq)) < 1.63 / math.sqrt(len(Q)) * 1.5 + 1e-4
+    kh = k / kn[:, None]
+    assert np.allclose(kh.T @ kh / len(kh), np.eye(3) / 3, atol=0.006)
+    # <A_F^2 / 2> with A_F = 2 A0 / (k sqrt(5 N)), over the law as drawn: u = v^3 on a fine midpoint
+    # grid of v through the oracle's inverse table (the random mean has infinite variance; in v the
+    # integrand 3 v^2 / Q(v^3)^2 is smooth at 0)
+    v = (np.arange(400_000) + 0.5) / 400_000
+    qq = np.array([o.k_inverse(x) for x in v ** 3])
+    drF = np.mean(3 * v ** 2 * 4 * A0 ** 2 / (5 * N * (qq / lmax) ** 2)) / 2
+    assert drF == pytest.approx(6 * A0 ** 2 * lmax ** 2 / (105 * N), rel=3e-3)
+    Nl_ = 3 / (lmin ** -3 - lmax ** -3)
+    drw = 2 / 105 * A0 ** 2 * Nl_ * (1 / lmin - 1 / lmax) / N
+    assert (1 - PF) * drw + PF * drF == pytest.approx(6 * A0 ** 2 * lmin ** 2 / (105 * N), rel=3e-3)
+    assert o.stats().dt_move * (lmin / O.lambda_a()) ** 2 == pytest.approx(6 * A0 ** 2 * lmin ** 2 / (105 * N), rel=1e-12)
