@@ -40,7 +40,15 @@ typedef enum wmcd_status {
 } wmcd_status;
 
 enum { WMCD_BOND_NONE = 0, WMCD_BOND_HARMONIC = 1, WMCD_BOND_FENE = 2 };
-enum { WMCD_PLANEWAVE_OFF = 0, WMCD_PLANEWAVE_PERIODIC = 1 };
+/* Plane-wave moves (Sec. VI): OFF; PERIODIC, the modes |l| <= lcut of the periodic box,
+ * normalised over that sphere; PERIODIC_FULL, the paper's periodic scheme (Appendix D): a
+ * discrete cube |l_i| <= lcut (its N_layers, 15 in the paper) and the quasi-continuous region
+ * outside it (|k| from P_k^inf restricted to the shell, snapped to the nearest mode, drawn again
+ * inside the cube), normalised over all modes; INFINITE, the infinite system (Sec. VI.B): |k|
+ * from P_k^inf (Eq. 52) by a tabulated inverse, k^ isotropic, P_F = (lambda_min/lambda_max)^3
+ * (Eq. 54), the field applied at the unwrapped positions. */
+enum { WMCD_PLANEWAVE_OFF = 0, WMCD_PLANEWAVE_PERIODIC = 1, WMCD_PLANEWAVE_PERIODIC_FULL = 2,
+       WMCD_PLANEWAVE_INFINITE = 3 };
 enum { WMCD_FP64 = 0, WMCD_MIXED = 1 };
 #define WMCD_MAX_LAYERS 16
 
@@ -59,8 +67,9 @@ typedef struct wmcd_params {
     double wca_sigma;         /* WCA repulsion (Eq. 2) between all pairs; eps = 0 disables */
     double wca_eps;
     double ext_kappa;         /* external well (kappa/2)|r - box centre|^2; 0 disables */
-    int32_t planewave_mode;   /* WMCD_PLANEWAVE_*: periodic plane-wave moves (Sec. VI) */
-    int32_t lcut;             /* plane-wave modes k = (2 pi / L) l with |l| <= lcut */
+    int32_t planewave_mode;   /* WMCD_PLANEWAVE_*: plane-wave moves (Sec. VI) */
+    int32_t lcut;             /* PERIODIC: modes k = (2 pi / L) l with |l| <= lcut (0..120);
+                                 PERIODIC_FULL: N_layers of the discrete cube (0..40) */
     int32_t precision;        /* WMCD_FP64, or WMCD_MIXED: FP32 displacements and pair
                                  energies, FP64 positions, FP64 recheck near the threshold */
     uint64_t seed;            /* Philox key, with sim_id */
@@ -112,7 +121,8 @@ typedef struct wmcd_handle wmcd_handle;
  * Validates: N >= 1; 0 < lambda_min < lambda_max <= L/2; A0 > 0; kT > 0; colour_K in 2..4;
  * grid_f >= 1 with L/grid_f >= the WCA cutoff 2^(1/6) sigma (when WCA is on);
  * 1 <= n_cap <= 256; each grid_layer[l] is 0 or a multiple of colour_K in [colour_K, 256];
- * at most 16 octave layers; lcut in 0..120 with plane waves. Returns WMCD_EINVAL otherwise.
+ * at most 16 octave layers; planewave_mode 0..3, lcut in 0..120 (PERIODIC) or 0..40
+ * (PERIODIC_FULL). Returns WMCD_EINVAL otherwise.
  * Synchronises `stream` before returning. *out receives the handle. */
 int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,
                 void* stream, wmcd_handle** out);
@@ -144,8 +154,9 @@ int wmcd_stats(wmcd_handle* h, wmcd_stats_t* out, void* stream);
 /* Per-slot outcome of the last sweep, for layer `layer` (wavelet moves) or layer = -1
  * (that sweep's plane-wave moves): out[j] = 1 accepted / 2 rejected, +4 when a concurrent
  * attempt was deferred and ran in the serial phase; n[j] = support size (plane waves: the
- * wave vector packed as (lx+128) | (ly+128) << 8 | (lz+128) << 16). Buffers are host memory
- * of `cap` entries; *count receives the number of slots. Synchronises `stream`. */
+ * wave vector packed as (lx+128) | (ly+128) << 8 | (lz+128) << 16, or -1 when a component is
+ * beyond 127 or the system is infinite: see wmcd_trace_pw_k). Buffers are host memory of `cap`
+ * entries; *count receives the number of slots. Synchronises `stream`. */
 int wmcd_trace(wmcd_handle* h, int layer, uint8_t* out, int32_t* n, int64_t cap, int64_t* count, void* stream);
 
 /* Energy change behind each wavelet decision of the last sweep, layer `layer` (host buffer of
@@ -153,6 +164,12 @@ int wmcd_trace(wmcd_handle* h, int layer, uint8_t* out, int32_t* n, int64_t cap,
  * deferred slot records the value of its serial attempt. In mixed precision the value is the
  * binary32 sum when that decided, the binary64 recheck otherwise. Synchronises `stream`. */
 int wmcd_trace_du(wmcd_handle* h, int layer, double* out, int64_t cap, int64_t* count, void* stream);
+
+/* Wave vectors of the plane waves of the last sweep (or of the last wmcd_planewave call), in
+ * units of 2 pi / L: the integer mode l for the periodic schemes, the continuous k L / (2 pi)
+ * for the infinite system. out: host, 3 doubles per move, `cap` moves; *count receives the
+ * number of moves. Synchronises `stream`. */
+int wmcd_trace_pw_k(wmcd_handle* h, double* out, int64_t cap, int64_t* count, void* stream);
 
 /* Checkpoint: the state is positions, image counters, carries, the sweep and plane-wave
  * call counters and the statistics. wmcd_state_size gives the byte size; get writes it to

@@ -212,33 +212,23 @@ static double k_inverse(const std::vector<double>& F, double u) {
     return i * KT_H + KT_H * ((std::cbrt(u) - a) / (b - a));
 }
 
-// Solid angle of the directions n with |n_x|, |n_y|, |n_z| <= t (t <= 1): by Archimedes the
-// sphere's area is uniform in n_z; at height n_z the circle of radius rho = sqrt(1 - n_z^2)
-// lies in the square [-t, t]^2 for rho <= t, is cut by its four sides (arcs 2 arccos(t/rho)
-// each) for t < rho <= t sqrt 2, and lies outside beyond.
+// Solid angle of the directions n with |n_x|, |n_y|, |n_z| <= t (t <= 1). For t >= 1/sqrt(2)
+// the sphere loses six caps that do not overlap, each of solid angle 2 pi (1 - t):
+// 4 pi - 12 pi (1 - t). Below, by Archimedes the area is uniform in n_z; at height n_z the
+// circle of radius rho = sqrt(1 - n_z^2) keeps the angle 2 pi - 8 arccos(t / rho) inside the
+// square |n_x|, |n_y| <= t while rho <= t sqrt 2 (none beyond), and rho > t on all of
+// |n_z| <= t: a smooth integrand from n_z = sqrt(1 - 2 t^2) to t.
 static double solid_angle_in_cube(double t) {
+    if (2.0 * t * t >= 1.0) return 4.0 * PI - 12.0 * PI * (1.0 - std::min(t, 1.0));
+    if (3.0 * t * t <= 1.0) return 0.0;
     std::vector<double> gx, gw;
     gauss_legendre(16, gx, gw);
-    auto arc = [&](double z) {
-        double rho = std::sqrt(std::max(0.0, 1.0 - z * z));
-        if (rho <= t) return TWO_PI;
-        if (rho <= t * std::sqrt(2.0)) return TWO_PI - 8.0 * std::acos(t / rho);
-        return 0.0;
-    };
-    // breakpoints in n_z where the regime changes, then 64 sub-panels per piece
-    std::vector<double> edges = {0.0};
-    double z1 = t < 1.0 ? std::sqrt(1.0 - t * t) : 1.0;                 // rho = t
-    double z2 = 2.0 * t * t < 1.0 ? std::sqrt(1.0 - 2.0 * t * t) : 0.0;  // rho = t sqrt 2
-    if (z2 > 0.0 && z2 < t) edges.push_back(z2);
-    if (z1 < t) edges.push_back(z1);
-    edges.push_back(std::min(t, 1.0));
-    std::sort(edges.begin(), edges.end());
-    double sum = 0.0;
-    for (size_t e = 0; e + 1 < edges.size(); e++) {
-        double a = edges[e], b = edges[e + 1];
-        for (int p = 0; p < 64; p++) {
-            double pa = a + (b - a) * p / 64.0, pb = a + (b - a) * (p + 1) / 64.0, c = 0.5 * (pa + pb), hh = 0.5 * (pb - pa);
-            for (int k = 0; k < 16; k++) sum += hh * gw[k] * arc(c + hh * gx[k]);
+    double a = std::sqrt(1.0 - 2.0 * t * t), b = t, sum = 0.0;
+    for (int p = 0; p < 16; p++) {
+        double pa = a + (b - a) * p / 16.0, pb = a + (b - a) * (p + 1) / 16.0, c = 0.5 * (pa + pb), hh = 0.5 * (pb - pa);
+        for (int k = 0; k < 16; k++) {
+            double z = c + hh * gx[k], rho = std::sqrt(1.0 - z * z);
+            sum += hh * gw[k] * (TWO_PI - 8.0 * std::acos(t / rho));
         }
     }
     return 2.0 * sum;                                                     // n_z and -n_z

@@ -82,6 +82,100 @@ static void G_table(const std::vector<double>& Q, std::vector<double>& out) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Distribution of |k| for the infinite system and the quasi-continuous shell (Sec. VI.B,
+// Eqs. 52-53): in Q = k lambda_max, P_k^inf ~ Q^2 G(Q) with integral M6/3, whose CDF is,
+// after an integration by parts (dG/dQ = -Q^3 phi~^2),
+//     F(Q) = [Q^3 G(Q) + Int_0^Q q^6 phi~(q)^2 dq] / M6.
+// Tabulated on Q_i = i kKtH (i = 0..kKtN); moves invert it by interpolation (the paper's
+// conversion table), F^(1/3) linear between grid points.
+// ---------------------------------------------------------------------------------------
+static double gl10_q6(double a, double b) {
+    double c = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+    for (int i = 0; i < 5; i++) {
+        for (int sg = -1; sg <= 1; sg += 2) {
+            const double q = c + sg * h * GL10_X[i], f = phit(q), q3 = q * q * q;
+            s += GL10_W[i] * q3 * q3 * f * f;
+        }
+    }
+    return s * h;
+}
+static const double kM6 = 8.0 * kPi * kPi * kPi / 5.0;
+static const std::vector<double>& k_cdf_table() {
+    static const std::vector<double> F = [] {
+        std::vector<double> Q(kKtN + 1), g;
+        for (int i = 0; i <= kKtN; i++) Q[i] = i * kKtH;
+        G_table(Q, g);
+        std::vector<double> t(kKtN + 1, 0.0);
+        double cum = 0.0;
+        for (int i = 1; i <= kKtN; i++) {
+            // two 10-point panels per grid step
+            cum += gl10_q6(Q[i - 1], Q[i - 1] + 0.5 * kKtH) + gl10_q6(Q[i - 1] + 0.5 * kKtH, Q[i]);
+            t[i] = (Q[i] * Q[i] * Q[i] * g[i] + cum) / kM6;
+        }
+        return t;
+    }();
+    return F;
+}
+// F(Q) directly (the shell's normalisation) and through the table (where the shell starts)
+static double k_cdf_direct(double Q) {
+    const double step = 0.5 * kKtH;
+    double cum = 0.0, a = 0.0;
+    while (a < Q) { const double b = std::min(Q, a + step); cum += gl10_q6(a, b); a = b; }
+    std::vector<double> g;
+    G_table(std::vector<double>{Q}, g);
+    return (Q * Q * Q * g[0] + cum) / kM6;
+}
+static double k_cdf_tabled(const std::vector<double>& F, double Q) {
+    if (Q >= kKtN * kKtH) return 1.0 - (1.0 - F[kKtN]) * (kKtN * kKtH) / Q;
+    int i = std::min((int)(Q / kKtH), kKtN - 1);
+    const double a = std::cbrt(F[i]), b = std::cbrt(F[i + 1]);
+    const double t = a + (b - a) * ((Q - i * kKtH) / kKtH);
+    return t * t * t;
+}
+// Solid angle of the unit vectors with every |component| <= t. With 2 t^2 >= 1 the six caps
+// n_i > t (or < -t) are disjoint, 2 pi (1 - t) each. Otherwise the area, uniform in n_z, is
+// taken height by height: for |n_z| <= t the circle of radius rho = sqrt(1 - n_z^2) > t keeps
+// 2 pi - 8 arccos(t / rho) inside the square |n_x|, |n_y| <= t when rho <= t sqrt(2), nothing
+// beyond, which leaves a smooth integral over n_z in [sqrt(1 - 2 t^2), t].
+static double cube_solid_angle(double t) {
+    if (2.0 * t * t >= 1.0) return 4.0 * kPi * (3.0 * std::min(t, 1.0) - 2.0);
+    if (3.0 * t * t <= 1.0) return 0.0;
+    const double a = std::sqrt(1.0 - 2.0 * t * t), b = t;
+    double sum = 0.0;
+    const int sub = 24;
+    for (int p = 0; p < sub; p++) {
+        const double pa = a + (b - a) * p / sub, pb = a + (b - a) * (p + 1) / sub;
+        const double c = 0.5 * (pa + pb), h = 0.5 * (pb - pa);
+        for (int i = 0; i < 5; i++)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const double z = c + sg * h * GL10_X[i], rho = std::sqrt(1.0 - z * z);
+                sum += h * GL10_W[i] * (kTwoPi - 8.0 * std::acos(t / rho));
+            }
+    }
+    return 2.0 * sum;
+}
+// Weight of the quasi-continuous shell, in mode-index units u = k L / (2 pi): the integral of
+// G(2 pi |u| lambda_max / L) over the u outside the cube [-c, c]^3, c = N_layers + 1/2; that is
+// the integral outside the ball |u| = c less the part of the cube outside that ball.
+static double shell_weight(int nl, double L, double lmax) {
+    const double c = nl + 0.5, scale = kTwoPi * lmax / L;
+    const double ball = 4.0 * kPi * (kM6 / 3.0) * (1.0 - k_cdf_direct(scale * c)) / (scale * scale * scale);
+    const double ub = c * std::sqrt(3.0);
+    std::vector<double> U, W, QU, g;
+    const int panels = 512;
+    for (int p = 0; p < panels; p++) {
+        const double a = c + (ub - c) * p / panels, b = c + (ub - c) * (p + 1) / panels, m = 0.5 * (a + b), h = 0.5 * (b - a);
+        for (int i = 0; i < 5; i++)
+            for (int sg = -1; sg <= 1; sg += 2) { U.push_back(m + sg * h * GL10_X[i]); W.push_back(h * GL10_W[i]); }
+    }
+    for (double u : U) QU.push_back(scale * u);
+    G_table(QU, g);
+    double corner = 0.0;
+    for (size_t i = 0; i < U.size(); i++) corner += W[i] * U[i] * U[i] * cube_solid_angle(c / U[i]) * g[i];
+    return ball - corner;
+}
+
 int last_cuda_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? WMCD_OK : WMCD_ECUDA;
@@ -184,8 +278,9 @@ int wmcd::validate_params(const wmcd_params* p) {
     if (p->bond_type < 0 || p->bond_type > 2 || p->colour_K < 2 || p->colour_K > 4 || p->grid_f < 1 ||
         p->n_cap < 1 || p->n_cap > kNCapMax || p->precision < 0 || p->precision > 1)
         return WMCD_EINVAL;
+    if (p->planewave_mode < 0 || p->planewave_mode > 3) return WMCD_EINVAL;
     if (p->planewave_mode == 1 && (p->lcut < 0 || p->lcut > 120)) return WMCD_EINVAL;
-    if (p->planewave_mode != 0 && p->planewave_mode != 1) return WMCD_EINVAL;
+    if (p->planewave_mode == 2 && (p->lcut < 0 || p->lcut > 40)) return WMCD_EINVAL;
     if ((int64_t)p->grid_f * p->grid_f * p->grid_f > ((int64_t)1 << 31) - 1) return WMCD_EINVAL;
     if (p->wca_eps != 0.0 && p->box_L / p->grid_f < kWcaCut * p->wca_sigma * (1.0 - 1e-12)) return WMCD_EINVAL;
     if (p->bond_type == 2 && !(p->fene_R0 > 0.0)) return WMCD_EINVAL;
@@ -236,17 +331,21 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     v.k0 = (uint32_t)P.seed;
     v.k1 = (uint32_t)(P.seed >> 32) ^ (uint32_t)P.sim_id;
 
-    // plane-wave tables and P_F (Eqs. 51, 55, 56)
+    // plane-wave tables and P_F (Eqs. 51, 55, 56): mode 1 the sphere |l| <= lcut normalised over
+    // itself; mode 2 the cube |l_i| <= lcut (N_layers) plus the quasi-continuous shell, normalised
+    // over all modes (Appendix D); mode 3 the infinite system, P_F = (lambda_min/lambda_max)^3 (Eq. 54)
     std::vector<int> modes;
     std::vector<double> cdf;
     h->p_fourier = 0.0;
-    if (P.planewave_mode == 1) {
+    double p_disc = 1.0, kF0 = 0.0;
+    const double rl = P.lambda_max / P.lambda_min;
+    if (P.planewave_mode == 1 || P.planewave_mode == 2) {
         std::vector<double> Q;
         for (int lx = -P.lcut; lx <= P.lcut; lx++)
             for (int ly = -P.lcut; ly <= P.lcut; ly++)
                 for (int lz = -P.lcut; lz <= P.lcut; lz++) {
                     int l2 = lx * lx + ly * ly + lz * lz;
-                    if (l2 > P.lcut * P.lcut) continue;
+                    if (P.planewave_mode == 1 && l2 > P.lcut * P.lcut) continue;
                     modes.push_back(lx); modes.push_back(ly); modes.push_back(lz);
                     Q.push_back(kTwoPi * std::sqrt((double)l2) / P.box_L * P.lambda_max);
                 }
@@ -254,14 +353,23 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         G_table(Q, g);
         double tot_w = 0.0;
         for (double x : g) tot_w += x;
+        double Z = tot_w;
+        if (P.planewave_mode == 2) {
+            const double zs = shell_weight(P.lcut, P.box_L, P.lambda_max);
+            Z = tot_w + zs;
+            p_disc = tot_w / Z;
+            kF0 = k_cdf_tabled(k_cdf_table(), kTwoPi * P.lambda_max / P.box_L * (P.lcut + 0.5));
+        }
         cdf.resize(g.size());
         double acc = 0.0;
-        for (size_t i = 0; i < g.size(); i++) { acc += g[i]; cdf[i] = acc / tot_w; }
+        for (size_t i = 0; i < g.size(); i++) { acc += g[i]; cdf[i] = p_disc * (acc / tot_w); }
         const double M6 = 8.0 * kPi * kPi * kPi / 5.0;
         const double ratio = P.box_L / P.lambda_max;
-        h->R = (1.0 / (6.0 * kPi * kPi)) * (ratio * ratio * ratio) * M6 / tot_w;
-        const double rl = P.lambda_max / P.lambda_min;
+        h->R = (1.0 / (6.0 * kPi * kPi)) * (ratio * ratio * ratio) * M6 / Z;
         h->p_fourier = 1.0 / (1.0 + h->R * (rl * rl * rl - 1.0));
+    } else if (P.planewave_mode == 3) {
+        h->R = 1.0;
+        h->p_fourier = 1.0 / (rl * rl * rl);
     }
     // octave layers of P_lambda (Eq. 32)
     int nL = 1;
@@ -297,7 +405,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2 pi)^3 = 1/105)
     {
         const double la = 1.0 / (1.125 - kLn2), A02 = P.A0 * P.A0, la2 = la * la;
-        if (P.planewave_mode == 1) h->dt_move = (6.0 * A02 * la2) / (105.0 * (double)h->N);
+        if (P.planewave_mode != 0) h->dt_move = (6.0 * A02 * la2) / (105.0 * (double)h->N);
         else {
             double Nl = 3.0 / (imin3 - imax3);
             h->dt_move = ((2.0 * A02 * la2) / (105.0 * (double)h->N)) * (Nl * imin3) * (1.0 - P.lambda_min / P.lambda_max);
@@ -318,7 +426,9 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     ok = ok && !dalloc(h, &v.serial_count, 4) && !dalloc(h, &v.carry_q, carry_total) &&
          !dalloc(h, &v.carry_serial, kMaxLayers);
     ok = ok && !dalloc(h, &v.tr_out, tr_total) && !dalloc(h, &v.tr_n, tr_total) && !dalloc(h, &v.tr_du, tr_total) && !dalloc(h, &v.tr_pw_out, pw_cap) &&
-         !dalloc(h, &v.tr_pw_mode, pw_cap) && !dalloc(h, &v.tr_pw_count, 1);
+         !dalloc(h, &v.tr_pw_mode, pw_cap) && !dalloc(h, &v.tr_pw_count, 1) && !dalloc(h, &v.tr_pw_k, 3 * (size_t)pw_cap);
+    double* d_kF = nullptr;
+    if (P.planewave_mode >= 2) ok = ok && !dalloc(h, &d_kF, kKtN + 1);
     ok = ok && !dalloc(h, &v.ctr, C_NCTR) && !dalloc(h, &v.err, 1);
     ok = ok && !dalloc(h, &v.s_ids, N) && !dalloc(h, &v.s_d, 4 * N) && !dalloc(h, &v.s_new, 3 * N) &&
          !dalloc(h, &v.s_img, N) && !dalloc(h, &v.s_slot, N) && !dalloc(h, &v.s_changed, 3 * N) &&
@@ -369,7 +479,13 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     v.mode_cdf = d_cdf;
     v.n_modes = (int)cdf.size();
     v.expect_F = (double)N * h->p_fourier;
-    v.pw_on = P.planewave_mode == 1;
+    v.pw_on = P.planewave_mode != 0;
+    v.pw_mode = P.planewave_mode;
+    v.pw_nl = P.lcut;
+    v.p_disc = p_disc;
+    v.kF0 = kF0;
+    v.kF = d_kF;
+    if (d_kF) cudaMemcpyAsync(d_kF, k_cdf_table().data(), (kKtN + 1) * sizeof(double), cudaMemcpyHostToDevice, s);
     {
         // shared-memory serial phase: small simulations without coloured layers, for the layers
         // of small scale (a support of a few beads; the large scales keep the cell lists)
@@ -542,16 +658,18 @@ extern "C" int wmcd_sweep(wmcd_handle* H, int64_t n_sweeps, void* stream) {
 extern "C" int wmcd_planewave(wmcd_handle* H, int64_t n_moves, void* stream) {
     if (!H || n_moves < 0) return WMCD_EINVAL;
     Handle* h = &H->h;
-    if (h->P.planewave_mode != 1) return WMCD_EINVAL;
+    if (h->P.planewave_mode == 0) return WMCD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (n_moves > h->v.tr_pw_cap) {
         // grow the trace so every move of this call is recorded
         cudaStreamSynchronize(s);
         uint8_t* o = nullptr;
         int* md = nullptr;
-        if (dalloc(h, &o, n_moves) || dalloc(h, &md, n_moves)) return WMCD_ENOMEM;
+        double* kk = nullptr;
+        if (dalloc(h, &o, n_moves) || dalloc(h, &md, n_moves) || dalloc(h, &kk, 3 * n_moves)) return WMCD_ENOMEM;
         h->v.tr_pw_out = o;
         h->v.tr_pw_mode = md;
+        h->v.tr_pw_k = kk;
         h->v.tr_pw_cap = (int)std::min<int64_t>(n_moves, 1 << 30);
         cudaMemcpyAsync(h->dview, &h->v, sizeof(SimView), cudaMemcpyHostToDevice, s);
         if (h->batch) batch_view_changed(h->batch);
@@ -684,6 +802,17 @@ static int64_t state_bytes(const Handle* h) {
     return (int64_t)sizeof(StateHeader) + 3 * h->N * (int64_t)(sizeof(double) + sizeof(int)) +
            carry_count(h) * (int64_t)sizeof(double) + kMaxLayers * (int64_t)sizeof(double) + (int64_t)sizeof(PWDev) +
            C_NCTR * (int64_t)sizeof(unsigned long long) + (int64_t)sizeof(uint32_t);
+}
+
+extern "C" int wmcd_trace_pw_k(wmcd_handle* H, double* out, int64_t cap, int64_t* count, void* stream) {
+    if (!H || !count || cap < 0 || (cap > 0 && !out)) return WMCD_EINVAL;
+    Handle* h = &H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t m = std::min<int64_t>(std::min<int64_t>(h->tr_pw_count, cap), h->v.tr_pw_cap);
+    if (m > 0) cudaMemcpyAsync(out, h->v.tr_pw_k, 3 * sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
+    *count = h->tr_pw_count;
+    return last_cuda_status();
 }
 
 extern "C" int wmcd_state_size(wmcd_handle* H, int64_t* bytes) {

@@ -74,7 +74,8 @@ WMCD_HD u4 philox4x32_10(u4 c, uint32_t k0, uint32_t k1) {
 // Stream kinds, placed in bits 24..31 of counter word 2.
 enum Kind : uint32_t {
     K_COUNT = 1, K_SLOT = 2, K_VB = 3, K_VP = 4, K_ACC = 5, K_PWCOUNT = 6, K_PWMODE = 7, K_PWDIR = 8,
-    K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12
+    K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12, K_PWSHELL = 14, K_PWKDIR = 15, K_DPWSHELL = 16,
+    K_DPWKDIR = 17
 };
 
 // counter = (index, sweep lo, kind << 24 | layer << 16 | attempt, sweep hi); key = (k0, k1)
@@ -88,6 +89,11 @@ WMCD_HD u4 draw(uint32_t k0, uint32_t k1, uint32_t kind, int layer, uint64_t swe
 WMCD_HD double u53(uint32_t hi, uint32_t lo) {
     uint64_t m = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
     return (double)m * (1.0 / 9007199254740992.0);
+}
+// uniform in (0, 1): the same 53 bits with the lowest set, so neither end is reached
+WMCD_HD double u_open(uint32_t hi, uint32_t lo) {
+    uint64_t m = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
+    return (double)(m | 1u) * (1.0 / 9007199254740992.0);
 }
 // uniform integer in [0, n): high word of the 64 x 64 product
 WMCD_HD int64_t pick(uint32_t hi, uint32_t lo, int64_t n) {

@@ -93,8 +93,16 @@ struct AuditDev {
     long long cap;
 };
 
+// |k| table of the infinite system and the quasi-continuous shell: F(Q), Q = |k| lambda_max,
+// on Q_i = i kKtH, i = 0..kKtN
+constexpr int kKtN = 8192;
+constexpr double kKtH = 3.141592653589793 / 128.0;
+
 struct PWDev {
     int lv[3];
+    int cont;                    // continuous wave vector (infinite system)
+    double kh[3], Q, kappa;      // ... its unit direction, |k| lambda_max, turns per unit length
+    double carry_Q;              // recycled |k| lambda_max (infinite system)
     int null_move;               // k = 0
     int accept;
     int mode_packed;
@@ -123,7 +131,13 @@ struct SimView {
     uint64_t* step;              // [0] sweep counter, [1] direct plane-wave call counter
     int* counts;                 // slots of the current sweep: [l] layer l, [kMaxLayers] plane waves
     double expect_F;             // expected plane-wave slots per sweep, N P_F
-    int pw_on;                   // periodic plane waves enabled
+    int pw_on;                   // plane waves enabled
+    int pw_mode;                 // 1 sphere |l| <= lcut, 2 cube + quasi-continuous shell, 3 infinite system
+    int pw_nl;                   // cube half-width N_layers (mode 2)
+    double p_disc;               // probability of the discrete cube (mode 2)
+    double kF0;                  // F at the shell's inner edge (mode 2)
+    const double* kF;            // the |k| table (modes 2, 3)
+    double* tr_pw_k;             // 3 per traced plane wave: wave vector in units of 2 pi / L
     // schedule scratch (sized for the largest layer)
     double* slot_lam;
     int* slot_bead;

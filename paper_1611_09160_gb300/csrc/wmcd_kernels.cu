@@ -1913,6 +1913,65 @@ namespace wmcd {
 // ======================================================================================
 // direct = 0: the m-th plane-wave slot of the current sweep (active if m < the sweep's count);
 // direct = 1: the m-th move of a direct call. The counter is the sweep or the call index.
+// inverse of the tabulated |k| CDF for u in (0, 1): the largest i with F_i <= u, then F^(1/3)
+// linear between Q_i and Q_{i+1}; beyond the table the Q^-1 tail of 1 - F
+__device__ double k_inverse(const double* F, double u) {
+    if (u >= F[kKtN]) return mul((double)kKtN * kKtH, dvd(sub(1.0, F[kKtN]), sub(1.0, u)));
+    int lo = 0, hi = kKtN;                 // F[lo] <= u < F[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (F[mid] <= u) lo = mid; else hi = mid;
+    }
+    const double a = cbrt(F[lo]), b = cbrt(F[lo + 1]);
+    return add(mul((double)lo, kKtH), mul(kKtH, dvd(sub(cbrt(u), a), sub(b, a))));
+}
+// a nonzero point of the unit ball by rejection (kind, counter and first attempt as given); the
+// unit vector along it
+__device__ void unit_by_rejection(const SimView& v, uint32_t kind, uint64_t ctr, uint32_t m, uint32_t a0,
+                                  double kh[3]) {
+    double V[3] = {0.0, 0.0, 1.0};
+    for (uint32_t b = 0; b < 64; b++) {
+        const u4 d = draw(v.k0, v.k1, kind, 0, ctr, m, a0 + b);
+        const double x = sym(d.x), y = sym(d.y), z = sym(d.z), q = norm2(x, y, z);
+        if (q <= 1.0 && q > 0.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+    }
+    const double r = sqr_t(norm2(V[0], V[1], V[2]));
+    for (int c = 0; c < 3; c++) kh[c] = dvd(V[c], r);
+}
+// Fresh wave vector (Appendix D): the infinite system's |k| from the table and an isotropic
+// direction; the quasi-continuous shell's snapped mode outside the discrete cube (up to 64
+// attempts, the last standing); otherwise a mode of the table by its cumulative probability.
+__device__ void pw_fresh_k(const SimView& v, uint32_t kshell, uint32_t kkdir, uint64_t ctr, uint32_t m, const u4& w1,
+                           int lv[3], double kh[3], double* Q) {
+    const double u_mode = u53(w1.x, w1.y);
+    if (v.pw_mode == 3) {
+        *Q = k_inverse(v.kF, u_open(w1.x, w1.y));
+        unit_by_rejection(v, kkdir, ctr, m, 0u, kh);
+        return;
+    }
+    if (v.pw_mode == 2 && !(u_mode < v.p_disc)) {
+        const double lmax = v.layer[v.nL - 1].hi;
+        for (uint32_t a = 0; a < 64; a++) {
+            const u4 w = draw(v.k0, v.k1, kshell, 0, ctr, m, a);
+            const double us = u_open(w.x, w.y);
+            const double q = k_inverse(v.kF, add(v.kF0, mul(us, sub(1.0, v.kF0))));
+            double d[3];
+            unit_by_rejection(v, kkdir, ctr, m, 64u * a, d);
+            const double sc = dvd(mul(q, v.L), mul(kTwoPi, lmax));
+            int inside = 1;
+            for (int c = 0; c < 3; c++) {
+                lv[c] = (int)floor(add(mul(sc, d[c]), 0.5));
+                if (abs(lv[c]) > v.pw_nl) inside = 0;
+            }
+            if (!inside) return;
+        }
+        return;
+    }
+    int lo = 0, hi = v.n_modes - 1;           // first mode with u < cdf
+    while (lo < hi) { int mid = (lo + hi) >> 1; if (u_mode < v.mode_cdf[mid]) hi = mid; else lo = mid + 1; }
+    for (int a = 0; a < 3; a++) lv[a] = v.modes[3 * lo + a];
+}
+
 __global__ void k_pw_setup(const SimView* __restrict__ vs, int direct, int m) {
     SIM_PROLOGUE
     if (threadIdx.x != 0) return;
@@ -1922,32 +1981,42 @@ __global__ void k_pw_setup(const SimView* __restrict__ vs, int direct, int m) {
     if (!P.active) return;
     const uint64_t ctr = v.step[direct ? 1 : 0];
     const int kmode = direct ? K_DPWMODE : K_PWMODE, kdir = direct ? K_DPWDIR : K_PWDIR;
+    const uint32_t kshell = direct ? K_DPWSHELL : K_PWSHELL, kkdir = direct ? K_DPWKDIR : K_PWKDIR;
+    const bool cont = v.pw_mode == 3;
     const int trace_index = m;
     u4 w1 = draw(v.k0, v.k1, (uint32_t)kmode, 0, ctr, (uint32_t)m, 0);
     u4 w2 = draw(v.k0, v.k1, (uint32_t)kdir, 0, ctr, (uint32_t)m, 0);
-    const double u_mode = u53(w1.x, w1.y), phi = u53(w1.z, w1.w), psi = u53(w2.x, w2.y);
+    const double phi = u53(w1.z, w1.w), psi = u53(w2.x, w2.y);
     const int perm = (int)(((uint64_t)w2.z * 6u) >> 32);
     const uint32_t signs = w2.w & 7u;
     const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    int lv[3];
-    if (P.carry) {
+    int lv[3] = {0, 0, 0};
+    double kh[3] = {0.0, 0.0, 1.0}, Q = 0.0;
+    if (P.carry && !cont) {
         // recycle |k| after a rejection: permute the components, flip each sign with prob 1/2
         for (int a = 0; a < 3; a++) {
             int x = P.carry_l[PERM[perm][a]];
             lv[a] = ((signs >> a) & 1u) ? -x : x;
         }
     } else {
-        int lo = 0, hi = v.n_modes - 1;           // first mode with u < cdf
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (u_mode < v.mode_cdf[mid]) hi = mid; else lo = mid + 1; }
-        for (int a = 0; a < 3; a++) lv[a] = v.modes[3 * lo + a];
+        pw_fresh_k(v, kshell, kkdir, ctr, (uint32_t)m, w1, lv, kh, &Q);
+        if (P.carry && cont) Q = P.carry_Q;     // the same |k|, a new direction
     }
+    const double lmax = v.layer[v.nL - 1].hi;
     for (int a = 0; a < 3; a++) P.lv[a] = lv[a];
-    P.mode_packed = (lv[0] + 128) | ((lv[1] + 128) << 8) | ((lv[2] + 128) << 16);
+    P.cont = cont;
+    P.Q = Q;
+    const bool fits = abs(lv[0]) <= 127 && abs(lv[1]) <= 127 && abs(lv[2]) <= 127;
+    P.mode_packed = (cont || !fits) ? -1 : (lv[0] + 128) | ((lv[1] + 128) << 8) | ((lv[2] + 128) << 16);
     P.phi = phi;
-    P.null_move = (lv[0] == 0 && lv[1] == 0 && lv[2] == 0);
+    P.null_move = !cont && (lv[0] == 0 && lv[1] == 0 && lv[2] == 0);
     P.accept = 0;
     atomicAdd(&v.ctr[C_PWATT], 1ull);
-    if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_mode[trace_index] = P.mode_packed;
+    if (trace_index >= 0 && trace_index < v.tr_pw_cap) {
+        v.tr_pw_mode[trace_index] = P.mode_packed;
+        const double sc = cont ? dvd(mul(Q, v.L), mul(kTwoPi, lmax)) : 0.0;
+        for (int a = 0; a < 3; a++) v.tr_pw_k[3 * trace_index + a] = cont ? mul(sc, kh[a]) : (double)lv[a];
+    }
     if (P.null_move) {
         // k = 0 moves nothing and is accepted (Sec. VI.A)
         P.accept = 1;
@@ -1957,17 +2026,32 @@ __global__ void k_pw_setup(const SimView* __restrict__ vs, int direct, int m) {
         if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_out[trace_index] = 1;
         return;
     }
-    // A_F = (2/k) sqrt(dU_est/(mu N)), dU_est/mu = M6 A0^2/(2 pi)^3 = A0^2/5 (Eq. 48)
-    const int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
-    const double lm = sqr_t((double)l2);
-    const double kmag = dvd(mul(kTwoPi, lm), v.L);
-    P.AF = dvd(mul(2.0, v.A0), mul(kmag, sqr_t(mul(5.0, (double)v.N))));
-    // polarisation e perpendicular to k: e = cos(psi) u1 + sin(psi) u2, u1 = k x z / |k x z|
-    double kh[3] = {dvd((double)lv[0], lm), dvd((double)lv[1], lm), dvd((double)lv[2], lm)}, u1[3], u2[3];
-    if (lv[0] == 0 && lv[1] == 0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
-    else {
-        double nr = sqr_t((double)(lv[0] * lv[0] + lv[1] * lv[1]));
-        u1[0] = dvd((double)lv[1], nr); u1[1] = dvd((double)(-lv[0]), nr); u1[2] = 0.0;
+    double u1[3], u2[3];
+    if (cont) {
+        // infinite system: A_F = (2/k) sqrt(dU_est/(mu N)) with k = Q / lambda_max (Eq. 48), the
+        // polarisation about the continuous direction kh, the phase in turns per unit length
+        const double kmag = dvd(Q, lmax);
+        P.AF = dvd(mul(2.0, v.A0), mul(kmag, sqr_t(mul(5.0, (double)v.N))));
+        P.kappa = dvd(Q, mul(kTwoPi, lmax));
+        for (int a = 0; a < 3; a++) P.kh[a] = kh[a];
+        if (kh[0] == 0.0 && kh[1] == 0.0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
+        else {
+            const double nr = sqr_t(add(mul(kh[0], kh[0]), mul(kh[1], kh[1])));
+            u1[0] = dvd(kh[1], nr); u1[1] = dvd(-kh[0], nr); u1[2] = 0.0;
+        }
+    } else {
+        // A_F = (2/k) sqrt(dU_est/(mu N)), dU_est/mu = M6 A0^2/(2 pi)^3 = A0^2/5 (Eq. 48)
+        const int l2 = lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2];
+        const double lm = sqr_t((double)l2);
+        const double kmag = dvd(mul(kTwoPi, lm), v.L);
+        P.AF = dvd(mul(2.0, v.A0), mul(kmag, sqr_t(mul(5.0, (double)v.N))));
+        // polarisation e perpendicular to k: e = cos(psi) u1 + sin(psi) u2, u1 = k x z / |k x z|
+        kh[0] = dvd((double)lv[0], lm); kh[1] = dvd((double)lv[1], lm); kh[2] = dvd((double)lv[2], lm);
+        if (lv[0] == 0 && lv[1] == 0) { u1[0] = 1.0; u1[1] = 0.0; u1[2] = 0.0; }
+        else {
+            double nr = sqr_t((double)(lv[0] * lv[0] + lv[1] * lv[1]));
+            u1[0] = dvd((double)lv[1], nr); u1[1] = dvd((double)(-lv[0]), nr); u1[2] = 0.0;
+        }
     }
     u2[0] = sub(mul(kh[1], u1[2]), mul(kh[2], u1[1]));
     u2[1] = sub(mul(kh[2], u1[0]), mul(kh[0], u1[2]));
@@ -1987,7 +2071,15 @@ __global__ void k_pw_disp(const SimView* __restrict__ vs) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.N; i += (int64_t)gridDim.x * blockDim.x) {
         const Bead b = v.bead[i];
         const double r[3] = {b.x, b.y, b.z};
-        const double t = add(dvd(add(add(mul(lx, r[0]), mul(ly, r[1])), mul(lz, r[2])), v.L), P.phi);
+        double t;
+        if (P.cont) {
+            // infinite system: the field at the unwrapped position
+            double X[3];
+            for (int a = 0; a < 3; a++) X[a] = add(r[a], mul((double)v.img[3 * i + a], v.L));
+            t = add(mul(P.kappa, add(add(mul(P.kh[0], X[0]), mul(P.kh[1], X[1])), mul(P.kh[2], X[2]))), P.phi);
+        } else {
+            t = add(dvd(add(add(mul(lx, r[0]), mul(ly, r[1])), mul(lz, r[2])), v.L), P.phi);
+        }
         double dl[3];
         if (v.precision == 0) {
             const double amp = mul(P.AF, cos2pi(t));
@@ -2090,6 +2182,7 @@ __global__ void __launch_bounds__(256) k_pw_decide(const SimView* __restrict__ v
     } else {
         P.carry = 1;
         for (int a = 0; a < 3; a++) P.carry_l[a] = P.lv[a];
+        P.carry_Q = P.Q;
     }
     if (trace_index >= 0 && trace_index < v.tr_pw_cap) v.tr_pw_out[trace_index] = (uint8_t)(acc ? 1 : 2);
 }

@@ -217,6 +217,8 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     v.counts = (int*)(base + oCounts);
     v.cl_stale = (int*)(base + oClStale);
     v.pw_on = 1;
+    v.pw_mode = WMCD_PLANEWAVE_PERIODIC;
+    v.pw_nl = P.lcut;
     SimView* dview = (SimView*)(base + oView);
     GroupDims g;
     g.S = 1;

@@ -26,7 +26,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 
 MAX_LAYERS = 16
 BOND_NONE, BOND_HARMONIC, BOND_FENE = 0, 1, 2
-PLANEWAVE_OFF, PLANEWAVE_PERIODIC = 0, 1
+PLANEWAVE_OFF, PLANEWAVE_PERIODIC, PLANEWAVE_PERIODIC_FULL, PLANEWAVE_INFINITE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 STATUS = {0: "WMCD_OK", -1: "WMCD_EINVAL", -2: "WMCD_ENOMEM", -3: "WMCD_ECUDA", -4: "WMCD_ETIMEOUT", -5: "WMCD_ESTATE",
           -6: "WMCD_EFULL"}
@@ -113,6 +113,7 @@ _SIGS = {
     "wmcd_stats": ["p", "p", "p"],
     "wmcd_trace": ["p", "i", "p", "p", "i64", "p", "p"],
     "wmcd_trace_du": ["p", "i", "p", "i64", "p", "p"],
+    "wmcd_trace_pw_k": ["p", "p", "i64", "p", "p"],
     "wmcd_state_size": ["p", "p"],
     "wmcd_get_state": ["p", "p", "i64", "p"],
     "wmcd_set_state": ["p", "p", "i64", "p"],
@@ -309,6 +310,15 @@ class Simulation:
         cnt = ctypes.c_int64()
         _check(self._lib.wmcd_trace_du(self.h, int(layer), out.ctypes.data, cap, ctypes.byref(cnt),
                                        _stream_ptr(stream)), "wmcd_trace_du")
+        return out[:min(cnt.value, cap)].copy()
+
+    def trace_pw_k(self, stream=None):
+        """Wave vectors (units of 2 pi / L) of the last sweep's or call's plane waves, N x 3."""
+        cap = 4 * self.n + 4096
+        out = np.zeros((cap, 3))
+        cnt = ctypes.c_int64()
+        _check(self._lib.wmcd_trace_pw_k(self.h, out.ctypes.data, cap, ctypes.byref(cnt), _stream_ptr(stream)),
+               "wmcd_trace_pw_k")
         return out[:min(cnt.value, cap)].copy()
 
     def get_state(self, stream=None) -> bytes:
