@@ -50,6 +50,8 @@ enum { WMCD_BOND_NONE = 0, WMCD_BOND_HARMONIC = 1, WMCD_BOND_FENE = 2 };
 enum { WMCD_PLANEWAVE_OFF = 0, WMCD_PLANEWAVE_PERIODIC = 1, WMCD_PLANEWAVE_PERIODIC_FULL = 2,
        WMCD_PLANEWAVE_INFINITE = 3 };
 enum { WMCD_FP64 = 0, WMCD_MIXED = 1 };
+enum { WMCD_ACCEPT_METROPOLIS = 0, WMCD_ACCEPT_GLAUBER = 1 };
+enum { WMCD_CENTRE_BEAD = 0, WMCD_CENTRE_UNIFORM = 1 };
 #define WMCD_MAX_LAYERS 16
 
 /* Parameters of one simulation. */
@@ -87,6 +89,11 @@ typedef struct wmcd_params {
                                  beads runs each of its moves on the whole GPU (Sec. VIII: large
                                  moves in parallel); 0 = 2048, negative = never. A launch choice:
                                  decisions do not depend on it */
+    int32_t acceptance;       /* WMCD_ACCEPT_METROPOLIS (Eq. 20) or WMCD_ACCEPT_GLAUBER (Secs. V.C,
+                                 VIII: accept with probability 1 / (1 + exp(dU / kT))) */
+    int32_t centring;         /* WMCD_CENTRE_BEAD: b within lambda of a picked bead (Eq. 26,
+                                 A_w of Eq. 29); WMCD_CENTRE_UNIFORM: b uniform in the box, A_w from
+                                 the mean support at the global density (Sec. V.D) */
 } wmcd_params;
 
 /* Counters since creation (or the last wmcd_set_state). */

@@ -44,7 +44,8 @@ class OParams(ctypes.Structure):
         ("planewave_mode", ctypes.c_int32), ("lcut", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("sim_id", ctypes.c_uint64),
         ("colour_K", ctypes.c_int32), ("grid_f", ctypes.c_int32), ("n_cap", ctypes.c_int32),
-        ("grid_layer", ctypes.c_int32 * 16),
+        ("grid_layer", ctypes.c_int32 * 16), ("big_support", ctypes.c_int32),
+        ("acceptance", ctypes.c_int32), ("centring", ctypes.c_int32),
     ]
 
 
@@ -96,6 +97,7 @@ def _load():
         "oracle_sweep_record": ([P, I64, P], ctypes.c_int),
         "oracle_pw_polarisation": ([P, D, P], None),
         "oracle_sweep_sample": ([P, I64], I64),
+        "oracle_sample_threshold": ([P, U64, I64, P], I64),
         "oracle_pw_tables": ([P, P], None),
         "oracle_k_cdf_exact": ([D], D),
         "oracle_k_inverse": ([P, D], D),
@@ -264,6 +266,12 @@ class Oracle:
         out = np.zeros(4)
         self._lib.oracle_pw_tables(self.h, _ptr(out))
         return tuple(out)
+
+    def sample_threshold(self, sweep: int, n: int) -> np.ndarray:
+        """Acceptance thresholds of n slots (accept iff dU <= threshold)."""
+        out = np.zeros(n)
+        self._lib.oracle_sample_threshold(self.h, int(sweep), int(n), _ptr(out))
+        return out
 
     def k_inverse(self, u: float) -> float:
         return float(self._lib.oracle_k_inverse(self.h, float(u)))

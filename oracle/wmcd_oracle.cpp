@@ -165,14 +165,17 @@ static void k_cdf_table(std::vector<double>& F) {
     G_many(Q, Gv);
     gauss_legendre(16, gx, gw);
     F.assign(KT_N + 1, 0.0);
-    double cum = 0.0;
+    double cum = 0.0, comp = 0.0;             // compensated (Kahan) running sum over the panels
     for (int i = 1; i <= KT_N; i++) {
-        double a = Q[i - 1], c = a + 0.5 * KT_H;
+        double a = Q[i - 1], c = a + 0.5 * KT_H, panel = 0.0;
         for (int k = 0; k < 16; k++) {
             double q = c + 0.5 * KT_H * gx[k], f = phitilde(q);
             double q3 = q * q * q;
-            cum += 0.5 * KT_H * gw[k] * (q3 * q3) * f * f;
+            panel += 0.5 * KT_H * gw[k] * (q3 * q3) * f * f;
         }
+        double y = panel - comp, t = cum + y;
+        comp = (t - cum) - y;
+        cum = t;
         F[i] = (Q[i] * Q[i] * Q[i] * Gv[i] + cum) / M6_EXACT;
     }
 }
@@ -181,13 +184,16 @@ static double k_cdf_exact(double Q) {
     std::vector<double> gx, gw, Gv;
     gauss_legendre(16, gx, gw);
     int panels = (int)std::ceil(Q / KT_H);
-    double cum = 0.0;
+    double cum = 0.0, comp = 0.0;
     for (int p = 0; p < panels; p++) {
-        double a = p * KT_H, b = std::min(Q, (p + 1) * KT_H), c = 0.5 * (a + b), hh = 0.5 * (b - a);
+        double a = p * KT_H, b = std::min(Q, (p + 1) * KT_H), c = 0.5 * (a + b), hh = 0.5 * (b - a), panel = 0.0;
         for (int k = 0; k < 16; k++) {
             double q = c + hh * gx[k], f = phitilde(q), q3 = q * q * q;
-            cum += hh * gw[k] * (q3 * q3) * f * f;
+            panel += hh * gw[k] * (q3 * q3) * f * f;
         }
+        double y = panel - comp, t = cum + y;
+        comp = (t - cum) - y;
+        cum = t;
     }
     G_many(std::vector<double>{Q}, Gv);
     return (Q * Q * Q * Gv[0] + cum) / M6_EXACT;
@@ -260,7 +266,7 @@ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
 // stream kinds (bits 24..31 of counter word 2)
 enum { K_COUNT = 1, K_SLOT = 2, K_VB = 3, K_VP = 4, K_ACC = 5, K_PWCOUNT = 6, K_PWMODE = 7, K_PWDIR = 8,
        K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12, K_PROPOSE = 13,
-       K_PWSHELL = 14, K_PWKDIR = 15, K_DPWSHELL = 16, K_DPWKDIR = 17 };
+       K_PWSHELL = 14, K_PWKDIR = 15, K_DPWSHELL = 16, K_DPWKDIR = 17, K_BUNI = 18 };
 
 struct Stream {
     uint32_t k0, k1;
@@ -412,6 +418,9 @@ typedef struct OParams {
     int32_t grid_f;               // fine cells per axis
     int32_t n_cap;                // largest support handled by a concurrent move
     int32_t grid_layer[16];       // coarse cells per axis per layer, 0 = serial layer
+    int32_t big_support;          // a launch choice of the GPU library; no meaning here
+    int32_t acceptance;           // 0 Metropolis (Eq. 20), 1 Glauber
+    int32_t centring;             // 0 centre near a picked bead (Eq. 26), 1 uniform in the box (Sec. V.D)
 } OParams;
 
 typedef struct OStats {
@@ -572,11 +581,20 @@ static double delta_U(Sim& s, const std::vector<int64_t>& S, const std::vector<d
     return dU;
 }
 
-// Metropolis test (Eq. 20): accept with probability min(1, exp(-dU/kT)), i.e. accept iff
-// dU <= -kT ln(1 - u) with u uniform in [0, 1); an infinite or undefined dU rejects.
-static bool metropolis(const Sim& s, double dU, double u) {
-    double thr = -s.P.kT * std::log(1.0 - u);
-    return dU <= thr;
+// Acceptance test on the draw w. Metropolis (Eq. 20): accept with probability
+// min(1, exp(-dU/kT)), i.e. iff dU <= -kT ln(1 - u) with u uniform in [0, 1). Glauber (the
+// paper's proposed alternative, Secs. V.C and VIII): accept with probability
+// 1 / (1 + exp(dU/kT)), i.e. iff dU <= kT (ln(1 - u) - ln u) with u uniform in (0, 1).
+// An infinite or undefined dU rejects.
+static double accept_threshold(const Sim& s, const U4& w) {
+    if (s.P.acceptance == 1) {
+        double u = u_open(w.v[0], w.v[1]);
+        return s.P.kT * (std::log(1.0 - u) - std::log(u));
+    }
+    return -s.P.kT * std::log(1.0 - u53(w.v[0], w.v[1]));
+}
+static bool metropolis(const Sim& s, double dU, const U4& w) {
+    return dU <= accept_threshold(s, w);
 }
 
 /* ---- proposal parameters (Appendix D) ---- */
@@ -599,6 +617,23 @@ static void polarisation(const Sim& s, int layer, uint64_t sweep, uint32_t j, do
     double q = (V[0] * V[0] + V[1] * V[1]) + V[2] * V[2];
     double r = std::sqrt(q);
     p[0] = V[0] / r; p[1] = V[1] / r; p[2] = V[2] / r;
+}
+
+// Centre uniform in the box (Sec. V.D, the homogeneous alternative with P_b = 1/L^3): each
+// coordinate L times a 32-bit uniform of the slot's own draw.
+static void uniform_centre(const Sim& s, int l, uint64_t sweep, uint32_t j, double b[3]) {
+    U4 w = s.rng.draw(K_BUNI, l, sweep, j, 0);
+    for (int a = 0; a < 3; a++) b[a] = s.L * ((double)w.v[a] * (1.0 / 4294967296.0));
+}
+// Amplitude of a wavelet move: A_w = A0 lam / sqrt(n) (Eq. 29) for a bead-centred move; with a
+// uniform centre n is replaced by its mean at the global density, N (4 pi / 3) lam^3 / L^3
+// (Sec. V.D: the mean count; this reading gives P_b A_w^2 = 3 A0^2 / (4 pi N lam) as Eq. 29 does).
+static double wavelet_amplitude(const Sim& s, double lam, int n) {
+    if (s.P.centring == 1) {
+        double nbar = ((double)s.N * ((4.0 * PI / 3.0) * ((lam * lam) * lam))) / ((s.L * s.L) * s.L);
+        return (s.P.A0 * lam) / std::sqrt(nbar);
+    }
+    return (s.P.A0 * lam) / std::sqrt((double)n);
 }
 
 // Displacement of a bead at minimum-image offset d from the centre (Sec. V.A):
@@ -685,10 +720,14 @@ static bool point_inside(const Sim& s, const Region& Rg, const double* p) {
 static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, const Region* Rg, int* n_out) {
     const uint64_t sw = s.sweep;
     s.last_du = 0.0;
-    // centre: b = r_i + lam V, V uniform in the unit ball (wrapped into the box)
+    // centre: b = r_i + lam V, V uniform in the unit ball (wrapped into the box); or uniform in
+    // the box
     double V[3], b[3];
-    ball_point(s, K_VB, l, sw, j, V, false);
-    for (int a = 0; a < 3; a++) b[a] = wrap(s.pos[3 * i + a] + lam * V[a], s.L, nullptr);
+    if (s.P.centring == 1) uniform_centre(s, l, sw, j, b);
+    else {
+        ball_point(s, K_VB, l, sw, j, V, false);
+        for (int a = 0; a < 3; a++) b[a] = wrap(s.pos[3 * i + a] + lam * V[a], s.L, nullptr);
+    }
     if (Rg && !ball_inside(s, *Rg, b, lam)) return DEFER;
     // support: beads strictly inside the ball, one image each (lam <= L/2)
     std::vector<int64_t> S;
@@ -709,7 +748,7 @@ static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, con
     std::vector<double> newp(3 * (size_t)n);
     std::vector<int32_t> newimg(3 * (size_t)n);
     if (n > 0) {
-        double Aw = (s.P.A0 * lam) / std::sqrt((double)n);
+        double Aw = wavelet_amplitude(s, lam, n);
         for (int k = 0; k < n; k++) {
             double dl[3];
             wavelet_disp(s, &D[4 * k], D[4 * k + 3], lam, Aw, p, dl);
@@ -735,7 +774,7 @@ static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, con
     double dU = n > 0 ? delta_U(s, S, newp) : 0.0;
     s.last_du = dU;
     U4 w = s.rng.draw(K_ACC, l, sw, j, 0);
-    bool acc = metropolis(s, dU, u53(w.v[0], w.v[1]));
+    bool acc = metropolis(s, dU, w);
     if (acc) {
         for (int k = 0; k < n; k++)
             for (int a = 0; a < 3; a++) { s.pos[3 * S[k] + a] = newp[3 * k + a]; s.img[3 * S[k] + a] = newimg[3 * k + a]; }
@@ -796,8 +835,10 @@ static void run_layer(Sim& s, int l) {
         std::vector<std::pair<int64_t, int64_t>> keyed(M);
         for (int64_t j = 0; j < M; j++) {
             int c[3];
+            double bc[3];
+            if (s.P.centring == 1) uniform_centre(s, l, sw, (uint32_t)j, bc);     // bucket by the centre
             for (int a = 0; a < 3; a++) {
-                int64_t v = (int64_t)std::floor(s.pos[3 * bead[j] + a] * invG);
+                int64_t v = (int64_t)std::floor((s.P.centring == 1 ? bc[a] : s.pos[3 * bead[j] + a]) * invG);
                 if (v < 0) v = 0;
                 if (v >= G) v = G - 1;
                 c[a] = (int)v;
@@ -1045,7 +1086,7 @@ static int planewave_attempt(Sim& s, int kmode, int kdir, int kacc, uint64_t ctr
             dU += U_pair(s, i, j, &newp[3 * i], &newp[3 * j]) - U_pair(s, i, j, &s.pos[3 * i], &s.pos[3 * j]);
     }
     U4 w3 = s.rng.draw(kacc, 0, ctr, m, 0);
-    bool acc = metropolis(s, dU, u53(w3.v[0], w3.v[1]));
+    bool acc = metropolis(s, dU, w3);
     if (acc) {
         s.pos.swap(newp);
         s.img.swap(newimg);
@@ -1091,7 +1132,8 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     const OParams& P = s.P;
     if (P.n_beads < 1 || !(P.box_L > 0) || !(P.lambda_min > 0) || !(P.lambda_max > P.lambda_min) ||
         P.lambda_max > 0.5 * P.box_L || !(P.A0 > 0) || !(P.kT > 0) || P.colour_K < 2 || P.colour_K > 4 ||
-        P.grid_f < 1 || P.n_cap < 1 || P.bond_type < 0 || P.bond_type > 2)
+        P.grid_f < 1 || P.n_cap < 1 || P.bond_type < 0 || P.bond_type > 2 || P.acceptance < 0 || P.acceptance > 1 ||
+        P.centring < 0 || P.centring > 1)
         return -1;
     s.N = P.n_beads;
     s.L = P.box_L;
@@ -1412,8 +1454,11 @@ int oracle_propose_moments(void* h, int64_t n_props, uint64_t offset, double* ou
         int64_t i;
         slot_draw(s, l, sw, 0, &lam, &i);
         double V[3], b[3], p[3];
-        ball_point(s, K_VB, l, sw, 0, V, false);
-        for (int a = 0; a < 3; a++) b[a] = wrap(s.pos[3 * i + a] + lam * V[a], s.L, nullptr);
+        if (s.P.centring == 1) uniform_centre(s, l, sw, 0, b);
+        else {
+            ball_point(s, K_VB, l, sw, 0, V, false);
+            for (int a = 0; a < 3; a++) b[a] = wrap(s.pos[3 * i + a] + lam * V[a], s.L, nullptr);
+        }
         polarisation(s, l, sw, 0, p);
         int n = 0;
         double dd[2][4];
@@ -1428,7 +1473,7 @@ int oracle_propose_moments(void* h, int64_t n_props, uint64_t offset, double* ou
             }
         }
         if (n == 0) continue;
-        double Aw = (s.P.A0 * lam) / std::sqrt((double)n), dl[2][3] = {{0, 0, 0}, {0, 0, 0}};
+        double Aw = wavelet_amplitude(s, lam, n), dl[2][3] = {{0, 0, 0}, {0, 0, 0}};
         for (int m = 0; m < 2; m++) if (in01[m]) wavelet_disp(s, dd[m], dd[m][3], lam, Aw, p, dl[m]);
         for (int a = 0; a < 3; a++)
             for (int bb = 0; bb < 3; bb++) {
@@ -1490,6 +1535,13 @@ int64_t oracle_trace_pw_k(void* h, double* out, int64_t cap) {
     for (int64_t j = 0; j < M && j < cap; j++)
         for (int a = 0; a < 3; a++) out[3 * j + a] = s.tr_pw_k[3 * j + a];
     return M;
+}
+
+// acceptance thresholds of n wavelet slots of layer 0 in sweep `sw` (accept iff dU <= threshold)
+int64_t oracle_sample_threshold(void* h, uint64_t sw, int64_t n, double* out) {
+    Sim& s = *(Sim*)h;
+    for (int64_t j = 0; j < n; j++) out[j] = accept_threshold(s, s.rng.draw(K_ACC, 0, sw, (uint32_t)j, 0));
+    return n;
 }
 
 // run n sweeps, recording the unwrapped position of bead 0 after each

@@ -107,10 +107,13 @@ static const std::vector<double>& k_cdf_table() {
         for (int i = 0; i <= kKtN; i++) Q[i] = i * kKtH;
         G_table(Q, g);
         std::vector<double> t(kKtN + 1, 0.0);
-        double cum = 0.0;
+        double cum = 0.0, comp = 0.0;         // compensated running sum
         for (int i = 1; i <= kKtN; i++) {
             // two 10-point panels per grid step
-            cum += gl10_q6(Q[i - 1], Q[i - 1] + 0.5 * kKtH) + gl10_q6(Q[i - 1] + 0.5 * kKtH, Q[i]);
+            const double y = (gl10_q6(Q[i - 1], Q[i - 1] + 0.5 * kKtH) + gl10_q6(Q[i - 1] + 0.5 * kKtH, Q[i])) - comp;
+            const double tt = cum + y;
+            comp = (tt - cum) - y;
+            cum = tt;
             t[i] = (Q[i] * Q[i] * Q[i] * g[i] + cum) / kM6;
         }
         return t;
@@ -120,8 +123,13 @@ static const std::vector<double>& k_cdf_table() {
 // F(Q) directly (the shell's normalisation) and through the table (where the shell starts)
 static double k_cdf_direct(double Q) {
     const double step = 0.5 * kKtH;
-    double cum = 0.0, a = 0.0;
-    while (a < Q) { const double b = std::min(Q, a + step); cum += gl10_q6(a, b); a = b; }
+    double cum = 0.0, comp = 0.0, a = 0.0;
+    while (a < Q) {
+        const double b = std::min(Q, a + step), y = gl10_q6(a, b) - comp, t = cum + y;
+        comp = (t - cum) - y;
+        cum = t;
+        a = b;
+    }
     std::vector<double> g;
     G_table(std::vector<double>{Q}, g);
     return (Q * Q * Q * g[0] + cum) / kM6;
@@ -279,6 +287,7 @@ int wmcd::validate_params(const wmcd_params* p) {
         p->n_cap < 1 || p->n_cap > kNCapMax || p->precision < 0 || p->precision > 1)
         return WMCD_EINVAL;
     if (p->planewave_mode < 0 || p->planewave_mode > 3) return WMCD_EINVAL;
+    if (p->acceptance < 0 || p->acceptance > 1 || p->centring < 0 || p->centring > 1) return WMCD_EINVAL;
     if (p->planewave_mode == 1 && (p->lcut < 0 || p->lcut > 120)) return WMCD_EINVAL;
     if (p->planewave_mode == 2 && (p->lcut < 0 || p->lcut > 40)) return WMCD_EINVAL;
     if ((int64_t)p->grid_f * p->grid_f * p->grid_f > ((int64_t)1 << 31) - 1) return WMCD_EINVAL;
@@ -330,6 +339,8 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     v.pot.L = v.L;
     v.k0 = (uint32_t)P.seed;
     v.k1 = (uint32_t)(P.seed >> 32) ^ (uint32_t)P.sim_id;
+    v.acceptance = P.acceptance;
+    v.centring = P.centring;
 
     // plane-wave tables and P_F (Eqs. 51, 55, 56): mode 1 the sphere |l| <= lcut normalised over
     // itself; mode 2 the cube |l_i| <= lcut (N_layers) plus the quasi-continuous shell, normalised

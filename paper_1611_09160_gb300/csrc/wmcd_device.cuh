@@ -75,7 +75,7 @@ WMCD_HD u4 philox4x32_10(u4 c, uint32_t k0, uint32_t k1) {
 enum Kind : uint32_t {
     K_COUNT = 1, K_SLOT = 2, K_VB = 3, K_VP = 4, K_ACC = 5, K_PWCOUNT = 6, K_PWMODE = 7, K_PWDIR = 8,
     K_PWACC = 9, K_DPWMODE = 10, K_DPWDIR = 11, K_DPWACC = 12, K_PWSHELL = 14, K_PWKDIR = 15, K_DPWSHELL = 16,
-    K_DPWKDIR = 17
+    K_DPWKDIR = 17, K_BUNI = 18
 };
 
 // counter = (index, sweep lo, kind << 24 | layer << 16 | attempt, sweep hi); key = (k0, k1)

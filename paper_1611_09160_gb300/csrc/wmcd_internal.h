@@ -199,6 +199,8 @@ struct SimView {
     const double* mode_cdf;
     int n_modes;
     AuditDev* audit;             // null: no audit of mixed-precision decisions
+    int acceptance;              // 0 Metropolis, 1 Glauber
+    int centring;                // 0 centre near a picked bead, 1 uniform in the box
 };
 
 // packed image change: three 2-bit fields holding -1, 0, +1 (as 0, 1, 2)

@@ -12,6 +12,31 @@ namespace wmcd {
 
 __device__ __forceinline__ void set_err(const SimView& v, int bit) { atomicOr(v.err, bit); }
 
+// Acceptance threshold of a move on its draw w (accept iff dU <= threshold): Metropolis
+// (Eq. 20), -kT ln(1 - u) with u in [0, 1); Glauber (Secs. V.C, VIII), accept with probability
+// 1 / (1 + exp(dU / kT)), i.e. kT (ln(1 - u) - ln u) with u in (0, 1).
+// Centre uniform in the box (Sec. V.D, the homogeneous scheme, P_b = 1/L^3): each coordinate L
+// times a 32-bit uniform of the slot's own draw.
+__device__ __forceinline__ void uniform_centre(const SimView& v, int l, uint64_t sweep, uint32_t j, double b[3]) {
+    const u4 w = draw(v.k0, v.k1, K_BUNI, l, sweep, j, 0);
+    b[0] = mul(v.L, (double)w.x * (1.0 / 4294967296.0));
+    b[1] = mul(v.L, (double)w.y * (1.0 / 4294967296.0));
+    b[2] = mul(v.L, (double)w.z * (1.0 / 4294967296.0));
+}
+// Amplitude with a uniform centre: A0 lam / sqrt(nbar), nbar = N (4 pi / 3) lam^3 / L^3 the mean
+// support at the global density (Eq. 29 with the mean count)
+__device__ __forceinline__ double uniform_aw(const SimView& v, double lam) {
+    const double nbar = dvd(mul((double)v.N, mul(4.0 * kPi / 3.0, mul(mul(lam, lam), lam))), mul(mul(v.L, v.L), v.L));
+    return dvd(mul(v.A0, lam), sqr_t(nbar));
+}
+__device__ __forceinline__ double accept_threshold(const SimView& v, const u4& w) {
+    if (v.acceptance == 1) {
+        const double u = u_open(w.x, w.y);
+        return v.kT * (log(1.0 - u) - log(u));
+    }
+    return -v.kT * log(1.0 - u53(w.x, w.y));
+}
+
 // One audited mixed-precision decision: d32 and band as the decision used them, thr_cmp the
 // threshold d32 was compared with, d64 the binary64 energy change and thr64 its threshold.
 __device__ void audit_record(const SimView& v, double d32, double band, double thr_cmp, double d64, double thr64) {
@@ -221,9 +246,13 @@ __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
     if (j >= M) return;
     const LayerDev& Ly = v.layer[l];
     const int G = Ly.G, K = v.K, Q = G / K;
-    Bead b = v.bead[v.slot_bead[j]];
+    double xs[3];
+    if (v.centring == 1) uniform_centre(v, l, v.step[0], (uint32_t)j, xs);      // bucket by the centre
+    else {
+        const Bead b = v.bead[v.slot_bead[j]];
+        xs[0] = b.x; xs[1] = b.y; xs[2] = b.z;
+    }
     int c[3];
-    double xs[3] = {b.x, b.y, b.z};
     for (int a = 0; a < 3; a++) {
         double f = floor(mul(xs[a], Ly.invG));
         int ci = (int)f;
@@ -653,11 +682,14 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     const float hLf = (float)hL;
     *du_out = 0.0;
     const int Gf = v.Gf;
-    // centre b = r_i + lam V (Appendix D), wrapped into the box
-    const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
+    // centre b = r_i + lam V (Appendix D), wrapped into the box; or uniform in the box
     double V[3], b[3];
-    warp_ball_point(v, K_VB, l, sweep, (uint32_t)j, false, lane, V);
-    for (int a = 0; a < 3; a++) b[a] = wrap(add(ri[a], mul(lam, V[a])), L, nullptr);
+    if (v.centring == 1) uniform_centre(v, l, sweep, (uint32_t)j, b);
+    else {
+        const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
+        warp_ball_point(v, K_VB, l, sweep, (uint32_t)j, false, lane, V);
+        for (int a = 0; a < 3; a++) b[a] = wrap(add(ri[a], mul(lam, V[a])), L, nullptr);
+    }
     // the influence ball must lie in fine cells wholly inside the queue's region
     const double R = add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
     for (int a = 0; a < 3; a++) {
@@ -715,7 +747,10 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     *n_out = n;
     if (n > v.n_cap) return DEFER;
     __syncwarp();
-    if (n == 0) return ACCEPT;           // no bead moves; dU = 0 passes the Metropolis test
+    if (n == 0) {                        // no bead moves: dU = 0 against the threshold
+        const u4 w0 = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+        return 0.0 <= accept_threshold(v, w0) ? ACCEPT : REJECT;
+    }
     // polarisation and amplitude A_w = A0 lam / sqrt(n) (Eq. 29)
     double p[3];
     warp_ball_point(v, K_VP, l, sweep, (uint32_t)j, true, lane, p);
@@ -723,7 +758,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
         const double r = sqr_t(norm2(p[0], p[1], p[2]));
         p[0] = dvd(p[0], r); p[1] = dvd(p[1], r); p[2] = dvd(p[2], r);
     }
-    const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+    const double Aw = v.centring == 1 ? uniform_aw(v, lam) : dvd(mul(v.A0, lam), sqr_t((double)n));
     for (int k = lane; k < n; k += 32) {
         double d[3];
         for (int a = 0; a < 3; a++) d[a] = mi(sub(sm.op[k][a], b[a]), L, hL);
@@ -761,7 +796,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
     partner_boxes(v, sm, n, lane, &ncols, &nzmax);
     // Metropolis threshold (Eq. 20): accept iff dU <= -kT ln(1 - u)
     const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
-    const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
+    const double thr = accept_threshold(v, w);
     bool acc;
     int pe = 0;
     if (PREC == 1) {
@@ -861,12 +896,13 @@ __global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
         if (q <= 1.0 && q > 0.0) { p[0] = x; p[1] = y; p[2] = z; break; }
     }
     const double r = sqr_t(norm2(p[0], p[1], p[2]));
+    if (v.centring == 1) uniform_centre(v, l, sweep, (uint32_t)j, V);   // slot_V holds the centre itself
     for (int a = 0; a < 3; a++) {
         v.slot_V[3 * j + a] = V[a];
         v.slot_p[3 * j + a] = dvd(p[a], r);
     }
     const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
-    v.slot_thr[j] = -v.kT * log(1.0 - u53(w.x, w.y));
+    v.slot_thr[j] = accept_threshold(v, w);
 }
 
 template <int PREC, int NT>
@@ -910,7 +946,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             sh_rl2f = rlf * rlf * (1.0f + 9.5367431640625e-7f);
             const double ri[3] = {v.bead[i].x, v.bead[i].y, v.bead[i].z};
             for (int a = 0; a < 3; a++) {
-                sh_b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), L, nullptr);
+                sh_b[a] = v.centring == 1 ? v.slot_V[3 * j + a] : wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), L, nullptr);
                 sh_p[a] = v.slot_p[3 * j + a];
                 sh_bf[a] = (float)sh_b[a];
             }
@@ -997,13 +1033,15 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         }
         __syncthreads();
         const int n = sh_n;
-        if (n == 0) {      // nothing inside: dU = 0, accepted with no motion
+        if (n == 0) {      // nothing inside: no motion, dU = 0 against the threshold
             if (tid == 0) {
-                att++; acc_n++;
-                v.tr_out[Ly.tr_off + j] = (uint8_t)(1 | (use_list ? 4 : 0));
+                const bool acc0 = 0.0 <= v.slot_thr[j];
+                att++;
+                if (acc0) acc_n++;
+                v.tr_out[Ly.tr_off + j] = (uint8_t)((acc0 ? 1 : 2) | (use_list ? 4 : 0));
                 v.tr_n[Ly.tr_off + j] = 0;
                 v.tr_du[Ly.tr_off + j] = 0.0;
-                sh_carry = 0.0;
+                sh_carry = acc0 ? 0.0 : lam;
             }
             __syncthreads();
             continue;
@@ -1011,7 +1049,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         const uint32_t tag = sh_tag;
         // A_w and the partner-box reach only in warps that hold a member
         const bool member_warp = (tid & ~31) < n;
-        const double Aw = member_warp ? dvd(mul(v.A0, lam), sqr_t((double)n)) : 0.0;
+        const double Aw = !member_warp ? 0.0 : (v.centring == 1 ? uniform_aw(v, lam) : dvd(mul(v.A0, lam), sqr_t((double)n)));
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
         for (int k = tid; k < n; k += NT) {
             int m = v.s_ids[k];
@@ -1460,7 +1498,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
             const int a = tid;
             const double lam0 = __double_as_longlong(sh_carry) > 0 ? sh_carry : v.slot_lam[j];
             const double ri = a == 0 ? px[i] : (a == 1 ? py[i] : pz[i]);
-            const double ba = wrap_u(add(ri, mul(lam0, v.slot_V[3 * j + a])), L, 7u, nullptr);
+            const double ba = v.centring == 1 ? v.slot_V[3 * j + a] : wrap_u(add(ri, mul(lam0, v.slot_V[3 * j + a])), L, 7u, nullptr);
             sh_b[a] = ba;
             sh_p[a] = v.slot_p[3 * j + a];
             sh_bf[a] = (float)ba;
@@ -1483,7 +1521,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
             // and the move's binary32 constants
             const double lam0 = __double_as_longlong(sh_carry) > 0 ? sh_carry : v.slot_lam[j];
             const int nn = tid - 31;
-            const double aw = dvd(mul(v.A0, lam0), s_sqrt[nn]);
+            const double aw = v.centring == 1 ? uniform_aw(v, lam0) : dvd(mul(v.A0, lam0), s_sqrt[nn]);
             sh_aw[nn] = aw;
             sh_awf[nn] = (float)aw;
             if (tid == 32) {
@@ -1520,13 +1558,15 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
         }
         __syncthreads();
         const int n = sh_n;
-        if (n == 0) {      // nothing inside: dU = 0, accepted with no motion
+        if (n == 0) {      // nothing inside: no motion, dU = 0 against the threshold
             if (tid == 0) {
-                att++; acc_n++;
-                v.tr_out[Ly.tr_off + j] = 1;
+                const bool acc0 = 0.0 <= v.slot_thr[j];
+                att++;
+                if (acc0) acc_n++;
+                v.tr_out[Ly.tr_off + j] = (uint8_t)(acc0 ? 1 : 2);
                 v.tr_n[Ly.tr_off + j] = 0;
                 v.tr_du[Ly.tr_off + j] = 0.0;
-                sh_carry = 0.0;
+                sh_carry = acc0 ? 0.0 : lam;
             }
             __syncthreads();
             continue;
@@ -1540,7 +1580,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) k_serial_smem(const Si
                 Aw = sh_aw[n];
                 af = sh_awf[n];
             } else {
-                Aw = dvd(mul(v.A0, lam), n <= kNCap ? s_sqrt[n] : sqr_t((double)n));
+                Aw = v.centring == 1 ? uniform_aw(v, lam) : dvd(mul(v.A0, lam), n <= kNCap ? s_sqrt[n] : sqr_t((double)n));
                 af = (float)Aw;
             }
             lamf = sh_lamf; pf[0] = sh_pf[0]; pf[1] = sh_pf[1]; pf[2] = sh_pf[2];
@@ -2170,7 +2210,7 @@ __global__ void __launch_bounds__(256) k_pw_decide(const SimView* __restrict__ v
     double dU = 0.0;
     for (int w = 0; w < 8; w++) dU += red[w];
     u4 w = draw(v.k0, v.k1, (uint32_t)kacc, 0, ctr, (uint32_t)m, 0);
-    const double thr = -v.kT * log(1.0 - u53(w.x, w.y));
+    const double thr = accept_threshold(v, w);
     const bool acc = dU <= thr;
     P.accept = acc;
     atomicAdd(&v.ctr[C_BU], (unsigned long long)v.N);
@@ -2244,7 +2284,7 @@ __global__ void k_big_setup(const SimView* __restrict__ vs, int l, int t) {
     const Bead bi = v.bead[v.slot_bead[j]];
     const double ri[3] = {bi.x, bi.y, bi.z};
     for (int a = 0; a < 3; a++) {
-        B.b[a] = wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), v.L, nullptr);
+        B.b[a] = v.centring == 1 ? v.slot_V[3 * j + a] : wrap(add(ri[a], mul(lam, v.slot_V[3 * j + a])), v.L, nullptr);
         B.p[a] = v.slot_p[3 * j + a];
     }
     B.lam = lam;
@@ -2284,7 +2324,7 @@ __global__ void k_big_disp(const SimView* __restrict__ vs, int l) {
     const BigMove& B = *v.big;
     const int n = B.n;
     const double lam = B.lam;
-    const double Aw = dvd(mul(v.A0, lam), sqr_t((double)n));
+    const double Aw = v.centring == 1 ? uniform_aw(v, lam) : dvd(mul(v.A0, lam), sqr_t((double)n));
     const double p[3] = {B.p[0], B.p[1], B.p[2]};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int m = v.s_ids[k];
@@ -2316,7 +2356,7 @@ __global__ void __launch_bounds__(256) k_big_energy(const SimView* __restrict__ 
     const uint32_t tag = B.tag;
     const double L = v.L, hL = v.halfL;
     const Pot& P = v.pot;
-    const double Aw = dvd(mul(v.A0, B.lam), sqr_t((double)n));
+    const double Aw = v.centring == 1 ? uniform_aw(v, B.lam) : dvd(mul(v.A0, B.lam), sqr_t((double)n));
     const double ext = add(v.rc, mul(0.25, Aw)) + 1e-9;
     double dU = 0.0;
     long long pe = 0;
@@ -2403,7 +2443,7 @@ __global__ void __launch_bounds__(256) k_big_decide(const SimView* __restrict__ 
     double dU = 0.0;
     for (int w = 0; w < 8; w++) dU += red[w];
     const LayerDev& Ly = v.layer[l];
-    const bool acc = n == 0 || dU <= B.thr;     // an empty support moves nothing and is accepted
+    const bool acc = (n == 0 ? 0.0 : dU) <= B.thr;   // an empty support moves nothing: dU = 0
     B.acc = acc;
     v.tr_out[Ly.tr_off + B.j] = (uint8_t)(acc ? 1 : 2);
     v.tr_n[Ly.tr_off + B.j] = n;
@@ -2804,32 +2844,45 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     const double L = v.L, hL = v.halfL;
     const int Gf = v.Gf;
     *du_out = 0.0;
+    const bool uni = v.centring == 1;             // centre uniform in the box: the chunk holds it in cV
     const int ti = S.cti[c];
-    if (ti < 0) return DEFER;                     // the picked bead lies outside the region interior
+    if (ti < 0 && !uni) return DEFER;             // the picked bead lies outside the region interior
     // centre b = r_i + lam V (Appendix D), wrapped; binary64 because the region rule and the
     // support must match the sequential definition exactly. For the slot's own scale lam V and
     // the influence radius R were formed ahead (same operations, same values); a carried scale
     // forms them here.
     const bool own = __double_as_longlong(lam) == __double_as_longlong(S.clam[c]);
     double b[3], lv[3];
-    for (int a = 0; a < 3; a++) lv[a] = own ? S.clamV[3 * c + a] : mul(lam, S.cV[3 * c + a]);
-    b[0] = add(S.sx[ti], lv[0]);
-    b[1] = add(S.sy[ti], lv[1]);
-    b[2] = add(S.sz[ti], lv[2]);
-    wrap3_u(b, L, FULL, nullptr);
+    if (uni) {
+        for (int a = 0; a < 3; a++) b[a] = S.cV[3 * c + a];
+    } else {
+        for (int a = 0; a < 3; a++) lv[a] = own ? S.clamV[3 * c + a] : mul(lam, S.cV[3 * c + a]);
+        b[0] = add(S.sx[ti], lv[0]);
+        b[1] = add(S.sy[ti], lv[1]);
+        b[2] = add(S.sz[ti], lv[2]);
+        wrap3_u(b, L, FULL, nullptr);
+    }
     const double R = own ? S.cR[c] : add(add(lam, mul(mul(0.25, v.A0), lam)), v.r_reach);
     const float lamf = own ? S.clamf[c] : (float)lam;
     // A_w = A0 lam / sqrt(n) (Eq. 29) for every support size up to 32, one per lane, formed
     // while the scan below runs; the scan's n picks one
     const double a0l = own ? S.cA0l[c] : mul(v.A0, lam);
-    const double aw_lane = dvd(a0l, C.sqrt_n[lane + 1]);
+    const double aw_lane = uni ? uniform_aw(v, lam) : dvd(a0l, C.sqrt_n[lane + 1]);
     // the centre relative to the region origin in binary32 (from the picked bead's staged local
     // coordinates): its error, a few 1e-7 of the region side plus lam, is far inside the margins
     // of the screens below
     float bh[3];
-    bh[0] = (S.hx[ti] + S.lx[ti]) + lamf * S.cVf[3 * c];
-    bh[1] = (S.hy[ti] + S.ly[ti]) + lamf * S.cVf[3 * c + 1];
-    bh[2] = (S.hz[ti] + S.lz[ti]) + lamf * S.cVf[3 * c + 2];
+    if (uni) {
+        for (int a = 0; a < 3; a++) {
+            float hi_, lo_;
+            local_split(b[a], org[a], L, hi_, lo_);
+            bh[a] = hi_ + lo_;
+        }
+    } else {
+        bh[0] = (S.hx[ti] + S.lx[ti]) + lamf * S.cVf[3 * c];
+        bh[1] = (S.hy[ti] + S.ly[ti]) + lamf * S.cVf[3 * c + 1];
+        bh[2] = (S.hz[ti] + S.lz[ti]) + lamf * S.cVf[3 * c + 2];
+    }
     // region rule: a binary32 screen proves most balls well inside the region's interior; the
     // others take the binary64 cell indices of the definition
     const float Rf = own ? S.cRf[c] : (float)R;
@@ -2907,10 +2960,11 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     __syncwarp();                                 // support and candidate lists are read by every lane
     *n_out = n;
     if (n > v.n_cap) return DEFER;
-    if (n == 0) return ACCEPT;                    // no bead moves; dU = 0 passes
+    if (n == 0) return 0.0 <= S.cthr[c] ? ACCEPT : REJECT;   // no bead moves: dU = 0 against the threshold
     const bool all_cand = nc > kCandCap;
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
-    const double Aw = n <= 32 ? __shfl_sync(FULL, aw_lane, n - 1) : dvd(a0l, n <= kNCap ? C.sqrt_n[n] : sqr_t((double)n));
+    const double Aw = uni ? aw_lane
+                          : (n <= 32 ? __shfl_sync(FULL, aw_lane, n - 1) : dvd(a0l, n <= kNCap ? C.sqrt_n[n] : sqr_t((double)n)));
     const double p[3] = {S.cp[3 * c], S.cp[3 * c + 1], S.cp[3 * c + 2]};
     const float af = (float)Aw, pf[3] = {S.cpf[3 * c], S.cpf[3 * c + 1], S.cpf[3 * c + 2]};
     bool bad = false;
@@ -3165,9 +3219,10 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                     if (qq <= 1.0 && qq > 0.0) { pp[0] = x; pp[1] = y; pp[2] = z; break; }
                 }
                 const double r = sqr_t(norm2(pp[0], pp[1], pp[2]));
+                if (v.centring == 1) uniform_centre(v, l, sweep, (uint32_t)j, V);   // cV holds the centre itself
                 for (int a = 0; a < 3; a++) { S.cV[3 * lane + a] = V[a]; S.cp[3 * lane + a] = dvd(pp[a], r); }
                 const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
-                S.cthr[lane] = -v.kT * log(1.0 - u53(w.x, w.y));
+                S.cthr[lane] = accept_threshold(v, w);
                 S.cthrf[lane] = (float)S.cthr[lane];
                 // what the move needs from its own scale, ahead of the sequential loop
                 const double lam_s = S.clam[lane];

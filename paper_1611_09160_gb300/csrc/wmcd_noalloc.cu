@@ -212,6 +212,8 @@ extern "C" int wmcd_planewave_noalloc(const wmcd_params* params, double* pos, co
     v.pot.L = v.L;
     v.k0 = (uint32_t)P.seed;
     v.k1 = (uint32_t)(P.seed >> 32) ^ (uint32_t)P.sim_id;
+    v.acceptance = P.acceptance;
+    v.centring = P.centring;
     v.pw_blocks = (int)((N + 255) / 256);
     v.step = (uint64_t*)(base + oStep);
     v.counts = (int*)(base + oCounts);

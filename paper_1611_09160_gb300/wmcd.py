@@ -28,6 +28,8 @@ MAX_LAYERS = 16
 BOND_NONE, BOND_HARMONIC, BOND_FENE = 0, 1, 2
 PLANEWAVE_OFF, PLANEWAVE_PERIODIC, PLANEWAVE_PERIODIC_FULL, PLANEWAVE_INFINITE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
+ACCEPT_METROPOLIS, ACCEPT_GLAUBER = 0, 1
+CENTRE_BEAD, CENTRE_UNIFORM = 0, 1
 STATUS = {0: "WMCD_OK", -1: "WMCD_EINVAL", -2: "WMCD_ENOMEM", -3: "WMCD_ECUDA", -4: "WMCD_ETIMEOUT", -5: "WMCD_ESTATE",
           -6: "WMCD_EFULL"}
 KERNEL_CLASSES = ["concurrent_wavelet", "serial_wavelet", "plane_wave", "cell_list", "schedule", "whole_gpu_serial"]
@@ -80,6 +82,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("sim_id", ctypes.c_uint64),
         ("colour_K", ctypes.c_int32), ("grid_f", ctypes.c_int32), ("n_cap", ctypes.c_int32),
         ("grid_layer", ctypes.c_int32 * MAX_LAYERS), ("big_support", ctypes.c_int32),
+        ("acceptance", ctypes.c_int32), ("centring", ctypes.c_int32),
     ]
 
 
@@ -199,7 +202,8 @@ def default_params(n_beads: int, box_L: float, *, lambda_min: float = 2.0, lambd
                    A0: float = 0.5, kT: float = 1.0, bond_type: int = BOND_HARMONIC, bond_k: float = 100.0,
                    bond_r0: float = 2.0, fene_R0: float = 3.0, wca_sigma: float = 2.0, wca_eps: float = 1.0,
                    ext_kappa: float = 0.0, planewave_mode: int = PLANEWAVE_OFF, lcut: int = 8,
-                   precision: int = FP64, seed: int = 1, sim_id: int = 0, colour_K: int = 2, **sched) -> dict:
+                   precision: int = FP64, seed: int = 1, sim_id: int = 0, colour_K: int = 2,
+                   acceptance: int = ACCEPT_METROPOLIS, centring: int = CENTRE_BEAD, **sched) -> dict:
     """Parameter fields of the benchmark systems: beads of radius a = 1, harmonic bonds
     k = 100 kT/a^2 with rest length 2a, WCA sigma = 2a, eps = 1 kT, lambda_min = 2a,
     lambda_max = L/2, A0 = 0.5, plus the default concurrent schedule for the box."""
@@ -207,7 +211,7 @@ def default_params(n_beads: int, box_L: float, *, lambda_min: float = 2.0, lambd
     d = dict(n_beads=int(n_beads), box_L=float(box_L), lambda_min=lambda_min, lambda_max=lmax, A0=A0, kT=kT,
              bond_type=bond_type, bond_k=bond_k, bond_r0=bond_r0, fene_R0=fene_R0, wca_sigma=wca_sigma,
              wca_eps=wca_eps, ext_kappa=ext_kappa, planewave_mode=planewave_mode, lcut=lcut, precision=precision,
-             seed=seed, sim_id=sim_id)
+             seed=seed, sim_id=sim_id, acceptance=acceptance, centring=centring)
     sched.setdefault("n_beads", int(n_beads))
     d.update(_schedule.choose(box_L, lambda_min, lmax, A0, wca_sigma, wca_eps, colour_K=colour_K, **sched))
     return d

@@ -27,7 +27,8 @@ def compare_pw(gpu, ref, label):
     assert np.array_equal(ma, mb), f"{label}: packed modes differ"
     ka, kb = gpu.trace_pw_k(), ref.trace_pw_k()
     assert ka.shape == kb.shape
-    assert np.allclose(ka, kb, rtol=1e-12, atol=0.0), f"{label}: wave vectors differ"
+    rel = np.max(np.abs(ka - kb) / np.maximum(np.abs(kb), 1e-300)) if len(ka) else 0.0
+    assert np.allclose(ka, kb, rtol=1e-12, atol=0.0), f"{label}: wave vectors differ (largest relative {rel:.3g})"
     return a, ka
 
 
