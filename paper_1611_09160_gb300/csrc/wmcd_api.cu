@@ -627,9 +627,9 @@ int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t*
         launches += 1;
         if (g.coloured[l]) {
             { ProfScope ps(prof, 4, s); launch_bucket(d, g, l, s); }
-            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launch_colour_staged(d, g, l, c, s); }
+            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launches += launch_colour_staged(d, g, l, c, s); }
             { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, l, s); }
-            launches += 5 + (int64_t)g.maxK3 * (4 + np) + 1;
+            launches += 5 + 1;
         }
         { ProfScope ps(prof, 1, s); launches += launch_serial(d, g, l, s, fj); }
         if (g.bigM[l] > 0) {

@@ -234,7 +234,7 @@ void launch_counts(const SimView* d, const GroupDims& g, cudaStream_t s);
 void launch_advance(const SimView* d, const GroupDims& g, int which, cudaStream_t s);
 void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
-void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s);
+int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s);  // kernels launched
 void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 // Side streams and events to run independent launches of a phase side by side (recorded as
 // parallel branches of a graph); null members mean one stream.

@@ -2550,6 +2550,11 @@ __host__ __device__ inline size_t warp_stride(int cap, int ncap) {
     size_t per = stage_bytes(cap, ncap) > sizeof(WarpSmem) ? stage_bytes(cap, ncap) : sizeof(WarpSmem);
     return (per + 15) & ~(size_t)15;
 }
+// per-warp bytes of a launch whose regions all fit `cap` (no global-memory path, so no room for
+// its scratch)
+__host__ __device__ inline size_t warp_stride_staged(int cap, int ncap) {
+    return (stage_bytes(cap, ncap) + 15) & ~(size_t)15;
+}
 __device__ inline Stage stage_carve(char* base, int cap, int ncap) {
     Stage S;
     S.cap = cap;
@@ -3105,14 +3110,34 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     return ACCEPT;
 }
 
+// Whether a block of the staged kernel has a queue to run: a slot in it and a region whose bead
+// count lies in [ns_lo, ns_hi] (read from global memory before the block copies anything).
+__device__ __forceinline__ bool staged_block_has_work(const SimView& g, int l, int colour, int qpb, int ns_lo,
+                                                      int ns_hi) {
+    const int Q = g.layer[l].G / g.K, nq = Q * Q * Q;
+    for (int w = 0; w < qpb; w++) {
+        const int q = (int)blockIdx.x * qpb + w;
+        if (q >= nq) break;
+        if (g.q_count[colour * nq + q] == 0) continue;
+        const int ns = g.rcount[q];
+        if (ns >= ns_lo && ns <= ns_hi) return true;
+    }
+    return false;
+}
+
 // A block serves qpb queues with one warp each, or (qpb = 1) one queue with all its warps: then
 // every warp stages a share of the region (the binary64 work of staging spreads over the SM's
-// four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue.
+// four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue; stride =
+// shared bytes per queue. Only queues whose region holds ns_lo..ns_hi beads run: a colour phase
+// is split between a launch for ordinary regions (small staging, more warps per SM) and one for
+// the dense ones, which take disjoint queues, so the split changes nothing in the results.
 template <int PREC>
 __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
-                                                                        int cap, int qpb, int ncap) {
+                                                                        int cap, int qpb, int ncap, int stride,
+                                                                        int ns_lo, int ns_hi) {
     SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
-                (int)(blockIdx.x * qpb) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K))
+                (int)(blockIdx.x * qpb) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) ||
+                !staged_block_has_work(gv, l, colour, qpb, ns_lo, ns_hi))
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
@@ -3132,7 +3157,11 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     const int key = colour * nq + q;
     const int start = v.q_start[key], cnt = v.q_count[key];
     if (cnt == 0) return;
-    char* base = dsm + (size_t)wib * warp_stride(cap, ncap);
+    {
+        const int ns0 = v.rcount[q];
+        if (ns0 < ns_lo || ns0 > ns_hi) return;   // another launch of this phase runs the queue
+    }
+    char* base = dsm + (size_t)wib * (size_t)stride;
     const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
     int64_t rlo[3], rhi[3];
     for (int a = 0; a < 3; a++) {
@@ -3329,6 +3358,13 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
 }
 
 size_t staged_smem_bytes(int cap, int warps, int ncap) { return (size_t)warps * warp_stride(cap, ncap); }
+// the launch of ordinary regions: regions of at most kLightCap beads, kMaxStageWarps queues per block
+constexpr int kLightCap = 80;
+static size_t light_smem_bytes(int ncap) { return (size_t)kMaxStageWarps * warp_stride_staged(kLightCap, ncap); }
+static bool split_layer(const GroupDims& g, int l, int cap) {
+    return g.cap_l[l] == 0 && cap > kLightCap &&
+           light_smem_bytes(g.ncap) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
+}
 static bool staged_fits(int cap, int queues, int ncap) {
     // dynamic shared memory + the static view copy, sqrt table and cooperative scratch within the
     // 227 KB of a block
@@ -3384,6 +3420,7 @@ void prepare_staged(const GroupDims& g) {
         int qpb = 1, warps = 1;
         staged_shape(g, cap, &qpb, &warps);
         smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, g.ncap));
+        if (split_layer(g, l, cap)) smem = std::max(smem, (int)light_smem_bytes(g.ncap));
     }
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
         cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -3395,7 +3432,7 @@ void prepare_staged(const GroupDims& g) {
     }
 }
 
-void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s) {
+int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s) {
     const int nq = g.nq[l];
     const int gb = (int)gx((g.maxN + 255) / 256, g.S);
     k_zero<<<dim3(gx((nq + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 1, l);
@@ -3408,9 +3445,23 @@ void launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colou
     const size_t smem = staged_smem_bytes(cap, qpb, g.ncap);
     const dim3 grid((nq + qpb - 1) / qpb, g.S);
     prepare_staged(g);
+    const int stride = (int)warp_stride(cap, g.ncap);
+    int lo = 0;
+    if (split_layer(g, l, cap)) {
+        // ordinary regions first (at most kLightCap beads): small staging, more warps on each SM
+        const int qL = kMaxStageWarps;
+        const dim3 gridL((nq + qL - 1) / qL, g.S);
+        const size_t smemL = light_smem_bytes(g.ncap);
+        const int strideL = (int)warp_stride_staged(kLightCap, g.ncap);
+        if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, g.ncap, strideL, 0, kLightCap);
+        if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, g.ncap, strideL, 0, kLightCap);
+        lo = kLightCap + 1;
+    }
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap);
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, lo, 1 << 30);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, lo, 1 << 30);
+    const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
+    return 4 + np * (lo > 0 ? 2 : 1);
 }
 
 }  // namespace wmcd
