@@ -591,6 +591,16 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     cudaMemcpyAsync(&err, v.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
     if (err) return WMCD_EINVAL;   // a coordinate outside [0, L) or not finite
+    if (!arena) {
+        // a lone simulation's side stream: the dense regions of a colour phase run on it beside
+        // the ordinary ones (a batch brings its own)
+        if (cudaStreamCreateWithFlags(&h->fj.side[0], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fj.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fj.join[0], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return WMCD_ECUDA;
+        }
+    }
     h->arena = nullptr;            // later allocations (trace growth) are the handle's own
     return WMCD_OK;
 }
@@ -627,7 +637,7 @@ int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t*
         launches += 1;
         if (g.coloured[l]) {
             { ProfScope ps(prof, 4, s); launch_bucket(d, g, l, s); }
-            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launches += launch_colour_staged(d, g, l, c, s); }
+            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launches += launch_colour_staged(d, g, l, c, s, fj); }
             { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, l, s); }
             launches += 5 + 1;
         }
@@ -653,7 +663,7 @@ static void run_sweep(Handle* h, cudaStream_t s) {
     int64_t hc[kMaxLayers + 1] = {0};
     for (int l = 0; l < h->nL; l++) hc[l] = slot_count(h, K_COUNT, l, h->sweep, h->expect[l]);
     hc[kMaxLayers] = h->g.pw ? slot_count(h, K_PWCOUNT, 0, h->sweep, h->v.expect_F) : 0;
-    h->launches += enqueue_sweep(h->dview, h->g, hc, h, s);
+    h->launches += enqueue_sweep(h->dview, h->g, hc, h, s, &h->fj);
     h->tr_pw_count = hc[kMaxLayers];
     h->sweep++;
 }
@@ -979,6 +989,9 @@ void wmcd::destroy_handle(wmcd_handle* H) {
     for (auto& u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->fj.side[0]) cudaStreamDestroy(h->fj.side[0]);
+    if (h->fj.fork) cudaEventDestroy(h->fj.fork);
+    if (h->fj.join[0]) cudaEventDestroy(h->fj.join[0]);
     cudaGetLastError();
     delete H;
 }

@@ -37,6 +37,7 @@ struct Handle {
     double* staging = nullptr;   // 3N doubles
     Arena* arena = nullptr;      // set while a batch places the state in its pool
     void* batch = nullptr;       // owning batch, if any
+    ForkJoin fj;                 // side stream and events: launches of a phase that run side by side
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;

@@ -234,7 +234,7 @@ void launch_counts(const SimView* d, const GroupDims& g, cudaStream_t s);
 void launch_advance(const SimView* d, const GroupDims& g, int which, cudaStream_t s);
 void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
-int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s);  // kernels launched
+
 void launch_defer_compact(const SimView* d, const GroupDims& g, int l, cudaStream_t s);
 // Side streams and events to run independent launches of a phase side by side (recorded as
 // parallel branches of a graph); null members mean one stream.
@@ -243,6 +243,8 @@ struct ForkJoin {
     cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 };
 constexpr int64_t kSmemClassHi[3] = {320, 1024, 1 << 30};
+// kernels launched; with side streams in fj the dense regions of the phase run beside the rest
+int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s, const ForkJoin* fj);
 int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj);  // kernels launched
 int launch_planewave(const SimView* d, const GroupDims& g, int direct, int m, cudaStream_t s);
 int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t s);     // kernels launched

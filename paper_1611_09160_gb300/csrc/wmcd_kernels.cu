@@ -3420,7 +3420,10 @@ void prepare_staged(const GroupDims& g) {
         int qpb = 1, warps = 1;
         staged_shape(g, cap, &qpb, &warps);
         smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, g.ncap));
-        if (split_layer(g, l, cap)) smem = std::max(smem, (int)light_smem_bytes(g.ncap));
+        if (split_layer(g, l, cap)) {
+            smem = std::max(smem, (int)light_smem_bytes(g.ncap));
+            smem = std::max(smem, (int)staged_smem_bytes(staged_cap_max(g.ncap), 1, g.ncap));
+        }
     }
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
         cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -3432,7 +3435,7 @@ void prepare_staged(const GroupDims& g) {
     }
 }
 
-int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s) {
+int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s, const ForkJoin* fj) {
     const int nq = g.nq[l];
     const int gb = (int)gx((g.maxN + 255) / 256, g.S);
     k_zero<<<dim3(gx((nq + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 1, l);
@@ -3446,22 +3449,37 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
     const dim3 grid((nq + qpb - 1) / qpb, g.S);
     prepare_staged(g);
     const int stride = (int)warp_stride(cap, g.ncap);
-    int lo = 0;
-    if (split_layer(g, l, cap)) {
-        // ordinary regions first (at most kLightCap beads): small staging, more warps on each SM
+    const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
+    if (split_layer(g, l, cap) && fj && fj->side[0]) {
+        // Ordinary regions (at most kLightCap beads) on the stream, one warp per queue and small
+        // staging; the dense regions (a chain's worth of beads, the longest queues of the phase)
+        // at the same time on a side stream, one block of cooperating warps per queue with room
+        // for the largest region. The two launches take disjoint queues of one colour.
         const int qL = kMaxStageWarps;
         const dim3 gridL((nq + qL - 1) / qL, g.S);
         const size_t smemL = light_smem_bytes(g.ncap);
         const int strideL = (int)warp_stride_staged(kLightCap, g.ncap);
+        const int capH = staged_cap_max(g.ncap);
+        const size_t smemH = staged_smem_bytes(capH, 1, g.ncap);
+        const int strideH = (int)warp_stride(capH, g.ncap);
+        const dim3 gridH(nq, g.S);
+        cudaEventRecord(fj->fork, s);
+        cudaStreamWaitEvent(fj->side[0], fj->fork, 0);
+        if (g.prec_mask & 1)
+            k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, g.ncap, strideH, kLightCap + 1, 1 << 30);
+        if (g.prec_mask & 2)
+            k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, g.ncap, strideH, kLightCap + 1, 1 << 30);
         if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, g.ncap, strideL, 0, kLightCap);
         if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, g.ncap, strideL, 0, kLightCap);
-        lo = kLightCap + 1;
+        cudaEventRecord(fj->join[0], fj->side[0]);
+        cudaStreamWaitEvent(s, fj->join[0], 0);
+        return 4 + 2 * np;
     }
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, lo, 1 << 30);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, lo, 1 << 30);
-    const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
-    return 4 + np * (lo > 0 ? 2 : 1);
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, 0, 1 << 30);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, 0, 1 << 30);
+    return 4 + np;
+
 }
 
 }  // namespace wmcd

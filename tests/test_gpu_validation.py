@@ -1,0 +1,50 @@
+"""Validation workloads on the GPU path at sizes beyond the oracle (the module
+paper_1611_09160_gb300.validate): closed forms of the paper checked at 10^6 beads, and the
+acceptance spectra and cost-scaling curves produced."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_09160_gb300 import validate as V
+from paper_1611_09160_gb300 import wmcd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    wmcd.build()
+    wmcd.load()
+
+
+def test_free_diffusion_at_a_million_beads():
+    """Eq. 33 (MSD per accepted move) and Eq. 34 (time step) on 10^6 free beads; the support count
+    per sweep against its closed-form mean."""
+    r = V.free_diffusion(n=1_000_000, sweeps=3)
+    assert r["accepted"] == r["attempted"]
+    assert abs(r["ratio"] - 1.0) < 4.5 * 1.5 * r["ratio_rel_se_over_moves"] + 2e-3, r
+    assert r["a2_dt_over_eq33"] == pytest.approx(1.0, rel=1e-12)
+    assert r["bead_updates_per_sweep"] == pytest.approx(r["expected_bead_updates_per_sweep"], rel=0.1)
+
+
+def test_acceptance_spectra_semidilute():
+    """Acceptance per octave of lambda (Sec. V.C) and per |k| bin (Sec. VI.A): probabilities in
+    (0, 1], every octave attempted, and large-k plane waves accepted more often than the
+    smallest-k ones (the strain estimate overestimates dU at large k)."""
+    r = V.acceptance_spectra(sweeps=3)
+    w = [b for b in r["wavelet"] if b["moves"] > 0]
+    assert len(w) >= 5
+    assert all(0.0 < b["p_acc"] <= 1.0 for b in w)
+    pw = [b for b in r["plane_wave"] if b["moves"] >= 10]
+    assert len(pw) >= 3
+    assert pw[-1]["p_acc"] >= pw[0]["p_acc"]
+
+
+def test_cost_scaling_follows_n_log_n():
+    """Bead-updates per simulated time grow as N (a + b ln(L / 2 lmin)) (Sec. V.F)."""
+    r = V.cost_scaling(sizes=(32_768, 131_072, 524_288), sweeps=2)
+    assert r["fit_max_rel_dev"] < 0.05
+    assert r["fit_b"] > 0
+    per_n = [row["bead_updates_per_tau"] / row["N"] for row in r["rows"]]
+    assert per_n[0] < per_n[1] < per_n[2]
