@@ -3360,7 +3360,11 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
 size_t staged_smem_bytes(int cap, int warps, int ncap) { return (size_t)warps * warp_stride(cap, ncap); }
 // the launch of ordinary regions: regions of at most kLightCap beads, kMaxStageWarps queues per block
 constexpr int kLightCap = 80;
-static size_t light_smem_bytes(int ncap) { return (size_t)kMaxStageWarps * warp_stride_staged(kLightCap, ncap); }
+// (its supports are at most its regions' kLightCap beads, so its support arrays need no more)
+static int light_ncap(int ncap) { return ncap < kLightCap ? ncap : kLightCap; }
+static size_t light_smem_bytes(int ncap) {
+    return (size_t)kMaxStageWarps * warp_stride_staged(kLightCap, light_ncap(ncap));
+}
 static bool split_layer(const GroupDims& g, int l, int cap) {
     return g.cap_l[l] == 0 && cap > kLightCap &&
            light_smem_bytes(g.ncap) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
@@ -3458,7 +3462,7 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         const int qL = kMaxStageWarps;
         const dim3 gridL((nq + qL - 1) / qL, g.S);
         const size_t smemL = light_smem_bytes(g.ncap);
-        const int strideL = (int)warp_stride_staged(kLightCap, g.ncap);
+        const int strideL = (int)warp_stride_staged(kLightCap, light_ncap(g.ncap));
         const int capH = staged_cap_max(g.ncap);
         const size_t smemH = staged_smem_bytes(capH, 1, g.ncap);
         const int strideH = (int)warp_stride(capH, g.ncap);
@@ -3469,8 +3473,9 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
             k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, g.ncap, strideH, kLightCap + 1, 1 << 30);
         if (g.prec_mask & 2)
             k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, g.ncap, strideH, kLightCap + 1, 1 << 30);
-        if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, g.ncap, strideL, 0, kLightCap);
-        if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, g.ncap, strideL, 0, kLightCap);
+        const int ncL = light_ncap(g.ncap);
+        if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap);
+        if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap);
         cudaEventRecord(fj->join[0], fj->side[0]);
         cudaStreamWaitEvent(s, fj->join[0], 0);
         return 4 + 2 * np;
