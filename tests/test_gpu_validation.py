@@ -45,8 +45,10 @@ def test_acceptance_spectra_semidilute():
 
 
 def test_cost_scaling_follows_n_log_n():
-    """Bead-updates per simulated time grow as N (a + b ln(L / 2 lmin)) (Sec. V.F)."""
-    r = V.cost_scaling(sizes=(32_768, 131_072, 524_288), sweeps=2)
+    """Bead-updates per simulated time grow as N (a + b ln(L / 2 lmin)) (Sec. V.F). One sweep's
+    count carries a few per cent of noise from the rare largest wavelets, so eight sweeps."""
+    r = V.cost_scaling(sizes=(32_768, 131_072, 524_288), sweeps=8)
+    print(r)
     assert r["fit_max_rel_dev"] < 0.05
     assert r["fit_b"] > 0
     per_n = [row["bead_updates_per_tau"] / row["N"] for row in r["rows"]]
