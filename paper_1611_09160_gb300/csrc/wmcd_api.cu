@@ -430,6 +430,8 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     bool ok = true;
     ok = ok && !dalloc(h, &v.bead, N) && !dalloc(h, &v.bf, N) && !dalloc(h, &v.prev, N) && !dalloc(h, &v.img, 3 * N) &&
          !dalloc(h, &v.bnext, N) && !dalloc(h, &v.head, ncell);
+    v.occ_w = (P.grid_f + 31) / 32;
+    ok = ok && !dalloc(h, &v.occ, (size_t)P.grid_f * P.grid_f * v.occ_w);
     ok = ok && !dalloc(h, &v.slot_V, 3 * Mall) && !dalloc(h, &v.slot_p, 3 * Mall) && !dalloc(h, &v.slot_thr, Mall);
     ok = ok && !dalloc(h, &v.slot_lam, Mall) && !dalloc(h, &v.slot_bead, Mall) && !dalloc(h, &v.slot_key, Mall) &&
          !dalloc(h, &v.q_slots, Mall) && !dalloc(h, &v.defer, Mall) && !dalloc(h, &v.serial_list, Mall);

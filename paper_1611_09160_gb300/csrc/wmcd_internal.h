@@ -120,6 +120,9 @@ struct SimView {
     int* img;                    // 3 per bead
     uint8_t* bnext;              // bead i bonded to i + 1
     int* head;                   // Gf^3 fine cells, -1 = empty
+    uint32_t* occ;               // occupancy bits of the fine cells: row (y, z) holds occ_w words,
+                                 // bit x of the row set iff head[x + Gf (y + Gf z)] != -1 (null: none)
+    int occ_w;                   // words per row, ceil(Gf / 32)
     int64_t N;
     double L, halfL, invf;
     int Gf, K, n_cap, precision;

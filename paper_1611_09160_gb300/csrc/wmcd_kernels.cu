@@ -103,6 +103,29 @@ __device__ __forceinline__ int cell_lin(const SimView& v, double x, double y, do
 }
 __device__ __forceinline__ int wrapi(int c, int G) { c %= G; return c < 0 ? c + G : c; }
 
+// occupancy bit of fine cell c (atomic: cells of neighbouring regions share a word)
+__device__ __forceinline__ void occ_bit(const SimView& v, int c, bool on) {
+    if (!v.occ) return;
+    const int x = c % v.Gf, yz = c / v.Gf;
+    uint32_t* w = &v.occ[(size_t)yz * v.occ_w + (x >> 5)];
+    if (on) atomicOr(w, 1u << (x & 31));
+    else atomicAnd(w, ~(1u << (x & 31)));
+}
+// Move bead m from the list of fine cell oc to the head of the list of ncl (lists doubly linked
+// through Bead::next and prev[]), keeping both cells' occupancy bits.
+__device__ __forceinline__ void relink(const SimView& v, int m, int oc, int ncl) {
+    const int pr = v.prev[m], nx = v.bead[m].next;
+    if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+    if (nx >= 0) v.prev[nx] = pr;
+    if (pr < 0 && nx < 0) occ_bit(v, oc, false);
+    const int hd = v.head[ncl];
+    v.bead[m].next = hd;
+    v.prev[m] = -1;
+    if (hd >= 0) v.prev[hd] = m;
+    v.head[ncl] = m;
+    occ_bit(v, ncl, true);
+}
+
 // ======================================================================================
 // Cell list: per fine cell a singly linked list through Bead::next plus prev[] for O(1)
 // removal. Built in canonical order (ascending bead id within a cell) so runs repeat.
@@ -122,6 +145,11 @@ __global__ void k_cl_clear(const SimView* __restrict__ vs, int use_flag) {
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
         v.head[c] = -1;
+    if (v.occ) {
+        const int64_t nw = (int64_t)v.Gf * v.Gf * v.occ_w;
+        for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+            v.occ[w] = 0u;
+    }
 }
 __global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
     SIM_EXIT_IF(cl_skip(gv, use_flag))
@@ -132,40 +160,55 @@ __global__ void k_cl_insert(const SimView* __restrict__ vs, int use_flag) {
         int c = cell_lin(v, b.x, b.y, b.z);
         int old = atomicExch(&v.head[c], (int)i);
         v.bead[i].next = old;
+        if (old < 0) occ_bit(v, c, true);
+    }
+}
+// put the list of fine cell c in ascending bead-id order and set prev[]
+__device__ void canon_cell(const SimView& v, int64_t c) {
+    int ids[32];
+    int n = 0, p = v.head[c];
+    bool small = true;
+    while (p >= 0) {
+        if (n < 32) ids[n] = p;
+        n++;
+        if (n > 32) small = false;
+        if (n > kMaxWalk) { set_err(v, E_WALK); break; }
+        p = v.bead[p].next;
+    }
+    if (n == 0) return;
+    if (small) {
+        for (int a = 1; a < n; a++) {      // insertion sort by bead id
+            int x = ids[a], b = a - 1;
+            while (b >= 0 && ids[b] > x) { ids[b + 1] = ids[b]; b--; }
+            ids[b + 1] = x;
+        }
+        v.head[c] = ids[0];
+        for (int a = 0; a < n; a++) {
+            v.bead[ids[a]].next = (a + 1 < n) ? ids[a + 1] : -1;
+            v.prev[ids[a]] = (a > 0) ? ids[a - 1] : -1;
+        }
+    } else {
+        int pr = -1;
+        for (int q = v.head[c]; q >= 0; q = v.bead[q].next) { v.prev[q] = pr; pr = q; }
     }
 }
 __global__ void k_cl_canon(const SimView* __restrict__ vs, int use_flag) {
     SIM_EXIT_IF(cl_skip(gv, use_flag))
     SIM_PROLOGUE
-    int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        int ids[32];
-        int n = 0, p = v.head[c];
-        bool small = true;
-        while (p >= 0) {
-            if (n < 32) ids[n] = p;
-            n++;
-            if (n > 32) small = false;
-            if (n > kMaxWalk) { set_err(v, E_WALK); break; }
-            p = v.bead[p].next;
+    if (v.occ) {
+        // only the occupied cells (the bits were set by the insert pass just before)
+        const int64_t nw = (int64_t)v.Gf * v.Gf * v.occ_w;
+        for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t yz = w / v.occ_w;
+            const int xb = (int)(w % v.occ_w) << 5;
+            for (uint32_t bits = v.occ[w]; bits; bits &= bits - 1u)
+                canon_cell(v, (int64_t)(xb + __ffs(bits) - 1) + (int64_t)v.Gf * yz);
         }
-        if (n == 0) continue;
-        if (small) {
-            for (int a = 1; a < n; a++) {      // insertion sort by bead id
-                int x = ids[a], b = a - 1;
-                while (b >= 0 && ids[b] > x) { ids[b + 1] = ids[b]; b--; }
-                ids[b + 1] = x;
-            }
-            v.head[c] = ids[0];
-            for (int a = 0; a < n; a++) {
-                v.bead[ids[a]].next = (a + 1 < n) ? ids[a + 1] : -1;
-                v.prev[ids[a]] = (a > 0) ? ids[a - 1] : -1;
-            }
-        } else {
-            int pr = -1;
-            for (int q = v.head[c]; q >= 0; q = v.bead[q].next) { v.prev[q] = pr; pr = q; }
-        }
+        return;
     }
+    int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        canon_cell(v, c);
 }
 // blocks per simulation for a grid-stride kernel: what the largest simulation needs, but no
 // more than keeps about 8k blocks over the whole group
@@ -848,14 +891,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
             const int oc = cell_lin(v, sm.op[k][0], sm.op[k][1], sm.op[k][2]);
             const int ncl = cell_lin(v, sm.np[k][0], sm.np[k][1], sm.np[k][2]);
             if (oc == ncl) continue;
-            const int pr = v.prev[m], nx = v.bead[m].next;
-            if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
-            if (nx >= 0) v.prev[nx] = pr;
-            const int hd = v.head[ncl];
-            v.bead[m].next = hd;
-            v.prev[m] = -1;
-            if (hd >= 0) v.prev[hd] = m;
-            v.head[ncl] = m;
+            relink(v, m, oc, ncl);
         }
     }
     __syncwarp();
@@ -1004,6 +1040,36 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                 for (int u = 0; u < 4; u++) {
                     const int64_t m = m0 + (int64_t)u * NT;
                     if (m < v.N && screened(f[u])) consider_exact((int)m, v.bead[m]);
+                }
+            }
+        } else if (v.occ) {
+            // rows (y, z) of the ball's cell box over the threads; each row's x range read as
+            // occupancy words, and only the lists of occupied cells walked
+            const int c0[3] = {sh_c0[0], sh_c0[1], sh_c0[2]}, nc[3] = {sh_nc[0], sh_nc[1], sh_nc[2]};
+            const int Gf = v.Gf, rows = nc[1] * nc[2];
+            const int x0 = wrapi(c0[0], Gf);
+            for (int r = tid; r < rows; r += NT) {
+                const int y = wrapi(c0[1] + r % nc[1], Gf), z = wrapi(c0[2] + r / nc[1], Gf);
+                const uint32_t* row = v.occ + ((size_t)y + (size_t)Gf * z) * v.occ_w;
+                const int rowcell = Gf * (y + Gf * z);
+                // the x range [x0, x0 + nc[0]) as at most two pieces inside [0, Gf)
+                for (int piece = 0; piece < 2; piece++) {
+                    const int a = piece == 0 ? x0 : 0;
+                    const int b = piece == 0 ? min(x0 + nc[0], Gf) : x0 + nc[0] - Gf;
+                    for (int wi = a >> 5; a < b && wi <= (b - 1) >> 5; wi++) {
+                        uint32_t bits = row[wi];
+                        const int lo = max(a - (wi << 5), 0), hi = min(b - (wi << 5), 32);
+                        bits &= (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+                        for (; bits; bits &= bits - 1u) {
+                            int guard = 0;
+                            for (int q = v.head[rowcell + (wi << 5) + __ffs(bits) - 1]; q >= 0;) {
+                                const Bead bb = v.bead[q];
+                                if (screened(v.bf[q])) consider_exact(q, bb);
+                                q = bb.next;
+                                if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+                            }
+                        }
+                    }
                 }
             }
         } else {
@@ -1381,14 +1447,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         if (tid == 0) {
             for (int c = 0; c < sh_nch; c++) {
                 int m = v.s_changed[3 * c], oc = v.s_changed[3 * c + 1], ncl = v.s_changed[3 * c + 2];
-                int pr = v.prev[m], nx = v.bead[m].next;
-                if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
-                if (nx >= 0) v.prev[nx] = pr;
-                int h = v.head[ncl];
-                v.bead[m].next = h;
-                v.prev[m] = -1;
-                if (h >= 0) v.prev[h] = m;
-                v.head[ncl] = m;
+                relink(v, m, oc, ncl);
             }
             att++;
             bu += n;
@@ -3328,14 +3387,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                 for (unsigned bits = ch; bits; bits &= bits - 1u) {
                     const int ln = __ffs(bits) - 1, tt = base2 + ln;
                     const int m = S.sid[tt], oc = S.cand[32 + ln], ncl = S.cand[ln];
-                    const int pr = v.prev[m], nx = v.bead[m].next;
-                    if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
-                    if (nx >= 0) v.prev[nx] = pr;
-                    const int hd = v.head[ncl];
-                    v.bead[m].next = hd;
-                    v.prev[m] = -1;
-                    if (hd >= 0) v.prev[hd] = m;
-                    v.head[ncl] = m;
+                    relink(v, m, oc, ncl);
                 }
             }
             __syncwarp();
