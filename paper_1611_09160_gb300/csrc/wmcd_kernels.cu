@@ -142,6 +142,19 @@ __device__ __forceinline__ bool cl_skip(const SimView& v, int use_flag) {
 __global__ void k_cl_clear(const SimView* __restrict__ vs, int use_flag) {
     SIM_EXIT_IF(cl_skip(gv, use_flag))
     SIM_PROLOGUE
+    if (v.occ && use_flag != 0) {
+        // lists and bits agree since the last full rebuild: empty only the occupied cells
+        const int64_t nw = (int64_t)v.Gf * v.Gf * v.occ_w;
+        for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+            const uint32_t bits0 = v.occ[w];
+            if (!bits0) continue;
+            const int64_t base = (w % v.occ_w) * 32 + (int64_t)v.Gf * (w / v.occ_w);
+            for (uint32_t bits = bits0; bits; bits &= bits - 1u) v.head[base + __ffs(bits) - 1] = -1;
+            v.occ[w] = 0u;
+        }
+        return;
+    }
+    // full rebuild (creation, new positions or state): every cell and every bit
     int64_t nc = (int64_t)v.Gf * v.Gf * v.Gf;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
         v.head[c] = -1;
