@@ -411,24 +411,34 @@ __global__ void k_defer_compact(const SimView* __restrict__ vs, int l) {
     SIM_PROLOGUE
     if (l >= v.nL || v.layer[l].G == 0) return;
     const int M = v.counts[l];
-    __shared__ int part[1024];
-    __shared__ int carry;
+    // the deferred slots in schedule order: per chunk of 1024 a vote per warp, an exclusive prefix
+    // of the 32 warp counts, and each deferred slot's place from the bits below it in its warp;
+    // chunks without a deferred slot (nearly all) cost one block vote
+    __shared__ int wpre[32], wtot, carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < M; base += 1024) {
-        int i = base + threadIdx.x;
-        int x = (i < M && v.defer[i]) ? 1 : 0;
-        part[threadIdx.x] = x;
+        const int i = base + threadIdx.x;
+        const int x = (i < M && v.defer[i]) ? 1 : 0;
+        if (!__syncthreads_or(x)) continue;
+        const unsigned b = __ballot_sync(0xffffffffu, x);
+        if (lane == 0) wpre[wid] = __popc(b);
         __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            int y = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-            __syncthreads();
-            part[threadIdx.x] += y;
-            __syncthreads();
+        if (wid == 0) {
+            const int c = wpre[lane];
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            wpre[lane] = incl - c;
+            if (lane == 31) wtot = incl;
         }
-        if (x) v.serial_list[carry + part[threadIdx.x] - 1] = v.q_slots[i];
         __syncthreads();
-        if (threadIdx.x == 1023) carry += part[1023];
+        if (x) v.serial_list[carry + wpre[wid] + __popc(b & ((1u << lane) - 1u))] = v.q_slots[i];
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wtot;
         __syncthreads();
     }
     if (threadIdx.x == 0) *v.serial_count = carry;
