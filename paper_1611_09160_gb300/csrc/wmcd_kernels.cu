@@ -111,6 +111,12 @@ __device__ __forceinline__ void occ_bit(const SimView& v, int c, bool on) {
     if (on) atomicOr(w, 1u << (x & 31));
     else atomicAnd(w, ~(1u << (x & 31)));
 }
+// the bits of occupancy word wi of a row that lie in the cell range [a, b) of the row
+__device__ __forceinline__ uint32_t occ_masked(uint32_t word, int a, int b, int wi) {
+    const int lo = max(a - (wi << 5), 0), hi = min(b - (wi << 5), 32);
+    if (hi <= lo) return 0u;
+    return word & (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+}
 // Move bead m from the list of fine cell oc to the head of the list of ncl (lists doubly linked
 // through Bead::next and prev[]), keeping both cells' occupancy bits.
 __device__ __forceinline__ void relink(const SimView& v, int m, int oc, int ncl) {
@@ -774,7 +780,67 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
         nc[a] = min(t1 - c0[a] + 1, Gf);
     }
     int n = 0;
-    {
+    // one bead per lane per step: test it, vote, append the members in vote order; a support
+    // above n_cap means the move is deferred, so the walk stops there
+    auto step = [&](int& ptr) {
+        bool in = false;
+        int nxt = -1;
+        Bead bb;
+        if (ptr >= 0) {
+            bb = v.bead[ptr];
+            nxt = bb.next;
+            const float d2f = norm2f(dif32(bb.x, b[0], L, hLf), dif32(bb.y, b[1], L, hLf), dif32(bb.z, b[2], L, hLf));
+            if (d2f < lin) in = true;
+            else if (d2f <= lout) {
+                const double e2 = norm2(mi(sub(bb.x, b[0]), L, hL), mi(sub(bb.y, b[1]), L, hL), mi(sub(bb.z, b[2]), L, hL));
+                in = e2 < lam2;
+            }
+        }
+        const unsigned msk = __ballot_sync(FULL, in);
+        const int slot = n + __popc(msk & ((1u << lane) - 1u));
+        if (in && slot < kNCapMax) {
+            sm.ids[slot] = ptr;
+            sm.op[slot][0] = bb.x; sm.op[slot][1] = bb.y; sm.op[slot][2] = bb.z;
+        }
+        n += __popc(msk);
+        ptr = nxt;
+    };
+    if (v.occ) {
+        // rows (y, z) of the ball's cell box over the lanes; each lane takes the occupied cells of
+        // its row's x range from the occupancy words, one list at a time
+        const int rows = nc[1] * nc[2], x0 = wrapi(c0[0], Gf);
+        int guard = 0;
+        for (int base = 0; base < rows; base += 32) {
+            const int r = base + lane;
+            bool live = r < rows;
+            const uint32_t* row = nullptr;
+            int rowcell = 0, piece = 0, a = x0, bnd = min(x0 + nc[0], Gf), wi = x0 >> 5;
+            uint32_t bits = 0u;
+            if (live) {
+                const int y = wrapi(c0[1] + r % nc[1], Gf), z = wrapi(c0[2] + r / nc[1], Gf);
+                row = v.occ + ((size_t)y + (size_t)Gf * z) * v.occ_w;
+                rowcell = Gf * (y + Gf * z);
+                bits = occ_masked(row[wi], a, bnd, wi);
+            }
+            int ptr = -1;
+            while (true) {
+                while (live && ptr < 0) {
+                    if (bits) { ptr = v.head[rowcell + (wi << 5) + __ffs(bits) - 1]; bits &= bits - 1u; continue; }
+                    if (wi < ((bnd - 1) >> 5)) { wi++; bits = occ_masked(row[wi], a, bnd, wi); continue; }
+                    if (piece == 0 && x0 + nc[0] > Gf) {
+                        piece = 1; a = 0; bnd = x0 + nc[0] - Gf; wi = 0;
+                        bits = occ_masked(row[0], a, bnd, 0);
+                        continue;
+                    }
+                    live = false;
+                }
+                if (!__any_sync(FULL, ptr >= 0)) break;
+                step(ptr);
+                if (n > v.n_cap) { *n_out = n; return DEFER; }
+                if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
+            }
+        }
+    } else {
         const int nxy = nc[0] * nc[1];
         int guard = 0;
         for (int base = 0; base < nxy; base += 32) {
@@ -784,27 +850,8 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
             for (int kz = 0; kz < nc[2]; kz++) {
                 int ptr = col ? v.head[colbase + Gf * Gf * wrapc(c0[2] + kz, Gf)] : -1;
                 while (__any_sync(FULL, ptr >= 0)) {
-                    bool in = false;
-                    int nxt = -1;
-                    Bead bb;
-                    if (ptr >= 0) {
-                        bb = v.bead[ptr];
-                        nxt = bb.next;
-                        const float d2f = norm2f(dif32(bb.x, b[0], L, hLf), dif32(bb.y, b[1], L, hLf), dif32(bb.z, b[2], L, hLf));
-                        if (d2f < lin) in = true;
-                        else if (d2f <= lout) {
-                            const double e2 = norm2(mi(sub(bb.x, b[0]), L, hL), mi(sub(bb.y, b[1]), L, hL), mi(sub(bb.z, b[2]), L, hL));
-                            in = e2 < lam2;
-                        }
-                    }
-                    const unsigned msk = __ballot_sync(FULL, in);
-                    const int slot = n + __popc(msk & ((1u << lane) - 1u));
-                    if (in && slot < kNCapMax) {
-                        sm.ids[slot] = ptr;
-                        sm.op[slot][0] = bb.x; sm.op[slot][1] = bb.y; sm.op[slot][2] = bb.z;
-                    }
-                    n += __popc(msk);
-                    ptr = nxt;
+                    step(ptr);
+                    if (n > v.n_cap) { *n_out = n; return DEFER; }
                     if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
                 }
             }
