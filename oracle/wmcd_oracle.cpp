@@ -421,6 +421,7 @@ typedef struct OParams {
     int32_t big_support;          // a launch choice of the GPU library; no meaning here
     int32_t acceptance;           // 0 Metropolis (Eq. 20), 1 Glauber
     int32_t centring;             // 0 centre near a picked bead (Eq. 26), 1 uniform in the box (Sec. V.D)
+    int32_t level2;               // 1: deferred slots get a second colouring on a grid half as fine
 } OParams;
 
 typedef struct OStats {
@@ -465,6 +466,7 @@ struct Sim {
     double p_fourier = 0.0;
     // carries of lambda after a rejection (Appendix D, parameter recycling)
     std::vector<std::vector<double>> carry_q;   // per layer, per coarse cell (0 = none)
+    std::vector<std::vector<double>> carry_q2;  // per layer, per cell of the second-level grid
     std::vector<double> carry_serial;           // per layer
     int pw_carry = -1;                          // carried plane-wave mode (index), -1 none
     int pw_carry_l[3] = {0, 0, 0};
@@ -717,7 +719,8 @@ static bool point_inside(const Sim& s, const Region& Rg, const double* p) {
 // scale lam (own draw or the carried scale of a rejected move). `Rg` is the concurrency
 // region when the move runs in a coloured phase, null in the serial phase.
 // Returns ACCEPT, REJECT or DEFER; n receives the number of beads in the support.
-static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, const Region* Rg, int* n_out) {
+static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, const Region* Rg, int* n_out,
+                           int ncap) {
     const uint64_t sw = s.sweep;
     s.last_du = 0.0;
     // centre: b = r_i + lam V, V uniform in the unit ball (wrapped into the box); or uniform in
@@ -741,7 +744,7 @@ static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, con
     }
     int n = (int)S.size();
     *n_out = n;
-    if (Rg && n > s.P.n_cap) return DEFER;
+    if (Rg && n > ncap) return DEFER;
     double p[3];
     polarisation(s, l, sw, j, p);
     // amplitude A_w = A0 lam / sqrt(n)  (Eq. 29) and the new positions
@@ -805,6 +808,15 @@ static int64_t slot_count(const Sim& s, int kind, int l, uint64_t ctr, double x)
     return (int64_t)f + ((u < x - f) ? 1 : 0);
 }
 
+/* ---- second-level grid of a coloured layer: K floor(G / 2K) coarse cells per axis when that
+ *      leaves at least two per colour and axis and the run asks for it, else none ---- */
+static const int SECOND_NCAP = 256;
+static int level2_grid(const Sim& s, int G) {
+    if (!s.P.level2 || G <= 0) return 0;
+    const int K = s.P.colour_K, G2 = K * (G / (2 * K));
+    return G2 >= 2 * K ? G2 : 0;
+}
+
 /* ---- one layer: coloured phases then the serial phase ---- */
 static void run_layer(Sim& s, int l) {
     const Layer& Ly = s.layers[l];
@@ -817,8 +829,10 @@ static void run_layer(Sim& s, int l) {
     s.tr_n[l].assign(M, 0);
     s.tr_du[l].assign(M, 0.0);
     std::vector<int64_t> serial;
-    auto record = [&](int64_t j, int r, int n, bool deferred) {
-        s.tr_out[l][j] = (uint8_t)((r == ACCEPT ? 1 : 2) | (deferred ? 4 : 0));
+    // flags: 4 = deferred from the first colouring, 8 = deferred from the second as well
+    bool second = false;
+    auto record = [&](int64_t j, int r, int n, int flags) {
+        s.tr_out[l][j] = (uint8_t)((r == ACCEPT ? 1 : 2) | flags);
         s.tr_n[l][j] = n;
         s.tr_du[l][j] = s.last_du;
         s.st.attempts[l]++;
@@ -864,13 +878,68 @@ static void run_layer(Sim& s, int l) {
                 int64_t j = keyed[t].second;
                 double lam_eff = carry > 0.0 ? carry : lam[j];
                 int n = 0;
-                int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, &Rg, &n);
+                int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, &Rg, &n, s.P.n_cap);
                 if (r == DEFER) { serial.push_back(j); s.st.deferred[l]++; continue; }
-                record(j, r, n, false);
+                record(j, r, n, 0);
                 carry = (r == ACCEPT) ? 0.0 : lam_eff;
             }
             s.carry_q[l][cell] = carry;
             a = e;
+        }
+        // second level (our schedule, as the first): the deferred slots are bucketed again on the
+        // grid G2 = K floor(G / 2K), by the coarse cell of their bead (or centre) now, and run in
+        // its colour phases, regions twice as wide and supports up to SECOND_NCAP beads; a slot
+        // deferred again runs in the serial phase, in this second schedule's order
+        const int G2 = level2_grid(s, G);
+        if (G2 > 0) {
+            const int Q2 = G2 / K;
+            const int64_t nq2 = (int64_t)Q2 * Q2 * Q2;
+            const double invG2 = (double)G2 / s.L;
+            std::vector<std::pair<int64_t, int64_t>> keyed2(serial.size());
+            for (size_t t = 0; t < serial.size(); t++) {
+                int64_t j = serial[t];
+                int c[3];
+                double bc[3];
+                if (s.P.centring == 1) uniform_centre(s, l, sw, (uint32_t)j, bc);
+                for (int a2 = 0; a2 < 3; a2++) {
+                    int64_t v = (int64_t)std::floor((s.P.centring == 1 ? bc[a2] : s.pos[3 * bead[j] + a2]) * invG2);
+                    if (v < 0) v = 0;
+                    if (v >= G2) v = G2 - 1;
+                    c[a2] = (int)v;
+                }
+                int64_t colour = (c[0] % K) + K * ((c[1] % K) + K * (c[2] % K));
+                int64_t q = (c[0] / K) + (int64_t)Q2 * ((c[1] / K) + (int64_t)Q2 * (c[2] / K));
+                keyed2[t] = {colour * nq2 + q, (int64_t)t};
+            }
+            std::sort(keyed2.begin(), keyed2.end());
+            std::vector<int64_t> serial2;
+            size_t a2 = 0;
+            while (a2 < keyed2.size()) {
+                int64_t key = keyed2[a2].first;
+                size_t e = a2;
+                while (e < keyed2.size() && keyed2[e].first == key) e++;
+                int64_t colour = key / nq2, q = key % nq2;
+                int c[3] = {(int)(K * (q % Q2) + colour % K), (int)(K * ((q / Q2) % Q2) + (colour / K) % K),
+                            (int)(K * (q / ((int64_t)Q2 * Q2)) + colour / (K * K))};
+                Region Rg = region_of(s, G2, c);
+                int64_t cell = c[0] + (int64_t)G2 * (c[1] + (int64_t)G2 * c[2]);
+                double carry = s.carry_q2[l][cell];
+                for (size_t t = a2; t < e; t++) {
+                    if (s.move_budget == 0) return;
+                    if (s.move_budget > 0) s.move_budget--;
+                    int64_t j = serial[keyed2[t].second];
+                    double lam_eff = carry > 0.0 ? carry : lam[j];
+                    int n = 0;
+                    int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, &Rg, &n, SECOND_NCAP);
+                    if (r == DEFER) { serial2.push_back(j); continue; }
+                    record(j, r, n, 4);
+                    carry = (r == ACCEPT) ? 0.0 : lam_eff;
+                }
+                s.carry_q2[l][cell] = carry;
+                a2 = e;
+            }
+            serial.swap(serial2);
+            second = true;
         }
     } else {
         for (int64_t j = 0; j < M; j++) serial.push_back(j);
@@ -882,8 +951,8 @@ static void run_layer(Sim& s, int l) {
         if (s.move_budget > 0) s.move_budget--;
         double lam_eff = carry > 0.0 ? carry : lam[j];
         int n = 0;
-        int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, nullptr, &n);
-        record(j, r, n, G > 0);
+        int r = wavelet_attempt(s, l, (uint32_t)j, bead[j], lam_eff, nullptr, &n, s.P.n_cap);
+        record(j, r, n, G > 0 ? (second ? 12 : 4) : 0);
         carry = (r == ACCEPT) ? 0.0 : lam_eff;
     }
     s.carry_serial[l] = carry;
@@ -1133,7 +1202,7 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     if (P.n_beads < 1 || !(P.box_L > 0) || !(P.lambda_min > 0) || !(P.lambda_max > P.lambda_min) ||
         P.lambda_max > 0.5 * P.box_L || !(P.A0 > 0) || !(P.kT > 0) || P.colour_K < 2 || P.colour_K > 4 ||
         P.grid_f < 1 || P.n_cap < 1 || P.bond_type < 0 || P.bond_type > 2 || P.acceptance < 0 || P.acceptance > 1 ||
-        P.centring < 0 || P.centring > 1)
+        P.centring < 0 || P.centring > 1 || P.level2 < 0 || P.level2 > 1)
         return -1;
     s.N = P.n_beads;
     s.L = P.box_L;
@@ -1244,6 +1313,11 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     s.carry_q.resize(nL);
     for (int l = 0; l < nL; l++) s.carry_q[l].assign(s.layers[l].G > 0 ? (size_t)s.layers[l].G * s.layers[l].G * s.layers[l].G : 0, 0.0);
     s.carry_serial.assign(nL, 0.0);
+    s.carry_q2.resize(nL);
+    for (int l = 0; l < nL; l++) {
+        int G2 = level2_grid(s, s.layers[l].G);
+        s.carry_q2[l].assign((size_t)G2 * G2 * G2, 0.0);
+    }
     s.tr_out.resize(nL);
     s.tr_n.resize(nL);
     s.tr_du.resize(nL);
