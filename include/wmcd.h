@@ -94,6 +94,11 @@ typedef struct wmcd_params {
     int32_t centring;         /* WMCD_CENTRE_BEAD: b within lambda of a picked bead (Eq. 26,
                                  A_w of Eq. 29); WMCD_CENTRE_UNIFORM: b uniform in the box, A_w from
                                  the mean support at the global density (Sec. V.D) */
+    int32_t level2;           /* bit l set: the slots coloured layer l defers get a second
+                                 colouring on K floor(G / 2K) coarse cells per axis (regions twice
+                                 as wide, supports up to 256 beads) before the serial phase, where
+                                 that leaves at least 2K cells; 0 = none (0..0xffff). Part of the
+                                 schedule: it changes the order of moves as the grid does */
 } wmcd_params;
 
 /* Counters since creation (or the last wmcd_set_state). */
@@ -128,7 +133,7 @@ typedef struct wmcd_handle wmcd_handle;
  * Validates: N >= 1; 0 < lambda_min < lambda_max <= L/2; A0 > 0; kT > 0; colour_K in 2..4;
  * grid_f >= 1 with L/grid_f >= the WCA cutoff 2^(1/6) sigma (when WCA is on);
  * 1 <= n_cap <= 256; each grid_layer[l] is 0 or a multiple of colour_K in [colour_K, 256];
- * at most 16 octave layers; planewave_mode 0..3, lcut in 0..120 (PERIODIC) or 0..40
+ * at most 16 octave layers; level2 in 0..0xffff; planewave_mode 0..3, lcut in 0..120 (PERIODIC) or 0..40
  * (PERIODIC_FULL). Returns WMCD_EINVAL otherwise.
  * Synchronises `stream` before returning. *out receives the handle. */
 int wmcd_create(const wmcd_params* params, const double* pos, const int32_t* chain_len, int64_t n_chains,

@@ -421,7 +421,7 @@ typedef struct OParams {
     int32_t big_support;          // a launch choice of the GPU library; no meaning here
     int32_t acceptance;           // 0 Metropolis (Eq. 20), 1 Glauber
     int32_t centring;             // 0 centre near a picked bead (Eq. 26), 1 uniform in the box (Sec. V.D)
-    int32_t level2;               // 1: deferred slots get a second colouring on a grid half as fine
+    int32_t level2;               // bit l: layer l's deferred slots get a second colouring on a grid half as fine
 } OParams;
 
 typedef struct OStats {
@@ -808,11 +808,11 @@ static int64_t slot_count(const Sim& s, int kind, int l, uint64_t ctr, double x)
     return (int64_t)f + ((u < x - f) ? 1 : 0);
 }
 
-/* ---- second-level grid of a coloured layer: K floor(G / 2K) coarse cells per axis when that
+/* ---- second-level grid of coloured layer l: K floor(G / 2K) coarse cells per axis when that
  *      leaves at least two per colour and axis and the run asks for it, else none ---- */
 static const int SECOND_NCAP = 256;
-static int level2_grid(const Sim& s, int G) {
-    if (!s.P.level2 || G <= 0) return 0;
+static int level2_grid(const Sim& s, int l, int G) {
+    if (!((s.P.level2 >> l) & 1) || G <= 0) return 0;
     const int K = s.P.colour_K, G2 = K * (G / (2 * K));
     return G2 >= 2 * K ? G2 : 0;
 }
@@ -890,7 +890,7 @@ static void run_layer(Sim& s, int l) {
         // grid G2 = K floor(G / 2K), by the coarse cell of their bead (or centre) now, and run in
         // its colour phases, regions twice as wide and supports up to SECOND_NCAP beads; a slot
         // deferred again runs in the serial phase, in this second schedule's order
-        const int G2 = level2_grid(s, G);
+        const int G2 = level2_grid(s, l, G);
         if (G2 > 0) {
             const int Q2 = G2 / K;
             const int64_t nq2 = (int64_t)Q2 * Q2 * Q2;
@@ -1202,7 +1202,7 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     if (P.n_beads < 1 || !(P.box_L > 0) || !(P.lambda_min > 0) || !(P.lambda_max > P.lambda_min) ||
         P.lambda_max > 0.5 * P.box_L || !(P.A0 > 0) || !(P.kT > 0) || P.colour_K < 2 || P.colour_K > 4 ||
         P.grid_f < 1 || P.n_cap < 1 || P.bond_type < 0 || P.bond_type > 2 || P.acceptance < 0 || P.acceptance > 1 ||
-        P.centring < 0 || P.centring > 1 || P.level2 < 0 || P.level2 > 1)
+        P.centring < 0 || P.centring > 1 || P.level2 < 0 || P.level2 > 0xffff)
         return -1;
     s.N = P.n_beads;
     s.L = P.box_L;
@@ -1315,7 +1315,7 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     s.carry_serial.assign(nL, 0.0);
     s.carry_q2.resize(nL);
     for (int l = 0; l < nL; l++) {
-        int G2 = level2_grid(s, s.layers[l].G);
+        int G2 = level2_grid(s, l, s.layers[l].G);
         s.carry_q2[l].assign((size_t)G2 * G2 * G2, 0.0);
     }
     s.tr_out.resize(nL);

@@ -288,6 +288,7 @@ int wmcd::validate_params(const wmcd_params* p) {
         return WMCD_EINVAL;
     if (p->planewave_mode < 0 || p->planewave_mode > 3) return WMCD_EINVAL;
     if (p->acceptance < 0 || p->acceptance > 1 || p->centring < 0 || p->centring > 1) return WMCD_EINVAL;
+    if (p->level2 < 0 || p->level2 > 0xffff) return WMCD_EINVAL;
     if (p->planewave_mode == 1 && (p->lcut < 0 || p->lcut > 120)) return WMCD_EINVAL;
     if (p->planewave_mode == 2 && (p->lcut < 0 || p->lcut > 40)) return WMCD_EINVAL;
     if ((int64_t)p->grid_f * p->grid_f * p->grid_f > ((int64_t)1 << 31) - 1) return WMCD_EINVAL;
@@ -413,6 +414,16 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
         Ly.tr_off = tr_total;
         tr_total += h->Mmax[l];
     }
+    // second colourings: K floor(G / 2K) cells per axis where that leaves at least 2K (their
+    // carries after all first-colouring ones)
+    for (int l = 0; l < nL; l++) {
+        LayerDev& Ly = v.layer[l];
+        const int K = P.colour_K, G2 = K * (Ly.G / (2 * K));
+        Ly.G2 = (((P.level2 >> l) & 1) && Ly.G > 0 && G2 >= 2 * K) ? G2 : 0;
+        Ly.invG2 = Ly.G2 > 0 ? (double)Ly.G2 / P.box_L : 0.0;
+        Ly.carry_off2 = (int)carry_total;
+        carry_total += (int64_t)Ly.G2 * Ly.G2 * Ly.G2;
+    }
     // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2 pi)^3 = 1/105)
     {
         const double la = 1.0 / (1.125 - kLn2), A02 = P.A0 * P.A0, la2 = la * la;
@@ -457,14 +468,19 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     ok = ok && !dalloc(h, &h->staging, 3 * N);
     // region assignment for staging: per-axis tables fine cell -> queue coordinate (-1 = the
     // cell straddles two regions of the colour), per layer and colour offset
-    std::vector<int> tab((size_t)nL * P.colour_K * P.grid_f, -1);
+    // (a second colouring's tables at schedule index kLevel2 + l)
+    const bool any2 = [&] { for (int l = 0; l < nL; l++) if (v.layer[l].G2 > 0) return true; return false; }();
+    const int n_tab = any2 ? kLevel2 + nL : nL;
+    std::vector<int> tab((size_t)n_tab * P.colour_K * P.grid_f, -1);
     int64_t nq_max = 1;
     double expect_region = 0.0;
-    for (int l = 0; l < nL; l++) {
-        const int G = v.layer[l].G, K = P.colour_K, Gf = P.grid_f;
+    for (int i = 0; i < n_tab; i++) {
+        const int l = i;
+        if (i >= nL && i < kLevel2) continue;
+        const int G = i < kLevel2 ? v.layer[l].G : v.layer[l - kLevel2].G2, K = P.colour_K, Gf = P.grid_f;
         if (G == 0) continue;
         nq_max = std::max<int64_t>(nq_max, (int64_t)(G / K) * (G / K) * (G / K));
-        if (expect_region == 0.0) expect_region = (double)N * std::pow((double)K / G, 3.0);
+        if (expect_region == 0.0 && i < kLevel2) expect_region = (double)N * std::pow((double)K / G, 3.0);
         for (int c = 0; c < G; c++) {
             const int64_t lo = ceildiv((2 * (int64_t)c - (K - 1)) * Gf, 2 * (int64_t)G);
             const int64_t hi = floordiv((2 * (int64_t)c + 2 + (K - 1)) * Gf, 2 * (int64_t)G) - 1;
@@ -555,6 +571,11 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
             const double region = G > 0 ? (double)N * std::pow((double)P.colour_K / G, 3.0) : 0.0;
             const int cmax = staged_cap_max(P.n_cap);
             g.cap_l[l] = (G > 0 && Q * Q * Q <= n_sm && region > 0.8 * v.stage_cap && region <= 0.8 * cmax) ? cmax : 0;
+            const int G2 = v.layer[l].G2, Q2 = G2 / P.colour_K, l2 = kLevel2 + l;
+            g.Mmax[l2] = h->Mmax[l];
+            g.keys[l2] = std::max(G2 * G2 * G2, 1);
+            g.nq[l2] = std::max(Q2 * Q2 * Q2, 1);
+            g.coloured[l2] = G2 > 0;
         }
     }
     cudaMemsetAsync(v.step, 0, 2 * sizeof(uint64_t), s);
@@ -637,10 +658,13 @@ int64_t wmcd::enqueue_sweep(const SimView* d, const GroupDims& g, const int64_t*
         if (hc && hc[l] <= 0) continue;
         { ProfScope ps(prof, 4, s); launch_slots(d, g, l, s); }
         launches += 1;
-        if (g.coloured[l]) {
-            { ProfScope ps(prof, 4, s); launch_bucket(d, g, l, s); }
-            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launches += launch_colour_staged(d, g, l, c, s, fj); }
-            { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, l, s); }
+        // a coloured layer's phases, then those of its second colouring (schedule index
+        // kLevel2 + l) over the slots the first deferred
+        for (int ls = l; ls < 2 * kMaxLayers; ls += kLevel2) {
+            if (!g.coloured[ls]) continue;
+            { ProfScope ps(prof, 4, s); launch_bucket(d, g, ls, s); }
+            for (int c = 0; c < g.maxK3; c++) { ProfScope ps(prof, 0, s); launches += launch_colour_staged(d, g, ls, c, s, fj); }
+            { ProfScope ps(prof, 4, s); launch_defer_compact(d, g, ls, s); }
             launches += 5 + 1;
         }
         { ProfScope ps(prof, 1, s); launches += launch_serial(d, g, l, s, fj); }
@@ -818,7 +842,10 @@ static const uint64_t kStateMagic = 0x574D434453543031ull;   // "WMCDST01"
 
 static int64_t carry_count(const Handle* h) {
     int64_t c = 0;
-    for (int l = 0; l < h->nL; l++) c += (int64_t)h->v.layer[l].G * h->v.layer[l].G * h->v.layer[l].G;
+    for (int l = 0; l < h->nL; l++) {
+        const LayerDev& Ly = h->v.layer[l];
+        c += (int64_t)Ly.G * Ly.G * Ly.G + (int64_t)Ly.G2 * Ly.G2 * Ly.G2;
+    }
     return c;
 }
 static int64_t state_bytes(const Handle* h) {

@@ -133,17 +133,21 @@ static GroupDims group_bounds(const std::vector<Member>& ms, int block_warps, in
         g.pw = g.pw || o.pw;
         g.prec_mask |= o.prec_mask;
         for (int l = 0; l < o.maxL; l++) {
-            g.Mmax[l] = std::max(g.Mmax[l], o.Mmax[l]);
-            g.keys[l] = std::max(g.keys[l], o.keys[l]);
-            g.nq[l] = std::max(g.nq[l], o.nq[l]);
-            g.coloured[l] = g.coloured[l] || o.coloured[l];
             g.bigM[l] = std::max(g.bigM[l], o.bigM[l]);
-            g.cap_l[l] = std::max(g.cap_l[l], o.cap_l[l]);
+            for (int ls = l; ls < 2 * kMaxLayers; ls += kLevel2) {   // the layer and its second colouring
+                g.Mmax[ls] = std::max(g.Mmax[ls], o.Mmax[ls]);
+                g.keys[ls] = std::max(g.keys[ls], o.keys[ls]);
+                g.nq[ls] = std::max(g.nq[ls], o.nq[ls]);
+                g.coloured[ls] = g.coloured[ls] || o.coloured[ls];
+                g.cap_l[ls] = std::max(g.cap_l[ls], o.cap_l[ls]);
+            }
         }
     }
     for (int l = 0; l < g.maxL; l++) {
-        g.keys[l] = std::max(g.keys[l], 1);
-        g.nq[l] = std::max(g.nq[l], 1);
+        for (int ls = l; ls < 2 * kMaxLayers; ls += kLevel2) {
+            g.keys[ls] = std::max(g.keys[ls], 1);
+            g.nq[ls] = std::max(g.nq[ls], 1);
+        }
     }
     return g;
 }

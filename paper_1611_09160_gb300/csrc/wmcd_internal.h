@@ -69,7 +69,16 @@ struct LayerDev {
     int G;                       // coarse cells per axis, 0 = serial layer
     int carry_off;               // offset of this layer's per-cell carries
     int64_t tr_off;              // offset of this layer's trace
+    // second colouring of the slots the layer defers: G2 = K floor(G / 2K) cells per axis
+    // (0 = none), their carries at carry_off2
+    int G2, carry_off2;
+    double invG2;
 };
+// The schedule index of a layer's second colouring: its phases run kernels written for a layer
+// with the index kMaxLayers + l (grid G2, carries at carry_off2, supports up to kNCapMax beads;
+// random draws, counters and trace those of layer l).
+constexpr int kLevel2 = kMaxLayers;
+WMCD_HD int layer_real(int l) { return l >= kLevel2 ? l - kLevel2 : l; }
 
 // The serial move of a large-scale layer that runs on the whole GPU, one kernel per step.
 struct BigMove {
@@ -217,10 +226,11 @@ struct GroupDims {
     int S = 1;
     int64_t maxN = 1, maxCells = 1;
     int maxL = 0, maxK3 = 1, maxMF = 0, stage_cap = 256, pw_blocks = 1;
-    int cap_l[kMaxLayers] = {0};  // staging capacity of a coloured layer when above stage_cap
+    // per schedule index: layer l, and kLevel2 + l for layer l's second colouring
+    int cap_l[2 * kMaxLayers] = {0};  // staging capacity of a coloured layer when above stage_cap
     int ncap = kNCap;            // largest n_cap of the group (sizes the staged support arrays)
-    int Mmax[kMaxLayers] = {0}, keys[kMaxLayers] = {0}, nq[kMaxLayers] = {0};
-    bool coloured[kMaxLayers] = {false};
+    int Mmax[2 * kMaxLayers] = {0}, keys[2 * kMaxLayers] = {0}, nq[2 * kMaxLayers] = {0};
+    bool coloured[2 * kMaxLayers] = {false};
     bool pw = false;
     int prec_mask = 3;           // bit 0: some simulation runs in binary64, bit 1: some in mixed precision
     int block_warps = kStageWarps;  // warps (queues) per block of the staged concurrent kernel, 1..4

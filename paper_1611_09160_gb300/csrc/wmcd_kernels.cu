@@ -299,17 +299,38 @@ void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
     k_slots<<<dim3((g.Mmax[l] + 255) / 256, g.S), 256, 0, s>>>(d, l);
 }
 
+// The layer record of schedule index l: layer l itself, or (l >= kLevel2) the second colouring
+// of layer l - kLevel2, with its grid and carries in place of the layer's own.
+__device__ __forceinline__ LayerDev sched_layer(const SimView& v, int l) {
+    if (l < kLevel2) return v.layer[l];
+    LayerDev y = v.layer[l - kLevel2];
+    y.G = y.G2;
+    y.invG = y.invG2;
+    y.carry_off = y.carry_off2;
+    return y;
+}
+__device__ __forceinline__ bool sched_on(const SimView& v, int l) {
+    return layer_real(l) < v.nL && (l < kLevel2 ? v.layer[l].G : v.layer[l - kLevel2].G2) > 0;
+}
+// slots a schedule index buckets: the layer's slots, or the ones its first colouring deferred
+__device__ __forceinline__ int sched_count(const SimView& v, int l) { return l < kLevel2 ? v.counts[l] : *v.serial_count; }
+// largest support a concurrent move of the index takes
+__device__ __forceinline__ int sched_ncap(const SimView& v, int l) { return l < kLevel2 ? v.n_cap : kNCapMax; }
+
+// The slots of schedule index l by coarse cell (of the picked bead now, or of the centre):
+// entry t is slot t of the layer, or for a second colouring the t-th slot its first deferred.
 __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || (int)(blockIdx.x * blockDim.x) >= gv.counts[l])
+    SIM_EXIT_IF(!sched_on(gv, l) || (int)(blockIdx.x * blockDim.x) >= sched_count(gv, l))
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0) return;
-    const int M = v.counts[l];
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
-    const LayerDev& Ly = v.layer[l];
+    if (!sched_on(v, l)) return;
+    const int M = sched_count(v, l);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    const int j = l < kLevel2 ? t : v.serial_list[t];
+    const LayerDev Ly = sched_layer(v, l);
     const int G = Ly.G, K = v.K, Q = G / K;
     double xs[3];
-    if (v.centring == 1) uniform_centre(v, l, v.step[0], (uint32_t)j, xs);      // bucket by the centre
+    if (v.centring == 1) uniform_centre(v, layer_real(l), v.step[0], (uint32_t)j, xs);      // bucket by the centre
     else {
         const Bead b = v.bead[v.slot_bead[j]];
         xs[0] = b.x; xs[1] = b.y; xs[2] = b.z;
@@ -325,16 +346,16 @@ __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
     int colour = (c[0] % K) + K * ((c[1] % K) + K * (c[2] % K));
     int q = (c[0] / K) + Q * ((c[1] / K) + Q * (c[2] / K));
     int key = colour * Q * Q * Q + q;
-    v.slot_key[j] = key;
+    v.slot_key[t] = key;
     atomicAdd(&v.q_count[key], 1);
 }
 // exclusive scan of n ints by one block per simulation: mode 0 = bucket counts of layer l
 // (G^3 keys), mode 1 = region counts of layer l (Q^3 queues)
 __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
+    SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0) return;
-    const int G = v.layer[l].G, Q = G / v.K;
+    if (!sched_on(v, l)) return;
+    const int G = sched_layer(v, l).G, Q = G / v.K;
     const int n = mode == 0 ? G * G * G : Q * Q * Q;
     const int* in = mode == 0 ? v.q_count : v.rcount;
     int* out = mode == 0 ? v.q_start : v.rstart;
@@ -362,36 +383,37 @@ __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
 // zero the per-phase counters: mode 0 = bucket counts, fills and deferral flags of layer l,
 // mode 1 = region counts and fills
 __global__ void k_zero(const SimView* __restrict__ vs, int mode, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
+    SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0) return;
-    const int G = v.layer[l].G, Q = G / v.K;
+    if (!sched_on(v, l)) return;
+    const int G = sched_layer(v, l).G, Q = G / v.K;
     const int n = mode == 0 ? G * G * G : Q * Q * Q;
     int* a = mode == 0 ? v.q_count : v.rcount;
     int* b = mode == 0 ? v.q_fill : v.rfill;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) { a[i] = 0; b[i] = 0; }
     if (mode == 0) {
-        const int M = v.layer[l].Mmax;
+        const int M = v.layer[layer_real(l)].Mmax;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) v.defer[i] = 0;
     }
 }
 __global__ void k_bucket_scatter(const SimView* __restrict__ vs, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || (int)(blockIdx.x * blockDim.x) >= gv.counts[l])
+    SIM_EXIT_IF(!sched_on(gv, l) || (int)(blockIdx.x * blockDim.x) >= sched_count(gv, l))
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0) return;
-    const int M = v.counts[l];
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
-    int key = v.slot_key[j];
+    if (!sched_on(v, l)) return;
+    const int M = sched_count(v, l);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    int key = v.slot_key[t];
     int pos = v.q_start[key] + atomicAdd(&v.q_fill[key], 1);
-    v.q_slots[pos] = j;
+    v.q_slots[pos] = t;
 }
-// slots of one queue in ascending slot id (the order of the sequential schedule)
+// slots of one queue in ascending slot id (the order of the sequential schedule); a second
+// colouring sorts its entries in first-schedule order and then names their slots
 __global__ void k_bucket_sort(const SimView* __restrict__ vs, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
+    SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0) return;
-    const int nkeys = v.layer[l].G * v.layer[l].G * v.layer[l].G;
+    if (!sched_on(v, l)) return;
+    const int G = sched_layer(v, l).G, nkeys = G * G * G;
     int key = blockIdx.x * blockDim.x + threadIdx.x;
     if (key >= nkeys) return;
     int s = v.q_start[key], n = v.q_count[key];
@@ -401,6 +423,8 @@ __global__ void k_bucket_sort(const SimView* __restrict__ vs, int l) {
         while (b >= 0 && a[b] > x) { a[b + 1] = a[b]; b--; }
         a[b + 1] = x;
     }
+    if (l >= kLevel2)
+        for (int i = 0; i < n; i++) a[i] = v.serial_list[a[i]];
 }
 void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
     const int keys = g.keys[l], M = g.Mmax[l];
@@ -413,10 +437,12 @@ void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) 
 
 // deferred slots in schedule order -> serial list
 __global__ void k_defer_compact(const SimView* __restrict__ vs, int l) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0)
+    SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0) return;
-    const int M = v.counts[l];
+    if (!sched_on(v, l)) return;
+    // (a second colouring's entries are the first one's deferred slots: read before the barrier
+    // below, ahead of the new count written at the end)
+    const int M = sched_count(v, l);
     // the deferred slots in schedule order: per chunk of 1024 a vote per warp, an exclusive prefix
     // of the 32 warp counts, and each deferred slot's place from the bits below it in its warp;
     // chunks without a deferred slot (nearly all) cost one block vote
@@ -746,10 +772,11 @@ __device__ void energy(const SimView& v, WarpSmem& sm, int n, int lane, int ncol
 }
 
 template <int PREC>
-__device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i, double lam, uint64_t sweep,
+__device__ int warp_attempt(const SimView& v, WarpSmem& sm, int ls, int j, int i, double lam, uint64_t sweep,
                             const int64_t rlo[3], const int64_t rhi[3], int lane, int* n_out, int* pe_out,
                             int* recheck_out, double* du_out) {
     const unsigned FULL = 0xffffffffu;
+    const int l = layer_real(ls), ncap = sched_ncap(v, ls);   // draws are the layer's own
     const double L = v.L, hL = v.halfL;
     const float hLf = (float)hL;
     *du_out = 0.0;
@@ -836,7 +863,7 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
                 }
                 if (!__any_sync(FULL, ptr >= 0)) break;
                 step(ptr);
-                if (n > v.n_cap) { *n_out = n; return DEFER; }
+                if (n > ncap) { *n_out = n; return DEFER; }
                 if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
             }
         }
@@ -851,14 +878,14 @@ __device__ int warp_attempt(const SimView& v, WarpSmem& sm, int l, int j, int i,
                 int ptr = col ? v.head[colbase + Gf * Gf * wrapc(c0[2] + kz, Gf)] : -1;
                 while (__any_sync(FULL, ptr >= 0)) {
                     step(ptr);
-                    if (n > v.n_cap) { *n_out = n; return DEFER; }
+                    if (n > ncap) { *n_out = n; return DEFER; }
                     if (++guard > kMaxWalk) { if (lane == 0) set_err(v, E_WALK); return DEFER; }
                 }
             }
         }
     }
     *n_out = n;
-    if (n > v.n_cap) return DEFER;
+    if (n > ncap) return DEFER;
     __syncwarp();
     if (n == 0) {                        // no bead moves: dU = 0 against the threshold
         const u4 w0 = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
@@ -1032,6 +1059,8 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     const double L = v.L, hL = v.halfL;
     const Pot& P = v.pot;
     const int count = use_list ? *v.serial_count : M;
+    // trace flags of a serial move: 4 deferred by the colouring, 8 by its second colouring too
+    const int dflag = use_list ? (v.layer[l].G2 > 0 ? 12 : 4) : 0;
     if (tid == 0) sh_carry = v.carry_serial[l];
     __syncthreads();
     long long att = 0, acc_n = 0, bu = 0, pe = 0, rechecks = 0, moved_n = 0;
@@ -1174,7 +1203,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                 const bool acc0 = 0.0 <= v.slot_thr[j];
                 att++;
                 if (acc0) acc_n++;
-                v.tr_out[Ly.tr_off + j] = (uint8_t)((acc0 ? 1 : 2) | (use_list ? 4 : 0));
+                v.tr_out[Ly.tr_off + j] = (uint8_t)((acc0 ? 1 : 2) | dflag);
                 v.tr_n[Ly.tr_off + j] = 0;
                 v.tr_du[Ly.tr_off + j] = 0.0;
                 sh_carry = acc0 ? 0.0 : lam;
@@ -1522,7 +1551,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             att++;
             bu += n;
             if (acc) { acc_n++; moved_n += n; }
-            v.tr_out[Ly.tr_off + j] = (uint8_t)((acc ? 1 : 2) | (use_list ? 4 : 0));
+            v.tr_out[Ly.tr_off + j] = (uint8_t)((acc ? 1 : 2) | dflag);
             v.tr_n[Ly.tr_off + j] = n;
             sh_carry = acc ? 0.0 : lam;
         }
@@ -2627,10 +2656,10 @@ namespace wmcd {
 // Beads are assigned to regions by a counting sort over all beads before each colour phase.
 // ======================================================================================
 __global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || colour >= gv.K * gv.K * gv.K)
+    SIM_EXIT_IF(!sched_on(gv, l) || colour >= gv.K * gv.K * gv.K)
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0 || colour >= v.K * v.K * v.K) return;
-    const int K = v.K, Gf = v.Gf, Q = v.layer[l].G / K;
+    if (!sched_on(v, l) || colour >= v.K * v.K * v.K) return;
+    const int K = v.K, Gf = v.Gf, Q = sched_layer(v, l).G / K;
     const int ox = colour % K, oy = (colour / K) % K, oz = colour / (K * K);
     const int* tab = v.axis_tab + (size_t)l * K * Gf;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
@@ -2644,9 +2673,9 @@ __global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour
     }
 }
 __global__ void k_region_scatter(const SimView* __restrict__ vs, int l, int colour) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || colour >= gv.K * gv.K * gv.K)
+    SIM_EXIT_IF(!sched_on(gv, l) || colour >= gv.K * gv.K * gv.K)
     SIM_PROLOGUE
-    if (l >= v.nL || v.layer[l].G == 0 || colour >= v.K * v.K * v.K) return;
+    if (!sched_on(v, l) || colour >= v.K * v.K * v.K) return;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
         const int key = v.rkey[m];
         if (key >= 0) v.rlist[v.rstart[key] + atomicAdd(&v.rfill[key], 1)] = (int)m;
@@ -3085,7 +3114,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
         }
         // in place only when the whole list fits (otherwise the move is deferred, or the
         // candidates are taken from all staged beads)
-        if (n <= v.n_cap)
+        if (n <= sched_ncap(v, l))
             for (int k = lane; k < nw; k += 32) S.mem[om + k] = X->memw[role][k];
         if (nc <= kCandCap)
             for (int k = lane; k < ncw; k += 32) S.cand[oc + k] = X->candw[role][k];
@@ -3093,7 +3122,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
     }
     __syncwarp();                                 // support and candidate lists are read by every lane
     *n_out = n;
-    if (n > v.n_cap) return DEFER;
+    if (n > sched_ncap(v, l)) return DEFER;
     if (n == 0) return 0.0 <= S.cthr[c] ? ACCEPT : REJECT;   // no bead moves: dU = 0 against the threshold
     const bool all_cand = nc > kCandCap;
     // displacement (Sec. V.A) with A_w = A0 lam / sqrt(n) (Eq. 29)
@@ -3243,7 +3272,7 @@ __device__ int stage_attempt(const SimView& v, const Stage& S, const Stage32& C,
 // count lies in [ns_lo, ns_hi] (read from global memory before the block copies anything).
 __device__ __forceinline__ bool staged_block_has_work(const SimView& g, int l, int colour, int qpb, int ns_lo,
                                                       int ns_hi) {
-    const int Q = g.layer[l].G / g.K, nq = Q * Q * Q;
+    const int Q = sched_layer(g, l).G / g.K, nq = Q * Q * Q;
     for (int w = 0; w < qpb; w++) {
         const int q = (int)blockIdx.x * qpb + w;
         if (q >= nq) break;
@@ -3264,12 +3293,12 @@ template <int PREC>
 __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
                                                                         int cap, int qpb, int ncap, int stride,
                                                                         int ns_lo, int ns_hi) {
-    SIM_EXIT_IF(l >= gv.nL || gv.layer[l].G == 0 || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
-                (int)(blockIdx.x * qpb) >= (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) * (gv.layer[l].G / gv.K) ||
+    SIM_EXIT_IF(!sched_on(gv, l) || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
+                (int)(blockIdx.x * qpb) >= (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) ||
                 !staged_block_has_work(gv, l, colour, qpb, ns_lo, ns_hi))
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
-    if (l >= v.nL || v.layer[l].G == 0 || v.precision != PREC || colour >= v.K * v.K * v.K) return;
+    if (!sched_on(v, l) || v.precision != PREC || colour >= v.K * v.K * v.K) return;
     // sqrt(n) for the amplitude A_w = A0 lam / sqrt(n) (Eq. 29), once per block
     __shared__ double s_sqrt[kNCap + 1];
     __shared__ CoopSh s_coop;
@@ -3279,7 +3308,10 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     const int H = (int)(blockDim.x >> 5) / qpb;     // warps per queue: 1, or all of the block
     const int wib = (int)(threadIdx.x >> 5) / H, role = (int)(threadIdx.x >> 5) % H, lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    const LayerDev& Ly = v.layer[l];
+    const LayerDev Ly = sched_layer(v, l);
+    // random draws, counters and trace are the layer's own; a second colouring's moves carry flag 4
+    const int lr = layer_real(l);
+    const uint8_t tflag = l >= kLevel2 ? 4 : 0;
     const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
     const int q = blockIdx.x * qpb + wib;
     if (q >= nq) return;                          // uniform over the warps of a queue
@@ -3317,7 +3349,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
             att++; bu += n;
             if (r == ACCEPT) { acc++; moved += n; }
             if (lane == 0) {
-                v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
+                v.tr_out[Ly.tr_off + j] = (uint8_t)((r == ACCEPT ? 1 : 2) | tflag);
                 v.tr_n[Ly.tr_off + j] = n;
                 v.tr_du[Ly.tr_off + j] = du;
             }
@@ -3367,19 +3399,19 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                 S.clam[lane] = v.slot_lam[j];
                 double V[3] = {0.0, 0.0, 0.0}, pp[3] = {0.0, 0.0, 1.0};
                 for (uint32_t a = 0; a < 64; a++) {
-                    const u4 w = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
+                    const u4 w = draw(v.k0, v.k1, K_VB, lr, sweep, (uint32_t)j, a);
                     const double x = sym(w.x), y = sym(w.y), z = sym(w.z);
                     if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
                 }
                 for (uint32_t a = 0; a < 64; a++) {
-                    const u4 w = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
+                    const u4 w = draw(v.k0, v.k1, K_VP, lr, sweep, (uint32_t)j, a);
                     const double x = sym(w.x), y = sym(w.y), z = sym(w.z), qq = norm2(x, y, z);
                     if (qq <= 1.0 && qq > 0.0) { pp[0] = x; pp[1] = y; pp[2] = z; break; }
                 }
                 const double r = sqr_t(norm2(pp[0], pp[1], pp[2]));
-                if (v.centring == 1) uniform_centre(v, l, sweep, (uint32_t)j, V);   // cV holds the centre itself
+                if (v.centring == 1) uniform_centre(v, lr, sweep, (uint32_t)j, V);   // cV holds the centre itself
                 for (int a = 0; a < 3; a++) { S.cV[3 * lane + a] = V[a]; S.cp[3 * lane + a] = dvd(pp[a], r); }
-                const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+                const u4 w = draw(v.k0, v.k1, K_ACC, lr, sweep, (uint32_t)j, 0);
                 S.cthr[lane] = accept_threshold(v, w);
                 S.cthrf[lane] = (float)S.cthr[lane];
                 // what the move needs from its own scale, ahead of the sequential loop
@@ -3422,7 +3454,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                 att++; bu += n;
                 if (r == ACCEPT) { acc++; moved += n; }
                 if (role == 0 && lane == 0) {
-                    v.tr_out[Ly.tr_off + j] = (uint8_t)(r == ACCEPT ? 1 : 2);
+                    v.tr_out[Ly.tr_off + j] = (uint8_t)((r == ACCEPT ? 1 : 2) | tflag);
                     v.tr_n[Ly.tr_off + j] = n;
                     v.tr_du[Ly.tr_off + j] = du;
                 }
@@ -3465,9 +3497,9 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     }
     if (lane == 0) {
         v.carry_q[Ly.carry_off + cell] = carry;
-        atomicAdd(&v.ctr[C_ATT + l], (unsigned long long)att);
-        atomicAdd(&v.ctr[C_ACC + l], (unsigned long long)acc);
-        atomicAdd(&v.ctr[C_DEF + l], (unsigned long long)def);
+        atomicAdd(&v.ctr[C_ATT + lr], (unsigned long long)att);
+        atomicAdd(&v.ctr[C_ACC + lr], (unsigned long long)acc);
+        if (l < kLevel2) atomicAdd(&v.ctr[C_DEF + lr], (unsigned long long)def);   // first deferrals only
         atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
         atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
         atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
@@ -3487,9 +3519,11 @@ static int light_ncap(int ncap) { return ncap < kLightCap ? ncap : kLightCap; }
 static size_t light_smem_bytes(int ncap) {
     return (size_t)kMaxStageWarps * warp_stride_staged(kLightCap, light_ncap(ncap));
 }
+// largest support of schedule index l's concurrent moves over the group
+static int sched_ncap_g(const GroupDims& g, int l) { return l >= kLevel2 ? kNCapMax : g.ncap; }
 static bool split_layer(const GroupDims& g, int l, int cap) {
     return g.cap_l[l] == 0 && cap > kLightCap &&
-           light_smem_bytes(g.ncap) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
+           light_smem_bytes(sched_ncap_g(g, l)) + sizeof(SimView) + sizeof(CoopSh) + 1024 <= 227u * 1024u;
 }
 static bool staged_fits(int cap, int queues, int ncap) {
     // dynamic shared memory + the static view copy, sqrt table and cooperative scratch within the
@@ -3504,14 +3538,14 @@ int staged_cap_max(int ncap) {
 // staging capacity of layer l's launches (the largest over the group, within one block's shared
 // memory: a region above it takes the global-memory path)
 static int layer_cap(const GroupDims& g, int l) {
-    return std::min(std::max(g.stage_cap, g.cap_l[l]), staged_cap_max(g.ncap));
+    return std::min(std::max(g.stage_cap, g.cap_l[l]), staged_cap_max(sched_ncap_g(g, l)));
 }
 // queues per block actually used: the requested count, lowered until the block's shared memory
 // fits; a block of one queue with a region larger than 1,024 beads gets kMaxStageWarps warps,
 // which share the staging
-static void staged_shape(const GroupDims& g, int cap, int* qpb, int* warps) {
+static void staged_shape(const GroupDims& g, int cap, int ncap, int* qpb, int* warps) {
     int nw = std::max(1, std::min(g.block_warps, kMaxStageWarps));
-    while (nw > 1 && !staged_fits(cap, nw, g.ncap)) nw--;
+    while (nw > 1 && !staged_fits(cap, nw, ncap)) nw--;
     *qpb = nw;
     *warps = (nw == 1 && cap > 1024) ? kMaxStageWarps : nw;
 }
@@ -3540,15 +3574,16 @@ void prepare_staged(const GroupDims& g) {
         }
     }
     int smem = 0;
-    for (int l = 0; l < g.maxL; l++) {
+    for (int i = 0; i < 2 * g.maxL; i++) {
+        const int l = i < g.maxL ? i : kLevel2 + i - g.maxL;
         if (!g.coloured[l]) continue;
-        const int cap = layer_cap(g, l);
+        const int cap = layer_cap(g, l), ncap = sched_ncap_g(g, l);
         int qpb = 1, warps = 1;
-        staged_shape(g, cap, &qpb, &warps);
-        smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, g.ncap));
+        staged_shape(g, cap, ncap, &qpb, &warps);
+        smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, ncap));
         if (split_layer(g, l, cap)) {
-            smem = std::max(smem, (int)light_smem_bytes(g.ncap));
-            smem = std::max(smem, (int)staged_smem_bytes(staged_cap_max(g.ncap), 1, g.ncap));
+            smem = std::max(smem, (int)light_smem_bytes(ncap));
+            smem = std::max(smem, (int)staged_smem_bytes(staged_cap_max(ncap), 1, ncap));
         }
     }
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
@@ -3568,13 +3603,13 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
     k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
     k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l);
     k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
-    const int cap = layer_cap(g, l);
+    const int cap = layer_cap(g, l), ncap = sched_ncap_g(g, l);
     int qpb = 1, warps = 1;
-    staged_shape(g, cap, &qpb, &warps);
-    const size_t smem = staged_smem_bytes(cap, qpb, g.ncap);
+    staged_shape(g, cap, ncap, &qpb, &warps);
+    const size_t smem = staged_smem_bytes(cap, qpb, ncap);
     const dim3 grid((nq + qpb - 1) / qpb, g.S);
     prepare_staged(g);
-    const int stride = (int)warp_stride(cap, g.ncap);
+    const int stride = (int)warp_stride(cap, ncap);
     const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
     if (split_layer(g, l, cap) && fj && fj->side[0]) {
         // Ordinary regions (at most kLightCap beads) on the stream, one warp per queue and small
@@ -3583,19 +3618,19 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         // for the largest region. The two launches take disjoint queues of one colour.
         const int qL = kMaxStageWarps;
         const dim3 gridL((nq + qL - 1) / qL, g.S);
-        const size_t smemL = light_smem_bytes(g.ncap);
-        const int strideL = (int)warp_stride_staged(kLightCap, light_ncap(g.ncap));
-        const int capH = staged_cap_max(g.ncap);
-        const size_t smemH = staged_smem_bytes(capH, 1, g.ncap);
-        const int strideH = (int)warp_stride(capH, g.ncap);
+        const size_t smemL = light_smem_bytes(ncap);
+        const int strideL = (int)warp_stride_staged(kLightCap, light_ncap(ncap));
+        const int capH = staged_cap_max(ncap);
+        const size_t smemH = staged_smem_bytes(capH, 1, ncap);
+        const int strideH = (int)warp_stride(capH, ncap);
         const dim3 gridH(nq, g.S);
         cudaEventRecord(fj->fork, s);
         cudaStreamWaitEvent(fj->side[0], fj->fork, 0);
         if (g.prec_mask & 1)
-            k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, g.ncap, strideH, kLightCap + 1, 1 << 30);
+            k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30);
         if (g.prec_mask & 2)
-            k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, g.ncap, strideH, kLightCap + 1, 1 << 30);
-        const int ncL = light_ncap(g.ncap);
+            k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30);
+        const int ncL = light_ncap(ncap);
         if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap);
         if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap);
         cudaEventRecord(fj->join[0], fj->side[0]);
@@ -3603,8 +3638,8 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         return 4 + 2 * np;
     }
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, 0, 1 << 30);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, g.ncap, stride, 0, 1 << 30);
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30);
     return 4 + np;
 
 }

@@ -39,8 +39,8 @@ def interaction_reach(wca_sigma: float, wca_eps: float) -> float:
 def choose(box_L: float, lambda_min: float, lambda_max: float, A0: float, wca_sigma: float, wca_eps: float,
            colour_K: int = 2, slack: float = 1.0, max_fine: int = 512, n_cap: int = 64,
            min_queues_per_axis: int = 2, cell_scale: float = 1.0, serial_only: bool = False,
-           n_beads: int | None = None) -> dict:
-    """Return the schedule fields: colour_K, grid_f, n_cap, grid_layer (list of 16).
+           n_beads: int | None = None, level2: int = 0) -> dict:
+    """Return the schedule fields: colour_K, grid_f, n_cap, grid_layer (list of 16), level2.
 
     cell_scale widens the fine cells beyond the interaction reach (fewer, fuller cells to walk
     in dilute systems); serial_only runs every layer in the serial phase. With n_beads given,
@@ -68,4 +68,5 @@ def choose(box_L: float, lambda_min: float, lambda_max: float, A0: float, wca_si
         G = colour_K * int(math.floor(box_L / (colour_K * h_min)))
         if G >= min_queues_per_axis * colour_K and not serial_only:
             grid_layer[l] = G
-    return {"colour_K": colour_K, "grid_f": grid_f, "n_cap": n_cap, "grid_layer": grid_layer}
+    return {"colour_K": colour_K, "grid_f": grid_f, "n_cap": n_cap, "grid_layer": grid_layer,
+            "level2": int(level2)}

@@ -82,7 +82,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("sim_id", ctypes.c_uint64),
         ("colour_K", ctypes.c_int32), ("grid_f", ctypes.c_int32), ("n_cap", ctypes.c_int32),
         ("grid_layer", ctypes.c_int32 * MAX_LAYERS), ("big_support", ctypes.c_int32),
-        ("acceptance", ctypes.c_int32), ("centring", ctypes.c_int32),
+        ("acceptance", ctypes.c_int32), ("centring", ctypes.c_int32), ("level2", ctypes.c_int32),
     ]
 
 

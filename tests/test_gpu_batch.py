@@ -40,6 +40,10 @@ def mixed_systems():
     p["grid_layer"] = [0] * 16
     p["big_support"] = 4          # its largest scales run as whole-GPU moves
     out.append((p, s))
+    s = I.make_system([32] * 48, 0, I.box_for_volume_fraction(1536, 0.08), seed=12)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=17, precision=wmcd.MIXED, n_cap=3, level2=1)
+    p["grid_layer"] = [8] + [0] * 15   # deferred slots get a second colouring on 4 cells per axis
+    out.append((p, s))
     return out
 
 
@@ -77,7 +81,7 @@ def test_batch_equals_each_simulation_alone():
 
 
 def test_batch_decisions_match_oracle_every_sweep():
-    pairs = [mixed_systems()[i] for i in (0, 2, 3)]
+    pairs = [mixed_systems()[i] for i in (0, 2, 3, 6)]
     b = wmcd.Batch(capacity=4, pool_bytes=pool_for(pairs))
     slots = [b.admit(p, s.pos, s.chain_len) for p, s in pairs]
     refs = [O.Oracle(p, s.pos, s.chain_len) for p, s in pairs]

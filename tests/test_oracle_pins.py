@@ -476,7 +476,7 @@ def test_coloured_schedule_keeps_free_diffusion_and_defers_correctly():
     # second-level colouring: regions on a grid of K floor(G / 2K) cells per axis are about twice
     # as wide, so some of the same deferred slots now fit; the rest run serially (flags 4 | 8);
     # every slot is still attempted once and the run equals the serial order's statistics
-    p3 = params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31, level2=1, **fine)
+    p3 = params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31, **dict(fine, level2=1))
     o3 = O.Oracle(p3, s.pos, s.chain_len)
     o3.sweep(1)
     st3 = o3.stats()
@@ -487,12 +487,16 @@ def test_coloured_schedule_keeps_free_diffusion_and_defers_correctly():
     assert 0 < lvl2.sum() < len(out3)
     assert np.all(n3[lvl2] <= 256)
     # level 2 never applies to a grid without two second-level cells per colour and axis
-    o4 = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31, level2=1,
-                         **dict(sch, grid_layer=[6] + [0] * 15)), s.pos, s.chain_len)
+    o4 = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31,
+                         **dict(sch, grid_layer=[6] + [0] * 15, level2=1)), s.pos, s.chain_len)
     o4.sweep(1)
     assert not np.any(o4.trace_layer(0)[0] & 8)
+    # nor to a layer whose bit the mask leaves out
+    o6 = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, seed=31, **dict(fine, level2=0xfffe)), s.pos, s.chain_len)
+    o6.sweep(1)
+    assert np.array_equal(o6.trace_layer(0)[0], out)
     # the schedule with the second level keeps Eq. 33
-    o5 = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, seed=37, level2=1, **fine), s.pos, s.chain_len)
+    o5 = O.Oracle(params(n_beads=N, box_L=L, lambda_max=L / 2, seed=37, **dict(fine, level2=1)), s.pos, s.chain_len)
     m5, se5 = _msd_per_move(o5, 20, 20)
     assert abs(m5 - want) < 4 * se5 + 1e-3 * want
 
