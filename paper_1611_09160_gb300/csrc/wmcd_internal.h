@@ -191,6 +191,7 @@ struct SimView {
     double* s_new;               // 3 per member: new wrapped position
     int* s_img;                  // per member: packed image change
     int* s_slot;                 // per bead: index in the support of the current serial move
+                                 // (between moves: ranks of the region scatter)
     int* s_changed;              // members whose fine cell changes
     int* s_box;                  // 6 per member: partner cell box (first cell, cells per axis)
     int* s_pre;                  // n + 1: prefix of the partner-box sizes

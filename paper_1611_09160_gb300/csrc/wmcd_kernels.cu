@@ -294,6 +294,29 @@ __global__ void k_slots(const SimView* __restrict__ vs, int l) {
     v.tr_out[Ly.tr_off + j] = 0;
     v.tr_n[Ly.tr_off + j] = 0;
     v.tr_du[Ly.tr_off + j] = 0.0;
+    // the rest of the slot's draws, whichever phase runs it: centre offset V in the unit ball
+    // (or the centre itself, uniform in the box), unit polarisation p by rejection (Appendix D),
+    // and the acceptance threshold (Eq. 20); one slot per thread, so full warps share the
+    // binary64 work
+    double V[3] = {0.0, 0.0, 0.0}, p[3] = {0.0, 0.0, 1.0};
+    for (uint32_t a = 0; a < 64; a++) {
+        const u4 wb = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
+        const double x = sym(wb.x), y = sym(wb.y), z = sym(wb.z);
+        if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+    }
+    for (uint32_t a = 0; a < 64; a++) {
+        const u4 wp = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
+        const double x = sym(wp.x), y = sym(wp.y), z = sym(wp.z), q = norm2(x, y, z);
+        if (q <= 1.0 && q > 0.0) { p[0] = x; p[1] = y; p[2] = z; break; }
+    }
+    const double r = sqr_t(norm2(p[0], p[1], p[2]));
+    if (v.centring == 1) uniform_centre(v, l, sweep, (uint32_t)j, V);   // slot_V holds the centre itself
+    for (int a = 0; a < 3; a++) {
+        v.slot_V[3 * j + a] = V[a];
+        v.slot_p[3 * j + a] = dvd(p[a], r);
+    }
+    const u4 wa = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
+    v.slot_thr[j] = accept_threshold(v, wa);
 }
 void launch_slots(const SimView* d, const GroupDims& g, int l, cudaStream_t s) {
     k_slots<<<dim3((g.Mmax[l] + 255) / 256, g.S), 256, 0, s>>>(d, l);
@@ -1007,36 +1030,6 @@ namespace wmcd {
 // the centre offset V and the polarisation by rejection from the unit ball (Appendix D), p
 // normalised, and the Metropolis threshold -kT ln(1 - u) (Eq. 20). They depend only on the
 // slot's counter, not on the state, so computing them early changes nothing.
-__global__ void k_serial_prep(const SimView* __restrict__ vs, int l) {
-    SIM_EXIT_IF(l >= gv.nL || (gv.layer[l].G == 0 && (int)(blockIdx.x * blockDim.x) >= gv.counts[l]))
-    SIM_PROLOGUE
-    if (l >= v.nL) return;
-    const bool use_list = v.layer[l].G > 0;
-    const int count = use_list ? *v.serial_count : v.counts[l];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const int j = use_list ? v.serial_list[t] : t;
-    const uint64_t sweep = v.step[0];
-    double V[3] = {0.0, 0.0, 0.0}, p[3] = {0.0, 0.0, 1.0};
-    for (uint32_t a = 0; a < 64; a++) {
-        const u4 w = draw(v.k0, v.k1, K_VB, l, sweep, (uint32_t)j, a);
-        const double x = sym(w.x), y = sym(w.y), z = sym(w.z);
-        if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
-    }
-    for (uint32_t a = 0; a < 64; a++) {
-        const u4 w = draw(v.k0, v.k1, K_VP, l, sweep, (uint32_t)j, a);
-        const double x = sym(w.x), y = sym(w.y), z = sym(w.z), q = norm2(x, y, z);
-        if (q <= 1.0 && q > 0.0) { p[0] = x; p[1] = y; p[2] = z; break; }
-    }
-    const double r = sqr_t(norm2(p[0], p[1], p[2]));
-    if (v.centring == 1) uniform_centre(v, l, sweep, (uint32_t)j, V);   // slot_V holds the centre itself
-    for (int a = 0; a < 3; a++) {
-        v.slot_V[3 * j + a] = V[a];
-        v.slot_p[3 * j + a] = dvd(p[a], r);
-    }
-    const u4 w = draw(v.k0, v.k1, K_ACC, l, sweep, (uint32_t)j, 0);
-    v.slot_thr[j] = accept_threshold(v, w);
-}
 
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs, int l) {
@@ -2040,9 +2033,8 @@ size_t smem_serial_bytes(int64_t n) { return (size_t)n * (3 * 8 + 3 * 8 + 6 * 4 
 
 int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, const ForkJoin* fj) {
     const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
-    int launched = 1 + (g.any_global_serial ? np : 0);
+    int launched = g.any_global_serial ? np : 0;
     prepare_staged(g);
-    k_serial_prep<<<dim3((g.Mmax[l] + 127) / 128, g.S), 128, 0, s>>>(d, l);
     // one launch per precision; each returns at once for simulations of the other precision
     const dim3 grid(1, g.S);
     if (g.smem_maxN > 0) {
@@ -2655,13 +2647,23 @@ namespace wmcd {
 // them into shared memory once, runs all its moves there and writes them back at the end.
 // Beads are assigned to regions by a counting sort over all beads before each colour phase.
 // ======================================================================================
+// With at most kRegionPriv queues per colour (coarse layers, whose regions hold thousands of
+// beads each) the counts are kept per block in shared memory and added to the global ones once
+// per block and queue: one global counter per queue would otherwise take an atomic per bead.
+constexpr int kRegionPriv = 8192;
 __global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour) {
     SIM_EXIT_IF(!sched_on(gv, l) || colour >= gv.K * gv.K * gv.K)
     SIM_PROLOGUE
     if (!sched_on(v, l) || colour >= v.K * v.K * v.K) return;
-    const int K = v.K, Gf = v.Gf, Q = sched_layer(v, l).G / K;
+    const int K = v.K, Gf = v.Gf, Q = sched_layer(v, l).G / K, nq = Q * Q * Q;
     const int ox = colour % K, oy = (colour / K) % K, oz = colour / (K * K);
     const int* tab = v.axis_tab + (size_t)l * K * Gf;
+    __shared__ int sh[kRegionPriv];
+    const bool priv = nq <= kRegionPriv;
+    if (priv) {
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
         const Bead b = v.bead[m];
         const int qx = tab[ox * Gf + fine_cell(b.x, v.invf, Gf)];
@@ -2669,16 +2671,45 @@ __global__ void k_region_count(const SimView* __restrict__ vs, int l, int colour
         const int qz = tab[oz * Gf + fine_cell(b.z, v.invf, Gf)];
         const int key = (qx < 0 || qy < 0 || qz < 0) ? -1 : qx + Q * (qy + Q * qz);
         v.rkey[m] = key;
-        if (key >= 0) atomicAdd(&v.rcount[key], 1);
+        if (key >= 0) atomicAdd(priv ? &sh[key] : &v.rcount[key], 1);
+    }
+    if (priv) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nq; i += blockDim.x)
+            if (sh[i]) atomicAdd(&v.rcount[i], sh[i]);
     }
 }
+// Bead ids grouped by queue (the order within a queue is immaterial: a staged region is
+// searched as a set). Per-block shared counts as above: each bead's rank within its block and
+// queue (kept in s_slot, free between moves), one reservation per block and queue, then the
+// placement.
 __global__ void k_region_scatter(const SimView* __restrict__ vs, int l, int colour) {
     SIM_EXIT_IF(!sched_on(gv, l) || colour >= gv.K * gv.K * gv.K)
     SIM_PROLOGUE
     if (!sched_on(v, l) || colour >= v.K * v.K * v.K) return;
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < v.N; m += (int64_t)gridDim.x * blockDim.x) {
+    const int Q = sched_layer(v, l).G / v.K, nq = Q * Q * Q;
+    const int64_t m0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ms = (int64_t)gridDim.x * blockDim.x;
+    if (nq > kRegionPriv) {
+        for (int64_t m = m0; m < v.N; m += ms) {
+            const int key = v.rkey[m];
+            if (key >= 0) v.rlist[v.rstart[key] + atomicAdd(&v.rfill[key], 1)] = (int)m;
+        }
+        return;
+    }
+    __shared__ int sh[kRegionPriv];
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t m = m0; m < v.N; m += ms) {
         const int key = v.rkey[m];
-        if (key >= 0) v.rlist[v.rstart[key] + atomicAdd(&v.rfill[key], 1)] = (int)m;
+        if (key >= 0) v.s_slot[m] = atomicAdd(&sh[key], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nq; i += blockDim.x)
+        if (sh[i]) sh[i] = v.rstart[i] + atomicAdd(&v.rfill[i], sh[i]);
+    __syncthreads();
+    for (int64_t m = m0; m < v.N; m += ms) {
+        const int key = v.rkey[m];
+        if (key >= 0) v.rlist[sh[key] + v.s_slot[m]] = (int)m;
     }
 }
 
@@ -3389,30 +3420,21 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
         if (H > 1) __syncthreads(); else __syncwarp();
         int tag = 0;
         for (int c0 = 0; c0 < cnt; c0 += kSlotChunk) {
-            // slot parameters of the chunk, one lane of warp 0 per slot: V, p by rejection
-            // (Appendix D) and the Metropolis threshold -kT ln(1 - u) (Eq. 20)
+            // slot parameters of the chunk, one lane of warp 0 per slot: V, p and the acceptance
+            // threshold as the slot kernel drew them (Appendix D, Eq. 20)
             const int t = c0 + lane;
             if (role == 0 && t < cnt) {
                 const int j = v.q_slots[start + t];
                 S.cj[lane] = j;
                 S.ci[lane] = v.slot_bead[j];
                 S.clam[lane] = v.slot_lam[j];
-                double V[3] = {0.0, 0.0, 0.0}, pp[3] = {0.0, 0.0, 1.0};
-                for (uint32_t a = 0; a < 64; a++) {
-                    const u4 w = draw(v.k0, v.k1, K_VB, lr, sweep, (uint32_t)j, a);
-                    const double x = sym(w.x), y = sym(w.y), z = sym(w.z);
-                    if (norm2(x, y, z) <= 1.0) { V[0] = x; V[1] = y; V[2] = z; break; }
+                double V[3];
+                for (int a = 0; a < 3; a++) {
+                    V[a] = v.slot_V[3 * j + a];             // with uniform centres: the centre itself
+                    S.cV[3 * lane + a] = V[a];
+                    S.cp[3 * lane + a] = v.slot_p[3 * j + a];
                 }
-                for (uint32_t a = 0; a < 64; a++) {
-                    const u4 w = draw(v.k0, v.k1, K_VP, lr, sweep, (uint32_t)j, a);
-                    const double x = sym(w.x), y = sym(w.y), z = sym(w.z), qq = norm2(x, y, z);
-                    if (qq <= 1.0 && qq > 0.0) { pp[0] = x; pp[1] = y; pp[2] = z; break; }
-                }
-                const double r = sqr_t(norm2(pp[0], pp[1], pp[2]));
-                if (v.centring == 1) uniform_centre(v, lr, sweep, (uint32_t)j, V);   // cV holds the centre itself
-                for (int a = 0; a < 3; a++) { S.cV[3 * lane + a] = V[a]; S.cp[3 * lane + a] = dvd(pp[a], r); }
-                const u4 w = draw(v.k0, v.k1, K_ACC, lr, sweep, (uint32_t)j, 0);
-                S.cthr[lane] = accept_threshold(v, w);
+                S.cthr[lane] = v.slot_thr[j];
                 S.cthrf[lane] = (float)S.cthr[lane];
                 // what the move needs from its own scale, ahead of the sequential loop
                 const double lam_s = S.clam[lane];
