@@ -75,7 +75,8 @@ def make_params(system, precision, seed, sim_id=0):
     return dict(p, precision=precision)
 
 
-SUSPENSION_CANDIDATES = ({"colour_K": 2, "max_fine": 768, "n_cap": 128}, {"colour_K": 2, "max_fine": 768},
+SUSPENSION_CANDIDATES = ({"colour_K": 2, "max_fine": 768, "n_cap": 128, "level2": 1},
+                         {"colour_K": 2, "max_fine": 768, "n_cap": 128}, {"colour_K": 2, "max_fine": 768},
                          {"colour_K": 2, "max_fine": 1024}, {"colour_K": 3, "max_fine": 768})
 
 

@@ -492,7 +492,8 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     }
     int* d_tab = nullptr;
     ok = ok && !dalloc(h, &v.rkey, N) && !dalloc(h, &v.rlist, N) && !dalloc(h, &v.rcount, nq_max) &&
-         !dalloc(h, &v.rstart, nq_max) && !dalloc(h, &v.rfill, nq_max) && !dalloc(h, &d_tab, tab.size());
+         !dalloc(h, &v.rstart, nq_max) && !dalloc(h, &v.rfill, nq_max) && !dalloc(h, &d_tab, tab.size()) &&
+         !dalloc(h, &v.hq_list, nq_max) && !dalloc(h, &v.hq_ctl, 2);
     if (!ok) return WMCD_ENOMEM;
     if (counting) return WMCD_OK;
     v.axis_tab = d_tab;

@@ -373,8 +373,10 @@ __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
     atomicAdd(&v.q_count[key], 1);
 }
 // exclusive scan of n ints by one block per simulation: mode 0 = bucket counts of layer l
-// (G^3 keys), mode 1 = region counts of layer l (Q^3 queues)
-__global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
+// (G^3 keys), mode 1 = region counts of layer l (Q^3 queues). With heavy_lo >= 0 (mode 1) it
+// also lists the queues of the colour phase that have slots and more than heavy_lo beads in
+// their region (in no particular order) and resets the list's work counter.
+__global__ void k_scan(const SimView* __restrict__ vs, int mode, int l, int colour, int heavy_lo) {
     SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
     if (!sched_on(v, l)) return;
@@ -401,6 +403,15 @@ __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l) {
         __syncthreads();
         if (threadIdx.x == 1023) carry += part[1023];
         __syncthreads();
+    }
+    if (mode == 1 && heavy_lo >= 0) {
+        __shared__ int hc;
+        if (threadIdx.x == 0) hc = 0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x)
+            if (in[q] > heavy_lo && v.q_count[colour * n + q] > 0) v.hq_list[atomicAdd(&hc, 1)] = q;
+        __syncthreads();
+        if (threadIdx.x == 0) { v.hq_ctl[0] = hc; v.hq_ctl[1] = 0; }
     }
 }
 // zero the per-phase counters: mode 0 = bucket counts, fills and deferral flags of layer l,
@@ -453,7 +464,7 @@ void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) 
     const int keys = g.keys[l], M = g.Mmax[l];
     k_zero<<<dim3(gx((std::max(keys, M) + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 0, l);
     k_bucket_count<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
-    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 0, l);
+    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 0, l, 0, -1);
     k_bucket_scatter<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
     k_bucket_sort<<<dim3((keys + 127) / 128, g.S), 128, 0, s>>>(d, l);
 }
@@ -3323,10 +3334,11 @@ __device__ __forceinline__ bool staged_block_has_work(const SimView& g, int l, i
 template <int PREC>
 __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
                                                                         int cap, int qpb, int ncap, int stride,
-                                                                        int ns_lo, int ns_hi) {
+                                                                        int ns_lo, int ns_hi, int list) {
     SIM_EXIT_IF(!sched_on(gv, l) || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
-                (int)(blockIdx.x * qpb) >= (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) ||
-                !staged_block_has_work(gv, l, colour, qpb, ns_lo, ns_hi))
+                (list ? (int)blockIdx.x >= gv.hq_ctl[0]
+                      : ((int)(blockIdx.x * qpb) >= (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) ||
+                         !staged_block_has_work(gv, l, colour, qpb, ns_lo, ns_hi))))
     SIM_PROLOGUE
     extern __shared__ __align__(16) char dsm[];
     if (!sched_on(v, l) || v.precision != PREC || colour >= v.K * v.K * v.K) return;
@@ -3344,193 +3356,209 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     const int lr = layer_real(l);
     const uint8_t tflag = l >= kLevel2 ? 4 : 0;
     const int G = Ly.G, K = v.K, Q = G / K, nq = Q * Q * Q;
-    const int q = blockIdx.x * qpb + wib;
-    if (q >= nq) return;                          // uniform over the warps of a queue
-    const int key = colour * nq + q;
-    const int start = v.q_start[key], cnt = v.q_count[key];
-    if (cnt == 0) return;
-    {
-        const int ns0 = v.rcount[q];
-        if (ns0 < ns_lo || ns0 > ns_hi) return;   // another launch of this phase runs the queue
-    }
-    char* base = dsm + (size_t)wib * (size_t)stride;
-    const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
-    int64_t rlo[3], rhi[3];
-    for (int a = 0; a < 3; a++) {
-        rlo[a] = ceildiv((2 * (int64_t)c[a] - (K - 1)) * v.Gf, 2 * (int64_t)G);
-        rhi[a] = floordiv((2 * (int64_t)c[a] + 2 + (K - 1)) * v.Gf, 2 * (int64_t)G) - 1;
-    }
-    const int cell = c[0] + G * (c[1] + G * c[2]);
-    double carry = v.carry_q[Ly.carry_off + cell];
-    int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
-    long long bu = 0, moved = 0;
-    const int rs = v.rstart[q], ns = v.rcount[q];
-    if (ns > cap) {
-        // region too full for shared memory: the global-memory path
-        if (role != 0) return;
-        WarpSmem& sm = *(WarpSmem*)base;
-        for (int t = 0; t < cnt; t++) {
-            const int j = v.q_slots[start + t];
-            const double lam = carry > 0.0 ? carry : v.slot_lam[j];
-            int n = 0;
-            double du = 0.0;
-            int r = warp_attempt<PREC>(v, sm, l, j, v.slot_bead[j], lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks, &du);
-            __syncwarp();
-            if (r == DEFER) { if (lane == 0) v.defer[start + t] = 1; def++; continue; }
-            att++; bu += n;
-            if (r == ACCEPT) { acc++; moved += n; }
-            if (lane == 0) {
-                v.tr_out[Ly.tr_off + j] = (uint8_t)((r == ACCEPT ? 1 : 2) | tflag);
-                v.tr_n[Ly.tr_off + j] = n;
-                v.tr_du[Ly.tr_off + j] = du;
-            }
-            carry = (r == ACCEPT) ? 0.0 : lam;
+    // one queue per warp (or per block), or (list) the block takes queues of the phase's list of
+    // dense regions one after another until the list is done; "continue" ends a queue
+    __shared__ int s_item;
+    for (int it = 0;; it++) {
+        int q;
+        if (list) {
+            if (threadIdx.x == 0) s_item = atomicAdd(&v.hq_ctl[1], 1);
+            __syncthreads();
+            const int i = s_item;
+            __syncthreads();                          // read by all before the next item is taken
+            if (i >= v.hq_ctl[0]) break;
+            q = v.hq_list[i];
+        } else {
+            if (it > 0) break;
+            q = blockIdx.x * qpb + wib;
         }
-    } else {
-        Stage S = stage_carve(base, cap, ncap);
-        Stage32 C32 = stage32(v);
-        C32.sqrt_n = s_sqrt;
-        for (int a = 0; a < 3; a++) C32.side[a] = (float)((double)(rhi[a] - rlo[a] + 1) * (v.L / v.Gf));
-        const int HT = 1 << S.hbits;
-        const int ql = role * 32 + lane, qstride = 32 * H;   // this thread among the queue's warps
-        for (int h = ql; h < HT; h += qstride) S.hkey[h] = -1;
-        if (H > 1) __syncthreads(); else __syncwarp();
-        const double hf = v.L / v.Gf;
-        const double org[3] = {(double)rlo[0] * hf, (double)rlo[1] * hf, (double)rlo[2] * hf};
-        const float sidef = (float)((double)(rhi[0] - rlo[0] + 1) * hf);
-        for (int t = ql; t < ns; t += qstride) {
-            const int m = v.rlist[rs + t];
-            const Bead bb = v.bead[m];
-            S.sx[t] = bb.x; S.sy[t] = bb.y; S.sz[t] = bb.z;
-            local_split(bb.x, org[0], v.L, S.hx[t], S.lx[t]);
-            local_split(bb.y, org[1], v.L, S.hy[t], S.ly[t]);
-            local_split(bb.z, org[2], v.L, S.hz[t], S.lz[t]);
-            S.sid[t] = m;
-            const int bflag = (v.bnext[m] ? 1 : 0) | (m > 0 && v.bnext[m - 1] ? 2 : 0);
-            S.sdim[t] = 128 | (128 << 8) | (128 << 16) | (bflag << 25);
-            S.stag[t] = 0;
-            const uint32_t mask = (uint32_t)HT - 1u;
-            uint32_t h = hslot(m, S.hbits);
-            for (int probe = 0; probe < HT; probe++) {
-                const int prev = atomicCAS(&S.hkey[h], -1, m);
-                if (prev == -1) { S.hval[h] = t; break; }
-                h = (h + 1u) & mask;
-            }
+        if (q >= nq) continue;                        // uniform over the warps of a queue
+        const int key = colour * nq + q;
+        const int start = v.q_start[key], cnt = v.q_count[key];
+        if (cnt == 0) continue;
+        {
+            const int ns0 = v.rcount[q];
+            if (ns0 < ns_lo || ns0 > ns_hi) continue; // another launch of this phase runs the queue
         }
-        if (H > 1) __syncthreads(); else __syncwarp();
-        int tag = 0;
-        for (int c0 = 0; c0 < cnt; c0 += kSlotChunk) {
-            // slot parameters of the chunk, one lane of warp 0 per slot: V, p and the acceptance
-            // threshold as the slot kernel drew them (Appendix D, Eq. 20)
-            const int t = c0 + lane;
-            if (role == 0 && t < cnt) {
+        char* base = dsm + (size_t)wib * (size_t)stride;
+        const int c[3] = {K * (q % Q) + colour % K, K * ((q / Q) % Q) + (colour / K) % K, K * (q / (Q * Q)) + colour / (K * K)};
+        int64_t rlo[3], rhi[3];
+        for (int a = 0; a < 3; a++) {
+            rlo[a] = ceildiv((2 * (int64_t)c[a] - (K - 1)) * v.Gf, 2 * (int64_t)G);
+            rhi[a] = floordiv((2 * (int64_t)c[a] + 2 + (K - 1)) * v.Gf, 2 * (int64_t)G) - 1;
+        }
+        const int cell = c[0] + G * (c[1] + G * c[2]);
+        double carry = v.carry_q[Ly.carry_off + cell];
+        int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
+        long long bu = 0, moved = 0;
+        const int rs = v.rstart[q], ns = v.rcount[q];
+        if (ns > cap) {
+            // region too full for shared memory: the global-memory path
+            if (role != 0) continue;
+            WarpSmem& sm = *(WarpSmem*)base;
+            for (int t = 0; t < cnt; t++) {
                 const int j = v.q_slots[start + t];
-                S.cj[lane] = j;
-                S.ci[lane] = v.slot_bead[j];
-                S.clam[lane] = v.slot_lam[j];
-                double V[3];
-                for (int a = 0; a < 3; a++) {
-                    V[a] = v.slot_V[3 * j + a];             // with uniform centres: the centre itself
-                    S.cV[3 * lane + a] = V[a];
-                    S.cp[3 * lane + a] = v.slot_p[3 * j + a];
-                }
-                S.cthr[lane] = v.slot_thr[j];
-                S.cthrf[lane] = (float)S.cthr[lane];
-                // what the move needs from its own scale, ahead of the sequential loop
-                const double lam_s = S.clam[lane];
-                const double R_s = add(add(lam_s, mul(mul(0.25, v.A0), lam_s)), v.r_reach);
-                S.cR[lane] = R_s;
-                S.cRf[lane] = (float)R_s;
-                S.clamf[lane] = (float)lam_s;
-                S.cA0l[lane] = mul(v.A0, lam_s);
-                for (int a = 0; a < 3; a++) {
-                    S.clamV[3 * lane + a] = mul(lam_s, V[a]);
-                    S.cVf[3 * lane + a] = (float)V[a];
-                    S.cpf[3 * lane + a] = (float)S.cp[3 * lane + a];
-                }
-                S.cti[lane] = stage_find(S, S.ci[lane]);
-            }
-            if (H > 1) __syncthreads(); else __syncwarp();
-            const int cend = min(kSlotChunk, cnt - c0);
-            for (int cc = 0; cc < cend; cc++) {
-                const int j = S.cj[cc];
-                const double lam = __double_as_longlong(carry) > 0 ? carry : S.clam[cc];
+                const double lam = carry > 0.0 ? carry : v.slot_lam[j];
                 int n = 0;
                 double du = 0.0;
-                tag++;
-                int r;
-                if (H > 1) {
-                    r = stage_attempt<PREC, true>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
-                                                  &rechecks, &du, H, role, &s_coop);
-                    __syncwarp();
-                    // warp 0's outcome (and its commit) reach every warp before the next move
-                    if (role == 0 && lane == 0) s_coop.r[tag & 1] = r;
-                    __syncthreads();
-                    r = s_coop.r[tag & 1];
-                } else {
-                    r = stage_attempt<PREC, false>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
-                                                   &rechecks, &du, 1, 0, nullptr);
-                    __syncwarp();
-                }
-                if (r == DEFER) { if (role == 0 && lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
+                int r = warp_attempt<PREC>(v, sm, l, j, v.slot_bead[j], lam, sweep, rlo, rhi, lane, &n, &pe, &rechecks, &du);
+                __syncwarp();
+                if (r == DEFER) { if (lane == 0) v.defer[start + t] = 1; def++; continue; }
                 att++; bu += n;
                 if (r == ACCEPT) { acc++; moved += n; }
-                if (role == 0 && lane == 0) {
+                if (lane == 0) {
                     v.tr_out[Ly.tr_off + j] = (uint8_t)((r == ACCEPT ? 1 : 2) | tflag);
                     v.tr_n[Ly.tr_off + j] = n;
                     v.tr_du[Ly.tr_off + j] = du;
                 }
                 carry = (r == ACCEPT) ? 0.0 : lam;
             }
-            // the chunk arrays are refilled only after every warp has finished this chunk
+        } else {
+            Stage S = stage_carve(base, cap, ncap);
+            Stage32 C32 = stage32(v);
+            C32.sqrt_n = s_sqrt;
+            for (int a = 0; a < 3; a++) C32.side[a] = (float)((double)(rhi[a] - rlo[a] + 1) * (v.L / v.Gf));
+            const int HT = 1 << S.hbits;
+            const int ql = role * 32 + lane, qstride = 32 * H;   // this thread among the queue's warps
+            for (int h = ql; h < HT; h += qstride) S.hkey[h] = -1;
             if (H > 1) __syncthreads(); else __syncwarp();
-        }
-        if (role != 0) return;                    // the write-back runs on warp 0
-        // write back the moved beads (lanes in parallel); cell-list moves by lane 0, in
-        // staged order, for the beads whose fine cell changed (the old cell from the bead's
-        // record, which nothing else writes during the phase)
-        for (int base2 = 0; base2 < ns; base2 += 32) {
-            const int t = base2 + lane;
-            int newcell = -1, oldcell = -1;
-            if (t < ns && (S.sdim[t] & (1 << 24))) {
-                const int dm = S.sdim[t];
-                const int m = S.sid[t];
-                const Bead ob = v.bead[m];
-                oldcell = cell_lin(v, ob.x, ob.y, ob.z);
-                put_bead(v.bead, v.bf, m, S.sx[t], S.sy[t], S.sz[t]);
-                const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
-                if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
-                const int nc2 = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
-                if (nc2 != oldcell) newcell = nc2;
-            }
-            const unsigned ch = __ballot_sync(FULL, newcell >= 0);
-            S.cand[lane] = newcell;
-            S.cand[32 + lane] = oldcell;
-            __syncwarp();
-            if (lane == 0) {
-                for (unsigned bits = ch; bits; bits &= bits - 1u) {
-                    const int ln = __ffs(bits) - 1, tt = base2 + ln;
-                    const int m = S.sid[tt], oc = S.cand[32 + ln], ncl = S.cand[ln];
-                    relink(v, m, oc, ncl);
+            const double hf = v.L / v.Gf;
+            const double org[3] = {(double)rlo[0] * hf, (double)rlo[1] * hf, (double)rlo[2] * hf};
+            const float sidef = (float)((double)(rhi[0] - rlo[0] + 1) * hf);
+            for (int t = ql; t < ns; t += qstride) {
+                const int m = v.rlist[rs + t];
+                const Bead bb = v.bead[m];
+                S.sx[t] = bb.x; S.sy[t] = bb.y; S.sz[t] = bb.z;
+                local_split(bb.x, org[0], v.L, S.hx[t], S.lx[t]);
+                local_split(bb.y, org[1], v.L, S.hy[t], S.ly[t]);
+                local_split(bb.z, org[2], v.L, S.hz[t], S.lz[t]);
+                S.sid[t] = m;
+                const int bflag = (v.bnext[m] ? 1 : 0) | (m > 0 && v.bnext[m - 1] ? 2 : 0);
+                S.sdim[t] = 128 | (128 << 8) | (128 << 16) | (bflag << 25);
+                S.stag[t] = 0;
+                const uint32_t mask = (uint32_t)HT - 1u;
+                uint32_t h = hslot(m, S.hbits);
+                for (int probe = 0; probe < HT; probe++) {
+                    const int prev = atomicCAS(&S.hkey[h], -1, m);
+                    if (prev == -1) { S.hval[h] = t; break; }
+                    h = (h + 1u) & mask;
                 }
             }
-            __syncwarp();
+            if (H > 1) __syncthreads(); else __syncwarp();
+            int tag = 0;
+            for (int c0 = 0; c0 < cnt; c0 += kSlotChunk) {
+                // slot parameters of the chunk, one lane of warp 0 per slot: V, p and the acceptance
+                // threshold as the slot kernel drew them (Appendix D, Eq. 20)
+                const int t = c0 + lane;
+                if (role == 0 && t < cnt) {
+                    const int j = v.q_slots[start + t];
+                    S.cj[lane] = j;
+                    S.ci[lane] = v.slot_bead[j];
+                    S.clam[lane] = v.slot_lam[j];
+                    double V[3];
+                    for (int a = 0; a < 3; a++) {
+                        V[a] = v.slot_V[3 * j + a];             // with uniform centres: the centre itself
+                        S.cV[3 * lane + a] = V[a];
+                        S.cp[3 * lane + a] = v.slot_p[3 * j + a];
+                    }
+                    S.cthr[lane] = v.slot_thr[j];
+                    S.cthrf[lane] = (float)S.cthr[lane];
+                    // what the move needs from its own scale, ahead of the sequential loop
+                    const double lam_s = S.clam[lane];
+                    const double R_s = add(add(lam_s, mul(mul(0.25, v.A0), lam_s)), v.r_reach);
+                    S.cR[lane] = R_s;
+                    S.cRf[lane] = (float)R_s;
+                    S.clamf[lane] = (float)lam_s;
+                    S.cA0l[lane] = mul(v.A0, lam_s);
+                    for (int a = 0; a < 3; a++) {
+                        S.clamV[3 * lane + a] = mul(lam_s, V[a]);
+                        S.cVf[3 * lane + a] = (float)V[a];
+                        S.cpf[3 * lane + a] = (float)S.cp[3 * lane + a];
+                    }
+                    S.cti[lane] = stage_find(S, S.ci[lane]);
+                }
+                if (H > 1) __syncthreads(); else __syncwarp();
+                const int cend = min(kSlotChunk, cnt - c0);
+                for (int cc = 0; cc < cend; cc++) {
+                    const int j = S.cj[cc];
+                    const double lam = __double_as_longlong(carry) > 0 ? carry : S.clam[cc];
+                    int n = 0;
+                    double du = 0.0;
+                    tag++;
+                    int r;
+                    if (H > 1) {
+                        r = stage_attempt<PREC, true>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
+                                                      &rechecks, &du, H, role, &s_coop);
+                        __syncwarp();
+                        // warp 0's outcome (and its commit) reach every warp before the next move
+                        if (role == 0 && lane == 0) s_coop.r[tag & 1] = r;
+                        __syncthreads();
+                        r = s_coop.r[tag & 1];
+                    } else {
+                        r = stage_attempt<PREC, false>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
+                                                       &rechecks, &du, 1, 0, nullptr);
+                        __syncwarp();
+                    }
+                    if (r == DEFER) { if (role == 0 && lane == 0) v.defer[start + c0 + cc] = 1; def++; continue; }
+                    att++; bu += n;
+                    if (r == ACCEPT) { acc++; moved += n; }
+                    if (role == 0 && lane == 0) {
+                        v.tr_out[Ly.tr_off + j] = (uint8_t)((r == ACCEPT ? 1 : 2) | tflag);
+                        v.tr_n[Ly.tr_off + j] = n;
+                        v.tr_du[Ly.tr_off + j] = du;
+                    }
+                    carry = (r == ACCEPT) ? 0.0 : lam;
+                }
+                // the chunk arrays are refilled only after every warp has finished this chunk
+                if (H > 1) __syncthreads(); else __syncwarp();
+            }
+            if (role != 0) continue;                    // the write-back runs on warp 0
+            // write back the moved beads (lanes in parallel); cell-list moves by lane 0, in
+            // staged order, for the beads whose fine cell changed (the old cell from the bead's
+            // record, which nothing else writes during the phase)
+            for (int base2 = 0; base2 < ns; base2 += 32) {
+                const int t = base2 + lane;
+                int newcell = -1, oldcell = -1;
+                if (t < ns && (S.sdim[t] & (1 << 24))) {
+                    const int dm = S.sdim[t];
+                    const int m = S.sid[t];
+                    const Bead ob = v.bead[m];
+                    oldcell = cell_lin(v, ob.x, ob.y, ob.z);
+                    put_bead(v.bead, v.bf, m, S.sx[t], S.sy[t], S.sz[t]);
+                    const int ax = (dm & 0xff) - 128, ay = ((dm >> 8) & 0xff) - 128, az = ((dm >> 16) & 0xff) - 128;
+                    if (ax | ay | az) { v.img[3 * m] += ax; v.img[3 * m + 1] += ay; v.img[3 * m + 2] += az; }
+                    const int nc2 = cell_lin(v, S.sx[t], S.sy[t], S.sz[t]);
+                    if (nc2 != oldcell) newcell = nc2;
+                }
+                const unsigned ch = __ballot_sync(FULL, newcell >= 0);
+                S.cand[lane] = newcell;
+                S.cand[32 + lane] = oldcell;
+                __syncwarp();
+                if (lane == 0) {
+                    for (unsigned bits = ch; bits; bits &= bits - 1u) {
+                        const int ln = __ffs(bits) - 1, tt = base2 + ln;
+                        const int m = S.sid[tt], oc = S.cand[32 + ln], ncl = S.cand[ln];
+                        relink(v, m, oc, ncl);
+                    }
+                }
+                __syncwarp();
+            }
         }
-    }
-    if (lane == 0) {
-        v.carry_q[Ly.carry_off + cell] = carry;
-        atomicAdd(&v.ctr[C_ATT + lr], (unsigned long long)att);
-        atomicAdd(&v.ctr[C_ACC + lr], (unsigned long long)acc);
-        if (l < kLevel2) atomicAdd(&v.ctr[C_DEF + lr], (unsigned long long)def);   // first deferrals only
-        atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
-        atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
-        atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
-        atomicAdd(&v.ctr[C_CBU], (unsigned long long)bu);
-        atomicAdd(&v.ctr[C_CMOVED], (unsigned long long)moved);
-        atomicAdd(&v.ctr[C_MOVED], (unsigned long long)moved);
-        atomicAdd(&v.ctr[C_CPE], (unsigned long long)pe);
-        if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
-    }
+        if (lane == 0) {
+            v.carry_q[Ly.carry_off + cell] = carry;
+            atomicAdd(&v.ctr[C_ATT + lr], (unsigned long long)att);
+            atomicAdd(&v.ctr[C_ACC + lr], (unsigned long long)acc);
+            if (l < kLevel2) atomicAdd(&v.ctr[C_DEF + lr], (unsigned long long)def);   // first deferrals only
+            atomicAdd(&v.ctr[C_ACCTOT], (unsigned long long)acc);
+            atomicAdd(&v.ctr[C_BU], (unsigned long long)bu);
+            atomicAdd(&v.ctr[C_PARTNER], (unsigned long long)pe);
+            atomicAdd(&v.ctr[C_CBU], (unsigned long long)bu);
+            atomicAdd(&v.ctr[C_CMOVED], (unsigned long long)moved);
+            atomicAdd(&v.ctr[C_MOVED], (unsigned long long)moved);
+            atomicAdd(&v.ctr[C_CPE], (unsigned long long)pe);
+            if (rechecks) atomicAdd(&v.ctr[C_RECHECK], (unsigned long long)rechecks);
+        }
+    }   // queues
 }
 
 size_t staged_smem_bytes(int cap, int warps, int ncap) { return (size_t)warps * warp_stride(cap, ncap); }
@@ -3618,14 +3646,29 @@ void prepare_staged(const GroupDims& g) {
     }
 }
 
+// multiprocessors of the current device (cached per device)
+static int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour, cudaStream_t s, const ForkJoin* fj) {
     const int nq = g.nq[l];
     const int gb = (int)gx((g.maxN + 255) / 256, g.S);
+    const int cap = layer_cap(g, l), ncap = sched_ncap_g(g, l);
+    const bool split = split_layer(g, l, cap) && fj && fj->side[0];
     k_zero<<<dim3(gx((nq + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 1, l);
     k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
-    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l);
+    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l, colour, split ? kLightCap : -1);
     k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
-    const int cap = layer_cap(g, l), ncap = sched_ncap_g(g, l);
     int qpb = 1, warps = 1;
     staged_shape(g, cap, ncap, &qpb, &warps);
     const size_t smem = staged_smem_bytes(cap, qpb, ncap);
@@ -3633,7 +3676,7 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
     prepare_staged(g);
     const int stride = (int)warp_stride(cap, ncap);
     const int np = (g.prec_mask & 1) + ((g.prec_mask >> 1) & 1);
-    if (split_layer(g, l, cap) && fj && fj->side[0]) {
+    if (split) {
         // Ordinary regions (at most kLightCap beads) on the stream, one warp per queue and small
         // staging; the dense regions (a chain's worth of beads, the longest queues of the phase)
         // at the same time on a side stream, one block of cooperating warps per queue with room
@@ -3645,23 +3688,23 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         const int capH = staged_cap_max(ncap);
         const size_t smemH = staged_smem_bytes(capH, 1, ncap);
         const int strideH = (int)warp_stride(capH, ncap);
-        const dim3 gridH(nq, g.S);
+        const dim3 gridH(std::min(nq, sm_count()), g.S);   // persistent: one block per SM over the list
         cudaEventRecord(fj->fork, s);
         cudaStreamWaitEvent(fj->side[0], fj->fork, 0);
         if (g.prec_mask & 1)
-            k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30);
+            k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30, 1);
         if (g.prec_mask & 2)
-            k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30);
+            k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30, 1);
         const int ncL = light_ncap(ncap);
-        if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap);
-        if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap);
+        if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
+        if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
         cudaEventRecord(fj->join[0], fj->side[0]);
         cudaStreamWaitEvent(s, fj->join[0], 0);
         return 4 + 2 * np;
     }
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30);
+    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
+    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
     return 4 + np;
 
 }
