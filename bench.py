@@ -63,13 +63,16 @@ def make_system(seed, sample=None):
     return I.suspension(seed=seed, **(sample or SUSPENSION))
 
 
-def make_params(system, precision, seed, sim_id=0):
+def make_params(system, precision, seed, sim_id=0, scaled=False):
     """The suspension's parameters with the schedule of its shape from the shipped table (the
-    table is keyed on the mixed-precision shape; the binary64 run uses the same schedule)."""
+    table is keyed on the mixed-precision shape; the binary64 run uses the same schedule). A
+    scaled-down copy for profiling takes the full size's first candidate without measuring."""
     from paper_1611_09160_gb300 import autotune as A
     from paper_1611_09160_gb300 import wmcd
     base = wmcd.default_params(system.n_beads, system.box_L, planewave_mode=wmcd.PLANEWAVE_PERIODIC, lcut=8,
                                precision=wmcd.MIXED, seed=seed, sim_id=sim_id)
+    if scaled:
+        return dict(A.Tuner.apply(base, SUSPENSION_CANDIDATES[0]), precision=precision)
     tuner = A.Tuner(path=None, warm=1, sweeps=1, seed_table=A.DEFAULT_TABLE)
     p = tuner.schedule(base, system=system, candidates=SUSPENSION_CANDIDATES)
     return dict(p, precision=precision)
@@ -512,12 +515,15 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     seed = 1 + rank
-    system = make_system(seed)
+    scale = max(1, args.profile_scale)
+    system = make_system(seed, None if scale == 1 else
+                         dict(SUSPENSION, n_spheres=SUSPENSION["n_spheres"] // scale, n_chains=SUSPENSION["n_chains"] // scale))
+    n_sys = system.n_beads
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
 
     def measure(precision, profile):
-        p = make_params(system, precision, seed, sim_id=rank)
+        p = make_params(system, precision, seed, sim_id=rank, scaled=scale > 1)
         sim = wmcd.Simulation(p, system.pos, system.chain_len, stream=stream)
         for _ in range(args.warmup):
             sim.sweep(1, stream=stream)
@@ -614,7 +620,9 @@ def run_gpu(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": dict(workload_config(), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "config": dict(workload_config(), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           **({} if scale == 1 else {"profile_scale": scale, "n_beads": n_sys,
+                                                      "workload": f"suspension scaled down {scale}x for profiling"})),
             "sim_time_per_s": simt_all / (total_ms_all * 1e-3),
             "fp64": {"value": fp64_value, "unit": UNIT, "speedup_mixed_over_fp64": value / fp64_value,
                      "ms_per_step": t64_all / args.steps},
@@ -648,6 +656,8 @@ def main():
     ap.add_argument("--serve-chunk", type=int, default=10)
     ap.add_argument("--drift-sweeps", type=int, default=10000,
                     help="sweeps of the mixed-against-binary64 drift check on the 32-bead chain (0: skip)")
+    ap.add_argument("--profile-scale", type=int, default=1,
+                    help="divide the suspension's spheres and chains by this (same density): profiling only")
     ap.add_argument("--drift-dilute-sweeps", type=int, default=1000,
                     help="sweeps of the same check on the dilute chains (0: skip)")
     args = ap.parse_args()

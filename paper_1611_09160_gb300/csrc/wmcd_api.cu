@@ -493,7 +493,7 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     int* d_tab = nullptr;
     ok = ok && !dalloc(h, &v.rkey, N) && !dalloc(h, &v.rlist, N) && !dalloc(h, &v.rcount, nq_max) &&
          !dalloc(h, &v.rstart, nq_max) && !dalloc(h, &v.rfill, nq_max) && !dalloc(h, &d_tab, tab.size()) &&
-         !dalloc(h, &v.hq_list, nq_max) && !dalloc(h, &v.hq_ctl, 2);
+         !dalloc(h, &v.hq_list, nq_max) && !dalloc(h, &v.hq_ctl, 4);
     if (!ok) return WMCD_ENOMEM;
     if (counting) return WMCD_OK;
     v.axis_tab = d_tab;
@@ -616,11 +616,13 @@ int wmcd::create_handle(wmcd_handle* H, const wmcd_params* params, const double*
     if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return WMCD_ECUDA; }
     if (err) return WMCD_EINVAL;   // a coordinate outside [0, L) or not finite
     if (!arena) {
-        // a lone simulation's side stream: the dense regions of a colour phase run on it beside
-        // the ordinary ones (a batch brings its own)
+        // a lone simulation's side streams: the dense regions of a colour phase run on them
+        // beside the ordinary ones (a batch brings its own)
         if (cudaStreamCreateWithFlags(&h->fj.side[0], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h->fj.side[1], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h->fj.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->fj.join[0], cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&h->fj.join[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fj.join[1], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return WMCD_ECUDA;
         }
@@ -1019,9 +1021,11 @@ void wmcd::destroy_handle(wmcd_handle* H) {
     for (auto& u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
-    if (h->fj.side[0]) cudaStreamDestroy(h->fj.side[0]);
+    for (int c = 0; c < 2; c++) {
+        if (h->fj.side[c]) cudaStreamDestroy(h->fj.side[c]);
+        if (h->fj.join[c]) cudaEventDestroy(h->fj.join[c]);
+    }
     if (h->fj.fork) cudaEventDestroy(h->fj.fork);
-    if (h->fj.join[0]) cudaEventDestroy(h->fj.join[0]);
     cudaGetLastError();
     delete H;
 }

@@ -185,7 +185,8 @@ struct SimView {
     int* rlist;                  // bead ids grouped by queue
     const int* axis_tab;         // per layer, per colour offset, per fine cell: queue coordinate or -1
     int* hq_list;                // queues of the current colour phase with dense regions
-    int* hq_ctl;                 // [0] their number, [1] work counter of the launch that runs them
+    int* hq_ctl;                 // [0] how many up to the middle size (front of the list), [1] their work
+                                 // counter, [2] how many larger (back of the list), [3] their counter
     int stage_cap;               // beads a warp can stage in shared memory
     // serial-phase scratch (n up to N)
     int* s_ids;

@@ -375,8 +375,9 @@ __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
 // exclusive scan of n ints by one block per simulation: mode 0 = bucket counts of layer l
 // (G^3 keys), mode 1 = region counts of layer l (Q^3 queues). With heavy_lo >= 0 (mode 1) it
 // also lists the queues of the colour phase that have slots and more than heavy_lo beads in
-// their region (in no particular order) and resets the list's work counter.
-__global__ void k_scan(const SimView* __restrict__ vs, int mode, int l, int colour, int heavy_lo) {
+// their region, in no particular order: those with at most heavy_mid beads from the front of
+// hq_list, the others from its back, and resets the two lists' work counters.
+__global__ void k_scan(const SimView* __restrict__ vs, int mode, int l, int colour, int heavy_lo, int heavy_mid) {
     SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
     if (!sched_on(v, l)) return;
@@ -405,13 +406,16 @@ __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l, int colo
         __syncthreads();
     }
     if (mode == 1 && heavy_lo >= 0) {
-        __shared__ int hc;
-        if (threadIdx.x == 0) hc = 0;
+        __shared__ int hc[2];
+        if (threadIdx.x < 2) hc[threadIdx.x] = 0;
         __syncthreads();
         for (int q = threadIdx.x; q < n; q += blockDim.x)
-            if (in[q] > heavy_lo && v.q_count[colour * n + q] > 0) v.hq_list[atomicAdd(&hc, 1)] = q;
+            if (in[q] > heavy_lo && v.q_count[colour * n + q] > 0) {
+                if (in[q] <= heavy_mid) v.hq_list[atomicAdd(&hc[0], 1)] = q;
+                else v.hq_list[n - 1 - atomicAdd(&hc[1], 1)] = q;
+            }
         __syncthreads();
-        if (threadIdx.x == 0) { v.hq_ctl[0] = hc; v.hq_ctl[1] = 0; }
+        if (threadIdx.x == 0) { v.hq_ctl[0] = hc[0]; v.hq_ctl[1] = 0; v.hq_ctl[2] = hc[1]; v.hq_ctl[3] = 0; }
     }
 }
 // zero the per-phase counters: mode 0 = bucket counts, fills and deferral flags of layer l,
@@ -464,7 +468,7 @@ void launch_bucket(const SimView* d, const GroupDims& g, int l, cudaStream_t s) 
     const int keys = g.keys[l], M = g.Mmax[l];
     k_zero<<<dim3(gx((std::max(keys, M) + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 0, l);
     k_bucket_count<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
-    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 0, l, 0, -1);
+    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 0, l, 0, -1, 0);
     k_bucket_scatter<<<dim3((M + 255) / 256, g.S), 256, 0, s>>>(d, l);
     k_bucket_sort<<<dim3((keys + 127) / 128, g.S), 128, 0, s>>>(d, l);
 }
@@ -3331,12 +3335,25 @@ __device__ __forceinline__ bool staged_block_has_work(const SimView& g, int l, i
 // shared bytes per queue. Only queues whose region holds ns_lo..ns_hi beads run: a colour phase
 // is split between a launch for ordinary regions (small staging, more warps per SM) and one for
 // the dense ones, which take disjoint queues, so the split changes nothing in the results.
-template <int PREC>
-__global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
+// The cooperative scratch of a block whose warps serve one queue together (none for the light
+// variant, whose blocks serve one queue per warp).
+template <bool USE>
+__device__ __forceinline__ CoopSh* coop_scratch() {
+    if constexpr (USE) {
+        __shared__ CoopSh s_coop;
+        return &s_coop;
+    } else {
+        return nullptr;
+    }
+}
+// LIGHT: a launch whose regions all fit its staging (one warp per queue): no global-memory path
+// and no cooperating warps are compiled in, which leaves fewer registers per thread.
+template <int PREC, bool LIGHT>
+__global__ void __launch_bounds__(kMaxStageWarps * 32, LIGHT ? 3 : 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
                                                                         int cap, int qpb, int ncap, int stride,
                                                                         int ns_lo, int ns_hi, int list) {
     SIM_EXIT_IF(!sched_on(gv, l) || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
-                (list ? (int)blockIdx.x >= gv.hq_ctl[0]
+                (list ? (int)blockIdx.x >= gv.hq_ctl[list == 2 ? 2 : 0]
                       : ((int)(blockIdx.x * qpb) >= (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) * (sched_layer(gv, l).G / gv.K) ||
                          !staged_block_has_work(gv, l, colour, qpb, ns_lo, ns_hi))))
     SIM_PROLOGUE
@@ -3344,11 +3361,11 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     if (!sched_on(v, l) || v.precision != PREC || colour >= v.K * v.K * v.K) return;
     // sqrt(n) for the amplitude A_w = A0 lam / sqrt(n) (Eq. 29), once per block
     __shared__ double s_sqrt[kNCap + 1];
-    __shared__ CoopSh s_coop;
+    CoopSh* const X = coop_scratch<!LIGHT>();
     for (int i = threadIdx.x; i <= kNCap; i += blockDim.x) s_sqrt[i] = sqr_t((double)i);
     __syncthreads();
     const uint64_t sweep = v.step[0];
-    const int H = (int)(blockDim.x >> 5) / qpb;     // warps per queue: 1, or all of the block
+    const int H = LIGHT ? 1 : (int)(blockDim.x >> 5) / qpb;     // warps per queue: 1, or all of the block
     const int wib = (int)(threadIdx.x >> 5) / H, role = (int)(threadIdx.x >> 5) % H, lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const LayerDev Ly = sched_layer(v, l);
@@ -3362,12 +3379,14 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
     for (int it = 0;; it++) {
         int q;
         if (list) {
-            if (threadIdx.x == 0) s_item = atomicAdd(&v.hq_ctl[1], 1);
+            // list 1: the front of hq_list (regions up to the middle size), list 2: its back
+            const int lc = list == 2 ? 2 : 0;
+            if (threadIdx.x == 0) s_item = atomicAdd(&v.hq_ctl[lc + 1], 1);
             __syncthreads();
             const int i = s_item;
             __syncthreads();                          // read by all before the next item is taken
-            if (i >= v.hq_ctl[0]) break;
-            q = v.hq_list[i];
+            if (i >= v.hq_ctl[lc]) break;
+            q = v.hq_list[list == 2 ? nq - 1 - i : i];
         } else {
             if (it > 0) break;
             q = blockIdx.x * qpb + wib;
@@ -3392,7 +3411,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
         int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
         long long bu = 0, moved = 0;
         const int rs = v.rstart[q], ns = v.rcount[q];
-        if (ns > cap) {
+        if (!LIGHT && ns > cap) {
             // region too full for shared memory: the global-memory path
             if (role != 0) continue;
             WarpSmem& sm = *(WarpSmem*)base;
@@ -3488,12 +3507,12 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
                     int r;
                     if (H > 1) {
                         r = stage_attempt<PREC, true>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
-                                                      &rechecks, &du, H, role, &s_coop);
+                                                      &rechecks, &du, H, role, X);
                         __syncwarp();
                         // warp 0's outcome (and its commit) reach every warp before the next move
-                        if (role == 0 && lane == 0) s_coop.r[tag & 1] = r;
+                        if (role == 0 && lane == 0) X->r[tag & 1] = r;
                         __syncthreads();
-                        r = s_coop.r[tag & 1];
+                        r = X->r[tag & 1];
                     } else {
                         r = stage_attempt<PREC, false>(v, S, C32, ns, org, sidef, l, cc, lam, rlo, rhi, lane, tag, &n, &pe,
                                                        &rechecks, &du, 1, 0, nullptr);
@@ -3564,6 +3583,9 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, 1) k_colour_staged(const 
 size_t staged_smem_bytes(int cap, int warps, int ncap) { return (size_t)warps * warp_stride(cap, ncap); }
 // the launch of ordinary regions: regions of at most kLightCap beads, kMaxStageWarps queues per block
 constexpr int kLightCap = 80;
+// the dense regions of a split phase: up to kMidCap beads staged by blocks small enough for two
+// per SM, the larger ones by blocks with the most shared memory
+constexpr int kMidCap = 512;
 // (its supports are at most its regions' kLightCap beads, so its support arrays need no more)
 static int light_ncap(int ncap) { return ncap < kLightCap ? ncap : kLightCap; }
 static size_t light_smem_bytes(int ncap) {
@@ -3602,7 +3624,7 @@ static void staged_shape(const GroupDims& g, int cap, int ncap, int* qpb, int* w
 
 // The largest dynamic shared memory each staged kernel was opened for, per device: raised
 // before a launch needs more, so that launches recorded into a graph set nothing.
-static int g_staged_smem[64][2];
+static int g_staged_smem[64][2][2];
 static int g_serial_smem[64][2];
 void prepare_staged(const GroupDims& g) {
     int dev = 0;
@@ -3623,7 +3645,7 @@ void prepare_staged(const GroupDims& g) {
             g_serial_smem[dev][1] = sm;
         }
     }
-    int smem = 0;
+    int smem = 0, smemL = 0;
     for (int i = 0; i < 2 * g.maxL; i++) {
         const int l = i < g.maxL ? i : kLevel2 + i - g.maxL;
         if (!g.coloured[l]) continue;
@@ -3632,17 +3654,25 @@ void prepare_staged(const GroupDims& g) {
         staged_shape(g, cap, ncap, &qpb, &warps);
         smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, ncap));
         if (split_layer(g, l, cap)) {
-            smem = std::max(smem, (int)light_smem_bytes(ncap));
+            smemL = std::max(smemL, (int)light_smem_bytes(ncap));
             smem = std::max(smem, (int)staged_smem_bytes(staged_cap_max(ncap), 1, ncap));
         }
     }
-    if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0]) {
-        cudaFuncSetAttribute(k_colour_staged<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        g_staged_smem[dev][0] = smem;
+    if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0][0]) {
+        cudaFuncSetAttribute(k_colour_staged<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        g_staged_smem[dev][0][0] = smem;
     }
-    if ((g.prec_mask & 2) && smem > g_staged_smem[dev][1]) {
-        cudaFuncSetAttribute(k_colour_staged<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        g_staged_smem[dev][1] = smem;
+    if ((g.prec_mask & 2) && smem > g_staged_smem[dev][1][0]) {
+        cudaFuncSetAttribute(k_colour_staged<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        g_staged_smem[dev][1][0] = smem;
+    }
+    if ((g.prec_mask & 1) && smemL > g_staged_smem[dev][0][1]) {
+        cudaFuncSetAttribute(k_colour_staged<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemL);
+        g_staged_smem[dev][0][1] = smemL;
+    }
+    if ((g.prec_mask & 2) && smemL > g_staged_smem[dev][1][1]) {
+        cudaFuncSetAttribute(k_colour_staged<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemL);
+        g_staged_smem[dev][1][1] = smemL;
     }
 }
 
@@ -3667,7 +3697,7 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
     const bool split = split_layer(g, l, cap) && fj && fj->side[0];
     k_zero<<<dim3(gx((nq + 255) / 256, g.S), g.S), 256, 0, s>>>(d, 1, l);
     k_region_count<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
-    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l, colour, split ? kLightCap : -1);
+    k_scan<<<dim3(1, g.S), 1024, 0, s>>>(d, 1, l, colour, split ? kLightCap : -1, kMidCap);
     k_region_scatter<<<dim3(gb, g.S), 256, 0, s>>>(d, l, colour);
     int qpb = 1, warps = 1;
     staged_shape(g, cap, ncap, &qpb, &warps);
@@ -3679,8 +3709,10 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
     if (split) {
         // Ordinary regions (at most kLightCap beads) on the stream, one warp per queue and small
         // staging; the dense regions (a chain's worth of beads, the longest queues of the phase)
-        // at the same time on a side stream, one block of cooperating warps per queue with room
-        // for the largest region. The two launches take disjoint queues of one colour.
+        // at the same time on side streams, one block of cooperating warps per queue: those up to
+        // kMidCap beads in blocks small enough for two per SM, the rest with room for the largest
+        // region. The launches take disjoint queues of one colour; the dense ones run
+        // persistently over the lists the region scan made.
         const int qL = kMaxStageWarps;
         const dim3 gridL((nq + qL - 1) / qL, g.S);
         const size_t smemL = light_smem_bytes(ncap);
@@ -3688,23 +3720,34 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         const int capH = staged_cap_max(ncap);
         const size_t smemH = staged_smem_bytes(capH, 1, ncap);
         const int strideH = (int)warp_stride(capH, ncap);
-        const dim3 gridH(std::min(nq, sm_count()), g.S);   // persistent: one block per SM over the list
+        const int strideM = (int)warp_stride_staged(kMidCap, ncap);   // its regions always fit
+        const dim3 gridH(std::min(nq, sm_count()), g.S), gridM(std::min(nq, 2 * sm_count()), g.S);
+        cudaStream_t sm_ = fj->side[0], sh_ = fj->side[1] ? fj->side[1] : fj->side[0];
         cudaEventRecord(fj->fork, s);
-        cudaStreamWaitEvent(fj->side[0], fj->fork, 0);
-        if (g.prec_mask & 1)
-            k_colour_staged<0><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30, 1);
-        if (g.prec_mask & 2)
-            k_colour_staged<1><<<gridH, kMaxStageWarps * 32, smemH, fj->side[0]>>>(d, l, colour, capH, 1, ncap, strideH, kLightCap + 1, 1 << 30, 1);
+        cudaStreamWaitEvent(sm_, fj->fork, 0);
+        if (sh_ != sm_) cudaStreamWaitEvent(sh_, fj->fork, 0);
+        if (g.prec_mask & 1) {
+            k_colour_staged<0, false><<<gridM, kMaxStageWarps * 32, strideM, sm_>>>(d, l, colour, kMidCap, 1, ncap, strideM, kLightCap + 1, kMidCap, 1);
+            k_colour_staged<0, false><<<gridH, kMaxStageWarps * 32, smemH, sh_>>>(d, l, colour, capH, 1, ncap, strideH, kMidCap + 1, 1 << 30, 2);
+        }
+        if (g.prec_mask & 2) {
+            k_colour_staged<1, false><<<gridM, kMaxStageWarps * 32, strideM, sm_>>>(d, l, colour, kMidCap, 1, ncap, strideM, kLightCap + 1, kMidCap, 1);
+            k_colour_staged<1, false><<<gridH, kMaxStageWarps * 32, smemH, sh_>>>(d, l, colour, capH, 1, ncap, strideH, kMidCap + 1, 1 << 30, 2);
+        }
         const int ncL = light_ncap(ncap);
-        if (g.prec_mask & 1) k_colour_staged<0><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
-        if (g.prec_mask & 2) k_colour_staged<1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
-        cudaEventRecord(fj->join[0], fj->side[0]);
+        if (g.prec_mask & 1) k_colour_staged<0, true><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
+        if (g.prec_mask & 2) k_colour_staged<1, true><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
+        cudaEventRecord(fj->join[0], sm_);
         cudaStreamWaitEvent(s, fj->join[0], 0);
-        return 4 + 2 * np;
+        if (sh_ != sm_) {
+            cudaEventRecord(fj->join[1], sh_);
+            cudaStreamWaitEvent(s, fj->join[1], 0);
+        }
+        return 4 + 3 * np;
     }
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
-    if (g.prec_mask & 2) k_colour_staged<1><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
+    if (g.prec_mask & 1) k_colour_staged<0, false><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
+    if (g.prec_mask & 2) k_colour_staged<1, false><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
     return 4 + np;
 
 }
