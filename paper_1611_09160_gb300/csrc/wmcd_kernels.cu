@@ -1046,6 +1046,10 @@ namespace wmcd {
 // normalised, and the Metropolis threshold -kT ln(1 - u) (Eq. 20). They depend only on the
 // slot's counter, not on the state, so computing them early changes nothing.
 
+// pairs a serial move keeps for its binary64 recheck (dynamic shared memory of the serial kernel
+// in its mixed-precision 512-thread form, the one lone simulations use; other forms walk again)
+constexpr int kSerialPairCap = 12288;
+template <int PREC, int NT> __host__ __device__ constexpr int serial_pair_cap() { return (PREC == 1 && NT >= 512) ? kSerialPairCap : 0; }
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs, int l) {
     SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || (((gv.smem_layers | gv.big_layers) >> l) & 1))
@@ -1054,7 +1058,11 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     if (threadIdx.x == 0) *v.cl_stale = 0;      // rebuilt just before this launch if it was stale
     const int M = v.counts[l];
     const int use_list = v.layer[l].G > 0;
-    __shared__ double sh_b[3], sh_p[3], sh_carry;
+    __shared__ double sh_b[3], sh_p[3], sh_carry, sh_awx[2];
+    // pairs within the WCA cutoff (old or new) found by the binary32 pass, for a binary64 pass
+    // that then visits only those (kSerialPairCap in dynamic shared memory; more: full walk)
+    extern __shared__ __align__(16) int2 sh_pairs[];
+    __shared__ int sh_np;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total, sh_need64;
     __shared__ float sh_a32[3];                   // binary32 energy change, band, threshold (audit)
@@ -1106,6 +1114,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             sh_n = 0;
             sh_total = 0;
             sh_nch = 0;
+            sh_np = 0;
             uint32_t tag = *v.serial_tag + 1u;
             if (tag == 0u) tag = 1u;
             *v.serial_tag = tag;
@@ -1220,9 +1229,16 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             continue;
         }
         const uint32_t tag = sh_tag;
-        // A_w and the partner-box reach only in warps that hold a member
-        const bool member_warp = (tid & ~31) < n;
-        const double Aw = !member_warp ? 0.0 : (v.centring == 1 ? uniform_aw(v, lam) : dvd(mul(v.A0, lam), sqr_t((double)n)));
+        // A_w (Eq. 29) and the partner-box reach, formed once by thread 0: on this part every
+        // binary64 instruction of a warp holds the unit for tens of cycles, so the division and
+        // square root are not repeated in every warp that holds a member
+        if (tid == 0) {
+            const double aw = v.centring == 1 ? uniform_aw(v, lam) : dvd(mul(v.A0, lam), sqr_t((double)n));
+            sh_awx[0] = aw;
+            sh_awx[1] = add(v.rc, mul(0.25, aw)) + 1e-9;
+        }
+        __syncthreads();
+        const double Aw = sh_awx[0];
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
         for (int k = tid; k < n; k += NT) {
             int m = v.s_ids[k];
@@ -1249,7 +1265,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         // binary64 positions rounded once, the new one formed from the old one and the binary32
         // displacements), deciding outside the rigorous error band; the binary64 pass decides
         // inside it and in binary64 mode.
-        const double ext = member_warp ? add(v.rc, mul(0.25, Aw)) + 1e-9 : 0.0;
+        const double ext = sh_awx[1];
         const double thr = v.slot_thr[j];
         // old-position difference a - b, minimum image, rounded once to binary32
         auto d32 = [&](double a, double b) {
@@ -1282,7 +1298,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                 int c0[3], nc[3];
                 cell_box(v, lo, hi, c0, nc);
                 for (int a = 0; a < 3; a++) { v.s_box[6 * k + a] = c0[a]; v.s_box[6 * k + 3 + a] = nc[a]; }
-                cnt = nc[0] * nc[1] * nc[2];
+                cnt = v.occ ? nc[1] * nc[2] : nc[0] * nc[1] * nc[2];   // rows (y, z), or cells
             }
             v.s_pre[k] = cnt;
         }
@@ -1311,9 +1327,11 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             __syncthreads();
         }
         // every (member, bead) pair of the partner boxes: each thread takes a contiguous run of
-        // items, with one search for its first member, member data reloaded only when the run
-        // crosses to the next member, and the head of the next item's cell loaded before the
-        // current cell is walked. visit(k, m, q, bead q)
+        // items, with one search for its first member and member data reloaded only when the run
+        // crosses to the next member. With occupancy bits an item is a row (y, z) of a member's
+        // box: its x range is read as occupancy words and only occupied cells are walked (most
+        // cells of a dilute box are empty); otherwise an item is a cell, and the head of the next
+        // item's cell is loaded before the current cell is walked. visit(k, m, q, bead q)
         auto for_pairs = [&](auto&& visit) {
             const int t0 = (int)((int64_t)tid * W / NT), t1 = (int)((int64_t)(tid + 1) * W / NT);
             if (t0 >= t1) return;
@@ -1325,29 +1343,50 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             int kn = lo_k, kn_start = v.s_pre[kn], kn_end = v.s_pre[kn + 1];
             int c0n[3] = {v.s_box[6 * kn], v.s_box[6 * kn + 1], v.s_box[6 * kn + 2]};
             int ncn[3] = {v.s_box[6 * kn + 3], v.s_box[6 * kn + 4], v.s_box[6 * kn + 5]};
-            auto next_cell = [&](int t) {
+            auto advance = [&](int t) {
                 while (t >= kn_end) {
                     kn++;
                     kn_start = kn_end;
                     kn_end = v.s_pre[kn + 1];
                     for (int a = 0; a < 3; a++) { c0n[a] = v.s_box[6 * kn + a]; ncn[a] = v.s_box[6 * kn + 3 + a]; }
                 }
-                return box_cell(v, c0n, ncn, t - kn_start);
             };
-            int h = v.head[next_cell(t0)];
-            int cur_k = kn;
-            for (int t = t0; t < t1; t++) {
-                int hn = -1, nk = cur_k;
-                if (t + 1 < t1) { hn = v.head[next_cell(t + 1)]; nk = kn; }
-                const int m = v.s_ids[cur_k];
+            auto walk = [&](int h, int k, int m) {
                 int guard = 0;
                 for (int q = h; q >= 0;) {
                     const Bead bq = v.bead[q];
                     const int nx = bq.next;
-                    if (q != m) visit(cur_k, m, q, bq);
+                    if (q != m) visit(k, m, q, bq);
                     q = nx;
                     if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
                 }
+            };
+            if (v.occ) {
+                const int Gf = v.Gf;
+                for (int t = t0; t < t1; t++) {
+                    advance(t);
+                    const int r = t - kn_start, m = v.s_ids[kn];
+                    const int y = wrapi(c0n[1] + r % ncn[1], Gf), z = wrapi(c0n[2] + r / ncn[1], Gf);
+                    const uint32_t* row = v.occ + ((size_t)y + (size_t)Gf * z) * v.occ_w;
+                    const int rowcell = Gf * (y + Gf * z), x0 = wrapi(c0n[0], Gf);
+                    // the x range [x0, x0 + nc) as at most two pieces inside [0, Gf)
+                    for (int piece = 0; piece < 2; piece++) {
+                        const int xa = piece == 0 ? x0 : 0;
+                        const int xb = piece == 0 ? min(x0 + ncn[0], Gf) : x0 + ncn[0] - Gf;
+                        for (int wi = xa >> 5; xa < xb && wi <= (xb - 1) >> 5; wi++)
+                            for (uint32_t bits = occ_masked(row[wi], xa, xb, wi); bits; bits &= bits - 1u)
+                                walk(v.head[rowcell + (wi << 5) + __ffs(bits) - 1], kn, m);
+                    }
+                }
+                return;
+            }
+            advance(t0);
+            int h = v.head[box_cell(v, c0n, ncn, t0 - kn_start)];
+            int cur_k = kn;
+            for (int t = t0; t < t1; t++) {
+                int hn = -1, nk = cur_k;
+                if (t + 1 < t1) { advance(t + 1); hn = v.head[box_cell(v, c0n, ncn, t + 1 - kn_start)]; nk = kn; }
+                walk(h, cur_k, v.s_ids[cur_k]);
                 h = hn;
                 cur_k = nk;
             }
@@ -1402,6 +1441,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                 }
             }
             if (eps_on) {
+                const float rc2p = P32.rc2 * 1.0001f;
                 int mk = -1;
                 double o[3] = {0.0, 0.0, 0.0};
                 float dlm[3] = {0.0f, 0.0f, 0.0f}, mh[3] = {0.0f, 0.0f, 0.0f}, ml[3] = {0.0f, 0.0f, 0.0f};
@@ -1437,6 +1477,11 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                     if (un != 0.0f || uo != 0.0f || mn != 0.0f || mo != 0.0f) {
                         a32 += un - uo; m32 += mn + mo; T += 2;
                         if (!member) pe++;
+                    }
+                    // within the cutoff with a margin far above the binary32 error of r^2
+                    if (rn < rc2p || ro < rc2p) {
+                        const int ip = atomicAdd(&sh_np, 1);
+                        if (ip < serial_pair_cap<PREC, NT>()) sh_pairs[ip] = make_int2(k, q);
                     }
                 });
             }
@@ -1491,7 +1536,24 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                     dU += U_bond(P, r2n) - U_bond(P, r2o);
                 }
             }
-            if (eps_on) {
+            // the pairs the binary32 pass listed (mixed precision, list complete), else all pairs
+            const int npairs = serial_pair_cap<PREC, NT>() > 0 ? sh_np : 1;
+            if (eps_on && npairs <= serial_pair_cap<PREC, NT>()) {
+                for (int ip = tid; ip < npairs; ip += NT) {
+                    const int2 pr = sh_pairs[ip];
+                    const int k = pr.x, m = v.s_ids[k], q = pr.y;
+                    const Bead bm = v.bead[m], bq = v.bead[q];
+                    const double nw[3] = {v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]};
+                    double qn[3] = {bq.x, bq.y, bq.z};
+                    if (bq.mark == tag) {
+                        const int sq = v.s_slot[q];
+                        qn[0] = v.s_new[3 * sq]; qn[1] = v.s_new[3 * sq + 1]; qn[2] = v.s_new[3 * sq + 2];
+                    }
+                    const double r2n = norm2(mi(nw[0] - qn[0], L, hL), mi(nw[1] - qn[1], L, hL), mi(nw[2] - qn[2], L, hL));
+                    const double r2o = norm2(mi(bm.x - bq.x, L, hL), mi(bm.y - bq.y, L, hL), mi(bm.z - bq.z, L, hL));
+                    if (r2n < P.rc2 || r2o < P.rc2) dU += U_wca(P, r2n) - U_wca(P, r2o);
+                }
+            } else if (eps_on) {
                 int mk = -1;
                 double o[3] = {0.0, 0.0, 0.0}, nw[3] = {0.0, 0.0, 0.0};
                 for_pairs([&](int k, int m, int q, const Bead& bq) {
@@ -2095,14 +2157,14 @@ int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, c
         launched += 3;
     }
     if (g.serial_threads <= 32) {
-        if (g.prec_mask & 1) k_serial<0, 32><<<grid, 32, 0, s>>>(d, l);
-        if (g.prec_mask & 2) k_serial<1, 32><<<grid, 32, 0, s>>>(d, l);
+        if (g.prec_mask & 1) k_serial<0, 32><<<grid, 32, serial_pair_cap<0, 32>() * sizeof(int2), s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 32><<<grid, 32, serial_pair_cap<1, 32>() * sizeof(int2), s>>>(d, l);
     } else if (g.serial_threads <= 128) {
-        if (g.prec_mask & 1) k_serial<0, 128><<<grid, 128, 0, s>>>(d, l);
-        if (g.prec_mask & 2) k_serial<1, 128><<<grid, 128, 0, s>>>(d, l);
+        if (g.prec_mask & 1) k_serial<0, 128><<<grid, 128, serial_pair_cap<0, 128>() * sizeof(int2), s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 128><<<grid, 128, serial_pair_cap<1, 128>() * sizeof(int2), s>>>(d, l);
     } else {
-        if (g.prec_mask & 1) k_serial<0, 512><<<grid, 512, 0, s>>>(d, l);
-        if (g.prec_mask & 2) k_serial<1, 512><<<grid, 512, 0, s>>>(d, l);
+        if (g.prec_mask & 1) k_serial<0, 512><<<grid, 512, serial_pair_cap<0, 512>() * sizeof(int2), s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 512><<<grid, 512, serial_pair_cap<1, 512>() * sizeof(int2), s>>>(d, l);
     }
     return launched;
 }
@@ -3630,6 +3692,12 @@ void prepare_staged(const GroupDims& g) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
+    static bool serial_opened[64] = {false};
+    if (!serial_opened[dev]) {
+        cudaFuncSetAttribute(k_serial<1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(serial_pair_cap<1, 512>() * sizeof(int2)));
+        serial_opened[dev] = true;
+    }
     if (g.smem_maxN > 0) {
         const int sm = (int)smem_serial_bytes(g.smem_maxN);
         if ((g.prec_mask & 1) && sm > g_serial_smem[dev][0]) {
