@@ -1050,6 +1050,14 @@ namespace wmcd {
 // in its mixed-precision 512-thread form, the one lone simulations use; other forms walk again)
 constexpr int kSerialPairCap = 12288;
 template <int PREC, int NT> __host__ __device__ constexpr int serial_pair_cap() { return (PREC == 1 && NT >= 512) ? kSerialPairCap : 0; }
+// support members the gather keeps in shared memory (the 512-thread forms): written there by the
+// few lanes that find a member, then to the global arrays in whole warps by the displacement
+// pass; single-lane global stores from the gather held the block's memory pipe ~37k cycles a move
+constexpr int kSerialMemCap = 2048;
+template <int NT> __host__ __device__ constexpr int serial_mem_cap() { return NT >= 512 ? kSerialMemCap : 0; }
+template <int PREC, int NT> __host__ __device__ constexpr size_t serial_dyn_bytes() {
+    return (size_t)serial_mem_cap<NT>() * (4 * sizeof(double) + sizeof(int)) + (size_t)serial_pair_cap<PREC, NT>() * sizeof(int2);
+}
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs, int l) {
     SIM_EXIT_IF(l >= gv.nL || gv.precision != PREC || (((gv.smem_layers | gv.big_layers) >> l) & 1))
@@ -1059,9 +1067,13 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     const int M = v.counts[l];
     const int use_list = v.layer[l].G > 0;
     __shared__ double sh_b[3], sh_p[3], sh_carry, sh_awx[2];
-    // pairs within the WCA cutoff (old or new) found by the binary32 pass, for a binary64 pass
-    // that then visits only those (kSerialPairCap in dynamic shared memory; more: full walk)
-    extern __shared__ __align__(16) int2 sh_pairs[];
+    // dynamic shared memory: support offsets (4 per member) and ids of the first members, then
+    // the pairs within the WCA cutoff (old or new) found by the binary32 pass, for a binary64
+    // pass that then visits only those (more than the capacity: the full walk again)
+    extern __shared__ __align__(16) double sh_dyn[];
+    double* const sm_d = sh_dyn;
+    int2* const sh_pairs = (int2*)(sh_dyn + 4 * serial_mem_cap<NT>());
+    int* const sm_ids = (int*)(sh_pairs + serial_pair_cap<PREC, NT>());
     __shared__ int sh_np;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total, sh_need64;
@@ -1138,8 +1150,11 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             double d2 = norm2(d0, d1, d2c);
             if (d2 < lam2) {
                 int idx = atomicAdd(&sh_n, 1);
-                v.s_ids[idx] = m;
-                v.s_d[4 * idx] = d0; v.s_d[4 * idx + 1] = d1; v.s_d[4 * idx + 2] = d2c; v.s_d[4 * idx + 3] = d2;
+                int* ids = v.s_ids;
+                double* dd = v.s_d;
+                if (idx < serial_mem_cap<NT>()) { ids = sm_ids; dd = sm_d; }
+                ids[idx] = m;
+                dd[4 * idx] = d0; dd[4 * idx + 1] = d1; dd[4 * idx + 2] = d2c; dd[4 * idx + 3] = d2;
             }
         };
         // four independent loads in flight per thread (the shadows of four beads, or the heads
@@ -1241,11 +1256,14 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         const double Aw = sh_awx[0];
         const double p[3] = {sh_p[0], sh_p[1], sh_p[2]};
         for (int k = tid; k < n; k += NT) {
-            int m = v.s_ids[k];
+            const bool in_sm = k < serial_mem_cap<NT>();
+            const double* dd = in_sm ? sm_d : v.s_d;
+            const int m = in_sm ? sm_ids[k] : v.s_ids[k];
+            if (in_sm) v.s_ids[k] = m;           // the later passes read the global arrays
             v.bead[m].mark = tag;
             v.s_slot[m] = k;
-            double d[3] = {v.s_d[4 * k], v.s_d[4 * k + 1], v.s_d[4 * k + 2]}, dl[3];
-            if (PREC == 0) wavelet_disp64(d, v.s_d[4 * k + 3], lam, Aw, p, dl);
+            double d[3] = {dd[4 * k], dd[4 * k + 1], dd[4 * k + 2]}, dl[3];
+            if (PREC == 0) wavelet_disp64(d, dd[4 * k + 3], lam, Aw, p, dl);
             else wavelet_disp32(d, lam, Aw, p, dl);
             const double o[3] = {v.bead[m].x, v.bead[m].y, v.bead[m].z};
             int im[3] = {0, 0, 0};
@@ -2157,14 +2175,14 @@ int launch_serial(const SimView* d, const GroupDims& g, int l, cudaStream_t s, c
         launched += 3;
     }
     if (g.serial_threads <= 32) {
-        if (g.prec_mask & 1) k_serial<0, 32><<<grid, 32, serial_pair_cap<0, 32>() * sizeof(int2), s>>>(d, l);
-        if (g.prec_mask & 2) k_serial<1, 32><<<grid, 32, serial_pair_cap<1, 32>() * sizeof(int2), s>>>(d, l);
+        if (g.prec_mask & 1) k_serial<0, 32><<<grid, 32, serial_dyn_bytes<0, 32>(), s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 32><<<grid, 32, serial_dyn_bytes<1, 32>(), s>>>(d, l);
     } else if (g.serial_threads <= 128) {
-        if (g.prec_mask & 1) k_serial<0, 128><<<grid, 128, serial_pair_cap<0, 128>() * sizeof(int2), s>>>(d, l);
-        if (g.prec_mask & 2) k_serial<1, 128><<<grid, 128, serial_pair_cap<1, 128>() * sizeof(int2), s>>>(d, l);
+        if (g.prec_mask & 1) k_serial<0, 128><<<grid, 128, serial_dyn_bytes<0, 128>(), s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 128><<<grid, 128, serial_dyn_bytes<1, 128>(), s>>>(d, l);
     } else {
-        if (g.prec_mask & 1) k_serial<0, 512><<<grid, 512, serial_pair_cap<0, 512>() * sizeof(int2), s>>>(d, l);
-        if (g.prec_mask & 2) k_serial<1, 512><<<grid, 512, serial_pair_cap<1, 512>() * sizeof(int2), s>>>(d, l);
+        if (g.prec_mask & 1) k_serial<0, 512><<<grid, 512, serial_dyn_bytes<0, 512>(), s>>>(d, l);
+        if (g.prec_mask & 2) k_serial<1, 512><<<grid, 512, serial_dyn_bytes<1, 512>(), s>>>(d, l);
     }
     return launched;
 }
@@ -3694,8 +3712,8 @@ void prepare_staged(const GroupDims& g) {
     if (dev < 0 || dev >= 64) dev = 0;
     static bool serial_opened[64] = {false};
     if (!serial_opened[dev]) {
-        cudaFuncSetAttribute(k_serial<1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(serial_pair_cap<1, 512>() * sizeof(int2)));
+        cudaFuncSetAttribute(k_serial<1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)serial_dyn_bytes<1, 512>());
+        cudaFuncSetAttribute(k_serial<0, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)serial_dyn_bytes<0, 512>());
         serial_opened[dev] = true;
     }
     if (g.smem_maxN > 0) {

@@ -1,8 +1,8 @@
 """GPU parity of the second colouring of deferred slots against the oracle, slot by slot: the
 slots a coloured layer l (bit l of level2) defers are bucketed again on K floor(G / 2K) coarse
 cells (by their bead, or centre, as it is then) and run in that grid's colour phases with
-supports up to 256 beads; only what this second colouring defers as well runs serially. Trace flags: 4 = deferred by the
-first colouring, 8 = by the second as well."""
+supports up to 256 beads; only what this second colouring defers as well runs serially. Trace
+flags: 4 = deferred by the first colouring, 8 = by the second as well."""
 import numpy as np
 import pytest
 
