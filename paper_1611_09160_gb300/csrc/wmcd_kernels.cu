@@ -372,11 +372,40 @@ __global__ void k_bucket_count(const SimView* __restrict__ vs, int l) {
     v.slot_key[t] = key;
     atomicAdd(&v.q_count[key], 1);
 }
-// exclusive scan of n ints by one block per simulation: mode 0 = bucket counts of layer l
-// (G^3 keys), mode 1 = region counts of layer l (Q^3 queues). With heavy_lo >= 0 (mode 1) it
-// also lists the queues of the colour phase that have slots and more than heavy_lo beads in
-// their region, in no particular order: those with at most heavy_mid beads from the front of
-// hq_list, the others from its back, and resets the two lists' work counters.
+// Exclusive prefix of one value per thread over a block of 1,024 threads (32 warps): a shuffle
+// scan per warp, the warp totals scanned by warp 0; two block barriers. *total receives the sum.
+__device__ __forceinline__ int block_excl_scan(int x, int* s_w, int* total) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int c = s_w[lane];
+        int ci = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, ci, o);
+            if (lane >= o) ci += y;
+        }
+        s_w[lane] = ci - c;
+        if (lane == 31) s_w[32] = ci;
+    }
+    __syncthreads();
+    *total = s_w[32];
+    return s_w[wid] + incl - x;
+}
+constexpr int kScanPer = 8;   // consecutive entries per thread in the single-block scans
+
+// exclusive scan of n ints by one block of 1,024 threads per simulation: mode 0 = bucket counts
+// of layer l (G^3 keys), mode 1 = region counts of layer l (Q^3 queues); each thread takes
+// kScanPer consecutive entries of a chunk. With heavy_lo >= 0 (mode 1) it also lists the queues
+// of the colour phase that have slots and more than heavy_lo beads in their region, in no
+// particular order: those with at most heavy_mid beads from the front of hq_list, the others
+// from its back, and resets the two lists' work counters.
 __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l, int colour, int heavy_lo, int heavy_mid) {
     SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
@@ -385,25 +414,22 @@ __global__ void k_scan(const SimView* __restrict__ vs, int mode, int l, int colo
     const int n = mode == 0 ? G * G * G : Q * Q * Q;
     const int* in = mode == 0 ? v.q_count : v.rcount;
     int* out = mode == 0 ? v.q_start : v.rstart;
-    __shared__ int part[1024];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += 1024) {
-        int i = base + threadIdx.x;
-        int x = i < n ? in[i] : 0;
-        part[threadIdx.x] = x;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            int y = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-            __syncthreads();
-            part[threadIdx.x] += y;
-            __syncthreads();
+    __shared__ int s_w[33];
+    int carry = 0;
+    for (int base = 0; base < n; base += kScanPer * 1024) {
+        const int i0 = base + kScanPer * (int)threadIdx.x;
+        int x[kScanPer], sum = 0;
+#pragma unroll
+        for (int u = 0; u < kScanPer; u++) { x[u] = i0 + u < n ? in[i0 + u] : 0; sum += x[u]; }
+        int total;
+        int pre = carry + block_excl_scan(sum, s_w, &total);
+#pragma unroll
+        for (int u = 0; u < kScanPer; u++) {
+            if (i0 + u < n) out[i0 + u] = pre;
+            pre += x[u];
         }
-        if (i < n) out[i] = carry + part[threadIdx.x] - x;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += part[1023];
-        __syncthreads();
+        carry += total;
+        __syncthreads();                          // s_w is rewritten by the next chunk
     }
     if (mode == 1 && heavy_lo >= 0) {
         __shared__ int hc[2];
@@ -478,38 +504,26 @@ __global__ void k_defer_compact(const SimView* __restrict__ vs, int l) {
     SIM_EXIT_IF(!sched_on(gv, l))
     SIM_PROLOGUE
     if (!sched_on(v, l)) return;
-    // (a second colouring's entries are the first one's deferred slots: read before the barrier
+    // (a second colouring's entries are the first one's deferred slots: read before the barriers
     // below, ahead of the new count written at the end)
     const int M = sched_count(v, l);
-    // the deferred slots in schedule order: per chunk of 1024 a vote per warp, an exclusive prefix
-    // of the 32 warp counts, and each deferred slot's place from the bits below it in its warp;
-    // chunks without a deferred slot (nearly all) cost one block vote
-    __shared__ int wpre[32], wtot, carry;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < M; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int x = (i < M && v.defer[i]) ? 1 : 0;
-        if (!__syncthreads_or(x)) continue;
-        const unsigned b = __ballot_sync(0xffffffffu, x);
-        if (lane == 0) wpre[wid] = __popc(b);
-        __syncthreads();
-        if (wid == 0) {
-            const int c = wpre[lane];
-            int incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            wpre[lane] = incl - c;
-            if (lane == 31) wtot = incl;
-        }
-        __syncthreads();
-        if (x) v.serial_list[carry + wpre[wid] + __popc(b & ((1u << lane) - 1u))] = v.q_slots[i];
-        __syncthreads();
-        if (threadIdx.x == 0) carry += wtot;
-        __syncthreads();
+    // the deferred slots in schedule order: each thread takes kScanPer consecutive entries of a
+    // chunk, a block prefix of the per-thread counts places them; chunks without a deferred slot
+    // (nearly all) cost one block vote
+    __shared__ int s_w[33];
+    int carry = 0;
+    for (int base = 0; base < M; base += kScanPer * 1024) {
+        const int i0 = base + kScanPer * (int)threadIdx.x;
+        unsigned f = 0u;
+#pragma unroll
+        for (int u = 0; u < kScanPer; u++)
+            if (i0 + u < M && v.defer[i0 + u]) f |= 1u << u;
+        if (!__syncthreads_or(f != 0u)) continue;
+        int total;
+        int pos = carry + block_excl_scan(__popc(f), s_w, &total);
+        for (; f; f &= f - 1u) v.serial_list[pos++] = v.q_slots[i0 + __ffs(f) - 1];
+        carry += total;
+        __syncthreads();                          // s_w is rewritten by the next chunk
     }
     if (threadIdx.x == 0) *v.serial_count = carry;
 }
