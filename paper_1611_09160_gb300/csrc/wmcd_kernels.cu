@@ -1085,6 +1085,11 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     // the pairs within the WCA cutoff (old or new) found by the binary32 pass, for a binary64
     // pass that then visits only those (more than the capacity: the full walk again)
     extern __shared__ __align__(16) double sh_dyn[];
+    // occupied cells of the ball found by the row pass, walked one per thread afterwards (a row
+    // of a dense region holds tens of beads: one thread walking it is the search's longest chain)
+    constexpr int kCellCap = NT >= 512 ? 4096 : 1;
+    __shared__ int sh_cells[kCellCap];
+    __shared__ int sh_ncell;
     double* const sm_d = sh_dyn;
     int2* const sh_pairs = (int2*)(sh_dyn + 4 * serial_mem_cap<NT>());
     int* const sm_ids = (int*)(sh_pairs + serial_pair_cap<PREC, NT>());
@@ -1141,6 +1146,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             sh_total = 0;
             sh_nch = 0;
             sh_np = 0;
+            sh_ncell = 0;
             uint32_t tag = *v.serial_tag + 1u;
             if (tag == 0u) tag = 1u;
             *v.serial_tag = tag;
@@ -1206,14 +1212,30 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                         const int lo = max(a - (wi << 5), 0), hi = min(b - (wi << 5), 32);
                         bits &= (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
                         for (; bits; bits &= bits - 1u) {
-                            int guard = 0;
-                            for (int q = v.head[rowcell + (wi << 5) + __ffs(bits) - 1]; q >= 0;) {
+                            const int cell = rowcell + (wi << 5) + __ffs(bits) - 1;
+                            const int slot = NT >= 512 ? atomicAdd(&sh_ncell, 1) : kCellCap;
+                            if (slot < kCellCap) { sh_cells[slot] = cell; continue; }
+                            int guard = 0;             // list full: walked here
+                            for (int q = v.head[cell]; q >= 0;) {
                                 const Bead bb = v.bead[q];
                                 if (screened(v.bf[q])) consider_exact(q, bb);
                                 q = bb.next;
                                 if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
                             }
                         }
+                    }
+                }
+            }
+            if (NT >= 512) {
+                __syncthreads();
+                const int nlist = min(sh_ncell, kCellCap);
+                for (int i = tid; i < nlist; i += NT) {
+                    int guard = 0;
+                    for (int q = v.head[sh_cells[i]]; q >= 0;) {
+                        const Bead bb = v.bead[q];
+                        if (screened(v.bf[q])) consider_exact(q, bb);
+                        q = bb.next;
+                        if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
                     }
                 }
             }
