@@ -1062,15 +1062,19 @@ namespace wmcd {
 
 // pairs a serial move keeps for its binary64 recheck (dynamic shared memory of the serial kernel
 // in its mixed-precision 512-thread form, the one lone simulations use; other forms walk again)
-constexpr int kSerialPairCap = 12288;
+constexpr int kSerialPairCap = 8192;
 template <int PREC, int NT> __host__ __device__ constexpr int serial_pair_cap() { return (PREC == 1 && NT >= 512) ? kSerialPairCap : 0; }
 // support members the gather keeps in shared memory (the 512-thread forms): written there by the
 // few lanes that find a member, then to the global arrays in whole warps by the displacement
 // pass; single-lane global stores from the gather held the block's memory pipe ~37k cycles a move
 constexpr int kSerialMemCap = 2048;
 template <int NT> __host__ __device__ constexpr int serial_mem_cap() { return NT >= 512 ? kSerialMemCap : 0; }
+// (member, occupied partner cell) entries of a move's pair search, walked one per thread
+constexpr int kSerialEntCap = 4096;
+template <int NT> __host__ __device__ constexpr int serial_ent_cap() { return NT >= 512 ? kSerialEntCap : 0; }
 template <int PREC, int NT> __host__ __device__ constexpr size_t serial_dyn_bytes() {
-    return (size_t)serial_mem_cap<NT>() * (4 * sizeof(double) + sizeof(int)) + (size_t)serial_pair_cap<PREC, NT>() * sizeof(int2);
+    return (size_t)serial_mem_cap<NT>() * (4 * sizeof(double) + sizeof(int)) + (size_t)serial_pair_cap<PREC, NT>() * sizeof(int2) +
+           (size_t)serial_ent_cap<NT>() * 2 * sizeof(int);
 }
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs, int l) {
@@ -1093,6 +1097,9 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     double* const sm_d = sh_dyn;
     int2* const sh_pairs = (int2*)(sh_dyn + 4 * serial_mem_cap<NT>());
     int* const sm_ids = (int*)(sh_pairs + serial_pair_cap<PREC, NT>());
+    int* const ent_k = sm_ids + serial_mem_cap<NT>();
+    int* const ent_c = ent_k + serial_ent_cap<NT>();
+    __shared__ int sh_nent;
     __shared__ int sh_np;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total, sh_need64;
@@ -1147,6 +1154,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             sh_nch = 0;
             sh_np = 0;
             sh_ncell = 0;
+            sh_nent = 0;
             uint32_t tag = *v.serial_tag + 1u;
             if (tag == 0u) tag = 1u;
             *v.serial_tag = tag;
@@ -1380,13 +1388,9 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
             if (tid == 0) v.s_pre[n] = W;
             __syncthreads();
         }
-        // every (member, bead) pair of the partner boxes: each thread takes a contiguous run of
-        // items, with one search for its first member and member data reloaded only when the run
-        // crosses to the next member. With occupancy bits an item is a row (y, z) of a member's
-        // box: its x range is read as occupancy words and only occupied cells are walked (most
-        // cells of a dilute box are empty); otherwise an item is a cell, and the head of the next
-        // item's cell is loaded before the current cell is walked. visit(k, m, q, bead q)
-        auto for_pairs = [&](auto&& visit) {
+        // each thread takes a contiguous run of items, with one search for its first member and
+        // member data reloaded only when the run crosses to the next member
+        auto run_items = [&](auto&& item) {
             const int t0 = (int)((int64_t)tid * W / NT), t1 = (int)((int64_t)(tid + 1) * W / NT);
             if (t0 >= t1) return;
             int lo_k = 0, hi_k = n - 1;                 // last member with s_pre <= t0
@@ -1405,17 +1409,22 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                     for (int a = 0; a < 3; a++) { c0n[a] = v.s_box[6 * kn + a]; ncn[a] = v.s_box[6 * kn + 3 + a]; }
                 }
             };
-            auto walk = [&](int h, int k, int m) {
-                int guard = 0;
-                for (int q = h; q >= 0;) {
-                    const Bead bq = v.bead[q];
-                    const int nx = bq.next;
-                    if (q != m) visit(k, m, q, bq);
-                    q = nx;
-                    if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
-                }
-            };
-            if (v.occ) {
+            item(t0, t1, advance, kn, kn_start, c0n, ncn);
+        };
+        auto walk = [&](auto&& visit, int h, int k, int m) {
+            int guard = 0;
+            for (int q = h; q >= 0;) {
+                const Bead bq = v.bead[q];
+                const int nx = bq.next;
+                if (q != m) visit(k, m, q, bq);
+                q = nx;
+                if (++guard > kMaxWalk) { set_err(v, E_WALK); break; }
+            }
+        };
+        // with occupancy bits an item is a row (y, z) of a member's partner box, whose x range is
+        // read as occupancy words: cellfn(k, m, cell) for each occupied cell
+        auto for_cells = [&](auto&& cellfn) {
+            run_items([&](int t0, int t1, auto& advance, int& kn, int& kn_start, int* c0n, int* ncn) {
                 const int Gf = v.Gf;
                 for (int t = t0; t < t1; t++) {
                     advance(t);
@@ -1429,21 +1438,51 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                         const int xb = piece == 0 ? min(x0 + ncn[0], Gf) : x0 + ncn[0] - Gf;
                         for (int wi = xa >> 5; xa < xb && wi <= (xb - 1) >> 5; wi++)
                             for (uint32_t bits = occ_masked(row[wi], xa, xb, wi); bits; bits &= bits - 1u)
-                                walk(v.head[rowcell + (wi << 5) + __ffs(bits) - 1], kn, m);
+                                cellfn(kn, m, rowcell + (wi << 5) + __ffs(bits) - 1);
                     }
+                }
+            });
+        };
+        // the (member, occupied cell) entries listed once, then walked one per thread: a run of
+        // items in a dense region walked by one thread was the pass's longest chain
+        int nent = 0;
+        bool listed = false;
+        if (eps_on && v.occ && serial_ent_cap<NT>() > 0) {
+            for_cells([&](int k, int m, int cell) {
+                const int i = atomicAdd(&sh_nent, 1);
+                if (i < serial_ent_cap<NT>()) { ent_k[i] = k; ent_c[i] = cell; }
+            });
+            __syncthreads();
+            nent = sh_nent;
+            listed = nent <= serial_ent_cap<NT>();
+        }
+        // every (member, bead) pair of the partner boxes: visit(k, m, q, bead q)
+        auto for_pairs = [&](auto&& visit) {
+            if (listed) {
+                for (int i = tid; i < nent; i += NT) {
+                    const int k = ent_k[i];
+                    walk(visit, v.head[ent_c[i]], k, v.s_ids[k]);
                 }
                 return;
             }
-            advance(t0);
-            int h = v.head[box_cell(v, c0n, ncn, t0 - kn_start)];
-            int cur_k = kn;
-            for (int t = t0; t < t1; t++) {
-                int hn = -1, nk = cur_k;
-                if (t + 1 < t1) { advance(t + 1); hn = v.head[box_cell(v, c0n, ncn, t + 1 - kn_start)]; nk = kn; }
-                walk(h, cur_k, v.s_ids[cur_k]);
-                h = hn;
-                cur_k = nk;
+            if (v.occ) {
+                for_cells([&](int k, int m, int cell) { walk(visit, v.head[cell], k, m); });
+                return;
             }
+            // an item is a cell; the head of the next item's cell is loaded before the current
+            // cell is walked
+            run_items([&](int t0, int t1, auto& advance, int& kn, int& kn_start, int* c0n, int* ncn) {
+                advance(t0);
+                int h = v.head[box_cell(v, c0n, ncn, t0 - kn_start)];
+                int cur_k = kn;
+                for (int t = t0; t < t1; t++) {
+                    int hn = -1, nk = cur_k;
+                    if (t + 1 < t1) { advance(t + 1); hn = v.head[box_cell(v, c0n, ncn, t + 1 - kn_start)]; nk = kn; }
+                    walk(visit, h, cur_k, v.s_ids[cur_k]);
+                    h = hn;
+                    cur_k = nk;
+                }
+            });
         };
         bool need64 = PREC == 0;
         if (PREC == 1) {
