@@ -1100,6 +1100,10 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
     int* const ent_k = sm_ids + serial_mem_cap<NT>();
     int* const ent_c = ent_k + serial_ent_cap<NT>();
     __shared__ int sh_nent;
+    // beads of an accepted move that change fine cell: (bead, old cell, new cell), relinked by
+    // one thread per old cell and then one per new cell (a cell's beads in list order)
+    constexpr int kChCap = NT >= 512 ? 1024 : 1;
+    __shared__ int sc_m[kChCap], sc_oc[kChCap], sc_nc[kChCap];
     __shared__ int sh_np;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_n, sh_nch, sh_acc, sh_brute, sh_c0[3], sh_nc[3], sh_total, sh_need64;
@@ -1702,15 +1706,53 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
                 if (oc != ncl) {
                     int idx = atomicAdd(&sh_nch, 1);
                     v.s_changed[3 * idx] = m; v.s_changed[3 * idx + 1] = oc; v.s_changed[3 * idx + 2] = ncl;
+                    if (idx < kChCap) { sc_m[idx] = m; sc_oc[idx] = oc; sc_nc[idx] = ncl; }
                 }
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            for (int c = 0; c < sh_nch; c++) {
+        const int nch = sh_nch;
+        if (NT >= 512 && nch > 1 && nch <= kChCap) {
+            // unlinks of one cell's leaving beads by one thread, cells side by side; then the
+            // same for the beads each cell receives, pushed in list order (the lists end as the
+            // one-at-a-time relinks leave them)
+            for (int c = tid; c < nch; c += NT) {
+                const int oc = sc_oc[c];
+                bool first = true;
+                for (int e = 0; e < c && first; e++) first = sc_oc[e] != oc;
+                if (!first) continue;
+                for (int e = c; e < nch; e++) {
+                    if (sc_oc[e] != oc) continue;
+                    const int m = sc_m[e], pr = v.prev[m], nx = v.bead[m].next;
+                    if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+                    if (nx >= 0) v.prev[nx] = pr;
+                    if (pr < 0 && nx < 0) occ_bit(v, oc, false);
+                }
+            }
+            __syncthreads();
+            for (int c = tid; c < nch; c += NT) {
+                const int ncl = sc_nc[c];
+                bool first = true;
+                for (int e = 0; e < c && first; e++) first = sc_nc[e] != ncl;
+                if (!first) continue;
+                for (int e = c; e < nch; e++) {
+                    if (sc_nc[e] != ncl) continue;
+                    const int m = sc_m[e], hd = v.head[ncl];
+                    v.bead[m].next = hd;
+                    v.prev[m] = -1;
+                    if (hd >= 0) v.prev[hd] = m;
+                    v.head[ncl] = m;
+                }
+                occ_bit(v, ncl, true);
+            }
+            __syncthreads();
+        } else if (tid == 0) {
+            for (int c = 0; c < nch; c++) {
                 int m = v.s_changed[3 * c], oc = v.s_changed[3 * c + 1], ncl = v.s_changed[3 * c + 2];
                 relink(v, m, oc, ncl);
             }
+        }
+        if (tid == 0) {
             att++;
             bu += n;
             if (acc) { acc_n++; moved_n += n; }
