@@ -84,6 +84,7 @@ WMCD_HD int layer_real(int l) { return l >= kLevel2 ? l - kLevel2 : l; }
 struct BigMove {
     int active;                  // this slot exists in the current sweep
     int j, n, acc;               // slot, support size (gathered), decision
+    int nch;                     // members of the accepted move that change fine cell
     uint32_t tag;                // support mark of this move
     double lam, thr, b[3], p[3];
 };

@@ -132,6 +132,43 @@ __device__ __forceinline__ void relink(const SimView& v, int m, int oc, int ncl)
     occ_bit(v, ncl, true);
 }
 
+// The cell changes of one accepted move, (bead, old cell, new cell) in cm/co/cn, applied by the
+// nt threads of a block together: one thread per old cell unlinks that cell's leaving beads,
+// then one thread per new cell pushes its arriving beads in entry order, so the lists end as
+// the one-at-a-time relinks leave them. Every thread of the block calls it (two barriers).
+__device__ void grouped_relink(const SimView& v, const int* cm, const int* co, const int* cn, int nch, int tid, int nt) {
+    for (int c = tid; c < nch; c += nt) {
+        const int oc = co[c];
+        bool first = true;
+        for (int e = 0; e < c && first; e++) first = co[e] != oc;
+        if (!first) continue;
+        for (int e = c; e < nch; e++) {
+            if (co[e] != oc) continue;
+            const int m = cm[e], pr = v.prev[m], nx = v.bead[m].next;
+            if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
+            if (nx >= 0) v.prev[nx] = pr;
+            if (pr < 0 && nx < 0) occ_bit(v, oc, false);
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < nch; c += nt) {
+        const int ncl = cn[c];
+        bool first = true;
+        for (int e = 0; e < c && first; e++) first = cn[e] != ncl;
+        if (!first) continue;
+        for (int e = c; e < nch; e++) {
+            if (cn[e] != ncl) continue;
+            const int m = cm[e], hd = v.head[ncl];
+            v.bead[m].next = hd;
+            v.prev[m] = -1;
+            if (hd >= 0) v.prev[hd] = m;
+            v.head[ncl] = m;
+        }
+        occ_bit(v, ncl, true);
+    }
+    __syncthreads();
+}
+
 // ======================================================================================
 // Cell list: per fine cell a singly linked list through Bead::next plus prev[] for O(1)
 // removal. Built in canonical order (ascending bead id within a cell) so runs repeat.
@@ -1713,39 +1750,7 @@ __global__ void __launch_bounds__(NT, 1) k_serial(const SimView* __restrict__ vs
         __syncthreads();
         const int nch = sh_nch;
         if (NT >= 512 && nch > 1 && nch <= kChCap) {
-            // unlinks of one cell's leaving beads by one thread, cells side by side; then the
-            // same for the beads each cell receives, pushed in list order (the lists end as the
-            // one-at-a-time relinks leave them)
-            for (int c = tid; c < nch; c += NT) {
-                const int oc = sc_oc[c];
-                bool first = true;
-                for (int e = 0; e < c && first; e++) first = sc_oc[e] != oc;
-                if (!first) continue;
-                for (int e = c; e < nch; e++) {
-                    if (sc_oc[e] != oc) continue;
-                    const int m = sc_m[e], pr = v.prev[m], nx = v.bead[m].next;
-                    if (pr >= 0) v.bead[pr].next = nx; else v.head[oc] = nx;
-                    if (nx >= 0) v.prev[nx] = pr;
-                    if (pr < 0 && nx < 0) occ_bit(v, oc, false);
-                }
-            }
-            __syncthreads();
-            for (int c = tid; c < nch; c += NT) {
-                const int ncl = sc_nc[c];
-                bool first = true;
-                for (int e = 0; e < c && first; e++) first = sc_nc[e] != ncl;
-                if (!first) continue;
-                for (int e = c; e < nch; e++) {
-                    if (sc_nc[e] != ncl) continue;
-                    const int m = sc_m[e], hd = v.head[ncl];
-                    v.bead[m].next = hd;
-                    v.prev[m] = -1;
-                    if (hd >= 0) v.prev[hd] = m;
-                    v.head[ncl] = m;
-                }
-                occ_bit(v, ncl, true);
-            }
-            __syncthreads();
+            grouped_relink(v, sc_m, sc_oc, sc_nc, nch, tid, NT);
         } else if (tid == 0) {
             for (int c = 0; c < nch; c++) {
                 int m = v.s_changed[3 * c], oc = v.s_changed[3 * c + 1], ncl = v.s_changed[3 * c + 2];
@@ -2654,6 +2659,7 @@ __global__ void k_big_setup(const SimView* __restrict__ vs, int l, int t) {
     B.thr = v.slot_thr[j];
     B.n = 0;
     B.acc = 0;
+    B.nch = 0;
     uint32_t tag = *v.serial_tag + 1u;
     if (tag == 0u) tag = 1u;
     *v.serial_tag = tag;
@@ -2824,9 +2830,15 @@ __global__ void k_big_commit(const SimView* __restrict__ vs, int l) {
     SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active || !gv.big->acc || gv.big->n == 0)
     SIM_PROLOGUE
     const int n = v.big->n;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *v.pw_rebuild = 1;   // the cell lists are rebuilt next
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int m = v.s_ids[k];
+        const Bead ob = v.bead[m];
+        const int oc = cell_lin(v, ob.x, ob.y, ob.z), ncl = cell_lin(v, v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]);
+        if (oc != ncl) {
+            // the cell changes, relinked next (or, beyond what one block relinks, a rebuild)
+            const int idx = atomicAdd(&v.big->nch, 1);
+            v.s_changed[3 * idx] = m; v.s_changed[3 * idx + 1] = oc; v.s_changed[3 * idx + 2] = ncl;
+        }
         put_bead(v.bead, v.bf, m, v.s_new[3 * k], v.s_new[3 * k + 1], v.s_new[3 * k + 2]);
         const int pk = v.s_img[k];
         if (pk != pack_img(0, 0, 0)) {
@@ -2837,6 +2849,25 @@ __global__ void k_big_commit(const SimView* __restrict__ vs, int l) {
     }
 }
 
+// the cell changes of an accepted whole-GPU move relinked by one block, or (more than it holds,
+// or lists left stale) the cell lists rebuilt by the launches after it
+constexpr int kBigRelinkCap = 3072;
+__global__ void __launch_bounds__(1024) k_big_relink(const SimView* __restrict__ vs, int l) {
+    SIM_EXIT_IF(l >= gv.nL || !((gv.big_layers >> l) & 1) || !gv.big->active || !gv.big->acc || gv.big->n == 0)
+    SIM_PROLOGUE
+    const int nch = v.big->nch;
+    // lists a shared-memory serial phase left stale cannot be relinked: rebuilt instead
+    if (nch > kBigRelinkCap || *v.cl_stale) {
+        if (threadIdx.x == 0) *v.pw_rebuild = 1;
+        return;
+    }
+    __shared__ int cm[kBigRelinkCap], co[kBigRelinkCap], cn[kBigRelinkCap];
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        cm[c] = v.s_changed[3 * c]; co[c] = v.s_changed[3 * c + 1]; cn[c] = v.s_changed[3 * c + 2];
+    }
+    __syncthreads();
+    grouped_relink(v, cm, co, cn, nch, threadIdx.x, blockDim.x);
+}
 int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t s) {
     const int gb = (int)gx((g.maxN + 255) / 256, g.S);
     k_big_setup<<<dim3(1, g.S), 32, 0, s>>>(d, l, t);
@@ -2845,8 +2876,9 @@ int launch_big(const SimView* d, const GroupDims& g, int l, int t, cudaStream_t 
     k_big_energy<<<dim3(g.pw_blocks, g.S), 256, 0, s>>>(d, l);
     k_big_decide<<<dim3(1, g.S), 256, 0, s>>>(d, l);
     k_big_commit<<<dim3(gb, g.S), 256, 0, s>>>(d, l);
+    k_big_relink<<<dim3(1, g.S), 1024, 0, s>>>(d, l);
     launch_cl_rebuild(d, g, s, 1);
-    return 9;
+    return 10;
 }
 
 }  // namespace wmcd
