@@ -199,8 +199,9 @@ def oracle_sample(seconds):
     dt = time.perf_counter() - t0
     st = o2.stats()
     desc = (f"first {done} wavelet moves of the first sweep, in schedule order, of the suspension's 1/64 subsample "
-            f"({sub.n_beads:,} beads in L = {sub.box_L:.1f}; sequential C++ FP64 oracle, brute-force neighbour "
-            f"search), {dt:.1f} s")
+            f"({sub.n_beads:,} beads in L = {sub.box_L:.1f}; sequential C++ oracle in its mixed-precision mode: "
+            f"binary32 displacements as the GPU's mixed path, binary64 positions, energies and decisions; "
+            f"brute-force neighbour search), {dt:.1f} s")
     return st.bead_updates, dt, done, st.sim_time, desc
 
 
@@ -230,12 +231,12 @@ def run_reference(args, rank, world):
     value = tot_bu / tot_dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_dt / steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": workload_config(),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"{steps} steps, each the first moves (about {per_step:.0f} s of work, "
                                        f"{tot_moves} moves in all) of a sweep of the suspension's 1/64 subsample, "
-                                       f"after {args.warmup} warm-up samples; sequential C++ FP64 oracle"},
+                                       f"after {args.warmup} warm-up samples; sequential C++ oracle in its mixed-precision mode"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sim_time_per_s": tot_sim / tot_dt}
     print(json.dumps(line), flush=True)
