@@ -58,7 +58,8 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     pos = np.zeros((10, 3))
     cl = np.array([10], np.int32)
     bad = [dict(lambda_max=30.0), dict(lambda_min=0.0), dict(A0=-1.0), dict(colour_K=5), dict(n_cap=257),
-           dict(grid_f=100)]       # L/grid_f below the WCA cutoff
+           dict(grid_f=100),       # L/grid_f below the WCA cutoff
+           dict(acceptance=2), dict(centring=-1), dict(level2=0x10000), dict(level2=-1), dict(planewave_mode=4)]
     for b in bad:
         q = wmcd.make_params(dict(wmcd.default_params(10, 50.0), **b))
         rc = lib.wmcd_create(ctypes.byref(q), pos.ctypes.data, cl.ctypes.data, 1, None, ctypes.byref(h))
