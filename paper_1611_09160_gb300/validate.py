@@ -13,8 +13,11 @@ closed form of the paper, or reports the spectra the paper plots:
 * ``cost_scaling``: bead-updates and wall time per unit simulated time for homogeneous systems
   of growing N at fixed density (Sec. V.F: cost per simulated time ~ N ln N), with the
   algorithmic count against N (1 + c ln(L / (2 lmin))).
+* ``chain_relaxation``: the radius of gyration of N_b = 10 chains relaxing from self-avoiding
+  walks (Sec. VII.A), and in theta solvent (no WCA), started from the ideal-chain equilibrium,
+  its plateau against the exact ideal-chain value (the dynamics must keep that equilibrium).
 
-``python -m paper_1611_09160_gb300.validate --out report.json`` runs all three at full size.
+``python -m paper_1611_09160_gb300.validate --out report.json`` runs them all at full size.
 """
 from __future__ import annotations
 
@@ -170,6 +173,88 @@ def cost_scaling(sizes=(65_536, 262_144, 1_048_576), phi: float = 0.05, sweeps: 
             "fit_max_rel_dev": float(np.max(np.abs(fit - y) / y)), "wall_exponent": float(slope)}
 
 
+def ideal_bond_msd(k: float, r0: float, kT: float = 1.0) -> float:
+    """<b^2> of a harmonic bond U = (k/2)(b - r0)^2 at temperature kT: b has the density
+    b^2 exp(-U/kT) on b > 0 (the bond vector's Boltzmann weight in three dimensions)."""
+    from scipy import integrate
+    w = lambda b: b * b * math.exp(-0.5 * k * (b - r0) ** 2 / kT)
+    hi = r0 + 40.0 * math.sqrt(kT / k)
+    z = integrate.quad(w, 0.0, hi, epsabs=0.0, epsrel=1e-12, limit=200)[0]
+    m2 = integrate.quad(lambda b: b * b * w(b), 0.0, hi, epsabs=0.0, epsrel=1e-12, limit=200)[0]
+    return m2 / z
+
+
+def ideal_chains(n_chains: int, n_b: int, box_L: float, k: float, r0: float, kT: float = 1.0, seed: int = 1):
+    """Chains drawn from the ideal-chain equilibrium of harmonic bonds: independent bond vectors,
+    isotropic, lengths with density b^2 exp(-(k/2)(b - r0)^2 / kT) (sampled through its tabulated
+    distribution function); first beads uniform in the box; positions wrapped into [0, L)."""
+    rng = np.random.default_rng(seed)
+    sd = math.sqrt(kT / k)
+    grid = np.linspace(max(0.0, r0 - 12 * sd), r0 + 12 * sd, 40001)
+    w = grid * grid * np.exp(-0.5 * k * (grid - r0) ** 2 / kT)
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (w[1:] + w[:-1]) * np.diff(grid))])
+    b = np.interp(rng.random((n_chains, n_b - 1)), cdf / cdf[-1], grid)
+    u = rng.normal(size=(n_chains, n_b - 1, 3))
+    u /= np.linalg.norm(u, axis=2, keepdims=True)
+    x0 = rng.random((n_chains, 1, 3)) * box_L
+    x = np.concatenate([x0, x0 + np.cumsum(b[:, :, None] * u, axis=1)], axis=1).reshape(-1, 3)
+    return np.minimum(np.mod(x, box_L), np.nextafter(box_L, 0.0))
+
+
+def chain_relaxation(n_chains: int = 20_000, n_b: int = 10, phi: float = 1e-3, sweeps: int = 600, every: int = 20,
+                     seed: int = 1, wca_eps: float = 0.0, start: str = "saw", A0: float = 0.5, **sched) -> dict:
+    """Radius of gyration of N_b-bead chains (Sec. VII.A uses N_b = 10) with harmonic bonds
+    (k = 100 kT/a^2, rest length 2a), wavelets and plane waves, from self-avoiding walks
+    (start="saw": the relaxation curve) or from the ideal-chain equilibrium (start="ideal"). With
+    WCA off (theta solvent) the chains are ideal: at equilibrium their bond vectors are independent,
+    so the Boltzmann value of <R_g^2> is <b^2> (N_b^2 - 1) / (6 N_b), with <b^2> of one harmonic
+    bond; the measured plateau (each chain's average over the last third of the run, the standard
+    error from the spread over chains) is compared with it. With WCA on (good solvent) the curve is
+    reported."""
+    s = I.dilute_chains(n_chains, n_b, phi, seed=seed)
+    p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, precision=wmcd.MIXED, wca_eps=wca_eps,
+                            planewave_mode=wmcd.PLANEWAVE_PERIODIC, A0=A0, **sched)
+    pos = s.pos if start == "saw" else ideal_chains(n_chains, n_b, s.box_L, p["bond_k"], p["bond_r0"], p["kT"],
+                                                      seed=seed)
+    sim = wmcd.Simulation(p, pos, s.chain_len)
+
+    def measure():
+        # each chain rebuilt from its bond vectors taken at minimum image (a chain may straddle a
+        # face of the periodic box; its bonds are far shorter than L / 2)
+        x = sim.positions(unwrapped=True).reshape(n_chains, n_b, 3)
+        d = np.diff(x, axis=1)
+        d -= s.box_L * np.round(d / s.box_L)
+        y = np.concatenate([np.zeros((n_chains, 1, 3)), np.cumsum(d, axis=1)], axis=1)
+        c = y - y.mean(axis=1, keepdims=True)
+        return (c * c).sum(axis=2).mean(axis=1), float((d * d).sum(axis=2).mean())
+
+    samples, bonds, curve = [], [], []
+    r, b2 = measure()
+    curve.append({"sweeps": 0, "sim_time": 0.0, "rg2": float(r.mean()), "b2": b2})
+    for k in range(sweeps // every):
+        sim.sweep(every)
+        r, b2 = measure()
+        samples.append(r)
+        bonds.append(b2)
+        curve.append({"sweeps": (k + 1) * every, "sim_time": sim.stats().sim_time, "rg2": float(r.mean()), "b2": b2})
+    st = sim.stats()
+    sim.close()
+    late = np.array(samples[(2 * len(samples)) // 3:])     # last third of the run
+    per_chain = late.mean(axis=0)
+    out = {"n_chains": n_chains, "n_b": n_b, "box_L": s.box_L, "wca_eps": wca_eps, "start": start, "A0": A0,
+           "curve": curve,
+           "rg2_initial": curve[0]["rg2"], "rg2_plateau": float(per_chain.mean()),
+           "rg2_plateau_se": float(per_chain.std(ddof=1) / math.sqrt(n_chains)),
+           "bond_msd_plateau": float(np.mean(bonds[(2 * len(bonds)) // 3:])), "error_flags": st.error_flags,
+           "accept_fraction": st.accepted_total / max(1, sum(st.attempts) + st.pw_attempts)}
+    if wca_eps == 0.0:
+        b2 = ideal_bond_msd(p["bond_k"], p["bond_r0"], p["kT"])
+        out["bond_msd_ideal"] = b2
+        out["rg2_ideal"] = b2 * (n_b * n_b - 1) / (6.0 * n_b)
+        out["ratio"] = out["rg2_plateau"] / out["rg2_ideal"]
+    return out
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -178,7 +263,9 @@ def main(argv=None):
     wmcd.build()
     wmcd.load()
     rep = {"free_diffusion": free_diffusion(), "acceptance_spectra": acceptance_spectra(),
-           "cost_scaling": cost_scaling()}
+           "cost_scaling": cost_scaling(), "chain_relaxation_theta": chain_relaxation(),
+           "chain_equilibrium_theta": chain_relaxation(start="ideal"),
+           "chain_relaxation_good": chain_relaxation(wca_eps=1.0)}
     with open(a.out, "w") as f:
         json.dump(rep, f, indent=1)
     print(json.dumps(rep, indent=1))
