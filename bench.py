@@ -164,11 +164,21 @@ def profile_traffic(kernel_src_sha):
         return None
 
 
-def kernel_sha():
+def code_sha(texts):
+    """Hash of CUDA sources with // comments and blank lines removed: an edit of comments alone
+    leaves the compiled kernels, and so the hash, unchanged."""
     h = hashlib.sha256()
-    for f in ["wmcd_kernels.cu", "wmcd_device.cuh", "wmcd_internal.h"]:
-        h.update(open(os.path.join(ROOT, "paper_1611_09160_gb300", "csrc", f), "rb").read())
+    for t in texts:
+        for line in t.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()
+
+
+def kernel_sha():
+    return code_sha(open(os.path.join(ROOT, "paper_1611_09160_gb300", "csrc", f)).read()
+                    for f in ["wmcd_kernels.cu", "wmcd_device.cuh", "wmcd_internal.h"])
 
 
 def peaks():

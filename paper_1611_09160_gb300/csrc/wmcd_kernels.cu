@@ -3558,12 +3558,6 @@ __device__ __forceinline__ bool staged_block_has_work(const SimView& g, int l, i
     return false;
 }
 
-// A block serves qpb queues with one warp each, or (qpb = 1) one queue with all its warps: then
-// every warp stages a share of the region (the binary64 work of staging spreads over the SM's
-// four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue; stride =
-// shared bytes per queue. Only queues whose region holds ns_lo..ns_hi beads run: a colour phase
-// is split between a launch for ordinary regions (small staging, more warps per SM) and one for
-// the dense ones, which take disjoint queues, so the split changes nothing in the results.
 // The cooperative scratch of a block whose warps serve one queue together (none for the light
 // variant, whose blocks serve one queue per warp).
 template <bool USE>
@@ -3575,6 +3569,14 @@ __device__ __forceinline__ CoopSh* coop_scratch() {
         return nullptr;
     }
 }
+// A block serves qpb queues with one warp each, or (qpb = 1) one queue with all its warps: then
+// every warp stages a share of the region (the binary64 work of staging spreads over the SM's
+// four schedulers) and warp 0 alone runs the moves. cap = staged beads per queue; stride =
+// shared bytes per queue. Only queues whose region holds ns_lo..ns_hi beads run: a colour phase
+// is split between a launch for ordinary regions (small staging, more warps per SM) and launches
+// for the dense ones, which take disjoint queues, so the split changes nothing in the results.
+// list = 0: queue blockIdx.x * qpb + warp; list = 1 or 2: the block takes queues from that list
+// of dense regions (built by the region scan) until it is done.
 // LIGHT: a launch whose regions all fit its staging (one warp per queue): no global-memory path
 // and no cooperating warps are compiled in, which leaves fewer registers per thread.
 template <int PREC, bool LIGHT>
