@@ -3577,10 +3577,12 @@ __device__ __forceinline__ CoopSh* coop_scratch() {
 // for the dense ones, which take disjoint queues, so the split changes nothing in the results.
 // list = 0: queue blockIdx.x * qpb + warp; list = 1 or 2: the block takes queues from that list
 // of dense regions (built by the region scan) until it is done.
-// LIGHT: a launch whose regions all fit its staging (one warp per queue): no global-memory path
-// and no cooperating warps are compiled in, which leaves fewer registers per thread.
-template <int PREC, bool LIGHT>
-__global__ void __launch_bounds__(kMaxStageWarps * 32, LIGHT ? 3 : 1) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
+// VAR 0: every path. VAR 1 (light): a launch whose regions all fit its staging, one warp per
+// queue: no global-memory path and no cooperating warps are compiled in. VAR 2 (middle dense
+// tier): cooperating warps, regions that always fit, no global-memory path. The narrower
+// variants leave fewer registers per thread, so three blocks fit an SM.
+template <int PREC, int VAR>
+__global__ void __launch_bounds__(kMaxStageWarps * 32, VAR == 0 ? 1 : 3) k_colour_staged(const SimView* __restrict__ vs, int l, int colour,
                                                                         int cap, int qpb, int ncap, int stride,
                                                                         int ns_lo, int ns_hi, int list) {
     SIM_EXIT_IF(!sched_on(gv, l) || gv.precision != PREC || colour >= gv.K * gv.K * gv.K ||
@@ -3592,6 +3594,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, LIGHT ? 3 : 1) k_colour_s
     if (!sched_on(v, l) || v.precision != PREC || colour >= v.K * v.K * v.K) return;
     // sqrt(n) for the amplitude A_w = A0 lam / sqrt(n) (Eq. 29), once per block
     __shared__ double s_sqrt[kNCap + 1];
+    constexpr bool LIGHT = VAR == 1, STAGED_ONLY = VAR != 0;
     CoopSh* const X = coop_scratch<!LIGHT>();
     for (int i = threadIdx.x; i <= kNCap; i += blockDim.x) s_sqrt[i] = sqr_t((double)i);
     __syncthreads();
@@ -3642,7 +3645,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, LIGHT ? 3 : 1) k_colour_s
         int att = 0, acc = 0, def = 0, pe = 0, rechecks = 0;
         long long bu = 0, moved = 0;
         const int rs = v.rstart[q], ns = v.rcount[q];
-        if (!LIGHT && ns > cap) {
+        if (!STAGED_ONLY && ns > cap) {
             // region too full for shared memory: the global-memory path
             if (role != 0) continue;
             WarpSmem& sm = *(WarpSmem*)base;
@@ -3814,7 +3817,7 @@ __global__ void __launch_bounds__(kMaxStageWarps * 32, LIGHT ? 3 : 1) k_colour_s
 size_t staged_smem_bytes(int cap, int warps, int ncap) { return (size_t)warps * warp_stride(cap, ncap); }
 // the launch of ordinary regions: regions of at most kLightCap beads, kMaxStageWarps queues per block
 constexpr int kLightCap = 80;
-// the dense regions of a split phase: up to kMidCap beads staged by blocks small enough for two
+// the dense regions of a split phase: up to kMidCap beads staged by blocks small enough for three
 // per SM, the larger ones by blocks with the most shared memory
 constexpr int kMidCap = 512;
 // (its supports are at most its regions' kLightCap beads, so its support arrays need no more)
@@ -3855,7 +3858,7 @@ static void staged_shape(const GroupDims& g, int cap, int ncap, int* qpb, int* w
 
 // The largest dynamic shared memory each staged kernel was opened for, per device: raised
 // before a launch needs more, so that launches recorded into a graph set nothing.
-static int g_staged_smem[64][2][2];
+static int g_staged_smem[64][2][3];
 static int g_serial_smem[64][2];
 void prepare_staged(const GroupDims& g) {
     int dev = 0;
@@ -3882,7 +3885,7 @@ void prepare_staged(const GroupDims& g) {
             g_serial_smem[dev][1] = sm;
         }
     }
-    int smem = 0, smemL = 0;
+    int smem = 0, smemL = 0, smemM = 0;
     for (int i = 0; i < 2 * g.maxL; i++) {
         const int l = i < g.maxL ? i : kLevel2 + i - g.maxL;
         if (!g.coloured[l]) continue;
@@ -3892,24 +3895,33 @@ void prepare_staged(const GroupDims& g) {
         smem = std::max(smem, (int)staged_smem_bytes(cap, qpb, ncap));
         if (split_layer(g, l, cap)) {
             smemL = std::max(smemL, (int)light_smem_bytes(ncap));
+            smemM = std::max(smemM, (int)warp_stride_staged(kMidCap, ncap));
             smem = std::max(smem, (int)staged_smem_bytes(staged_cap_max(ncap), 1, ncap));
         }
     }
     if ((g.prec_mask & 1) && smem > g_staged_smem[dev][0][0]) {
-        cudaFuncSetAttribute(k_colour_staged<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_colour_staged<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         g_staged_smem[dev][0][0] = smem;
     }
     if ((g.prec_mask & 2) && smem > g_staged_smem[dev][1][0]) {
-        cudaFuncSetAttribute(k_colour_staged<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_colour_staged<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         g_staged_smem[dev][1][0] = smem;
     }
     if ((g.prec_mask & 1) && smemL > g_staged_smem[dev][0][1]) {
-        cudaFuncSetAttribute(k_colour_staged<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemL);
+        cudaFuncSetAttribute(k_colour_staged<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemL);
         g_staged_smem[dev][0][1] = smemL;
     }
     if ((g.prec_mask & 2) && smemL > g_staged_smem[dev][1][1]) {
-        cudaFuncSetAttribute(k_colour_staged<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemL);
+        cudaFuncSetAttribute(k_colour_staged<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemL);
         g_staged_smem[dev][1][1] = smemL;
+    }
+    if ((g.prec_mask & 1) && smemM > g_staged_smem[dev][0][2]) {
+        cudaFuncSetAttribute(k_colour_staged<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemM);
+        g_staged_smem[dev][0][2] = smemM;
+    }
+    if ((g.prec_mask & 2) && smemM > g_staged_smem[dev][1][2]) {
+        cudaFuncSetAttribute(k_colour_staged<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemM);
+        g_staged_smem[dev][1][2] = smemM;
     }
 }
 
@@ -3947,8 +3959,8 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         // Ordinary regions (at most kLightCap beads) on the stream, one warp per queue and small
         // staging; the dense regions (a chain's worth of beads, the longest queues of the phase)
         // at the same time on side streams, one block of cooperating warps per queue: those up to
-        // kMidCap beads in blocks small enough for two per SM, the rest with room for the largest
-        // region. The launches take disjoint queues of one colour; the dense ones run
+        // kMidCap beads by a variant without the global-memory path (three blocks per SM), the
+        // rest with room for the largest region. The launches take disjoint queues of one colour; the dense ones run
         // persistently over the lists the region scan made.
         const int qL = kMaxStageWarps;
         const dim3 gridL((nq + qL - 1) / qL, g.S);
@@ -3958,22 +3970,22 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         const size_t smemH = staged_smem_bytes(capH, 1, ncap);
         const int strideH = (int)warp_stride(capH, ncap);
         const int strideM = (int)warp_stride_staged(kMidCap, ncap);   // its regions always fit
-        const dim3 gridH(std::min(nq, sm_count()), g.S), gridM(std::min(nq, 2 * sm_count()), g.S);
+        const dim3 gridH(std::min(nq, sm_count()), g.S), gridM(std::min(nq, 3 * sm_count()), g.S);
         cudaStream_t sm_ = fj->side[0], sh_ = fj->side[1] ? fj->side[1] : fj->side[0];
         cudaEventRecord(fj->fork, s);
         cudaStreamWaitEvent(sm_, fj->fork, 0);
         if (sh_ != sm_) cudaStreamWaitEvent(sh_, fj->fork, 0);
         if (g.prec_mask & 1) {
-            k_colour_staged<0, false><<<gridM, kMaxStageWarps * 32, strideM, sm_>>>(d, l, colour, kMidCap, 1, ncap, strideM, kLightCap + 1, kMidCap, 1);
-            k_colour_staged<0, false><<<gridH, kMaxStageWarps * 32, smemH, sh_>>>(d, l, colour, capH, 1, ncap, strideH, kMidCap + 1, 1 << 30, 2);
+            k_colour_staged<0, 2><<<gridM, kMaxStageWarps * 32, strideM, sm_>>>(d, l, colour, kMidCap, 1, ncap, strideM, kLightCap + 1, kMidCap, 1);
+            k_colour_staged<0, 0><<<gridH, kMaxStageWarps * 32, smemH, sh_>>>(d, l, colour, capH, 1, ncap, strideH, kMidCap + 1, 1 << 30, 2);
         }
         if (g.prec_mask & 2) {
-            k_colour_staged<1, false><<<gridM, kMaxStageWarps * 32, strideM, sm_>>>(d, l, colour, kMidCap, 1, ncap, strideM, kLightCap + 1, kMidCap, 1);
-            k_colour_staged<1, false><<<gridH, kMaxStageWarps * 32, smemH, sh_>>>(d, l, colour, capH, 1, ncap, strideH, kMidCap + 1, 1 << 30, 2);
+            k_colour_staged<1, 2><<<gridM, kMaxStageWarps * 32, strideM, sm_>>>(d, l, colour, kMidCap, 1, ncap, strideM, kLightCap + 1, kMidCap, 1);
+            k_colour_staged<1, 0><<<gridH, kMaxStageWarps * 32, smemH, sh_>>>(d, l, colour, capH, 1, ncap, strideH, kMidCap + 1, 1 << 30, 2);
         }
         const int ncL = light_ncap(ncap);
-        if (g.prec_mask & 1) k_colour_staged<0, true><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
-        if (g.prec_mask & 2) k_colour_staged<1, true><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
+        if (g.prec_mask & 1) k_colour_staged<0, 1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
+        if (g.prec_mask & 2) k_colour_staged<1, 1><<<gridL, qL * 32, smemL, s>>>(d, l, colour, kLightCap, qL, ncL, strideL, 0, kLightCap, 0);
         cudaEventRecord(fj->join[0], sm_);
         cudaStreamWaitEvent(s, fj->join[0], 0);
         if (sh_ != sm_) {
@@ -3983,8 +3995,8 @@ int launch_colour_staged(const SimView* d, const GroupDims& g, int l, int colour
         return 4 + 3 * np;
     }
     // one launch per precision; each returns at once for simulations of the other precision
-    if (g.prec_mask & 1) k_colour_staged<0, false><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
-    if (g.prec_mask & 2) k_colour_staged<1, false><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
+    if (g.prec_mask & 1) k_colour_staged<0, 0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
+    if (g.prec_mask & 2) k_colour_staged<1, 0><<<grid, warps * 32, smem, s>>>(d, l, colour, cap, qpb, ncap, stride, 0, 1 << 30, 0);
     return 4 + np;
 
 }
