@@ -16,6 +16,9 @@ closed form of the paper, or reports the spectra the paper plots:
 * ``chain_relaxation``: the radius of gyration of N_b = 10 chains relaxing from self-avoiding
   walks (Sec. VII.A), and in theta solvent (no WCA), started from the ideal-chain equilibrium,
   its plateau against the exact ideal-chain value (the dynamics must keep that equilibrium).
+* ``chain_diffusivity``: the centre-of-mass diffusion constant D(N_b) of dilute chains in good
+  and theta solvent in the paper's reduced units (Sec. VII.B), with the periodic-image
+  correction of Eq. 60, and the exponent of D ~ N_b^-nu.
 
 ``python -m paper_1611_09160_gb300.validate --out report.json`` runs them all at full size.
 """
@@ -255,6 +258,116 @@ def chain_relaxation(n_chains: int = 20_000, n_b: int = 10, phi: float = 1e-3, s
     return out
 
 
+# Sec. II's reduced units (length 2^(1/6) sigma, energy eps), chosen there to match the polymer
+# systems of the benchmarks the paper compares with
+SIGMA_BAR = 2.0 ** (-1.0 / 6.0)
+K_FENE_BAR = 7.0 * 2.0 ** (1.0 / 3.0)
+R0_FENE_BAR = 2.0 * 2.0 ** (-1.0 / 6.0)
+LMIN_BAR = 0.700
+KT_BAR = 1.2
+R0_THETA_BAR = 0.9691          # Sec. VII.B: the harmonic rest length matching the good solvent's mean bond
+BOND_START_BAR = 0.97          # bond length of the generated starting walks, near both solvents' mean
+PERIODIC_SELF = 2.837          # Eq. 60: periodic images lower the self-mobility by 2.837 a / L
+
+
+def paper_unit_params(solvent: str) -> dict:
+    """Potential and wavelet parameters of Sec. II in its reduced units. Good solvent: FENE bonds
+    (Eq. 1) and WCA (Eq. 2) between all beads. Theta solvent (Sec. VII.B): WCA off and the bond
+    (3/2) k_FENE (r - r0)^2, i.e. k = 3 k_FENE in the library's harmonic form (k/2)(r - r0)^2."""
+    base = dict(lambda_min=LMIN_BAR, kT=KT_BAR, wca_sigma=SIGMA_BAR)
+    if solvent == "good":
+        return dict(base, wca_eps=1.0, bond_type=wmcd.BOND_FENE, bond_k=K_FENE_BAR, fene_R0=R0_FENE_BAR)
+    if solvent == "theta":
+        return dict(base, wca_eps=0.0, bond_type=wmcd.BOND_HARMONIC, bond_k=3.0 * K_FENE_BAR,
+                    bond_r0=R0_THETA_BAR)
+    raise ValueError(f"solvent must be 'good' or 'theta', not {solvent!r}")
+
+
+def com_diffusion(com, times, max_lag: int | None = None, groups: int = 8) -> dict:
+    """D = <|dR_CoM|^2> / (6 t) (Sec. VII.B) from sampled centre-of-mass trajectories, over every
+    time origin. ``com`` is (samples, chains, 3), in coordinates that are continuous in time;
+    ``times`` the simulated time of each sample. For each lag of m = 1..max_lag samples: the mean
+    square displacement over all origins and chains, and the mean time lag t_m; D is the
+    least-squares slope through the origin of MSD against 6 t_m. Its standard error is the spread
+    of the same estimate over ``groups`` disjoint sets of chains (motion that one large wavelet
+    gives to several chains at once correlates them, which this error does not include)."""
+    com = np.asarray(com, dtype=np.float64)
+    times = np.asarray(times, dtype=np.float64)
+    n_s, n_c = com.shape[0], com.shape[1]
+    if n_s < 2 or times.shape != (n_s,):
+        raise ValueError("need at least two samples and one time per sample")
+    max_lag = n_s - 1 if max_lag is None else max(1, min(int(max_lag), n_s - 1))
+    lags = range(1, max_lag + 1)
+    t = np.array([float((times[m:] - times[:-m]).mean()) for m in lags])
+
+    def slope(c):
+        msd = np.array([float(((c[m:] - c[:-m]) ** 2).sum(axis=2).mean()) for m in lags])
+        return float((msd * t).sum() / (6.0 * (t * t).sum())), msd
+
+    D, msd = slope(com)
+    parts = [p for p in np.array_split(np.arange(n_c), min(groups, n_c)) if len(p)]
+    Dg = np.array([slope(com[:, p])[0] for p in parts])
+    se = float(Dg.std(ddof=1) / math.sqrt(len(Dg))) if len(Dg) > 1 else float("nan")
+    return {"D": D, "D_se": se, "lag_time": t.tolist(), "msd": msd.tolist()}
+
+
+def fit_exponent(n, D, se) -> tuple[float, float]:
+    """nu and its standard error in D ~ N^-nu: weighted least squares of ln D on ln N, the weight
+    of each point (D / se)^2."""
+    x = np.log(np.asarray(n, dtype=np.float64))
+    y = np.log(np.asarray(D, dtype=np.float64))
+    w = (np.asarray(D, dtype=np.float64) / np.asarray(se, dtype=np.float64)) ** 2
+    xm = (w * x).sum() / w.sum()
+    ym = (w * y).sum() / w.sum()
+    sxx = (w * (x - xm) ** 2).sum()
+    b = (w * (x - xm) * (y - ym)).sum() / sxx
+    return float(-b), float(math.sqrt(1.0 / sxx))
+
+
+def chain_diffusivity(solvent: str = "good", n_bs=(8, 16, 32), beads: int = 32_768, chain_gap: float = 25.0,
+                      sweeps: int = 600, every: int = 20, max_lag: int = 10, seed: int = 1, A0: float = 0.5,
+                      **sched) -> dict:
+    """Centre-of-mass diffusion of dilute chains of N_b beads (Sec. VII.B) in Sec. II's reduced
+    units, wavelets and plane waves, mixed precision. For each N_b, beads / N_b self-avoiding walks
+    (bond 0.97, no two beads closer than sigma) in a periodic box giving each chain a cube of side
+    ``chain_gap``; the chains' centres of mass sampled every ``every`` sweeps from the unwrapped
+    positions; D by ``com_diffusion``, then corrected for the periodic images by Eq. 60:
+    D_inf = D_L + 2.837 D_0 a / L, with D_0 = a^2 / 6 (tau units) the diffusivity of one free sphere
+    and a = lambda_min / lambda_a (Eq. 42). D / D_0 is the bracket of the paper's series for D: the
+    free-draining (Rouse) value is 1 / N_b; hydrodynamic interactions raise it. nu is fitted to
+    D_inf ~ N_b^-nu (Zimm scaling: 0.588 in good, 0.5 in theta solvent; free draining: 1)."""
+    a = LMIN_BAR / LAMBDA_A
+    D0 = a * a / 6.0
+    rows = []
+    for n_b in n_bs:
+        n_chains = max(2, beads // n_b)
+        L = chain_gap * n_chains ** (1.0 / 3.0)
+        s = I.make_system([n_b] * n_chains, 0, L, seed, bond=BOND_START_BAR, min_dist=SIGMA_BAR)
+        p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, precision=wmcd.MIXED, A0=A0,
+                                planewave_mode=wmcd.PLANEWAVE_PERIODIC, **paper_unit_params(solvent), **sched)
+        sim = wmcd.Simulation(p, s.pos, s.chain_len)
+        t0 = time.perf_counter()
+        com, times = [], []
+        for k in range(sweeps // every + 1):
+            if k:
+                sim.sweep(every)
+            com.append(sim.positions(unwrapped=True).reshape(n_chains, n_b, 3).mean(axis=1))
+            times.append(sim.stats().sim_time)
+        wall = time.perf_counter() - t0
+        st = sim.stats()
+        sim.close()
+        r = com_diffusion(np.stack(com), np.array(times), max_lag=max_lag)
+        corr = PERIODIC_SELF * D0 * a / L
+        rows.append({"n_b": n_b, "n_chains": n_chains, "box_L": L, "sim_time": times[-1], "wall_s": wall,
+                     "D_L": r["D"], "D_se": r["D_se"], "D_inf": r["D"] + corr, "periodic_correction": corr,
+                     "D_over_D0": (r["D"] + corr) / D0, "rouse_ratio": n_b * (r["D"] + corr) / D0,
+                     "lag_time": r["lag_time"], "msd": r["msd"], "error_flags": st.error_flags,
+                     "accept_fraction": st.accepted_total / max(1, sum(st.attempts) + st.pw_attempts)})
+    nu, nu_se = fit_exponent([r["n_b"] for r in rows], [r["D_inf"] for r in rows], [r["D_se"] for r in rows])
+    return {"solvent": solvent, "a": a, "D0": D0, "A0": A0, "rows": rows, "nu": nu, "nu_se": nu_se,
+            "nu_zimm": 0.588 if solvent == "good" else 0.5}
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -265,7 +378,9 @@ def main(argv=None):
     rep = {"free_diffusion": free_diffusion(), "acceptance_spectra": acceptance_spectra(),
            "cost_scaling": cost_scaling(), "chain_relaxation_theta": chain_relaxation(),
            "chain_equilibrium_theta": chain_relaxation(start="ideal"),
-           "chain_relaxation_good": chain_relaxation(wca_eps=1.0)}
+           "chain_relaxation_good": chain_relaxation(wca_eps=1.0),
+           "chain_diffusivity_good": chain_diffusivity("good", n_bs=(8, 16, 32, 64), sweeps=2000),
+           "chain_diffusivity_theta": chain_diffusivity("theta", n_bs=(8, 16, 32, 64), sweeps=2000)}
     with open(a.out, "w") as f:
         json.dump(rep, f, indent=1)
     print(json.dumps(rep, indent=1))
