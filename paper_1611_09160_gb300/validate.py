@@ -205,18 +205,35 @@ def ideal_chains(n_chains: int, n_b: int, box_L: float, k: float, r0: float, kT:
 
 
 def chain_relaxation(n_chains: int = 20_000, n_b: int = 10, phi: float = 1e-3, sweeps: int = 600, every: int = 20,
-                     seed: int = 1, wca_eps: float = 0.0, start: str = "saw", A0: float = 0.5, **sched) -> dict:
-    """Radius of gyration of N_b-bead chains (Sec. VII.A uses N_b = 10) with harmonic bonds
-    (k = 100 kT/a^2, rest length 2a), wavelets and plane waves, from self-avoiding walks
-    (start="saw": the relaxation curve) or from the ideal-chain equilibrium (start="ideal"). With
-    WCA off (theta solvent) the chains are ideal: at equilibrium their bond vectors are independent,
-    so the Boltzmann value of <R_g^2> is <b^2> (N_b^2 - 1) / (6 N_b), with <b^2> of one harmonic
-    bond; the measured plateau (each chain's average over the last third of the run, the standard
-    error from the spread over chains) is compared with it. With WCA on (good solvent) the curve is
-    reported."""
-    s = I.dilute_chains(n_chains, n_b, phi, seed=seed)
-    p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, precision=wmcd.MIXED, wca_eps=wca_eps,
-                            planewave_mode=wmcd.PLANEWAVE_PERIODIC, A0=A0, **sched)
+                     seed: int = 1, wca_eps: float = 0.0, start: str = "saw", A0: float = 0.5,
+                     paper_units: bool = False, bond0: float = 0.97, chain_gap: float = 25.0, **sched) -> dict:
+    """Radius of gyration of N_b-bead chains (Sec. VII.A uses N_b = 10), wavelets and plane waves.
+
+    Bench units (default): harmonic bonds (k = 100 kT/a^2, rest length 2a), from self-avoiding
+    walks (start="saw": the relaxation curve) or from the ideal-chain equilibrium (start="ideal").
+    With WCA off (theta solvent) the chains are ideal: at equilibrium their bond vectors are
+    independent, so the Boltzmann value of <R_g^2> is <b^2> (N_b^2 - 1) / (6 N_b), with <b^2> of one
+    harmonic bond; the measured plateau (each chain's average over the last third of the run, the
+    standard error from the spread over chains) is compared with it. With WCA on (good solvent)
+    the curve is reported.
+
+    paper_units=True: the system of Sec. VII.A in Sec. II's reduced units, FENE bonds and WCA
+    between all beads (good solvent), from self-avoiding walks whose bonds start at ``bond0``,
+    compressed or stretched against the equilibrium mean of about 0.98, one chain per cube of side
+    ``chain_gap``. The curve and the plateau are reported (the paper compares them with a value
+    from another study that its text does not give)."""
+    if paper_units:
+        if start != "saw":
+            raise ValueError("in paper units the chains start from self-avoiding walks of bond bond0")
+        L = chain_gap * n_chains ** (1.0 / 3.0)
+        s = I.make_system([n_b] * n_chains, 0, L, seed, bond=bond0, min_dist=0.999 * min(SIGMA_BAR, bond0))
+        p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, precision=wmcd.MIXED,
+                                planewave_mode=wmcd.PLANEWAVE_PERIODIC, A0=A0, **paper_unit_params("good"), **sched)
+        wca_eps = p["wca_eps"]
+    else:
+        s = I.dilute_chains(n_chains, n_b, phi, seed=seed)
+        p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, precision=wmcd.MIXED, wca_eps=wca_eps,
+                                planewave_mode=wmcd.PLANEWAVE_PERIODIC, A0=A0, **sched)
     pos = s.pos if start == "saw" else ideal_chains(n_chains, n_b, s.box_L, p["bond_k"], p["bond_r0"], p["kT"],
                                                       seed=seed)
     sim = wmcd.Simulation(p, pos, s.chain_len)
@@ -245,12 +262,13 @@ def chain_relaxation(n_chains: int = 20_000, n_b: int = 10, phi: float = 1e-3, s
     late = np.array(samples[(2 * len(samples)) // 3:])     # last third of the run
     per_chain = late.mean(axis=0)
     out = {"n_chains": n_chains, "n_b": n_b, "box_L": s.box_L, "wca_eps": wca_eps, "start": start, "A0": A0,
+           "paper_units": paper_units, "bond0": bond0 if paper_units else p["bond_r0"],
            "curve": curve,
            "rg2_initial": curve[0]["rg2"], "rg2_plateau": float(per_chain.mean()),
            "rg2_plateau_se": float(per_chain.std(ddof=1) / math.sqrt(n_chains)),
            "bond_msd_plateau": float(np.mean(bonds[(2 * len(bonds)) // 3:])), "error_flags": st.error_flags,
            "accept_fraction": st.accepted_total / max(1, sum(st.attempts) + st.pw_attempts)}
-    if wca_eps == 0.0:
+    if wca_eps == 0.0 and not paper_units:
         b2 = ideal_bond_msd(p["bond_k"], p["bond_r0"], p["kT"])
         out["bond_msd_ideal"] = b2
         out["rg2_ideal"] = b2 * (n_b * n_b - 1) / (6.0 * n_b)

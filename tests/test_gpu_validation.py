@@ -94,3 +94,22 @@ def test_chain_diffusivity_follows_zimm_scaling_in_both_solvents():
         rouse = [row["rouse_ratio"] for row in r["rows"]]
         assert rouse[0] > 1.5 and rouse[0] < rouse[1] < rouse[2]
         assert 0.45 < r["nu"] < 0.7, r["nu"]
+
+
+def test_chain_relaxation_in_paper_units_from_compressed_and_stretched_bonds():
+    """Sec. VII.A in the reduced units of Sec. II: 10-bead chains with FENE bonds and WCA between
+    all beads (good solvent), started with every bond compressed (0.8) or stretched (1.4) against
+    the equilibrium mean of about 0.98. The compressed chains swell, the stretched ones shrink, and
+    after 2,400 sweeps (about 145 tau) the two mean-square radii of gyration are within a tenth of
+    their starting gap of each other; the bonds have reached one mean-square length in both."""
+    kw = dict(n_chains=2000, n_b=10, sweeps=2400, every=100, seed=2, paper_units=True)
+    up = V.chain_relaxation(bond0=0.8, **kw)
+    down = V.chain_relaxation(bond0=1.4, **kw)
+    for r in (up, down):
+        print({k: v for k, v in r.items() if k != "curve"}, [(c["sweeps"], round(c["rg2"], 4)) for c in r["curve"]])
+        assert r["error_flags"] == 0
+    gap0 = down["rg2_initial"] - up["rg2_initial"]
+    end_up, end_down = up["curve"][-1]["rg2"], down["curve"][-1]["rg2"]
+    assert up["rg2_initial"] < end_up and end_down < down["rg2_initial"]
+    assert abs(end_down - end_up) < 0.1 * gap0
+    assert up["bond_msd_plateau"] == pytest.approx(down["bond_msd_plateau"], rel=0.01)
