@@ -15,7 +15,8 @@ closed form of the paper, or reports the spectra the paper plots:
   algorithmic count against N (1 + c ln(L / (2 lmin))).
 * ``chain_relaxation``: the radius of gyration of N_b = 10 chains relaxing from self-avoiding
   walks (Sec. VII.A), and in theta solvent (no WCA), started from the ideal-chain equilibrium,
-  its plateau against the exact ideal-chain value (the dynamics must keep that equilibrium).
+  its plateau against the exact ideal-chain value (the dynamics must keep that equilibrium); and
+  the paper's own FENE + WCA chains in its reduced units from compressed and stretched bonds.
 * ``chain_diffusivity``: the centre-of-mass diffusion constant D(N_b) of dilute chains in good
   and theta solvent in the paper's reduced units (Sec. VII.B), with the periodic-image
   correction of Eq. 60, and the exponent of D ~ N_b^-nu.
@@ -397,6 +398,8 @@ def main(argv=None):
            "cost_scaling": cost_scaling(), "chain_relaxation_theta": chain_relaxation(),
            "chain_equilibrium_theta": chain_relaxation(start="ideal"),
            "chain_relaxation_good": chain_relaxation(wca_eps=1.0),
+           "chain_relaxation_paper_compressed": chain_relaxation(sweeps=6000, every=100, paper_units=True, bond0=0.8),
+           "chain_relaxation_paper_stretched": chain_relaxation(sweeps=6000, every=100, paper_units=True, bond0=1.4),
            "chain_diffusivity_good": chain_diffusivity("good", n_bs=(8, 16, 32, 64), sweeps=2000),
            "chain_diffusivity_theta": chain_diffusivity("theta", n_bs=(8, 16, 32, 64), sweeps=2000)}
     with open(a.out, "w") as f:
