@@ -75,6 +75,7 @@ def _load():
         "oracle_trace_layer": ([P, ctypes.c_int, P, P, I64], I64),
         "oracle_trace_pw": ([P, P, P, I64], I64),
         "oracle_trace_du": ([P, ctypes.c_int, P, I64], I64),
+        "oracle_trace_lam": ([P, ctypes.c_int, P, I64], I64),
         "oracle_philox": ([P, P, P], None),
         "oracle_phitilde": ([D], D),
         "oracle_moment": ([ctypes.c_int], D),
@@ -188,6 +189,13 @@ class Oracle:
         cap = 4 * self.n + 16
         out = np.zeros(cap)
         m = self._lib.oracle_trace_du(self.h, int(l), _ptr(out), cap)
+        return out[:m].copy()
+
+    def trace_lam(self, l: int):
+        """The lambda each wavelet slot of layer l used in the last sweep (0: not attempted)."""
+        cap = 4 * self.n + 16
+        out = np.zeros(cap)
+        m = self._lib.oracle_trace_lam(self.h, int(l), _ptr(out), cap)
         return out[:m].copy()
 
     def trace_pw(self):

@@ -486,7 +486,8 @@ struct Sim {
     std::vector<std::vector<uint8_t>> tr_out;
     std::vector<std::vector<int32_t>> tr_n;
     std::vector<std::vector<double>> tr_du;
-    double last_du = 0.0;
+    std::vector<std::vector<double>> tr_lam;    // the lambda each slot's attempt used (its own or a carry)
+    double last_du = 0.0, last_lam = 0.0;
     std::vector<uint8_t> tr_pw_out;
     std::vector<int32_t> tr_pw_mode;
     // scratch
@@ -723,6 +724,7 @@ static int wavelet_attempt(Sim& s, int l, uint32_t j, int64_t i, double lam, con
                            int ncap) {
     const uint64_t sw = s.sweep;
     s.last_du = 0.0;
+    s.last_lam = lam;
     // centre: b = r_i + lam V, V uniform in the unit ball (wrapped into the box); or uniform in
     // the box
     double V[3], b[3];
@@ -828,6 +830,7 @@ static void run_layer(Sim& s, int l) {
     s.tr_out[l].assign(M, 0);
     s.tr_n[l].assign(M, 0);
     s.tr_du[l].assign(M, 0.0);
+    s.tr_lam[l].assign(M, 0.0);
     std::vector<int64_t> serial;
     // flags: 4 = deferred from the first colouring, 8 = deferred from the second as well
     bool second = false;
@@ -835,6 +838,7 @@ static void run_layer(Sim& s, int l) {
         s.tr_out[l][j] = (uint8_t)((r == ACCEPT ? 1 : 2) | flags);
         s.tr_n[l][j] = n;
         s.tr_du[l][j] = s.last_du;
+        s.tr_lam[l][j] = s.last_lam;
         s.st.attempts[l]++;
         s.st.bead_updates += n;
         if (r == ACCEPT) { s.st.accepts[l]++; s.st.accepted_total++; s.st.moved_beads += n; }
@@ -1321,6 +1325,7 @@ static int setup(Sim& s, const OParams* p, const double* pos, const int32_t* cha
     s.tr_out.resize(nL);
     s.tr_n.resize(nL);
     s.tr_du.resize(nL);
+    s.tr_lam.resize(nL);
     // time per accepted move: Eq. 57 with plane waves, Eq. 34 without (M4/(2pi)^3 = 1/105)
     double A02 = P.A0 * P.A0, la2 = LAMBDA_A * LAMBDA_A;
     if (P.planewave_mode != 0) s.dt_move = (6.0 * A02 * la2) / (105.0 * (double)s.N);
@@ -1401,6 +1406,15 @@ int64_t oracle_trace_du(void* h, int l, double* out, int64_t cap) {
     if (l < 0 || l >= (int)s.layers.size()) return -1;
     int64_t M = (int64_t)s.tr_du[l].size();
     for (int64_t j = 0; j < M && j < cap; j++) out[j] = s.tr_du[l][j];
+    return M;
+}
+// lambda used by each wavelet slot's attempt in the last sweep (a carried one after a rejection,
+// Appendix D parameter recycling); 0 for a slot not attempted
+int64_t oracle_trace_lam(void* h, int l, double* out, int64_t cap) {
+    Sim& s = *(Sim*)h;
+    if (l < 0 || l >= (int)s.layers.size()) return -1;
+    int64_t M = (int64_t)s.tr_lam[l].size();
+    for (int64_t j = 0; j < M && j < cap; j++) out[j] = s.tr_lam[l][j];
     return M;
 }
 int64_t oracle_trace_pw(void* h, uint8_t* out, int32_t* mode, int64_t cap) {

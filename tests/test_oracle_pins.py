@@ -855,3 +855,50 @@ def test_uniform_centres_are_uniform_and_empty_balls_still_count():
     out, n = o.trace_layer(0)
     assert np.mean(n == 0) > 0.9
     assert st.accepted_total == sum(st.attempts)          # free beads: every move accepted (Metropolis)
+
+
+# ---- wavelet parameter recycling (Appendix D) ----------------------------------------------
+
+def _accepted_and_attempted_lambda(n_chains, grid0, sweeps):
+    """lambda of every accepted and every attempted layer-0 wavelet move of dense chains
+    (volume fraction 0.15, A0 = 1: acceptance about 0.2, falling across the band)."""
+    s = I.make_system([16] * n_chains, 0, I.box_for_volume_fraction(16 * n_chains, 0.15), seed=4)
+    L = s.box_L
+    p = params(n_beads=s.n_beads, box_L=L, lambda_max=L / 2, A0=1.0, bond_type=1, bond_k=100.0, wca_eps=1.0,
+               grid_f=int(L / 2.3), seed=9, grid_layer=[grid0] + [0] * 15)
+    o = O.Oracle(p, s.pos, s.chain_len)
+    acc, att, deferred = [], [], 0
+    for _ in range(sweeps):
+        o.sweep(1)
+        out, _ = o.trace_layer(0)
+        lam = o.trace_lam(0)
+        done = (out & 3) != 0
+        acc.append(lam[(out & 3) == 1])
+        att.append(lam[done])
+        deferred += int(((out & 4) != 0).sum())
+    o.close()
+    att = np.concatenate(att)
+    return np.concatenate(acc), att, deferred / len(att), p["lambda_min"]
+
+
+@pytest.mark.parametrize("n_chains,grid0,sweeps", [(64, 0, 40), (192, 2, 10)])
+def test_wavelet_lambda_recycling_keeps_the_accepted_law(n_chains, grid0, sweeps):
+    """Appendix D, parameter recycling: a rejected wavelet's lambda is used again by the next
+    attempt until it is accepted, so every drawn lambda ends in exactly one accepted move and the
+    accepted lambdas follow the drawn law (Eq. 32 on the layer's band) however strongly the
+    acceptance depends on lambda; the attempts lean towards the lambdas that are rejected more.
+    Serial schedule, and a coloured layer 0 whose carries stay in their queues across sweeps
+    (with deferrals rare: a deferred slot runs its own lambda or the serial carry)."""
+    acc, att, deferred, lo = _accepted_and_attempted_lambda(n_chains, grid0, sweeps)
+    hi = 2 * lo
+    F = lambda x: (lo ** -3 - x ** -3) / (lo ** -3 - hi ** -3)
+    assert len(acc) > 4000 and np.all((att >= lo) & (att < hi))
+    # the acceptance per attempt falls across the band by more than half: without recycling the
+    # accepted lambdas would lean to the low end by that much
+    q_att = np.floor(F(att) * 4).astype(int)
+    q_acc = np.floor(F(acc) * 4).astype(int)
+    pacc = [(q_acc == k).sum() / (q_att == k).sum() for k in range(4)]
+    assert pacc[0] > 1.8 * pacc[3]
+    assert stats.kstest(acc, F).pvalue > 1e-3
+    assert stats.kstest(att, F).pvalue < 1e-9
+    assert deferred < 0.01
