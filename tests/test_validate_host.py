@@ -74,3 +74,48 @@ def test_paper_units_of_the_two_solvents():
     assert V.LMIN_BAR / V.LAMBDA_A == pytest.approx(0.3023, abs=1e-4)
     with pytest.raises(ValueError):
         V.paper_unit_params("poor")
+
+
+class _OracleEngine:
+    """The oracle behind the Simulation interface the workloads use (sweep, positions, stats,
+    close), so their host code runs on the CPU at a small size."""
+
+    def __init__(self, params, pos, chain_len):
+        import oracle
+        self.o = oracle.Oracle(params, pos, chain_len)
+
+    def sweep(self, n):
+        self.o.sweep(n)
+
+    def positions(self, unwrapped=False):
+        return self.o.positions(unwrapped=unwrapped)
+
+    def stats(self):
+        import types
+        s = self.o.stats()
+        ns = types.SimpleNamespace(**{k: getattr(s, k) for k, _ in s._fields_})
+        ns.attempts = list(s.attempts)
+        ns.error_flags = 0
+        return ns
+
+    def close(self):
+        self.o.close()
+
+
+def test_chain_workloads_host_code_on_a_stand_in_engine(monkeypatch):
+    monkeypatch.setattr(wmcd, "Simulation", _OracleEngine)
+    r = V.chain_diffusivity("theta", n_bs=(4, 8), beads=192, sweeps=60, every=10, max_lag=3, seed=2)
+    assert [row["n_b"] for row in r["rows"]] == [4, 8]
+    for row in r["rows"]:
+        assert row["n_chains"] == 192 // row["n_b"]
+        assert row["sim_time"] > 0 and row["D_L"] > 0 and np.isfinite(row["D_se"])
+        assert len(row["msd"]) == 3 and row["D_inf"] > row["D_L"]
+        assert row["periodic_correction"] == pytest.approx(V.PERIODIC_SELF * r["D0"] * r["a"] / row["box_L"])
+    assert np.isfinite(r["nu"]) and r["nu_zimm"] == 0.5
+    up = V.chain_relaxation(n_chains=12, n_b=10, sweeps=60, every=20, seed=2, paper_units=True, bond0=0.8)
+    assert up["paper_units"] and up["wca_eps"] == 1.0 and len(up["curve"]) == 4
+    # every bond starts at 0.8: the walk's bonds are exactly that long
+    assert up["curve"][0]["b2"] == pytest.approx(0.64, rel=1e-9)
+    assert up["curve"][-1]["b2"] > 0.64 and "rg2_ideal" not in up
+    with pytest.raises(ValueError):
+        V.chain_relaxation(n_chains=2, n_b=10, sweeps=10, every=10, paper_units=True, start="ideal")
