@@ -343,14 +343,16 @@ def fit_exponent(n, D, se) -> tuple[float, float]:
     return float(-b), float(math.sqrt(1.0 / sxx))
 
 
-def chain_diffusivity(solvent: str = "good", n_bs=(8, 16, 32), beads: int = 32_768, chain_gap: float = 25.0,
+def chain_diffusivity(solvent: str = "good", n_bs=(8, 16, 32), beads: int = 32_768, bead_gap: float = 8.0,
                       sweeps: int = 600, every: int = 20, max_lag: int = 10, seed: int = 1, A0: float = 0.5,
                       **sched) -> dict:
     """Centre-of-mass diffusion of dilute chains of N_b beads (Sec. VII.B) in Sec. II's reduced
     units, wavelets and plane waves, mixed precision. For each N_b, beads / N_b self-avoiding walks
-    (bond 0.97, no two beads closer than sigma) in a periodic box giving each chain a cube of side
-    ``chain_gap``; the chains' centres of mass sampled every ``every`` sweeps from the unwrapped
-    positions; D by ``com_diffusion``, then corrected for the periodic images by Eq. 60:
+    (bond 0.97, no two beads closer than sigma) in one periodic box of side bead_gap * beads^(1/3)
+    for every N_b, so the bead density is the same at every chain length (the wavelet amplitude
+    A0 lambda / sqrt(n) of Eq. 29 counts every bead in the ball, the other chains' included). The
+    chains' centres of mass are sampled every ``every`` sweeps from the unwrapped positions; D by
+    ``com_diffusion``, then corrected for the periodic images by Eq. 60:
     D_inf = D_L + 2.837 D_0 a / L, with D_0 = a^2 / 6 (tau units) the diffusivity of one free sphere
     and a = lambda_min / lambda_a (Eq. 42). D / D_0 is the bracket of the paper's series for D: the
     free-draining (Rouse) value is 1 / N_b; hydrodynamic interactions raise it. nu is fitted to
@@ -360,7 +362,7 @@ def chain_diffusivity(solvent: str = "good", n_bs=(8, 16, 32), beads: int = 32_7
     rows = []
     for n_b in n_bs:
         n_chains = max(2, beads // n_b)
-        L = chain_gap * n_chains ** (1.0 / 3.0)
+        L = bead_gap * beads ** (1.0 / 3.0)
         s = I.make_system([n_b] * n_chains, 0, L, seed, bond=BOND_START_BAR, min_dist=SIGMA_BAR)
         p = wmcd.default_params(s.n_beads, s.box_L, seed=seed, precision=wmcd.MIXED, A0=A0,
                                 planewave_mode=wmcd.PLANEWAVE_PERIODIC, **paper_unit_params(solvent), **sched)

@@ -104,7 +104,7 @@ class _OracleEngine:
 
 def test_chain_workloads_host_code_on_a_stand_in_engine(monkeypatch):
     monkeypatch.setattr(wmcd, "Simulation", _OracleEngine)
-    r = V.chain_diffusivity("theta", n_bs=(4, 8), beads=192, sweeps=60, every=10, max_lag=3, seed=2)
+    r = V.chain_diffusivity("theta", n_bs=(4, 8), beads=192, bead_gap=12.0, sweeps=60, every=10, max_lag=3, seed=2)
     assert [row["n_b"] for row in r["rows"]] == [4, 8]
     for row in r["rows"]:
         assert row["n_chains"] == 192 // row["n_b"]
